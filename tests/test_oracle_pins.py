@@ -1,0 +1,525 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a published
+vector, a closed form, a hand-derived optimum, brute force on a tiny problem,
+an optimality condition evaluated independently, or an invariant the paper
+states.  A dropped term, a wrong sign or a transposed index in the oracle
+fails at least one of them.
+"""
+
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    rows = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                parts = line.split()
+                rows.setdefault(parts[0], {})[parts[1]] = [float(x) for x in parts[2:]]
+    return rows
+
+
+def _dense_objective(X, y, loss, lam, w):
+    t = X @ w
+    if loss == "squared":
+        f = 0.5 * (y - t) ** 2
+    else:
+        f = np.logaddexp(0.0, -y * t)
+    return f.mean() + lam * np.abs(w).sum()
+
+
+def _dense_grad(X, y, loss, w):
+    t = X @ w
+    d = (t - y) if loss == "squared" else -y / (1.0 + np.exp(y * t))
+    return X.T @ d / X.shape[0]
+
+
+# --- selection randomness -------------------------------------------------------
+
+def test_splitmix64_published_vectors():
+    with open(os.path.join(GOLDEN, "splitmix64_seed0.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    for idx, hexval in rows:
+        assert oracle.splitmix64(0, int(idx)) == int(hexval, 16)
+
+
+def test_permutation_sorts_the_keys():
+    for seed, epoch, m in [(0, 0, 1), (7, 3, 257), (2**63 + 5, 11, 5000)]:
+        perm = oracle.permutation(seed, epoch, m)
+        assert sorted(perm.tolist()) == list(range(m))
+        s = oracle.splitmix64(seed, epoch)
+        keys = [(oracle.splitmix64(s, i) >> 32, i) for i in range(m)]
+        assert [i for _, i in sorted(keys)] == perm.tolist()
+    assert not np.array_equal(oracle.permutation(1, 0, 100), oracle.permutation(1, 1, 100))
+
+
+# --- losses and the step -------------------------------------------------------
+
+@pytest.mark.parametrize("loss", ["squared", "logistic"])
+def test_dloss_is_the_derivative_in_t(loss):
+    h = 1e-5
+    for y in (-1.0, 1.0, 0.3):
+        if loss == "logistic" and abs(y) != 1.0:
+            continue
+        for t in (-30.0, -2.0, -0.1, 0.0, 0.7, 5.0, 40.0):
+            fd = (oracle.loss(loss, y, t + h) - oracle.loss(loss, y, t - h)) / (2 * h)
+            assert oracle.dloss(loss, y, t) == pytest.approx(fd, rel=1e-7, abs=1e-10)
+
+
+def test_beta_bounds_the_second_derivative():
+    # Section 3.2: beta = 1 (squared) and 1/4 (logistic), and it is the supremum.
+    assert oracle.beta("squared") == 1.0
+    assert oracle.beta("logistic") == 0.25
+    h = 1e-4
+    ts = np.linspace(-20, 20, 4001)
+    for loss in ("squared", "logistic"):
+        d2 = [(oracle.dloss(loss, 1.0, t + h) - oracle.dloss(loss, 1.0, t - h)) / (2 * h) for t in ts]
+        assert max(d2) <= oracle.beta(loss) + 1e-7
+        assert max(d2) >= oracle.beta(loss) - 1e-6
+
+
+def test_logistic_loss_is_stable_at_large_margins():
+    assert oracle.loss("logistic", 1.0, 800.0) == pytest.approx(np.exp(-800.0), abs=1e-300)
+    assert oracle.loss("logistic", 1.0, -800.0) == pytest.approx(800.0, rel=1e-15)
+    assert oracle.dloss("logistic", -1.0, -800.0) == 0.0 or abs(oracle.dloss("logistic", -1.0, -800.0)) < 1e-300
+
+
+def test_eq4_clip_form_equals_soft_threshold_form():
+    # Section 3.1: -psi(w; (g-l)/H, (g+l)/H) == s_{l/H}(w - g/H) - w.
+    rng = np.random.default_rng(1)
+    for _ in range(20000):
+        g, w = rng.normal(size=2) * rng.choice([1e-3, 1.0, 1e3], size=2)
+        lam = abs(rng.normal()) * rng.choice([0.0, 1e-3, 1.0])
+        H = abs(rng.normal()) + 1e-3
+        d, _ = oracle.step(g, w, lam, H)
+        x = w - g / H
+        soft = np.sign(x) * max(abs(x) - lam / H, 0.0)
+        assert d == pytest.approx(soft - w, rel=1e-12, abs=1e-12 * (abs(w) + abs(g) / H + lam / H))
+
+
+def test_step_sign_and_proxy_special_cases():
+    # w = 0 and |g| <= lambda: no move, proxy 0.
+    assert oracle.step(0.3, 0.0, 0.5, 2.0) == (0.0, 0.0)
+    # w = 0 and g > lambda: move negative by (g - lambda)/beta.
+    d, phi = oracle.step(1.5, 0.0, 0.5, 2.0)
+    assert d == -0.5
+    assert phi == pytest.approx(0.5 * 2.0 * 0.25 + 1.5 * (-0.5) + 0.5 * 0.5)  # = -0.25
+    assert phi == pytest.approx(-0.25)
+    # beta_j == 0 (empty column): the exact minimiser of lambda |w + d|.
+    assert oracle.step(0.0, 2.0, 0.1, 0.0) == (-2.0, pytest.approx(-0.2))
+
+
+def _random_state(prob, rng, frac=0.3):
+    w = np.where(rng.random(prob.k) < frac, rng.normal(0, 0.5, prob.k), 0.0)
+    return w
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_squared_step_is_the_exact_coordinate_minimiser(seed):
+    # For squared loss beta_j = c_j = H_jj (Eq. 4 == Eq. 7) and the proxy of
+    # Eq. 9 is the exact change of the objective.
+    prob = workloads.uniform_problem(60, 40, 6, values="lognormal", loss="squared", seed=seed)
+    X = prob.to_dense()
+    lam = 0.02
+    o = oracle.Oracle(prob, lam)
+    rng = np.random.default_rng(seed)
+    w = _random_state(prob, rng)
+    z = o.fitted(w)
+    J = np.arange(prob.k, dtype=np.int32)
+    delta, phi = o.propose(w, z, J)
+    P0 = _dense_objective(X, prob.y, "squared", lam, w)
+    for j in range(prob.k):
+        e = np.zeros(prob.k)
+        e[j] = 1.0
+        f = lambda d: _dense_objective(X, prob.y, "squared", lam, w + d * e)
+        # golden-section search on the true objective around the proposal
+        a, b = delta[j] - 2.0, delta[j] + 2.0
+        gr = (np.sqrt(5) - 1) / 2
+        for _ in range(200):
+            c, d = b - gr * (b - a), a + gr * (b - a)
+            if f(c) < f(d):
+                b = d
+            else:
+                a = c
+        # the search resolves the argmin only to ~sqrt(eps) of a flat quadratic
+        assert delta[j] == pytest.approx(0.5 * (a + b), abs=1e-6)
+        assert f(delta[j]) <= f(0.5 * (a + b)) + 1e-14
+        assert phi[j] == pytest.approx(f(delta[j]) - P0, abs=1e-12)
+
+
+@pytest.mark.parametrize("beta_mode", [0, 1])
+def test_logistic_step_never_increases_the_objective(beta_mode):
+    # Eq. 5-6: the surrogate bounds F from above, so the true change is <= phi <= 0.
+    prob = workloads.uniform_problem(80, 50, 8, values="lognormal", loss="logistic", seed=3)
+    X = prob.to_dense()
+    lam = 0.003
+    o = oracle.Oracle(prob, lam, beta_mode=beta_mode)
+    rng = np.random.default_rng(5)
+    w = _random_state(prob, rng)
+    z = o.fitted(w)
+    delta, phi = o.propose(w, z, np.arange(prob.k, dtype=np.int32))
+    P0 = _dense_objective(X, prob.y, "logistic", lam, w)
+    assert (phi <= 0).all()
+    assert (phi < 0).any()
+    for j in range(prob.k):
+        w2 = w.copy()
+        w2[j] += delta[j]
+        change = _dense_objective(X, prob.y, "logistic", lam, w2) - P0
+        assert change <= phi[j] + 1e-13
+
+
+def test_gradient_and_col_scale_match_dense_algebra():
+    prob = workloads.uniform_problem(50, 30, 7, values="lognormal", loss="logistic", seed=2)
+    X = prob.to_dense()
+    o = oracle.Oracle(prob, 0.01)
+    w = _random_state(prob, np.random.default_rng(2))
+    z = o.fitted(w)
+    np.testing.assert_allclose(z, X @ w, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(o.gradient(z), _dense_grad(X, prob.y, "logistic", w), rtol=1e-12, atol=1e-16)
+    np.testing.assert_allclose(o.col_scale(), (X * X).sum(0) / prob.n, rtol=1e-14)
+    assert o.objective(w) == pytest.approx(_dense_objective(X, prob.y, "logistic", 0.01, w), rel=1e-13)
+
+
+# --- optima --------------------------------------------------------------------
+
+def test_golden_worked_examples():
+    g = _golden("worked_examples.txt")
+    p = workloads.csc_from_dense(np.array([[1.0, 1.0], [1.0, -1.0]]), np.array([3.0, 1.0]), "squared")
+    o = oracle.Oracle(p, 0.5)
+    w, z, it, kkt, _ = o.solve("ccd", tol_kkt=1e-14)
+    np.testing.assert_allclose(w, g["lasso_orthogonal_2x2"]["w"], rtol=0, atol=1e-14)
+    assert o.objective(w) == pytest.approx(g["lasso_orthogonal_2x2"]["objective"][0], rel=1e-15)
+
+    p = workloads.csc_from_dense(np.ones((3, 1)), np.ones(3), "logistic")
+    o = oracle.Oracle(p, 0.1)
+    w, z, it, kkt, _ = o.solve("ccd", tol_kkt=1e-15, max_iter=100000)
+    assert w[0] == pytest.approx(g["logistic_constant_column"]["w"][0], rel=1e-12)
+    assert o.objective(w) == pytest.approx(g["logistic_constant_column"]["objective"][0], rel=1e-14)
+
+
+def test_orthogonal_design_lasso_is_soft_thresholding():
+    # Disjoint column supports: the optimum is w_j = s_lambda(X_j^T y / n) / c_j.
+    rng = np.random.default_rng(4)
+    n, k = 120, 30
+    X = np.zeros((n, k))
+    rows = rng.permutation(n)
+    for j in range(k):
+        X[rows[4 * j:4 * j + 4], j] = rng.normal(size=4)
+    y = rng.normal(size=n)
+    p = workloads.csc_from_dense(X, y, "squared")
+    b = X.T @ y / n
+    lam = 0.5 * np.abs(b).max()
+    o = oracle.Oracle(p, lam)
+    w, _, _, kkt, _ = o.solve("ccd", tol_kkt=1e-14)
+    c = (X * X).sum(0) / n
+    expect = np.sign(b) * np.maximum(np.abs(b) - lam, 0.0) / c
+    np.testing.assert_allclose(w, expect, rtol=1e-12, atol=1e-14)
+    assert (w == 0).sum() > 0 and (w != 0).sum() > 0
+
+
+def test_k1_lasso_is_exact_in_one_step():
+    rng = np.random.default_rng(6)
+    X = rng.normal(size=(40, 1))
+    y = rng.normal(size=40) + 2 * X[:, 0]
+    p = workloads.csc_from_dense(X, y, "squared")
+    lam = 0.1
+    o = oracle.Oracle(p, lam)
+    w, _, _, _ = o.run("ccd", 1)
+    b = X[:, 0] @ y / 40
+    c = X[:, 0] @ X[:, 0] / 40
+    assert w[0] == pytest.approx(np.sign(b) * max(abs(b) - lam, 0) / c, rel=1e-14)
+
+
+def test_k1_logistic_matches_bisection_on_the_subgradient():
+    rng = np.random.default_rng(7)
+    X = rng.normal(size=(50, 1))
+    y = np.where(X[:, 0] + rng.normal(size=50) > 0, 1.0, -1.0)
+    p = workloads.csc_from_dense(X, y, "logistic")
+    lam = 0.02
+    o = oracle.Oracle(p, lam)
+    w, _, _, kkt, _ = o.solve("ccd", tol_kkt=1e-13, max_iter=10**6)
+
+    def g(v):  # derivative of F along the single coordinate
+        return float(np.mean(-y * X[:, 0] / (1.0 + np.exp(y * X[:, 0] * v))))
+
+    assert abs(g(0.0)) > lam  # optimum away from zero
+    s = -np.sign(g(0.0))
+    lo, hi = 0.0, s * 100.0
+    for _ in range(200):  # g(v) + lambda s = 0 on the side of sign s
+        mid = 0.5 * (lo + hi)
+        if (g(mid) + lam * s) * s < 0:
+            lo = mid
+        else:
+            hi = mid
+    assert w[0] == pytest.approx(0.5 * (lo + hi), rel=1e-9)
+
+
+def _brute_force(X, y, loss, lam):
+    """Enumerate sign patterns; solve the smooth restricted problem; keep the
+    pattern whose solution is sign-consistent and satisfies the KKT conditions."""
+    n, k = X.shape
+    best = None
+    for pattern in itertools.product((-1, 0, 1), repeat=k):
+        s = np.array(pattern, float)
+        S = np.flatnonzero(s)
+        w = np.zeros(k)
+        if S.size:
+            XS = X[:, S]
+            if loss == "squared":
+                A = XS.T @ XS / n
+                rhs = XS.T @ y / n - lam * s[S]
+                w[S] = np.linalg.solve(A, rhs)
+            else:
+                # damped Newton on the smooth F(w_S) + lambda s_S^T w_S; this
+                # restricted problem may have no minimiser (then skip it)
+                def h(v):
+                    return np.logaddexp(0.0, -y * (XS @ v)).mean() + lam * s[S] @ v
+
+                v = np.zeros(S.size)
+                converged = False
+                for _ in range(200):
+                    t = XS @ v
+                    sig = 0.5 * (1.0 - np.tanh(0.5 * y * t))  # 1 / (1 + e^{y t})
+                    grad = XS.T @ (-y * sig) / n + lam * s[S]
+                    if np.abs(grad).max() < 1e-10:  # rounding floor is ~1e-13
+                        converged = True
+                    if np.abs(grad).max() < 1e-15:
+                        break
+                    Hs = (XS.T * (sig * (1 - sig))) @ XS / n + 1e-300 * np.eye(S.size)
+                    try:
+                        step = np.linalg.solve(Hs, grad)
+                    except np.linalg.LinAlgError:
+                        break
+                    a = 1.0
+                    while h(v - a * step) > h(v) - 1e-4 * a * (grad @ step) and a > 1e-12:
+                        a *= 0.5
+                    if np.abs(a * step).max() <= 1e-16 * (1 + np.abs(v).max()):
+                        break
+                    v = v - a * step
+                    if np.abs(v).max() > 1e6:
+                        converged = False
+                        break
+                if not converged:
+                    continue
+                w[S] = v
+            if np.any(np.sign(w[S]) != s[S]):
+                continue
+        g = _dense_grad(X, y, loss, w)
+        ok = True
+        for j in range(k):
+            if s[j] == 0 and abs(g[j]) > lam + 1e-10:
+                ok = False
+            if s[j] != 0 and abs(g[j] + lam * s[j]) > 1e-8:
+                ok = False
+        if ok:
+            P = _dense_objective(X, y, loss, lam, w)
+            if best is None or P < best[0]:
+                best = (P, w)
+    return best
+
+
+@pytest.mark.parametrize("loss", ["squared", "logistic"])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_tiny_problems_match_brute_force(loss, seed):
+    p = workloads.tiny_problem(8, 4, loss=loss, seed=seed)
+    X = p.to_dense()
+    o = oracle.Oracle(p)
+    lam = 0.2 * o.lambda_max()
+    o.set_lambda(lam)
+    Pbf, wbf = _brute_force(X, p.y, loss, lam)
+    w, _, _, kkt, _ = o.solve("ccd", tol_kkt=1e-13, max_iter=10**7)
+    assert kkt <= 1e-13
+    np.testing.assert_allclose(w, wbf, rtol=1e-7, atol=1e-9)
+    assert o.objective(w) == pytest.approx(Pbf, rel=1e-12)
+    assert ((w != 0) == (np.abs(wbf) > 0)).all()
+
+
+def test_lambda_max_is_the_zero_threshold():
+    p = workloads.uniform_problem(100, 60, 5, values="lognormal", loss="logistic", seed=9)
+    o = oracle.Oracle(p)
+    lm = o.lambda_max()
+    X = p.to_dense()
+    assert lm == pytest.approx(np.abs(_dense_grad(X, p.y, "logistic", np.zeros(p.k))).max(), rel=1e-13)
+    o.set_lambda(lm * (1 + 1e-9))
+    w, _, it, kkt, _ = o.solve("ccd", tol_kkt=0.0, max_iter=5 * p.k)
+    assert (w == 0).all() and kkt == 0.0
+    o.set_lambda(lm * 0.999)
+    w, _, _, _, _ = o.solve("ccd", tol_kkt=1e-12)
+    assert (w != 0).sum() >= 1
+
+
+@pytest.mark.parametrize("loss", ["squared", "logistic"])
+def test_kkt_conditions_hold_at_convergence(loss):
+    p = workloads.uniform_problem(300, 400, 10, values="pm1", loss=loss, n_planted=20, seed=11)
+    o = oracle.Oracle(p)
+    lam = 0.05 * o.lambda_max()
+    o.set_lambda(lam)
+    w, z, it, kkt, _ = o.solve("ccd", tol_kkt=1e-9)
+    g = _dense_grad(p.to_dense(), p.y, loss, w)
+    zero = w == 0
+    assert np.all(np.abs(g[zero]) <= lam + 1e-9)
+    assert np.all(np.abs(g[~zero] + lam * np.sign(w[~zero])) <= 1e-8)
+    assert (~zero).sum() > 0
+
+
+# --- invariants the paper states ------------------------------------------------
+
+@pytest.mark.parametrize("variant", ["ccd", "coloring"])
+def test_objective_is_monotone_for_sequential_and_coloring(variant):
+    # Section 3.2: the Eq. 7 step never increases the objective; Section 4.1:
+    # Coloring behaves like sequential CD.
+    p = workloads.uniform_problem(200, 300, 8, values="lognormal", loss="logistic", seed=12)
+    o = oracle.Oracle(p)
+    o.set_lambda(0.02 * o.lambda_max())
+    colors = o.color()[0] if variant == "coloring" else None
+    _, _, tr, _ = o.run(variant, 600, colors=colors, seed=3, trace=True)
+    P0 = o.objective(np.zeros(p.k))
+    seq = np.concatenate([[P0], tr])
+    assert np.all(np.diff(seq) <= 1e-15 * np.abs(seq[:-1]))
+    assert seq[-1] < P0
+
+
+def test_coloring_equals_ccd_in_colour_major_order():
+    # Section 4.1: updating one colour class == updating its features in sequence.
+    p = workloads.uniform_problem(150, 200, 6, values="lognormal", loss="logistic", seed=13)
+    o = oracle.Oracle(p)
+    o.set_lambda(0.01 * o.lambda_max())
+    colors, C = o.color()
+    seed = 21
+    w_col, z_col, _, _ = o.run("coloring", C, colors=colors, seed=seed)
+    order = []
+    for c in oracle.permutation(seed, 0, C):
+        order.extend(np.flatnonzero(colors == c).tolist())
+    assert sorted(order) == list(range(p.k))
+    # relabel the columns so that colour-major order becomes index order, then CCD
+    X = p.to_dense()[:, order]
+    q = workloads.csc_from_dense(X, p.y, "logistic")
+    oq = oracle.Oracle(q, o.lam)
+    w_ccd, z_ccd, _, _ = oq.run("ccd", p.k)
+    assert np.array_equal(w_ccd, w_col[order])
+    assert np.array_equal(z_ccd, z_col)
+
+
+def test_greedy_equals_thread_greedy_with_one_partition():
+    p = workloads.uniform_problem(150, 200, 6, values="pm1", loss="logistic", seed=14)
+    o = oracle.Oracle(p)
+    o.set_lambda(0.05 * o.lambda_max())
+    a = o.run("greedy", 40)
+    b = o.run("thread_greedy", 40, B=1)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert (a[0] != 0).sum() >= 1
+
+
+def test_thread_greedy_accepts_the_best_proxy_per_partition():
+    p = workloads.uniform_problem(120, 97, 5, values="lognormal", loss="squared", seed=15)
+    o = oracle.Oracle(p)
+    o.set_lambda(0.1 * o.lambda_max())
+    rng = np.random.default_rng(15)
+    w0 = _random_state(p, rng, 0.2)
+    z0 = o.fitted(w0)
+    delta, phi = o.propose(w0, z0, np.arange(p.k, dtype=np.int32))
+    for B in (1, 7, 97, 200):
+        w, _, _, st = o.run("thread_greedy", 1, w=w0, z=z0, B=B)
+        expect = w0.copy()
+        accepted = 0
+        for b in range(B):
+            lo, hi = b * p.k // B, (b + 1) * p.k // B
+            if hi > lo:
+                j = lo + int(np.argmin(phi[lo:hi]))  # argmin keeps the first minimum
+                if phi[j] < 0:
+                    expect[j] += delta[j]
+                    accepted += 1
+        np.testing.assert_array_equal(w, expect)
+        assert st[0] == accepted  # a partition whose best proxy is 0 accepts nothing
+    assert (phi == 0).any() and (phi < 0).any()
+
+
+def test_thread_greedy_ties_go_to_the_lower_column():
+    # Duplicate columns give identical proxies; the lower index must win.
+    rng = np.random.default_rng(19)
+    base = rng.normal(size=(40, 3)) * (rng.random((40, 3)) < 0.5)
+    X = np.concatenate([base, base], axis=1)[:, [0, 3, 1, 4, 2, 5]]  # pairs (0,1), (2,3), (4,5)
+    y = rng.normal(size=40)
+    p = workloads.csc_from_dense(X, y, "squared")
+    o = oracle.Oracle(p, 0.0)
+    for B in (1, 3):
+        w, _, _, _ = o.run("thread_greedy", 1, B=B)
+        moved = np.flatnonzero(w)
+        assert moved.size == B and all(j % 2 == 0 for j in moved)
+
+
+def test_shotgun_selects_each_column_once_per_epoch():
+    p = workloads.uniform_problem(100, 103, 4, values="pm1", loss="squared", seed=16)
+    o = oracle.Oracle(p)
+    o.set_lambda(0.5 * o.lambda_max())
+    P = 10
+    perm = oracle.permutation(5, 0, p.k)
+    w0 = np.zeros(p.k)
+    z0 = o.fitted(w0)
+    # one epoch = ceil(103/10) = 11 iterations; the Jacobi step of each chunk
+    w, z = w0, z0
+    for t in range(11):
+        J = np.sort(perm[t * P:(t + 1) * P]).astype(np.int32)
+        d, _ = o.propose(w, z, J)
+        w = w.copy()
+        w[J] += d
+        z = o.fitted(w)
+    w_run, z_run, _, st = o.run("shotgun", 11, P=P, seed=5)
+    np.testing.assert_allclose(w_run, w, rtol=1e-14, atol=1e-16)
+    assert st[0] == p.k  # every column proposed and accepted once
+
+
+def test_coloring_is_a_valid_first_fit_distance2_colouring():
+    p = workloads.uniform_problem(90, 150, 5, values="pm1", loss="squared", seed=17)
+    o = oracle.Oracle(p)
+    colors, C = o.color()
+    X = p.to_dense() != 0
+    assert colors.min() == 0 and colors.max() == C - 1
+    for i in range(p.n):  # columns sharing a row have distinct colours
+        cs = colors[X[i]]
+        assert len(set(cs.tolist())) == cs.size
+    assert C >= X.sum(1).max()
+    adj = (X.T.astype(int) @ X.astype(int)) > 0
+    for j in range(p.k):  # first-fit: every smaller colour is used by a lower neighbour
+        lower = set(colors[:j][adj[j, :j]].tolist())
+        assert all(c in lower for c in range(colors[j]))
+        assert colors[j] not in lower
+
+
+def test_spectral_radius_matches_eigvalsh():
+    p = workloads.uniform_problem(80, 60, 6, values="lognormal", loss="squared", seed=18)
+    scale = np.random.default_rng(18).uniform(0.2, 5.0, p.k)  # columns of different norms
+    p.val = p.val * np.repeat(scale, np.diff(p.col_ptr))
+    X = p.to_dense()
+    d = 1.0 / np.sqrt((X * X).sum(0))
+    M = (X * d).T @ (X * d)
+    rho_exact = np.linalg.eigvalsh(M)[-1]
+    rho, it = oracle.Oracle(p).spectral_radius(max_iter=5000, rel_tol=1e-15)
+    assert rho == pytest.approx(rho_exact, rel=1e-9)
+    assert oracle.pstar(p.k, rho) == max(1, int(np.floor(p.k / (2 * rho_exact))))
+
+
+def test_empty_columns_and_rows_are_handled():
+    X = np.zeros((6, 5))
+    X[0, 0], X[2, 0], X[2, 2], X[5, 2], X[1, 4] = 1.0, -2.0, 0.5, 1.5, 3.0
+    y = np.array([1.0, -1.0, 1.0, -1.0, 1.0, 1.0])
+    p = workloads.csc_from_dense(X, y, "logistic")
+    o = oracle.Oracle(p)
+    o.set_lambda(0.05)
+    w0 = np.array([0.0, 0.7, 0.0, -0.3, 0.0])  # weights on the empty columns 1 and 3
+    w, _, _, _, _ = o.solve("ccd", tol_kkt=1e-12, w=w0)
+    assert w[1] == 0.0 and w[3] == 0.0
+    assert o.kkt(w) <= 1e-12
+    Pbf, wbf = _brute_force(X[:, [0, 2, 4]], y, "logistic", 0.05)
+    np.testing.assert_allclose(w[[0, 2, 4]], wbf, atol=1e-8)

@@ -1,0 +1,56 @@
+"""The seeded generators produce the documented shapes and structure."""
+
+import numpy as np
+import pytest
+
+import workloads
+
+
+def _check_csc(p):
+    assert p.col_ptr.dtype == np.int64 and p.row_idx.dtype == np.int32 and p.val.dtype == np.float64
+    assert p.col_ptr[0] == 0 and np.all(np.diff(p.col_ptr) >= 0) and p.col_ptr[-1] == p.row_idx.size
+    for j in range(p.k):
+        r = p.row_idx[p.col_ptr[j]:p.col_ptr[j + 1]]
+        assert np.all(np.diff(r) > 0) and (r.size == 0 or (r[0] >= 0 and r[-1] < p.n))
+
+
+def test_config1_shape_and_values():
+    p = workloads.config1("logistic")
+    assert (p.n, p.k, p.nnz) == (2000, 5000, 100_000)
+    assert set(np.unique(p.val)) == {-1.0, 1.0}
+    assert set(np.unique(p.y)) == {-1.0, 1.0}
+    assert (p.w_star != 0).sum() == 50
+    assert np.all(np.diff(p.col_ptr) == 20)
+    _check_csc(p)
+    q = workloads.config1("logistic")
+    assert p.sha256() == q.sha256()  # seeded
+    s = workloads.config1("squared")
+    assert s.y.dtype == np.float64 and len(np.unique(s.y)) > 100
+
+
+def test_zipf_counts_hit_the_target():
+    c = workloads.synthetic.zipf_counts(4_000_000, 200_000_000, cap=50_000)
+    assert abs(c.sum() - 2e8) <= 0.005 * 2e8
+    assert c.max() == 50_000 and c.min() >= 1
+    assert 400 <= (c == 50_000).sum() <= 800
+
+
+def test_scaled_zipf_problem_structure():
+    p = workloads.config2_scaled(0.002)
+    _check_csc(p)
+    counts = p.col_nnz()
+    assert counts.min() >= 1
+    norms = np.sqrt(np.add.reduceat(p.val ** 2, p.col_ptr[:-1]))
+    np.testing.assert_allclose(norms, 1.0, rtol=1e-12)
+    assert np.all(p.val > 0)
+    assert set(np.unique(p.y)) <= {-1.0, 1.0}
+
+
+def test_distinct_rows_are_uniform_without_replacement():
+    rng = np.random.default_rng(0)
+    counts = np.array([5, 0, 10, 10])
+    rows = workloads.synthetic._distinct_rows(10, counts, rng)
+    assert rows[5:15].tolist() == list(range(10))
+    assert rows[15:].tolist() == list(range(10))
+    with pytest.raises(ValueError):
+        workloads.synthetic._distinct_rows(3, np.array([4]), rng)

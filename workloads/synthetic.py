@@ -1,0 +1,264 @@
+"""Seeded generators for sparse l1 problems shaped like the paper's workloads.
+
+The paper measures on DOROTHEA (binary, 800 x 100,000, 7.3 nnz/column) and
+REUTERS RCV1-v2 (tf-idf, 23,865 x 47,237, 37.2 nnz/column), both with columns
+normalised (Section 4.4, Table 3).  Neither data set is available here, so these
+generators draw stand-ins with the same structure: sparse column-major X,
+binary/+-1 or log-normal values, unit-norm columns, k >> n, a planted sparse
+model and noisy labels.
+
+Every generator uses ``numpy.random.Generator(PCG64(seed))`` and a fixed draw
+order (documented per function), so the same seed gives the same bytes on any
+machine.  Nothing here evaluates the objective, its gradient or a step of the
+method.
+
+CSC layout: ``col_ptr`` int64[k+1], ``row_idx`` int32[nnz] (sorted, distinct
+within a column), ``val`` float64[nnz]; labels ``y`` float64[n].
+"""
+
+from __future__ import annotations
+
+import dataclasses
+import hashlib
+
+import numpy as np
+
+SQUARED = "squared"
+LOGISTIC = "logistic"
+
+
+@dataclasses.dataclass
+class Problem:
+    n: int
+    k: int
+    col_ptr: np.ndarray
+    row_idx: np.ndarray
+    val: np.ndarray
+    y: np.ndarray
+    loss: str
+    w_star: np.ndarray
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col_ptr[-1])
+
+    def col_nnz(self) -> np.ndarray:
+        return np.diff(self.col_ptr)
+
+    def sha256(self) -> str:
+        h = hashlib.sha256()
+        for a in (self.col_ptr, self.row_idx, self.val, self.y):
+            h.update(np.ascontiguousarray(a).tobytes())
+        return h.hexdigest()
+
+    def to_dense(self) -> np.ndarray:
+        X = np.zeros((self.n, self.k))
+        for j in range(self.k):
+            s, e = self.col_ptr[j], self.col_ptr[j + 1]
+            X[self.row_idx[s:e], j] = self.val[s:e]
+        return X
+
+    def with_loss(self, loss: str, y: np.ndarray) -> "Problem":
+        return dataclasses.replace(self, loss=loss, y=np.ascontiguousarray(y, np.float64))
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _distinct_rows(n: int, counts: np.ndarray, rng: np.random.Generator) -> np.ndarray:
+    """Rows for each column, uniform without replacement, sorted per column.
+
+    Draws with replacement, then redraws the duplicates until every column's
+    rows are distinct (the result is a uniform draw without replacement).
+    Returns the concatenated int32 row indices in column order.
+    """
+    counts = np.asarray(counts, np.int64)
+    if counts.size and counts.max() > n:
+        raise ValueError("a column cannot hold more than n distinct rows")
+    k = counts.size
+    col = np.repeat(np.arange(k, dtype=np.int64), counts)
+    key = col * n + rng.integers(0, n, size=col.size, dtype=np.int64)
+    key.sort()
+    while True:
+        dup = np.flatnonzero(key[1:] == key[:-1]) + 1
+        if dup.size == 0:
+            break
+        c = key[dup] // n
+        key[dup] = c * n + rng.integers(0, n, size=dup.size, dtype=np.int64)
+        key.sort()
+    return (key - col * n).astype(np.int32)
+
+
+def _col_ptr(counts: np.ndarray) -> np.ndarray:
+    cp = np.zeros(len(counts) + 1, np.int64)
+    np.cumsum(counts, out=cp[1:])
+    return cp
+
+
+def _matvec(col_ptr, row_idx, val, n, w) -> np.ndarray:
+    """X @ w for the planted model (label generation only)."""
+    counts = np.diff(col_ptr)
+    contrib = val * np.repeat(w, counts)
+    return np.bincount(row_idx, weights=contrib, minlength=n).astype(np.float64)
+
+
+def _labels(loss: str, t: np.ndarray, noise_sd: float, rng: np.random.Generator) -> np.ndarray:
+    eps = rng.normal(0.0, noise_sd, size=t.size)
+    if loss == LOGISTIC:
+        return np.where(t + eps >= 0.0, 1.0, -1.0)  # sign(0) = +1
+    return t + eps
+
+
+def _normalise_columns(col_ptr, val) -> np.ndarray:
+    counts = np.diff(col_ptr)
+    nz = counts > 0
+    ss = np.zeros(counts.size)
+    ss[nz] = np.add.reduceat(val * val, col_ptr[:-1][nz])
+    scale = np.where(ss > 0, 1.0 / np.sqrt(np.where(ss > 0, ss, 1.0)), 0.0)
+    return val * np.repeat(scale, counts)
+
+
+def uniform_problem(n, k, nnz_per_col, *, values="pm1", n_planted=50, loss=LOGISTIC,
+                    noise_sd=None, seed=0, name="") -> Problem:
+    """Every column holds ``nnz_per_col`` distinct rows drawn uniformly.
+
+    Draw order: rows, values, planted support, planted weights, label noise.
+    ``values``: "pm1" (+-1 at p=1/2), "ones" (binary, DOROTHEA-like) or
+    "lognormal" (LogNormal(0,1) then unit-norm columns, tf-idf-like).
+    """
+    rng = _rng(seed)
+    counts = np.full(k, nnz_per_col, np.int64)
+    col_ptr = _col_ptr(counts)
+    row_idx = _distinct_rows(n, counts, rng)
+    nnz = int(col_ptr[-1])
+    if values == "pm1":
+        val = np.where(rng.random(nnz) < 0.5, -1.0, 1.0)
+    elif values == "ones":
+        val = np.ones(nnz)
+    elif values == "lognormal":
+        val = _normalise_columns(col_ptr, rng.lognormal(0.0, 1.0, nnz))
+    else:
+        raise ValueError(values)
+    w_star = np.zeros(k)
+    support = rng.choice(k, size=min(n_planted, k), replace=False)
+    w_star[support] = rng.normal(0.0, 1.0, support.size)
+    t = _matvec(col_ptr, row_idx, val, n, w_star)
+    if noise_sd is None:
+        noise_sd = 0.1 if loss == LOGISTIC else 0.01
+    y = _labels(loss, t, noise_sd, rng)
+    return Problem(n, k, col_ptr, row_idx, val.astype(np.float64), y, loss, w_star, name)
+
+
+def config1(loss=LOGISTIC, seed=0) -> Problem:
+    """n=2,000, k=5,000, 20 nnz/column at uniform rows, values +-1; 50 planted
+    N(0,1) weights; logistic y = sign(Xw*+N(0,0.1^2)), Lasso y = Xw*+N(0,0.01^2)."""
+    return uniform_problem(2000, 5000, 20, values="pm1", n_planted=50, loss=loss,
+                           seed=seed, name=f"uniform-2000x5000-20nnz-pm1-{loss}")
+
+
+def zipf_counts(k, nnz_total, s=1.1, cap=50_000, n=None) -> np.ndarray:
+    """Column nnz by rank r: clamp(round(C r^-s), 1, cap), with C found by
+    bisection so that the total is nnz_total (to 0.5%)."""
+    cap = min(cap, n) if n is not None else cap
+    r = np.arange(1, k + 1, dtype=np.float64) ** (-s)
+
+    def total(C):
+        return np.clip(np.rint(C * r), 1, cap).sum()
+
+    lo, hi = 0.0, float(nnz_total) * 10.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if total(mid) < nnz_total:
+            lo = mid
+        else:
+            hi = mid
+    counts = np.clip(np.rint(hi * r), 1, cap).astype(np.int64)
+    if abs(counts.sum() - nnz_total) > 0.005 * nnz_total:
+        raise ValueError("cannot meet the nnz target with this cap")
+    return counts
+
+
+def zipf_problem(n, k, nnz_total, *, s=1.1, cap=50_000, n_planted=2000, loss=LOGISTIC,
+                 seed=0, name="") -> Problem:
+    """Zipf(s) column lengths assigned to columns by a seeded permutation, rows
+    uniform without replacement, LogNormal(0,1) values, unit-norm columns.
+
+    Draw order: rank-to-column permutation, rows, values, planted support,
+    planted weights, label noise.  Labels: y = sign(Xw* + eps) with
+    eps ~ N(0, (0.1 rms(Xw*))^2) (logistic), y = Xw* + eps (squared).
+    """
+    rng = _rng(seed)
+    by_rank = zipf_counts(k, nnz_total, s=s, cap=cap, n=n)
+    perm = rng.permutation(k)
+    counts = np.empty(k, np.int64)
+    counts[perm] = by_rank
+    col_ptr = _col_ptr(counts)
+    row_idx = _distinct_rows(n, counts, rng)
+    val = _normalise_columns(col_ptr, rng.lognormal(0.0, 1.0, int(col_ptr[-1])))
+    w_star = np.zeros(k)
+    support = rng.choice(k, size=min(n_planted, k), replace=False)
+    w_star[support] = rng.normal(0.0, 1.0, support.size)
+    t = _matvec(col_ptr, row_idx, val, n, w_star)
+    rms = float(np.sqrt(np.mean(t * t))) if n else 0.0
+    y = _labels(loss, t, 0.1 * rms if rms > 0 else 0.1, rng)
+    return Problem(n, k, col_ptr, row_idx, val, y, loss, w_star, name)
+
+
+def config2(loss=LOGISTIC, seed=0) -> Problem:
+    """n=1,000,000, k=4,000,000, Zipf(1.1) column nnz capped at 50,000,
+    2.00e8 nnz, log-normal unit-norm columns, 2,000 planted weights."""
+    return zipf_problem(1_000_000, 4_000_000, 200_000_000, cap=50_000, n_planted=2000,
+                        loss=loss, seed=seed, name=f"zipf1.1-1Mx4M-200Mnnz-{loss}")
+
+
+def config2_scaled(scale=0.02, loss=LOGISTIC, seed=0) -> Problem:
+    """config2's structure at a fraction of its size (rows, columns, nnz and the
+    column cap all scaled), for tests that must run in seconds."""
+    n = max(1000, int(1_000_000 * scale))
+    k = max(1000, int(4_000_000 * scale))
+    nnz = int(200_000_000 * scale)
+    cap = max(50, int(50_000 * scale))
+    return zipf_problem(n, k, nnz, cap=cap, n_planted=max(10, int(2000 * scale)), loss=loss,
+                        seed=seed, name=f"zipf1.1-{n}x{k}-{nnz}nnz-{loss}")
+
+
+def tiny_problem(n, k, density=0.6, loss=LOGISTIC, seed=0, max_tries=1000) -> Problem:
+    """A small problem with n >= k and full column rank (so the l1 optimum is
+    unique), for brute-force checks.  Values are N(0,1) on a random pattern."""
+    rng = _rng(seed)
+    for _ in range(max_tries):
+        mask = rng.random((n, k)) < density
+        vals = rng.normal(0.0, 1.0, (n, k))
+        X = np.where(mask, vals, 0.0)
+        if np.linalg.matrix_rank(X) < k or (np.abs(X).sum(axis=0) == 0).any():
+            continue
+        w_star = rng.normal(0.0, 1.0, k) * (rng.random(k) < 0.5)
+        t = X @ w_star
+        if loss == LOGISTIC:
+            y = np.where(t + rng.normal(0.0, 1.0, n) >= 0.0, 1.0, -1.0)
+        else:
+            y = t + rng.normal(0.0, 0.1, n)
+        p = csc_from_dense(X, y, loss)
+        p.w_star = w_star
+        return p
+    raise RuntimeError("could not draw a full-rank tiny problem")
+
+
+def csc_from_dense(X: np.ndarray, y: np.ndarray, loss: str, name="") -> Problem:
+    """CSC arrays of a dense matrix (structural zeros dropped)."""
+    X = np.asarray(X, np.float64)
+    n, k = X.shape
+    cols, rows, vals = [], [], []
+    counts = np.zeros(k, np.int64)
+    for j in range(k):
+        nz = np.flatnonzero(X[:, j])
+        counts[j] = nz.size
+        rows.append(nz.astype(np.int32))
+        vals.append(X[nz, j])
+    col_ptr = _col_ptr(counts)
+    row_idx = np.concatenate(rows) if rows else np.zeros(0, np.int32)
+    val = np.concatenate(vals) if vals else np.zeros(0)
+    return Problem(n, k, col_ptr, row_idx.astype(np.int32), val.astype(np.float64),
+                   np.asarray(y, np.float64), loss, np.zeros(k), name)
