@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Throughput of the GenCD hot path on GB300: non-zeros processed per second.
+
+One step = one Thread-Greedy GenCD iteration (Algorithm 1, Table 2) over the
+whole synthetic workload: Select (all columns), Propose (streaming pass over
+X computing g, the Eq. 7 step and the Eq. 9 proxy for every column), the
+convergence quantities of the start state (KKT violation and objective),
+Accept (best proxy per partition), Update (atomic scatter into z) and the
+refresh of u on the touched rows.
+
+Workload: logistic l1 problem with n=1,000,000 rows, k=4,000,000 columns,
+Zipf(1.1) column lengths capped at 50,000 (2.0e8 non-zeros), log-normal values
+with unit-norm columns, 2,000 planted weights, lambda = 0.05 lambda_max.
+
+  value   nnz processed per second with X resident in HBM (CUDA events on the
+          library's stream, max over ranks)
+  e2e     the same metric through the C ABI from pinned host buffers: each step
+          creates the problem from host memory (H2D of X and y), runs one
+          iteration and reads the objective and KKT value back (D2H)
+
+`--impl reference` times the FP64 CPU oracle on the host cores instead (the
+paper's method has no other runnable implementation).  Under torchrun every
+rank runs an independent replica (the path is replicated, not sharded).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WORKLOAD_DESC = ("logistic l1, n=1,000,000, k=4,000,000, Zipf(1.1) column nnz capped at 50,000, "
+                 "2.0e8 nnz, log-normal unit-norm columns, lambda=0.05*lambda_max, seed 0")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gencd", choices=["gencd", "reference"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--variant", default="thread_greedy", choices=["thread_greedy", "greedy"])
+    ap.add_argument("--blocks", type=int, default=1024)
+    ap.add_argument("--scale", type=float, default=1.0, help="fraction of the full workload (tests)")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def load_problem(scale):
+    if scale >= 1.0:
+        return workloads.config2("logistic")
+    return workloads.config2_scaled(scale, "logistic")
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel_src, precision):
+    """DRAM bytes per launch of the streaming propose from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    src_hash = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", f"propose_all_config2_{precision}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, src_hash
+    fields = dict(line.split(":", 1) for line in text.splitlines() if line.startswith(("source_sha256", "dram_bytes_per_launch")))
+    if fields.get("source_sha256", "").strip() != src_hash:
+        return None, src_hash
+    try:
+        return float(fields["dram_bytes_per_launch"].strip()), src_hash
+    except (KeyError, ValueError):
+        return None, src_hash
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_rate(prob, lam, seconds, blocks):
+    """The FP64 oracle (single thread, as it stands) running Thread-Greedy
+    iterations on a column slice of the workload for about `seconds`."""
+    import oracle
+
+    # contiguous slice of the first columns holding ~2e7 non-zeros
+    kk = int(np.searchsorted(prob.col_ptr, 20_000_000))
+    kk = max(1, min(kk, prob.k))
+    sub = workloads.Problem(prob.n, kk, prob.col_ptr[:kk + 1].copy(), prob.row_idx[:prob.col_ptr[kk]],
+                            prob.val[:prob.col_ptr[kk]], prob.y, prob.loss, prob.w_star[:kk], "slice")
+    orc = oracle.Oracle(sub, lam)
+    B = max(1, int(round(blocks * kk / prob.k)))
+    w = np.zeros(kk)
+    z = np.zeros(prob.n)
+    t0 = time.perf_counter()
+    nnz = 0
+    iters = 0
+    while True:
+        w, z, _, st = orc.run("thread_greedy", 1, w=w, z=z, t0=iters, B=B)
+        nnz += int(st[1])
+        iters += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return nnz / el, {"kind": "oracle", "cores": 1, "value": nnz / el, "unit": "nnz/s",
+                      "sample": f"{iters} Thread-Greedy iterations (B={B}) of the FP64 oracle on the first "
+                                f"{kk} columns ({int(sub.col_ptr[-1])} nnz) of the workload, "
+                                f"{el:.1f} s on 1 host core"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    prob = load_problem(args.scale)
+    import oracle
+
+    orc_full = oracle.Oracle(prob)
+    lam = 0.05 * orc_full.lambda_max()
+    steps, warm = args.steps, args.warmup
+    # each step: about one second of oracle work on a column slice
+    per_step = 1.0
+    for _ in range(warm):
+        cpu_oracle_rate(prob, lam, per_step * 0.25, args.blocks)
+    rates = []
+    sample = None
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        r, info = cpu_oracle_rate(prob, lam, per_step, args.blocks)
+        rates.append(r)
+        sample = info["sample"]
+    el = time.perf_counter() - t0
+    value = statistics.mean(rates)
+    line = {"impl": "reference", "metric": "nnz processed/s", "value": value, "unit": "nnz/s", "n_gpus": world,
+            "steps": steps, "warmup": warm, "ms_per_step": 1000.0 * el / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "variant": "thread_greedy", "precision": "f64"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": "nnz/s",
+                             "sample": "per step: " + sample},
+            "e2e": {"value": value, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gencd(args):
+    import torch
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1206_6409_gb300 import binding as gb
+
+    gb.lib()
+    prob = load_problem(args.scale)
+    stream = torch.cuda.current_stream()
+    val = prob.val.astype(np.float32) if args.precision == "f32" else prob.val
+
+    # ---- device-resident arm ----------------------------------------------
+    p = gb.Problem(n=prob.n, k=prob.k, col_ptr=prob.col_ptr, row_idx=prob.row_idx, val=val, y=prob.y,
+                   loss="logistic", precision=args.precision, stream=stream.cuda_stream)
+    lam = 0.05 * p.lambda_max()
+    p.set_lambda(lam)
+    p.set_params(variant=args.variant, blocks=args.blocks, seed=0)
+    for _ in range(args.warmup):
+        p.iterate(1, sync=False)
+    torch.cuda.synchronize()
+    gb.gencd_profile_reset(p.h)
+    p.stats_reset()
+    gb.gencd_profile_enable(p.h, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        p.iterate(1, sync=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    st = p.stats()
+    prof = {name: gb.gencd_profile_read(p.h, name) for name in gb.KERNELS}
+    gb.gencd_profile_enable(p.h, False)
+    launches = int(sum(v[1] for v in prof.values()))
+    nnz_done = int(st.nnz_processed)
+    if world > 1:
+        t = torch.tensor([ms, float(nnz_done)], device="cuda", dtype=torch.float64)
+        mx = t.clone()
+        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+        sm = t.clone()
+        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+        ms, nnz_total = float(mx[0]), float(sm[1])
+    else:
+        nnz_total = float(nnz_done)
+    value = nnz_total / (ms / 1000.0)
+
+    # roofline of the dominant kernel (the streaming propose)
+    pa_ms, pa_n = prof["propose_all"]
+    sv = 4 if args.precision == "f32" else 8
+    bytes_per_launch = prob.nnz * (4 + sv) + 8 * (prob.k + 1) + 8 * prob.k
+    achieved = bytes_per_launch / (pa_ms / pa_n / 1000.0) / 1e9 if pa_n else None
+    peak, peak_kind = measured_peak()
+    traffic, src_hash = recorded_traffic(os.path.join(ROOT, "paper_1206_6409_gb300", "csrc", "kernels_propose.cu"),
+                                         args.precision)
+    p.close()
+    del p
+
+    # ---- end-to-end arm through the C ABI from pinned host buffers ---------
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = {}
+        for name, a in (("col_ptr", prob.col_ptr), ("row_idx", prob.row_idx), ("val", val), ("y", prob.y)):
+            t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+            pin[name] = t.numpy()
+        h2d = sum(a.nbytes for a in pin.values())
+        d2h = 64  # objective, KKT and the work counters
+        torch.cuda.synchronize()
+        t_e2e = 0.0
+        nnz_e2e = 0
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            q = gb.Problem(n=prob.n, k=prob.k, loss="logistic", precision=args.precision,
+                           stream=stream.cuda_stream, **pin)
+            q.set_lambda(0.05 * q.lambda_max())
+            q.set_params(variant=args.variant, blocks=args.blocks, seed=0)
+            q.stats_reset()
+            q.iterate(1, sync=False)
+            r = q.stats()
+            q.close()
+            el = time.perf_counter() - t0
+            if i > 0:  # the first step is a warm-up
+                t_e2e += el
+                nnz_e2e += int(r.nnz_processed)
+        e2e = {"value": nnz_e2e / t_e2e, "unit": "nnz/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": d2h,
+               "ms_per_step": 1000.0 * t_e2e / args.e2e_steps}
+        if world > 1:
+            t = torch.tensor([t_e2e, float(nnz_e2e)], device="cuda", dtype=torch.float64)
+            mx = t.clone()
+            torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+            sm = t.clone()
+            torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+            e2e["value"] = float(sm[1]) / float(mx[0])
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        _, cpu = cpu_oracle_rate(prob, lam, args.cpu_seconds, args.blocks)
+
+    if rank == 0:
+        line = {
+            "metric": "nnz processed/s", "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC if args.scale >= 1.0 else f"scaled {args.scale}: {prob.name}",
+                       "variant": args.variant, "blocks": args.blocks, "precision": args.precision,
+                       "nnz": prob.nnz, "n": prob.n, "k": prob.k,
+                       "l2": "inputs larger than L2: each step streams all of X (%.2f GB)" % (bytes_per_launch / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "kernel": "k_propose_all", "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": achieved / peak if achieved else None, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": bytes_per_launch,
+                         "launch_ms": pa_ms / pa_n if pa_n else None, "source_sha256": src_hash},
+            "kernel_ms": {k: (v[0] / v[1] if v[1] else 0.0, v[1]) for k, v in prof.items() if v[1]},
+            "gpu_launches": launches,
+            "updates_per_step": st.updates / args.steps,
+            "objective": st.objective, "kkt": st.kkt,
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gencd(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,230 @@
+/*
+ * gencd.h -- C ABI of libgencd, a GB300 (sm_103a) implementation of the
+ * data-parallel hot path of GenCD from Scherrer, Halappanavar, Tewari and
+ * Haglin, "Scaling Up Coordinate Descent Algorithms for Large l1
+ * Regularization Problems".
+ *
+ * Problem (Section 1, Eq. 1):
+ *     min_w (1/n) sum_i l(y_i, (Xw)_i) + lambda ||w||_1
+ * with squared loss l(y,t) = (y - t)^2 / 2 (Lasso) or logistic loss
+ * l(y,t) = log(1 + exp(-y t)), X an n x k sparse matrix.
+ *
+ * One GenCD iteration (Algorithm 1) is Select -> Propose -> Accept -> Update:
+ *   Propose (Algorithm 4): g_j = <l'(y, z), X_j> / n, the step of Eq. 7,
+ *           delta_j = -psi(w_j; (g_j - lambda)/beta_j, (g_j + lambda)/beta_j),
+ *           and the proxy of Eq. 9,
+ *           phi_j = beta_j/2 delta_j^2 + g_j delta_j + lambda(|w_j+delta_j| - |w_j|);
+ *   Accept  (Table 2): Shotgun and Coloring accept all proposals, Thread-Greedy
+ *           the best proxy per partition, Greedy the single best;
+ *   Update  (Algorithm 3): w_j += delta_j, z += delta_j X_j, and the loss
+ *           derivative u = l'(y, z) on the touched rows (Section 2.4).
+ *
+ * Conventions for every entry point:
+ *  - Return value: GENCD_OK (0), GENCD_NOT_CONVERGED (1, results valid) or a
+ *    negative error code.  On error, gencd_last_error() returns a message
+ *    (thread-local, valid until the next call on the same thread).  No C++
+ *    exception crosses this boundary.
+ *  - `memory` selects where a caller buffer lives: GENCD_HOST (pageable or
+ *    pinned host memory) or GENCD_DEVICE (memory of the problem's GPU).
+ *  - All GPU work runs on the CUDA stream given to gencd_create.  Calls that
+ *    return values to the host synchronise that stream before returning.
+ *  - Indices are 0-based.  Limits: n, k < 2^31, nnz < 2^31 - 64.
+ *  - A problem handle must not be used from two threads at once.
+ */
+#ifndef GENCD_H
+#define GENCD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define GENCD_OK 0
+#define GENCD_NOT_CONVERGED 1 /* max_iter or timeout reached; w is valid      */
+#define GENCD_EINVAL (-1)     /* bad argument or malformed CSC input          */
+#define GENCD_ENOMEM (-2)     /* device or pinned host allocation failed      */
+#define GENCD_ECUDA (-3)      /* a CUDA runtime call failed                   */
+#define GENCD_ETIMEOUT (-4)   /* a bounded device wait gave up                */
+#define GENCD_EDIVERGED (-5)  /* objective or KKT value became non-finite     */
+#define GENCD_ESTATE (-6)     /* call not valid in the problem's state        */
+
+typedef enum { GENCD_LOSS_SQUARED = 0, GENCD_LOSS_LOGISTIC = 1 } gencd_loss;
+
+/* Table 2 of the paper. */
+typedef enum {
+  GENCD_SHOTGUN = 0,       /* Select: random subset of P columns; Accept: all   */
+  GENCD_THREAD_GREEDY = 1, /* Select: all; Accept: best proxy per partition     */
+  GENCD_GREEDY = 2,        /* Select: all; Accept: the single best proxy        */
+  GENCD_COLORING = 3       /* Select: random colour class; Accept: all          */
+} gencd_variant;
+
+typedef enum { GENCD_F64 = 0, GENCD_F32 = 1 } gencd_precision;
+typedef enum { GENCD_HOST = 0, GENCD_DEVICE = 1 } gencd_memory;
+
+typedef struct gencd_problem gencd_problem; /* opaque, owned by the library */
+
+typedef struct {
+  int32_t variant;     /* gencd_variant                                         */
+  int32_t blocks;      /* Thread-Greedy partitions B (contiguous column chunks
+                          [floor(b k/B), floor((b+1) k/B))); 0 => min(k, 1024)  */
+  int64_t P;           /* Shotgun subset size; 0 => P* = floor(k / (2 rho)),
+                          rho = spectral radius of D^-1/2 X^T X D^-1/2 (Sec 4.1) */
+  uint64_t seed;       /* seed of the selection stream (SplitMix64)             */
+  int64_t max_iter;    /* iteration cap of gencd_solve                          */
+  double tol_kkt;      /* gencd_solve stops when the KKT violation <= tol_kkt   */
+  int32_t check_every; /* iterations between convergence checks                 */
+  int32_t beta_mode;   /* 0: beta_j = beta * ||X_j||^2 / n (default);
+                          1: the literal beta of Eq. 7 (1 squared, 1/4 logistic) */
+  double timeout_s;    /* wall-clock cap of gencd_solve in seconds; 0 = none    */
+} gencd_params;
+
+typedef struct {
+  int32_t status;        /* return code of the call                           */
+  int32_t reserved;
+  int64_t iters;         /* GenCD iterations run by the call                  */
+  int64_t updates;       /* accepted proposals applied (Algorithm 3)          */
+  int64_t nnz_processed; /* sum over proposals and updates of column nnz      */
+  double objective;      /* P(w) of Eq. 1 after the call (FP64)               */
+  double kkt;            /* max_j KKT violation after the call (FP64):
+                            max(|g_j| - lambda, 0) if w_j = 0,
+                            |g_j + lambda sign(w_j)| otherwise                 */
+  double seconds;        /* host wall time of the call                        */
+} gencd_result;
+
+/*
+ * Creates a problem from X in CSC form (Table 1; X is traversed by columns,
+ * Section 1) and labels y.
+ *   col_ptr  int64[k+1], non-decreasing, col_ptr[0] = 0, col_ptr[k] = nnz
+ *   row_idx  int32[nnz], strictly increasing within each column, in [0, n)
+ *   val      nnz values, double (val_dtype 0) or float (val_dtype 1)
+ *   y        double[n]; for logistic loss every y_i must be -1 or +1
+ *   loss     gencd_loss;  precision  gencd_precision of the device copy of X
+ *            and of u (FP32 mode accumulates X_j^T u in FP32 per thread)
+ *   memory   where col_ptr/row_idx/val/y live; the library copies them into
+ *            its own device buffers, so the caller may free them on return
+ *   stream   cudaStream_t (may be NULL for the legacy default stream)
+ * Initial state: w = 0, z = 0, lambda = 0, default parameters, iteration 0.
+ * Errors: GENCD_EINVAL for malformed input (the message names the first bad
+ * index), GENCD_ENOMEM, GENCD_ECUDA.  *out is NULL on error.
+ */
+int gencd_create(gencd_problem** out, int64_t n, int64_t k, int64_t nnz, const int64_t* col_ptr,
+                 const int32_t* row_idx, const void* val, int32_t val_dtype, const double* y,
+                 int32_t loss, int32_t precision, int32_t memory, void* stream);
+
+/* Frees every device and host buffer of the problem.  NULL is ignored. */
+void gencd_destroy(gencd_problem* p);
+
+/* Sets the l1 weight lambda >= 0 of Eq. 1 (state w, z is kept). */
+int gencd_set_lambda(gencd_problem* p, double lambda);
+
+/* lambda_max = max_j |g_j(w = 0)|, the smallest lambda for which w = 0 is
+ * optimal.  Computed on the GPU at create time. */
+int gencd_lambda_max(gencd_problem* p, double* lambda_max);
+
+/* Fills *out with the default parameters (Thread-Greedy, B = 0 (auto),
+ * P = 0 (auto), seed 0, max_iter 100000, tol_kkt 1e-8, check_every 10,
+ * beta_mode 0, no timeout). */
+int gencd_default_params(gencd_params* out);
+
+/* Validates and stores the iteration parameters. */
+int gencd_set_params(gencd_problem* p, const gencd_params* params);
+int gencd_get_params(gencd_problem* p, gencd_params* params);
+
+/*
+ * Runs GenCD iterations (Algorithm 1) until the KKT violation is at most
+ * tol_kkt, max_iter iterations or the timeout.  Convergence is checked every
+ * check_every iterations with a full pass over X.  Returns GENCD_OK,
+ * GENCD_NOT_CONVERGED, GENCD_EDIVERGED (non-finite objective) or an error.
+ * `out` (nullable) receives the statistics of the call.
+ */
+int gencd_solve(gencd_problem* p, gencd_result* out);
+
+/*
+ * Enqueues exactly `iters` GenCD iterations of the configured variant with no
+ * convergence test between them, then synchronises and fills `out` (nullable)
+ * with the objective and the KKT violation of the final state.  When `out` is
+ * NULL the call returns without synchronising (the work stays queued on the
+ * stream) and evaluates no objective.
+ */
+int gencd_iterate(gencd_problem* p, int64_t iters, gencd_result* out);
+
+/*
+ * Work counters accumulated since the last gencd_stats_reset (or since the
+ * last gencd_solve / gencd_iterate call made with a non-NULL result):
+ * iterations, accepted updates and non-zeros processed; objective and kkt
+ * hold the values last computed on the device (Thread-Greedy and Greedy
+ * iterations compute both for their start state).  Synchronises the stream.
+ */
+int gencd_stats(gencd_problem* p, gencd_result* out);
+int gencd_stats_reset(gencd_problem* p);
+
+/* Iteration counter t that drives Select (Shotgun chunk, Coloring colour). */
+int gencd_set_iteration(gencd_problem* p, int64_t t);
+int gencd_get_iteration(gencd_problem* p, int64_t* t);
+
+/* Copies w (double[k]) out to, or in from, a caller buffer.  gencd_set_w
+ * recomputes z = Xw (from a row-major copy of X built on first use) and u. */
+int gencd_get_w(gencd_problem* p, double* w, int64_t k, int32_t memory);
+int gencd_set_w(gencd_problem* p, const double* w, int64_t k, int32_t memory);
+/* Copies z = Xw (double[n], maintained incrementally by Algorithm 3). */
+int gencd_get_z(gencd_problem* p, double* z, int64_t n, int32_t memory);
+
+/* Objective P(w) of Eq. 1 and the KKT violation at the current state. */
+int gencd_objective(gencd_problem* p, double* objective, double* kkt);
+
+/*
+ * Parity hook for Algorithm 4: for the m columns J[0..m) (int32, in [0, k),
+ * repeats allowed) computes delta (Eq. 7) and phi (Eq. 9) at the current
+ * state without changing it.  J, delta and phi (double[m]) live in `memory`.
+ */
+int gencd_propose_at(gencd_problem* p, const int32_t* J, int64_t m, double* delta, double* phi,
+                     int32_t memory);
+
+/*
+ * Streaming propose over all k columns (the Thread-Greedy / Greedy Propose
+ * step, Table 2): writes delta and phi (double[k]) for every column at the
+ * current state; *kkt (nullable) receives the KKT violation.
+ */
+int gencd_propose_all(gencd_problem* p, double* delta, double* phi, int32_t memory, double* kkt);
+
+/* Spectral radius of D^-1/2 X^T X D^-1/2 by power iteration from the all-ones
+ * vector (at most 100 iterations, relative change 1e-6), and Shotgun's
+ * P* = max(1, floor(k / (2 rho))) (Section 4.1). */
+int gencd_spectral_radius(gencd_problem* p, double* rho, int64_t* pstar, int32_t* iters);
+
+/*
+ * Partial distance-2 colouring of the columns (Section 4.1: columns that
+ * share a row get different colours), computed on the GPU.  The result equals
+ * greedy first-fit in column order.  *ncolors receives the colour count.
+ */
+int gencd_color(gencd_problem* p, int32_t* ncolors);
+/* Copies the colours (int32[k]) out, or installs caller colours (validated:
+ * columns sharing a row must differ; colours in [0, k)). */
+int gencd_get_colors(gencd_problem* p, int32_t* colors, int64_t k, int32_t memory);
+int gencd_set_colors(gencd_problem* p, const int32_t* colors, int64_t k, int32_t memory);
+
+/*
+ * Selection permutation of 0..m-1 for `epoch` (computed on the GPU): the sort
+ * of (key_i >> 32, i) where key_i is output i of the SplitMix64 stream seeded
+ * with output `epoch` of the stream seeded with `seed`.  perm is int32[m] on
+ * the host.  Uses the problem's stream and scratch memory.
+ */
+int gencd_permutation(gencd_problem* p, uint64_t seed, int64_t epoch, int64_t m, int32_t* perm);
+
+/* Launch counts and, when profiling is enabled, summed device time (ms, CUDA
+ * events on the problem's stream) per kernel family:
+ * 0 streaming propose, 1 finalize, 2 accept, 3 update, 4 refresh,
+ * 5 list propose, 6 Coloring iteration, 7 objective, 8 setup/selection. */
+int gencd_profile_enable(gencd_problem* p, int32_t enable);
+int gencd_profile_read(gencd_problem* p, int32_t kernel, double* ms, int64_t* launches);
+int gencd_profile_reset(gencd_problem* p);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* gencd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,436 @@
+"""Thin ctypes binding of libgencd (include/gencd.h).
+
+Argument marshalling only: every step of GenCD runs in the CUDA library.
+Functions keep the C names.  Host buffers are numpy arrays; device buffers are
+CUDA torch tensors (their data pointer is passed with GENCD_DEVICE).  The CUDA
+stream defaults to torch's current stream.
+
+Loading fails loudly when the library has not been built: there is no CPU
+fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgencd.so")
+
+GENCD_OK = 0
+GENCD_NOT_CONVERGED = 1
+GENCD_EINVAL = -1
+GENCD_ENOMEM = -2
+GENCD_ECUDA = -3
+GENCD_ETIMEOUT = -4
+GENCD_EDIVERGED = -5
+GENCD_ESTATE = -6
+
+GENCD_LOSS_SQUARED, GENCD_LOSS_LOGISTIC = 0, 1
+GENCD_SHOTGUN, GENCD_THREAD_GREEDY, GENCD_GREEDY, GENCD_COLORING = 0, 1, 2, 3
+GENCD_F64, GENCD_F32 = 0, 1
+GENCD_HOST, GENCD_DEVICE = 0, 1
+
+LOSSES = {"squared": GENCD_LOSS_SQUARED, "logistic": GENCD_LOSS_LOGISTIC}
+VARIANTS = {"shotgun": GENCD_SHOTGUN, "thread_greedy": GENCD_THREAD_GREEDY, "greedy": GENCD_GREEDY,
+            "coloring": GENCD_COLORING}
+PRECISIONS = {"f64": GENCD_F64, "f32": GENCD_F32}
+KERNELS = ["propose_all", "finalize", "accept", "update", "refresh", "propose_list", "coloring_iter",
+           "objective", "setup"]
+
+# every symbol include/gencd.h declares
+EXPORTS = ["gencd_create", "gencd_destroy", "gencd_set_lambda", "gencd_lambda_max",
+           "gencd_default_params", "gencd_set_params", "gencd_get_params", "gencd_solve",
+           "gencd_iterate", "gencd_set_iteration", "gencd_get_iteration", "gencd_get_w",
+           "gencd_set_w", "gencd_get_z", "gencd_objective", "gencd_propose_at", "gencd_propose_all",
+           "gencd_spectral_radius", "gencd_color", "gencd_get_colors", "gencd_set_colors",
+           "gencd_permutation", "gencd_profile_enable", "gencd_profile_read", "gencd_profile_reset",
+           "gencd_last_error", "gencd_stats", "gencd_stats_reset"]
+
+
+class gencd_params(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("blocks", C.c_int32), ("P", C.c_int64), ("seed", C.c_uint64),
+                ("max_iter", C.c_int64), ("tol_kkt", C.c_double), ("check_every", C.c_int32),
+                ("beta_mode", C.c_int32), ("timeout_s", C.c_double)]
+
+
+class gencd_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("reserved", C.c_int32), ("iters", C.c_int64),
+                ("updates", C.c_int64), ("nnz_processed", C.c_int64), ("objective", C.c_double),
+                ("kkt", C.c_double), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class GencdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"gencd error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Loads libgencd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        pp = C.POINTER(C.c_void_p)
+        sig = {
+            "gencd_create": (C.c_int, [pp, i64, i64, i64, vp, vp, vp, i32, vp, i32, i32, i32, vp]),
+            "gencd_destroy": (None, [vp]),
+            "gencd_set_lambda": (C.c_int, [vp, f64]),
+            "gencd_lambda_max": (C.c_int, [vp, C.POINTER(f64)]),
+            "gencd_default_params": (C.c_int, [C.POINTER(gencd_params)]),
+            "gencd_set_params": (C.c_int, [vp, C.POINTER(gencd_params)]),
+            "gencd_get_params": (C.c_int, [vp, C.POINTER(gencd_params)]),
+            "gencd_solve": (C.c_int, [vp, C.POINTER(gencd_result)]),
+            "gencd_iterate": (C.c_int, [vp, i64, C.POINTER(gencd_result)]),
+            "gencd_set_iteration": (C.c_int, [vp, i64]),
+            "gencd_get_iteration": (C.c_int, [vp, C.POINTER(i64)]),
+            "gencd_get_w": (C.c_int, [vp, vp, i64, i32]),
+            "gencd_set_w": (C.c_int, [vp, vp, i64, i32]),
+            "gencd_get_z": (C.c_int, [vp, vp, i64, i32]),
+            "gencd_objective": (C.c_int, [vp, C.POINTER(f64), C.POINTER(f64)]),
+            "gencd_propose_at": (C.c_int, [vp, vp, i64, vp, vp, i32]),
+            "gencd_propose_all": (C.c_int, [vp, vp, vp, i32, C.POINTER(f64)]),
+            "gencd_spectral_radius": (C.c_int, [vp, C.POINTER(f64), C.POINTER(i64), C.POINTER(i32)]),
+            "gencd_color": (C.c_int, [vp, C.POINTER(i32)]),
+            "gencd_get_colors": (C.c_int, [vp, vp, i64, i32]),
+            "gencd_set_colors": (C.c_int, [vp, vp, i64, i32]),
+            "gencd_permutation": (C.c_int, [vp, C.c_uint64, i64, i64, vp]),
+            "gencd_profile_enable": (C.c_int, [vp, i32]),
+            "gencd_profile_read": (C.c_int, [vp, i32, C.POINTER(f64), C.POINTER(i64)]),
+            "gencd_profile_reset": (C.c_int, [vp]),
+            "gencd_last_error": (C.c_char_p, []),
+            "gencd_stats": (C.c_int, [vp, C.POINTER(gencd_result)]),
+            "gencd_stats_reset": (C.c_int, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def gencd_last_error() -> str:
+    return lib().gencd_last_error().decode()
+
+
+def _check(rc):
+    if rc < 0:
+        raise GencdError(rc, gencd_last_error())
+    return rc
+
+
+def _is_cuda_tensor(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _buf(a, dtype):
+    """(pointer, memory kind, keep-alive) of a numpy array or a CUDA tensor."""
+    if a is None:
+        return None, GENCD_HOST, None
+    if _is_cuda_tensor(a):
+        if not a.is_contiguous():
+            raise ValueError("device tensors must be contiguous")
+        return C.c_void_p(a.data_ptr()), GENCD_DEVICE, a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return C.c_void_p(arr.ctypes.data), GENCD_HOST, arr
+
+
+def default_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return 0
+
+
+def gencd_create(n, k, nnz, col_ptr, row_idx, val, y, loss="logistic", precision="f64", stream=None):
+    """Returns an opaque handle (c_void_p).  Inputs are all numpy arrays (host)
+    or all CUDA tensors (device); the library copies them."""
+    if _is_cuda_tensor(val):
+        val_dtype = 0 if str(val.dtype) == "torch.float64" else 1
+        vdt = None
+    else:
+        vdt = np.float32 if np.asarray(val).dtype == np.float32 else np.float64
+        val_dtype = 0 if vdt == np.float64 else 1
+    cp, m0, k0 = _buf(col_ptr, np.int64)
+    ri, m1, k1 = _buf(row_idx, np.int32)
+    va, m2, k2 = _buf(val, vdt)
+    yy, m3, k3 = _buf(y, np.float64)
+    mems = {m0, m1, m2, m3} if nnz > 0 else {m0, m3}
+    if len(mems) != 1:
+        raise ValueError("inputs must be all host arrays or all device tensors")
+    handle = C.c_void_p()
+    st = default_stream() if stream is None else int(stream)
+    _check(lib().gencd_create(C.byref(handle), int(n), int(k), int(nnz), cp, ri, va, val_dtype, yy,
+                              LOSSES.get(loss, loss), PRECISIONS.get(precision, precision), mems.pop(),
+                              C.c_void_p(st)))
+    del k0, k1, k2, k3
+    return handle
+
+
+def gencd_destroy(h):
+    lib().gencd_destroy(h)
+
+
+def gencd_set_lambda(h, lam):
+    _check(lib().gencd_set_lambda(h, float(lam)))
+
+
+def gencd_lambda_max(h) -> float:
+    v = C.c_double()
+    _check(lib().gencd_lambda_max(h, C.byref(v)))
+    return v.value
+
+
+def gencd_default_params() -> gencd_params:
+    p = gencd_params()
+    _check(lib().gencd_default_params(C.byref(p)))
+    return p
+
+
+def gencd_set_params(h, params: gencd_params):
+    _check(lib().gencd_set_params(h, C.byref(params)))
+
+
+def gencd_get_params(h) -> gencd_params:
+    p = gencd_params()
+    _check(lib().gencd_get_params(h, C.byref(p)))
+    return p
+
+
+def gencd_solve(h) -> gencd_result:
+    """Runs to convergence; a diverged solve is reported in result.status
+    (GENCD_EDIVERGED) rather than raised."""
+    r = gencd_result()
+    rc = lib().gencd_solve(h, C.byref(r))
+    if rc < 0 and rc != GENCD_EDIVERGED:
+        _check(rc)
+    return r
+
+
+def gencd_iterate(h, iters, sync=True):
+    if not sync:
+        _check(lib().gencd_iterate(h, int(iters), None))
+        return None
+    r = gencd_result()
+    _check(lib().gencd_iterate(h, int(iters), C.byref(r)))
+    return r
+
+
+def gencd_stats(h) -> gencd_result:
+    r = gencd_result()
+    _check(lib().gencd_stats(h, C.byref(r)))
+    return r
+
+
+def gencd_stats_reset(h):
+    _check(lib().gencd_stats_reset(h))
+
+
+def gencd_set_iteration(h, t):
+    _check(lib().gencd_set_iteration(h, int(t)))
+
+
+def gencd_get_iteration(h) -> int:
+    v = C.c_int64()
+    _check(lib().gencd_get_iteration(h, C.byref(v)))
+    return v.value
+
+
+def gencd_get_w(h, k, out=None):
+    """w as a numpy array (or into `out`, a CUDA float64 tensor)."""
+    if out is not None and _is_cuda_tensor(out):
+        _check(lib().gencd_get_w(h, C.c_void_p(out.data_ptr()), int(k), GENCD_DEVICE))
+        return out
+    w = np.empty(int(k))
+    _check(lib().gencd_get_w(h, C.c_void_p(w.ctypes.data), int(k), GENCD_HOST))
+    return w
+
+
+def gencd_set_w(h, w):
+    ptr, mem, keep = _buf(w, np.float64)
+    n = keep.numel() if _is_cuda_tensor(keep) else keep.size
+    _check(lib().gencd_set_w(h, ptr, int(n), mem))
+
+
+def gencd_get_z(h, n):
+    z = np.empty(int(n))
+    _check(lib().gencd_get_z(h, C.c_void_p(z.ctypes.data), int(n), GENCD_HOST))
+    return z
+
+
+def gencd_objective(h):
+    o, kk = C.c_double(), C.c_double()
+    _check(lib().gencd_objective(h, C.byref(o), C.byref(kk)))
+    return o.value, kk.value
+
+
+def gencd_propose_at(h, J):
+    J = np.ascontiguousarray(J, np.int32)
+    d = np.empty(J.size)
+    f = np.empty(J.size)
+    _check(lib().gencd_propose_at(h, C.c_void_p(J.ctypes.data), J.size, C.c_void_p(d.ctypes.data),
+                                  C.c_void_p(f.ctypes.data), GENCD_HOST))
+    return d, f
+
+
+def gencd_propose_all(h, k):
+    d = np.empty(int(k))
+    f = np.empty(int(k))
+    kk = C.c_double()
+    _check(lib().gencd_propose_all(h, C.c_void_p(d.ctypes.data), C.c_void_p(f.ctypes.data), GENCD_HOST,
+                                   C.byref(kk)))
+    return d, f, kk.value
+
+
+def gencd_spectral_radius(h):
+    rho, ps, it = C.c_double(), C.c_int64(), C.c_int32()
+    _check(lib().gencd_spectral_radius(h, C.byref(rho), C.byref(ps), C.byref(it)))
+    return rho.value, ps.value, it.value
+
+
+def gencd_color(h) -> int:
+    c = C.c_int32()
+    _check(lib().gencd_color(h, C.byref(c)))
+    return c.value
+
+
+def gencd_get_colors(h, k):
+    c = np.empty(int(k), np.int32)
+    _check(lib().gencd_get_colors(h, C.c_void_p(c.ctypes.data), int(k), GENCD_HOST))
+    return c
+
+
+def gencd_set_colors(h, colors):
+    c = np.ascontiguousarray(colors, np.int32)
+    _check(lib().gencd_set_colors(h, C.c_void_p(c.ctypes.data), c.size, GENCD_HOST))
+
+
+def gencd_permutation(h, seed, epoch, m):
+    out = np.empty(int(m), np.int32)
+    _check(lib().gencd_permutation(h, int(seed) & ((1 << 64) - 1), int(epoch), int(m),
+                                   C.c_void_p(out.ctypes.data)))
+    return out
+
+
+def gencd_profile_enable(h, enable=True):
+    _check(lib().gencd_profile_enable(h, 1 if enable else 0))
+
+
+def gencd_profile_read(h, kernel):
+    kid = KERNELS.index(kernel) if isinstance(kernel, str) else int(kernel)
+    ms, n = C.c_double(), C.c_int64()
+    _check(lib().gencd_profile_read(h, kid, C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+def gencd_profile_reset(h):
+    _check(lib().gencd_profile_reset(h))
+
+
+class Problem:
+    """Owns one gencd handle; methods forward to the C calls above."""
+
+    def __init__(self, prob=None, *, n=None, k=None, col_ptr=None, row_idx=None, val=None, y=None,
+                 loss=None, precision="f64", stream=None):
+        if prob is not None:
+            n, k, col_ptr, row_idx, val, y = prob.n, prob.k, prob.col_ptr, prob.row_idx, prob.val, prob.y
+            loss = loss or prob.loss
+        nnz = int(col_ptr[-1]) if not _is_cuda_tensor(col_ptr) else int(col_ptr[-1].item())
+        self.n, self.k, self.nnz = int(n), int(k), nnz
+        self.h = gencd_create(n, k, nnz, col_ptr, row_idx, val, y, loss or "logistic", precision, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            gencd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_lambda(self, lam):
+        gencd_set_lambda(self.h, lam)
+
+    def lambda_max(self):
+        return gencd_lambda_max(self.h)
+
+    def set_params(self, **kw):
+        p = gencd_get_params(self.h)
+        for key, v in kw.items():
+            if key == "variant" and isinstance(v, str):
+                v = VARIANTS[v]
+            setattr(p, key, v)
+        gencd_set_params(self.h, p)
+        return p
+
+    def solve(self):
+        return gencd_solve(self.h)
+
+    def iterate(self, iters, sync=True):
+        return gencd_iterate(self.h, iters, sync)
+
+    def w(self):
+        return gencd_get_w(self.h, self.k)
+
+    def z(self):
+        return gencd_get_z(self.h, self.n)
+
+    def set_w(self, w):
+        gencd_set_w(self.h, w)
+
+    def objective(self):
+        return gencd_objective(self.h)
+
+    def propose_at(self, J):
+        return gencd_propose_at(self.h, J)
+
+    def propose_all(self):
+        return gencd_propose_all(self.h, self.k)
+
+    def spectral_radius(self):
+        return gencd_spectral_radius(self.h)
+
+    def color(self):
+        return gencd_color(self.h)
+
+    def colors(self):
+        return gencd_get_colors(self.h, self.k)
+
+    def set_colors(self, c):
+        gencd_set_colors(self.h, c)
+
+    def permutation(self, seed, epoch, m):
+        return gencd_permutation(self.h, seed, epoch, m)
+
+    def set_iteration(self, t):
+        gencd_set_iteration(self.h, t)
+
+    def stats(self):
+        return gencd_stats(self.h)
+
+    def stats_reset(self):
+        gencd_stats_reset(self.h)

@@ -1,0 +1,770 @@
+// api.cu -- the C ABI of libgencd: problem lifecycle, the GenCD iteration
+// loop (Algorithm 1) for each variant of Table 2, and the parity hooks.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "device_math.cuh"
+#include "gencd_internal.cuh"
+
+namespace gencd {
+
+static thread_local std::string g_err;
+void set_error(const std::string& m) { g_err = m; }
+const char* last_error() { return g_err.c_str(); }
+
+static int fail(int code, const std::string& m) {
+  set_error(m);
+  return code;
+}
+
+// ---- profiling -------------------------------------------------------------
+static void prof_flush(gencd_problem* p) {
+  if (p->prof.used == 0) return;
+  cudaStreamSynchronize(p->stream);
+  for (size_t q = 0; q < p->prof.pending_id.size(); ++q) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->prof.pool[2 * q], p->prof.pool[2 * q + 1]) == cudaSuccess)
+      p->prof.ms[p->prof.pending_id[q]] += ms;
+  }
+  cudaGetLastError();
+  p->prof.pending_id.clear();
+  p->prof.used = 0;
+}
+
+void prof_begin(gencd_problem* p, int id, cudaEvent_t* stop) {
+  p->prof.launches[id] += 1;
+  *stop = nullptr;
+  if (!p->prof.enabled || p->prof.pool.empty()) return;
+  if (p->prof.used + 2 > p->prof.pool.size()) prof_flush(p);
+  cudaEvent_t a = p->prof.pool[p->prof.used];
+  *stop = p->prof.pool[p->prof.used + 1];
+  p->prof.used += 2;
+  p->prof.pending_id.push_back(id);
+  cudaEventRecord(a, p->stream);
+}
+
+void prof_end(gencd_problem* p, cudaEvent_t stop) {
+  if (stop) cudaEventRecord(stop, p->stream);
+}
+
+// ---- small kernels used only here -------------------------------------------
+template <typename S, typename D>
+__global__ void k_convert(const S* __restrict__ in, int64_t m, D* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) out[i] = (D)in[i];
+}
+
+__global__ void k_dinv(const double* __restrict__ c, int64_t k, double n, double* __restrict__ dinv,
+                       double* __restrict__ v) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const double v0 = 1.0 / sqrt((double)k);
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) {
+    const double s = c[j] * n;  // ||X_j||^2
+    dinv[j] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+    v[j] = v0;
+  }
+}
+
+// t_j = dinv_j * gacc_j (gacc reset to 0); red[block] = sum of t_j^2
+__global__ void __launch_bounds__(kThreads)
+    k_power_finish(double* __restrict__ gacc, const double* __restrict__ dinv, int64_t k,
+                   double* __restrict__ t, double* __restrict__ red) {
+  __shared__ double sm[kThreads / 32];
+  double s = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) {
+    const double x = dinv[j] * gacc[j];
+    gacc[j] = 0.0;
+    t[j] = x;
+    s = fma(x, x, s);
+  }
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) b += sm[q];
+    red[blockIdx.x] = b;
+  }
+}
+
+__global__ void k_sum_partials(const double* __restrict__ red, int nb, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += red[b];
+    *out = s;
+  }
+}
+
+__global__ void k_div(const double* __restrict__ t, int64_t k, double r, double* __restrict__ v) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) v[j] = t[j] / r;
+}
+
+__global__ void k_check_colors(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                               const int32_t* __restrict__ color, int64_t n, int64_t k,
+                               unsigned long long* __restrict__ bad) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    for (int64_t a = row_ptr[i]; a < row_ptr[i + 1]; ++a) {
+      const int32_t ca = color[col_idx[a]];
+      if (ca < 0 || ca >= k) atomicMin(bad, (unsigned long long)i);
+      for (int64_t b = a + 1; b < row_ptr[i + 1]; ++b)
+        if (color[col_idx[b]] == ca) atomicMin(bad, (unsigned long long)i);
+    }
+  }
+}
+
+__global__ void k_max_i32(const int32_t* __restrict__ a, int64_t m, unsigned long long* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int32_t mx = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) mx = a[i] > mx ? a[i] : mx;
+  atomicMax(out, (unsigned long long)mx);
+}
+
+// ---- helpers -----------------------------------------------------------------
+static cudaMemcpyKind kind_in(int32_t memory) {
+  return memory == GENCD_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+static cudaMemcpyKind kind_out(int32_t memory) {
+  return memory == GENCD_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+template <typename T>
+static int dalloc(T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc((void**)ptr, sizeof(T) * count) != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return fail(GENCD_ENOMEM, "cudaMalloc of " + std::to_string(sizeof(T) * count) + " bytes failed");
+  }
+  return GENCD_OK;
+}
+
+static int reset_counters(gencd_problem* p) {
+  GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal + 4, 0, 2 * sizeof(double), p->stream));
+  p->stat_iters = 0;
+  p->stat_host_nnz = 0;
+  return GENCD_OK;
+}
+
+static int effective_B(const gencd_problem* p) {
+  if (p->params.variant == GENCD_GREEDY) return 1;
+  int64_t B = p->params.blocks > 0 ? p->params.blocks : 1024;
+  if (B > p->k) B = p->k;
+  return (int)B;
+}
+
+// KKT violation (dscal[0]) and objective (dscal[1]) of the current state
+static int enqueue_evaluate(gencd_problem* p) {
+  GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal, 0, sizeof(double), p->stream));
+  GENCD_TRY(launch_propose_all(p, p->u, p->precision == GENCD_F64));
+  GENCD_TRY(launch_finalize(p, p->lambda, false));
+  GENCD_TRY(launch_objective(p));
+  return GENCD_OK;
+}
+
+static int read_scalars(gencd_problem* p) {
+  GENCD_CUDA_TRY(cudaMemcpyAsync(p->hpin, p->dscal, 8 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  GENCD_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return GENCD_OK;
+}
+
+static int compute_pstar(gencd_problem* p, int32_t* iters_out);
+
+static int ensure_selection(gencd_problem* p, int64_t epoch, int64_t m) {
+  if (p->perm_epoch == epoch && p->perm_m == m) return GENCD_OK;
+  GENCD_TRY(make_permutation(p, p->params.seed, epoch, m, p->perm));
+  p->perm_epoch = epoch;
+  p->perm_m = m;
+  return GENCD_OK;
+}
+
+// one GenCD iteration (Algorithm 1) of the configured variant, enqueued
+static int enqueue_iteration(gencd_problem* p, int64_t* host_nnz) {
+  const int v = p->params.variant;
+  if (v == GENCD_THREAD_GREEDY || v == GENCD_GREEDY) {
+    const int B = effective_B(p);
+    GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal, 0, sizeof(double), p->stream));
+    GENCD_TRY(launch_propose_all(p, p->u, p->precision == GENCD_F64));  // Propose, all columns
+    GENCD_TRY(launch_finalize(p, p->lambda, true));                      // + KKT of the start state
+    GENCD_TRY(launch_objective(p));                                      // objective of the start state
+    GENCD_TRY(launch_accept(p, B));                                      // Accept, best per partition
+    GENCD_TRY(launch_update_list(p, p->list_j, p->list_d, B, true));     // Update (atomic z)
+    GENCD_TRY(launch_refresh_list(p, p->list_j, p->list_d, B, true));
+    *host_nnz += p->nnz;
+    p->stat_host_nnz += p->nnz;
+  } else if (v == GENCD_SHOTGUN) {
+    if (p->pstar == 0 && p->params.P == 0) GENCD_TRY(compute_pstar(p, nullptr));
+    int64_t P = p->params.P > 0 ? p->params.P : p->pstar;
+    if (P > p->k) P = p->k;
+    const int64_t per_epoch = (p->k + P - 1) / P;
+    const int64_t e = p->t / per_epoch, q = p->t % per_epoch;
+    GENCD_TRY(ensure_selection(p, e, p->k));                             // Select, random subset
+    const int64_t lo = q * P, m = (lo + P <= p->k ? P : p->k - lo);
+    const int32_t* J = p->perm + lo;
+    GENCD_TRY(launch_propose_list(p, J, m, p->list_d, p->phi));          // Propose (Jacobi)
+    GENCD_TRY(launch_update_list(p, J, p->list_d, m, false));            // Accept all, Update
+    GENCD_TRY(launch_refresh_list(p, J, p->list_d, m, false));
+  } else if (v == GENCD_COLORING) {
+    if (!p->color) GENCD_TRY(run_coloring(p));
+    const int64_t C = p->ncolors;
+    const int64_t e = p->t / C, q = p->t % C;
+    GENCD_TRY(ensure_selection(p, e, C));                                // Select, random colour
+    GENCD_TRY(launch_coloring_iter(p, q));                               // Propose + Update fused
+  } else {
+    return fail(GENCD_EINVAL, "unknown variant");
+  }
+  p->t += 1;
+  p->stat_iters += 1;
+  return GENCD_OK;
+}
+
+static int compute_pstar(gencd_problem* p, int32_t* iters_out) {
+  GENCD_TRY(build_csr(p));
+  const int64_t k = p->k;
+  double *dinv = nullptr, *v = nullptr, *s = nullptr, *t = nullptr, *r = nullptr;
+  int rc = GENCD_OK;
+  if ((rc = dalloc(&dinv, k)) || (rc = dalloc(&v, k)) || (rc = dalloc(&s, k)) || (rc = dalloc(&t, k)) ||
+      (rc = dalloc(&r, p->n))) {
+    cudaFree(dinv);
+    cudaFree(v);
+    cudaFree(s);
+    cudaFree(t);
+    cudaFree(r);
+    return rc;
+  }
+  const int g = p->num_sms * 8;
+  k_dinv<<<grid_for(k, kThreads, g), kThreads, 0, p->stream>>>(p->c, k, (double)p->n, dinv, v);
+  double rho = 0.0;
+  int it = 0;
+  const int nb = grid_for(k, kThreads, kRedBlocks);
+  for (it = 1; it <= 100 && rc == GENCD_OK; ++it) {
+    if ((rc = launch_power_step(p, v, dinv, r, s)) != GENCD_OK) break;
+    k_power_finish<<<nb, kThreads, 0, p->stream>>>(p->gacc, dinv, k, t, p->red);
+    k_sum_partials<<<1, 32, 0, p->stream>>>(p->red, nb, p->dscal + 6);
+    p->prof.launches[K_SETUP] += 2;
+    if ((rc = read_scalars(p)) != GENCD_OK) break;
+    const double rho_new = std::sqrt(p->hpin[6]);
+    if (rho_new == 0.0) {
+      rho = 0.0;
+      break;
+    }
+    k_div<<<grid_for(k, kThreads, g), kThreads, 0, p->stream>>>(t, k, rho_new, v);
+    const bool done = std::fabs(rho_new - rho) <= 1e-6 * rho_new;
+    rho = rho_new;
+    if (done) break;
+  }
+  if (it > 100) it = 100;
+  cudaFree(dinv);
+  cudaFree(v);
+  cudaFree(s);
+  cudaFree(t);
+  cudaFree(r);
+  if (rc != GENCD_OK) return rc;
+  p->rho = rho;
+  double ps = rho > 0.0 ? std::floor((double)k / (2.0 * rho)) : (double)k;
+  if (ps < 1.0) ps = 1.0;
+  if (ps > (double)k) ps = (double)k;
+  p->pstar = (int64_t)ps;
+  if (iters_out) *iters_out = it;
+  return GENCD_OK;
+}
+
+static void free_problem(gencd_problem* p) {
+  if (!p) return;
+  void* bufs[] = {p->col_ptr, p->row_idx, p->val, p->y, p->z, p->u, p->w, p->c, p->tile_col, p->gacc,
+                  p->delta, p->phi, p->list_j, p->list_d, p->dscal, p->red, p->perm, p->sort_tmp,
+                  p->row_ptr, p->col_idx, p->csr_val, p->color, p->color_ptr, p->cols_by_color};
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (p->hpin) cudaFreeHost(p->hpin);
+  for (cudaEvent_t e : p->prof.pool) cudaEventDestroy(e);
+  cudaGetLastError();
+  delete p;
+}
+
+static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* row_idx, const void* val,
+                       int32_t val_dtype, const double* y, int32_t memory) {
+  const int64_t n = p->n, k = p->k, nnz = p->nnz;
+  GENCD_CUDA_TRY(cudaGetDevice(&p->device));
+  GENCD_CUDA_TRY(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+  p->items = p->precision == GENCD_F64 ? kItemsF64 : kItemsF32;
+  p->nnz_pad = ((nnz + kPadNnz - 1) / kPadNnz) * kPadNnz + kPadNnz;
+  const int64_t tile = 32LL * p->items;
+  p->ntiles = (nnz + tile - 1) / tile;
+  const size_t vsz = p->precision == GENCD_F64 ? 8 : 4;
+
+  GENCD_TRY(dalloc(&p->col_ptr, k + 1));
+  GENCD_TRY(dalloc(&p->row_idx, p->nnz_pad));
+  GENCD_TRY(dalloc((char**)&p->val, vsz * p->nnz_pad));
+  GENCD_TRY(dalloc(&p->y, n));
+  GENCD_TRY(dalloc(&p->z, n));
+  GENCD_TRY(dalloc((char**)&p->u, vsz * n));
+  GENCD_TRY(dalloc(&p->w, k));
+  GENCD_TRY(dalloc(&p->c, k));
+  GENCD_TRY(dalloc(&p->tile_col, p->ntiles + 1));
+  GENCD_TRY(dalloc(&p->gacc, k));
+  GENCD_TRY(dalloc(&p->delta, k));
+  GENCD_TRY(dalloc(&p->phi, k));
+  GENCD_TRY(dalloc(&p->list_j, k));
+  GENCD_TRY(dalloc(&p->list_d, k));
+  GENCD_TRY(dalloc(&p->perm, k));
+  GENCD_TRY(dalloc(&p->dscal, 8));
+  GENCD_TRY(dalloc(&p->red, 2 * kRedBlocks));
+  if (cudaMallocHost((void**)&p->hpin, 8 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GENCD_ENOMEM, "pinned host allocation failed");
+  }
+  cudaStream_t st = p->stream;
+  GENCD_CUDA_TRY(cudaMemsetAsync(p->row_idx, 0, sizeof(int32_t) * p->nnz_pad, st));
+  GENCD_CUDA_TRY(cudaMemsetAsync(p->val, 0, vsz * p->nnz_pad, st));
+  GENCD_CUDA_TRY(cudaMemcpyAsync(p->col_ptr, col_ptr, sizeof(int64_t) * (k + 1), kind_in(memory), st));
+  if (nnz > 0) {
+    GENCD_CUDA_TRY(cudaMemcpyAsync(p->row_idx, row_idx, sizeof(int32_t) * nnz, kind_in(memory), st));
+    const size_t in_sz = val_dtype == 0 ? 8 : 4;
+    if (in_sz == vsz) {
+      GENCD_CUDA_TRY(cudaMemcpyAsync(p->val, val, vsz * nnz, kind_in(memory), st));
+    } else {
+      void* tmp = nullptr;
+      GENCD_CUDA_TRY(cudaMallocAsync(&tmp, in_sz * nnz, st));
+      GENCD_CUDA_TRY(cudaMemcpyAsync(tmp, val, in_sz * nnz, kind_in(memory), st));
+      const int g = grid_for(nnz, kThreads, p->num_sms * 8);
+      if (val_dtype == 0)
+        k_convert<double, float><<<g, kThreads, 0, st>>>((const double*)tmp, nnz, (float*)p->val);
+      else
+        k_convert<float, double><<<g, kThreads, 0, st>>>((const float*)tmp, nnz, (double*)p->val);
+      GENCD_CUDA_TRY(cudaGetLastError());
+      GENCD_CUDA_TRY(cudaFreeAsync(tmp, st));
+    }
+  }
+  GENCD_CUDA_TRY(cudaMemcpyAsync(p->y, y, sizeof(double) * n, kind_in(memory), st));
+
+  int64_t bad_col = -1, bad_row = -1;
+  int stage = 0;
+  GENCD_TRY(validate_input(p, &bad_col, &bad_row, &stage));
+  if (bad_col >= 0)
+    return fail(GENCD_EINVAL, stage == 0 ? "col_ptr is not a valid CSC pointer array at column " +
+                                               std::to_string(bad_col)
+                                         : "column " + std::to_string(bad_col) +
+                                               " has unsorted, duplicate or out-of-range rows or a "
+                                               "non-finite value");
+  if (bad_row >= 0)
+    return fail(GENCD_EINVAL, "label y[" + std::to_string(bad_row) + "] is not finite" +
+                                  (p->loss == GENCD_LOSS_LOGISTIC ? " or not -1/+1 (logistic loss)" : ""));
+
+  GENCD_CUDA_TRY(cudaMemsetAsync(p->z, 0, sizeof(double) * n, st));
+  GENCD_CUDA_TRY(cudaMemsetAsync(p->w, 0, sizeof(double) * k, st));
+  GENCD_CUDA_TRY(cudaMemsetAsync(p->gacc, 0, sizeof(double) * k, st));
+  GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal, 0, 8 * sizeof(double), st));
+  GENCD_TRY(launch_col_scale(p));
+  GENCD_TRY(launch_tile_map(p));
+  GENCD_TRY(launch_fill_u(p));
+  // lambda_max = KKT violation of w = 0 at lambda = 0
+  GENCD_TRY(launch_propose_all(p, p->u, p->precision == GENCD_F64));
+  GENCD_TRY(launch_finalize(p, 0.0, false));
+  GENCD_TRY(read_scalars(p));
+  p->lambda_max = p->hpin[0];
+  gencd_default_params(&p->params);
+  for (int i = 0; i < 2 * 4096; ++i) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) break;
+    p->prof.pool.push_back(e);
+  }
+  cudaGetLastError();
+  return GENCD_OK;
+}
+
+}  // namespace gencd
+
+using namespace gencd;
+
+#define GENCD_CHECK_HANDLE(p)                                      \
+  do {                                                             \
+    if (!(p)) return fail(GENCD_EINVAL, "problem handle is NULL"); \
+  } while (0)
+
+extern "C" {
+
+const char* gencd_last_error(void) { return last_error(); }
+
+int gencd_default_params(gencd_params* out) {
+  if (!out) return fail(GENCD_EINVAL, "params is NULL");
+  std::memset(out, 0, sizeof(*out));
+  out->variant = GENCD_THREAD_GREEDY;
+  out->blocks = 0;
+  out->P = 0;
+  out->seed = 0;
+  out->max_iter = 100000;
+  out->tol_kkt = 1e-8;
+  out->check_every = 10;
+  out->beta_mode = 0;
+  out->timeout_s = 0.0;
+  return GENCD_OK;
+}
+
+int gencd_create(gencd_problem** out, int64_t n, int64_t k, int64_t nnz, const int64_t* col_ptr,
+                 const int32_t* row_idx, const void* val, int32_t val_dtype, const double* y, int32_t loss,
+                 int32_t precision, int32_t memory, void* stream) {
+  set_error("");
+  if (!out) return fail(GENCD_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || k < 1 || nnz < 0) return fail(GENCD_EINVAL, "need n >= 1, k >= 1, nnz >= 0");
+  if (n >= (int64_t(1) << 31) || k >= (int64_t(1) << 31) || nnz >= (int64_t(1) << 31) - 2 * kPadNnz)
+    return fail(GENCD_EINVAL, "n, k and nnz must be below 2^31");
+  if (!col_ptr || !y || (nnz > 0 && (!row_idx || !val)))
+    return fail(GENCD_EINVAL, "a required input pointer is NULL");
+  if (val_dtype != 0 && val_dtype != 1) return fail(GENCD_EINVAL, "val_dtype must be 0 (double) or 1 (float)");
+  if (loss != GENCD_LOSS_SQUARED && loss != GENCD_LOSS_LOGISTIC) return fail(GENCD_EINVAL, "unknown loss");
+  if (precision != GENCD_F64 && precision != GENCD_F32) return fail(GENCD_EINVAL, "unknown precision");
+  if (memory != GENCD_HOST && memory != GENCD_DEVICE) return fail(GENCD_EINVAL, "unknown memory kind");
+  gencd_problem* p = new (std::nothrow) gencd_problem();
+  if (!p) return fail(GENCD_ENOMEM, "host allocation failed");
+  p->n = n;
+  p->k = k;
+  p->nnz = nnz;
+  p->loss = loss;
+  p->precision = precision;
+  p->stream = (cudaStream_t)stream;
+  int rc = create_impl(p, col_ptr, row_idx, val, val_dtype, y, memory);
+  if (rc != GENCD_OK) {
+    std::string keep = last_error();
+    free_problem(p);
+    set_error(keep);
+    return rc;
+  }
+  *out = p;
+  return GENCD_OK;
+}
+
+void gencd_destroy(gencd_problem* p) { free_problem(p); }
+
+int gencd_set_lambda(gencd_problem* p, double lambda) {
+  GENCD_CHECK_HANDLE(p);
+  if (!(lambda >= 0.0) || !std::isfinite(lambda)) return fail(GENCD_EINVAL, "lambda must be finite and >= 0");
+  p->lambda = lambda;
+  return GENCD_OK;
+}
+
+int gencd_lambda_max(gencd_problem* p, double* lambda_max) {
+  GENCD_CHECK_HANDLE(p);
+  if (!lambda_max) return fail(GENCD_EINVAL, "lambda_max is NULL");
+  *lambda_max = p->lambda_max;
+  return GENCD_OK;
+}
+
+int gencd_set_params(gencd_problem* p, const gencd_params* a) {
+  GENCD_CHECK_HANDLE(p);
+  if (!a) return fail(GENCD_EINVAL, "params is NULL");
+  if (a->variant < 0 || a->variant > 3) return fail(GENCD_EINVAL, "unknown variant");
+  if (a->blocks < 0 || a->P < 0 || a->max_iter < 0 || !(a->tol_kkt >= 0.0) || a->check_every < 1 ||
+      (a->beta_mode != 0 && a->beta_mode != 1) || !(a->timeout_s >= 0.0))
+    return fail(GENCD_EINVAL, "parameter out of range");
+  const bool reseed = a->seed != p->params.seed;
+  p->params = *a;
+  if (reseed) p->perm_epoch = -1;
+  return GENCD_OK;
+}
+
+int gencd_get_params(gencd_problem* p, gencd_params* a) {
+  GENCD_CHECK_HANDLE(p);
+  if (!a) return fail(GENCD_EINVAL, "params is NULL");
+  *a = p->params;
+  return GENCD_OK;
+}
+
+int gencd_set_iteration(gencd_problem* p, int64_t t) {
+  GENCD_CHECK_HANDLE(p);
+  if (t < 0) return fail(GENCD_EINVAL, "iteration must be >= 0");
+  p->t = t;
+  return GENCD_OK;
+}
+
+int gencd_get_iteration(gencd_problem* p, int64_t* t) {
+  GENCD_CHECK_HANDLE(p);
+  if (!t) return fail(GENCD_EINVAL, "t is NULL");
+  *t = p->t;
+  return GENCD_OK;
+}
+
+static void fill_result(gencd_problem* p, gencd_result* out, int status, int64_t iters, int64_t host_nnz,
+                        double secs) {
+  if (!out) return;
+  std::memset(out, 0, sizeof(*out));
+  out->status = status;
+  out->iters = iters;
+  int64_t upd, nz;
+  std::memcpy(&upd, p->hpin + 4, 8);
+  std::memcpy(&nz, p->hpin + 5, 8);
+  out->updates = upd;
+  out->nnz_processed = nz + host_nnz;
+  out->objective = p->hpin[1];
+  out->kkt = p->hpin[0];
+  out->seconds = secs;
+}
+
+int gencd_iterate(gencd_problem* p, int64_t iters, gencd_result* out) {
+  GENCD_CHECK_HANDLE(p);
+  if (iters < 0) return fail(GENCD_EINVAL, "iters must be >= 0");
+  auto t0 = std::chrono::steady_clock::now();
+  if (out) GENCD_TRY(reset_counters(p));
+  int64_t host_nnz = 0;
+  for (int64_t i = 0; i < iters; ++i) GENCD_TRY(enqueue_iteration(p, &host_nnz));
+  if (!out) {
+    GENCD_CUDA_TRY(cudaGetLastError());
+    return GENCD_OK;
+  }
+  GENCD_TRY(enqueue_evaluate(p));
+  GENCD_TRY(read_scalars(p));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  fill_result(p, out, GENCD_OK, iters, host_nnz, secs);
+  return GENCD_OK;
+}
+
+int gencd_solve(gencd_problem* p, gencd_result* out) {
+  GENCD_CHECK_HANDLE(p);
+  auto t0 = std::chrono::steady_clock::now();
+  GENCD_TRY(reset_counters(p));
+  int64_t host_nnz = 0, iters = 0;
+  GENCD_TRY(enqueue_evaluate(p));
+  GENCD_TRY(read_scalars(p));
+  int status = GENCD_NOT_CONVERGED;
+  const gencd_params& a = p->params;
+  for (;;) {
+    const double kkt = p->hpin[0], obj = p->hpin[1];
+    if (!std::isfinite(kkt) || !std::isfinite(obj)) {
+      status = GENCD_EDIVERGED;
+      set_error("objective or KKT value is not finite");
+      break;
+    }
+    if (kkt <= a.tol_kkt) {
+      status = GENCD_OK;
+      break;
+    }
+    if (iters >= a.max_iter) break;
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (a.timeout_s > 0.0 && el >= a.timeout_s) break;
+    const int64_t step = std::min<int64_t>(a.check_every, a.max_iter - iters);
+    for (int64_t i = 0; i < step; ++i) GENCD_TRY(enqueue_iteration(p, &host_nnz));
+    iters += step;
+    host_nnz += p->nnz;  // the convergence check streams X once
+    p->stat_host_nnz += p->nnz;
+    GENCD_TRY(enqueue_evaluate(p));
+    GENCD_TRY(read_scalars(p));
+  }
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  fill_result(p, out, status, iters, host_nnz, secs);
+  return status;
+}
+
+int gencd_stats(gencd_problem* p, gencd_result* out) {
+  GENCD_CHECK_HANDLE(p);
+  if (!out) return fail(GENCD_EINVAL, "out is NULL");
+  GENCD_TRY(read_scalars(p));
+  fill_result(p, out, GENCD_OK, p->stat_iters, p->stat_host_nnz, 0.0);
+  return GENCD_OK;
+}
+
+int gencd_stats_reset(gencd_problem* p) {
+  GENCD_CHECK_HANDLE(p);
+  GENCD_TRY(reset_counters(p));
+  return GENCD_OK;
+}
+
+int gencd_get_w(gencd_problem* p, double* w, int64_t k, int32_t memory) {
+  GENCD_CHECK_HANDLE(p);
+  if (!w || k != p->k) return fail(GENCD_EINVAL, "w must hold exactly k doubles");
+  GENCD_CUDA_TRY(cudaMemcpyAsync(w, p->w, sizeof(double) * k, kind_out(memory), p->stream));
+  GENCD_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return GENCD_OK;
+}
+
+int gencd_get_z(gencd_problem* p, double* z, int64_t n, int32_t memory) {
+  GENCD_CHECK_HANDLE(p);
+  if (!z || n != p->n) return fail(GENCD_EINVAL, "z must hold exactly n doubles");
+  GENCD_CUDA_TRY(cudaMemcpyAsync(z, p->z, sizeof(double) * n, kind_out(memory), p->stream));
+  GENCD_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return GENCD_OK;
+}
+
+int gencd_set_w(gencd_problem* p, const double* w, int64_t k, int32_t memory) {
+  GENCD_CHECK_HANDLE(p);
+  if (!w || k != p->k) return fail(GENCD_EINVAL, "w must hold exactly k doubles");
+  if (memory == GENCD_HOST) {
+    for (int64_t j = 0; j < k; ++j)
+      if (!std::isfinite(w[j])) return fail(GENCD_EINVAL, "w[" + std::to_string(j) + "] is not finite");
+  }
+  GENCD_CUDA_TRY(cudaMemcpyAsync(p->w, w, sizeof(double) * k, kind_in(memory), p->stream));
+  GENCD_TRY(build_csr(p));
+  GENCD_TRY(launch_csr_spmv(p, p->w, p->z));
+  GENCD_TRY(launch_fill_u(p));
+  GENCD_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return GENCD_OK;
+}
+
+int gencd_objective(gencd_problem* p, double* objective, double* kkt) {
+  GENCD_CHECK_HANDLE(p);
+  GENCD_TRY(enqueue_evaluate(p));
+  GENCD_TRY(read_scalars(p));
+  if (objective) *objective = p->hpin[1];
+  if (kkt) *kkt = p->hpin[0];
+  return GENCD_OK;
+}
+
+int gencd_propose_at(gencd_problem* p, const int32_t* J, int64_t m, double* delta, double* phi,
+                     int32_t memory) {
+  GENCD_CHECK_HANDLE(p);
+  if (m < 0 || (m > 0 && (!J || !delta || !phi))) return fail(GENCD_EINVAL, "bad J / outputs");
+  if (m == 0) return GENCD_OK;
+  std::vector<int32_t> hj((size_t)m);
+  GENCD_CUDA_TRY(cudaMemcpy(hj.data(), J, sizeof(int32_t) * m,
+                            memory == GENCD_DEVICE ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+  for (int64_t e = 0; e < m; ++e)
+    if (hj[e] < 0 || hj[e] >= p->k) return fail(GENCD_EINVAL, "J[" + std::to_string(e) + "] out of range");
+  int32_t* dj = nullptr;
+  double *dd = nullptr, *df = nullptr;
+  int rc = GENCD_OK;
+  if ((rc = dalloc(&dj, m)) || (rc = dalloc(&dd, m)) || (rc = dalloc(&df, m))) {
+    cudaFree(dj);
+    cudaFree(dd);
+    cudaFree(df);
+    return rc;
+  }
+  if (cudaMemcpyAsync(dj, hj.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
+    rc = fail(GENCD_ECUDA, "copy of J failed");
+  if (rc == GENCD_OK) rc = launch_propose_list(p, dj, m, dd, df);
+  if (rc == GENCD_OK && (cudaMemcpyAsync(delta, dd, sizeof(double) * m, kind_out(memory), p->stream) != cudaSuccess ||
+                         cudaMemcpyAsync(phi, df, sizeof(double) * m, kind_out(memory), p->stream) != cudaSuccess ||
+                         cudaStreamSynchronize(p->stream) != cudaSuccess))
+    rc = fail(GENCD_ECUDA, std::string("propose_at: ") + cudaGetErrorString(cudaGetLastError()));
+  cudaFree(dj);
+  cudaFree(dd);
+  cudaFree(df);
+  return rc;
+}
+
+int gencd_propose_all(gencd_problem* p, double* delta, double* phi, int32_t memory, double* kkt) {
+  GENCD_CHECK_HANDLE(p);
+  GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal, 0, sizeof(double), p->stream));
+  GENCD_TRY(launch_propose_all(p, p->u, p->precision == GENCD_F64));
+  GENCD_TRY(launch_finalize(p, p->lambda, true));
+  if (delta) GENCD_CUDA_TRY(cudaMemcpyAsync(delta, p->delta, sizeof(double) * p->k, kind_out(memory), p->stream));
+  if (phi) GENCD_CUDA_TRY(cudaMemcpyAsync(phi, p->phi, sizeof(double) * p->k, kind_out(memory), p->stream));
+  GENCD_TRY(read_scalars(p));
+  if (kkt) *kkt = p->hpin[0];
+  return GENCD_OK;
+}
+
+int gencd_spectral_radius(gencd_problem* p, double* rho, int64_t* pstar, int32_t* iters) {
+  GENCD_CHECK_HANDLE(p);
+  int32_t it = 0;
+  GENCD_TRY(compute_pstar(p, &it));
+  if (rho) *rho = p->rho;
+  if (pstar) *pstar = p->pstar;
+  if (iters) *iters = it;
+  return GENCD_OK;
+}
+
+int gencd_color(gencd_problem* p, int32_t* ncolors) {
+  GENCD_CHECK_HANDLE(p);
+  GENCD_TRY(run_coloring(p));
+  if (ncolors) *ncolors = p->ncolors;
+  return GENCD_OK;
+}
+
+int gencd_get_colors(gencd_problem* p, int32_t* colors, int64_t k, int32_t memory) {
+  GENCD_CHECK_HANDLE(p);
+  if (!colors || k != p->k) return fail(GENCD_EINVAL, "colors must hold exactly k ints");
+  if (!p->color) return fail(GENCD_ESTATE, "no colouring yet: call gencd_color or gencd_set_colors");
+  GENCD_CUDA_TRY(cudaMemcpyAsync(colors, p->color, sizeof(int32_t) * k, kind_out(memory), p->stream));
+  GENCD_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return GENCD_OK;
+}
+
+int gencd_set_colors(gencd_problem* p, const int32_t* colors, int64_t k, int32_t memory) {
+  GENCD_CHECK_HANDLE(p);
+  if (!colors || k != p->k) return fail(GENCD_EINVAL, "colors must hold exactly k ints");
+  GENCD_TRY(build_csr(p));
+  if (!p->color) GENCD_TRY(dalloc(&p->color, k));
+  GENCD_CUDA_TRY(cudaMemcpyAsync(p->color, colors, sizeof(int32_t) * k, kind_in(memory), p->stream));
+  unsigned long long* chk = nullptr;
+  GENCD_TRY(dalloc(&chk, 2));
+  GENCD_CUDA_TRY(cudaMemsetAsync(chk, 0xff, sizeof(unsigned long long), p->stream));
+  GENCD_CUDA_TRY(cudaMemsetAsync(chk + 1, 0, sizeof(unsigned long long), p->stream));
+  const int g = p->num_sms * 8;
+  k_check_colors<<<grid_for(p->n, kThreads, g), kThreads, 0, p->stream>>>(p->row_ptr, p->col_idx, p->color,
+                                                                          p->n, k, chk);
+  k_max_i32<<<grid_for(k, kThreads, g), kThreads, 0, p->stream>>>(p->color, k, chk + 1);
+  unsigned long long h[2];
+  GENCD_CUDA_TRY(cudaMemcpyAsync(h, chk, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
+  GENCD_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  cudaFree(chk);
+  int32_t mn = 0;
+  {
+    std::vector<int32_t> hc((size_t)k);
+    GENCD_CUDA_TRY(cudaMemcpy(hc.data(), p->color, sizeof(int32_t) * k, cudaMemcpyDeviceToHost));
+    for (int32_t c : hc) mn = c < mn ? c : mn;
+  }
+  if (mn < 0 || h[1] >= (unsigned long long)k) {
+    cudaFree(p->color);
+    p->color = nullptr;
+    return fail(GENCD_EINVAL, "colours must lie in [0, k)");
+  }
+  if (h[0] != ~0ull) {
+    cudaFree(p->color);
+    p->color = nullptr;
+    return fail(GENCD_EINVAL, "two columns sharing row " + std::to_string(h[0]) + " have the same colour");
+  }
+  p->ncolors = (int32_t)h[1] + 1;
+  return build_color_classes(p);
+}
+
+int gencd_permutation(gencd_problem* p, uint64_t seed, int64_t epoch, int64_t m, int32_t* perm) {
+  GENCD_CHECK_HANDLE(p);
+  if (m < 0 || epoch < 0 || (m > 0 && !perm)) return fail(GENCD_EINVAL, "bad permutation arguments");
+  if (m == 0) return GENCD_OK;
+  int32_t* d = nullptr;
+  GENCD_TRY(dalloc(&d, m));
+  int rc = make_permutation(p, seed, epoch, m, d);
+  if (rc == GENCD_OK &&
+      (cudaMemcpyAsync(perm, d, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+       cudaStreamSynchronize(p->stream) != cudaSuccess))
+    rc = fail(GENCD_ECUDA, "permutation copy failed");
+  cudaFree(d);
+  return rc;
+}
+
+int gencd_profile_enable(gencd_problem* p, int32_t enable) {
+  GENCD_CHECK_HANDLE(p);
+  if (!enable) prof_flush(p);
+  p->prof.enabled = enable != 0;
+  return GENCD_OK;
+}
+
+int gencd_profile_read(gencd_problem* p, int32_t kernel, double* ms, int64_t* launches) {
+  GENCD_CHECK_HANDLE(p);
+  if (kernel < 0 || kernel >= K_NUM) return fail(GENCD_EINVAL, "unknown kernel family");
+  prof_flush(p);
+  if (ms) *ms = p->prof.ms[kernel];
+  if (launches) *launches = p->prof.launches[kernel];
+  return GENCD_OK;
+}
+
+int gencd_profile_reset(gencd_problem* p) {
+  GENCD_CHECK_HANDLE(p);
+  prof_flush(p);
+  for (int i = 0; i < K_NUM; ++i) {
+    p->prof.ms[i] = 0.0;
+    p->prof.launches[i] = 0;
+  }
+  return GENCD_OK;
+}
+
+}  // extern "C"

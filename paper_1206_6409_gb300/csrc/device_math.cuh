@@ -1,0 +1,76 @@
+// device_math.cuh -- per-element math of GenCD on the GPU.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gencd {
+
+// Section 1 losses.  t is the fitted value (Xw)_i.
+__device__ __forceinline__ double loss_value(int loss, double y, double t) {
+  if (loss == 0) {  // squared: (y - t)^2 / 2
+    double r = y - t;
+    return 0.5 * r * r;
+  }
+  double m = -y * t;  // logistic: log(1 + e^m), overflow-free on both sides of 0
+  return m > 0.0 ? m + log1p(exp(-m)) : log1p(exp(m));
+}
+
+// Derivative of the loss in t, u_i = l'(y_i, z_i): t - y (squared),
+// -y / (1 + e^{y t}) (logistic).
+__device__ __forceinline__ double loss_deriv(int loss, double y, double t) {
+  if (loss == 0) return t - y;
+  double m = y * t;
+  if (m > 0.0) {
+    double e = exp(-m);
+    return -y * e / (1.0 + e);
+  }
+  return -y / (1.0 + exp(m));
+}
+
+// Eq. 7 step and Eq. 9 proxy for coordinate j with gradient g, weight wj,
+// curvature bound bj.  bj == 0 only for a column without non-zeros, whose
+// coordinate does not enter F: the step is the minimiser of lambda |w_j + d|.
+__device__ __forceinline__ void eq7_step(double g, double wj, double lam, double bj, double& d,
+                                         double& phi) {
+  if (bj > 0.0) {
+    double lo = (g - lam) / bj;
+    double hi = (g + lam) / bj;
+    double clipped = wj < lo ? lo : (wj > hi ? hi : wj);  // psi(w_j; lo, hi)
+    d = -clipped;
+    phi = 0.5 * bj * d * d + g * d + lam * (fabs(wj + d) - fabs(wj));
+  } else {
+    d = -wj;
+    phi = -lam * fabs(wj);
+  }
+}
+
+// KKT violation of coordinate j.
+__device__ __forceinline__ double kkt_violation(double g, double wj, double lam) {
+  if (wj == 0.0) return fmax(fabs(g) - lam, 0.0);
+  return fabs(g + (wj > 0.0 ? lam : -lam));
+}
+
+// SplitMix64 output i of the stream whose state starts at s
+// (Steele, Lea, Flood 2014).
+__host__ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t s, uint64_t i) {
+  uint64_t x = s + (i + 1ull) * 0x9e3779b97f4a7c15ull;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+
+// Non-negative doubles order like their bit patterns as unsigned integers.
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(addr),
+            static_cast<unsigned long long>(__double_as_longlong(v)));
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace gencd

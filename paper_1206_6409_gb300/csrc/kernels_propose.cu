@@ -1,0 +1,375 @@
+// kernels_propose.cu -- the Propose and Accept steps of GenCD on sm_103a.
+//
+//  * k_propose_all: Algorithm 4's inner product g_j = <u, X_j> for every
+//    column, streamed over the CSC arrays in nnz order.  Each warp owns a tile
+//    of 32*ITEMS consecutive non-zeros, each lane ITEMS of them, loaded with
+//    128-bit streaming loads; u is gathered through the read-only path.  A lane
+//    sums its non-zeros column by column in registers (one FMA per non-zero);
+//    a column that lies inside one lane is stored, a column cut by a lane or
+//    tile boundary is added atomically into gacc (FP64).  Work per warp is
+//    constant whatever the column lengths (1 ... 50,000 non-zeros).
+//  * k_finalize: g_j = gacc_j / n, the Eq. 7 step, the Eq. 9 proxy and the
+//    KKT violation per column; resets gacc for the next launch.
+//  * k_accept: Thread-Greedy / Greedy accept (Table 2), one CTA per partition,
+//    argmin of phi with ties to the lower column; accepted iff phi < 0.
+//  * k_propose_list: Algorithm 4 over a selected list J (Shotgun, parity hook),
+//    one warp per column with a shuffle reduction.
+//  * k_objective_*: P(w) of Eq. 1 in FP64 with a fixed-order two-pass sum.
+#include <float.h>
+
+#include "device_math.cuh"
+#include "gencd_internal.cuh"
+
+namespace gencd {
+
+// ---------------------------------------------------------------------------
+// 128-bit streaming loads of ITEMS consecutive entries (16-byte aligned).
+template <int ITEMS>
+__device__ __forceinline__ void load_idx(const int32_t* __restrict__ p, int32_t (&r)[ITEMS]) {
+#pragma unroll
+  for (int q = 0; q < ITEMS / 4; ++q) {
+    int4 v = __ldcs(reinterpret_cast<const int4*>(p) + q);
+    r[4 * q + 0] = v.x;
+    r[4 * q + 1] = v.y;
+    r[4 * q + 2] = v.z;
+    r[4 * q + 3] = v.w;
+  }
+}
+
+template <int ITEMS>
+__device__ __forceinline__ void load_val(const double* __restrict__ p, double (&v)[ITEMS]) {
+#pragma unroll
+  for (int q = 0; q < ITEMS / 2; ++q) {
+    double2 x = __ldcs(reinterpret_cast<const double2*>(p) + q);
+    v[2 * q + 0] = x.x;
+    v[2 * q + 1] = x.y;
+  }
+}
+
+template <int ITEMS>
+__device__ __forceinline__ void load_val(const float* __restrict__ p, float (&v)[ITEMS]) {
+#pragma unroll
+  for (int q = 0; q < ITEMS / 4; ++q) {
+    float4 x = __ldcs(reinterpret_cast<const float4*>(p) + q);
+    v[4 * q + 0] = x.x;
+    v[4 * q + 1] = x.y;
+    v[4 * q + 2] = x.z;
+    v[4 * q + 3] = x.w;
+  }
+}
+
+__device__ __forceinline__ void emit_partial(double* __restrict__ gacc, int32_t c, double s,
+                                             bool whole) {
+  if (whole)
+    gacc[c] = s;  // the only writer of this column
+  else
+    atomicAdd(gacc + c, s);
+}
+
+template <typename V, typename U, int ITEMS>
+__global__ void __launch_bounds__(kThreads)
+    k_propose_all(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
+                  const V* __restrict__ val, const U* __restrict__ u,
+                  const int32_t* __restrict__ tile_col, int64_t nnz, int64_t ntiles,
+                  double* __restrict__ gacc) {
+  constexpr int TILE = 32 * ITEMS;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = warp; t < ntiles; t += nwarps) {
+    const int64_t a = t * TILE + (int64_t)lane * ITEMS;
+    if (a >= nnz) continue;
+    int32_t r[ITEMS];
+    V v[ITEMS];
+    load_idx<ITEMS>(row_idx + a, r);  // arrays are padded: always in bounds
+    load_val<ITEMS>(val + a, v);
+    const int64_t b = a + ITEMS < nnz ? a + ITEMS : nnz;
+    const int nvalid = (int)(b - a);
+    U uu[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) uu[i] = i < nvalid ? __ldg(u + r[i]) : U(0);
+
+    // column holding position a: the largest c in [tile_col[t], tile_col[t+1]]
+    // with col_ptr[c] <= a (empty columns share their start with the next one)
+    int32_t lo = __ldg(tile_col + t), hi = __ldg(tile_col + t + 1);
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if (__ldg(col_ptr + mid) <= a)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    int32_t c = lo;
+    int64_t cend = __ldg(col_ptr + c + 1);
+    bool whole = __ldg(col_ptr + c) >= a;
+    V acc = V(0);
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      if (i < nvalid) {
+        const int64_t p = a + i;
+        while (p >= cend) {  // column c ended before p (c + 1 <= k - 1 since p < nnz)
+          emit_partial(gacc, c, (double)acc, whole);
+          ++c;
+          cend = __ldg(col_ptr + c + 1);
+          acc = V(0);
+          whole = true;
+        }
+        acc = fma(v[i], (V)uu[i], acc);
+      }
+    }
+    emit_partial(gacc, c, (double)acc, whole && cend <= b);
+  }
+}
+
+template <int NT>
+__device__ __forceinline__ double block_max_nan(double v) {
+  __shared__ double sm[NT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double x = __shfl_xor_sync(0xffffffffu, v, o);
+    v = (x > v || x != x) ? x : v;
+  }
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) sm[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < NT / 32 ? sm[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double x = __shfl_xor_sync(0xffffffffu, v, o);
+      v = (x > v || x != x) ? x : v;
+    }
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_finalize(double* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ c,
+               int64_t k, double n, double lam, double beta, int beta_mode, double* __restrict__ delta,
+               double* __restrict__ phi, double* __restrict__ kkt_out, int write_steps) {
+  double vmax = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) {
+    const double g = gacc[j] / n;
+    gacc[j] = 0.0;
+    const double wj = w[j];
+    if (write_steps) {
+      const double bj = beta_mode ? beta : beta * c[j];
+      double d, f;
+      eq7_step(g, wj, lam, bj, d, f);
+      delta[j] = d;
+      phi[j] = f;
+    }
+    const double v = kkt_violation(g, wj, lam);
+    vmax = (v > vmax || v != v) ? v : vmax;
+  }
+  vmax = block_max_nan<kThreads>(vmax);
+  if (threadIdx.x == 0) atomic_max_nonneg(kkt_out, vmax);
+}
+
+// argmin of phi over each partition [floor(b k / B), floor((b+1) k / B))
+__global__ void __launch_bounds__(kThreads)
+    k_accept(const double* __restrict__ phi, const double* __restrict__ delta, int64_t k, int64_t B,
+             int32_t* __restrict__ list_j, double* __restrict__ list_d) {
+  __shared__ double s_phi[kThreads / 32];
+  __shared__ int32_t s_j[kThreads / 32];
+  for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
+    const int64_t lo = b * k / B, hi = (b + 1) * k / B;
+    double bp = DBL_MAX;
+    int32_t bj = INT32_MAX;
+    for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+      const double f = phi[j];
+      if (f < bp) {  // j increases along a thread's loop: equal keeps the lower
+        bp = f;
+        bj = (int32_t)j;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double xp = __shfl_xor_sync(0xffffffffu, bp, o);
+      const int32_t xj = __shfl_xor_sync(0xffffffffu, bj, o);
+      if (xp < bp || (xp == bp && xj < bj)) {
+        bp = xp;
+        bj = xj;
+      }
+    }
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+      s_phi[wid] = bp;
+      s_j[wid] = bj;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int q = 1; q < kThreads / 32; ++q)
+        if (s_phi[q] < bp || (s_phi[q] == bp && s_j[q] < bj)) {
+          bp = s_phi[q];
+          bj = s_j[q];
+        }
+      const bool ok = bj != INT32_MAX && bp < 0.0;
+      list_j[b] = ok ? bj : -1;
+      list_d[b] = ok ? delta[bj] : 0.0;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename V, typename U>
+__global__ void __launch_bounds__(kThreads)
+    k_propose_list(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
+                   const V* __restrict__ val, const U* __restrict__ u, const double* __restrict__ w,
+                   const double* __restrict__ c, const int32_t* __restrict__ J, int64_t m, double n,
+                   double lam, double beta, int beta_mode, double* __restrict__ delta,
+                   double* __restrict__ phi, unsigned long long* __restrict__ counters) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = warp; e < m; e += nwarps) {
+    const int32_t j = J[e];
+    const int64_t s = col_ptr[j], t = col_ptr[j + 1];
+    V acc = V(0);
+    for (int64_t p = s + lane; p < t; p += 32) acc = fma(val[p], (V)__ldg(u + row_idx[p]), acc);
+    const double g = warp_sum((double)acc) / n;
+    if (lane == 0) {
+      const double bj = beta_mode ? beta : beta * c[j];
+      double d, f;
+      eq7_step(g, w[j], lam, bj, d, f);
+      delta[e] = d;
+      phi[e] = f;
+      if (counters) atomicAdd(counters + 1, (unsigned long long)(t - s));
+    }
+  }
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sm) {
+  v = warp_sum(v);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sm[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < NT / 32; ++q) s += sm[q];
+  return s;
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_objective_partial(const double* __restrict__ y, const double* __restrict__ z, int64_t n,
+                        const double* __restrict__ w, int64_t k, int loss, double* __restrict__ red) {
+  __shared__ double sm[kThreads / 32];
+  double sl = 0.0, sw = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t i = i0; i < n; i += stride) sl += loss_value(loss, y[i], z[i]);
+  for (int64_t j = i0; j < k; j += stride) sw += fabs(w[j]);
+  sl = block_sum<kThreads>(sl, sm);
+  sw = block_sum<kThreads>(sw, sm);
+  if (threadIdx.x == 0) {
+    red[blockIdx.x] = sl;
+    red[kRedBlocks + blockIdx.x] = sw;
+  }
+}
+
+__global__ void k_objective_final(const double* __restrict__ red, int nblocks, double n, double lam,
+                                  double* __restrict__ dscal) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double sl = 0.0, sw = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+      sl += red[b];
+      sw += red[kRedBlocks + b];
+    }
+    dscal[1] = (n > 0 ? sl / n : 0.0) + lam * sw;
+    dscal[2] = sl;
+    dscal[3] = sw;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+
+static int blocks_per_sm_cap(gencd_problem* p, int per_sm) { return p->num_sms * per_sm; }
+
+int launch_propose_all(gencd_problem* p, const void* u_vec, bool u_is_double) {
+  if (p->ntiles == 0) return GENCD_OK;
+  const int64_t tile = 32LL * p->items;
+  const int64_t warps_needed = p->ntiles;
+  const int grid = grid_for(warps_needed * 32, kThreads, blocks_per_sm_cap(p, 8));
+  cudaEvent_t ev = nullptr;
+  prof_begin(p, K_PROPOSE_ALL, &ev);
+  if (p->precision == GENCD_F64) {
+    k_propose_all<double, double, kItemsF64><<<grid, kThreads, 0, p->stream>>>(
+        p->col_ptr, p->row_idx, (const double*)p->val, (const double*)u_vec, p->tile_col, p->nnz,
+        p->ntiles, p->gacc);
+  } else if (u_is_double) {
+    k_propose_all<float, double, kItemsF32><<<grid, kThreads, 0, p->stream>>>(
+        p->col_ptr, p->row_idx, (const float*)p->val, (const double*)u_vec, p->tile_col, p->nnz,
+        p->ntiles, p->gacc);
+  } else {
+    k_propose_all<float, float, kItemsF32><<<grid, kThreads, 0, p->stream>>>(
+        p->col_ptr, p->row_idx, (const float*)p->val, (const float*)u_vec, p->tile_col, p->nnz,
+        p->ntiles, p->gacc);
+  }
+  (void)tile;
+  prof_end(p, ev);
+  GENCD_CUDA_TRY(cudaGetLastError());
+  return GENCD_OK;
+}
+
+int launch_finalize(gencd_problem* p, double lambda, bool write_steps) {
+  const double beta = p->loss == GENCD_LOSS_SQUARED ? 1.0 : 0.25;
+  const int grid = grid_for(p->k, kThreads, blocks_per_sm_cap(p, 8));
+  cudaEvent_t ev = nullptr;
+  prof_begin(p, K_FINALIZE, &ev);
+  k_finalize<<<grid, kThreads, 0, p->stream>>>(p->gacc, p->w, p->c, p->k, (double)p->n, lambda, beta,
+                                               p->params.beta_mode, p->delta, p->phi, p->dscal + 0,
+                                               write_steps ? 1 : 0);
+  prof_end(p, ev);
+  GENCD_CUDA_TRY(cudaGetLastError());
+  return GENCD_OK;
+}
+
+int launch_accept(gencd_problem* p, int64_t B) {
+  const int grid = (int)(B < (int64_t)p->num_sms * 16 ? B : (int64_t)p->num_sms * 16);
+  cudaEvent_t ev = nullptr;
+  prof_begin(p, K_ACCEPT, &ev);
+  k_accept<<<grid, kThreads, 0, p->stream>>>(p->phi, p->delta, p->k, B, p->list_j, p->list_d);
+  prof_end(p, ev);
+  GENCD_CUDA_TRY(cudaGetLastError());
+  return GENCD_OK;
+}
+
+int launch_propose_list(gencd_problem* p, const int32_t* J, int64_t m, double* delta, double* phi) {
+  if (m <= 0) return GENCD_OK;
+  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(p->dscal + 4);
+  const double beta = p->loss == GENCD_LOSS_SQUARED ? 1.0 : 0.25;
+  const int grid = grid_for(m * 32, kThreads, blocks_per_sm_cap(p, 8));
+  cudaEvent_t ev = nullptr;
+  prof_begin(p, K_PROPOSE_LIST, &ev);
+  if (p->precision == GENCD_F64)
+    k_propose_list<double, double><<<grid, kThreads, 0, p->stream>>>(
+        p->col_ptr, p->row_idx, (const double*)p->val, (const double*)p->u, p->w, p->c, J, m,
+        (double)p->n, p->lambda, beta, p->params.beta_mode, delta, phi, ctr);
+  else
+    k_propose_list<float, float><<<grid, kThreads, 0, p->stream>>>(
+        p->col_ptr, p->row_idx, (const float*)p->val, (const float*)p->u, p->w, p->c, J, m,
+        (double)p->n, p->lambda, beta, p->params.beta_mode, delta, phi, ctr);
+  prof_end(p, ev);
+  GENCD_CUDA_TRY(cudaGetLastError());
+  return GENCD_OK;
+}
+
+int launch_objective(gencd_problem* p) {
+  const int64_t work = p->n > p->k ? p->n : p->k;
+  const int grid = grid_for(work, kThreads, kRedBlocks);
+  cudaEvent_t ev = nullptr;
+  prof_begin(p, K_OBJECTIVE, &ev);
+  k_objective_partial<<<grid, kThreads, 0, p->stream>>>(p->y, p->z, p->n, p->w, p->k, p->loss,
+                                                        p->red);
+  k_objective_final<<<1, 32, 0, p->stream>>>(p->red, grid, (double)p->n, p->lambda, p->dscal);
+  prof_end(p, ev);
+  p->prof.launches[K_OBJECTIVE] += 1;  // two launches per objective
+  GENCD_CUDA_TRY(cudaGetLastError());
+  return GENCD_OK;
+}
+
+}  // namespace gencd

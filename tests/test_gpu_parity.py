@@ -1,0 +1,356 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (step and proxy, from the condition of the sum g_j = (1/n) sum_i
+X_ij u_i): with S_j = (1/n) sum_i |X_ij u_i| and sd_j = |delta_j| + S_j/beta_j,
+  |delta_gpu - delta_cpu| <= tol * sd_j,
+  |phi_gpu - phi_cpu|     <= tol * sd_j * (S_j + beta_j sd_j + lambda),
+tol = 1e-12 in FP64 mode and 1e-5 in FP32 mode.  Integer results (colours,
+permutations, supports) are compared exactly.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1206_6409_gb300 import build
+
+    build.build()
+    from paper_1206_6409_gb300 import binding
+
+    binding.lib()
+    return binding
+
+
+def _u(prob, z):
+    if prob.loss == "squared":
+        return z - prob.y
+    return -prob.y / (1.0 + np.exp(prob.y * z))
+
+
+def _scales(prob, z, lam, beta_mode=0):
+    u = _u(prob, z)
+    counts = np.diff(prob.col_ptr)
+    a = np.abs(prob.val * u[prob.row_idx])
+    S = np.zeros(prob.k)
+    nz = counts > 0
+    S[nz] = np.add.reduceat(a, prob.col_ptr[:-1][nz]) / prob.n
+    beta = 1.0 if prob.loss == "squared" else 0.25
+    c = np.zeros(prob.k)
+    c[nz] = np.add.reduceat(prob.val ** 2, prob.col_ptr[:-1][nz]) / prob.n
+    bj = np.full(prob.k, beta) if beta_mode else beta * c
+    return S, bj
+
+
+def assert_steps_close(prob, z, w, lam, J, d_gpu, f_gpu, d_cpu, f_cpu, tol, beta_mode=0):
+    S, bj = _scales(prob, z, lam, beta_mode)
+    S, bj, wj = S[J], bj[J], w[J]
+    sd = np.abs(d_cpu) + np.where(bj > 0, S / np.where(bj > 0, bj, 1.0), np.abs(wj))
+    td = tol * sd + 1e-300
+    tf = tol * sd * (S + bj * sd + lam) + 1e-300
+    bad = np.flatnonzero(np.abs(d_gpu - d_cpu) > td)
+    assert bad.size == 0, (bad[:5], d_gpu[bad[:5]], d_cpu[bad[:5]], td[bad[:5]])
+    bad = np.flatnonzero(np.abs(f_gpu - f_cpu) > tf)
+    assert bad.size == 0, (bad[:5], f_gpu[bad[:5]], f_cpu[bad[:5]], tf[bad[:5]])
+
+
+def _state(prob, seed, frac=0.1, scale=0.5):
+    rng = np.random.default_rng(seed)
+    return np.where(rng.random(prob.k) < frac, rng.normal(0, scale, prob.k), 0.0)
+
+
+def ragged_problem(loss="logistic", seed=0):
+    """Column lengths at the kernel's edges (0, 1, 31..33, tile sizes, 4096,
+    50,000), empty rows, a ragged tail."""
+    rng = np.random.default_rng(seed)
+    n = 60_000
+    lengths = [0, 1, 2, 3, 31, 32, 33, 0, 0, 127, 128, 129, 255, 256, 257, 4096, 50_000, 5, 0, 1000,
+               7, 1, 0]
+    lengths += list(rng.integers(0, 40, size=300))
+    lengths += [1, 0, 0, 3]
+    counts = np.array(lengths, np.int64)
+    col_ptr = np.zeros(counts.size + 1, np.int64)
+    np.cumsum(counts, out=col_ptr[1:])
+    rows = workloads.synthetic._distinct_rows(n - 100, counts, rng)  # the last 100 rows stay empty
+    val = rng.lognormal(0.0, 1.0, rows.size) * np.where(rng.random(rows.size) < 0.3, -1.0, 1.0)
+    y = np.where(rng.random(n) < 0.5, -1.0, 1.0) if loss == "logistic" else rng.normal(size=n)
+    return workloads.Problem(n, counts.size, col_ptr, rows, val, y, loss, np.zeros(counts.size), "ragged")
+
+
+PROBLEMS = {
+    "cfg1-logistic": lambda: workloads.config1("logistic"),
+    "cfg1-squared": lambda: workloads.config1("squared"),
+    "ragged-logistic": lambda: ragged_problem("logistic"),
+    "ragged-squared": lambda: ragged_problem("squared", 1),
+    "zipf-logistic": lambda: workloads.config2_scaled(0.002, "logistic"),
+}
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_propose_matches_oracle(gb, name, precision):
+    prob = PROBLEMS[name]()
+    orc = oracle.Oracle(prob)
+    lam = 0.05 * orc.lambda_max()
+    orc.set_lambda(lam)
+    w = _state(prob, 1)
+    z = orc.fitted(w)
+    rng = np.random.default_rng(2)
+    J = np.concatenate([np.arange(prob.k), rng.integers(0, prob.k, 500)]).astype(np.int32)
+    d_cpu, f_cpu = orc.propose(w, z, J)
+    with gb.Problem(prob, precision=precision) as p:
+        p.set_lambda(lam)
+        p.set_w(w)
+        d_gpu, f_gpu = p.propose_at(J)
+        assert_steps_close(prob, z, w, lam, J, d_gpu, f_gpu, d_cpu, f_cpu, TOL[precision])
+        # the streaming pass over all columns (Thread-Greedy's Propose)
+        d_all, f_all, kkt = p.propose_all()
+        Jall = np.arange(prob.k)
+        assert_steps_close(prob, z, w, lam, Jall, d_all, f_all, d_cpu[:prob.k], f_cpu[:prob.k],
+                           TOL[precision])
+        S, _ = _scales(prob, z, lam)
+        assert abs(kkt - orc.kkt(w, z)) <= TOL[precision] * (S.max() + lam) * 10
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_lambda_max_and_objective(gb, precision):
+    for loss in ("logistic", "squared"):
+        prob = workloads.config1(loss)
+        orc = oracle.Oracle(prob)
+        with gb.Problem(prob, precision=precision) as p:
+            lm = p.lambda_max()
+            assert lm == pytest.approx(orc.lambda_max(), rel=TOL[precision] * 10)
+            lam = 0.02 * orc.lambda_max()
+            orc.set_lambda(lam)
+            p.set_lambda(lam)
+            w = _state(prob, 5)
+            p.set_w(w)
+            obj, kkt = p.objective()
+            assert obj == pytest.approx(orc.objective(w), rel=1e-13 if precision == "f64" else 1e-6)
+            np.testing.assert_allclose(p.z(), orc.fitted(w), rtol=0,
+                                       atol=1e-12 if precision == "f64" else 1e-5)
+
+
+def test_permutation_is_bit_exact(gb):
+    prob = workloads.config1("logistic")
+    with gb.Problem(prob) as p:
+        for seed, epoch, m in [(0, 0, 1), (0, 0, 4096), (7, 3, 4097), (2**64 - 1, 11, 100_003),
+                               (123, 0, 1_000_000)]:
+            np.testing.assert_array_equal(p.permutation(seed, epoch, m), oracle.permutation(seed, epoch, m))
+
+
+@pytest.mark.parametrize("name", ["cfg1-logistic", "ragged-squared", "zipf-logistic"])
+def test_coloring_equals_first_fit(gb, name):
+    prob = PROBLEMS[name]()
+    colors_cpu, nc_cpu = oracle.Oracle(prob).color()
+    with gb.Problem(prob) as p:
+        assert p.color() == nc_cpu
+        np.testing.assert_array_equal(p.colors(), colors_cpu)
+
+
+@pytest.mark.parametrize("precision", ["f64"])
+@pytest.mark.parametrize("loss", ["logistic", "squared"])
+def test_coloring_iterations_match(gb, loss, precision):
+    prob = workloads.config1(loss)
+    orc = oracle.Oracle(prob)
+    lam = 0.05 * orc.lambda_max()
+    orc.set_lambda(lam)
+    colors, C = orc.color()
+    iters = C + C // 2  # crosses an epoch boundary
+    w_cpu, z_cpu, _, _ = orc.run("coloring", iters, colors=colors, seed=9)
+    with gb.Problem(prob, precision=precision) as p:
+        p.set_lambda(lam)
+        p.set_colors(colors)
+        p.set_params(variant="coloring", seed=9)
+        p.iterate(iters)
+        w_gpu = p.w()
+    np.testing.assert_array_equal(w_gpu != 0, w_cpu != 0)
+    np.testing.assert_allclose(w_gpu, w_cpu, rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("variant,B,P", [("thread_greedy", 64, 0), ("thread_greedy", 5000, 0),
+                                          ("greedy", 1, 0), ("shotgun", 0, 200)])
+def test_iterations_match(gb, variant, B, P):
+    prob = workloads.config1("logistic")
+    orc = oracle.Oracle(prob)
+    lam = 0.05 * orc.lambda_max()
+    orc.set_lambda(lam)
+    iters = 40
+    w_cpu, z_cpu, _, _ = orc.run(variant, iters, B=B or 1, P=P or 1, seed=4)
+    with gb.Problem(prob) as p:
+        p.set_lambda(lam)
+        p.set_params(variant=variant, blocks=B, P=P, seed=4)
+        r = p.iterate(iters)
+        w_gpu = p.w()
+        assert r.iters == iters and np.isfinite(r.objective)
+    np.testing.assert_array_equal(w_gpu != 0, w_cpu != 0)
+    np.testing.assert_allclose(w_gpu, w_cpu, rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("loss", ["logistic", "squared"])
+@pytest.mark.parametrize("variant", ["shotgun", "thread_greedy", "coloring"])
+def test_solve_reaches_the_oracle_optimum(gb, loss, variant):
+    prob = workloads.uniform_problem(1000, 2000, 10, values="pm1", loss=loss, n_planted=30, seed=21)
+    orc = oracle.Oracle(prob)
+    lam = 0.05 * orc.lambda_max()
+    orc.set_lambda(lam)
+    w_opt, _, _, kkt, _ = orc.solve("ccd", tol_kkt=1e-11)
+    assert kkt <= 1e-11
+    P_opt = orc.objective(w_opt)
+    with gb.Problem(prob) as p:
+        p.set_lambda(lam)
+        p.set_params(variant=variant, tol_kkt=1e-10, max_iter=200_000, check_every=50, blocks=256)
+        r = p.solve()
+        assert r.status == 0, r.as_dict()
+        w = p.w()
+    assert r.objective == pytest.approx(P_opt, rel=1e-6)
+    big = (np.abs(w_opt) > 1e-6) | (np.abs(w) > 1e-6)
+    np.testing.assert_array_equal(np.sign(w[big]), np.sign(w_opt[big]))
+
+
+@pytest.mark.parametrize("loss", ["logistic", "squared"])
+def test_config1_shotgun_solve_matches_oracle(gb, loss):
+    """Plain L1 problem of n=2,000, k=5,000 (20 nnz/column, +-1 values), FP64,
+    Shotgun with P* against the oracle's cyclic-CD optimum."""
+    prob = workloads.config1(loss)
+    orc = oracle.Oracle(prob)
+    lam = 0.01 * orc.lambda_max()
+    orc.set_lambda(lam)
+    w_opt, _, _, kkt, _ = orc.solve("ccd", tol_kkt=1e-9)
+    P_opt = orc.objective(w_opt)
+    with gb.Problem(prob) as p:
+        p.set_lambda(lam)
+        rho, pstar, _ = p.spectral_radius()
+        rho_cpu, _ = orc.spectral_radius()
+        assert rho == pytest.approx(rho_cpu, rel=1e-6)
+        p.set_params(variant="shotgun", P=0, tol_kkt=1e-9, max_iter=2_000_000, check_every=200)
+        r = p.solve()
+        assert r.status == 0, r.as_dict()
+        w = p.w()
+    assert r.objective == pytest.approx(P_opt, rel=1e-6)
+    big = (np.abs(w_opt) > 1e-6) | (np.abs(w) > 1e-6)
+    np.testing.assert_array_equal(np.sign(w[big]), np.sign(w_opt[big]))
+
+
+def test_f32_solve_reaches_the_optimum(gb):
+    prob = workloads.config2_scaled(0.002, "logistic")
+    orc = oracle.Oracle(prob)
+    lam = 0.05 * orc.lambda_max()
+    orc.set_lambda(lam)
+    w_opt, _, _, _, _ = orc.solve("ccd", tol_kkt=1e-10)
+    with gb.Problem(prob, precision="f32") as p:
+        p.set_lambda(lam)
+        p.set_params(variant="thread_greedy", blocks=128, tol_kkt=1e-7, max_iter=100_000, check_every=50)
+        r = p.solve()
+        assert r.status == 0, r.as_dict()
+    assert r.objective == pytest.approx(orc.objective(w_opt), rel=1e-6)
+
+
+def test_edge_cases(gb):
+    # one column, one row, all-empty columns, lambda above lambda_max
+    X = np.array([[2.0]])
+    p1 = workloads.csc_from_dense(X, np.array([1.0]), "logistic")
+    with gb.Problem(p1) as p:
+        p.set_lambda(0.01)
+        p.set_params(variant="greedy", tol_kkt=1e-12, max_iter=100000, check_every=1)
+        r = p.solve()
+        assert r.status == 0
+        o = oracle.Oracle(p1, 0.01)
+        w_opt, _, _, _, _ = o.solve("ccd", tol_kkt=1e-13, max_iter=10**6)
+        assert p.w()[0] == pytest.approx(w_opt[0], rel=1e-9)
+    empty = workloads.Problem(5, 4, np.zeros(5, np.int64), np.zeros(0, np.int32), np.zeros(0),
+                              np.array([1.0, -1, 1, 1, -1]), "logistic", np.zeros(4))
+    with gb.Problem(empty) as p:
+        assert p.lambda_max() == 0.0
+        p.set_lambda(0.1)
+        p.set_params(variant="thread_greedy")
+        r = p.solve()
+        assert r.status == 0 and r.iters == 0
+        assert (p.w() == 0).all()
+        p.set_w(np.array([1.0, 0.0, -2.0, 0.0]))  # weights on empty columns go to 0 in one step
+        p.iterate(1)
+        assert (p.w() == 0).all()
+    prob = ragged_problem("squared", 3)
+    with gb.Problem(prob) as p:
+        lm = p.lambda_max()
+        p.set_lambda(lm * (1 + 1e-9))
+        p.set_params(variant="thread_greedy", tol_kkt=0.0, max_iter=5)
+        r = p.solve()
+        assert (p.w() == 0).all()
+
+
+def test_invalid_input_is_rejected(gb):
+    good = workloads.uniform_problem(20, 10, 3, seed=1)
+    cases = []
+    bad = good.row_idx.copy()
+    bad[0], bad[1] = bad[1], bad[0]  # unsorted rows in column 0
+    cases.append(("rows", dict(row_idx=bad)))
+    bad = good.row_idx.copy()
+    bad[4] = bad[3]  # duplicate row in column 1
+    cases.append(("rows", dict(row_idx=bad)))
+    bad = good.row_idx.copy()
+    bad[7] = 20  # out of range
+    cases.append(("rows", dict(row_idx=bad)))
+    bad = good.col_ptr.copy()
+    bad[3] = bad[5]  # not monotone
+    cases.append(("col_ptr", dict(col_ptr=bad)))
+    bad_y = good.y.copy()
+    bad_y[2] = 0.5  # logistic labels must be +-1
+    cases.append(("label", dict(y=bad_y)))
+    bad_v = good.val.copy()
+    bad_v[2] = np.nan
+    cases.append(("value", dict(val=bad_v)))
+    for _, kw in cases:
+        args = dict(col_ptr=good.col_ptr, row_idx=good.row_idx, val=good.val, y=good.y)
+        args.update(kw)
+        with pytest.raises(gb.GencdError) as e:
+            gb.gencd_create(good.n, good.k, good.nnz, args["col_ptr"], args["row_idx"], args["val"], args["y"],
+                            "logistic", "f64")
+        assert e.value.code == gb.GENCD_EINVAL
+    with pytest.raises(gb.GencdError):
+        gb.gencd_create(good.n, good.k, good.nnz + 1, good.col_ptr, good.row_idx, good.val, good.y)
+
+
+def test_device_inputs_match_host_inputs(gb):
+    import torch
+
+    prob = workloads.config1("logistic")
+    dev = dict(col_ptr=torch.from_numpy(prob.col_ptr).cuda(), row_idx=torch.from_numpy(prob.row_idx).cuda(),
+               val=torch.from_numpy(prob.val).cuda(), y=torch.from_numpy(prob.y).cuda())
+    lam = 0.05 * oracle.Oracle(prob).lambda_max()
+    ws = []
+    for kw in (dict(prob=prob), dict(n=prob.n, k=prob.k, loss="logistic", **dev)):
+        with gb.Problem(**kw) as p:
+            p.set_lambda(lam)
+            p.set_params(variant="thread_greedy", blocks=100)
+            p.iterate(10)
+            ws.append(p.w())
+    np.testing.assert_array_equal(ws[0], ws[1])
+
+
+def test_not_converged_and_diverged_are_reported(gb):
+    prob = workloads.config1("logistic")
+    with gb.Problem(prob) as p:
+        p.set_lambda(1e-4 * p.lambda_max())
+        p.set_params(variant="thread_greedy", max_iter=5, tol_kkt=1e-14, check_every=5)
+        r = p.solve()
+        assert r.status == gb.GENCD_NOT_CONVERGED and r.iters == 5
+    # literal beta with columns of norm^2 >> n makes every step overshoot
+    X = np.array([[300.0, 0.0], [0.0, 200.0], [100.0, 100.0]])
+    big = workloads.csc_from_dense(X, np.array([1.0, -2.0, 0.5]), "squared")
+    with gb.Problem(big) as p:
+        p.set_lambda(1e-3)
+        p.set_params(variant="thread_greedy", beta_mode=1, max_iter=100000, check_every=10, tol_kkt=0.0)
+        r = p.solve()
+        assert r.status == gb.GENCD_EDIVERGED

@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import dataclasses
 import hashlib
+import os
 
 import numpy as np
 
@@ -206,11 +207,28 @@ def zipf_problem(n, k, nnz_total, *, s=1.1, cap=50_000, n_planted=2000, loss=LOG
     return Problem(n, k, col_ptr, row_idx, val, y, loss, w_star, name)
 
 
-def config2(loss=LOGISTIC, seed=0) -> Problem:
+def config2(loss=LOGISTIC, seed=0, cache_dir=None) -> Problem:
     """n=1,000,000, k=4,000,000, Zipf(1.1) column nnz capped at 50,000,
-    2.00e8 nnz, log-normal unit-norm columns, 2,000 planted weights."""
-    return zipf_problem(1_000_000, 4_000_000, 200_000_000, cap=50_000, n_planted=2000,
-                        loss=loss, seed=seed, name=f"zipf1.1-1Mx4M-200Mnnz-{loss}")
+    2.00e8 nnz, log-normal unit-norm columns, 2,000 planted weights.
+
+    ``cache_dir`` (default: $GENCD_WORKLOAD_CACHE) keeps the drawn arrays as
+    .npy files so that several processes of one session draw them once."""
+    name = f"zipf1.1-1Mx4M-200Mnnz-{loss}-seed{seed}"
+    cache_dir = cache_dir or os.environ.get("GENCD_WORKLOAD_CACHE")
+    if cache_dir:
+        base = os.path.join(cache_dir, name)
+        files = [base + f".{a}.npy" for a in ("col_ptr", "row_idx", "val", "y", "w_star")]
+        if all(os.path.exists(f) for f in files):
+            a = [np.load(f, mmap_mode=None) for f in files]
+            return Problem(1_000_000, 4_000_000, a[0], a[1], a[2], a[3], loss, a[4], name)
+    p = zipf_problem(1_000_000, 4_000_000, 200_000_000, cap=50_000, n_planted=2000,
+                     loss=loss, seed=seed, name=name)
+    if cache_dir:
+        os.makedirs(cache_dir, exist_ok=True)
+        for a, f in zip((p.col_ptr, p.row_idx, p.val, p.y, p.w_star), files):
+            np.save(f + ".tmp.npy", a)
+            os.replace(f + ".tmp.npy", f)
+    return p
 
 
 def config2_scaled(scale=0.02, loss=LOGISTIC, seed=0) -> Problem:
