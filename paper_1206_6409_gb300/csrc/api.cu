@@ -94,11 +94,10 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 __global__ void k_sum_partials(const double* __restrict__ red, int nb, double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += red[b];
-    *out = s;
-  }
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += 32) s += red[b];
+  s = warp_sum(s);
+  if (threadIdx.x == 0) *out = s;
 }
 
 __global__ void k_div(const double* __restrict__ t, int64_t k, double r, double* __restrict__ v) {
@@ -192,9 +191,9 @@ static int enqueue_iteration(gencd_problem* p, int64_t* host_nnz) {
   if (v == GENCD_THREAD_GREEDY || v == GENCD_GREEDY) {
     const int B = effective_B(p);
     GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal, 0, sizeof(double), p->stream));
+    GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal + 7, 0, sizeof(double), p->stream));
     GENCD_TRY(launch_propose_all(p, p->u, p->precision == GENCD_F64));  // Propose, all columns
     GENCD_TRY(launch_finalize(p, p->lambda, true));                      // + KKT of the start state
-    GENCD_TRY(launch_objective(p));                                      // objective of the start state
     GENCD_TRY(launch_accept(p, B));                                      // Accept, best per partition
     GENCD_TRY(launch_update_list(p, p->list_j, p->list_d, B, true));     // Update (atomic z)
     GENCD_TRY(launch_refresh_list(p, p->list_j, p->list_d, B, true));
@@ -209,6 +208,7 @@ static int enqueue_iteration(gencd_problem* p, int64_t* host_nnz) {
     GENCD_TRY(ensure_selection(p, e, p->k));                             // Select, random subset
     const int64_t lo = q * P, m = (lo + P <= p->k ? P : p->k - lo);
     const int32_t* J = p->perm + lo;
+    GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal + 7, 0, sizeof(double), p->stream));
     GENCD_TRY(launch_propose_list(p, J, m, p->list_d, p->phi));          // Propose (Jacobi)
     GENCD_TRY(launch_update_list(p, J, p->list_d, m, false));            // Accept all, Update
     GENCD_TRY(launch_refresh_list(p, J, p->list_d, m, false));
@@ -535,8 +535,15 @@ int gencd_solve(gencd_problem* p, gencd_result* out) {
   int64_t host_nnz = 0, iters = 0;
   GENCD_TRY(enqueue_evaluate(p));
   GENCD_TRY(read_scalars(p));
+  p->stat_host_nnz += p->nnz;
+  host_nnz += p->nnz;
   int status = GENCD_NOT_CONVERGED;
   const gencd_params& a = p->params;
+  // Thread-Greedy and Greedy compute the KKT violation of each iteration's
+  // start state inside the iteration; their checks read it and only run a
+  // full evaluation to confirm convergence.  Shotgun and Coloring evaluate.
+  const bool fused = a.variant == GENCD_THREAD_GREEDY || a.variant == GENCD_GREEDY;
+  bool evaluated = true;  // hpin holds the KKT of the current state
   for (;;) {
     const double kkt = p->hpin[0], obj = p->hpin[1];
     if (!std::isfinite(kkt) || !std::isfinite(obj)) {
@@ -545,8 +552,16 @@ int gencd_solve(gencd_problem* p, gencd_result* out) {
       break;
     }
     if (kkt <= a.tol_kkt) {
-      status = GENCD_OK;
-      break;
+      if (evaluated) {
+        status = GENCD_OK;
+        break;
+      }
+      GENCD_TRY(enqueue_evaluate(p));  // confirm on the current state
+      GENCD_TRY(read_scalars(p));
+      host_nnz += p->nnz;
+      p->stat_host_nnz += p->nnz;
+      evaluated = true;
+      continue;
     }
     if (iters >= a.max_iter) break;
     const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -554,10 +569,23 @@ int gencd_solve(gencd_problem* p, gencd_result* out) {
     const int64_t step = std::min<int64_t>(a.check_every, a.max_iter - iters);
     for (int64_t i = 0; i < step; ++i) GENCD_TRY(enqueue_iteration(p, &host_nnz));
     iters += step;
-    host_nnz += p->nnz;  // the convergence check streams X once
-    p->stat_host_nnz += p->nnz;
-    GENCD_TRY(enqueue_evaluate(p));
+    if (fused) {
+      GENCD_TRY(launch_objective(p));  // divergence watch on the current state
+      GENCD_TRY(read_scalars(p));
+      evaluated = false;
+    } else {
+      GENCD_TRY(enqueue_evaluate(p));
+      GENCD_TRY(read_scalars(p));
+      host_nnz += p->nnz;  // the convergence check streams X once
+      p->stat_host_nnz += p->nnz;
+      evaluated = true;
+    }
+  }
+  if (!evaluated && status != GENCD_EDIVERGED) {
+    GENCD_TRY(enqueue_evaluate(p));  // report the values of the returned state
     GENCD_TRY(read_scalars(p));
+    host_nnz += p->nnz;
+    p->stat_host_nnz += p->nnz;
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   fill_result(p, out, status, iters, host_nnz, secs);

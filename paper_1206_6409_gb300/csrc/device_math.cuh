@@ -28,6 +28,29 @@ __device__ __forceinline__ double loss_deriv(int loss, double y, double t) {
   return -y / (1.0 + exp(m));
 }
 
+// u_i in the storage precision of u: FP64 mode evaluates l' in FP64; FP32 mode
+// evaluates the logistic derivative in FP32 arithmetic (its result is stored
+// in FP32 anyway), from the FP64 fitted value.
+template <typename U>
+__device__ __forceinline__ U u_value(int loss, double y, double t);
+
+template <>
+__device__ __forceinline__ double u_value<double>(int loss, double y, double t) {
+  return loss_deriv(loss, y, t);
+}
+
+template <>
+__device__ __forceinline__ float u_value<float>(int loss, double y, double t) {
+  if (loss == 0) return (float)(t - y);
+  const float yf = (float)y;
+  const float m = (float)(y * t);
+  if (m > 0.0f) {
+    const float e = expf(-m);
+    return -yf * e / (1.0f + e);
+  }
+  return -yf / (1.0f + expf(m));
+}
+
 // Eq. 7 step and Eq. 9 proxy for coordinate j with gradient g, weight wj,
 // curvature bound bj.  bj == 0 only for a column without non-zeros, whose
 // coordinate does not enter F: the step is the minimiser of lambda |w_j + d|.

@@ -270,14 +270,19 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// fixed-order reduction of the per-block partials: lane l sums blocks
+// l, l+32, ...; then a fixed butterfly
 __global__ void k_objective_final(const double* __restrict__ red, int nblocks, double n, double lam,
                                   double* __restrict__ dscal) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double sl = 0.0, sw = 0.0;
-    for (int b = 0; b < nblocks; ++b) {
-      sl += red[b];
-      sw += red[kRedBlocks + b];
-    }
+  const int lane = threadIdx.x & 31;
+  double sl = 0.0, sw = 0.0;
+  for (int b = lane; b < nblocks; b += 32) {
+    sl += red[b];
+    sw += red[kRedBlocks + b];
+  }
+  sl = warp_sum(sl);
+  sw = warp_sum(sw);
+  if (threadIdx.x == 0) {
     dscal[1] = (n > 0 ? sl / n : 0.0) + lam * sw;
     dscal[2] = sl;
     dscal[3] = sw;

@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(kThreads)
              U* __restrict__ u) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    u[i] = (U)loss_deriv(loss, y[i], z[i]);
+    u[i] = u_value<U>(loss, y[i], z[i]);
 }
 
 template <typename V>
@@ -39,24 +39,34 @@ __global__ void __launch_bounds__(kThreads)
       w[j] += d;
       atomicAdd(counters + 0, 1ull);
       atomicAdd(counters + 1, (unsigned long long)(t - s));
+      atomicAdd(counters + 3, (unsigned long long)(t - s));  // touched this iteration
     }
     for (int64_t p = s + threadIdx.x; p < t; p += blockDim.x) atomicAdd(z + row_idx[p], d * (double)val[p]);
   }
 }
 
+// When the updates of the iteration touched at least n non-zeros, one dense
+// pass over all rows is cheaper than revisiting every touched entry (each
+// costs a gather and an exp); both leave u = l'(y, z) on every touched row.
 template <typename U>
 __global__ void __launch_bounds__(kThreads)
     k_refresh_list(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
                    const int32_t* __restrict__ J, const double* __restrict__ D, int64_t m,
-                   const double* __restrict__ y, const double* __restrict__ z, int loss,
-                   U* __restrict__ u) {
+                   const double* __restrict__ y, const double* __restrict__ z, int64_t n, int loss,
+                   U* __restrict__ u, const unsigned long long* __restrict__ touched) {
+  if (*touched >= (unsigned long long)n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+      u[i] = u_value<U>(loss, y[i], z[i]);
+    return;
+  }
   for (int64_t e = blockIdx.x; e < m; e += gridDim.x) {
     const int32_t j = J[e];
     if (j < 0 || D[e] == 0.0) continue;
     const int64_t s = col_ptr[j], t = col_ptr[j + 1];
     for (int64_t p = s + threadIdx.x; p < t; p += blockDim.x) {
       const int32_t i = row_idx[p];
-      u[i] = (U)loss_deriv(loss, y[i], z[i]);
+      u[i] = u_value<U>(loss, y[i], z[i]);
     }
   }
 }
@@ -93,7 +103,7 @@ __global__ void __launch_bounds__(kThreads)
         const int32_t i = row_idx[p];
         const double zi = z[i] + d * (double)val[p];
         z[i] = zi;
-        u[i] = (U)loss_deriv(loss, y[i], zi);
+        u[i] = u_value<U>(loss, y[i], zi);
       }
       if (lane == 0) w[j] = wj + d;
       upd += 1;
@@ -157,15 +167,16 @@ int launch_update_list(gencd_problem* p, const int32_t* J, const double* d, int6
 
 int launch_refresh_list(gencd_problem* p, const int32_t* J, const double* d, int64_t m, bool) {
   if (m <= 0) return GENCD_OK;
-  const int grid = (int)(m < (int64_t)p->num_sms * 16 ? m : (int64_t)p->num_sms * 16);
+  const int grid = p->num_sms * 16;
+  const unsigned long long* touched = reinterpret_cast<const unsigned long long*>(p->dscal + 7);
   cudaEvent_t ev = nullptr;
   prof_begin(p, K_REFRESH, &ev);
   if (p->precision == GENCD_F64)
     k_refresh_list<double><<<grid, kThreads, 0, p->stream>>>(p->col_ptr, p->row_idx, J, d, m, p->y, p->z,
-                                                             p->loss, (double*)p->u);
+                                                             p->n, p->loss, (double*)p->u, touched);
   else
     k_refresh_list<float><<<grid, kThreads, 0, p->stream>>>(p->col_ptr, p->row_idx, J, d, m, p->y, p->z,
-                                                            p->loss, (float*)p->u);
+                                                            p->n, p->loss, (float*)p->u, touched);
   prof_end(p, ev);
   GENCD_CUDA_TRY(cudaGetLastError());
   return GENCD_OK;

@@ -201,6 +201,8 @@ def test_iterations_match(gb, variant, B, P):
 @pytest.mark.parametrize("loss", ["logistic", "squared"])
 @pytest.mark.parametrize("variant", ["shotgun", "thread_greedy", "coloring"])
 def test_solve_reaches_the_oracle_optimum(gb, loss, variant):
+    # B = 16 partitions: Thread-Greedy has no convergence guarantee (Section 7)
+    # and the oracle itself diverges on this problem for B >= 64.
     prob = workloads.uniform_problem(1000, 2000, 10, values="pm1", loss=loss, n_planted=30, seed=21)
     orc = oracle.Oracle(prob)
     lam = 0.05 * orc.lambda_max()
@@ -210,7 +212,7 @@ def test_solve_reaches_the_oracle_optimum(gb, loss, variant):
     P_opt = orc.objective(w_opt)
     with gb.Problem(prob) as p:
         p.set_lambda(lam)
-        p.set_params(variant=variant, tol_kkt=1e-10, max_iter=200_000, check_every=50, blocks=256)
+        p.set_params(variant=variant, tol_kkt=1e-10, max_iter=200_000, check_every=50, blocks=16)
         r = p.solve()
         assert r.status == 0, r.as_dict()
         w = p.w()
