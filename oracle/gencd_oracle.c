@@ -150,6 +150,17 @@ double oracle_lambda_max(const oracle_problem* pr) {
 
 /* ---- Section 3.2-3.3: the step of Eq. 7 and the proxy of Eq. 9 ---------- */
 
+/* |w + d| - |w| of Eq. 9.  When w + d keeps the sign of w the difference is
+ * exactly sign(w) d; evaluating it that way avoids the cancellation of two
+ * nearly equal magnitudes, which otherwise rounds a tiny negative proxy up to
+ * zero near the optimum and stalls the greedy accept rules. */
+static double abs_change(double w, double d) {
+  double x = w + d;
+  if (w > 0.0 && x >= 0.0) return d;
+  if (w < 0.0 && x <= 0.0) return -d;
+  return fabs(x) - fabs(w);
+}
+
 /* psi(x; a, b): clip x into [a, b] (Section 3.1). */
 static double psi(double x, double a, double b) {
   if (x < a) return a;
@@ -161,7 +172,7 @@ void oracle_step(double g, double w_j, double lambda, double beta_j, double* del
   if (beta_j > 0.0) {
     double d = -psi(w_j, (g - lambda) / beta_j, (g + lambda) / beta_j);        /* Eq. 7 */
     *delta = d;
-    *phi = 0.5 * beta_j * d * d + g * d + lambda * (fabs(w_j + d) - fabs(w_j)); /* Eq. 9 */
+    *phi = 0.5 * beta_j * d * d + g * d + lambda * abs_change(w_j, d);          /* Eq. 9 */
   } else { /* R2: F does not depend on w_j */
     *delta = -w_j;
     *phi = -lambda * fabs(w_j);

@@ -51,6 +51,15 @@ __device__ __forceinline__ float u_value<float>(int loss, double y, double t) {
   return -yf / (1.0f + expf(m));
 }
 
+// |w + d| - |w| of Eq. 9, exact (sign(w) d) while w + d keeps the sign of w,
+// so that a small negative proxy is not lost to cancellation near the optimum.
+__device__ __forceinline__ double abs_change(double w, double d) {
+  const double x = w + d;
+  if (w > 0.0 && x >= 0.0) return d;
+  if (w < 0.0 && x <= 0.0) return -d;
+  return fabs(x) - fabs(w);
+}
+
 // Eq. 7 step and Eq. 9 proxy for coordinate j with gradient g, weight wj,
 // curvature bound bj.  bj == 0 only for a column without non-zeros, whose
 // coordinate does not enter F: the step is the minimiser of lambda |w_j + d|.
@@ -61,7 +70,7 @@ __device__ __forceinline__ void eq7_step(double g, double wj, double lam, double
     double hi = (g + lam) / bj;
     double clipped = wj < lo ? lo : (wj > hi ? hi : wj);  // psi(w_j; lo, hi)
     d = -clipped;
-    phi = 0.5 * bj * d * d + g * d + lam * (fabs(wj + d) - fabs(wj));
+    phi = 0.5 * bj * d * d + g * d + lam * abs_change(wj, d);
   } else {
     d = -wj;
     phi = -lam * fabs(wj);

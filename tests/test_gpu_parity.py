@@ -338,7 +338,9 @@ def test_device_inputs_match_host_inputs(gb):
             p.set_params(variant="thread_greedy", blocks=100)
             p.iterate(10)
             ws.append(p.w())
-    np.testing.assert_array_equal(ws[0], ws[1])
+    # FP64 atomics combine partial sums of columns cut by lane boundaries in
+    # arrival order, so two runs agree to rounding, not bit for bit
+    np.testing.assert_allclose(ws[0], ws[1], rtol=1e-13, atol=1e-15)
 
 
 def test_not_converged_and_diverged_are_reported(gb):
