@@ -146,6 +146,22 @@ static int dalloc(T** ptr, size_t count) {
   return GENCD_OK;
 }
 
+int ensure_slots(gencd_problem* p, int64_t count) {
+  if (count <= p->slot_cap) return GENCD_OK;
+  GENCD_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  cudaFree(p->slot_f);
+  cudaFree(p->slot_d);
+  cudaFree(p->slot_j);
+  p->slot_f = p->slot_d = nullptr;
+  p->slot_j = nullptr;
+  p->slot_cap = 0;
+  GENCD_TRY(dalloc(&p->slot_f, count));
+  GENCD_TRY(dalloc(&p->slot_d, count));
+  GENCD_TRY(dalloc(&p->slot_j, count));
+  p->slot_cap = count;
+  return GENCD_OK;
+}
+
 static int reset_counters(gencd_problem* p) {
   GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal + 4, 0, 2 * sizeof(double), p->stream));
   p->stat_iters = 0;
@@ -193,8 +209,7 @@ static int enqueue_iteration(gencd_problem* p, int64_t* host_nnz) {
     GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal, 0, sizeof(double), p->stream));
     GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal + 7, 0, sizeof(double), p->stream));
     GENCD_TRY(launch_propose_all(p, p->u, p->precision == GENCD_F64));  // Propose, all columns
-    GENCD_TRY(launch_finalize(p, p->lambda, true));                      // + KKT of the start state
-    GENCD_TRY(launch_accept(p, B));                                      // Accept, best per partition
+    GENCD_TRY(launch_finalize_accept(p, B));  // step, proxy, KKT of the start state; Accept
     GENCD_TRY(launch_update_list(p, p->list_j, p->list_d, B, true));     // Update (atomic z)
     GENCD_TRY(launch_refresh_list(p, p->list_j, p->list_d, B, true));
     *host_nnz += p->nnz;
@@ -281,7 +296,8 @@ static void free_problem(gencd_problem* p) {
   if (!p) return;
   void* bufs[] = {p->col_ptr, p->row_idx, p->val, p->y, p->z, p->u, p->w, p->c, p->tile_col, p->gacc,
                   p->delta, p->phi, p->list_j, p->list_d, p->dscal, p->red, p->perm, p->sort_tmp,
-                  p->row_ptr, p->col_idx, p->csr_val, p->color, p->color_ptr, p->cols_by_color};
+                  p->row_ptr, p->col_idx, p->csr_val, p->color, p->color_ptr, p->cols_by_color,
+                  p->slot_f, p->slot_d, p->slot_j, p->list_off, p->scan_tmp};
   if (p->stream) cudaStreamSynchronize(p->stream);
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -317,6 +333,8 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
   GENCD_TRY(dalloc(&p->list_j, k));
   GENCD_TRY(dalloc(&p->list_d, k));
   GENCD_TRY(dalloc(&p->perm, k));
+  GENCD_TRY(dalloc(&p->list_off, k + 2));
+  GENCD_TRY(dalloc(&p->scan_tmp, scan_tmp_words(k + 2)));
   GENCD_TRY(dalloc(&p->dscal, 8));
   GENCD_TRY(dalloc(&p->red, 2 * kRedBlocks));
   if (cudaMallocHost((void**)&p->hpin, 8 * sizeof(double)) != cudaSuccess) {
@@ -364,8 +382,8 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
   GENCD_CUDA_TRY(cudaMemsetAsync(p->w, 0, sizeof(double) * k, st));
   GENCD_CUDA_TRY(cudaMemsetAsync(p->gacc, 0, sizeof(double) * k, st));
   GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal, 0, 8 * sizeof(double), st));
-  GENCD_TRY(launch_col_scale(p));
   GENCD_TRY(launch_tile_map(p));
+  GENCD_TRY(launch_col_scale(p));
   GENCD_TRY(launch_fill_u(p));
   // lambda_max = KKT violation of w = 0 at lambda = 0
   GENCD_TRY(launch_propose_all(p, p->u, p->precision == GENCD_F64));
@@ -373,12 +391,6 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
   GENCD_TRY(read_scalars(p));
   p->lambda_max = p->hpin[0];
   gencd_default_params(&p->params);
-  for (int i = 0; i < 2 * 4096; ++i) {
-    cudaEvent_t e;
-    if (cudaEventCreate(&e) != cudaSuccess) break;
-    p->prof.pool.push_back(e);
-  }
-  cudaGetLastError();
   return GENCD_OK;
 }
 
@@ -772,6 +784,14 @@ int gencd_permutation(gencd_problem* p, uint64_t seed, int64_t epoch, int64_t m,
 int gencd_profile_enable(gencd_problem* p, int32_t enable) {
   GENCD_CHECK_HANDLE(p);
   if (!enable) prof_flush(p);
+  if (enable && p->prof.pool.empty()) {  // event pairs, created on first use
+    for (int i = 0; i < 2 * 4096; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) break;
+      p->prof.pool.push_back(e);
+    }
+    cudaGetLastError();
+  }
   p->prof.enabled = enable != 0;
   return GENCD_OK;
 }

@@ -110,6 +110,14 @@ struct gencd_problem {
   // accepted / selected lists (capacity k)
   int32_t* list_j = nullptr;
   double* list_d = nullptr;
+  uint32_t* list_off = nullptr;  // exclusive prefix of the listed columns' nnz (k + 2)
+  uint32_t* scan_tmp = nullptr;  // scratch of the prefix sum
+
+  // accept candidates of (chunk, partition) pairs when partitions are few
+  double* slot_f = nullptr;
+  double* slot_d = nullptr;
+  int32_t* slot_j = nullptr;
+  int64_t slot_cap = 0;
 
   // device scalars: [0] kkt bits, [1] objective, [2] loss sum, [3] l1 sum,
   // [4] updates (int64), [5] nnz processed (int64), [6] scratch
@@ -153,9 +161,14 @@ constexpr int kRedBlocks = 1024;
 // kernels_propose.cu
 int launch_propose_all(gencd_problem* p, const void* u_vec, bool u_is_double);
 int launch_finalize(gencd_problem* p, double lambda, bool write_steps);
-int launch_accept(gencd_problem* p, int64_t B);
+int launch_finalize_accept(gencd_problem* p, int64_t B);  // Thread-Greedy / Greedy
+int ensure_slots(gencd_problem* p, int64_t count);
+// exclusive prefix sum of m uint32 (in place allowed); tmp holds scan_tmp_words(m)
+int exclusive_scan(gencd_problem* p, const uint32_t* in, uint32_t* out, int64_t m, uint32_t* tmp);
+int64_t scan_tmp_words(int64_t m);
 int launch_propose_list(gencd_problem* p, const int32_t* J, int64_t m, double* delta, double* phi);
 int launch_objective(gencd_problem* p);
+int launch_col_sumsq(gencd_problem* p);  // gacc_j = sum_i X_ij^2
 
 // kernels_update.cu
 int launch_fill_u(gencd_problem* p);

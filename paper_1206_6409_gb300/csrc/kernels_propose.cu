@@ -66,7 +66,8 @@ __device__ __forceinline__ void emit_partial(double* __restrict__ gacc, int32_t 
     atomicAdd(gacc + c, s);
 }
 
-template <typename V, typename U, int ITEMS>
+// SQ: sum X_ij^2 instead of X_ij u_i (the column scales c_j, at setup)
+template <typename V, typename U, int ITEMS, bool SQ = false>
 __global__ void __launch_bounds__(kThreads)
     k_propose_all(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
                   const V* __restrict__ val, const U* __restrict__ u,
@@ -87,7 +88,12 @@ __global__ void __launch_bounds__(kThreads)
     const int nvalid = (int)(b - a);
     U uu[ITEMS];
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) uu[i] = i < nvalid ? __ldg(u + r[i]) : U(0);
+    for (int i = 0; i < ITEMS; ++i) {
+      if (SQ)
+        uu[i] = (U)v[i];
+      else
+        uu[i] = i < nvalid ? __ldg(u + r[i]) : U(0);
+    }
 
     // column holding position a: the largest c in [tile_col[t], tile_col[t+1]]
     // with col_ptr[c] <= a (empty columns share their start with the next one)
@@ -143,71 +149,197 @@ __device__ __forceinline__ double block_max_nan(double v) {
   return v;
 }
 
+// Per-column part of Propose: Eq. 7 step, Eq. 9 proxy and KKT violation from
+// g_j.  A column with w_j = 0 and |g_j| <= lambda does not move (delta = 0,
+// phi = 0, KKT 0): that test replaces the FP64 divisions for the bulk of the
+// columns of a sparse solution.
+__device__ __forceinline__ bool column_is_idle(double g, double wj, double lam) {
+  return wj == 0.0 && fabs(g) <= lam;
+}
+
 __global__ void __launch_bounds__(kThreads)
     k_finalize(double* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ c,
-               int64_t k, double n, double lam, double beta, int beta_mode, double* __restrict__ delta,
+               int64_t k, double inv_n, double lam, double beta, int beta_mode, double* __restrict__ delta,
                double* __restrict__ phi, double* __restrict__ kkt_out, int write_steps) {
   double vmax = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) {
-    const double g = gacc[j] / n;
+    const double g = gacc[j] * inv_n;
     gacc[j] = 0.0;
     const double wj = w[j];
+    double d = 0.0, f = 0.0, v = 0.0;
+    if (!column_is_idle(g, wj, lam)) {
+      eq7_step(g, wj, lam, beta_mode ? beta : beta * c[j], d, f);
+      v = kkt_violation(g, wj, lam);
+    }
     if (write_steps) {
-      const double bj = beta_mode ? beta : beta * c[j];
-      double d, f;
-      eq7_step(g, wj, lam, bj, d, f);
       delta[j] = d;
       phi[j] = f;
     }
-    const double v = kkt_violation(g, wj, lam);
     vmax = (v > vmax || v != v) ? v : vmax;
   }
   vmax = block_max_nan<kThreads>(vmax);
   if (threadIdx.x == 0) atomic_max_nonneg(kkt_out, vmax);
 }
 
-// argmin of phi over each partition [floor(b k / B), floor((b+1) k / B))
-__global__ void __launch_bounds__(kThreads)
-    k_accept(const double* __restrict__ phi, const double* __restrict__ delta, int64_t k, int64_t B,
-             int32_t* __restrict__ list_j, double* __restrict__ list_d) {
-  __shared__ double s_phi[kThreads / 32];
+// candidate ordering of the accept rules: lower proxy, then lower column
+__device__ __forceinline__ bool better(double fa, int32_t ja, double fb, int32_t jb) {
+  return fa < fb || (fa == fb && ja < jb);
+}
+
+// block argmin of (phi, j) carrying delta; the result is valid in thread 0
+__device__ __forceinline__ void block_argmin(double& f, int32_t& j, double& d) {
+  __shared__ double s_f[kThreads / 32], s_d[kThreads / 32];
   __shared__ int32_t s_j[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double xf = __shfl_xor_sync(0xffffffffu, f, o);
+    const int32_t xj = __shfl_xor_sync(0xffffffffu, j, o);
+    const double xd = __shfl_xor_sync(0xffffffffu, d, o);
+    if (better(xf, xj, f, j)) {
+      f = xf;
+      j = xj;
+      d = xd;
+    }
+  }
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) {
+    s_f[wid] = f;
+    s_j[wid] = j;
+    s_d[wid] = d;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int q = 1; q < kThreads / 32; ++q)
+      if (better(s_f[q], s_j[q], f, j)) {
+        f = s_f[q];
+        j = s_j[q];
+        d = s_d[q];
+      }
+}
+
+// partition of column j: the b with floor(b k / B) <= j < floor((b+1) k / B)
+__device__ __forceinline__ int64_t partition_of(int64_t j, int64_t k, int64_t B) {
+  return ((j + 1) * B - 1) / k;
+}
+
+// Thread-Greedy with many partitions: one CTA per partition computes the
+// per-column step, proxy and KKT of its columns and accepts the best proxy
+// (Table 2, "greedy per thread"), so delta and phi never reach memory.
+__global__ void __launch_bounds__(kThreads)
+    k_finalize_accept(double* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ c,
+                      int64_t k, double inv_n, double lam, double beta, int beta_mode, int64_t B,
+                      int32_t* __restrict__ list_j, double* __restrict__ list_d, double* __restrict__ kkt_out) {
+  double vmax = 0.0;
   for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
     const int64_t lo = b * k / B, hi = (b + 1) * k / B;
-    double bp = DBL_MAX;
+    double bf = DBL_MAX, bd = 0.0;
     int32_t bj = INT32_MAX;
     for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
-      const double f = phi[j];
-      if (f < bp) {  // j increases along a thread's loop: equal keeps the lower
-        bp = f;
+      const double g = gacc[j] * inv_n;
+      gacc[j] = 0.0;
+      const double wj = w[j];
+      if (column_is_idle(g, wj, lam)) continue;  // phi = 0: never accepted
+      double d, f;
+      eq7_step(g, wj, lam, beta_mode ? beta : beta * c[j], d, f);
+      const double v = kkt_violation(g, wj, lam);
+      vmax = (v > vmax || v != v) ? v : vmax;
+      if (better(f, (int32_t)j, bf, bj)) {
+        bf = f;
         bj = (int32_t)j;
+        bd = d;
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double xp = __shfl_xor_sync(0xffffffffu, bp, o);
-      const int32_t xj = __shfl_xor_sync(0xffffffffu, bj, o);
-      if (xp < bp || (xp == bp && xj < bj)) {
-        bp = xp;
-        bj = xj;
+    block_argmin(bf, bj, bd);
+    if (threadIdx.x == 0) {
+      const bool ok = bj != INT32_MAX && bf < 0.0;
+      list_j[b] = ok ? bj : -1;
+      list_d[b] = ok ? bd : 0.0;
+    }
+  }
+  vmax = block_max_nan<kThreads>(vmax);
+  if (threadIdx.x == 0) atomic_max_nonneg(kkt_out, vmax);
+}
+
+// Thread-Greedy with few partitions (Greedy: B = 1), stage 1: one CTA per
+// chunk of S <= floor(k / B) columns, which meets at most two partitions;
+// the best candidate of (chunk c, partition b) goes to slot c + b.
+__global__ void __launch_bounds__(kThreads)
+    k_finalize_chunks(double* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ c,
+                      int64_t k, double inv_n, double lam, double beta, int beta_mode, int64_t B, int64_t S,
+                      double* __restrict__ slot_f, int32_t* __restrict__ slot_j, double* __restrict__ slot_d,
+                      double* __restrict__ kkt_out) {
+  const int64_t nchunks = (k + S - 1) / S;
+  double vmax = 0.0;
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int64_t lo = ch * S, hi = lo + S < k ? lo + S : k;
+    const int64_t b0 = partition_of(lo, k, B), b1 = partition_of(hi - 1, k, B);
+    double f0 = DBL_MAX, d0 = 0.0, f1 = DBL_MAX, d1 = 0.0;
+    int32_t j0 = INT32_MAX, j1 = INT32_MAX;
+    for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+      const double g = gacc[j] * inv_n;
+      gacc[j] = 0.0;
+      const double wj = w[j];
+      if (column_is_idle(g, wj, lam)) continue;
+      double d, f;
+      eq7_step(g, wj, lam, beta_mode ? beta : beta * c[j], d, f);
+      const double v = kkt_violation(g, wj, lam);
+      vmax = (v > vmax || v != v) ? v : vmax;
+      if (partition_of(j, k, B) == b0) {
+        if (better(f, (int32_t)j, f0, j0)) {
+          f0 = f;
+          j0 = (int32_t)j;
+          d0 = d;
+        }
+      } else if (better(f, (int32_t)j, f1, j1)) {
+        f1 = f;
+        j1 = (int32_t)j;
+        d1 = d;
       }
     }
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) {
-      s_phi[wid] = bp;
-      s_j[wid] = bj;
+    block_argmin(f0, j0, d0);
+    block_argmin(f1, j1, d1);
+    if (threadIdx.x == 0) {
+      slot_f[ch + b0] = f0;
+      slot_j[ch + b0] = j0;
+      slot_d[ch + b0] = d0;
+      if (b1 != b0) {
+        slot_f[ch + b1] = f1;
+        slot_j[ch + b1] = j1;
+        slot_d[ch + b1] = d1;
+      }
     }
     __syncthreads();
+  }
+  vmax = block_max_nan<kThreads>(vmax);
+  if (threadIdx.x == 0) atomic_max_nonneg(kkt_out, vmax);
+}
+
+// stage 2: partition b reduces its slots c + b for the chunks c it meets
+__global__ void __launch_bounds__(kThreads)
+    k_accept_slots(const double* __restrict__ slot_f, const int32_t* __restrict__ slot_j,
+                   const double* __restrict__ slot_d, int64_t k, int64_t B, int64_t S,
+                   int32_t* __restrict__ list_j, double* __restrict__ list_d) {
+  for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
+    const int64_t lo = b * k / B, hi = (b + 1) * k / B;
+    const int64_t c0 = lo / S, c1 = (hi - 1) / S;
+    double bf = DBL_MAX, bd = 0.0;
+    int32_t bj = INT32_MAX;
+    for (int64_t ch = c0 + threadIdx.x; ch <= c1; ch += blockDim.x) {
+      const double f = slot_f[ch + b];
+      const int32_t j = slot_j[ch + b];
+      if (better(f, j, bf, bj)) {
+        bf = f;
+        bj = j;
+        bd = slot_d[ch + b];
+      }
+    }
+    block_argmin(bf, bj, bd);
     if (threadIdx.x == 0) {
-      for (int q = 1; q < kThreads / 32; ++q)
-        if (s_phi[q] < bp || (s_phi[q] == bp && s_j[q] < bj)) {
-          bp = s_phi[q];
-          bj = s_j[q];
-        }
-      const bool ok = bj != INT32_MAX && bp < 0.0;
+      const bool ok = bj != INT32_MAX && bf < 0.0;
       list_j[b] = ok ? bj : -1;
-      list_d[b] = ok ? delta[bj] : 0.0;
+      list_d[b] = ok ? bd : 0.0;
     }
     __syncthreads();
   }
@@ -320,12 +452,26 @@ int launch_propose_all(gencd_problem* p, const void* u_vec, bool u_is_double) {
   return GENCD_OK;
 }
 
+int launch_col_sumsq(gencd_problem* p) {
+  if (p->ntiles == 0) return GENCD_OK;
+  const int grid = grid_for(p->ntiles * 32, kThreads, blocks_per_sm_cap(p, 8));
+  if (p->precision == GENCD_F64)
+    k_propose_all<double, double, kItemsF64, true><<<grid, kThreads, 0, p->stream>>>(
+        p->col_ptr, p->row_idx, (const double*)p->val, nullptr, p->tile_col, p->nnz, p->ntiles, p->gacc);
+  else
+    k_propose_all<float, double, kItemsF32, true><<<grid, kThreads, 0, p->stream>>>(
+        p->col_ptr, p->row_idx, (const float*)p->val, nullptr, p->tile_col, p->nnz, p->ntiles, p->gacc);
+  p->prof.launches[K_SETUP] += 1;
+  GENCD_CUDA_TRY(cudaGetLastError());
+  return GENCD_OK;
+}
+
 int launch_finalize(gencd_problem* p, double lambda, bool write_steps) {
   const double beta = p->loss == GENCD_LOSS_SQUARED ? 1.0 : 0.25;
   const int grid = grid_for(p->k, kThreads, blocks_per_sm_cap(p, 8));
   cudaEvent_t ev = nullptr;
   prof_begin(p, K_FINALIZE, &ev);
-  k_finalize<<<grid, kThreads, 0, p->stream>>>(p->gacc, p->w, p->c, p->k, (double)p->n, lambda, beta,
+  k_finalize<<<grid, kThreads, 0, p->stream>>>(p->gacc, p->w, p->c, p->k, 1.0 / (double)p->n, lambda, beta,
                                                p->params.beta_mode, p->delta, p->phi, p->dscal + 0,
                                                write_steps ? 1 : 0);
   prof_end(p, ev);
@@ -333,11 +479,30 @@ int launch_finalize(gencd_problem* p, double lambda, bool write_steps) {
   return GENCD_OK;
 }
 
-int launch_accept(gencd_problem* p, int64_t B) {
-  const int grid = (int)(B < (int64_t)p->num_sms * 16 ? B : (int64_t)p->num_sms * 16);
+int launch_finalize_accept(gencd_problem* p, int64_t B) {
+  const double beta = p->loss == GENCD_LOSS_SQUARED ? 1.0 : 0.25;
+  const double inv_n = 1.0 / (double)p->n;
   cudaEvent_t ev = nullptr;
-  prof_begin(p, K_ACCEPT, &ev);
-  k_accept<<<grid, kThreads, 0, p->stream>>>(p->phi, p->delta, p->k, B, p->list_j, p->list_d);
+  prof_begin(p, K_FINALIZE, &ev);
+  if (B >= 2LL * p->num_sms) {
+    const int grid = (int)(B < (int64_t)p->num_sms * 16 ? B : (int64_t)p->num_sms * 16);
+    k_finalize_accept<<<grid, kThreads, 0, p->stream>>>(p->gacc, p->w, p->c, p->k, inv_n, p->lambda, beta,
+                                                        p->params.beta_mode, B, p->list_j, p->list_d,
+                                                        p->dscal + 0);
+  } else {
+    int64_t S = p->k / B;  // >= 1 since B <= k; a chunk meets at most two partitions
+    if (S > 4096) S = 4096;
+    const int64_t nchunks = (p->k + S - 1) / S;
+    GENCD_TRY(ensure_slots(p, nchunks + B));
+    const int grid = grid_for(nchunks * kThreads, kThreads, blocks_per_sm_cap(p, 8));
+    k_finalize_chunks<<<grid, kThreads, 0, p->stream>>>(p->gacc, p->w, p->c, p->k, inv_n, p->lambda, beta,
+                                                        p->params.beta_mode, B, S, p->slot_f, p->slot_j,
+                                                        p->slot_d, p->dscal + 0);
+    const int g2 = (int)(B < (int64_t)p->num_sms * 16 ? B : (int64_t)p->num_sms * 16);
+    k_accept_slots<<<g2, kThreads, 0, p->stream>>>(p->slot_f, p->slot_j, p->slot_d, p->k, B, S, p->list_j,
+                                                   p->list_d);
+    p->prof.launches[K_ACCEPT] += 1;
+  }
   prof_end(p, ev);
   GENCD_CUDA_TRY(cudaGetLastError());
   return GENCD_OK;

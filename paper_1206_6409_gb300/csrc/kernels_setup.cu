@@ -34,21 +34,36 @@ __global__ void k_validate_colptr(const int64_t* __restrict__ col_ptr, int64_t k
   }
 }
 
-template <typename V>
-__global__ void k_validate_rows(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
-                                const V* __restrict__ val, int64_t k, int64_t n,
-                                unsigned long long* __restrict__ err) {
+// bit p of starts is set when nnz position p begins a non-empty column
+__global__ void k_mark_starts(const int64_t* __restrict__ col_ptr, int64_t k, uint32_t* __restrict__ starts) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) {
-    int64_t prev = -1;
-    for (int64_t p = col_ptr[j]; p < col_ptr[j + 1]; ++p) {
-      const int64_t r = row_idx[p];
-      const double v = (double)val[p];
-      if (r <= prev || r >= n || !isfinite(v)) {
-        atomicMin(err, (unsigned long long)j);
-        break;
+    const int64_t s = col_ptr[j];
+    if (col_ptr[j + 1] > s) atomicOr(starts + (s >> 5), 1u << (s & 31));
+  }
+}
+
+// one thread per non-zero: row in range, rows strictly increasing inside a
+// column, finite value; a failure records the column (found by bisection)
+template <typename V>
+__global__ void k_validate_rows(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
+                                const V* __restrict__ val, const uint32_t* __restrict__ starts, int64_t k,
+                                int64_t n, int64_t nnz, unsigned long long* __restrict__ err) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) {
+    const int32_t r = row_idx[p];
+    const bool start = (starts[p >> 5] >> (p & 31)) & 1u;
+    bool bad = r < 0 || r >= n || !isfinite((double)val[p]) || (!start && r <= row_idx[p - 1]);
+    if (bad) {
+      int64_t lo = 0, hi = k - 1;  // the column holding p: last c with col_ptr[c] <= p
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (col_ptr[mid] <= p)
+          lo = mid;
+        else
+          hi = mid - 1;
       }
-      prev = r;
+      atomicMin(err, (unsigned long long)lo);
     }
   }
 }
@@ -60,25 +75,6 @@ __global__ void k_validate_y(const double* __restrict__ y, int64_t n, int logist
     const double v = y[i];
     bool bad = !isfinite(v) || (logistic && v != 1.0 && v != -1.0);
     if (bad) atomicMin(err, (unsigned long long)i);
-  }
-}
-
-// c_j = ||X_j||^2 / n, one warp per column, FP64 sum
-template <typename V>
-__global__ void __launch_bounds__(kThreads)
-    k_col_scale(const int64_t* __restrict__ col_ptr, const V* __restrict__ val, int64_t k, double n,
-                double* __restrict__ c) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t j = warp; j < k; j += nwarps) {
-    double s = 0.0;
-    for (int64_t p = col_ptr[j] + lane; p < col_ptr[j + 1]; p += 32) {
-      const double v = (double)val[p];
-      s = fma(v, v, s);
-    }
-    s = warp_sum(s);
-    if (lane == 0) c[j] = s / n;
   }
 }
 
@@ -132,9 +128,10 @@ __global__ void __launch_bounds__(kThreads)
   if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
 
+// in and out may be the same array: every thread reads its entries before the
+// block-wide scan and writes them after it
 __global__ void __launch_bounds__(kThreads)
-    k_scan_apply(const uint32_t* __restrict__ in, int64_t m, const uint32_t* __restrict__ offs,
-                 uint32_t* __restrict__ out) {
+    k_scan_apply(const uint32_t* in, int64_t m, const uint32_t* __restrict__ offs, uint32_t* out) {
   const int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanItems;
   uint32_t x[kScanItems];
   uint32_t s = 0;
@@ -153,7 +150,7 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // out = exclusive_scan(in); tmp needs scan_tmp_words(m) uint32 words
-static int64_t scan_tmp_words(int64_t m) {
+int64_t scan_tmp_words(int64_t m) {
   int64_t w = 0;
   while (m > kScanBlock) {
     m = (m + kScanBlock - 1) / kScanBlock;
@@ -162,7 +159,7 @@ static int64_t scan_tmp_words(int64_t m) {
   return w + 2;
 }
 
-static int exclusive_scan(gencd_problem* p, const uint32_t* in, uint32_t* out, int64_t m, uint32_t* tmp) {
+int exclusive_scan(gencd_problem* p, const uint32_t* in, uint32_t* out, int64_t m, uint32_t* tmp) {
   if (m <= 0) return GENCD_OK;
   const int64_t nb = (m + kScanBlock - 1) / kScanBlock;
   if (nb == 1) {
@@ -600,12 +597,19 @@ int launch_power_step(gencd_problem* p, const double* v, const double* dinv, dou
   return launch_propose_all(p, r, true);
 }
 
+__global__ void k_scale_from_acc(double* __restrict__ gacc, int64_t k, double inv_n, double* __restrict__ c) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) {
+    c[j] = gacc[j] * inv_n;
+    gacc[j] = 0.0;
+  }
+}
+
+// c_j = ||X_j||^2 / n with the load-balanced streaming pass (needs the tile map)
 int launch_col_scale(gencd_problem* p) {
-  const int g = grid_for(p->k * 32, kThreads, p->num_sms * 8);
-  if (p->precision == GENCD_F64)
-    k_col_scale<double><<<g, kThreads, 0, p->stream>>>(p->col_ptr, (const double*)p->val, p->k, (double)p->n, p->c);
-  else
-    k_col_scale<float><<<g, kThreads, 0, p->stream>>>(p->col_ptr, (const float*)p->val, p->k, (double)p->n, p->c);
+  GENCD_TRY(launch_col_sumsq(p));
+  k_scale_from_acc<<<grid_for(p->k, kThreads, p->num_sms * 8), kThreads, 0, p->stream>>>(
+      p->gacc, p->k, 1.0 / (double)p->n, p->c);
   p->prof.launches[K_SETUP] += 1;
   GENCD_CUDA_TRY(cudaGetLastError());
   return GENCD_OK;
@@ -637,15 +641,21 @@ int validate_input(gencd_problem* p, int64_t* bad_col, int64_t* bad_row, int* st
     return GENCD_OK;
   }
   *stage = 1;
+  uint32_t* starts = nullptr;
+  const int64_t words = (p->nnz + 31) / 32 + 1;
+  GENCD_CUDA_TRY(cudaMallocAsync((void**)&starts, words * sizeof(uint32_t), p->stream));
+  GENCD_CUDA_TRY(cudaMemsetAsync(starts, 0, words * sizeof(uint32_t), p->stream));
+  k_mark_starts<<<grid_for(p->k, kThreads, g), kThreads, 0, p->stream>>>(p->col_ptr, p->k, starts);
   if (p->precision == GENCD_F64)
-    k_validate_rows<double><<<grid_for(p->k, kThreads, g), kThreads, 0, p->stream>>>(
-        p->col_ptr, p->row_idx, (const double*)p->val, p->k, p->n, err);
+    k_validate_rows<double><<<grid_for(p->nnz, kThreads, g), kThreads, 0, p->stream>>>(
+        p->col_ptr, p->row_idx, (const double*)p->val, starts, p->k, p->n, p->nnz, err);
   else
-    k_validate_rows<float><<<grid_for(p->k, kThreads, g), kThreads, 0, p->stream>>>(
-        p->col_ptr, p->row_idx, (const float*)p->val, p->k, p->n, err);
+    k_validate_rows<float><<<grid_for(p->nnz, kThreads, g), kThreads, 0, p->stream>>>(
+        p->col_ptr, p->row_idx, (const float*)p->val, starts, p->k, p->n, p->nnz, err);
+  GENCD_CUDA_TRY(cudaFreeAsync(starts, p->stream));
   k_validate_y<<<grid_for(p->n, kThreads, g), kThreads, 0, p->stream>>>(p->y, p->n,
                                                                         p->loss == GENCD_LOSS_LOGISTIC, err + 1);
-  p->prof.launches[K_SETUP] += 3;
+  p->prof.launches[K_SETUP] += 4;
   GENCD_CUDA_TRY(cudaMemcpyAsync(h, err, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
   GENCD_CUDA_TRY(cudaStreamSynchronize(p->stream));
   cudaFree(err);

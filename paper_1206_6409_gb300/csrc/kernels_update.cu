@@ -1,9 +1,10 @@
 // kernels_update.cu -- the Update step of GenCD (Algorithm 3) on sm_103a.
 //
-//  * k_update_list: w_j += delta_j and z += delta_j X_j for accepted columns
-//    that may share rows (Shotgun, Thread-Greedy, Greedy): one CTA per column,
-//    FP64 atomic adds into z (the paper's OpenMP `atomic`, Section 4.2).
-//  * k_refresh_list: u_i = l'(y_i, z_i) on the rows of the accepted columns,
+//  * k_update_flat: z += delta_j X_j for accepted columns that may share rows
+//    (Shotgun, Thread-Greedy, Greedy), FP64 atomic adds into z (the paper's
+//    OpenMP `atomic`, Section 4.2), work spread evenly over the non-zeros of
+//    all accepted columns; k_apply_w does w_j += delta_j.
+//  * k_refresh_flat: u_i = l'(y_i, z_i) on the rows of the accepted columns,
 //    launched after every atomic add of the iteration has landed.
 //  * k_coloring_iter: one Coloring iteration fused into a single pass: the
 //    columns of one colour class share no row (Section 4.1), so each warp
@@ -24,47 +25,105 @@ __global__ void __launch_bounds__(kThreads)
     u[i] = u_value<U>(loss, y[i], z[i]);
 }
 
-template <typename V>
-__global__ void __launch_bounds__(kThreads)
-    k_update_list(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
-                  const V* __restrict__ val, const int32_t* __restrict__ J,
-                  const double* __restrict__ D, int64_t m, double* __restrict__ w,
-                  double* __restrict__ z, unsigned long long* __restrict__ counters) {
-  for (int64_t e = blockIdx.x; e < m; e += gridDim.x) {
-    const int32_t j = J[e];
-    const double d = D[e];
-    if (j < 0 || d == 0.0) continue;  // rejected (Thread-Greedy) or a null step
-    const int64_t s = col_ptr[j], t = col_ptr[j + 1];
-    if (threadIdx.x == 0) {
-      w[j] += d;
-      atomicAdd(counters + 0, 1ull);
-      atomicAdd(counters + 1, (unsigned long long)(t - s));
-      atomicAdd(counters + 3, (unsigned long long)(t - s));  // touched this iteration
+// The applied columns of a list (J[e] >= 0 and D[e] != 0) are laid end to end
+// in a virtual range [0, off[m]) (off = exclusive prefix of their lengths), and
+// threads take equal runs of that range: a 50,000-nnz column is spread over
+// the whole GPU instead of one CTA.
+__global__ void k_list_len(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ J,
+                           const double* __restrict__ D, int64_t m, uint32_t* __restrict__ len) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e <= m; e += stride) {
+    uint32_t l = 0;
+    if (e < m) {
+      const int32_t j = J[e];
+      if (j >= 0 && D[e] != 0.0) l = (uint32_t)(col_ptr[j + 1] - col_ptr[j]);
     }
-    for (int64_t p = s + threadIdx.x; p < t; p += blockDim.x) atomicAdd(z + row_idx[p], d * (double)val[p]);
+    len[e] = l;
   }
 }
 
-// When the updates of the iteration touched at least n non-zeros, one dense
-// pass over all rows is cheaper than revisiting every touched entry (each
-// costs a gather and an exp); both leave u = l'(y, z) on every touched row.
+// w_j += delta_j for the applied entries (distinct columns), and the counters
+__global__ void k_apply_w(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ J,
+                          const double* __restrict__ D, int64_t m, double* __restrict__ w,
+                          unsigned long long* __restrict__ counters) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned long long upd = 0, work = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    const int32_t j = J[e];
+    const double d = D[e];
+    if (j < 0 || d == 0.0) continue;
+    w[j] += d;
+    upd += 1;
+    work += (unsigned long long)(col_ptr[j + 1] - col_ptr[j]);
+  }
+  upd = warp_sum(upd);
+  work = warp_sum(work);
+  if ((threadIdx.x & 31) == 0 && upd) {
+    atomicAdd(counters + 0, upd);
+    atomicAdd(counters + 1, work);
+    atomicAdd(counters + 3, work);  // touched this iteration
+  }
+}
+
+// last entry e in [0, m) with off[e] <= q
+__device__ __forceinline__ int64_t entry_of(const uint32_t* __restrict__ off, int64_t m, uint32_t q) {
+  int64_t lo = 0, hi = m - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= q)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+constexpr int kFlatRun = 4;  // consecutive virtual positions per thread
+
+// z_i += delta_j X_ij over the applied columns (atomic: columns may share rows)
+template <typename V>
+__global__ void __launch_bounds__(kThreads)
+    k_update_flat(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
+                  const V* __restrict__ val, const int32_t* __restrict__ J, const double* __restrict__ D,
+                  const uint32_t* __restrict__ off, int64_t m, double* __restrict__ z) {
+  const uint32_t total = off[m];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * kFlatRun;
+  for (int64_t q0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kFlatRun; q0 < total; q0 += stride) {
+    int64_t e = entry_of(off, m, (uint32_t)q0);
+    for (int r = 0; r < kFlatRun; ++r) {
+      const uint32_t q = (uint32_t)(q0 + r);
+      if (q >= total) break;
+      while (q >= off[e + 1]) ++e;
+      const int32_t j = J[e];
+      const int64_t p = col_ptr[j] + (q - off[e]);
+      atomicAdd(z + row_idx[p], D[e] * (double)val[p]);
+    }
+  }
+}
+
+// u_i = l'(y_i, z_i) on the rows of the applied columns, or on all rows when
+// the iteration touched at least n entries (one dense pass is cheaper then)
 template <typename U>
 __global__ void __launch_bounds__(kThreads)
-    k_refresh_list(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
-                   const int32_t* __restrict__ J, const double* __restrict__ D, int64_t m,
+    k_refresh_flat(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
+                   const int32_t* __restrict__ J, const uint32_t* __restrict__ off, int64_t m,
                    const double* __restrict__ y, const double* __restrict__ z, int64_t n, int loss,
-                   U* __restrict__ u, const unsigned long long* __restrict__ touched) {
-  if (*touched >= (unsigned long long)n) {
+                   U* __restrict__ u) {
+  const uint32_t total = off[m];
+  if ((int64_t)total >= n) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
       u[i] = u_value<U>(loss, y[i], z[i]);
     return;
   }
-  for (int64_t e = blockIdx.x; e < m; e += gridDim.x) {
-    const int32_t j = J[e];
-    if (j < 0 || D[e] == 0.0) continue;
-    const int64_t s = col_ptr[j], t = col_ptr[j + 1];
-    for (int64_t p = s + threadIdx.x; p < t; p += blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * kFlatRun;
+  for (int64_t q0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kFlatRun; q0 < total; q0 += stride) {
+    int64_t e = entry_of(off, m, (uint32_t)q0);
+    for (int r = 0; r < kFlatRun; ++r) {
+      const uint32_t q = (uint32_t)(q0 + r);
+      if (q >= total) break;
+      while (q >= off[e + 1]) ++e;
+      const int64_t p = col_ptr[J[e]] + (q - off[e]);
       const int32_t i = row_idx[p];
       u[i] = u_value<U>(loss, y[i], z[i]);
     }
@@ -148,35 +207,40 @@ int launch_fill_u(gencd_problem* p) {
   return GENCD_OK;
 }
 
+// Update (Algorithm 3) for the list (J, d): w, then z (atomic), then u.
 int launch_update_list(gencd_problem* p, const int32_t* J, const double* d, int64_t m, bool) {
   if (m <= 0) return GENCD_OK;
-  const int grid = (int)(m < (int64_t)p->num_sms * 16 ? m : (int64_t)p->num_sms * 16);
   unsigned long long* ctr = reinterpret_cast<unsigned long long*>(p->dscal + 4);
+  const int g = p->num_sms * 8;
   cudaEvent_t ev = nullptr;
   prof_begin(p, K_UPDATE, &ev);
+  k_list_len<<<grid_for(m + 1, kThreads, g), kThreads, 0, p->stream>>>(p->col_ptr, J, d, m, p->list_off);
+  GENCD_TRY(exclusive_scan(p, p->list_off, p->list_off, m + 1, p->scan_tmp));
+  k_apply_w<<<grid_for(m, kThreads, g), kThreads, 0, p->stream>>>(p->col_ptr, J, d, m, p->w, ctr);
   if (p->precision == GENCD_F64)
-    k_update_list<double><<<grid, kThreads, 0, p->stream>>>(p->col_ptr, p->row_idx, (const double*)p->val,
-                                                            J, d, m, p->w, p->z, ctr);
+    k_update_flat<double><<<g, kThreads, 0, p->stream>>>(p->col_ptr, p->row_idx, (const double*)p->val, J, d,
+                                                         p->list_off, m, p->z);
   else
-    k_update_list<float><<<grid, kThreads, 0, p->stream>>>(p->col_ptr, p->row_idx, (const float*)p->val,
-                                                           J, d, m, p->w, p->z, ctr);
+    k_update_flat<float><<<g, kThreads, 0, p->stream>>>(p->col_ptr, p->row_idx, (const float*)p->val, J, d,
+                                                        p->list_off, m, p->z);
   prof_end(p, ev);
+  p->prof.launches[K_UPDATE] += 2;  // length, apply-w and scatter kernels (+ the scan)
   GENCD_CUDA_TRY(cudaGetLastError());
   return GENCD_OK;
 }
 
-int launch_refresh_list(gencd_problem* p, const int32_t* J, const double* d, int64_t m, bool) {
+// needs the prefix list_off left by launch_update_list for the same list
+int launch_refresh_list(gencd_problem* p, const int32_t* J, const double*, int64_t m, bool) {
   if (m <= 0) return GENCD_OK;
-  const int grid = p->num_sms * 16;
-  const unsigned long long* touched = reinterpret_cast<const unsigned long long*>(p->dscal + 7);
+  const int g = p->num_sms * 8;
   cudaEvent_t ev = nullptr;
   prof_begin(p, K_REFRESH, &ev);
   if (p->precision == GENCD_F64)
-    k_refresh_list<double><<<grid, kThreads, 0, p->stream>>>(p->col_ptr, p->row_idx, J, d, m, p->y, p->z,
-                                                             p->n, p->loss, (double*)p->u, touched);
+    k_refresh_flat<double><<<g, kThreads, 0, p->stream>>>(p->col_ptr, p->row_idx, J, p->list_off, m, p->y, p->z,
+                                                           p->n, p->loss, (double*)p->u);
   else
-    k_refresh_list<float><<<grid, kThreads, 0, p->stream>>>(p->col_ptr, p->row_idx, J, d, m, p->y, p->z,
-                                                            p->n, p->loss, (float*)p->u, touched);
+    k_refresh_flat<float><<<g, kThreads, 0, p->stream>>>(p->col_ptr, p->row_idx, J, p->list_off, m, p->y, p->z,
+                                                          p->n, p->loss, (float*)p->u);
   prof_end(p, ev);
   GENCD_CUDA_TRY(cudaGetLastError());
   return GENCD_OK;
