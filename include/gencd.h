@@ -135,8 +135,11 @@ int gencd_get_params(gencd_problem* p, gencd_params* params);
 /*
  * Runs GenCD iterations (Algorithm 1) until the KKT violation is at most
  * tol_kkt, max_iter iterations or the timeout.  Convergence is checked every
- * check_every iterations with a full pass over X.  Returns GENCD_OK,
- * GENCD_NOT_CONVERGED, GENCD_EDIVERGED (non-finite objective) or an error.
+ * check_every iterations (Thread-Greedy and Greedy read the KKT value their
+ * Propose step computes and confirm convergence with one full pass; Shotgun
+ * and Coloring make a full pass over X at each check).  Returns GENCD_OK,
+ * GENCD_NOT_CONVERGED, GENCD_EDIVERGED (objective non-finite, or above 1e6
+ * times its value at the start of the call) or an error.
  * `out` (nullable) receives the statistics of the call.
  */
 int gencd_solve(gencd_problem* p, gencd_result* out);

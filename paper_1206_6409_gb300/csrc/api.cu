@@ -59,6 +59,26 @@ __global__ void k_convert(const S* __restrict__ in, int64_t m, D* __restrict__ o
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) out[i] = (D)in[i];
 }
 
+__global__ void k_inv_beta(const double* __restrict__ c, int64_t k, double beta, int beta_mode,
+                           double* __restrict__ ib) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) {
+    const double b = beta_mode ? beta : beta * c[j];
+    ib[j] = b > 0.0 ? 1.0 / b : 0.0;
+  }
+}
+
+int launch_inv_beta(gencd_problem* p) {
+  if (p->ib_mode == p->params.beta_mode) return GENCD_OK;
+  const double beta = p->loss == GENCD_LOSS_SQUARED ? 1.0 : 0.25;
+  k_inv_beta<<<grid_for(p->k, kThreads, p->num_sms * 8), kThreads, 0, p->stream>>>(p->c, p->k, beta,
+                                                                                     p->params.beta_mode, p->ib);
+  p->prof.launches[K_SETUP] += 1;
+  GENCD_CUDA_TRY(cudaGetLastError());
+  p->ib_mode = p->params.beta_mode;
+  return GENCD_OK;
+}
+
 __global__ void k_dinv(const double* __restrict__ c, int64_t k, double n, double* __restrict__ dinv,
                        double* __restrict__ v) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -294,11 +314,12 @@ static int compute_pstar(gencd_problem* p, int32_t* iters_out) {
 
 static void free_problem(gencd_problem* p) {
   if (!p) return;
-  void* bufs[] = {p->col_ptr, p->row_idx, p->val, p->y, p->z, p->u, p->w, p->c, p->tile_col, p->gacc,
+  void* bufs[] = {p->col_ptr, p->row_idx, p->val, p->y, p->z, p->u, p->w, p->c, p->ib, p->tile_col, p->gacc,
                   p->delta, p->phi, p->list_j, p->list_d, p->dscal, p->red, p->perm, p->sort_tmp,
                   p->row_ptr, p->col_idx, p->csr_val, p->color, p->color_ptr, p->cols_by_color,
                   p->slot_f, p->slot_d, p->slot_j, p->list_off, p->scan_tmp};
   if (p->stream) cudaStreamSynchronize(p->stream);
+  free_propose_plan(p);
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p->hpin) cudaFreeHost(p->hpin);
@@ -326,6 +347,7 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
   GENCD_TRY(dalloc((char**)&p->u, vsz * n));
   GENCD_TRY(dalloc(&p->w, k));
   GENCD_TRY(dalloc(&p->c, k));
+  GENCD_TRY(dalloc(&p->ib, k));
   GENCD_TRY(dalloc(&p->tile_col, p->ntiles + 1));
   GENCD_TRY(dalloc(&p->gacc, k));
   GENCD_TRY(dalloc(&p->delta, k));
@@ -384,6 +406,7 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
   GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal, 0, 8 * sizeof(double), st));
   GENCD_TRY(launch_tile_map(p));
   GENCD_TRY(launch_col_scale(p));
+  GENCD_TRY(build_propose_plan(p));
   GENCD_TRY(launch_fill_u(p));
   // lambda_max = KKT violation of w = 0 at lambda = 0
   GENCD_TRY(launch_propose_all(p, p->u, p->precision == GENCD_F64));
@@ -391,6 +414,7 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
   GENCD_TRY(read_scalars(p));
   p->lambda_max = p->hpin[0];
   gencd_default_params(&p->params);
+  GENCD_TRY(launch_inv_beta(p));
   return GENCD_OK;
 }
 
@@ -482,6 +506,7 @@ int gencd_set_params(gencd_problem* p, const gencd_params* a) {
   const bool reseed = a->seed != p->params.seed;
   p->params = *a;
   if (reseed) p->perm_epoch = -1;
+  GENCD_TRY(launch_inv_beta(p));
   return GENCD_OK;
 }
 
@@ -551,6 +576,7 @@ int gencd_solve(gencd_problem* p, gencd_result* out) {
   host_nnz += p->nnz;
   int status = GENCD_NOT_CONVERGED;
   const gencd_params& a = p->params;
+  const double obj_start = p->hpin[1];
   // Thread-Greedy and Greedy compute the KKT violation of each iteration's
   // start state inside the iteration; their checks read it and only run a
   // full evaluation to confirm convergence.  Shotgun and Coloring evaluate.
@@ -558,9 +584,9 @@ int gencd_solve(gencd_problem* p, gencd_result* out) {
   bool evaluated = true;  // hpin holds the KKT of the current state
   for (;;) {
     const double kkt = p->hpin[0], obj = p->hpin[1];
-    if (!std::isfinite(kkt) || !std::isfinite(obj)) {
+    if (!std::isfinite(kkt) || !std::isfinite(obj) || obj > 1e6 * (std::fabs(obj_start) + 1e-300)) {
       status = GENCD_EDIVERGED;
-      set_error("objective or KKT value is not finite");
+      set_error("objective is not finite or grew beyond 1e6 times its starting value");
       break;
     }
     if (kkt <= a.tol_kkt) {

@@ -77,6 +77,22 @@ __device__ __forceinline__ void eq7_step(double g, double wj, double lam, double
   }
 }
 
+// Eq. 7 with the clip tested in multiplied form and 1/beta_j precomputed:
+// for b > 0, w < (g - lam)/b <=> w b < g - lam and w > (g + lam)/b <=> w b > g + lam.
+// Same step as eq7_step up to rounding, without FP64 divisions.
+__device__ __forceinline__ void eq7_step_fast(double g, double wj, double lam, double bj, double ibj,
+                                              double& d, double& phi) {
+  if (bj > 0.0) {
+    const double t = wj * bj;
+    const double lo = g - lam, hi = g + lam;
+    d = t < lo ? -lo * ibj : (t > hi ? -hi * ibj : -wj);
+    phi = 0.5 * bj * d * d + g * d + lam * abs_change(wj, d);
+  } else {
+    d = -wj;
+    phi = -lam * fabs(wj);
+  }
+}
+
 // KKT violation of coordinate j.
 __device__ __forceinline__ double kkt_violation(double g, double wj, double lam) {
   if (wj == 0.0) return fmax(fabs(g) - lam, 0.0);

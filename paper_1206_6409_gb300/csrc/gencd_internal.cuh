@@ -72,6 +72,54 @@ struct Profiler {
   int64_t launches[K_NUM] = {0};       // counted whether or not profiling is on
 };
 
+// A CSC matrix as the streaming propose sees it (cmap: column map, may be null)
+struct CscView {
+  const int64_t* col_ptr;
+  const int32_t* row_idx;
+  const void* val;
+  const int32_t* tile_col;
+  int64_t nnz;
+  int64_t ntiles;
+  const int32_t* cmap;
+};
+
+// Row-slab plan of the streaming propose.  Rows are cut into slabs of
+// slab_rows rows, small enough that a slab of u fits in shared memory.
+// Heavy columns (>= heavy_min non-zeros) are stored slab by slab: for each
+// slab, the entries of every heavy column with rows in it (a "pair"), row as
+// a 16-bit offset inside the slab.  Each pair yields one partial sum; a
+// column's partials are contiguous (slot order) and summed into gacc.  Light
+// columns keep a compact CSC copy for the lane-segmented pass.
+struct ProposePlan {
+  bool built = false;
+  int32_t slab_rows = 0, nslabs = 0;
+  int64_t heavy_min = 0;
+  // light columns
+  int64_t nlight = 0, light_nnz = 0, light_ntiles = 0;
+  int32_t* light_cols = nullptr;
+  int64_t* light_col_ptr = nullptr;
+  int32_t* light_row = nullptr;
+  void* light_val = nullptr;
+  int32_t* light_tile_col = nullptr;
+  // heavy columns
+  int64_t nheavy = 0, entries = 0, npairs = 0, ntiles = 0;
+  int32_t* heavy_cols = nullptr;   // original column of heavy id h
+  uint16_t* s_row = nullptr;       // slab-local row of each entry
+  void* s_val = nullptr;           // value of each entry (padding: 0)
+  uint32_t* pair_start = nullptr;  // first entry of each pair; [npairs] = entries
+  uint32_t* pair_slot = nullptr;   // partial slot of each pair (column-major)
+  uint32_t* hslot_ptr = nullptr;   // first slot of heavy column h; [nheavy] = npairs
+  double* partial = nullptr;       // one partial sum per pair, zero between launches
+  uint32_t* tile_start = nullptr;  // tiles of 32*ITEMS entries inside one slab
+  uint32_t* tile_end = nullptr;
+  uint32_t* tile_pair = nullptr;   // pairs holding the tile's first and last entry
+  uint32_t* tile_pair_last = nullptr;
+  int32_t* tile_slab = nullptr;
+  int32_t* slab_tile_begin = nullptr;  // nslabs + 1
+  int32_t* cta_tile_begin = nullptr;   // grid + 1
+  int grid = 0;
+};
+
 // ---------------------------------------------------------------------------
 }  // namespace gencd
 
@@ -98,6 +146,8 @@ struct gencd_problem {
   void* u = nullptr;
   double* w = nullptr;
   double* c = nullptr;
+  double* ib = nullptr;     // 1 / beta_j (0 for a column without non-zeros)
+  int32_t ib_mode = -1;     // beta_mode that ib was computed for
 
   // streaming propose over all columns
   int items = 4;
@@ -151,6 +201,7 @@ struct gencd_problem {
   int64_t pstar = 0;
 
   gencd::Profiler prof;
+  gencd::ProposePlan plan;
 };
 
 namespace gencd {
@@ -160,15 +211,29 @@ constexpr int kRedBlocks = 1024;
 // ---- launchers (defined next to their kernels) ------------------------------
 // kernels_propose.cu
 int launch_propose_all(gencd_problem* p, const void* u_vec, bool u_is_double);
+int launch_propose_csc(gencd_problem* p, const CscView& a, const void* u_vec, bool u_is_double);
+// propose_plan.cu
+int build_propose_plan(gencd_problem* p);
+int launch_propose_plan(gencd_problem* p, const void* u_vec);
+void free_propose_plan(gencd_problem* p);
 int launch_finalize(gencd_problem* p, double lambda, bool write_steps);
 int launch_finalize_accept(gencd_problem* p, int64_t B);  // Thread-Greedy / Greedy
 int ensure_slots(gencd_problem* p, int64_t count);
 // exclusive prefix sum of m uint32 (in place allowed); tmp holds scan_tmp_words(m)
 int exclusive_scan(gencd_problem* p, const uint32_t* in, uint32_t* out, int64_t m, uint32_t* tmp);
 int64_t scan_tmp_words(int64_t m);
+size_t radix_tmp_words(int64_t m);
+int radix_sort_with_tmp(gencd_problem* p, uint32_t* keys, uint32_t* vals, int64_t m, int bits,
+                        uint32_t* keys_alt, uint32_t* vals_alt, uint32_t* tmp, bool* result_in_alt);
+int bits_for_max(int64_t maxval);
+int lower_bounds_u32_to_i64(gencd_problem* p, const uint32_t* sorted, int64_t m, int64_t count, int64_t* out);
+int iota_u32(gencd_problem* p, uint32_t* a, int64_t m);
+int fail_plan(const char* msg);
+int launch_tile_map_of(gencd_problem* p, const int64_t* col_ptr, int64_t k, int64_t ntiles, int32_t* tile_col);
 int launch_propose_list(gencd_problem* p, const int32_t* J, int64_t m, double* delta, double* phi);
 int launch_objective(gencd_problem* p);
 int launch_col_sumsq(gencd_problem* p);  // gacc_j = sum_i X_ij^2
+int launch_inv_beta(gencd_problem* p);   // ib_j = 1 / beta_j for the current beta_mode
 
 // kernels_update.cu
 int launch_fill_u(gencd_problem* p);

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kThreads)
     k_propose_all(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
                   const V* __restrict__ val, const U* __restrict__ u,
                   const int32_t* __restrict__ tile_col, int64_t nnz, int64_t ntiles,
-                  double* __restrict__ gacc) {
+                  const int32_t* __restrict__ cmap, double* __restrict__ gacc) {
   constexpr int TILE = 32 * ITEMS;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kThreads)
       if (i < nvalid) {
         const int64_t p = a + i;
         while (p >= cend) {  // column c ended before p (c + 1 <= k - 1 since p < nnz)
-          emit_partial(gacc, c, (double)acc, whole);
+          emit_partial(gacc, cmap ? cmap[c] : c, (double)acc, whole);
           ++c;
           cend = __ldg(col_ptr + c + 1);
           acc = V(0);
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kThreads)
         acc = fma(v[i], (V)uu[i], acc);
       }
     }
-    emit_partial(gacc, c, (double)acc, whole && cend <= b);
+    emit_partial(gacc, cmap ? cmap[c] : c, (double)acc, whole && cend <= b);
   }
 }
 
@@ -159,8 +159,9 @@ __device__ __forceinline__ bool column_is_idle(double g, double wj, double lam) 
 
 __global__ void __launch_bounds__(kThreads)
     k_finalize(double* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ c,
-               int64_t k, double inv_n, double lam, double beta, int beta_mode, double* __restrict__ delta,
-               double* __restrict__ phi, double* __restrict__ kkt_out, int write_steps) {
+               const double* __restrict__ ib, int64_t k, double inv_n, double lam, double beta, int beta_mode,
+               double* __restrict__ delta, double* __restrict__ phi, double* __restrict__ kkt_out,
+               int write_steps) {
   double vmax = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) {
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(kThreads)
     const double wj = w[j];
     double d = 0.0, f = 0.0, v = 0.0;
     if (!column_is_idle(g, wj, lam)) {
-      eq7_step(g, wj, lam, beta_mode ? beta : beta * c[j], d, f);
+      eq7_step_fast(g, wj, lam, beta_mode ? beta : beta * c[j], ib[j], d, f);
       v = kkt_violation(g, wj, lam);
     }
     if (write_steps) {
@@ -229,7 +230,7 @@ __device__ __forceinline__ int64_t partition_of(int64_t j, int64_t k, int64_t B)
 // (Table 2, "greedy per thread"), so delta and phi never reach memory.
 __global__ void __launch_bounds__(kThreads)
     k_finalize_accept(double* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ c,
-                      int64_t k, double inv_n, double lam, double beta, int beta_mode, int64_t B,
+                      const double* __restrict__ ib, int64_t k, double inv_n, double lam, double beta, int beta_mode, int64_t B,
                       int32_t* __restrict__ list_j, double* __restrict__ list_d, double* __restrict__ kkt_out) {
   double vmax = 0.0;
   for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(kThreads)
       const double wj = w[j];
       if (column_is_idle(g, wj, lam)) continue;  // phi = 0: never accepted
       double d, f;
-      eq7_step(g, wj, lam, beta_mode ? beta : beta * c[j], d, f);
+      eq7_step_fast(g, wj, lam, beta_mode ? beta : beta * c[j], ib[j], d, f);
       const double v = kkt_violation(g, wj, lam);
       vmax = (v > vmax || v != v) ? v : vmax;
       if (better(f, (int32_t)j, bf, bj)) {
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(kThreads)
 // the best candidate of (chunk c, partition b) goes to slot c + b.
 __global__ void __launch_bounds__(kThreads)
     k_finalize_chunks(double* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ c,
-                      int64_t k, double inv_n, double lam, double beta, int beta_mode, int64_t B, int64_t S,
+                      const double* __restrict__ ib, int64_t k, double inv_n, double lam, double beta, int beta_mode, int64_t B, int64_t S,
                       double* __restrict__ slot_f, int32_t* __restrict__ slot_j, double* __restrict__ slot_d,
                       double* __restrict__ kkt_out) {
   const int64_t nchunks = (k + S - 1) / S;
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(kThreads)
       const double wj = w[j];
       if (column_is_idle(g, wj, lam)) continue;
       double d, f;
-      eq7_step(g, wj, lam, beta_mode ? beta : beta * c[j], d, f);
+      eq7_step_fast(g, wj, lam, beta_mode ? beta : beta * c[j], ib[j], d, f);
       const double v = kkt_violation(g, wj, lam);
       vmax = (v > vmax || v != v) ? v : vmax;
       if (partition_of(j, k, B) == b0) {
@@ -349,7 +350,8 @@ template <typename V, typename U>
 __global__ void __launch_bounds__(kThreads)
     k_propose_list(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
                    const V* __restrict__ val, const U* __restrict__ u, const double* __restrict__ w,
-                   const double* __restrict__ c, const int32_t* __restrict__ J, int64_t m, double n,
+                   const double* __restrict__ c, const double* __restrict__ ib, const int32_t* __restrict__ J,
+                   int64_t m, double n,
                    double lam, double beta, int beta_mode, double* __restrict__ delta,
                    double* __restrict__ phi, unsigned long long* __restrict__ counters) {
   const int lane = threadIdx.x & 31;
@@ -364,7 +366,7 @@ __global__ void __launch_bounds__(kThreads)
     if (lane == 0) {
       const double bj = beta_mode ? beta : beta * c[j];
       double d, f;
-      eq7_step(g, w[j], lam, bj, d, f);
+      eq7_step_fast(g, w[j], lam, bj, ib[j], d, f);
       delta[e] = d;
       phi[e] = f;
       if (counters) atomicAdd(counters + 1, (unsigned long long)(t - s));
@@ -426,29 +428,42 @@ __global__ void k_objective_final(const double* __restrict__ red, int nblocks, d
 
 static int blocks_per_sm_cap(gencd_problem* p, int per_sm) { return p->num_sms * per_sm; }
 
-int launch_propose_all(gencd_problem* p, const void* u_vec, bool u_is_double) {
-  if (p->ntiles == 0) return GENCD_OK;
-  const int64_t tile = 32LL * p->items;
-  const int64_t warps_needed = p->ntiles;
-  const int grid = grid_for(warps_needed * 32, kThreads, blocks_per_sm_cap(p, 8));
-  cudaEvent_t ev = nullptr;
-  prof_begin(p, K_PROPOSE_ALL, &ev);
+// Lane-segmented streaming pass over a CSC (the whole X, or the compact copy
+// of the light columns with its column map): gacc[col] += X_col^T u.
+int launch_propose_csc(gencd_problem* p, const CscView& a, const void* u_vec, bool u_is_double) {
+  if (a.ntiles == 0) return GENCD_OK;
+  const int grid = grid_for(a.ntiles * 32, kThreads, blocks_per_sm_cap(p, 8));
   if (p->precision == GENCD_F64) {
     k_propose_all<double, double, kItemsF64><<<grid, kThreads, 0, p->stream>>>(
-        p->col_ptr, p->row_idx, (const double*)p->val, (const double*)u_vec, p->tile_col, p->nnz,
-        p->ntiles, p->gacc);
+        a.col_ptr, a.row_idx, (const double*)a.val, (const double*)u_vec, a.tile_col, a.nnz, a.ntiles, a.cmap,
+        p->gacc);
   } else if (u_is_double) {
     k_propose_all<float, double, kItemsF32><<<grid, kThreads, 0, p->stream>>>(
-        p->col_ptr, p->row_idx, (const float*)p->val, (const double*)u_vec, p->tile_col, p->nnz,
-        p->ntiles, p->gacc);
+        a.col_ptr, a.row_idx, (const float*)a.val, (const double*)u_vec, a.tile_col, a.nnz, a.ntiles, a.cmap,
+        p->gacc);
   } else {
     k_propose_all<float, float, kItemsF32><<<grid, kThreads, 0, p->stream>>>(
-        p->col_ptr, p->row_idx, (const float*)p->val, (const float*)u_vec, p->tile_col, p->nnz,
-        p->ntiles, p->gacc);
+        a.col_ptr, a.row_idx, (const float*)a.val, (const float*)u_vec, a.tile_col, a.nnz, a.ntiles, a.cmap,
+        p->gacc);
   }
-  (void)tile;
-  prof_end(p, ev);
   GENCD_CUDA_TRY(cudaGetLastError());
+  return GENCD_OK;
+}
+
+// gacc_j = X_j^T u for every column: the row-slab plan (heavy columns, u from
+// shared memory) plus the light columns, or the plain CSC pass when u is not
+// in the storage precision (power iteration) or no plan was built.
+int launch_propose_all(gencd_problem* p, const void* u_vec, bool u_is_double) {
+  cudaEvent_t ev = nullptr;
+  prof_begin(p, K_PROPOSE_ALL, &ev);
+  const bool native = u_is_double == (p->precision == GENCD_F64);
+  if (p->plan.built && native) {
+    GENCD_TRY(launch_propose_plan(p, u_vec));
+  } else {
+    CscView a{p->col_ptr, p->row_idx, p->val, p->tile_col, p->nnz, p->ntiles, nullptr};
+    GENCD_TRY(launch_propose_csc(p, a, u_vec, u_is_double));
+  }
+  prof_end(p, ev);
   return GENCD_OK;
 }
 
@@ -457,10 +472,12 @@ int launch_col_sumsq(gencd_problem* p) {
   const int grid = grid_for(p->ntiles * 32, kThreads, blocks_per_sm_cap(p, 8));
   if (p->precision == GENCD_F64)
     k_propose_all<double, double, kItemsF64, true><<<grid, kThreads, 0, p->stream>>>(
-        p->col_ptr, p->row_idx, (const double*)p->val, nullptr, p->tile_col, p->nnz, p->ntiles, p->gacc);
+        p->col_ptr, p->row_idx, (const double*)p->val, nullptr, p->tile_col, p->nnz, p->ntiles, nullptr,
+        p->gacc);
   else
     k_propose_all<float, double, kItemsF32, true><<<grid, kThreads, 0, p->stream>>>(
-        p->col_ptr, p->row_idx, (const float*)p->val, nullptr, p->tile_col, p->nnz, p->ntiles, p->gacc);
+        p->col_ptr, p->row_idx, (const float*)p->val, nullptr, p->tile_col, p->nnz, p->ntiles, nullptr,
+        p->gacc);
   p->prof.launches[K_SETUP] += 1;
   GENCD_CUDA_TRY(cudaGetLastError());
   return GENCD_OK;
@@ -471,7 +488,7 @@ int launch_finalize(gencd_problem* p, double lambda, bool write_steps) {
   const int grid = grid_for(p->k, kThreads, blocks_per_sm_cap(p, 8));
   cudaEvent_t ev = nullptr;
   prof_begin(p, K_FINALIZE, &ev);
-  k_finalize<<<grid, kThreads, 0, p->stream>>>(p->gacc, p->w, p->c, p->k, 1.0 / (double)p->n, lambda, beta,
+  k_finalize<<<grid, kThreads, 0, p->stream>>>(p->gacc, p->w, p->c, p->ib, p->k, 1.0 / (double)p->n, lambda, beta,
                                                p->params.beta_mode, p->delta, p->phi, p->dscal + 0,
                                                write_steps ? 1 : 0);
   prof_end(p, ev);
@@ -486,7 +503,7 @@ int launch_finalize_accept(gencd_problem* p, int64_t B) {
   prof_begin(p, K_FINALIZE, &ev);
   if (B >= 2LL * p->num_sms) {
     const int grid = (int)(B < (int64_t)p->num_sms * 16 ? B : (int64_t)p->num_sms * 16);
-    k_finalize_accept<<<grid, kThreads, 0, p->stream>>>(p->gacc, p->w, p->c, p->k, inv_n, p->lambda, beta,
+    k_finalize_accept<<<grid, kThreads, 0, p->stream>>>(p->gacc, p->w, p->c, p->ib, p->k, inv_n, p->lambda, beta,
                                                         p->params.beta_mode, B, p->list_j, p->list_d,
                                                         p->dscal + 0);
   } else {
@@ -495,7 +512,7 @@ int launch_finalize_accept(gencd_problem* p, int64_t B) {
     const int64_t nchunks = (p->k + S - 1) / S;
     GENCD_TRY(ensure_slots(p, nchunks + B));
     const int grid = grid_for(nchunks * kThreads, kThreads, blocks_per_sm_cap(p, 8));
-    k_finalize_chunks<<<grid, kThreads, 0, p->stream>>>(p->gacc, p->w, p->c, p->k, inv_n, p->lambda, beta,
+    k_finalize_chunks<<<grid, kThreads, 0, p->stream>>>(p->gacc, p->w, p->c, p->ib, p->k, inv_n, p->lambda, beta,
                                                         p->params.beta_mode, B, S, p->slot_f, p->slot_j,
                                                         p->slot_d, p->dscal + 0);
     const int g2 = (int)(B < (int64_t)p->num_sms * 16 ? B : (int64_t)p->num_sms * 16);
@@ -517,11 +534,11 @@ int launch_propose_list(gencd_problem* p, const int32_t* J, int64_t m, double* d
   prof_begin(p, K_PROPOSE_LIST, &ev);
   if (p->precision == GENCD_F64)
     k_propose_list<double, double><<<grid, kThreads, 0, p->stream>>>(
-        p->col_ptr, p->row_idx, (const double*)p->val, (const double*)p->u, p->w, p->c, J, m,
+        p->col_ptr, p->row_idx, (const double*)p->val, (const double*)p->u, p->w, p->c, p->ib, J, m,
         (double)p->n, p->lambda, beta, p->params.beta_mode, delta, phi, ctr);
   else
     k_propose_list<float, float><<<grid, kThreads, 0, p->stream>>>(
-        p->col_ptr, p->row_idx, (const float*)p->val, (const float*)p->u, p->w, p->c, J, m,
+        p->col_ptr, p->row_idx, (const float*)p->val, (const float*)p->u, p->w, p->c, p->ib, J, m,
         (double)p->n, p->lambda, beta, p->params.beta_mode, delta, phi, ctr);
   prof_end(p, ev);
   GENCD_CUDA_TRY(cudaGetLastError());

@@ -253,7 +253,7 @@ int ensure_sort_tmp(gencd_problem* p, size_t bytes) {
 }
 
 // scratch layout for sorting m pairs: counts (256 * nblocks) + offsets + scan tmp
-static size_t radix_tmp_words(int64_t m) {
+size_t radix_tmp_words(int64_t m) {
   const int64_t nb = (m + kRsTile - 1) / kRsTile;
   const int64_t nc = 256 * (nb > 0 ? nb : 1);
   return (size_t)(2 * nc + scan_tmp_words(nc));
@@ -262,8 +262,8 @@ static size_t radix_tmp_words(int64_t m) {
 // Sorts (keys, vals) by the low `bits` bits of the keys, stably.  Ping-pongs
 // with (keys_alt, vals_alt); *result_in_alt tells where the result is.
 // Needs radix_tmp_words(m) words at the start of p->sort_tmp... provided by caller
-static int radix_sort_impl(gencd_problem* p, uint32_t* keys, uint32_t* vals, int64_t m, int bits,
-                           uint32_t* keys_alt, uint32_t* vals_alt, uint32_t* tmp, bool* result_in_alt) {
+int radix_sort_with_tmp(gencd_problem* p, uint32_t* keys, uint32_t* vals, int64_t m, int bits,
+                        uint32_t* keys_alt, uint32_t* vals_alt, uint32_t* tmp, bool* result_in_alt) {
   *result_in_alt = false;
   if (m <= 1 || bits <= 0) return GENCD_OK;
   const int64_t nb = (m + kRsTile - 1) / kRsTile;
@@ -293,7 +293,7 @@ int radix_sort_pairs(gencd_problem* p, uint32_t* keys, uint32_t* vals, int64_t m
   uint32_t* tmp = nullptr;
   const size_t words = radix_tmp_words(m);
   GENCD_CUDA_TRY(cudaMallocAsync((void**)&tmp, words * 4, p->stream));
-  int rc = radix_sort_impl(p, keys, vals, m, bits, keys_alt, vals_alt, tmp, result_in_alt);
+  int rc = radix_sort_with_tmp(p, keys, vals, m, bits, keys_alt, vals_alt, tmp, result_in_alt);
   cudaFreeAsync(tmp, p->stream);
   return rc;
 }
@@ -319,7 +319,7 @@ int make_permutation(gencd_problem* p, uint64_t seed, int64_t epoch, int64_t m, 
   p->prof.launches[K_SETUP] += 1;
   GENCD_CUDA_TRY(cudaGetLastError());
   bool in_alt = false;
-  GENCD_TRY(radix_sort_impl(p, keys, vals, m, 32, ka, va, tmp, &in_alt));
+  GENCD_TRY(radix_sort_with_tmp(p, keys, vals, m, 32, ka, va, tmp, &in_alt));
   GENCD_CUDA_TRY(cudaMemcpyAsync(out, in_alt ? va : vals, (size_t)m * 4, cudaMemcpyDeviceToDevice, p->stream));
   return GENCD_OK;
 }
@@ -373,10 +373,35 @@ __global__ void k_lower_bounds(const uint32_t* __restrict__ sorted, int64_t m, i
   }
 }
 
-static int bits_for(int64_t maxval) {
+int bits_for_max(int64_t maxval) {
   int b = 1;
   while (b < 32 && (int64_t(1) << b) <= maxval) ++b;
   return b;
+}
+
+int lower_bounds_u32_to_i64(gencd_problem* p, const uint32_t* sorted, int64_t m, int64_t count, int64_t* out) {
+  k_lower_bounds<<<grid_for(count + 1, kThreads, p->num_sms * 8), kThreads, 0, p->stream>>>(sorted, m, count, out,
+                                                                                            nullptr);
+  p->prof.launches[K_SETUP] += 1;
+  GENCD_CUDA_TRY(cudaGetLastError());
+  return GENCD_OK;
+}
+
+__global__ void k_iota_u32(uint32_t* __restrict__ a, int64_t m) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) a[i] = (uint32_t)i;
+}
+
+int iota_u32(gencd_problem* p, uint32_t* a, int64_t m) {
+  k_iota_u32<<<grid_for(m, kThreads, p->num_sms * 8), kThreads, 0, p->stream>>>(a, m);
+  p->prof.launches[K_SETUP] += 1;
+  GENCD_CUDA_TRY(cudaGetLastError());
+  return GENCD_OK;
+}
+
+int fail_plan(const char* msg) {
+  set_error(msg);
+  return GENCD_EINVAL;
 }
 
 int build_csr(gencd_problem* p) {
@@ -401,7 +426,7 @@ int build_csr(gencd_problem* p) {
   p->prof.launches[K_SETUP] += 2;
   GENCD_CUDA_TRY(cudaGetLastError());
   bool in_alt = false;
-  GENCD_TRY(radix_sort_impl(p, keys, vals, nnz, bits_for(p->n - 1), ka, va, tmp, &in_alt));
+  GENCD_TRY(radix_sort_with_tmp(p, keys, vals, nnz, bits_for_max(p->n - 1), ka, va, tmp, &in_alt));
   const uint32_t* sk = in_alt ? ka : keys;
   const uint32_t* sv = in_alt ? va : vals;
   if (p->precision == GENCD_F64)
@@ -509,7 +534,7 @@ int build_color_classes(gencd_problem* p) {
   k_color_keys<<<grid_for(k, kThreads, g), kThreads, 0, p->stream>>>(p->color, k, keys, vals);
   GENCD_CUDA_TRY(cudaGetLastError());
   bool in_alt = false;
-  GENCD_TRY(radix_sort_impl(p, keys, vals, k, bits_for(p->ncolors - 1), ka, va, tmp, &in_alt));
+  GENCD_TRY(radix_sort_with_tmp(p, keys, vals, k, bits_for_max(p->ncolors - 1), ka, va, tmp, &in_alt));
   if (p->color_ptr) cudaFree(p->color_ptr);
   p->color_ptr = nullptr;
   GENCD_CUDA_TRY(cudaMalloc(&p->color_ptr, sizeof(int32_t) * (size_t)(p->ncolors + 1)));
@@ -615,14 +640,15 @@ int launch_col_scale(gencd_problem* p) {
   return GENCD_OK;
 }
 
-int launch_tile_map(gencd_problem* p) {
+int launch_tile_map_of(gencd_problem* p, const int64_t* col_ptr, int64_t k, int64_t ntiles, int32_t* tile_col) {
   const int64_t tile = 32LL * p->items;
-  k_tile_map<<<grid_for(p->k, kThreads, p->num_sms * 8), kThreads, 0, p->stream>>>(p->col_ptr, p->k, tile,
-                                                                                    p->ntiles, p->tile_col);
+  k_tile_map<<<grid_for(k, kThreads, p->num_sms * 8), kThreads, 0, p->stream>>>(col_ptr, k, tile, ntiles, tile_col);
   p->prof.launches[K_SETUP] += 1;
   GENCD_CUDA_TRY(cudaGetLastError());
   return GENCD_OK;
 }
+
+int launch_tile_map(gencd_problem* p) { return launch_tile_map_of(p, p->col_ptr, p->k, p->ntiles, p->tile_col); }
 
 // validation entry used by the API: returns first bad column / row or -1
 int validate_input(gencd_problem* p, int64_t* bad_col, int64_t* bad_row, int* stage) {

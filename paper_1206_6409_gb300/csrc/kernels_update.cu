@@ -134,7 +134,7 @@ template <typename V, typename U>
 __global__ void __launch_bounds__(kThreads)
     k_coloring_iter(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
                     const V* __restrict__ val, U* __restrict__ u, double* __restrict__ w,
-                    const double* __restrict__ c, double* __restrict__ z,
+                    const double* __restrict__ c, const double* __restrict__ ib, double* __restrict__ z,
                     const double* __restrict__ y, const int32_t* __restrict__ perm, int64_t q,
                     const int32_t* __restrict__ color_ptr, const int32_t* __restrict__ cols_by_color,
                     double n, double lam, double beta, int beta_mode, int loss,
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kThreads)
     const double wj = w[j];
     const double bj = beta_mode ? beta : beta * c[j];
     double d, f;
-    eq7_step(g, wj, lam, bj, d, f);  // identical on every lane
+    eq7_step_fast(g, wj, lam, bj, ib[j], d, f);  // identical on every lane
     work += (unsigned long long)(t - s);
     if (d != 0.0) {
       // every lane has read its u values above (warp_sum synchronised them)
@@ -255,11 +255,11 @@ int launch_coloring_iter(gencd_problem* p, int64_t q) {
   prof_begin(p, K_COLOR_ITER, &ev);
   if (p->precision == GENCD_F64)
     k_coloring_iter<double, double><<<grid, kThreads, 0, p->stream>>>(
-        p->col_ptr, p->row_idx, (const double*)p->val, (double*)p->u, p->w, p->c, p->z, p->y, p->perm, q,
+        p->col_ptr, p->row_idx, (const double*)p->val, (double*)p->u, p->w, p->c, p->ib, p->z, p->y, p->perm, q,
         p->color_ptr, p->cols_by_color, (double)p->n, p->lambda, beta, p->params.beta_mode, p->loss, ctr);
   else
     k_coloring_iter<float, float><<<grid, kThreads, 0, p->stream>>>(
-        p->col_ptr, p->row_idx, (const float*)p->val, (float*)p->u, p->w, p->c, p->z, p->y, p->perm, q,
+        p->col_ptr, p->row_idx, (const float*)p->val, (float*)p->u, p->w, p->c, p->ib, p->z, p->y, p->perm, q,
         p->color_ptr, p->cols_by_color, (double)p->n, p->lambda, beta, p->params.beta_mode, p->loss, ctr);
   prof_end(p, ev);
   GENCD_CUDA_TRY(cudaGetLastError());

@@ -1,0 +1,579 @@
+// propose_plan.cu -- row-slab layout of the streaming propose (g = X^T u over
+// all columns) on sm_103a.
+//
+// Gathering u_i at random rows costs one 32-byte L2 sector per 4- or 8-byte
+// value, which makes a plain CSC pass L2-bound long before HBM is saturated.
+// Here the rows are cut into slabs of at most 192 KB of u.  A persistent CTA
+// (one per SM, 1024 threads) copies the u slab of its work into shared memory
+// once and gathers from there.  Only columns with at least heavy_min
+// non-zeros use this layout (their entries are regrouped slab by slab, with
+// 16-bit in-slab rows); every (slab, column) "pair" produces one partial sum,
+// and the partials of a column are added in slab order afterwards.  Columns
+// with fewer non-zeros would produce about one partial per non-zero, so they
+// keep a compact CSC copy and the lane-segmented pass with gathers from L2.
+//
+// Within a slab the kernel works like the CSC pass: a warp owns a tile of
+// 256 consecutive entries, a lane 8 of them (128-bit loads of rows and
+// values), a lane sums its entries pair by pair in registers and emits each
+// partial with a store (pair inside the lane) or an FP64 atomic add.
+#include <algorithm>
+#include <vector>
+
+#include "device_math.cuh"
+#include "gencd_internal.cuh"
+
+namespace gencd {
+
+constexpr int kSlabBytes = 192 * 1024;
+constexpr int kSlabThreads = 1024;
+constexpr int kSlabItems = 8;
+constexpr int kSlabTile = 32 * kSlabItems;
+
+// ---------------------------------------------------------------------------
+// the kernel
+
+template <typename V>
+__device__ __forceinline__ void load8(const V* __restrict__ p, V (&v)[8]);
+
+template <>
+__device__ __forceinline__ void load8<float>(const float* __restrict__ p, float (&v)[8]) {
+  const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+  const float4 b = __ldcs(reinterpret_cast<const float4*>(p) + 1);
+  v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+}
+
+template <>
+__device__ __forceinline__ void load8<double>(const double* __restrict__ p, double (&v)[8]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double2 x = __ldcs(reinterpret_cast<const double2*>(p) + q);
+    v[2 * q] = x.x;
+    v[2 * q + 1] = x.y;
+  }
+}
+
+__device__ __forceinline__ void emit_pair(double* __restrict__ partial, uint32_t slot, double s, bool whole) {
+  if (whole)
+    partial[slot] = s;
+  else
+    atomicAdd(partial + slot, s);
+}
+
+template <typename V, typename U>
+__global__ void __launch_bounds__(kSlabThreads, 1)
+    k_propose_slabs(const uint16_t* __restrict__ s_row, const V* __restrict__ s_val,
+                    const uint32_t* __restrict__ pair_start, const uint32_t* __restrict__ pair_slot,
+                    const uint32_t* __restrict__ tile_start, const uint32_t* __restrict__ tile_end,
+                    const uint32_t* __restrict__ tile_pair, const uint32_t* __restrict__ tile_pair_last,
+                    const int32_t* __restrict__ tile_slab, const int32_t* __restrict__ slab_tile_begin,
+                    const int32_t* __restrict__ cta_tile_begin, const U* __restrict__ u, int64_t n,
+                    int32_t slab_rows, double* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  U* s_u = reinterpret_cast<U*>(smem_raw);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int t_end = cta_tile_begin[blockIdx.x + 1];
+  int t0 = cta_tile_begin[blockIdx.x];
+  while (t0 < t_end) {
+    const int r = tile_slab[t0];
+    const int t1 = min(t_end, slab_tile_begin[r + 1]);
+    const int64_t row0 = (int64_t)r * slab_rows;
+    const int rows = (int)min((int64_t)slab_rows, n - row0);
+    __syncthreads();  // the previous slab is no longer read
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) s_u[i] = u[row0 + i];
+    __syncthreads();
+    for (int t = t0 + warp; t < t1; t += nw) {
+      const uint32_t a = tile_start[t] + lane * kSlabItems;
+      if (a >= tile_end[t]) continue;  // tile ends are multiples of 8: lanes are full
+      const uint4 rr = __ldcs(reinterpret_cast<const uint4*>(s_row + a));
+      V v[8];
+      load8<V>(s_val + a, v);
+      const uint32_t w4[4] = {rr.x, rr.y, rr.z, rr.w};
+      U uu[8];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uu[2 * q] = s_u[w4[q] & 0xffffu];
+        uu[2 * q + 1] = s_u[w4[q] >> 16];
+      }
+      // pair holding entry a: the largest q in [tile_pair, tile_pair_last]
+      // with pair_start[q] <= a
+      uint32_t lo = tile_pair[t], hi = tile_pair_last[t];
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(pair_start + mid) <= a)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      uint32_t q = lo;
+      uint32_t cend = __ldg(pair_start + q + 1);
+      bool whole = __ldg(pair_start + q) >= a;
+      V acc = V(0);
+#pragma unroll
+      for (int i = 0; i < kSlabItems; ++i) {
+        const uint32_t p = a + i;
+        while (p >= cend) {
+          emit_pair(partial, __ldg(pair_slot + q), (double)acc, whole);
+          ++q;
+          cend = __ldg(pair_start + q + 1);
+          acc = V(0);
+          whole = true;
+        }
+        acc = fma(v[i], (V)uu[i], acc);
+      }
+      emit_pair(partial, __ldg(pair_slot + q), (double)acc, whole && cend <= a + kSlabItems);
+    }
+    t0 = t1;
+  }
+}
+
+// gacc of each heavy column = its partials in slab order; partials reset
+__global__ void k_pairs_to_gacc(const uint32_t* __restrict__ hslot_ptr, const int32_t* __restrict__ heavy_cols,
+                                int64_t nheavy, double* __restrict__ partial, double* __restrict__ gacc) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nheavy; h += stride) {
+    double s = 0.0;
+    for (uint32_t q = hslot_ptr[h]; q < hslot_ptr[h + 1]; ++q) {
+      s += partial[q];
+      partial[q] = 0.0;
+    }
+    gacc[heavy_cols[h]] = s;
+  }
+}
+
+int launch_propose_plan(gencd_problem* p, const void* u_vec) {
+  ProposePlan& P = p->plan;
+  if (P.nlight > 0) {
+    CscView a{P.light_col_ptr, P.light_row, P.light_val, P.light_tile_col, P.light_nnz, P.light_ntiles,
+              P.light_cols};
+    GENCD_TRY(launch_propose_csc(p, a, u_vec, p->precision == GENCD_F64));
+  }
+  if (P.nheavy > 0) {
+    const size_t smem = (size_t)P.slab_rows * (p->precision == GENCD_F64 ? 8 : 4);
+    if (p->precision == GENCD_F64)
+      k_propose_slabs<double, double><<<P.grid, kSlabThreads, smem, p->stream>>>(
+          P.s_row, (const double*)P.s_val, P.pair_start, P.pair_slot, P.tile_start, P.tile_end, P.tile_pair,
+          P.tile_pair_last, P.tile_slab, P.slab_tile_begin, P.cta_tile_begin, (const double*)u_vec, p->n,
+          P.slab_rows, P.partial);
+    else
+      k_propose_slabs<float, float><<<P.grid, kSlabThreads, smem, p->stream>>>(
+          P.s_row, (const float*)P.s_val, P.pair_start, P.pair_slot, P.tile_start, P.tile_end, P.tile_pair,
+          P.tile_pair_last, P.tile_slab, P.slab_tile_begin, P.cta_tile_begin, (const float*)u_vec, p->n,
+          P.slab_rows, P.partial);
+    GENCD_CUDA_TRY(cudaGetLastError());
+    k_pairs_to_gacc<<<grid_for(P.nheavy, kThreads, p->num_sms * 8), kThreads, 0, p->stream>>>(
+        P.hslot_ptr, P.heavy_cols, P.nheavy, P.partial, p->gacc);
+    p->prof.launches[K_PROPOSE_ALL] += 1;
+    GENCD_CUDA_TRY(cudaGetLastError());
+  }
+  return GENCD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// building the plan (once per problem)
+
+__global__ void k_plan_classify(const int64_t* __restrict__ col_ptr, int64_t k, int64_t hmin,
+                                uint32_t* __restrict__ hid, uint32_t* __restrict__ lid,
+                                uint32_t* __restrict__ hoff, uint32_t* __restrict__ loff) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= k; j += stride) {
+    uint32_t len = j < k ? (uint32_t)(col_ptr[j + 1] - col_ptr[j]) : 0u;
+    const bool heavy = len > 0 && (int64_t)len >= hmin;
+    const bool light = len > 0 && !heavy;
+    hid[j] = heavy;
+    lid[j] = light;
+    hoff[j] = heavy ? len : 0u;
+    loff[j] = light ? len : 0u;
+  }
+}
+
+__global__ void k_plan_columns(const int64_t* __restrict__ col_ptr, int64_t k, int64_t hmin,
+                               const uint32_t* __restrict__ hid, const uint32_t* __restrict__ lid,
+                               const uint32_t* __restrict__ loff, int32_t* __restrict__ heavy_cols,
+                               int32_t* __restrict__ light_cols, int64_t* __restrict__ light_col_ptr) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) {
+    const int64_t len = col_ptr[j + 1] - col_ptr[j];
+    if (len <= 0) continue;
+    if (len >= hmin) {
+      heavy_cols[hid[j]] = (int32_t)j;
+    } else {
+      light_cols[lid[j]] = (int32_t)j;
+      light_col_ptr[lid[j]] = loff[j];
+    }
+  }
+}
+
+template <typename V>
+__global__ void k_plan_copy_light(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
+                                  const V* __restrict__ val, int64_t k, int64_t hmin,
+                                  const uint32_t* __restrict__ loff, int32_t* __restrict__ lrow,
+                                  V* __restrict__ lval) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = warp; j < k; j += nwarps) {
+    const int64_t s = col_ptr[j], len = col_ptr[j + 1] - s;
+    if (len <= 0 || len >= hmin) continue;
+    for (int64_t t = lane; t < len; t += 32) {
+      lrow[loff[j] + t] = row_idx[s + t];
+      lval[loff[j] + t] = val[s + t];
+    }
+  }
+}
+
+// heavy entry e (column-major order): key = slab, plus its row, value, heavy id
+template <typename V>
+__global__ void k_plan_heavy_entries(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
+                                     const V* __restrict__ val, int64_t k, int64_t hmin,
+                                     const uint32_t* __restrict__ hid, const uint32_t* __restrict__ hoff,
+                                     int32_t slab_rows, uint32_t* __restrict__ keys, uint32_t* __restrict__ order,
+                                     uint32_t* __restrict__ hrow, uint32_t* __restrict__ hh, V* __restrict__ hval) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = warp; j < k; j += nwarps) {
+    const int64_t s = col_ptr[j], len = col_ptr[j + 1] - s;
+    if (len <= 0 || len < hmin) continue;
+    for (int64_t t = lane; t < len; t += 32) {
+      const uint32_t e = hoff[j] + (uint32_t)t;
+      const int32_t r = row_idx[s + t];
+      keys[e] = (uint32_t)(r / slab_rows);
+      order[e] = e;
+      hrow[e] = (uint32_t)r;
+      hh[e] = hid[j];
+      hval[e] = val[s + t];
+    }
+  }
+}
+
+// entries in slab order -> padded slab arrays, and the flag "a pair starts here"
+template <typename V>
+__global__ void k_plan_fill_slabs(const uint32_t* __restrict__ sk, const uint32_t* __restrict__ se, int64_t E,
+                                  const int64_t* __restrict__ slab_begin, const int64_t* __restrict__ pad_off,
+                                  int32_t slab_rows, const uint32_t* __restrict__ hrow,
+                                  const uint32_t* __restrict__ hh, const V* __restrict__ hval,
+                                  uint16_t* __restrict__ s_row, V* __restrict__ s_val,
+                                  uint32_t* __restrict__ newpair) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < E; i += stride) {
+    const uint32_t r = sk[i], e = se[i];
+    const int64_t ip = pad_off[r] + (i - slab_begin[r]);
+    s_row[ip] = (uint16_t)(hrow[e] - r * (uint32_t)slab_rows);
+    s_val[ip] = hval[e];
+    newpair[i] = (i == slab_begin[r] || hh[e] != hh[se[i - 1]]) ? 1u : 0u;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) newpair[E] = 0u;
+}
+
+__global__ void k_plan_fill_pairs(const uint32_t* __restrict__ sk, const uint32_t* __restrict__ se, int64_t E,
+                                  const int64_t* __restrict__ slab_begin, const int64_t* __restrict__ pad_off,
+                                  const uint32_t* __restrict__ hh, const uint32_t* __restrict__ pidx,
+                                  uint32_t* __restrict__ pair_start, uint32_t* __restrict__ pair_h) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < E; i += stride) {
+    if (pidx[i + 1] == pidx[i]) continue;
+    const uint32_t q = pidx[i], r = sk[i];
+    pair_start[q] = (uint32_t)(pad_off[r] + (i - slab_begin[r]));
+    pair_h[q] = hh[se[i]];
+  }
+}
+
+__global__ void k_plan_slots(const uint32_t* __restrict__ q_sorted, int64_t npairs, uint32_t* __restrict__ slot) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < npairs; s += stride) slot[q_sorted[s]] = (uint32_t)s;
+}
+
+__global__ void k_plan_lower_bounds(const uint32_t* __restrict__ sorted, int64_t m, int64_t count,
+                                    uint32_t* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= count; i += stride) {
+    int64_t lo = 0, hi = m;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)sorted[mid] < i)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    out[i] = (uint32_t)lo;
+  }
+}
+
+__global__ void k_plan_tiles(const int32_t* __restrict__ slab_tile_begin, const int64_t* __restrict__ pad_off,
+                             int32_t R, int64_t T, const uint32_t* __restrict__ pair_start, int64_t npairs,
+                             uint32_t* __restrict__ tile_start, uint32_t* __restrict__ tile_end,
+                             uint32_t* __restrict__ tile_pair, uint32_t* __restrict__ tile_pair_last,
+                             int32_t* __restrict__ tile_slab) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += stride) {
+    int32_t lo = 0, hi = R - 1;  // slab: last r with slab_tile_begin[r] <= t
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if (slab_tile_begin[mid] <= t)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const int32_t r = lo;
+    const int64_t s = pad_off[r] + (t - slab_tile_begin[r]) * (int64_t)kSlabTile;
+    const int64_t e = s + kSlabTile < pad_off[r + 1] ? s + kSlabTile : pad_off[r + 1];
+    tile_start[t] = (uint32_t)s;
+    tile_end[t] = (uint32_t)e;
+    tile_slab[t] = r;
+    for (int side = 0; side < 2; ++side) {
+      const int64_t x = side == 0 ? s : e - 1;
+      int64_t a = 0, b = npairs - 1;  // last pair with pair_start <= x
+      while (a < b) {
+        const int64_t mid = (a + b + 1) >> 1;
+        if ((int64_t)pair_start[mid] <= x)
+          a = mid;
+        else
+          b = mid - 1;
+      }
+      (side == 0 ? tile_pair : tile_pair_last)[t] = (uint32_t)a;
+    }
+  }
+}
+
+void free_propose_plan(gencd_problem* p) {
+  ProposePlan& P = p->plan;
+  void* bufs[] = {P.light_cols, P.light_col_ptr, P.light_row, P.light_val, P.light_tile_col, P.heavy_cols,
+                  P.s_row, P.s_val, P.pair_start, P.pair_slot, P.hslot_ptr, P.partial, P.tile_start,
+                  P.tile_end, P.tile_pair, P.tile_pair_last, P.tile_slab, P.slab_tile_begin, P.cta_tile_begin};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  P = ProposePlan();
+}
+
+template <typename T>
+static int palloc(T** ptr, int64_t count) {
+  *ptr = nullptr;
+  if (cudaMalloc((void**)ptr, sizeof(T) * (size_t)(count > 0 ? count : 1)) != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    set_error("out of device memory while building the row-slab plan");
+    return GENCD_ENOMEM;
+  }
+  return GENCD_OK;
+}
+
+// scratch that is freed when the build returns
+struct Scratch {
+  std::vector<void*> bufs;
+  template <typename T>
+  int get(T** ptr, int64_t count) {
+    int rc = palloc(ptr, count);
+    if (rc == GENCD_OK) bufs.push_back(*ptr);
+    return rc;
+  }
+  ~Scratch() {
+    for (void* b : bufs) cudaFree(b);
+  }
+};
+
+static int build_plan_impl(gencd_problem* p, Scratch& S) {
+  ProposePlan& P = p->plan;
+  const int64_t k = p->k, n = p->n;
+  const bool f64 = p->precision == GENCD_F64;
+  const size_t vsz = f64 ? 8 : 4;
+  const int g = p->num_sms * 8;
+  cudaStream_t st = p->stream;
+  P.slab_rows = (int32_t)(kSlabBytes / (f64 ? 8 : 4));
+  P.nslabs = (int32_t)((n + P.slab_rows - 1) / P.slab_rows);
+  // one slab: every non-empty column reads u from shared memory; otherwise a
+  // column takes this layout once it averages >= 8 entries per slab
+  P.heavy_min = P.nslabs == 1 ? 1 : 8LL * P.nslabs;
+
+  // classify, number and offset the columns
+  uint32_t *hid, *lid, *hoff, *loff, *tmp;
+  GENCD_TRY(S.get(&hid, k + 1));
+  GENCD_TRY(S.get(&lid, k + 1));
+  GENCD_TRY(S.get(&hoff, k + 1));
+  GENCD_TRY(S.get(&loff, k + 1));
+  GENCD_TRY(S.get(&tmp, scan_tmp_words(k + 1)));
+  k_plan_classify<<<grid_for(k + 1, kThreads, g), kThreads, 0, st>>>(p->col_ptr, k, P.heavy_min, hid, lid, hoff,
+                                                                      loff);
+  GENCD_TRY(exclusive_scan(p, hid, hid, k + 1, tmp));
+  GENCD_TRY(exclusive_scan(p, lid, lid, k + 1, tmp));
+  GENCD_TRY(exclusive_scan(p, hoff, hoff, k + 1, tmp));
+  GENCD_TRY(exclusive_scan(p, loff, loff, k + 1, tmp));
+  uint32_t tot[4];
+  GENCD_CUDA_TRY(cudaMemcpyAsync(&tot[0], hid + k, 4, cudaMemcpyDeviceToHost, st));
+  GENCD_CUDA_TRY(cudaMemcpyAsync(&tot[1], lid + k, 4, cudaMemcpyDeviceToHost, st));
+  GENCD_CUDA_TRY(cudaMemcpyAsync(&tot[2], hoff + k, 4, cudaMemcpyDeviceToHost, st));
+  GENCD_CUDA_TRY(cudaMemcpyAsync(&tot[3], loff + k, 4, cudaMemcpyDeviceToHost, st));
+  GENCD_CUDA_TRY(cudaStreamSynchronize(st));
+  P.nheavy = tot[0];
+  P.nlight = tot[1];
+  const int64_t E = tot[2];
+  P.light_nnz = tot[3];
+
+  GENCD_TRY(palloc(&P.heavy_cols, P.nheavy));
+  GENCD_TRY(palloc(&P.light_cols, P.nlight));
+  GENCD_TRY(palloc(&P.light_col_ptr, P.nlight + 1));
+  k_plan_columns<<<grid_for(k, kThreads, g), kThreads, 0, st>>>(p->col_ptr, k, P.heavy_min, hid, lid, loff,
+                                                                 P.heavy_cols, P.light_cols, P.light_col_ptr);
+  GENCD_CUDA_TRY(cudaGetLastError());
+
+  // light columns: compact CSC copy and its tile map
+  if (P.nlight > 0) {
+    const int64_t lpad = ((P.light_nnz + kPadNnz - 1) / kPadNnz) * kPadNnz + kPadNnz;
+    GENCD_TRY(palloc(&P.light_row, lpad));
+    GENCD_TRY(palloc((char**)&P.light_val, lpad * (int64_t)vsz));
+    GENCD_CUDA_TRY(cudaMemsetAsync(P.light_row, 0, sizeof(int32_t) * lpad, st));
+    GENCD_CUDA_TRY(cudaMemsetAsync(P.light_val, 0, vsz * lpad, st));
+    const int64_t ln = P.light_nnz;
+    GENCD_CUDA_TRY(cudaMemcpyAsync(P.light_col_ptr + P.nlight, &ln, 8, cudaMemcpyHostToDevice, st));
+    if (f64)
+      k_plan_copy_light<double><<<grid_for(k * 32, kThreads, g), kThreads, 0, st>>>(
+          p->col_ptr, p->row_idx, (const double*)p->val, k, P.heavy_min, loff, P.light_row, (double*)P.light_val);
+    else
+      k_plan_copy_light<float><<<grid_for(k * 32, kThreads, g), kThreads, 0, st>>>(
+          p->col_ptr, p->row_idx, (const float*)p->val, k, P.heavy_min, loff, P.light_row, (float*)P.light_val);
+    GENCD_CUDA_TRY(cudaGetLastError());
+    const int64_t tile = 32LL * p->items;
+    P.light_ntiles = (P.light_nnz + tile - 1) / tile;
+    GENCD_TRY(palloc(&P.light_tile_col, P.light_ntiles + 1));
+    GENCD_TRY(launch_tile_map_of(p, P.light_col_ptr, P.nlight, P.light_ntiles, P.light_tile_col));
+  }
+  if (P.nheavy == 0) return GENCD_OK;
+
+  // heavy entries grouped by slab (stable: column-major order kept inside a slab)
+  uint32_t *keys, *order, *ka, *va, *hrow, *hh, *stmp;
+  char* hval;
+  GENCD_TRY(S.get(&keys, E));
+  GENCD_TRY(S.get(&order, E));
+  GENCD_TRY(S.get(&ka, E));
+  GENCD_TRY(S.get(&va, E));
+  GENCD_TRY(S.get(&hrow, E));
+  GENCD_TRY(S.get(&hh, E));
+  GENCD_TRY(S.get(&hval, E * (int64_t)vsz));
+  GENCD_TRY(S.get(&stmp, (int64_t)radix_tmp_words(E)));
+  if (f64)
+    k_plan_heavy_entries<double><<<grid_for(k * 32, kThreads, g), kThreads, 0, st>>>(
+        p->col_ptr, p->row_idx, (const double*)p->val, k, P.heavy_min, hid, hoff, P.slab_rows, keys, order, hrow,
+        hh, (double*)hval);
+  else
+    k_plan_heavy_entries<float><<<grid_for(k * 32, kThreads, g), kThreads, 0, st>>>(
+        p->col_ptr, p->row_idx, (const float*)p->val, k, P.heavy_min, hid, hoff, P.slab_rows, keys, order, hrow,
+        hh, (float*)hval);
+  GENCD_CUDA_TRY(cudaGetLastError());
+  bool in_alt = false;
+  GENCD_TRY(radix_sort_with_tmp(p, keys, order, E, bits_for_max(P.nslabs - 1), ka, va, stmp, &in_alt));
+  const uint32_t* sk = in_alt ? ka : keys;
+  const uint32_t* se = in_alt ? va : order;
+
+  // slab offsets (unpadded from the sorted keys; padded to 8 entries on the host)
+  const int R = P.nslabs;
+  int64_t *slab_begin, *pad_off;
+  GENCD_TRY(S.get(&slab_begin, R + 1));
+  GENCD_TRY(S.get(&pad_off, R + 1));
+  GENCD_TRY(lower_bounds_u32_to_i64(p, sk, E, R, slab_begin));
+  std::vector<int64_t> hb(R + 1), hp(R + 1);
+  GENCD_CUDA_TRY(cudaMemcpyAsync(hb.data(), slab_begin, 8 * (R + 1), cudaMemcpyDeviceToHost, st));
+  GENCD_CUDA_TRY(cudaStreamSynchronize(st));
+  hp[0] = 0;
+  for (int r = 0; r < R; ++r) hp[r + 1] = hp[r] + ((hb[r + 1] - hb[r] + kSlabItems - 1) / kSlabItems) * kSlabItems;
+  P.entries = hp[R];
+  if (P.entries >= (int64_t(1) << 32)) return fail_plan("heavy entries exceed 2^32");
+  GENCD_CUDA_TRY(cudaMemcpyAsync(pad_off, hp.data(), 8 * (R + 1), cudaMemcpyHostToDevice, st));
+
+  GENCD_TRY(palloc(&P.s_row, P.entries + 8));
+  GENCD_TRY(palloc((char**)&P.s_val, (P.entries + 8) * (int64_t)vsz));
+  GENCD_CUDA_TRY(cudaMemsetAsync(P.s_row, 0, 2 * (P.entries + 8), st));
+  GENCD_CUDA_TRY(cudaMemsetAsync(P.s_val, 0, vsz * (P.entries + 8), st));
+  uint32_t* pidx;
+  GENCD_TRY(S.get(&pidx, E + 1));
+  if (f64)
+    k_plan_fill_slabs<double><<<grid_for(E, kThreads, g), kThreads, 0, st>>>(
+        sk, se, E, slab_begin, pad_off, P.slab_rows, hrow, hh, (const double*)hval, P.s_row, (double*)P.s_val,
+        pidx);
+  else
+    k_plan_fill_slabs<float><<<grid_for(E, kThreads, g), kThreads, 0, st>>>(
+        sk, se, E, slab_begin, pad_off, P.slab_rows, hrow, hh, (const float*)hval, P.s_row, (float*)P.s_val, pidx);
+  GENCD_CUDA_TRY(cudaGetLastError());
+  uint32_t* ptmp;
+  GENCD_TRY(S.get(&ptmp, scan_tmp_words(E + 1)));
+  GENCD_TRY(exclusive_scan(p, pidx, pidx, E + 1, ptmp));
+  uint32_t np32 = 0;
+  GENCD_CUDA_TRY(cudaMemcpyAsync(&np32, pidx + E, 4, cudaMemcpyDeviceToHost, st));
+  GENCD_CUDA_TRY(cudaStreamSynchronize(st));
+  P.npairs = np32;
+
+  // pairs: first entry and heavy column; slots in column-major order
+  uint32_t *pair_h, *qa, *qb, *ha, *qtmp;
+  GENCD_TRY(palloc(&P.pair_start, P.npairs + 1));
+  GENCD_TRY(S.get(&pair_h, P.npairs));
+  k_plan_fill_pairs<<<grid_for(E, kThreads, g), kThreads, 0, st>>>(sk, se, E, slab_begin, pad_off, hh, pidx,
+                                                                    P.pair_start, pair_h);
+  const uint32_t ent32 = (uint32_t)P.entries;
+  GENCD_CUDA_TRY(cudaMemcpyAsync(P.pair_start + P.npairs, &ent32, 4, cudaMemcpyHostToDevice, st));
+  GENCD_TRY(S.get(&qa, P.npairs));
+  GENCD_TRY(S.get(&qb, P.npairs));
+  GENCD_TRY(S.get(&ha, P.npairs));
+  GENCD_TRY(S.get(&qtmp, (int64_t)radix_tmp_words(P.npairs)));
+  GENCD_TRY(iota_u32(p, qa, P.npairs));
+  bool q_alt = false;
+  GENCD_TRY(radix_sort_with_tmp(p, pair_h, qa, P.npairs, bits_for_max(P.nheavy - 1), ha, qb, qtmp, &q_alt));
+  const uint32_t* h_sorted = q_alt ? ha : pair_h;
+  const uint32_t* q_sorted = q_alt ? qb : qa;
+  GENCD_TRY(palloc(&P.pair_slot, P.npairs));
+  GENCD_TRY(palloc(&P.hslot_ptr, P.nheavy + 1));
+  GENCD_TRY(palloc(&P.partial, P.npairs));
+  GENCD_CUDA_TRY(cudaMemsetAsync(P.partial, 0, 8 * (size_t)P.npairs, st));
+  k_plan_slots<<<grid_for(P.npairs, kThreads, g), kThreads, 0, st>>>(q_sorted, P.npairs, P.pair_slot);
+  k_plan_lower_bounds<<<grid_for(P.nheavy + 1, kThreads, g), kThreads, 0, st>>>(h_sorted, P.npairs, P.nheavy,
+                                                                                 P.hslot_ptr);
+  GENCD_CUDA_TRY(cudaGetLastError());
+
+  // tiles inside each slab, and contiguous runs of tiles per CTA
+  std::vector<int32_t> tb(R + 1);
+  tb[0] = 0;
+  for (int r = 0; r < R; ++r) tb[r + 1] = tb[r] + (int32_t)((hp[r + 1] - hp[r] + kSlabTile - 1) / kSlabTile);
+  P.ntiles = tb[R];
+  GENCD_TRY(palloc(&P.slab_tile_begin, R + 1));
+  GENCD_TRY(palloc(&P.tile_start, P.ntiles));
+  GENCD_TRY(palloc(&P.tile_end, P.ntiles));
+  GENCD_TRY(palloc(&P.tile_pair, P.ntiles));
+  GENCD_TRY(palloc(&P.tile_pair_last, P.ntiles));
+  GENCD_TRY(palloc(&P.tile_slab, P.ntiles));
+  GENCD_CUDA_TRY(cudaMemcpyAsync(P.slab_tile_begin, tb.data(), 4 * (R + 1), cudaMemcpyHostToDevice, st));
+  k_plan_tiles<<<grid_for(P.ntiles, kThreads, g), kThreads, 0, st>>>(P.slab_tile_begin, pad_off, R, P.ntiles,
+                                                                      P.pair_start, P.npairs, P.tile_start,
+                                                                      P.tile_end, P.tile_pair, P.tile_pair_last,
+                                                                      P.tile_slab);
+  GENCD_CUDA_TRY(cudaGetLastError());
+  P.grid = p->num_sms;
+  std::vector<int32_t> ctb(P.grid + 1);
+  for (int b = 0; b <= P.grid; ++b) ctb[b] = (int32_t)((int64_t)b * P.ntiles / P.grid);
+  GENCD_TRY(palloc(&P.cta_tile_begin, P.grid + 1));
+  GENCD_CUDA_TRY(cudaMemcpyAsync(P.cta_tile_begin, ctb.data(), 4 * (P.grid + 1), cudaMemcpyHostToDevice, st));
+  const int smem = (int)((size_t)P.slab_rows * (f64 ? 8 : 4));
+  if (f64)
+    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_slabs<double, double>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  else
+    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_slabs<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        smem));
+  GENCD_CUDA_TRY(cudaStreamSynchronize(st));  // scratch is freed on return
+  p->prof.launches[K_SETUP] += 10;
+  return GENCD_OK;
+}
+
+int build_propose_plan(gencd_problem* p) {
+  free_propose_plan(p);
+  int rc;
+  {
+    Scratch S;
+    rc = build_plan_impl(p, S);
+    if (rc != GENCD_OK) cudaStreamSynchronize(p->stream);
+  }
+  if (rc != GENCD_OK) {
+    free_propose_plan(p);
+    return rc;
+  }
+  p->plan.built = true;
+  return GENCD_OK;
+}
+
+}  // namespace gencd

@@ -94,6 +94,9 @@ PROBLEMS = {
     "ragged-logistic": lambda: ragged_problem("logistic"),
     "ragged-squared": lambda: ragged_problem("squared", 1),
     "zipf-logistic": lambda: workloads.config2_scaled(0.002, "logistic"),
+    # several row slabs, heavy and light columns
+    "zipf-slabs-squared": lambda: workloads.zipf_problem(120_000, 20_000, 400_000, cap=20_000, n_planted=10,
+                                                         loss="squared", seed=5),
 }
 
 
