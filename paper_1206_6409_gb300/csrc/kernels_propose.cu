@@ -151,10 +151,17 @@ __device__ __forceinline__ double block_max_nan(double v) {
 
 // Per-column part of Propose: Eq. 7 step, Eq. 9 proxy and KKT violation from
 // g_j.  A column with w_j = 0 and |g_j| <= lambda does not move (delta = 0,
-// phi = 0, KKT 0): that test replaces the FP64 divisions for the bulk of the
-// columns of a sparse solution.
-__device__ __forceinline__ bool column_is_idle(double g, double wj, double lam) {
-  return wj == 0.0 && fabs(g) <= lam;
+// phi = 0, KKT 0).  That test runs on the raw sum: |gacc_j| <= lambda n, both
+// sides non-negative doubles, whose order is the order of their bit patterns,
+// so the idle bulk of a sparse solution costs integer compares only.
+__device__ __forceinline__ bool column_is_idle(double gacc, double wj, uint64_t lam_n_bits) {
+  const uint64_t wb = (uint64_t)__double_as_longlong(wj) << 1;            // drop the sign
+  const uint64_t gb = (uint64_t)__double_as_longlong(gacc) & 0x7fffffffffffffffull;
+  return wb == 0 && gb <= lam_n_bits;
+}
+
+__device__ __forceinline__ uint64_t lam_n_bits_of(double lam, double n) {
+  return (uint64_t)__double_as_longlong(lam * n);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -163,13 +170,15 @@ __global__ void __launch_bounds__(kThreads)
                double* __restrict__ delta, double* __restrict__ phi, double* __restrict__ kkt_out,
                int write_steps) {
   double vmax = 0.0;
+  const uint64_t lnb = lam_n_bits_of(lam, 1.0 / inv_n);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) {
-    const double g = gacc[j] * inv_n;
+    const double ga = gacc[j];
     gacc[j] = 0.0;
     const double wj = w[j];
     double d = 0.0, f = 0.0, v = 0.0;
-    if (!column_is_idle(g, wj, lam)) {
+    if (!column_is_idle(ga, wj, lnb)) {
+      const double g = ga * inv_n;
       eq7_step_fast(g, wj, lam, beta_mode ? beta : beta * c[j], ib[j], d, f);
       v = kkt_violation(g, wj, lam);
     }
@@ -233,15 +242,17 @@ __global__ void __launch_bounds__(kThreads)
                       const double* __restrict__ ib, int64_t k, double inv_n, double lam, double beta, int beta_mode, int64_t B,
                       int32_t* __restrict__ list_j, double* __restrict__ list_d, double* __restrict__ kkt_out) {
   double vmax = 0.0;
+  const uint64_t lnb = lam_n_bits_of(lam, 1.0 / inv_n);
   for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
     const int64_t lo = b * k / B, hi = (b + 1) * k / B;
     double bf = DBL_MAX, bd = 0.0;
     int32_t bj = INT32_MAX;
     for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
-      const double g = gacc[j] * inv_n;
+      const double ga = gacc[j];
       gacc[j] = 0.0;
       const double wj = w[j];
-      if (column_is_idle(g, wj, lam)) continue;  // phi = 0: never accepted
+      if (column_is_idle(ga, wj, lnb)) continue;  // phi = 0: never accepted
+      const double g = ga * inv_n;
       double d, f;
       eq7_step_fast(g, wj, lam, beta_mode ? beta : beta * c[j], ib[j], d, f);
       const double v = kkt_violation(g, wj, lam);
@@ -272,6 +283,7 @@ __global__ void __launch_bounds__(kThreads)
                       double* __restrict__ slot_f, int32_t* __restrict__ slot_j, double* __restrict__ slot_d,
                       double* __restrict__ kkt_out) {
   const int64_t nchunks = (k + S - 1) / S;
+  const uint64_t lnb = lam_n_bits_of(lam, 1.0 / inv_n);
   double vmax = 0.0;
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const int64_t lo = ch * S, hi = lo + S < k ? lo + S : k;
@@ -279,10 +291,11 @@ __global__ void __launch_bounds__(kThreads)
     double f0 = DBL_MAX, d0 = 0.0, f1 = DBL_MAX, d1 = 0.0;
     int32_t j0 = INT32_MAX, j1 = INT32_MAX;
     for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
-      const double g = gacc[j] * inv_n;
+      const double ga = gacc[j];
       gacc[j] = 0.0;
       const double wj = w[j];
-      if (column_is_idle(g, wj, lam)) continue;
+      if (column_is_idle(ga, wj, lnb)) continue;
+      const double g = ga * inv_n;
       double d, f;
       eq7_step_fast(g, wj, lam, beta_mode ? beta : beta * c[j], ib[j], d, f);
       const double v = kkt_violation(g, wj, lam);

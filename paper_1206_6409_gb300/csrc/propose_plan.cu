@@ -59,6 +59,20 @@ __device__ __forceinline__ void emit_pair(double* __restrict__ partial, uint32_t
     atomicAdd(partial + slot, s);
 }
 
+// the entries of one lane: 8 in-slab rows (one 128-bit load) and 8 values
+template <typename V>
+struct LaneLoad {
+  uint4 rr;
+  V v[8];
+};
+
+template <typename V>
+__device__ __forceinline__ void load_lane(const uint16_t* __restrict__ s_row, const V* __restrict__ s_val,
+                                          uint32_t a, LaneLoad<V>& L) {
+  L.rr = __ldcs(reinterpret_cast<const uint4*>(s_row + a));
+  load8<V>(s_val + a, L.v);
+}
+
 template <typename V, typename U>
 __global__ void __launch_bounds__(kSlabThreads, 1)
     k_propose_slabs(const uint16_t* __restrict__ s_row, const V* __restrict__ s_val,
@@ -68,6 +82,8 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
                     const int32_t* __restrict__ tile_slab, const int32_t* __restrict__ slab_tile_begin,
                     const int32_t* __restrict__ cta_tile_begin, const U* __restrict__ u, int64_t n,
                     int32_t slab_rows, double* __restrict__ partial) {
+  // FP32 tiles are small enough to keep the next tile's loads in flight
+  constexpr bool kPrefetch = sizeof(V) == 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   U* s_u = reinterpret_cast<U*>(smem_raw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -81,46 +97,76 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
     __syncthreads();  // the previous slab is no longer read
     for (int i = threadIdx.x; i < rows; i += blockDim.x) s_u[i] = u[row0 + i];
     __syncthreads();
-    for (int t = t0 + warp; t < t1; t += nw) {
+    LaneLoad<V> nxt;
+    int t = t0 + warp;
+    if (kPrefetch && t < t1) {
       const uint32_t a = tile_start[t] + lane * kSlabItems;
-      if (a >= tile_end[t]) continue;  // tile ends are multiples of 8: lanes are full
-      const uint4 rr = __ldcs(reinterpret_cast<const uint4*>(s_row + a));
-      V v[8];
-      load8<V>(s_val + a, v);
-      const uint32_t w4[4] = {rr.x, rr.y, rr.z, rr.w};
-      U uu[8];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        uu[2 * q] = s_u[w4[q] & 0xffffu];
-        uu[2 * q + 1] = s_u[w4[q] >> 16];
-      }
-      // pair holding entry a: the largest q in [tile_pair, tile_pair_last]
-      // with pair_start[q] <= a
-      uint32_t lo = tile_pair[t], hi = tile_pair_last[t];
-      while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (__ldg(pair_start + mid) <= a)
-          lo = mid;
-        else
-          hi = mid - 1;
-      }
-      uint32_t q = lo;
-      uint32_t cend = __ldg(pair_start + q + 1);
-      bool whole = __ldg(pair_start + q) >= a;
-      V acc = V(0);
-#pragma unroll
-      for (int i = 0; i < kSlabItems; ++i) {
-        const uint32_t p = a + i;
-        while (p >= cend) {
-          emit_pair(partial, __ldg(pair_slot + q), (double)acc, whole);
-          ++q;
-          cend = __ldg(pair_start + q + 1);
-          acc = V(0);
-          whole = true;
+      if (a < tile_end[t]) load_lane(s_row, s_val, a, nxt);
+    }
+    for (; t < t1; t += nw) {  // warp-uniform loop
+      const uint32_t ts = tile_start[t], te = tile_end[t];
+      const uint32_t a = ts + lane * kSlabItems;
+      const bool active = a < te;  // tile ends are multiples of 8
+      LaneLoad<V> cur;
+      if (kPrefetch) {
+        cur = nxt;
+        const int tn = t + nw;
+        if (tn < t1) {
+          const uint32_t an = tile_start[tn] + lane * kSlabItems;
+          if (an < tile_end[tn]) load_lane(s_row, s_val, an, nxt);
         }
-        acc = fma(v[i], (V)uu[i], acc);
+      } else if (active) {
+        load_lane(s_row, s_val, a, cur);
       }
-      emit_pair(partial, __ldg(pair_slot + q), (double)acc, whole && cend <= a + kSlabItems);
+      V acc = V(0);
+      uint32_t q = 0, q_first = 0, cend = 0;
+      bool whole = false;
+      if (active) {
+        const uint32_t w4[4] = {cur.rr.x, cur.rr.y, cur.rr.z, cur.rr.w};
+        U uu[8];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          uu[2 * h] = s_u[w4[h] & 0xffffu];
+          uu[2 * h + 1] = s_u[w4[h] >> 16];
+        }
+        // pair holding entry a: the largest q in [tile_pair, tile_pair_last]
+        // with pair_start[q] <= a
+        uint32_t lo = tile_pair[t], hi = tile_pair_last[t];
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi + 1) >> 1;
+          if (__ldg(pair_start + mid) <= a)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        q = q_first = lo;
+        cend = __ldg(pair_start + q + 1);
+        whole = __ldg(pair_start + q) >= a;
+#pragma unroll
+        for (int i = 0; i < kSlabItems; ++i) {
+          const uint32_t p = a + i;
+          while (p >= cend) {
+            emit_pair(partial, __ldg(pair_slot + q), (double)acc, whole);
+            ++q;
+            cend = __ldg(pair_start + q + 1);
+            acc = V(0);
+            whole = true;
+          }
+          acc = fma(cur.v[i], (V)uu[i], acc);
+        }
+      }
+      // a full tile inside one pair: one warp sum and one emit instead of 32
+      const uint32_t qf = __shfl_sync(0xffffffffu, q_first, 0);
+      const uint32_t ql = __shfl_sync(0xffffffffu, q, 31);
+      if (te - ts == (uint32_t)kSlabTile && qf == ql) {
+        const V sum = warp_sum(acc);
+        if (lane == 0) {
+          const bool in_tile = __ldg(pair_start + qf) >= ts && __ldg(pair_start + qf + 1) <= te;
+          emit_pair(partial, __ldg(pair_slot + qf), (double)sum, in_tile);
+        }
+      } else if (active) {
+        emit_pair(partial, __ldg(pair_slot + q), (double)acc, whole && cend <= a + kSlabItems);
+      }
     }
     t0 = t1;
   }
