@@ -266,6 +266,8 @@ def run_gencd(args):
     st = p.stats()
     prof = {name: gb.gencd_profile_read(p.h, name) for name in gb.KERNELS}
     gb.gencd_profile_enable(p.h, False)
+    final_obj, final_kkt = p.objective()  # after the timed region
+    w_nonzeros = int(np.count_nonzero(p.w()))
     launches = int(sum(v[1] for v in prof.values()))
     nnz_done = int(st.nnz_processed)
     if world > 1:
@@ -350,7 +352,7 @@ def run_gencd(args):
             "kernel_ms": {k: (v[0] / v[1] if v[1] else 0.0, v[1]) for k, v in prof.items() if v[1]},
             "gpu_launches": launches,
             "updates_per_step": st.updates / args.steps,
-            "objective": st.objective, "kkt": st.kkt,
+            "objective": final_obj, "kkt": final_kkt, "w_nonzeros": w_nonzeros,
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,

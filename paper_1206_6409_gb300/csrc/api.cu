@@ -60,10 +60,11 @@ __global__ void k_convert(const S* __restrict__ in, int64_t m, D* __restrict__ o
 }
 
 __global__ void k_inv_beta(const double* __restrict__ c, int64_t k, double beta, int beta_mode,
-                           double* __restrict__ ib) {
+                           double* __restrict__ bj, double* __restrict__ ib) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) {
     const double b = beta_mode ? beta : beta * c[j];
+    bj[j] = b;
     ib[j] = b > 0.0 ? 1.0 / b : 0.0;
   }
 }
@@ -72,7 +73,7 @@ int launch_inv_beta(gencd_problem* p) {
   if (p->ib_mode == p->params.beta_mode) return GENCD_OK;
   const double beta = p->loss == GENCD_LOSS_SQUARED ? 1.0 : 0.25;
   k_inv_beta<<<grid_for(p->k, kThreads, p->num_sms * 8), kThreads, 0, p->stream>>>(p->c, p->k, beta,
-                                                                                     p->params.beta_mode, p->ib);
+                                                                                     p->params.beta_mode, p->bj, p->ib);
   p->prof.launches[K_SETUP] += 1;
   GENCD_CUDA_TRY(cudaGetLastError());
   p->ib_mode = p->params.beta_mode;
@@ -169,13 +170,14 @@ static int dalloc(T** ptr, size_t count) {
 int ensure_slots(gencd_problem* p, int64_t count) {
   if (count <= p->slot_cap) return GENCD_OK;
   GENCD_CUDA_TRY(cudaStreamSynchronize(p->stream));
-  cudaFree(p->slot_f);
+  cudaFree(p->slot_m);
   cudaFree(p->slot_d);
   cudaFree(p->slot_j);
-  p->slot_f = p->slot_d = nullptr;
+  p->slot_m = nullptr;
+  p->slot_d = nullptr;
   p->slot_j = nullptr;
   p->slot_cap = 0;
-  GENCD_TRY(dalloc(&p->slot_f, count));
+  GENCD_TRY(dalloc(&p->slot_m, count));
   GENCD_TRY(dalloc(&p->slot_d, count));
   GENCD_TRY(dalloc(&p->slot_j, count));
   p->slot_cap = count;
@@ -222,14 +224,14 @@ static int ensure_selection(gencd_problem* p, int64_t epoch, int64_t m) {
 }
 
 // one GenCD iteration (Algorithm 1) of the configured variant, enqueued
-static int enqueue_iteration(gencd_problem* p, int64_t* host_nnz) {
+static int enqueue_iteration(gencd_problem* p, int64_t* host_nnz, bool want_kkt) {
   const int v = p->params.variant;
   if (v == GENCD_THREAD_GREEDY || v == GENCD_GREEDY) {
     const int B = effective_B(p);
     GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal, 0, sizeof(double), p->stream));
     GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal + 7, 0, sizeof(double), p->stream));
     GENCD_TRY(launch_propose_all(p, p->u, p->precision == GENCD_F64));  // Propose, all columns
-    GENCD_TRY(launch_finalize_accept(p, B));  // step, proxy, KKT of the start state; Accept
+    GENCD_TRY(launch_finalize_accept(p, B, want_kkt));  // step, proxy (+ KKT of the start state); Accept
     GENCD_TRY(launch_update_list(p, p->list_j, p->list_d, B, true));     // Update (atomic z)
     GENCD_TRY(launch_refresh_list(p, p->list_j, p->list_d, B, true));
     *host_nnz += p->nnz;
@@ -317,7 +319,7 @@ static void free_problem(gencd_problem* p) {
   void* bufs[] = {p->col_ptr, p->row_idx, p->val, p->y, p->z, p->u, p->w, p->c, p->ib, p->tile_col, p->gacc,
                   p->delta, p->phi, p->list_j, p->list_d, p->dscal, p->red, p->perm, p->sort_tmp,
                   p->row_ptr, p->col_idx, p->csr_val, p->color, p->color_ptr, p->cols_by_color,
-                  p->slot_f, p->slot_d, p->slot_j, p->list_off, p->scan_tmp};
+                  p->slot_m, p->slot_d, p->slot_j, p->list_off, p->scan_tmp, p->bj};
   if (p->stream) cudaStreamSynchronize(p->stream);
   free_propose_plan(p);
   for (void* b : bufs)
@@ -348,6 +350,7 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
   GENCD_TRY(dalloc(&p->w, k));
   GENCD_TRY(dalloc(&p->c, k));
   GENCD_TRY(dalloc(&p->ib, k));
+  GENCD_TRY(dalloc(&p->bj, k));
   GENCD_TRY(dalloc(&p->tile_col, p->ntiles + 1));
   GENCD_TRY(dalloc(&p->gacc, k));
   GENCD_TRY(dalloc(&p->delta, k));
@@ -408,13 +411,13 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
   GENCD_TRY(launch_col_scale(p));
   GENCD_TRY(build_propose_plan(p));
   GENCD_TRY(launch_fill_u(p));
+  gencd_default_params(&p->params);
+  GENCD_TRY(launch_inv_beta(p));
   // lambda_max = KKT violation of w = 0 at lambda = 0
   GENCD_TRY(launch_propose_all(p, p->u, p->precision == GENCD_F64));
   GENCD_TRY(launch_finalize(p, 0.0, false));
   GENCD_TRY(read_scalars(p));
   p->lambda_max = p->hpin[0];
-  gencd_default_params(&p->params);
-  GENCD_TRY(launch_inv_beta(p));
   return GENCD_OK;
 }
 
@@ -553,7 +556,10 @@ int gencd_iterate(gencd_problem* p, int64_t iters, gencd_result* out) {
   auto t0 = std::chrono::steady_clock::now();
   if (out) GENCD_TRY(reset_counters(p));
   int64_t host_nnz = 0;
-  for (int64_t i = 0; i < iters; ++i) GENCD_TRY(enqueue_iteration(p, &host_nnz));
+  // the KKT violation of the start state is reduced in every check_every-th
+  // iteration (a5 of the hot path) and in the last one
+  for (int64_t i = 0; i < iters; ++i)
+    GENCD_TRY(enqueue_iteration(p, &host_nnz, i + 1 == iters || (p->t + 1) % p->params.check_every == 0));
   if (!out) {
     GENCD_CUDA_TRY(cudaGetLastError());
     return GENCD_OK;
@@ -605,7 +611,7 @@ int gencd_solve(gencd_problem* p, gencd_result* out) {
     const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (a.timeout_s > 0.0 && el >= a.timeout_s) break;
     const int64_t step = std::min<int64_t>(a.check_every, a.max_iter - iters);
-    for (int64_t i = 0; i < step; ++i) GENCD_TRY(enqueue_iteration(p, &host_nnz));
+    for (int64_t i = 0; i < step; ++i) GENCD_TRY(enqueue_iteration(p, &host_nnz, i + 1 == step));
     iters += step;
     if (fused) {
       GENCD_TRY(launch_objective(p));  // divergence watch on the current state

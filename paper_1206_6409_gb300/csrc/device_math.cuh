@@ -51,52 +51,39 @@ __device__ __forceinline__ float u_value<float>(int loss, double y, double t) {
   return -yf / (1.0f + expf(m));
 }
 
-// |w + d| - |w| of Eq. 9, exact (sign(w) d) while w + d keeps the sign of w,
-// so that a small negative proxy is not lost to cancellation near the optimum.
-__device__ __forceinline__ double abs_change(double w, double d) {
-  const double x = w + d;
-  if (w > 0.0 && x >= 0.0) return d;
-  if (w < 0.0 && x <= 0.0) return -d;
-  return fabs(x) - fabs(w);
-}
-
-// Eq. 7 step and Eq. 9 proxy for coordinate j with gradient g, weight wj,
-// curvature bound bj.  bj == 0 only for a column without non-zeros, whose
-// coordinate does not enter F: the step is the minimiser of lambda |w_j + d|.
-__device__ __forceinline__ void eq7_step(double g, double wj, double lam, double bj, double& d,
+// Eq. 7 step and Eq. 9 proxy for coordinate j from its gradient g, weight
+// wj, curvature bound bj = beta_j and ibj = 1/beta_j:
+//   delta = -psi(w_j; (g - lam)/b, (g + lam)/b),
+//   phi   = b/2 delta^2 + g delta + lam (|w_j + delta| - |w_j|).
+// For b > 0 the clip is tested in multiplied form (w b < g - lam, w b > g + lam)
+// and the bound is applied with the precomputed 1/b: no FP64 divisions, the
+// same step up to rounding.  |w + delta| - |w| is taken as sign(w) delta
+// (exact) while w + delta keeps the sign of w, so that a small negative proxy
+// is not lost to cancellation near the optimum; the sign tests use the bit
+// patterns.  bj == 0 only for a column without non-zeros, whose coordinate
+// does not enter F: the step is the minimiser of lam |w_j + delta|.
+__device__ __forceinline__ void eq7_step(double g, double wj, double lam, double bj, double ibj, double& d,
                                          double& phi) {
-  if (bj > 0.0) {
-    double lo = (g - lam) / bj;
-    double hi = (g + lam) / bj;
-    double clipped = wj < lo ? lo : (wj > hi ? hi : wj);  // psi(w_j; lo, hi)
-    d = -clipped;
-    phi = 0.5 * bj * d * d + g * d + lam * abs_change(wj, d);
-  } else {
-    d = -wj;
-    phi = -lam * fabs(wj);
-  }
-}
-
-// Eq. 7 with the clip tested in multiplied form and 1/beta_j precomputed:
-// for b > 0, w < (g - lam)/b <=> w b < g - lam and w > (g + lam)/b <=> w b > g + lam.
-// Same step as eq7_step up to rounding, without FP64 divisions.
-__device__ __forceinline__ void eq7_step_fast(double g, double wj, double lam, double bj, double ibj,
-                                              double& d, double& phi) {
   if (bj > 0.0) {
     const double t = wj * bj;
     const double lo = g - lam, hi = g + lam;
     d = t < lo ? -lo * ibj : (t > hi ? -hi * ibj : -wj);
-    phi = 0.5 * bj * d * d + g * d + lam * abs_change(wj, d);
   } else {
     d = -wj;
-    phi = -lam * fabs(wj);
   }
+  const double x = wj + d;
+  const uint64_t sw = (uint64_t)__double_as_longlong(wj), sx = (uint64_t)__double_as_longlong(x);
+  const bool keep = (sw << 1) != 0 && (((sw ^ sx) >> 63) == 0 || (sx << 1) == 0);
+  const double dabs = keep ? ((sw >> 63) ? -d : d) : fabs(x) - fabs(wj);
+  phi = bj > 0.0 ? d * fma(0.5 * bj, d, g) + lam * dabs : -lam * fabs(wj);
 }
 
-// KKT violation of coordinate j.
+// KKT violation of coordinate j: max(|g| - lam, 0) if w_j = 0, else
+// |g + lam sign(w_j)|.
 __device__ __forceinline__ double kkt_violation(double g, double wj, double lam) {
-  if (wj == 0.0) return fmax(fabs(g) - lam, 0.0);
-  return fabs(g + (wj > 0.0 ? lam : -lam));
+  const uint64_t sw = (uint64_t)__double_as_longlong(wj);
+  if ((sw << 1) == 0) return fmax(fabs(g) - lam, 0.0);
+  return fabs(g + ((sw >> 63) ? -lam : lam));
 }
 
 // SplitMix64 output i of the stream whose state starts at s

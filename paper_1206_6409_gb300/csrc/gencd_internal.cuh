@@ -147,6 +147,7 @@ struct gencd_problem {
   double* w = nullptr;
   double* c = nullptr;
   double* ib = nullptr;     // 1 / beta_j (0 for a column without non-zeros)
+  double* bj = nullptr;     // beta_j of the current beta_mode
   int32_t ib_mode = -1;     // beta_mode that ib was computed for
 
   // streaming propose over all columns
@@ -164,7 +165,7 @@ struct gencd_problem {
   uint32_t* scan_tmp = nullptr;  // scratch of the prefix sum
 
   // accept candidates of (chunk, partition) pairs when partitions are few
-  double* slot_f = nullptr;
+  uint64_t* slot_m = nullptr;
   double* slot_d = nullptr;
   int32_t* slot_j = nullptr;
   int64_t slot_cap = 0;
@@ -217,7 +218,7 @@ int build_propose_plan(gencd_problem* p);
 int launch_propose_plan(gencd_problem* p, const void* u_vec);
 void free_propose_plan(gencd_problem* p);
 int launch_finalize(gencd_problem* p, double lambda, bool write_steps);
-int launch_finalize_accept(gencd_problem* p, int64_t B);  // Thread-Greedy / Greedy
+int launch_finalize_accept(gencd_problem* p, int64_t B, bool want_kkt);  // Thread-Greedy / Greedy
 int ensure_slots(gencd_problem* p, int64_t count);
 // exclusive prefix sum of m uint32 (in place allowed); tmp holds scan_tmp_words(m)
 int exclusive_scan(gencd_problem* p, const uint32_t* in, uint32_t* out, int64_t m, uint32_t* tmp);

@@ -127,27 +127,6 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-template <int NT>
-__device__ __forceinline__ double block_max_nan(double v) {
-  __shared__ double sm[NT / 32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    double x = __shfl_xor_sync(0xffffffffu, v, o);
-    v = (x > v || x != x) ? x : v;
-  }
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) sm[wid] = v;
-  __syncthreads();
-  if (wid == 0) {
-    v = lane < NT / 32 ? sm[lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      double x = __shfl_xor_sync(0xffffffffu, v, o);
-      v = (x > v || x != x) ? x : v;
-    }
-  }
-  return v;
-}
 
 // Per-column part of Propose: Eq. 7 step, Eq. 9 proxy and KKT violation from
 // g_j.  A column with w_j = 0 and |g_j| <= lambda does not move (delta = 0,
@@ -160,54 +139,34 @@ __device__ __forceinline__ bool column_is_idle(double gacc, double wj, uint64_t 
   return wb == 0 && gb <= lam_n_bits;
 }
 
-__device__ __forceinline__ uint64_t lam_n_bits_of(double lam, double n) {
-  return (uint64_t)__double_as_longlong(lam * n);
+
+// Accept candidates.  Only a proxy phi < 0 can be accepted; among negative
+// doubles the order of phi is the reverse of the order of |phi|'s bit pattern,
+// so "lowest phi, then lowest column" becomes "largest magnitude bits, then
+// lowest column" -- integer compares, no FP64 instructions.  mag = 0 means
+// "no candidate" (phi >= 0, -0, or NaN).
+__device__ __forceinline__ uint64_t candidate_mag(double phi) {
+  const uint64_t b = (uint64_t)__double_as_longlong(phi);
+  const uint64_t m = b & 0x7fffffffffffffffull;
+  return ((b >> 63) && m != 0 && m <= 0x7ff0000000000000ull) ? m : 0ull;
 }
 
-__global__ void __launch_bounds__(kThreads)
-    k_finalize(double* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ c,
-               const double* __restrict__ ib, int64_t k, double inv_n, double lam, double beta, int beta_mode,
-               double* __restrict__ delta, double* __restrict__ phi, double* __restrict__ kkt_out,
-               int write_steps) {
-  double vmax = 0.0;
-  const uint64_t lnb = lam_n_bits_of(lam, 1.0 / inv_n);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) {
-    const double ga = gacc[j];
-    gacc[j] = 0.0;
-    const double wj = w[j];
-    double d = 0.0, f = 0.0, v = 0.0;
-    if (!column_is_idle(ga, wj, lnb)) {
-      const double g = ga * inv_n;
-      eq7_step_fast(g, wj, lam, beta_mode ? beta : beta * c[j], ib[j], d, f);
-      v = kkt_violation(g, wj, lam);
-    }
-    if (write_steps) {
-      delta[j] = d;
-      phi[j] = f;
-    }
-    vmax = (v > vmax || v != v) ? v : vmax;
-  }
-  vmax = block_max_nan<kThreads>(vmax);
-  if (threadIdx.x == 0) atomic_max_nonneg(kkt_out, vmax);
+__device__ __forceinline__ bool cand_better(uint64_t ma, int32_t ja, uint64_t mb, int32_t jb) {
+  return ma > mb || (ma == mb && ma != 0 && ja < jb);
 }
 
-// candidate ordering of the accept rules: lower proxy, then lower column
-__device__ __forceinline__ bool better(double fa, int32_t ja, double fb, int32_t jb) {
-  return fa < fb || (fa == fb && ja < jb);
-}
-
-// block argmin of (phi, j) carrying delta; the result is valid in thread 0
-__device__ __forceinline__ void block_argmin(double& f, int32_t& j, double& d) {
-  __shared__ double s_f[kThreads / 32], s_d[kThreads / 32];
+// block reduction of the best candidate (mag, j, delta); valid in thread 0
+__device__ __forceinline__ void block_best(uint64_t& m, int32_t& j, double& d) {
+  __shared__ uint64_t s_m[kThreads / 32];
+  __shared__ double s_d[kThreads / 32];
   __shared__ int32_t s_j[kThreads / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double xf = __shfl_xor_sync(0xffffffffu, f, o);
+    const uint64_t xm = __shfl_xor_sync(0xffffffffu, m, o);
     const int32_t xj = __shfl_xor_sync(0xffffffffu, j, o);
     const double xd = __shfl_xor_sync(0xffffffffu, d, o);
-    if (better(xf, xj, f, j)) {
-      f = xf;
+    if (cand_better(xm, xj, m, j)) {
+      m = xm;
       j = xj;
       d = xd;
     }
@@ -215,18 +174,33 @@ __device__ __forceinline__ void block_argmin(double& f, int32_t& j, double& d) {
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();
   if (lane == 0) {
-    s_f[wid] = f;
+    s_m[wid] = m;
     s_j[wid] = j;
     s_d[wid] = d;
   }
   __syncthreads();
   if (threadIdx.x == 0)
     for (int q = 1; q < kThreads / 32; ++q)
-      if (better(s_f[q], s_j[q], f, j)) {
-        f = s_f[q];
+      if (cand_better(s_m[q], s_j[q], m, j)) {
+        m = s_m[q];
         j = s_j[q];
         d = s_d[q];
       }
+}
+
+// NaN-propagating max of non-negative doubles on their bit patterns
+__device__ __forceinline__ void max_bits(uint64_t& acc, double v) {
+  const uint64_t b = (uint64_t)__double_as_longlong(v);
+  acc = b > acc ? b : acc;
+}
+
+__device__ __forceinline__ void block_max_bits_to(double* out, uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t x = __shfl_xor_sync(0xffffffffu, v, o);
+    v = x > v ? x : v;
+  }
+  if ((threadIdx.x & 31) == 0 && v) atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)v);
 }
 
 // partition of column j: the b with floor(b k / B) <= j < floor((b+1) k / B)
@@ -234,126 +208,158 @@ __device__ __forceinline__ int64_t partition_of(int64_t j, int64_t k, int64_t B)
   return ((j + 1) * B - 1) / k;
 }
 
-// Thread-Greedy with many partitions: one CTA per partition computes the
-// per-column step, proxy and KKT of its columns and accepts the best proxy
-// (Table 2, "greedy per thread"), so delta and phi never reach memory.
+// Eq. 7 step and Eq. 9 proxy of an active column from its raw sum
+__device__ __forceinline__ void active_step(double ga, double inv_n, double wj, double lam, double bj, double ibj,
+                                            double& g, double& d, double& phi) {
+  g = ga * inv_n;
+  eq7_step(g, wj, lam, bj, ibj, d, phi);
+}
+
+// Per-column step, proxy and KKT for every column (the parity hook
+// gencd_propose_all and the convergence checks); same arithmetic as the
+// fused Thread-Greedy kernel.
 __global__ void __launch_bounds__(kThreads)
-    k_finalize_accept(double* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ c,
-                      const double* __restrict__ ib, int64_t k, double inv_n, double lam, double beta, int beta_mode, int64_t B,
-                      int32_t* __restrict__ list_j, double* __restrict__ list_d, double* __restrict__ kkt_out) {
-  double vmax = 0.0;
-  const uint64_t lnb = lam_n_bits_of(lam, 1.0 / inv_n);
+    k_finalize(double* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ bjs,
+               const double* __restrict__ ib, int64_t k, double inv_n, double lam, uint64_t lnb,
+               double* __restrict__ delta, double* __restrict__ phi, double* __restrict__ kkt_out,
+               int write_steps) {
+  uint64_t vmax = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) {
+    const double ga = gacc[j];
+    gacc[j] = 0.0;
+    const double wj = w[j];
+    double d = 0.0, f = 0.0;
+    if (!column_is_idle(ga, wj, lnb)) {
+      double g;
+      active_step(ga, inv_n, wj, lam, bjs[j], ib[j], g, d, f);
+      max_bits(vmax, kkt_violation(g, wj, lam));
+    }
+    if (write_steps) {
+      delta[j] = d;
+      phi[j] = f;
+    }
+  }
+  block_max_bits_to(kkt_out, vmax);
+}
+
+// Thread-Greedy with many partitions: one CTA per partition computes the
+// step and proxy of its columns and accepts the best proxy (Table 2, "greedy
+// per thread"), so delta and phi never reach memory.  want_kkt: also reduce
+// the KKT violation (convergence checks only).
+__global__ void __launch_bounds__(kThreads)
+    k_finalize_accept(double* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ bjs,
+                      const double* __restrict__ ib, int64_t k, double inv_n, double lam, uint64_t lnb,
+                      int64_t B, int want_kkt, int32_t* __restrict__ list_j, double* __restrict__ list_d,
+                      double* __restrict__ kkt_out) {
+  uint64_t vmax = 0;
   for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
     const int64_t lo = b * k / B, hi = (b + 1) * k / B;
-    double bf = DBL_MAX, bd = 0.0;
+    uint64_t bm = 0;
     int32_t bj = INT32_MAX;
+    double bd = 0.0;
     for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
       const double ga = gacc[j];
       gacc[j] = 0.0;
       const double wj = w[j];
       if (column_is_idle(ga, wj, lnb)) continue;  // phi = 0: never accepted
-      const double g = ga * inv_n;
-      double d, f;
-      eq7_step_fast(g, wj, lam, beta_mode ? beta : beta * c[j], ib[j], d, f);
-      const double v = kkt_violation(g, wj, lam);
-      vmax = (v > vmax || v != v) ? v : vmax;
-      if (better(f, (int32_t)j, bf, bj)) {
-        bf = f;
+      double g, d, f;
+      active_step(ga, inv_n, wj, lam, bjs[j], ib[j], g, d, f);
+      if (want_kkt) max_bits(vmax, kkt_violation(g, wj, lam));
+      const uint64_t m = candidate_mag(f);
+      if (cand_better(m, (int32_t)j, bm, bj)) {
+        bm = m;
         bj = (int32_t)j;
         bd = d;
       }
     }
-    block_argmin(bf, bj, bd);
+    block_best(bm, bj, bd);
     if (threadIdx.x == 0) {
-      const bool ok = bj != INT32_MAX && bf < 0.0;
-      list_j[b] = ok ? bj : -1;
-      list_d[b] = ok ? bd : 0.0;
+      list_j[b] = bm ? bj : -1;
+      list_d[b] = bm ? bd : 0.0;
     }
   }
-  vmax = block_max_nan<kThreads>(vmax);
-  if (threadIdx.x == 0) atomic_max_nonneg(kkt_out, vmax);
+  if (want_kkt) block_max_bits_to(kkt_out, vmax);
 }
 
 // Thread-Greedy with few partitions (Greedy: B = 1), stage 1: one CTA per
 // chunk of S <= floor(k / B) columns, which meets at most two partitions;
 // the best candidate of (chunk c, partition b) goes to slot c + b.
 __global__ void __launch_bounds__(kThreads)
-    k_finalize_chunks(double* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ c,
-                      const double* __restrict__ ib, int64_t k, double inv_n, double lam, double beta, int beta_mode, int64_t B, int64_t S,
-                      double* __restrict__ slot_f, int32_t* __restrict__ slot_j, double* __restrict__ slot_d,
-                      double* __restrict__ kkt_out) {
+    k_finalize_chunks(double* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ bjs,
+                      const double* __restrict__ ib, int64_t k, double inv_n, double lam, uint64_t lnb,
+                      int64_t B, int64_t S, int want_kkt, uint64_t* __restrict__ slot_m,
+                      int32_t* __restrict__ slot_j, double* __restrict__ slot_d, double* __restrict__ kkt_out) {
   const int64_t nchunks = (k + S - 1) / S;
-  const uint64_t lnb = lam_n_bits_of(lam, 1.0 / inv_n);
-  double vmax = 0.0;
+  uint64_t vmax = 0;
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const int64_t lo = ch * S, hi = lo + S < k ? lo + S : k;
     const int64_t b0 = partition_of(lo, k, B), b1 = partition_of(hi - 1, k, B);
-    double f0 = DBL_MAX, d0 = 0.0, f1 = DBL_MAX, d1 = 0.0;
+    uint64_t m0 = 0, m1 = 0;
     int32_t j0 = INT32_MAX, j1 = INT32_MAX;
+    double d0 = 0.0, d1 = 0.0;
     for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
       const double ga = gacc[j];
       gacc[j] = 0.0;
       const double wj = w[j];
       if (column_is_idle(ga, wj, lnb)) continue;
-      const double g = ga * inv_n;
-      double d, f;
-      eq7_step_fast(g, wj, lam, beta_mode ? beta : beta * c[j], ib[j], d, f);
-      const double v = kkt_violation(g, wj, lam);
-      vmax = (v > vmax || v != v) ? v : vmax;
+      double g, d, f;
+      active_step(ga, inv_n, wj, lam, bjs[j], ib[j], g, d, f);
+      if (want_kkt) max_bits(vmax, kkt_violation(g, wj, lam));
+      const uint64_t m = candidate_mag(f);
       if (partition_of(j, k, B) == b0) {
-        if (better(f, (int32_t)j, f0, j0)) {
-          f0 = f;
+        if (cand_better(m, (int32_t)j, m0, j0)) {
+          m0 = m;
           j0 = (int32_t)j;
           d0 = d;
         }
-      } else if (better(f, (int32_t)j, f1, j1)) {
-        f1 = f;
+      } else if (cand_better(m, (int32_t)j, m1, j1)) {
+        m1 = m;
         j1 = (int32_t)j;
         d1 = d;
       }
     }
-    block_argmin(f0, j0, d0);
-    block_argmin(f1, j1, d1);
+    block_best(m0, j0, d0);
+    block_best(m1, j1, d1);
     if (threadIdx.x == 0) {
-      slot_f[ch + b0] = f0;
+      slot_m[ch + b0] = m0;
       slot_j[ch + b0] = j0;
       slot_d[ch + b0] = d0;
       if (b1 != b0) {
-        slot_f[ch + b1] = f1;
+        slot_m[ch + b1] = m1;
         slot_j[ch + b1] = j1;
         slot_d[ch + b1] = d1;
       }
     }
     __syncthreads();
   }
-  vmax = block_max_nan<kThreads>(vmax);
-  if (threadIdx.x == 0) atomic_max_nonneg(kkt_out, vmax);
+  if (want_kkt) block_max_bits_to(kkt_out, vmax);
 }
 
 // stage 2: partition b reduces its slots c + b for the chunks c it meets
 __global__ void __launch_bounds__(kThreads)
-    k_accept_slots(const double* __restrict__ slot_f, const int32_t* __restrict__ slot_j,
+    k_accept_slots(const uint64_t* __restrict__ slot_m, const int32_t* __restrict__ slot_j,
                    const double* __restrict__ slot_d, int64_t k, int64_t B, int64_t S,
                    int32_t* __restrict__ list_j, double* __restrict__ list_d) {
   for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
     const int64_t lo = b * k / B, hi = (b + 1) * k / B;
     const int64_t c0 = lo / S, c1 = (hi - 1) / S;
-    double bf = DBL_MAX, bd = 0.0;
+    uint64_t bm = 0;
     int32_t bj = INT32_MAX;
+    double bd = 0.0;
     for (int64_t ch = c0 + threadIdx.x; ch <= c1; ch += blockDim.x) {
-      const double f = slot_f[ch + b];
+      const uint64_t m = slot_m[ch + b];
       const int32_t j = slot_j[ch + b];
-      if (better(f, j, bf, bj)) {
-        bf = f;
+      if (cand_better(m, j, bm, bj)) {
+        bm = m;
         bj = j;
         bd = slot_d[ch + b];
       }
     }
-    block_argmin(bf, bj, bd);
+    block_best(bm, bj, bd);
     if (threadIdx.x == 0) {
-      const bool ok = bj != INT32_MAX && bf < 0.0;
-      list_j[b] = ok ? bj : -1;
-      list_d[b] = ok ? bd : 0.0;
+      list_j[b] = bm ? bj : -1;
+      list_d[b] = bm ? bd : 0.0;
     }
     __syncthreads();
   }
@@ -363,9 +369,8 @@ template <typename V, typename U>
 __global__ void __launch_bounds__(kThreads)
     k_propose_list(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
                    const V* __restrict__ val, const U* __restrict__ u, const double* __restrict__ w,
-                   const double* __restrict__ c, const double* __restrict__ ib, const int32_t* __restrict__ J,
-                   int64_t m, double n,
-                   double lam, double beta, int beta_mode, double* __restrict__ delta,
+                   const double* __restrict__ bjs, const double* __restrict__ ib, const int32_t* __restrict__ J,
+                   int64_t m, double n, double lam, double* __restrict__ delta,
                    double* __restrict__ phi, unsigned long long* __restrict__ counters) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -377,9 +382,8 @@ __global__ void __launch_bounds__(kThreads)
     for (int64_t p = s + lane; p < t; p += 32) acc = fma(val[p], (V)__ldg(u + row_idx[p]), acc);
     const double g = warp_sum((double)acc) / n;
     if (lane == 0) {
-      const double bj = beta_mode ? beta : beta * c[j];
       double d, f;
-      eq7_step_fast(g, w[j], lam, bj, ib[j], d, f);
+      eq7_step(g, w[j], lam, bjs[j], ib[j], d, f);
       delta[e] = d;
       phi[e] = f;
       if (counters) atomicAdd(counters + 1, (unsigned long long)(t - s));
@@ -497,39 +501,37 @@ int launch_col_sumsq(gencd_problem* p) {
 }
 
 int launch_finalize(gencd_problem* p, double lambda, bool write_steps) {
-  const double beta = p->loss == GENCD_LOSS_SQUARED ? 1.0 : 0.25;
   const int grid = grid_for(p->k, kThreads, blocks_per_sm_cap(p, 8));
+  const uint64_t lnb = (uint64_t)__builtin_bit_cast(int64_t, lambda * (double)p->n);
   cudaEvent_t ev = nullptr;
   prof_begin(p, K_FINALIZE, &ev);
-  k_finalize<<<grid, kThreads, 0, p->stream>>>(p->gacc, p->w, p->c, p->ib, p->k, 1.0 / (double)p->n, lambda, beta,
-                                               p->params.beta_mode, p->delta, p->phi, p->dscal + 0,
-                                               write_steps ? 1 : 0);
+  k_finalize<<<grid, kThreads, 0, p->stream>>>(p->gacc, p->w, p->bj, p->ib, p->k, 1.0 / (double)p->n, lambda, lnb,
+                                               p->delta, p->phi, p->dscal + 0, write_steps ? 1 : 0);
   prof_end(p, ev);
   GENCD_CUDA_TRY(cudaGetLastError());
   return GENCD_OK;
 }
 
-int launch_finalize_accept(gencd_problem* p, int64_t B) {
-  const double beta = p->loss == GENCD_LOSS_SQUARED ? 1.0 : 0.25;
+int launch_finalize_accept(gencd_problem* p, int64_t B, bool want_kkt) {
   const double inv_n = 1.0 / (double)p->n;
+  const uint64_t lnb = (uint64_t)__builtin_bit_cast(int64_t, p->lambda * (double)p->n);
   cudaEvent_t ev = nullptr;
   prof_begin(p, K_FINALIZE, &ev);
   if (B >= 2LL * p->num_sms) {
     const int grid = (int)(B < (int64_t)p->num_sms * 16 ? B : (int64_t)p->num_sms * 16);
-    k_finalize_accept<<<grid, kThreads, 0, p->stream>>>(p->gacc, p->w, p->c, p->ib, p->k, inv_n, p->lambda, beta,
-                                                        p->params.beta_mode, B, p->list_j, p->list_d,
-                                                        p->dscal + 0);
+    k_finalize_accept<<<grid, kThreads, 0, p->stream>>>(p->gacc, p->w, p->bj, p->ib, p->k, inv_n, p->lambda, lnb, B,
+                                                        want_kkt ? 1 : 0, p->list_j, p->list_d, p->dscal + 0);
   } else {
     int64_t S = p->k / B;  // >= 1 since B <= k; a chunk meets at most two partitions
     if (S > 4096) S = 4096;
     const int64_t nchunks = (p->k + S - 1) / S;
     GENCD_TRY(ensure_slots(p, nchunks + B));
     const int grid = grid_for(nchunks * kThreads, kThreads, blocks_per_sm_cap(p, 8));
-    k_finalize_chunks<<<grid, kThreads, 0, p->stream>>>(p->gacc, p->w, p->c, p->ib, p->k, inv_n, p->lambda, beta,
-                                                        p->params.beta_mode, B, S, p->slot_f, p->slot_j,
-                                                        p->slot_d, p->dscal + 0);
+    k_finalize_chunks<<<grid, kThreads, 0, p->stream>>>(p->gacc, p->w, p->bj, p->ib, p->k, inv_n, p->lambda, lnb, B,
+                                                        S, want_kkt ? 1 : 0, p->slot_m, p->slot_j, p->slot_d,
+                                                        p->dscal + 0);
     const int g2 = (int)(B < (int64_t)p->num_sms * 16 ? B : (int64_t)p->num_sms * 16);
-    k_accept_slots<<<g2, kThreads, 0, p->stream>>>(p->slot_f, p->slot_j, p->slot_d, p->k, B, S, p->list_j,
+    k_accept_slots<<<g2, kThreads, 0, p->stream>>>(p->slot_m, p->slot_j, p->slot_d, p->k, B, S, p->list_j,
                                                    p->list_d);
     p->prof.launches[K_ACCEPT] += 1;
   }
@@ -541,18 +543,17 @@ int launch_finalize_accept(gencd_problem* p, int64_t B) {
 int launch_propose_list(gencd_problem* p, const int32_t* J, int64_t m, double* delta, double* phi) {
   if (m <= 0) return GENCD_OK;
   unsigned long long* ctr = reinterpret_cast<unsigned long long*>(p->dscal + 4);
-  const double beta = p->loss == GENCD_LOSS_SQUARED ? 1.0 : 0.25;
   const int grid = grid_for(m * 32, kThreads, blocks_per_sm_cap(p, 8));
   cudaEvent_t ev = nullptr;
   prof_begin(p, K_PROPOSE_LIST, &ev);
   if (p->precision == GENCD_F64)
     k_propose_list<double, double><<<grid, kThreads, 0, p->stream>>>(
-        p->col_ptr, p->row_idx, (const double*)p->val, (const double*)p->u, p->w, p->c, p->ib, J, m,
-        (double)p->n, p->lambda, beta, p->params.beta_mode, delta, phi, ctr);
+        p->col_ptr, p->row_idx, (const double*)p->val, (const double*)p->u, p->w, p->bj, p->ib, J, m,
+        (double)p->n, p->lambda, delta, phi, ctr);
   else
     k_propose_list<float, float><<<grid, kThreads, 0, p->stream>>>(
-        p->col_ptr, p->row_idx, (const float*)p->val, (const float*)p->u, p->w, p->c, p->ib, J, m,
-        (double)p->n, p->lambda, beta, p->params.beta_mode, delta, phi, ctr);
+        p->col_ptr, p->row_idx, (const float*)p->val, (const float*)p->u, p->w, p->bj, p->ib, J, m,
+        (double)p->n, p->lambda, delta, phi, ctr);
   prof_end(p, ev);
   GENCD_CUDA_TRY(cudaGetLastError());
   return GENCD_OK;

@@ -134,10 +134,10 @@ template <typename V, typename U>
 __global__ void __launch_bounds__(kThreads)
     k_coloring_iter(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
                     const V* __restrict__ val, U* __restrict__ u, double* __restrict__ w,
-                    const double* __restrict__ c, const double* __restrict__ ib, double* __restrict__ z,
+                    const double* __restrict__ bjs, const double* __restrict__ ib, double* __restrict__ z,
                     const double* __restrict__ y, const int32_t* __restrict__ perm, int64_t q,
                     const int32_t* __restrict__ color_ptr, const int32_t* __restrict__ cols_by_color,
-                    double n, double lam, double beta, int beta_mode, int loss,
+                    double n, double lam, int loss,
                     unsigned long long* __restrict__ counters) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -152,9 +152,8 @@ __global__ void __launch_bounds__(kThreads)
     for (int64_t p = s + lane; p < t; p += 32) acc = fma(val[p], (V)u[row_idx[p]], acc);
     const double g = warp_sum((double)acc) / n;
     const double wj = w[j];
-    const double bj = beta_mode ? beta : beta * c[j];
     double d, f;
-    eq7_step_fast(g, wj, lam, bj, ib[j], d, f);  // identical on every lane
+    eq7_step(g, wj, lam, bjs[j], ib[j], d, f);  // identical on every lane
     work += (unsigned long long)(t - s);
     if (d != 0.0) {
       // every lane has read its u values above (warp_sum synchronised them)
@@ -247,7 +246,6 @@ int launch_refresh_list(gencd_problem* p, const int32_t* J, const double*, int64
 }
 
 int launch_coloring_iter(gencd_problem* p, int64_t q) {
-  const double beta = p->loss == GENCD_LOSS_SQUARED ? 1.0 : 0.25;
   const int64_t warps = p->max_class > 0 ? p->max_class : 1;
   const int grid = grid_for(warps * 32, kThreads, p->num_sms * 8);
   unsigned long long* ctr = reinterpret_cast<unsigned long long*>(p->dscal + 4);
@@ -255,12 +253,12 @@ int launch_coloring_iter(gencd_problem* p, int64_t q) {
   prof_begin(p, K_COLOR_ITER, &ev);
   if (p->precision == GENCD_F64)
     k_coloring_iter<double, double><<<grid, kThreads, 0, p->stream>>>(
-        p->col_ptr, p->row_idx, (const double*)p->val, (double*)p->u, p->w, p->c, p->ib, p->z, p->y, p->perm, q,
-        p->color_ptr, p->cols_by_color, (double)p->n, p->lambda, beta, p->params.beta_mode, p->loss, ctr);
+        p->col_ptr, p->row_idx, (const double*)p->val, (double*)p->u, p->w, p->bj, p->ib, p->z, p->y, p->perm, q,
+        p->color_ptr, p->cols_by_color, (double)p->n, p->lambda, p->loss, ctr);
   else
     k_coloring_iter<float, float><<<grid, kThreads, 0, p->stream>>>(
-        p->col_ptr, p->row_idx, (const float*)p->val, (float*)p->u, p->w, p->c, p->ib, p->z, p->y, p->perm, q,
-        p->color_ptr, p->cols_by_color, (double)p->n, p->lambda, beta, p->params.beta_mode, p->loss, ctr);
+        p->col_ptr, p->row_idx, (const float*)p->val, (float*)p->u, p->w, p->bj, p->ib, p->z, p->y, p->perm, q,
+        p->color_ptr, p->cols_by_color, (double)p->n, p->lambda, p->loss, ctr);
   prof_end(p, ev);
   GENCD_CUDA_TRY(cudaGetLastError());
   return GENCD_OK;
