@@ -322,6 +322,7 @@ static void free_problem(gencd_problem* p) {
                   p->slot_m, p->slot_d, p->slot_j, p->list_off, p->scan_tmp, p->bj};
   if (p->stream) cudaStreamSynchronize(p->stream);
   free_propose_plan(p);
+  if (p->gnat && p->gnat != p->gacc) cudaFree(p->gnat);
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p->hpin) cudaFreeHost(p->hpin);
@@ -353,6 +354,13 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
   GENCD_TRY(dalloc(&p->bj, k));
   GENCD_TRY(dalloc(&p->tile_col, p->ntiles + 1));
   GENCD_TRY(dalloc(&p->gacc, k));
+  if (p->precision == GENCD_F64) {
+    p->gnat = p->gacc;
+  } else {
+    float* gf = nullptr;
+    GENCD_TRY(dalloc(&gf, k));
+    p->gnat = gf;
+  }
   GENCD_TRY(dalloc(&p->delta, k));
   GENCD_TRY(dalloc(&p->phi, k));
   GENCD_TRY(dalloc(&p->list_j, k));
@@ -406,6 +414,7 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
   GENCD_CUDA_TRY(cudaMemsetAsync(p->z, 0, sizeof(double) * n, st));
   GENCD_CUDA_TRY(cudaMemsetAsync(p->w, 0, sizeof(double) * k, st));
   GENCD_CUDA_TRY(cudaMemsetAsync(p->gacc, 0, sizeof(double) * k, st));
+  if (p->gnat != p->gacc) GENCD_CUDA_TRY(cudaMemsetAsync(p->gnat, 0, sizeof(float) * k, st));
   GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal, 0, 8 * sizeof(double), st));
   GENCD_TRY(launch_tile_map(p));
   GENCD_TRY(launch_col_scale(p));

@@ -109,7 +109,7 @@ struct ProposePlan {
   uint32_t* pair_start = nullptr;  // first entry of each pair; [npairs] = entries
   uint32_t* pair_slot = nullptr;   // partial slot of each pair (column-major)
   uint32_t* hslot_ptr = nullptr;   // first slot of heavy column h; [nheavy] = npairs
-  double* partial = nullptr;       // one partial sum per pair, zero between launches
+  void* partial = nullptr;         // one partial sum per pair (storage precision), zero between launches
   uint32_t* tile_start = nullptr;  // tiles of 32*ITEMS entries inside one slab
   uint32_t* tile_end = nullptr;
   uint32_t* tile_pair = nullptr;   // pairs holding the tile's first and last entry
@@ -154,7 +154,8 @@ struct gencd_problem {
   int items = 4;
   int64_t ntiles = 0;
   int32_t* tile_col = nullptr;
-  double* gacc = nullptr;
+  double* gacc = nullptr;   // FP64 sums (setup passes, power iteration)
+  void* gnat = nullptr;     // sums of the hot path in the storage precision (== gacc in FP64 mode)
   double* delta = nullptr;
   double* phi = nullptr;
 

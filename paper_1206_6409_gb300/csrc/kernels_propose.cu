@@ -58,21 +58,23 @@ __device__ __forceinline__ void load_val(const float* __restrict__ p, float (&v)
   }
 }
 
-__device__ __forceinline__ void emit_partial(double* __restrict__ gacc, int32_t c, double s,
-                                             bool whole) {
+template <typename G>
+__device__ __forceinline__ void emit_partial(G* __restrict__ gacc, int32_t c, G s, bool whole) {
   if (whole)
     gacc[c] = s;  // the only writer of this column
   else
     atomicAdd(gacc + c, s);
 }
 
-// SQ: sum X_ij^2 instead of X_ij u_i (the column scales c_j, at setup)
-template <typename V, typename U, int ITEMS, bool SQ = false>
+// SQ: sum X_ij^2 instead of X_ij u_i (the column scales c_j, at setup).
+// G: type of the sums in gacc (float in FP32 mode, so that no FP64 unit work
+// or conversion is on this path; double otherwise).
+template <typename V, typename U, int ITEMS, typename G, bool SQ = false>
 __global__ void __launch_bounds__(kThreads)
     k_propose_all(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
                   const V* __restrict__ val, const U* __restrict__ u,
                   const int32_t* __restrict__ tile_col, int64_t nnz, int64_t ntiles,
-                  const int32_t* __restrict__ cmap, double* __restrict__ gacc) {
+                  const int32_t* __restrict__ cmap, G* __restrict__ gacc) {
   constexpr int TILE = 32 * ITEMS;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -114,7 +116,7 @@ __global__ void __launch_bounds__(kThreads)
       if (i < nvalid) {
         const int64_t p = a + i;
         while (p >= cend) {  // column c ended before p (c + 1 <= k - 1 since p < nnz)
-          emit_partial(gacc, cmap ? cmap[c] : c, (double)acc, whole);
+          emit_partial<G>(gacc, cmap ? cmap[c] : c, (G)acc, whole);
           ++c;
           cend = __ldg(col_ptr + c + 1);
           acc = V(0);
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(kThreads)
         acc = fma(v[i], (V)uu[i], acc);
       }
     }
-    emit_partial(gacc, cmap ? cmap[c] : c, (double)acc, whole && cend <= b);
+    emit_partial<G>(gacc, cmap ? cmap[c] : c, (G)acc, whole && cend <= b);
   }
 }
 
@@ -215,29 +217,67 @@ __device__ __forceinline__ void active_step(double ga, double inv_n, double wj, 
   eq7_step(g, wj, lam, bj, ibj, d, phi);
 }
 
+// A column with w_j = 0 whose raw sum satisfies |gacc_j| <= lambda n does not
+// move; tested on bit patterns (both sides non-negative), no FP64 unit work.
+__device__ __forceinline__ bool idle_raw(double ga, double wj, uint64_t lnb64, uint32_t) {
+  return column_is_idle(ga, wj, lnb64);
+}
+__device__ __forceinline__ bool idle_raw(float ga, double wj, uint64_t, uint32_t lnb32) {
+  const uint64_t wb = (uint64_t)__double_as_longlong(wj) << 1;
+  return wb == 0 && ((uint32_t)__float_as_int(ga) & 0x7fffffffu) <= lnb32;
+}
+
+constexpr int kColsPerThread = 4;
+
 // Per-column step, proxy and KKT for every column (the parity hook
 // gencd_propose_all and the convergence checks); same arithmetic as the
-// fused Thread-Greedy kernel.
+// fused Thread-Greedy kernel.  Each thread takes 4 columns per round (their
+// loads in flight together); a warp with no active column skips the math.
+template <typename G>
 __global__ void __launch_bounds__(kThreads)
-    k_finalize(double* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ bjs,
-               const double* __restrict__ ib, int64_t k, double inv_n, double lam, uint64_t lnb,
+    k_finalize(G* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ bjs,
+               const double* __restrict__ ib, int64_t k, double inv_n, double lam, uint64_t lnb64, uint32_t lnb32,
                double* __restrict__ delta, double* __restrict__ phi, double* __restrict__ kkt_out,
                int write_steps) {
   uint64_t vmax = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) {
-    const double ga = gacc[j];
-    gacc[j] = 0.0;
-    const double wj = w[j];
-    double d = 0.0, f = 0.0;
-    if (!column_is_idle(ga, wj, lnb)) {
-      double g;
-      active_step(ga, inv_n, wj, lam, bjs[j], ib[j], g, d, f);
-      max_bits(vmax, kkt_violation(g, wj, lam));
+  const int64_t rounds = (k + kColsPerThread * stride - 1) / (kColsPerThread * stride);
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t it = 0; it < rounds; ++it) {  // warp-uniform trip count
+    G ga[kColsPerThread];
+    double wv[kColsPerThread];
+    bool act[kColsPerThread];
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < kColsPerThread; ++q) {
+      const int64_t j = t0 + (it * kColsPerThread + q) * stride;
+      ga[q] = j < k ? gacc[j] : G(0);
+      wv[q] = j < k ? w[j] : 0.0;
     }
-    if (write_steps) {
-      delta[j] = d;
-      phi[j] = f;
+#pragma unroll
+    for (int q = 0; q < kColsPerThread; ++q) {
+      const int64_t j = t0 + (it * kColsPerThread + q) * stride;
+      if (j < k) gacc[j] = G(0);
+      act[q] = j < k && !idle_raw(ga[q], wv[q], lnb64, lnb32);
+      any |= act[q];
+      if (write_steps && j < k && !act[q]) {
+        delta[j] = 0.0;
+        phi[j] = 0.0;
+      }
+    }
+    if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+      for (int q = 0; q < kColsPerThread; ++q) {
+        if (!act[q]) continue;
+        const int64_t j = t0 + (it * kColsPerThread + q) * stride;
+        double g, d, f;
+        active_step((double)ga[q], inv_n, wv[q], lam, bjs[j], ib[j], g, d, f);
+        max_bits(vmax, kkt_violation(g, wv[q], lam));
+        if (write_steps) {
+          delta[j] = d;
+          phi[j] = f;
+        }
+      }
     }
   }
   block_max_bits_to(kkt_out, vmax);
@@ -247,30 +287,53 @@ __global__ void __launch_bounds__(kThreads)
 // step and proxy of its columns and accepts the best proxy (Table 2, "greedy
 // per thread"), so delta and phi never reach memory.  want_kkt: also reduce
 // the KKT violation (convergence checks only).
+template <typename G>
 __global__ void __launch_bounds__(kThreads)
-    k_finalize_accept(double* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ bjs,
-                      const double* __restrict__ ib, int64_t k, double inv_n, double lam, uint64_t lnb,
-                      int64_t B, int want_kkt, int32_t* __restrict__ list_j, double* __restrict__ list_d,
-                      double* __restrict__ kkt_out) {
+    k_finalize_accept(G* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ bjs,
+                      const double* __restrict__ ib, int64_t k, double inv_n, double lam, uint64_t lnb64,
+                      uint32_t lnb32, int64_t B, int want_kkt, int32_t* __restrict__ list_j,
+                      double* __restrict__ list_d, double* __restrict__ kkt_out) {
   uint64_t vmax = 0;
   for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
     const int64_t lo = b * k / B, hi = (b + 1) * k / B;
+    const int64_t span = (int64_t)kColsPerThread * blockDim.x;
+    const int64_t rounds = (hi - lo + span - 1) / span;
     uint64_t bm = 0;
     int32_t bj = INT32_MAX;
     double bd = 0.0;
-    for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
-      const double ga = gacc[j];
-      gacc[j] = 0.0;
-      const double wj = w[j];
-      if (column_is_idle(ga, wj, lnb)) continue;  // phi = 0: never accepted
-      double g, d, f;
-      active_step(ga, inv_n, wj, lam, bjs[j], ib[j], g, d, f);
-      if (want_kkt) max_bits(vmax, kkt_violation(g, wj, lam));
-      const uint64_t m = candidate_mag(f);
-      if (cand_better(m, (int32_t)j, bm, bj)) {
-        bm = m;
-        bj = (int32_t)j;
-        bd = d;
+    for (int64_t it = 0; it < rounds; ++it) {  // uniform across the CTA
+      G ga[kColsPerThread];
+      double wv[kColsPerThread];
+      bool act[kColsPerThread];
+      bool any = false;
+#pragma unroll
+      for (int q = 0; q < kColsPerThread; ++q) {
+        const int64_t j = lo + it * span + q * blockDim.x + threadIdx.x;
+        ga[q] = j < hi ? gacc[j] : G(0);
+        wv[q] = j < hi ? w[j] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < kColsPerThread; ++q) {
+        const int64_t j = lo + it * span + q * blockDim.x + threadIdx.x;
+        if (j < hi) gacc[j] = G(0);
+        act[q] = j < hi && !idle_raw(ga[q], wv[q], lnb64, lnb32);  // idle: phi = 0, never accepted
+        any |= act[q];
+      }
+      if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+        for (int q = 0; q < kColsPerThread; ++q) {
+          if (!act[q]) continue;
+          const int64_t j = lo + it * span + q * blockDim.x + threadIdx.x;
+          double g, d, f;
+          active_step((double)ga[q], inv_n, wv[q], lam, bjs[j], ib[j], g, d, f);
+          if (want_kkt) max_bits(vmax, kkt_violation(g, wv[q], lam));
+          const uint64_t m = candidate_mag(f);
+          if (cand_better(m, (int32_t)j, bm, bj)) {
+            bm = m;
+            bj = (int32_t)j;
+            bd = d;
+          }
+        }
       }
     }
     block_best(bm, bj, bd);
@@ -285,9 +348,11 @@ __global__ void __launch_bounds__(kThreads)
 // Thread-Greedy with few partitions (Greedy: B = 1), stage 1: one CTA per
 // chunk of S <= floor(k / B) columns, which meets at most two partitions;
 // the best candidate of (chunk c, partition b) goes to slot c + b.
+template <typename G>
 __global__ void __launch_bounds__(kThreads)
-    k_finalize_chunks(double* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ bjs,
-                      const double* __restrict__ ib, int64_t k, double inv_n, double lam, uint64_t lnb,
+    k_finalize_chunks(G* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ bjs,
+                      const double* __restrict__ ib, int64_t k, double inv_n, double lam, uint64_t lnb64,
+                      uint32_t lnb32,
                       int64_t B, int64_t S, int want_kkt, uint64_t* __restrict__ slot_m,
                       int32_t* __restrict__ slot_j, double* __restrict__ slot_d, double* __restrict__ kkt_out) {
   const int64_t nchunks = (k + S - 1) / S;
@@ -299,12 +364,12 @@ __global__ void __launch_bounds__(kThreads)
     int32_t j0 = INT32_MAX, j1 = INT32_MAX;
     double d0 = 0.0, d1 = 0.0;
     for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
-      const double ga = gacc[j];
-      gacc[j] = 0.0;
+      const G ga = gacc[j];
+      gacc[j] = G(0);
       const double wj = w[j];
-      if (column_is_idle(ga, wj, lnb)) continue;
+      if (idle_raw(ga, wj, lnb64, lnb32)) continue;
       double g, d, f;
-      active_step(ga, inv_n, wj, lam, bjs[j], ib[j], g, d, f);
+      active_step((double)ga, inv_n, wj, lam, bjs[j], ib[j], g, d, f);
       if (want_kkt) max_bits(vmax, kkt_violation(g, wj, lam));
       const uint64_t m = candidate_mag(f);
       if (partition_of(j, k, B) == b0) {
@@ -446,30 +511,33 @@ __global__ void k_objective_final(const double* __restrict__ red, int nblocks, d
 static int blocks_per_sm_cap(gencd_problem* p, int per_sm) { return p->num_sms * per_sm; }
 
 // Lane-segmented streaming pass over a CSC (the whole X, or the compact copy
-// of the light columns with its column map): gacc[col] += X_col^T u.
+// of the light columns with its column map): out[col] += X_col^T u.  With u
+// in the storage precision the sums go to the native accumulator (float in
+// FP32 mode), otherwise (power iteration in FP32 mode) to the FP64 gacc.
 int launch_propose_csc(gencd_problem* p, const CscView& a, const void* u_vec, bool u_is_double) {
   if (a.ntiles == 0) return GENCD_OK;
   const int grid = grid_for(a.ntiles * 32, kThreads, blocks_per_sm_cap(p, 8));
   if (p->precision == GENCD_F64) {
-    k_propose_all<double, double, kItemsF64><<<grid, kThreads, 0, p->stream>>>(
+    k_propose_all<double, double, kItemsF64, double><<<grid, kThreads, 0, p->stream>>>(
         a.col_ptr, a.row_idx, (const double*)a.val, (const double*)u_vec, a.tile_col, a.nnz, a.ntiles, a.cmap,
         p->gacc);
   } else if (u_is_double) {
-    k_propose_all<float, double, kItemsF32><<<grid, kThreads, 0, p->stream>>>(
+    k_propose_all<float, double, kItemsF32, double><<<grid, kThreads, 0, p->stream>>>(
         a.col_ptr, a.row_idx, (const float*)a.val, (const double*)u_vec, a.tile_col, a.nnz, a.ntiles, a.cmap,
         p->gacc);
   } else {
-    k_propose_all<float, float, kItemsF32><<<grid, kThreads, 0, p->stream>>>(
+    k_propose_all<float, float, kItemsF32, float><<<grid, kThreads, 0, p->stream>>>(
         a.col_ptr, a.row_idx, (const float*)a.val, (const float*)u_vec, a.tile_col, a.nnz, a.ntiles, a.cmap,
-        p->gacc);
+        (float*)p->gnat);
   }
   GENCD_CUDA_TRY(cudaGetLastError());
   return GENCD_OK;
 }
 
-// gacc_j = X_j^T u for every column: the row-slab plan (heavy columns, u from
-// shared memory) plus the light columns, or the plain CSC pass when u is not
-// in the storage precision (power iteration) or no plan was built.
+// native accumulator <- X^T u for every column: the row-slab plan (heavy
+// columns, u from shared memory) plus the light columns, or the plain CSC
+// pass when no plan was built.  Non-native u (power iteration in FP32 mode)
+// always takes the plain pass into the FP64 gacc.
 int launch_propose_all(gencd_problem* p, const void* u_vec, bool u_is_double) {
   cudaEvent_t ev = nullptr;
   prof_begin(p, K_PROPOSE_ALL, &ev);
@@ -488,11 +556,11 @@ int launch_col_sumsq(gencd_problem* p) {
   if (p->ntiles == 0) return GENCD_OK;
   const int grid = grid_for(p->ntiles * 32, kThreads, blocks_per_sm_cap(p, 8));
   if (p->precision == GENCD_F64)
-    k_propose_all<double, double, kItemsF64, true><<<grid, kThreads, 0, p->stream>>>(
+    k_propose_all<double, double, kItemsF64, double, true><<<grid, kThreads, 0, p->stream>>>(
         p->col_ptr, p->row_idx, (const double*)p->val, nullptr, p->tile_col, p->nnz, p->ntiles, nullptr,
         p->gacc);
   else
-    k_propose_all<float, double, kItemsF32, true><<<grid, kThreads, 0, p->stream>>>(
+    k_propose_all<float, double, kItemsF32, double, true><<<grid, kThreads, 0, p->stream>>>(
         p->col_ptr, p->row_idx, (const float*)p->val, nullptr, p->tile_col, p->nnz, p->ntiles, nullptr,
         p->gacc);
   p->prof.launches[K_SETUP] += 1;
@@ -500,13 +568,26 @@ int launch_col_sumsq(gencd_problem* p) {
   return GENCD_OK;
 }
 
+static void lambda_bits(gencd_problem* p, double lambda, uint64_t* b64, uint32_t* b32) {
+  const double ln = lambda * (double)p->n;
+  *b64 = (uint64_t)__builtin_bit_cast(int64_t, ln);
+  *b32 = (uint32_t)__builtin_bit_cast(int32_t, (float)ln);
+}
+
 int launch_finalize(gencd_problem* p, double lambda, bool write_steps) {
   const int grid = grid_for(p->k, kThreads, blocks_per_sm_cap(p, 8));
-  const uint64_t lnb = (uint64_t)__builtin_bit_cast(int64_t, lambda * (double)p->n);
+  uint64_t b64;
+  uint32_t b32;
+  lambda_bits(p, lambda, &b64, &b32);
+  const double inv_n = 1.0 / (double)p->n;
   cudaEvent_t ev = nullptr;
   prof_begin(p, K_FINALIZE, &ev);
-  k_finalize<<<grid, kThreads, 0, p->stream>>>(p->gacc, p->w, p->bj, p->ib, p->k, 1.0 / (double)p->n, lambda, lnb,
-                                               p->delta, p->phi, p->dscal + 0, write_steps ? 1 : 0);
+  if (p->precision == GENCD_F64)
+    k_finalize<double><<<grid, kThreads, 0, p->stream>>>((double*)p->gnat, p->w, p->bj, p->ib, p->k, inv_n, lambda,
+                                                         b64, b32, p->delta, p->phi, p->dscal + 0, write_steps ? 1 : 0);
+  else
+    k_finalize<float><<<grid, kThreads, 0, p->stream>>>((float*)p->gnat, p->w, p->bj, p->ib, p->k, inv_n, lambda,
+                                                        b64, b32, p->delta, p->phi, p->dscal + 0, write_steps ? 1 : 0);
   prof_end(p, ev);
   GENCD_CUDA_TRY(cudaGetLastError());
   return GENCD_OK;
@@ -514,22 +595,36 @@ int launch_finalize(gencd_problem* p, double lambda, bool write_steps) {
 
 int launch_finalize_accept(gencd_problem* p, int64_t B, bool want_kkt) {
   const double inv_n = 1.0 / (double)p->n;
-  const uint64_t lnb = (uint64_t)__builtin_bit_cast(int64_t, p->lambda * (double)p->n);
+  uint64_t b64;
+  uint32_t b32;
+  lambda_bits(p, p->lambda, &b64, &b32);
+  const bool f64 = p->precision == GENCD_F64;
   cudaEvent_t ev = nullptr;
   prof_begin(p, K_FINALIZE, &ev);
   if (B >= 2LL * p->num_sms) {
     const int grid = (int)(B < (int64_t)p->num_sms * 16 ? B : (int64_t)p->num_sms * 16);
-    k_finalize_accept<<<grid, kThreads, 0, p->stream>>>(p->gacc, p->w, p->bj, p->ib, p->k, inv_n, p->lambda, lnb, B,
-                                                        want_kkt ? 1 : 0, p->list_j, p->list_d, p->dscal + 0);
+    if (f64)
+      k_finalize_accept<double><<<grid, kThreads, 0, p->stream>>>((double*)p->gnat, p->w, p->bj, p->ib, p->k, inv_n,
+                                                                  p->lambda, b64, b32, B, want_kkt ? 1 : 0, p->list_j,
+                                                                  p->list_d, p->dscal + 0);
+    else
+      k_finalize_accept<float><<<grid, kThreads, 0, p->stream>>>((float*)p->gnat, p->w, p->bj, p->ib, p->k, inv_n,
+                                                                 p->lambda, b64, b32, B, want_kkt ? 1 : 0, p->list_j,
+                                                                 p->list_d, p->dscal + 0);
   } else {
     int64_t S = p->k / B;  // >= 1 since B <= k; a chunk meets at most two partitions
     if (S > 4096) S = 4096;
     const int64_t nchunks = (p->k + S - 1) / S;
     GENCD_TRY(ensure_slots(p, nchunks + B));
     const int grid = grid_for(nchunks * kThreads, kThreads, blocks_per_sm_cap(p, 8));
-    k_finalize_chunks<<<grid, kThreads, 0, p->stream>>>(p->gacc, p->w, p->bj, p->ib, p->k, inv_n, p->lambda, lnb, B,
-                                                        S, want_kkt ? 1 : 0, p->slot_m, p->slot_j, p->slot_d,
-                                                        p->dscal + 0);
+    if (f64)
+      k_finalize_chunks<double><<<grid, kThreads, 0, p->stream>>>((double*)p->gnat, p->w, p->bj, p->ib, p->k, inv_n,
+                                                                  p->lambda, b64, b32, B, S, want_kkt ? 1 : 0,
+                                                                  p->slot_m, p->slot_j, p->slot_d, p->dscal + 0);
+    else
+      k_finalize_chunks<float><<<grid, kThreads, 0, p->stream>>>((float*)p->gnat, p->w, p->bj, p->ib, p->k, inv_n,
+                                                                 p->lambda, b64, b32, B, S, want_kkt ? 1 : 0,
+                                                                 p->slot_m, p->slot_j, p->slot_d, p->dscal + 0);
     const int g2 = (int)(B < (int64_t)p->num_sms * 16 ? B : (int64_t)p->num_sms * 16);
     k_accept_slots<<<g2, kThreads, 0, p->stream>>>(p->slot_m, p->slot_j, p->slot_d, p->k, B, S, p->list_j,
                                                    p->list_d);

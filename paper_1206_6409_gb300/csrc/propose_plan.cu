@@ -15,7 +15,9 @@
 // Within a slab the kernel works like the CSC pass: a warp owns a tile of
 // 256 consecutive entries, a lane 8 of them (128-bit loads of rows and
 // values), a lane sums its entries pair by pair in registers and emits each
-// partial with a store (pair inside the lane) or an FP64 atomic add.
+// partial with a store (pair inside the lane) or an atomic add; a full tile
+// inside one pair is reduced by the warp first.  Partial sums are kept in the
+// storage precision (FP32 atomics in FP32 mode).
 #include <algorithm>
 #include <vector>
 
@@ -52,7 +54,8 @@ __device__ __forceinline__ void load8<double>(const double* __restrict__ p, doub
   }
 }
 
-__device__ __forceinline__ void emit_pair(double* __restrict__ partial, uint32_t slot, double s, bool whole) {
+template <typename G>
+__device__ __forceinline__ void emit_pair(G* __restrict__ partial, uint32_t slot, G s, bool whole) {
   if (whole)
     partial[slot] = s;
   else
@@ -73,7 +76,7 @@ __device__ __forceinline__ void load_lane(const uint16_t* __restrict__ s_row, co
   load8<V>(s_val + a, L.v);
 }
 
-template <typename V, typename U>
+template <typename V, typename U, typename G>
 __global__ void __launch_bounds__(kSlabThreads, 1)
     k_propose_slabs(const uint16_t* __restrict__ s_row, const V* __restrict__ s_val,
                     const uint32_t* __restrict__ pair_start, const uint32_t* __restrict__ pair_slot,
@@ -81,7 +84,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
                     const uint32_t* __restrict__ tile_pair, const uint32_t* __restrict__ tile_pair_last,
                     const int32_t* __restrict__ tile_slab, const int32_t* __restrict__ slab_tile_begin,
                     const int32_t* __restrict__ cta_tile_begin, const U* __restrict__ u, int64_t n,
-                    int32_t slab_rows, double* __restrict__ partial) {
+                    int32_t slab_rows, G* __restrict__ partial) {
   // FP32 tiles are small enough to keep the next tile's loads in flight
   constexpr bool kPrefetch = sizeof(V) == 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -146,7 +149,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
         for (int i = 0; i < kSlabItems; ++i) {
           const uint32_t p = a + i;
           while (p >= cend) {
-            emit_pair(partial, __ldg(pair_slot + q), (double)acc, whole);
+            emit_pair<G>(partial, __ldg(pair_slot + q), (G)acc, whole);
             ++q;
             cend = __ldg(pair_start + q + 1);
             acc = V(0);
@@ -162,25 +165,26 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
         const V sum = warp_sum(acc);
         if (lane == 0) {
           const bool in_tile = __ldg(pair_start + qf) >= ts && __ldg(pair_start + qf + 1) <= te;
-          emit_pair(partial, __ldg(pair_slot + qf), (double)sum, in_tile);
+          emit_pair<G>(partial, __ldg(pair_slot + qf), (G)sum, in_tile);
         }
       } else if (active) {
-        emit_pair(partial, __ldg(pair_slot + q), (double)acc, whole && cend <= a + kSlabItems);
+        emit_pair<G>(partial, __ldg(pair_slot + q), (G)acc, whole && cend <= a + kSlabItems);
       }
     }
     t0 = t1;
   }
 }
 
-// gacc of each heavy column = its partials in slab order; partials reset
+// sum of each heavy column = its partials in slab order; partials reset
+template <typename G>
 __global__ void k_pairs_to_gacc(const uint32_t* __restrict__ hslot_ptr, const int32_t* __restrict__ heavy_cols,
-                                int64_t nheavy, double* __restrict__ partial, double* __restrict__ gacc) {
+                                int64_t nheavy, G* __restrict__ partial, G* __restrict__ gacc) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nheavy; h += stride) {
-    double s = 0.0;
+    G s = G(0);
     for (uint32_t q = hslot_ptr[h]; q < hslot_ptr[h + 1]; ++q) {
       s += partial[q];
-      partial[q] = 0.0;
+      partial[q] = G(0);
     }
     gacc[heavy_cols[h]] = s;
   }
@@ -195,19 +199,22 @@ int launch_propose_plan(gencd_problem* p, const void* u_vec) {
   }
   if (P.nheavy > 0) {
     const size_t smem = (size_t)P.slab_rows * (p->precision == GENCD_F64 ? 8 : 4);
-    if (p->precision == GENCD_F64)
-      k_propose_slabs<double, double><<<P.grid, kSlabThreads, smem, p->stream>>>(
+    const int g2 = grid_for(P.nheavy, kThreads, p->num_sms * 8);
+    if (p->precision == GENCD_F64) {
+      k_propose_slabs<double, double, double><<<P.grid, kSlabThreads, smem, p->stream>>>(
           P.s_row, (const double*)P.s_val, P.pair_start, P.pair_slot, P.tile_start, P.tile_end, P.tile_pair,
           P.tile_pair_last, P.tile_slab, P.slab_tile_begin, P.cta_tile_begin, (const double*)u_vec, p->n,
-          P.slab_rows, P.partial);
-    else
-      k_propose_slabs<float, float><<<P.grid, kSlabThreads, smem, p->stream>>>(
+          P.slab_rows, (double*)P.partial);
+      k_pairs_to_gacc<double><<<g2, kThreads, 0, p->stream>>>(P.hslot_ptr, P.heavy_cols, P.nheavy,
+                                                               (double*)P.partial, (double*)p->gnat);
+    } else {
+      k_propose_slabs<float, float, float><<<P.grid, kSlabThreads, smem, p->stream>>>(
           P.s_row, (const float*)P.s_val, P.pair_start, P.pair_slot, P.tile_start, P.tile_end, P.tile_pair,
           P.tile_pair_last, P.tile_slab, P.slab_tile_begin, P.cta_tile_begin, (const float*)u_vec, p->n,
-          P.slab_rows, P.partial);
-    GENCD_CUDA_TRY(cudaGetLastError());
-    k_pairs_to_gacc<<<grid_for(P.nheavy, kThreads, p->num_sms * 8), kThreads, 0, p->stream>>>(
-        P.hslot_ptr, P.heavy_cols, P.nheavy, P.partial, p->gacc);
+          P.slab_rows, (float*)P.partial);
+      k_pairs_to_gacc<float><<<g2, kThreads, 0, p->stream>>>(P.hslot_ptr, P.heavy_cols, P.nheavy,
+                                                              (float*)P.partial, (float*)p->gnat);
+    }
     p->prof.launches[K_PROPOSE_ALL] += 1;
     GENCD_CUDA_TRY(cudaGetLastError());
   }
@@ -565,8 +572,8 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   const uint32_t* q_sorted = q_alt ? qb : qa;
   GENCD_TRY(palloc(&P.pair_slot, P.npairs));
   GENCD_TRY(palloc(&P.hslot_ptr, P.nheavy + 1));
-  GENCD_TRY(palloc(&P.partial, P.npairs));
-  GENCD_CUDA_TRY(cudaMemsetAsync(P.partial, 0, 8 * (size_t)P.npairs, st));
+  GENCD_TRY(palloc((char**)&P.partial, P.npairs * (int64_t)vsz));
+  GENCD_CUDA_TRY(cudaMemsetAsync(P.partial, 0, vsz * (size_t)P.npairs, st));
   k_plan_slots<<<grid_for(P.npairs, kThreads, g), kThreads, 0, st>>>(q_sorted, P.npairs, P.pair_slot);
   k_plan_lower_bounds<<<grid_for(P.nheavy + 1, kThreads, g), kThreads, 0, st>>>(h_sorted, P.npairs, P.nheavy,
                                                                                  P.hslot_ptr);
@@ -596,10 +603,10 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   GENCD_CUDA_TRY(cudaMemcpyAsync(P.cta_tile_begin, ctb.data(), 4 * (P.grid + 1), cudaMemcpyHostToDevice, st));
   const int smem = (int)((size_t)P.slab_rows * (f64 ? 8 : 4));
   if (f64)
-    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_slabs<double, double>,
+    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_slabs<double, double, double>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   else
-    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_slabs<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_slabs<float, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         smem));
   GENCD_CUDA_TRY(cudaStreamSynchronize(st));  // scratch is freed on return
   p->prof.launches[K_SETUP] += 10;
