@@ -228,57 +228,73 @@ __device__ __forceinline__ bool idle_raw(float ga, double wj, uint64_t, uint32_t
 }
 
 constexpr int kColsPerThread = 4;
+constexpr int kRoundCols = kColsPerThread * kThreads;  // columns a CTA scans per round
+
+// One round of the per-column pass: every thread loads 4 columns (loads in
+// flight together), zeroes their sums, tests them with integer compares, and
+// queues the active ones in shared memory; after a barrier the queue is
+// processed packed (one active column per thread), so FP64 work is
+// proportional to the number of active columns, not to the warps that hold
+// one.  Returns the queue length; the queue holds (j, raw sum, w_j).
+template <typename G>
+__device__ __forceinline__ int scan_round(G* __restrict__ gacc, const double* __restrict__ w, int64_t base,
+                                          int64_t hi, uint64_t lnb64, uint32_t lnb32, int* s_n, int64_t* s_j,
+                                          double* s_g, double* s_w, double* delta, double* phi) {
+  G ga[kColsPerThread];
+  double wv[kColsPerThread];
+#pragma unroll
+  for (int q = 0; q < kColsPerThread; ++q) {
+    const int64_t j = base + q * kThreads + threadIdx.x;
+    ga[q] = j < hi ? gacc[j] : G(0);
+    wv[q] = j < hi ? w[j] : 0.0;
+  }
+#pragma unroll
+  for (int q = 0; q < kColsPerThread; ++q) {
+    const int64_t j = base + q * kThreads + threadIdx.x;
+    if (j >= hi) continue;
+    gacc[j] = G(0);
+    if (!idle_raw(ga[q], wv[q], lnb64, lnb32)) {
+      const int slot = atomicAdd(s_n, 1);
+      s_j[slot] = j;
+      s_g[slot] = (double)ga[q];
+      s_w[slot] = wv[q];
+    } else if (delta) {
+      delta[j] = 0.0;
+      phi[j] = 0.0;
+    }
+  }
+  __syncthreads();
+  return *s_n;
+}
 
 // Per-column step, proxy and KKT for every column (the parity hook
 // gencd_propose_all and the convergence checks); same arithmetic as the
-// fused Thread-Greedy kernel.  Each thread takes 4 columns per round (their
-// loads in flight together); a warp with no active column skips the math.
+// fused Thread-Greedy kernel.
 template <typename G>
 __global__ void __launch_bounds__(kThreads)
     k_finalize(G* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ bjs,
                const double* __restrict__ ib, int64_t k, double inv_n, double lam, uint64_t lnb64, uint32_t lnb32,
                double* __restrict__ delta, double* __restrict__ phi, double* __restrict__ kkt_out,
                int write_steps) {
+  __shared__ int s_n;
+  __shared__ int64_t s_j[kRoundCols];
+  __shared__ double s_g[kRoundCols], s_w[kRoundCols];
   uint64_t vmax = 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t rounds = (k + kColsPerThread * stride - 1) / (kColsPerThread * stride);
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (int64_t it = 0; it < rounds; ++it) {  // warp-uniform trip count
-    G ga[kColsPerThread];
-    double wv[kColsPerThread];
-    bool act[kColsPerThread];
-    bool any = false;
-#pragma unroll
-    for (int q = 0; q < kColsPerThread; ++q) {
-      const int64_t j = t0 + (it * kColsPerThread + q) * stride;
-      ga[q] = j < k ? gacc[j] : G(0);
-      wv[q] = j < k ? w[j] : 0.0;
-    }
-#pragma unroll
-    for (int q = 0; q < kColsPerThread; ++q) {
-      const int64_t j = t0 + (it * kColsPerThread + q) * stride;
-      if (j < k) gacc[j] = G(0);
-      act[q] = j < k && !idle_raw(ga[q], wv[q], lnb64, lnb32);
-      any |= act[q];
-      if (write_steps && j < k && !act[q]) {
-        delta[j] = 0.0;
-        phi[j] = 0.0;
+  for (int64_t base = (int64_t)blockIdx.x * kRoundCols; base < k; base += (int64_t)gridDim.x * kRoundCols) {
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    const int na = scan_round(gacc, w, base, k, lnb64, lnb32, &s_n, s_j, s_g, s_w, write_steps ? delta : nullptr, phi);
+    for (int e = threadIdx.x; e < na; e += kThreads) {
+      const int64_t j = s_j[e];
+      double g, d, f;
+      active_step(s_g[e], inv_n, s_w[e], lam, bjs[j], ib[j], g, d, f);
+      max_bits(vmax, kkt_violation(g, s_w[e], lam));
+      if (write_steps) {
+        delta[j] = d;
+        phi[j] = f;
       }
     }
-    if (__any_sync(0xffffffffu, any)) {
-#pragma unroll
-      for (int q = 0; q < kColsPerThread; ++q) {
-        if (!act[q]) continue;
-        const int64_t j = t0 + (it * kColsPerThread + q) * stride;
-        double g, d, f;
-        active_step((double)ga[q], inv_n, wv[q], lam, bjs[j], ib[j], g, d, f);
-        max_bits(vmax, kkt_violation(g, wv[q], lam));
-        if (write_steps) {
-          delta[j] = d;
-          phi[j] = f;
-        }
-      }
-    }
+    __syncthreads();  // the queue is reused
   }
   block_max_bits_to(kkt_out, vmax);
 }
@@ -286,55 +302,41 @@ __global__ void __launch_bounds__(kThreads)
 // Thread-Greedy with many partitions: one CTA per partition computes the
 // step and proxy of its columns and accepts the best proxy (Table 2, "greedy
 // per thread"), so delta and phi never reach memory.  want_kkt: also reduce
-// the KKT violation (convergence checks only).
+// the KKT violation (convergence checks only).  Idle columns (phi = 0) are
+// never accepted and are not queued.
 template <typename G>
 __global__ void __launch_bounds__(kThreads)
     k_finalize_accept(G* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ bjs,
                       const double* __restrict__ ib, int64_t k, double inv_n, double lam, uint64_t lnb64,
                       uint32_t lnb32, int64_t B, int want_kkt, int32_t* __restrict__ list_j,
                       double* __restrict__ list_d, double* __restrict__ kkt_out) {
+  __shared__ int s_n;
+  __shared__ int64_t s_j[kRoundCols];
+  __shared__ double s_g[kRoundCols], s_w[kRoundCols];
   uint64_t vmax = 0;
   for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
     const int64_t lo = b * k / B, hi = (b + 1) * k / B;
-    const int64_t span = (int64_t)kColsPerThread * blockDim.x;
-    const int64_t rounds = (hi - lo + span - 1) / span;
     uint64_t bm = 0;
     int32_t bj = INT32_MAX;
     double bd = 0.0;
-    for (int64_t it = 0; it < rounds; ++it) {  // uniform across the CTA
-      G ga[kColsPerThread];
-      double wv[kColsPerThread];
-      bool act[kColsPerThread];
-      bool any = false;
-#pragma unroll
-      for (int q = 0; q < kColsPerThread; ++q) {
-        const int64_t j = lo + it * span + q * blockDim.x + threadIdx.x;
-        ga[q] = j < hi ? gacc[j] : G(0);
-        wv[q] = j < hi ? w[j] : 0.0;
-      }
-#pragma unroll
-      for (int q = 0; q < kColsPerThread; ++q) {
-        const int64_t j = lo + it * span + q * blockDim.x + threadIdx.x;
-        if (j < hi) gacc[j] = G(0);
-        act[q] = j < hi && !idle_raw(ga[q], wv[q], lnb64, lnb32);  // idle: phi = 0, never accepted
-        any |= act[q];
-      }
-      if (__any_sync(0xffffffffu, any)) {
-#pragma unroll
-        for (int q = 0; q < kColsPerThread; ++q) {
-          if (!act[q]) continue;
-          const int64_t j = lo + it * span + q * blockDim.x + threadIdx.x;
-          double g, d, f;
-          active_step((double)ga[q], inv_n, wv[q], lam, bjs[j], ib[j], g, d, f);
-          if (want_kkt) max_bits(vmax, kkt_violation(g, wv[q], lam));
-          const uint64_t m = candidate_mag(f);
-          if (cand_better(m, (int32_t)j, bm, bj)) {
-            bm = m;
-            bj = (int32_t)j;
-            bd = d;
-          }
+    for (int64_t base = lo; base < hi; base += kRoundCols) {  // uniform across the CTA
+      if (threadIdx.x == 0) s_n = 0;
+      __syncthreads();
+      const int na = scan_round(gacc, w, base, hi, lnb64, lnb32, &s_n, s_j, s_g, s_w, (double*)nullptr,
+                                (double*)nullptr);
+      for (int e = threadIdx.x; e < na; e += kThreads) {
+        const int64_t j = s_j[e];
+        double g, d, f;
+        active_step(s_g[e], inv_n, s_w[e], lam, bjs[j], ib[j], g, d, f);
+        if (want_kkt) max_bits(vmax, kkt_violation(g, s_w[e], lam));
+        const uint64_t m = candidate_mag(f);
+        if (cand_better(m, (int32_t)j, bm, bj)) {
+          bm = m;
+          bj = (int32_t)j;
+          bd = d;
         }
       }
+      __syncthreads();
     }
     block_best(bm, bj, bd);
     if (threadIdx.x == 0) {
