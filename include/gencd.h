@@ -224,6 +224,36 @@ int gencd_profile_enable(gencd_problem* p, int32_t enable);
 int gencd_profile_read(gencd_problem* p, int32_t kernel, double* ms, int64_t* launches);
 int gencd_profile_reset(gencd_problem* p);
 
+/*
+ * gencd_propose_all_noalloc -- the streaming Propose over all k columns
+ * (same quantities as gencd_propose_all) for callers that cannot allocate
+ * device memory: a thread that must not block on cudaMalloc/cudaFree, a
+ * process whose framework already holds all device memory in its own pool, or
+ * code enqueueing work on a stream that another thread is capturing.  The
+ * paper has no counterpart; this is a deployment entry point.
+ *
+ * It allocates nothing: no problem handle, no cudaMalloc/cudaFree, no
+ * allocating library call.  Its scratch is a fixed device array of 8.5 MB
+ * (every GPU that loads this library holds it until the process exits), which
+ * bounds the input: k <= 524,288 columns and nnz <= 33,554,432 non-zeros;
+ * larger inputs return GENCD_EINVAL.  The first call on each device looks up
+ * the scratch's device address (cudaGetSymbolAddress); make that first call
+ * before capturing any stream.  All calls on a device share the scratch and
+ * each clears what it accumulates into, so calls that overlap on the GPU
+ * (no stream ordering between them) race.
+ *
+ * Inputs (device memory of the current device, not re-validated: they must
+ * satisfy the CSC rules of gencd_create): col_ptr int64[k+1], row_idx
+ * int32[nnz], val double[nnz], y double[n], z = Xw double[n], w double[k];
+ * loss, lambda >= 0, beta_mode as in gencd_params.  u = l'(y, z) is evaluated
+ * on the fly.  Outputs (device): delta, phi double[k], kkt double[1].
+ * Work is enqueued on `stream`; the call returns without synchronising.
+ */
+int gencd_propose_all_noalloc(int64_t n, int64_t k, int64_t nnz, const int64_t* col_ptr, const int32_t* row_idx,
+                              const double* val, const double* y, const double* z, const double* w, int32_t loss,
+                              double lambda, int32_t beta_mode, double* delta, double* phi, double* kkt,
+                              void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* gencd_last_error(void);
 

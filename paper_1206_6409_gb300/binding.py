@@ -47,7 +47,7 @@ EXPORTS = ["gencd_create", "gencd_destroy", "gencd_set_lambda", "gencd_lambda_ma
            "gencd_set_w", "gencd_get_z", "gencd_objective", "gencd_propose_at", "gencd_propose_all",
            "gencd_spectral_radius", "gencd_color", "gencd_get_colors", "gencd_set_colors",
            "gencd_permutation", "gencd_profile_enable", "gencd_profile_read", "gencd_profile_reset",
-           "gencd_last_error", "gencd_stats", "gencd_stats_reset"]
+           "gencd_last_error", "gencd_stats", "gencd_stats_reset", "gencd_propose_all_noalloc"]
 
 
 class gencd_params(C.Structure):
@@ -113,6 +113,8 @@ def lib():
             "gencd_last_error": (C.c_char_p, []),
             "gencd_stats": (C.c_int, [vp, C.POINTER(gencd_result)]),
             "gencd_stats_reset": (C.c_int, [vp]),
+            "gencd_propose_all_noalloc": (C.c_int, [i64, i64, i64, vp, vp, vp, vp, vp, vp, i32, f64, i32, vp, vp,
+                                                    vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -341,6 +343,21 @@ def gencd_profile_read(h, kernel):
 
 def gencd_profile_reset(h):
     _check(lib().gencd_profile_reset(h))
+
+
+def gencd_propose_all_noalloc(n, k, nnz, col_ptr, row_idx, val, y, z, w, loss, lam, beta_mode, delta, phi, kkt,
+                              stream=None):
+    """The allocation-free streaming Propose.  Every array argument is a
+    contiguous CUDA tensor on the current device (inputs and the outputs
+    delta, phi of k float64 and kkt of one float64); nothing is allocated and
+    the call does not synchronise."""
+    ts = [col_ptr, row_idx, val, y, z, w, delta, phi, kkt]
+    if not all(_is_cuda_tensor(t) and t.is_contiguous() for t in ts):
+        raise ValueError("gencd_propose_all_noalloc takes contiguous CUDA tensors only")
+    ptr = [C.c_void_p(t.data_ptr()) for t in ts]
+    st = default_stream() if stream is None else int(stream)
+    _check(lib().gencd_propose_all_noalloc(int(n), int(k), int(nnz), *ptr[:6], LOSSES.get(loss, loss), float(lam),
+                                           int(beta_mode), *ptr[6:], C.c_void_p(st)))
 
 
 class Problem:

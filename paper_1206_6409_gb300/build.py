@@ -19,7 +19,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgencd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "kernels_propose.cu", "kernels_update.cu", "kernels_setup.cu", "propose_plan.cu"]
+SOURCES = ["api.cu", "kernels_propose.cu", "kernels_update.cu", "kernels_setup.cu", "propose_plan.cu",
+           "noalloc.cu"]
 
 
 def _nvcc() -> str:
