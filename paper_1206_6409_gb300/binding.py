@@ -38,7 +38,7 @@ VARIANTS = {"shotgun": GENCD_SHOTGUN, "thread_greedy": GENCD_THREAD_GREEDY, "gre
             "coloring": GENCD_COLORING}
 PRECISIONS = {"f64": GENCD_F64, "f32": GENCD_F32}
 KERNELS = ["propose_all", "finalize", "accept", "update", "refresh", "propose_list", "coloring_iter",
-           "objective", "setup"]
+           "objective", "setup", "propose_light", "propose_slabs", "pairs_reduce"]
 
 # every symbol include/gencd.h declares
 EXPORTS = ["gencd_create", "gencd_destroy", "gencd_set_lambda", "gencd_lambda_max",
@@ -108,7 +108,7 @@ def lib():
             "gencd_set_colors": (C.c_int, [vp, vp, i64, i32]),
             "gencd_permutation": (C.c_int, [vp, C.c_uint64, i64, i64, vp]),
             "gencd_profile_enable": (C.c_int, [vp, i32]),
-            "gencd_profile_read": (C.c_int, [vp, i32, C.POINTER(f64), C.POINTER(i64)]),
+            "gencd_profile_read": (C.c_int, [vp, i32, C.POINTER(f64), C.POINTER(i64), C.POINTER(i64)]),
             "gencd_profile_reset": (C.c_int, [vp]),
             "gencd_last_error": (C.c_char_p, []),
             "gencd_stats": (C.c_int, [vp, C.POINTER(gencd_result)]),
@@ -335,10 +335,11 @@ def gencd_profile_enable(h, enable=True):
 
 
 def gencd_profile_read(h, kernel):
+    """(summed ms, kernel launches, timed invocations) of a kernel family."""
     kid = KERNELS.index(kernel) if isinstance(kernel, str) else int(kernel)
-    ms, n = C.c_double(), C.c_int64()
-    _check(lib().gencd_profile_read(h, kid, C.byref(ms), C.byref(n)))
-    return ms.value, n.value
+    ms, n, calls = C.c_double(), C.c_int64(), C.c_int64()
+    _check(lib().gencd_profile_read(h, kid, C.byref(ms), C.byref(n), C.byref(calls)))
+    return ms.value, n.value, calls.value
 
 
 def gencd_profile_reset(h):

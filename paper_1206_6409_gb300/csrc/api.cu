@@ -36,8 +36,9 @@ static void prof_flush(gencd_problem* p) {
   p->prof.used = 0;
 }
 
-void prof_begin(gencd_problem* p, int id, cudaEvent_t* stop) {
-  p->prof.launches[id] += 1;
+void prof_begin(gencd_problem* p, int id, cudaEvent_t* stop, int launches) {
+  p->prof.launches[id] += launches;
+  p->prof.calls[id] += 1;
   *stop = nullptr;
   if (!p->prof.enabled || p->prof.pool.empty()) return;
   if (p->prof.used + 2 > p->prof.pool.size()) prof_flush(p);
@@ -837,12 +838,13 @@ int gencd_profile_enable(gencd_problem* p, int32_t enable) {
   return GENCD_OK;
 }
 
-int gencd_profile_read(gencd_problem* p, int32_t kernel, double* ms, int64_t* launches) {
+int gencd_profile_read(gencd_problem* p, int32_t kernel, double* ms, int64_t* launches, int64_t* calls) {
   GENCD_CHECK_HANDLE(p);
   if (kernel < 0 || kernel >= K_NUM) return fail(GENCD_EINVAL, "unknown kernel family");
   prof_flush(p);
   if (ms) *ms = p->prof.ms[kernel];
   if (launches) *launches = p->prof.launches[kernel];
+  if (calls) *calls = p->prof.calls[kernel];
   return GENCD_OK;
 }
 
@@ -852,6 +854,7 @@ int gencd_profile_reset(gencd_problem* p) {
   for (int i = 0; i < K_NUM; ++i) {
     p->prof.ms[i] = 0.0;
     p->prof.launches[i] = 0;
+    p->prof.calls[i] = 0;
   }
   return GENCD_OK;
 }

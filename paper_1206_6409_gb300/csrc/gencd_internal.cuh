@@ -60,6 +60,9 @@ enum KernelId {
   K_COLOR_ITER,       // fused Coloring iteration
   K_OBJECTIVE,        // objective reduction
   K_SETUP,            // one-time and selection kernels
+  K_PROPOSE_LIGHT,    // streaming propose: lane-segmented pass over the light columns
+  K_PROPOSE_SLABS,    // streaming propose: row-slab pass over the heavy columns
+  K_PAIRS,            // streaming propose: sum of each heavy column's partials
   K_NUM
 };
 
@@ -69,7 +72,8 @@ struct Profiler {
   std::vector<int> pending_id;         // kernel id of each recorded pair
   size_t used = 0;
   double ms[K_NUM] = {0};
-  int64_t launches[K_NUM] = {0};       // counted whether or not profiling is on
+  int64_t launches[K_NUM] = {0};       // kernel launches, counted whether or not profiling is on
+  int64_t calls[K_NUM] = {0};          // timed invocations (one event pair each)
 };
 
 // A CSC matrix as the streaming propose sees it (cmap: column map, may be null)
@@ -257,7 +261,7 @@ int launch_power_step(gencd_problem* p, const double* v, const double* dinv, dou
 int validate_input(gencd_problem* p, int64_t* bad_col, int64_t* bad_row, int* stage);
 
 // profiling helpers (api.cu)
-void prof_begin(gencd_problem* p, int id, cudaEvent_t* stop_out);
+void prof_begin(gencd_problem* p, int id, cudaEvent_t* stop_out, int launches = 1);
 void prof_end(gencd_problem* p, cudaEvent_t stop);
 
 // grow a device allocation

@@ -542,13 +542,16 @@ int launch_propose_csc(gencd_problem* p, const CscView& a, const void* u_vec, bo
 // always takes the plain pass into the FP64 gacc.
 int launch_propose_all(gencd_problem* p, const void* u_vec, bool u_is_double) {
   cudaEvent_t ev = nullptr;
-  prof_begin(p, K_PROPOSE_ALL, &ev);
+  prof_begin(p, K_PROPOSE_ALL, &ev, 0);  // the whole family; its kernels count their launches
   const bool native = u_is_double == (p->precision == GENCD_F64);
   if (p->plan.built && native) {
     GENCD_TRY(launch_propose_plan(p, u_vec));
   } else {
     CscView a{p->col_ptr, p->row_idx, p->val, p->tile_col, p->nnz, p->ntiles, nullptr};
+    cudaEvent_t e2 = nullptr;
+    prof_begin(p, K_PROPOSE_LIGHT, &e2);
     GENCD_TRY(launch_propose_csc(p, a, u_vec, u_is_double));
+    prof_end(p, e2);
   }
   prof_end(p, ev);
   return GENCD_OK;

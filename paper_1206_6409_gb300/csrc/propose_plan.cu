@@ -195,26 +195,35 @@ int launch_propose_plan(gencd_problem* p, const void* u_vec) {
   if (P.nlight > 0) {
     CscView a{P.light_col_ptr, P.light_row, P.light_val, P.light_tile_col, P.light_nnz, P.light_ntiles,
               P.light_cols};
+    cudaEvent_t e = nullptr;
+    prof_begin(p, K_PROPOSE_LIGHT, &e);
     GENCD_TRY(launch_propose_csc(p, a, u_vec, p->precision == GENCD_F64));
+    prof_end(p, e);
   }
   if (P.nheavy > 0) {
     const size_t smem = (size_t)P.slab_rows * (p->precision == GENCD_F64 ? 8 : 4);
     const int g2 = grid_for(P.nheavy, kThreads, p->num_sms * 8);
-    if (p->precision == GENCD_F64) {
+    cudaEvent_t e1 = nullptr, e2 = nullptr;
+    prof_begin(p, K_PROPOSE_SLABS, &e1);
+    if (p->precision == GENCD_F64)
       k_propose_slabs<double, double, double><<<P.grid, kSlabThreads, smem, p->stream>>>(
           P.s_row, (const double*)P.s_val, P.pair_start, P.pair_slot, P.tile_start, P.tile_end, P.tile_pair,
           P.tile_pair_last, P.tile_slab, P.slab_tile_begin, P.cta_tile_begin, (const double*)u_vec, p->n,
           P.slab_rows, (double*)P.partial);
-      k_pairs_to_gacc<double><<<g2, kThreads, 0, p->stream>>>(P.hslot_ptr, P.heavy_cols, P.nheavy,
-                                                               (double*)P.partial, (double*)p->gnat);
-    } else {
+    else
       k_propose_slabs<float, float, float><<<P.grid, kSlabThreads, smem, p->stream>>>(
           P.s_row, (const float*)P.s_val, P.pair_start, P.pair_slot, P.tile_start, P.tile_end, P.tile_pair,
           P.tile_pair_last, P.tile_slab, P.slab_tile_begin, P.cta_tile_begin, (const float*)u_vec, p->n,
           P.slab_rows, (float*)P.partial);
+    prof_end(p, e1);
+    prof_begin(p, K_PAIRS, &e2);
+    if (p->precision == GENCD_F64)
+      k_pairs_to_gacc<double><<<g2, kThreads, 0, p->stream>>>(P.hslot_ptr, P.heavy_cols, P.nheavy,
+                                                               (double*)P.partial, (double*)p->gnat);
+    else
       k_pairs_to_gacc<float><<<g2, kThreads, 0, p->stream>>>(P.hslot_ptr, P.heavy_cols, P.nheavy,
                                                               (float*)P.partial, (float*)p->gnat);
-    }
+    prof_end(p, e2);
     p->prof.launches[K_PROPOSE_ALL] += 1;
     GENCD_CUDA_TRY(cudaGetLastError());
   }
