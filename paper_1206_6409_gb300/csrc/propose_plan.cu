@@ -15,10 +15,11 @@
 // Within a slab the kernel works like the CSC pass: a warp owns a tile of
 // 256 consecutive entries, a lane 8 of them (128-bit loads of rows and
 // values), a lane sums its entries pair by pair in registers and emits each
-// partial with a store when the pair lies inside the lane; sums of pairs cut
-// by lane boundaries are combined by a warp scan, and only pairs cut by the
-// tile's ends take atomic adds.  Partial sums are kept in the storage
-// precision (FP32 atomics in FP32 mode).
+// partial with a store (pair inside the lane) or an atomic add; a full tile
+// inside one pair is reduced by the warp first.  (A warp scan over lane-cut
+// pairs removes most atomics but costs more instructions than it saves in
+// this issue-bound kernel.)  Partial sums are kept in the storage precision
+// (FP32 atomics in FP32 mode).
 #include <algorithm>
 #include <vector>
 
@@ -53,6 +54,14 @@ __device__ __forceinline__ void load8<double>(const double* __restrict__ p, doub
     v[2 * q] = x.x;
     v[2 * q + 1] = x.y;
   }
+}
+
+template <typename G>
+__device__ __forceinline__ void emit_pair(G* __restrict__ partial, uint32_t slot, G s, bool whole) {
+  if (whole)
+    partial[slot] = s;
+  else
+    atomicAdd(partial + slot, s);
 }
 
 // the entries of one lane: 8 in-slab rows (one 128-bit load) and 8 values
@@ -114,9 +123,9 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
       } else if (active) {
         load_lane(s_row, s_val, a, cur);
       }
-      V acc = V(0), head = V(0), right = V(0);
-      uint32_t q = 0, q0 = 0, cend = 0;
-      bool closed = false, open_left = false, open_right = false, through = false, starts = false;
+      V acc = V(0);
+      uint32_t q = 0, q_first = 0, cend = 0;
+      bool whole = false;
       if (active) {
         const uint32_t w4[4] = {cur.rr.x, cur.rr.y, cur.rr.z, cur.rr.w};
         U uu[8];
@@ -135,82 +144,59 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
           else
             hi = mid - 1;
         }
-        q = q0 = lo;
-        open_left = __ldg(pair_start + q) < a;
+        q = q_first = lo;
+        const uint32_t qs = __ldg(pair_start + q);
         cend = __ldg(pair_start + q + 1);
+        whole = qs >= a;
+        if (cend >= a + kSlabItems) {
+          // the lane's entries all belong to pair q (the common case): no
+          // per-entry boundary test
 #pragma unroll
-        for (int i = 0; i < kSlabItems; ++i) {
-          const uint32_t p = a + i;
-          while (p >= cend) {  // pair q closes before p
-            if (!closed && open_left)
-              head = acc;  // its earlier part is in previous lanes
-            else
-              partial[__ldg(pair_slot + q)] = (G)acc;  // complete inside this lane
-            closed = true;
-            ++q;
-            cend = __ldg(pair_start + q + 1);
-            acc = V(0);
-          }
-          acc = fma(cur.v[i], (V)uu[i], acc);
-        }
-        open_right = cend > a + kSlabItems;
-        if (!closed) {  // one pair in this lane
-          through = open_left && open_right;
-          if (open_right) {
-            right = acc;
-            starts = !open_left;
-          } else if (open_left) {
-            head = acc;  // the chain ends at this lane's end
-          } else {
-            partial[__ldg(pair_slot + q)] = (G)acc;
-          }
-        } else if (open_right) {
-          right = acc;
-          starts = true;
+          for (int i = 0; i < kSlabItems; ++i) acc = fma(cur.v[i], (V)uu[i], acc);
         } else {
-          partial[__ldg(pair_slot + q)] = (G)acc;
+#pragma unroll
+          for (int i = 0; i < kSlabItems; ++i) {
+            const uint32_t p = a + i;
+            while (p >= cend) {
+              emit_pair<G>(partial, __ldg(pair_slot + q), (G)acc, whole);
+              ++q;
+              cend = __ldg(pair_start + q + 1);
+              acc = V(0);
+              whole = true;
+            }
+            acc = fma(cur.v[i], (V)uu[i], acc);
+          }
         }
       }
-      // pairs cut by lane boundaries: combined by the warp; only pairs cut by
-      // the tile's ends take atomic adds
-      V cin, cout;
-      bool from_tile;
-      warp_chain_scan(right, through, starts, cin, from_tile, cout);
-      if (active && open_left && !through) {
-        if (from_tile)
-          partial[__ldg(pair_slot + q0)] = (G)(head + cin);
-        else
-          atomicAdd(partial + __ldg(pair_slot + q0), (G)(head + cin));
+      // a full tile inside one pair: one warp sum and one emit instead of 32
+      const uint32_t qf = __shfl_sync(0xffffffffu, q_first, 0);
+      const uint32_t ql = __shfl_sync(0xffffffffu, q, 31);
+      if (te - ts == (uint32_t)kSlabTile && qf == ql) {
+        const V sum = warp_sum(acc);
+        if (lane == 0) {
+          const bool in_tile = __ldg(pair_start + qf) >= ts && __ldg(pair_start + qf + 1) <= te;
+          emit_pair<G>(partial, __ldg(pair_slot + qf), (G)sum, in_tile);
+        }
+      } else if (active) {
+        emit_pair<G>(partial, __ldg(pair_slot + q), (G)acc, whole && cend <= a + kSlabItems);
       }
-      if (active && open_right && a + kSlabItems >= te) atomicAdd(partial + __ldg(pair_slot + q), (G)cout);
     }
     t0 = t1;
   }
 }
 
-// sum of each heavy column = its partials; 8 lanes per column add the slots
-// l, l+8, ... and a fixed butterfly combines them; partials reset
+// sum of each heavy column = its partials in slab order; partials reset
 template <typename G>
 __global__ void k_pairs_to_gacc(const uint32_t* __restrict__ hslot_ptr, const int32_t* __restrict__ heavy_cols,
                                 int64_t nheavy, G* __restrict__ partial, G* __restrict__ gacc) {
-  const int sub = threadIdx.x & 7;
-  const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 3;
-  const int64_t h0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
-  const int64_t rounds = (nheavy + stride - 1) / stride;
-  for (int64_t it = 0; it < rounds; ++it) {  // uniform: every lane reaches the shuffles
-    const int64_t h = h0 + it * stride;
-    G s = G(0);
-    if (h < nheavy) {
-      for (uint32_t q = hslot_ptr[h] + sub; q < hslot_ptr[h + 1]; q += 8) {
-        s += partial[q];
-        partial[q] = G(0);
-      }
-    }
-    s += __shfl_xor_sync(0xffffffffu, s, 4);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    if (h < nheavy && sub == 0) gacc[heavy_cols[h]] = s;
+  const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= nheavy) return;
+  G s = G(0);
+  for (uint32_t q = hslot_ptr[h]; q < hslot_ptr[h + 1]; ++q) {
+    s += partial[q];
+    partial[q] = G(0);
   }
+  gacc[heavy_cols[h]] = s;
 }
 
 int launch_propose_plan(gencd_problem* p, const void* u_vec) {
@@ -225,7 +211,7 @@ int launch_propose_plan(gencd_problem* p, const void* u_vec) {
   }
   if (P.nheavy > 0) {
     const size_t smem = (size_t)P.slab_rows * (p->precision == GENCD_F64 ? 8 : 4);
-    const int g2 = grid_for(P.nheavy * 8, kThreads, p->num_sms * 8);
+    const int g2 = (int)((P.nheavy + kThreads - 1) / kThreads);  // one thread per heavy column
     cudaEvent_t e1 = nullptr, e2 = nullptr;
     prof_begin(p, K_PROPOSE_SLABS, &e1);
     if (p->precision == GENCD_F64)
