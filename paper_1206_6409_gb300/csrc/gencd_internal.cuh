@@ -104,20 +104,20 @@ struct ProposePlan {
   int64_t* light_col_ptr = nullptr;
   int32_t* light_row = nullptr;
   void* light_val = nullptr;
-  int32_t* light_tile_col = nullptr;
+  int32_t* light_tile_lc = nullptr;  // light column of each 256-entry tile's first entry
+  uint8_t* lmask = nullptr;          // per 8 light entries: bit i = entry 8g + i starts a column
   // heavy columns
   int64_t nheavy = 0, entries = 0, npairs = 0, ntiles = 0;
   int32_t* heavy_cols = nullptr;   // original column of heavy id h
   uint16_t* s_row = nullptr;       // slab-local row of each entry
   void* s_val = nullptr;           // value of each entry (padding: 0)
-  uint32_t* pair_start = nullptr;  // first entry of each pair; [npairs] = entries
-  uint32_t* pair_slot = nullptr;   // partial slot of each pair (column-major)
-  uint32_t* hslot_ptr = nullptr;   // first slot of heavy column h; [nheavy] = npairs
-  void* partial = nullptr;         // one partial sum per pair (storage precision), zero between launches
+  uint8_t* pmask = nullptr;        // per 8 entries: bit i = entry 8g + i starts a pair (pairs in entry order)
+  uint32_t* pair_slot = nullptr;   // partial slot of each pair: column-major, each column's in slab order
+  uint32_t* hslot_ptr = nullptr;   // heavy column h owns slots hslot_ptr[h] .. hslot_ptr[h+1]
+  void* partial = nullptr;         // one partial sum per slot (storage precision), zero between launches
   uint32_t* tile_start = nullptr;  // tiles of 32*ITEMS entries inside one slab
   uint32_t* tile_end = nullptr;
-  uint32_t* tile_pair = nullptr;   // pairs holding the tile's first and last entry
-  uint32_t* tile_pair_last = nullptr;
+  uint32_t* tile_pair = nullptr;   // pair holding the tile's first entry
   int32_t* tile_slab = nullptr;
   int32_t* slab_tile_begin = nullptr;  // nslabs + 1
   int32_t* cta_tile_begin = nullptr;   // grid + 1
@@ -236,7 +236,9 @@ int bits_for_max(int64_t maxval);
 int lower_bounds_u32_to_i64(gencd_problem* p, const uint32_t* sorted, int64_t m, int64_t count, int64_t* out);
 int iota_u32(gencd_problem* p, uint32_t* a, int64_t m);
 int fail_plan(const char* msg);
-int launch_tile_map_of(gencd_problem* p, const int64_t* col_ptr, int64_t k, int64_t ntiles, int32_t* tile_col);
+// tile_col[t] = column holding entry t * tile (columns without entries hold none)
+int launch_tile_map_of(gencd_problem* p, const int64_t* col_ptr, int64_t k, int64_t ntiles, int32_t* tile_col,
+                       int64_t tile);
 int launch_propose_list(gencd_problem* p, const int32_t* J, int64_t m, double* delta, double* phi);
 int launch_objective(gencd_problem* p);
 int launch_col_sumsq(gencd_problem* p);  // gacc_j = sum_i X_ij^2

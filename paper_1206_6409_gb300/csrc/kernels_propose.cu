@@ -313,9 +313,17 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ int s_n;
   __shared__ int64_t s_j[kRoundCols];
   __shared__ double s_g[kRoundCols], s_w[kRoundCols];
+  __shared__ int64_t s_lo, s_hi;
   uint64_t vmax = 0;
   for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
-    const int64_t lo = b * k / B, hi = (b + 1) * k / B;
+    // 64-bit divisions run on the FP64 unit, which is small on this GPU:
+    // one thread computes the partition bounds
+    if (threadIdx.x == 0) {
+      s_lo = b * k / B;
+      s_hi = (b + 1) * k / B;
+    }
+    __syncthreads();
+    const int64_t lo = s_lo, hi = s_hi;
     uint64_t bm = 0;
     int32_t bj = INT32_MAX;
     double bd = 0.0;
@@ -355,13 +363,19 @@ __global__ void __launch_bounds__(kThreads)
     k_finalize_chunks(G* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ bjs,
                       const double* __restrict__ ib, int64_t k, double inv_n, double lam, uint64_t lnb64,
                       uint32_t lnb32,
-                      int64_t B, int64_t S, int want_kkt, uint64_t* __restrict__ slot_m,
+                      int64_t B, int64_t S, int64_t nchunks, int want_kkt, uint64_t* __restrict__ slot_m,
                       int32_t* __restrict__ slot_j, double* __restrict__ slot_d, double* __restrict__ kkt_out) {
-  const int64_t nchunks = (k + S - 1) / S;
+  __shared__ int64_t s_b[3];
   uint64_t vmax = 0;
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const int64_t lo = ch * S, hi = lo + S < k ? lo + S : k;
-    const int64_t b0 = partition_of(lo, k, B), b1 = partition_of(hi - 1, k, B);
+    if (threadIdx.x == 0) {  // one thread does the 64-bit divisions (FP64 unit)
+      s_b[0] = partition_of(lo, k, B);
+      s_b[1] = partition_of(hi - 1, k, B);
+      s_b[2] = (s_b[0] + 1) * k / B;  // first column after partition b0
+    }
+    __syncthreads();
+    const int64_t b0 = s_b[0], b1 = s_b[1], end0 = s_b[2];
     uint64_t m0 = 0, m1 = 0;
     int32_t j0 = INT32_MAX, j1 = INT32_MAX;
     double d0 = 0.0, d1 = 0.0;
@@ -374,7 +388,7 @@ __global__ void __launch_bounds__(kThreads)
       active_step((double)ga, inv_n, wj, lam, bjs[j], ib[j], g, d, f);
       if (want_kkt) max_bits(vmax, kkt_violation(g, wj, lam));
       const uint64_t m = candidate_mag(f);
-      if (partition_of(j, k, B) == b0) {
+      if (j < end0) {  // partition b0
         if (cand_better(m, (int32_t)j, m0, j0)) {
           m0 = m;
           j0 = (int32_t)j;
@@ -408,9 +422,14 @@ __global__ void __launch_bounds__(kThreads)
     k_accept_slots(const uint64_t* __restrict__ slot_m, const int32_t* __restrict__ slot_j,
                    const double* __restrict__ slot_d, int64_t k, int64_t B, int64_t S,
                    int32_t* __restrict__ list_j, double* __restrict__ list_d) {
+  __shared__ int64_t s_c[2];
   for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
-    const int64_t lo = b * k / B, hi = (b + 1) * k / B;
-    const int64_t c0 = lo / S, c1 = (hi - 1) / S;
+    if (threadIdx.x == 0) {  // one thread does the 64-bit divisions (FP64 unit)
+      s_c[0] = (b * k / B) / S;
+      s_c[1] = ((b + 1) * k / B - 1) / S;
+    }
+    __syncthreads();
+    const int64_t c0 = s_c[0], c1 = s_c[1];
     uint64_t bm = 0;
     int32_t bj = INT32_MAX;
     double bd = 0.0;
@@ -749,11 +768,11 @@ int launch_finalize_accept(gencd_problem* p, int64_t B, bool want_kkt) {
     const int grid = grid_for(nchunks * kThreads, kThreads, blocks_per_sm_cap(p, 8));
     if (f64)
       k_finalize_chunks<double><<<grid, kThreads, 0, p->stream>>>((double*)p->gnat, p->w, p->bj, p->ib, p->k, inv_n,
-                                                                  p->lambda, b64, b32, B, S, want_kkt ? 1 : 0,
+                                                                  p->lambda, b64, b32, B, S, nchunks, want_kkt ? 1 : 0,
                                                                   p->slot_m, p->slot_j, p->slot_d, p->dscal + 0);
     else
       k_finalize_chunks<float><<<grid, kThreads, 0, p->stream>>>((float*)p->gnat, p->w, p->bj, p->ib, p->k, inv_n,
-                                                                 p->lambda, b64, b32, B, S, want_kkt ? 1 : 0,
+                                                                 p->lambda, b64, b32, B, S, nchunks, want_kkt ? 1 : 0,
                                                                  p->slot_m, p->slot_j, p->slot_d, p->dscal + 0);
     const int g2 = (int)(B < (int64_t)p->num_sms * 16 ? B : (int64_t)p->num_sms * 16);
     k_accept_slots<<<g2, kThreads, 0, p->stream>>>(p->slot_m, p->slot_j, p->slot_d, p->k, B, S, p->list_j,

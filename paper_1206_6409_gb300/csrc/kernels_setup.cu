@@ -640,15 +640,17 @@ int launch_col_scale(gencd_problem* p) {
   return GENCD_OK;
 }
 
-int launch_tile_map_of(gencd_problem* p, const int64_t* col_ptr, int64_t k, int64_t ntiles, int32_t* tile_col) {
-  const int64_t tile = 32LL * p->items;
+int launch_tile_map_of(gencd_problem* p, const int64_t* col_ptr, int64_t k, int64_t ntiles, int32_t* tile_col,
+                       int64_t tile) {
   k_tile_map<<<grid_for(k, kThreads, p->num_sms * 8), kThreads, 0, p->stream>>>(col_ptr, k, tile, ntiles, tile_col);
   p->prof.launches[K_SETUP] += 1;
   GENCD_CUDA_TRY(cudaGetLastError());
   return GENCD_OK;
 }
 
-int launch_tile_map(gencd_problem* p) { return launch_tile_map_of(p, p->col_ptr, p->k, p->ntiles, p->tile_col); }
+int launch_tile_map(gencd_problem* p) {
+  return launch_tile_map_of(p, p->col_ptr, p->k, p->ntiles, p->tile_col, 32LL * p->items);
+}
 
 // validation entry used by the API: returns first bad column / row or -1
 int validate_input(gencd_problem* p, int64_t* bad_col, int64_t* bad_row, int* stage) {

@@ -65,6 +65,72 @@ __global__ void k_apply_w(const int64_t* __restrict__ col_ptr, const int32_t* __
   }
 }
 
+// One CTA for lists of at most kListPlanMax entries: lengths of the applied
+// entries, their exclusive prefix (off[0..m]), w_j += delta_j and the counters
+// -- k_list_len, the scan and k_apply_w in one launch.
+constexpr int kListPlanThreads = 1024;
+constexpr int kListPlanPer = 4;
+constexpr int64_t kListPlanMax = (int64_t)kListPlanThreads * kListPlanPer;
+
+__global__ void __launch_bounds__(kListPlanThreads)
+    k_list_plan(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ J, const double* __restrict__ D,
+                int64_t m, double* __restrict__ w, uint32_t* __restrict__ off,
+                unsigned long long* __restrict__ counters) {
+  __shared__ uint32_t s_warp[kListPlanThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  uint32_t len[kListPlanPer];
+  uint32_t mine = 0, upd = 0;
+#pragma unroll
+  for (int q = 0; q < kListPlanPer; ++q) {
+    const int64_t e = (int64_t)tid * kListPlanPer + q;
+    len[q] = 0;
+    if (e < m) {
+      const int32_t j = J[e];
+      const double d = D[e];
+      if (j >= 0 && d != 0.0) {
+        len[q] = (uint32_t)(col_ptr[j + 1] - col_ptr[j]);
+        w[j] += d;  // the entries name distinct columns
+        ++upd;
+      }
+    }
+    mine += len[q];
+  }
+  // block-wide exclusive prefix of the per-thread sums
+  uint32_t incl = mine;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += y;
+  }
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t v = s_warp[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane >= d) v += y;
+    }
+    s_warp[lane] = v;  // inclusive over warps
+  }
+  __syncthreads();
+  uint32_t run = (wid > 0 ? s_warp[wid - 1] : 0u) + incl - mine;
+#pragma unroll
+  for (int q = 0; q < kListPlanPer; ++q) {
+    const int64_t e = (int64_t)tid * kListPlanPer + q;
+    if (e < m) off[e] = run;
+    run += len[q];
+  }
+  const uint32_t total = s_warp[kListPlanThreads / 32 - 1];
+  if (tid == 0) off[m] = total;
+  const unsigned long long u_all = warp_sum((unsigned long long)upd);
+  if (lane == 0 && u_all) atomicAdd(counters + 0, u_all);
+  if (tid == 0 && total) {
+    atomicAdd(counters + 1, (unsigned long long)total);
+    atomicAdd(counters + 3, (unsigned long long)total);  // touched this iteration
+  }
+}
+
 // last entry e in [0, m) with off[e] <= q
 __device__ __forceinline__ int64_t entry_of(const uint32_t* __restrict__ off, int64_t m, uint32_t q) {
   int64_t lo = 0, hi = m - 1;
@@ -212,10 +278,15 @@ int launch_update_list(gencd_problem* p, const int32_t* J, const double* d, int6
   unsigned long long* ctr = reinterpret_cast<unsigned long long*>(p->dscal + 4);
   const int g = p->num_sms * 8;
   cudaEvent_t ev = nullptr;
-  prof_begin(p, K_UPDATE, &ev);
-  k_list_len<<<grid_for(m + 1, kThreads, g), kThreads, 0, p->stream>>>(p->col_ptr, J, d, m, p->list_off);
-  GENCD_TRY(exclusive_scan(p, p->list_off, p->list_off, m + 1, p->scan_tmp));
-  k_apply_w<<<grid_for(m, kThreads, g), kThreads, 0, p->stream>>>(p->col_ptr, J, d, m, p->w, ctr);
+  const bool one_cta = m <= kListPlanMax;
+  prof_begin(p, K_UPDATE, &ev, one_cta ? 2 : 3);  // plan kernel(s) and the scatter (+ the scan)
+  if (one_cta) {
+    k_list_plan<<<1, kListPlanThreads, 0, p->stream>>>(p->col_ptr, J, d, m, p->w, p->list_off, ctr);
+  } else {
+    k_list_len<<<grid_for(m + 1, kThreads, g), kThreads, 0, p->stream>>>(p->col_ptr, J, d, m, p->list_off);
+    GENCD_TRY(exclusive_scan(p, p->list_off, p->list_off, m + 1, p->scan_tmp));
+    k_apply_w<<<grid_for(m, kThreads, g), kThreads, 0, p->stream>>>(p->col_ptr, J, d, m, p->w, ctr);
+  }
   if (p->precision == GENCD_F64)
     k_update_flat<double><<<g, kThreads, 0, p->stream>>>(p->col_ptr, p->row_idx, (const double*)p->val, J, d,
                                                          p->list_off, m, p->z);
@@ -223,7 +294,6 @@ int launch_update_list(gencd_problem* p, const int32_t* J, const double* d, int6
     k_update_flat<float><<<g, kThreads, 0, p->stream>>>(p->col_ptr, p->row_idx, (const float*)p->val, J, d,
                                                         p->list_off, m, p->z);
   prof_end(p, ev);
-  p->prof.launches[K_UPDATE] += 2;  // length, apply-w and scatter kernels (+ the scan)
   GENCD_CUDA_TRY(cudaGetLastError());
   return GENCD_OK;
 }

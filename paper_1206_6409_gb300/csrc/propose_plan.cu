@@ -78,17 +78,46 @@ __device__ __forceinline__ void load_lane(const uint16_t* __restrict__ s_row, co
   load8<V>(s_val + a, L.v);
 }
 
+// Segmented suffix sum over the lanes: T_L = x_L + x_{L+1} + ... + x_M where M
+// is the first lane >= L with stop set (all lanes to 31 when there is none);
+// ended_L reports whether such an M exists.  Five shuffle steps.
+template <typename V>
+__device__ __forceinline__ V lane_suffix_sum(V x, bool stop, int lane, bool& ended) {
+  V t = x;
+  bool e = stop;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const V tn = __shfl_down_sync(0xffffffffu, t, d);
+    const bool en = __shfl_down_sync(0xffffffffu, (int)e, d) != 0;
+    if (!e && lane + d < 32) {
+      t += tn;
+      e = en;
+    }
+  }
+  ended = e;
+  return t;
+}
+
+// Pairs are numbered in entry order; pmask holds one byte per 8 entries whose
+// bit i says "entry 8g + i starts a pair", and tile_pair[t] is the pair of the
+// tile's first entry.  A lane finds the pair of its first entry from a warp
+// prefix count of the start bits, so no pair table is searched.  Per lane:
+// runs that start and end inside the lane are stored; the run that continues
+// from the left (cont) and the run that leaves to the right (tail) are
+// combined across the warp by a segmented suffix sum, so only the tile's first
+// and last pairs take atomic adds.
 template <typename V, typename U, typename G>
 __global__ void __launch_bounds__(kSlabThreads, 1)
     k_propose_slabs(const uint16_t* __restrict__ s_row, const V* __restrict__ s_val,
-                    const uint32_t* __restrict__ pair_start, const uint32_t* __restrict__ pair_slot,
-                    const uint32_t* __restrict__ tile_start, const uint32_t* __restrict__ tile_end,
-                    const uint32_t* __restrict__ tile_pair, const uint32_t* __restrict__ tile_pair_last,
+                    const uint8_t* __restrict__ pmask, const uint32_t* __restrict__ pair_slot,
+                    const uint32_t* __restrict__ tile_start,
+                    const uint32_t* __restrict__ tile_end, const uint32_t* __restrict__ tile_pair,
                     const int32_t* __restrict__ tile_slab, const int32_t* __restrict__ slab_tile_begin,
                     const int32_t* __restrict__ cta_tile_begin, const U* __restrict__ u, int64_t n,
                     int32_t slab_rows, G* __restrict__ partial) {
   // FP32 tiles are small enough to keep the next tile's loads in flight
   constexpr bool kPrefetch = sizeof(V) == 4;
+  const unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   U* s_u = reinterpret_cast<U*>(smem_raw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -103,29 +132,63 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
     for (int i = threadIdx.x; i < rows; i += blockDim.x) s_u[i] = u[row0 + i];
     __syncthreads();
     LaneLoad<V> nxt;
+    uint32_t nts = 0, nte = 0, nq0 = 0, nm = 0;
     int t = t0 + warp;
     if (kPrefetch && t < t1) {
-      const uint32_t a = tile_start[t] + lane * kSlabItems;
-      if (a < tile_end[t]) load_lane(s_row, s_val, a, nxt);
+      nts = tile_start[t];
+      nte = tile_end[t];
+      nq0 = tile_pair[t];
+      const uint32_t a = nts + lane * kSlabItems;
+      if (a < nte) {
+        load_lane(s_row, s_val, a, nxt);
+        nm = pmask[a >> 3];
+      }
     }
     for (; t < t1; t += nw) {  // warp-uniform loop
-      const uint32_t ts = tile_start[t], te = tile_end[t];
-      const uint32_t a = ts + lane * kSlabItems;
-      const bool active = a < te;  // tile ends are multiples of 8
+      uint32_t ts, te, q0, m;
       LaneLoad<V> cur;
       if (kPrefetch) {
+        ts = nts, te = nte, q0 = nq0, m = nm;
         cur = nxt;
         const int tn = t + nw;
         if (tn < t1) {
-          const uint32_t an = tile_start[tn] + lane * kSlabItems;
-          if (an < tile_end[tn]) load_lane(s_row, s_val, an, nxt);
+          nts = tile_start[tn];
+          nte = tile_end[tn];
+          nq0 = tile_pair[tn];
+          const uint32_t an = nts + lane * kSlabItems;
+          nm = 0;
+          if (an < nte) {
+            load_lane(s_row, s_val, an, nxt);
+            nm = pmask[an >> 3];
+          }
         }
-      } else if (active) {
-        load_lane(s_row, s_val, a, cur);
+      } else {
+        ts = tile_start[t], te = tile_end[t], q0 = tile_pair[t], m = 0;
+        const uint32_t a0 = ts + lane * kSlabItems;
+        if (a0 < te) {
+          load_lane(s_row, s_val, a0, cur);
+          m = pmask[a0 >> 3];
+        }
       }
-      V acc = V(0);
-      uint32_t q = 0, q_first = 0, cend = 0;
-      bool whole = false;
+      const uint32_t a = ts + lane * kSlabItems;
+      const bool active = a < te;  // tile ends are multiples of 8
+      if (!active) m = 0;
+      // pair of the lane's first entry: q0 + start bits in (ts, a] of the tile
+      const uint32_t cnt = __popc(lane == 0 ? (m & 0xfeu) : m);
+      uint32_t incl = cnt;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += y;
+      }
+      uint32_t q = q0 + (incl - cnt) + (lane > 0 ? (m & 1u) : 0u);
+      // column-major slots of the pairs this lane may emit, loaded early: the
+      // tile's first pair (lane 0) and the pair of the lane's last run
+      const bool lead = lane == 0 && active && !(m & 1u);
+      const uint32_t slot0 = lead ? __ldg(pair_slot + q0) : 0u;
+      const uint32_t slot_last = (active && m != 0u) ? __ldg(pair_slot + q + __popc(m & 0xfeu)) : 0u;
+      V acc = V(0), cont = V(0), tail = V(0);
+      bool has_tail = false;
       if (active) {
         const uint32_t w4[4] = {cur.rr.x, cur.rr.y, cur.rr.z, cur.rr.w};
         U uu[8];
@@ -134,67 +197,170 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
           uu[2 * h] = s_u[w4[h] & 0xffffu];
           uu[2 * h + 1] = s_u[w4[h] >> 16];
         }
-        // pair holding entry a: the largest q in [tile_pair, tile_pair_last]
-        // with pair_start[q] <= a
-        uint32_t lo = tile_pair[t], hi = tile_pair_last[t];
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi + 1) >> 1;
-          if (__ldg(pair_start + mid) <= a)
-            lo = mid;
-          else
-            hi = mid - 1;
-        }
-        q = q_first = lo;
-        const uint32_t qs = __ldg(pair_start + q);
-        cend = __ldg(pair_start + q + 1);
-        whole = qs >= a;
-        if (cend >= a + kSlabItems) {
-          // the lane's entries all belong to pair q (the common case): no
-          // per-entry boundary test
+        if (m <= 1u) {  // no pair starts after the lane's first entry (the common case)
 #pragma unroll
           for (int i = 0; i < kSlabItems; ++i) acc = fma(cur.v[i], (V)uu[i], acc);
         } else {
+          bool first_run = true;
 #pragma unroll
           for (int i = 0; i < kSlabItems; ++i) {
-            const uint32_t p = a + i;
-            while (p >= cend) {
-              emit_pair<G>(partial, __ldg(pair_slot + q), (G)acc, whole);
+            if (i > 0 && ((m >> i) & 1u)) {
+              if (first_run && !(m & 1u))
+                cont = acc;  // continues from the left
+              else
+                partial[__ldg(pair_slot + q)] = (G)acc;  // started and ended inside the lane
               ++q;
-              cend = __ldg(pair_start + q + 1);
               acc = V(0);
-              whole = true;
+              first_run = false;
             }
             acc = fma(cur.v[i], (V)uu[i], acc);
           }
+          if (!first_run || (m & 1u)) {
+            tail = acc;
+            has_tail = true;
+            acc = V(0);
+          }
+        }
+        if (m == 1u) {  // one run, starting at the lane's first entry
+          tail = acc;
+          has_tail = true;
+        } else if (m == 0u) {
+          cont = acc;
         }
       }
-      // a full tile inside one pair: one warp sum and one emit instead of 32
-      const uint32_t qf = __shfl_sync(0xffffffffu, q_first, 0);
-      const uint32_t ql = __shfl_sync(0xffffffffu, q, 31);
-      if (te - ts == (uint32_t)kSlabTile && qf == ql) {
-        const V sum = warp_sum(acc);
-        if (lane == 0) {
-          const bool in_tile = __ldg(pair_start + qf) >= ts && __ldg(pair_start + qf + 1) <= te;
-          emit_pair<G>(partial, __ldg(pair_slot + qf), (G)sum, in_tile);
+      const bool stop = !active || m != 0u;
+      if (__ballot_sync(FULL, stop) == 0u) {
+        // the whole tile lies inside pair q0
+        const V sum = warp_sum(cont);
+        if (lane == 0) atomicAdd(partial + slot0, (G)sum);
+      } else {
+        bool ended;
+        const V tsum = lane_suffix_sum(cont, stop, lane, ended);
+        const V t1s = __shfl_down_sync(FULL, tsum, 1);
+        const bool e1 = __shfl_down_sync(FULL, (int)ended, 1) != 0;
+        if (lead) atomicAdd(partial + slot0, (G)tsum);  // pair from the previous tile
+        if (has_tail) {
+          const V sum = tail + (lane < 31 ? t1s : V(0));
+          emit_pair<G>(partial, slot_last, (G)sum, lane < 31 && e1);
         }
-      } else if (active) {
-        emit_pair<G>(partial, __ldg(pair_slot + q), (G)acc, whole && cend <= a + kSlabItems);
       }
     }
     t0 = t1;
   }
 }
 
-// sum of each heavy column = its partials in slab order; partials reset
+// ---------------------------------------------------------------------------
+// the light columns: a compact CSC copy streamed in 256-entry tiles, u gathered
+// from L2.  Column starts are marked like pair starts above (one byte per 8
+// entries), tile_lc[t] is the light column of the tile's first entry, and the
+// same per-lane runs / segmented suffix sum assign every partial sum to its
+// column without a search; results go to out[light_cols[lc]].
+constexpr int kLightItems = 8;
+constexpr int kLightTile = 32 * kLightItems;
+
+__device__ __forceinline__ void load_rows8(const int32_t* __restrict__ p, int32_t (&r)[8]) {
+  const int4 a = __ldcs(reinterpret_cast<const int4*>(p));
+  const int4 b = __ldcs(reinterpret_cast<const int4*>(p) + 1);
+  r[0] = a.x, r[1] = a.y, r[2] = a.z, r[3] = a.w, r[4] = b.x, r[5] = b.y, r[6] = b.z, r[7] = b.w;
+}
+
+template <typename V, typename U, typename G>
+__global__ void __launch_bounds__(kThreads, 4)
+    k_propose_light_runs(const int32_t* __restrict__ row, const V* __restrict__ val,
+                         const uint8_t* __restrict__ lmask, const int32_t* __restrict__ tile_lc,
+                         const int32_t* __restrict__ light_cols, const U* __restrict__ u, int64_t nnz,
+                         int64_t ntiles, G* __restrict__ out) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = warp; t < ntiles; t += nwarps) {  // warp-uniform
+    const int64_t a = t * kLightTile + (int64_t)lane * kLightItems;
+    const bool active = a < nnz;  // the arrays are padded: a lane's 8 entries are in bounds
+    int32_t r[8];
+    V v[8];
+    uint32_t m = 0;
+    if (active) {
+      load_rows8(row + a, r);
+      load8<V>(val + a, v);
+      m = lmask[a >> 3];
+    }
+    const uint32_t lc0 = (uint32_t)__ldg(tile_lc + t);
+    const uint32_t cnt = __popc(lane == 0 ? (m & 0xfeu) : m);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, incl, d);
+      if (lane >= d) incl += y;
+    }
+    uint32_t q = lc0 + (incl - cnt) + (lane > 0 ? (m & 1u) : 0u);
+    // columns this lane may write, loaded early
+    const bool lead = lane == 0 && active && !(m & 1u);
+    const int32_t j0 = lead ? __ldg(light_cols + lc0) : 0;
+    const int32_t jl = (active && m != 0u) ? __ldg(light_cols + q + __popc(m & 0xfeu)) : 0;
+    V acc = V(0), cont = V(0), tail = V(0);
+    bool has_tail = false;
+    if (active) {
+      U uu[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) uu[i] = __ldg(u + r[i]);  // padding rows are 0, values 0
+      if (m <= 1u) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc = fma(v[i], (V)uu[i], acc);
+        if (m == 1u) {
+          tail = acc;
+          has_tail = true;
+        } else {
+          cont = acc;
+        }
+      } else {
+        bool first_run = true;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          if (i > 0 && ((m >> i) & 1u)) {
+            if (first_run && !(m & 1u))
+              cont = acc;
+            else
+              out[__ldg(light_cols + q)] = (G)acc;  // a whole column inside the lane
+            ++q;
+            acc = V(0);
+            first_run = false;
+          }
+          acc = fma(v[i], (V)uu[i], acc);
+        }
+        tail = acc;
+        has_tail = true;
+      }
+    }
+    const bool stop = !active || m != 0u;
+    if (__ballot_sync(FULL, stop) == 0u) {
+      const V sum = warp_sum(cont);  // the whole tile is inside column lc0
+      if (lane == 0) atomicAdd(out + j0, (G)sum);
+    } else {
+      bool ended;
+      const V tsum = lane_suffix_sum(cont, stop, lane, ended);
+      const V t1s = __shfl_down_sync(FULL, tsum, 1);
+      const bool e1 = __shfl_down_sync(FULL, (int)ended, 1) != 0;
+      if (lead) atomicAdd(out + j0, (G)tsum);  // column from the previous tile
+      if (has_tail) {
+        const V sum = tail + (lane < 31 ? t1s : V(0));
+        emit_pair<G>(out, (uint32_t)jl, (G)sum, lane < 31 && e1);
+      }
+    }
+  }
+}
+
+// sum of each heavy column = its partials in slab order (the slots of column h
+// are hslot_ptr[h] .. hslot_ptr[h+1]); partials reset
 template <typename G>
 __global__ void k_pairs_to_gacc(const uint32_t* __restrict__ hslot_ptr, const int32_t* __restrict__ heavy_cols,
                                 int64_t nheavy, G* __restrict__ partial, G* __restrict__ gacc) {
   const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= nheavy) return;
   G s = G(0);
-  for (uint32_t q = hslot_ptr[h]; q < hslot_ptr[h + 1]; ++q) {
-    s += partial[q];
-    partial[q] = G(0);
+  for (uint32_t x = hslot_ptr[h]; x < hslot_ptr[h + 1]; ++x) {
+    s += partial[x];
+    partial[x] = G(0);
   }
   gacc[heavy_cols[h]] = s;
 }
@@ -202,12 +368,19 @@ __global__ void k_pairs_to_gacc(const uint32_t* __restrict__ hslot_ptr, const in
 int launch_propose_plan(gencd_problem* p, const void* u_vec) {
   ProposePlan& P = p->plan;
   if (P.nlight > 0) {
-    CscView a{P.light_col_ptr, P.light_row, P.light_val, P.light_tile_col, P.light_nnz, P.light_ntiles,
-              P.light_cols};
     cudaEvent_t e = nullptr;
     prof_begin(p, K_PROPOSE_LIGHT, &e);
-    GENCD_TRY(launch_propose_light(p, a, u_vec));
+    const int grid = grid_for(P.light_ntiles * 32, kThreads, p->num_sms * 8);
+    if (p->precision == GENCD_F64)
+      k_propose_light_runs<double, double, double><<<grid, kThreads, 0, p->stream>>>(
+          P.light_row, (const double*)P.light_val, P.lmask, P.light_tile_lc, P.light_cols, (const double*)u_vec,
+          P.light_nnz, P.light_ntiles, (double*)p->gnat);
+    else
+      k_propose_light_runs<float, float, float><<<grid, kThreads, 0, p->stream>>>(
+          P.light_row, (const float*)P.light_val, P.lmask, P.light_tile_lc, P.light_cols, (const float*)u_vec,
+          P.light_nnz, P.light_ntiles, (float*)p->gnat);
     prof_end(p, e);
+    GENCD_CUDA_TRY(cudaGetLastError());
   }
   if (P.nheavy > 0) {
     const size_t smem = (size_t)P.slab_rows * (p->precision == GENCD_F64 ? 8 : 4);
@@ -216,14 +389,12 @@ int launch_propose_plan(gencd_problem* p, const void* u_vec) {
     prof_begin(p, K_PROPOSE_SLABS, &e1);
     if (p->precision == GENCD_F64)
       k_propose_slabs<double, double, double><<<P.grid, kSlabThreads, smem, p->stream>>>(
-          P.s_row, (const double*)P.s_val, P.pair_start, P.pair_slot, P.tile_start, P.tile_end, P.tile_pair,
-          P.tile_pair_last, P.tile_slab, P.slab_tile_begin, P.cta_tile_begin, (const double*)u_vec, p->n,
-          P.slab_rows, (double*)P.partial);
+          P.s_row, (const double*)P.s_val, P.pmask, P.pair_slot, P.tile_start, P.tile_end, P.tile_pair, P.tile_slab,
+          P.slab_tile_begin, P.cta_tile_begin, (const double*)u_vec, p->n, P.slab_rows, (double*)P.partial);
     else
       k_propose_slabs<float, float, float><<<P.grid, kSlabThreads, smem, p->stream>>>(
-          P.s_row, (const float*)P.s_val, P.pair_start, P.pair_slot, P.tile_start, P.tile_end, P.tile_pair,
-          P.tile_pair_last, P.tile_slab, P.slab_tile_begin, P.cta_tile_begin, (const float*)u_vec, p->n,
-          P.slab_rows, (float*)P.partial);
+          P.s_row, (const float*)P.s_val, P.pmask, P.pair_slot, P.tile_start, P.tile_end, P.tile_pair, P.tile_slab,
+          P.slab_tile_begin, P.cta_tile_begin, (const float*)u_vec, p->n, P.slab_rows, (float*)P.partial);
     prof_end(p, e1);
     prof_begin(p, K_PAIRS, &e2);
     if (p->precision == GENCD_F64)
@@ -233,7 +404,6 @@ int launch_propose_plan(gencd_problem* p, const void* u_vec) {
       k_pairs_to_gacc<float><<<g2, kThreads, 0, p->stream>>>(P.hslot_ptr, P.heavy_cols, P.nheavy,
                                                               (float*)P.partial, (float*)p->gnat);
     prof_end(p, e2);
-    p->prof.launches[K_PROPOSE_ALL] += 1;
     GENCD_CUDA_TRY(cudaGetLastError());
   }
   return GENCD_OK;
@@ -292,6 +462,17 @@ __global__ void k_plan_copy_light(const int64_t* __restrict__ col_ptr, const int
   }
 }
 
+// bit p % 32 of word p / 32 (= bit p % 8 of byte p / 8) for the first entry p of
+// every light column
+__global__ void k_plan_light_starts(const int64_t* __restrict__ light_col_ptr, int64_t nlight,
+                                    uint32_t* __restrict__ words) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nlight; c += stride) {
+    const int64_t p = light_col_ptr[c];
+    atomicOr(words + (p >> 5), 1u << (p & 31));
+  }
+}
+
 // heavy entry e (column-major order): key = slab, plus its row, value, heavy id
 template <typename V>
 __global__ void k_plan_heavy_entries(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
@@ -324,14 +505,17 @@ __global__ void k_plan_fill_slabs(const uint32_t* __restrict__ sk, const uint32_
                                   int32_t slab_rows, const uint32_t* __restrict__ hrow,
                                   const uint32_t* __restrict__ hh, const V* __restrict__ hval,
                                   uint16_t* __restrict__ s_row, V* __restrict__ s_val,
-                                  uint32_t* __restrict__ newpair) {
+                                  uint32_t* __restrict__ newpair, uint32_t* __restrict__ pmask_words) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < E; i += stride) {
     const uint32_t r = sk[i], e = se[i];
     const int64_t ip = pad_off[r] + (i - slab_begin[r]);
     s_row[ip] = (uint16_t)(hrow[e] - r * (uint32_t)slab_rows);
     s_val[ip] = hval[e];
-    newpair[i] = (i == slab_begin[r] || hh[e] != hh[se[i - 1]]) ? 1u : 0u;
+    const bool starts = i == slab_begin[r] || hh[e] != hh[se[i - 1]];
+    newpair[i] = starts ? 1u : 0u;
+    // bit ip % 32 of word ip / 32 = bit ip % 8 of byte ip / 8 (little-endian)
+    if (starts) atomicOr(pmask_words + (ip >> 5), 1u << (ip & 31));
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) newpair[E] = 0u;
 }
@@ -373,8 +557,7 @@ __global__ void k_plan_lower_bounds(const uint32_t* __restrict__ sorted, int64_t
 __global__ void k_plan_tiles(const int32_t* __restrict__ slab_tile_begin, const int64_t* __restrict__ pad_off,
                              int32_t R, int64_t T, const uint32_t* __restrict__ pair_start, int64_t npairs,
                              uint32_t* __restrict__ tile_start, uint32_t* __restrict__ tile_end,
-                             uint32_t* __restrict__ tile_pair, uint32_t* __restrict__ tile_pair_last,
-                             int32_t* __restrict__ tile_slab) {
+                             uint32_t* __restrict__ tile_pair, int32_t* __restrict__ tile_slab) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += stride) {
     int32_t lo = 0, hi = R - 1;  // slab: last r with slab_tile_begin[r] <= t
@@ -391,26 +574,23 @@ __global__ void k_plan_tiles(const int32_t* __restrict__ slab_tile_begin, const 
     tile_start[t] = (uint32_t)s;
     tile_end[t] = (uint32_t)e;
     tile_slab[t] = r;
-    for (int side = 0; side < 2; ++side) {
-      const int64_t x = side == 0 ? s : e - 1;
-      int64_t a = 0, b = npairs - 1;  // last pair with pair_start <= x
-      while (a < b) {
-        const int64_t mid = (a + b + 1) >> 1;
-        if ((int64_t)pair_start[mid] <= x)
-          a = mid;
-        else
-          b = mid - 1;
-      }
-      (side == 0 ? tile_pair : tile_pair_last)[t] = (uint32_t)a;
+    int64_t a = 0, b = npairs - 1;  // pair of the tile's first entry: last q with pair_start[q] <= s
+    while (a < b) {
+      const int64_t mid = (a + b + 1) >> 1;
+      if ((int64_t)pair_start[mid] <= s)
+        a = mid;
+      else
+        b = mid - 1;
     }
+    tile_pair[t] = (uint32_t)a;
   }
 }
 
 void free_propose_plan(gencd_problem* p) {
   ProposePlan& P = p->plan;
-  void* bufs[] = {P.light_cols, P.light_col_ptr, P.light_row, P.light_val, P.light_tile_col, P.heavy_cols,
-                  P.s_row, P.s_val, P.pair_start, P.pair_slot, P.hslot_ptr, P.partial, P.tile_start,
-                  P.tile_end, P.tile_pair, P.tile_pair_last, P.tile_slab, P.slab_tile_begin, P.cta_tile_begin};
+  void* bufs[] = {P.light_cols, P.light_col_ptr, P.light_row, P.light_val, P.light_tile_lc, P.lmask, P.heavy_cols,
+                  P.s_row, P.s_val, P.pmask, P.pair_slot, P.hslot_ptr, P.partial, P.tile_start,
+                  P.tile_end, P.tile_pair, P.tile_slab, P.slab_tile_begin, P.cta_tile_begin};
   for (void* b : bufs)
     if (b) cudaFree(b);
   P = ProposePlan();
@@ -502,10 +682,15 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
       k_plan_copy_light<float><<<grid_for(k * 32, kThreads, g), kThreads, 0, st>>>(
           p->col_ptr, p->row_idx, (const float*)p->val, k, P.heavy_min, loff, P.light_row, (float*)P.light_val);
     GENCD_CUDA_TRY(cudaGetLastError());
-    const int64_t tile = 32LL * p->items;
-    P.light_ntiles = (P.light_nnz + tile - 1) / tile;
-    GENCD_TRY(palloc(&P.light_tile_col, P.light_ntiles + 1));
-    GENCD_TRY(launch_tile_map_of(p, P.light_col_ptr, P.nlight, P.light_ntiles, P.light_tile_col));
+    P.light_ntiles = (P.light_nnz + kLightTile - 1) / kLightTile;
+    GENCD_TRY(palloc(&P.light_tile_lc, P.light_ntiles + 1));
+    GENCD_TRY(launch_tile_map_of(p, P.light_col_ptr, P.nlight, P.light_ntiles, P.light_tile_lc, kLightTile));
+    const int64_t lwords = (lpad + 31) / 32;  // start bits, one byte per 8 entries
+    GENCD_TRY(palloc((uint32_t**)&P.lmask, lwords));
+    GENCD_CUDA_TRY(cudaMemsetAsync(P.lmask, 0, 4 * (size_t)lwords, st));
+    k_plan_light_starts<<<grid_for(P.nlight, kThreads, g), kThreads, 0, st>>>(P.light_col_ptr, P.nlight,
+                                                                              (uint32_t*)P.lmask);
+    GENCD_CUDA_TRY(cudaGetLastError());
   }
   if (P.nheavy == 0) return GENCD_OK;
 
@@ -553,15 +738,20 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   GENCD_TRY(palloc((char**)&P.s_val, (P.entries + 8) * (int64_t)vsz));
   GENCD_CUDA_TRY(cudaMemsetAsync(P.s_row, 0, 2 * (P.entries + 8), st));
   GENCD_CUDA_TRY(cudaMemsetAsync(P.s_val, 0, vsz * (P.entries + 8), st));
+  // start bits: one byte per 8 entries, written as 32-bit words (entries + 8 bits, rounded up to words)
+  const int64_t mask_words = (P.entries + 8 + 31) / 32;
+  GENCD_TRY(palloc((uint32_t**)&P.pmask, mask_words));
+  GENCD_CUDA_TRY(cudaMemsetAsync(P.pmask, 0, 4 * (size_t)mask_words, st));
   uint32_t* pidx;
   GENCD_TRY(S.get(&pidx, E + 1));
   if (f64)
     k_plan_fill_slabs<double><<<grid_for(E, kThreads, g), kThreads, 0, st>>>(
         sk, se, E, slab_begin, pad_off, P.slab_rows, hrow, hh, (const double*)hval, P.s_row, (double*)P.s_val,
-        pidx);
+        pidx, (uint32_t*)P.pmask);
   else
     k_plan_fill_slabs<float><<<grid_for(E, kThreads, g), kThreads, 0, st>>>(
-        sk, se, E, slab_begin, pad_off, P.slab_rows, hrow, hh, (const float*)hval, P.s_row, (float*)P.s_val, pidx);
+        sk, se, E, slab_begin, pad_off, P.slab_rows, hrow, hh, (const float*)hval, P.s_row, (float*)P.s_val, pidx,
+        (uint32_t*)P.pmask);
   GENCD_CUDA_TRY(cudaGetLastError());
   uint32_t* ptmp;
   GENCD_TRY(S.get(&ptmp, scan_tmp_words(E + 1)));
@@ -571,20 +761,20 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   GENCD_CUDA_TRY(cudaStreamSynchronize(st));
   P.npairs = np32;
 
-  // pairs: first entry and heavy column; slots in column-major order
-  uint32_t *pair_h, *qa, *qb, *ha, *qtmp;
-  GENCD_TRY(palloc(&P.pair_start, P.npairs + 1));
+  // pairs: first entry and heavy column; the pairs of each column in slab order
+  uint32_t *pair_start, *pair_h, *qa, *qb, *ha, *qtmp;
+  GENCD_TRY(S.get(&pair_start, P.npairs + 1));
   GENCD_TRY(S.get(&pair_h, P.npairs));
   k_plan_fill_pairs<<<grid_for(E, kThreads, g), kThreads, 0, st>>>(sk, se, E, slab_begin, pad_off, hh, pidx,
-                                                                    P.pair_start, pair_h);
+                                                                    pair_start, pair_h);
   const uint32_t ent32 = (uint32_t)P.entries;
-  GENCD_CUDA_TRY(cudaMemcpyAsync(P.pair_start + P.npairs, &ent32, 4, cudaMemcpyHostToDevice, st));
+  GENCD_CUDA_TRY(cudaMemcpyAsync(pair_start + P.npairs, &ent32, 4, cudaMemcpyHostToDevice, st));
   GENCD_TRY(S.get(&qa, P.npairs));
   GENCD_TRY(S.get(&qb, P.npairs));
   GENCD_TRY(S.get(&ha, P.npairs));
   GENCD_TRY(S.get(&qtmp, (int64_t)radix_tmp_words(P.npairs)));
   GENCD_TRY(iota_u32(p, qa, P.npairs));
-  bool q_alt = false;
+  bool q_alt = false;  // stable: a column's pairs stay in slab order
   GENCD_TRY(radix_sort_with_tmp(p, pair_h, qa, P.npairs, bits_for_max(P.nheavy - 1), ha, qb, qtmp, &q_alt));
   const uint32_t* h_sorted = q_alt ? ha : pair_h;
   const uint32_t* q_sorted = q_alt ? qb : qa;
@@ -606,13 +796,11 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   GENCD_TRY(palloc(&P.tile_start, P.ntiles));
   GENCD_TRY(palloc(&P.tile_end, P.ntiles));
   GENCD_TRY(palloc(&P.tile_pair, P.ntiles));
-  GENCD_TRY(palloc(&P.tile_pair_last, P.ntiles));
   GENCD_TRY(palloc(&P.tile_slab, P.ntiles));
   GENCD_CUDA_TRY(cudaMemcpyAsync(P.slab_tile_begin, tb.data(), 4 * (R + 1), cudaMemcpyHostToDevice, st));
   k_plan_tiles<<<grid_for(P.ntiles, kThreads, g), kThreads, 0, st>>>(P.slab_tile_begin, pad_off, R, P.ntiles,
-                                                                      P.pair_start, P.npairs, P.tile_start,
-                                                                      P.tile_end, P.tile_pair, P.tile_pair_last,
-                                                                      P.tile_slab);
+                                                                      pair_start, P.npairs, P.tile_start,
+                                                                      P.tile_end, P.tile_pair, P.tile_slab);
   GENCD_CUDA_TRY(cudaGetLastError());
   P.grid = p->num_sms;
   std::vector<int32_t> ctb(P.grid + 1);
