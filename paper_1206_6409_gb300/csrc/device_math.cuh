@@ -109,47 +109,3 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 }  // namespace gencd
-
-namespace gencd {
-
-// Warp-level combination of segment sums that lane boundaries cut.
-// Each lane owns consecutive entries of a warp tile and sums them segment by
-// segment.  A segment (a column, or a slab-column pair) that continues past a
-// lane's right end forms a chain with the following lanes.  Per lane:
-//   right   the sum of its last segment if that segment continues past the
-//           lane (else 0);
-//   through the lane holds one segment that continues on both sides;
-//   starts  its right-open segment begins inside the lane.
-// The scan composes x_L = right_L + (through_L ? x_{L-1} : 0) over lanes
-// 0..L (five shuffle steps) and returns, for lane L:
-//   carry_in   x_{L-1}: the chain sum arriving at its left end;
-//   from_tile  that chain began inside this warp tile;
-//   carry_out  x_L: the chain sum leaving its right end.
-template <typename A>
-__device__ __forceinline__ void warp_chain_scan(A right, bool through, bool starts, A& carry_in, bool& from_tile,
-                                                A& carry_out) {
-  const int lane = threadIdx.x & 31;
-  A x = right;
-  bool b = through;
-  bool f = through ? false : starts;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const A xp = __shfl_up_sync(0xffffffffu, x, o);
-    const bool bp = __shfl_up_sync(0xffffffffu, b, o);
-    const bool fp = __shfl_up_sync(0xffffffffu, f, o);
-    if (lane >= o) {
-      if (b) {
-        x = x + xp;
-        f = fp;
-      }
-      b = b && bp;
-    }
-  }
-  carry_out = x;
-  const A xin = __shfl_up_sync(0xffffffffu, x, 1);
-  const bool fin = __shfl_up_sync(0xffffffffu, f, 1);
-  carry_in = lane > 0 ? xin : A(0);
-  from_tile = lane > 0 ? fin : false;
-}
-
-}  // namespace gencd

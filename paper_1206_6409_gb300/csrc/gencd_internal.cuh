@@ -218,7 +218,6 @@ constexpr int kRedBlocks = 1024;
 // kernels_propose.cu
 int launch_propose_all(gencd_problem* p, const void* u_vec, bool u_is_double);
 int launch_propose_csc(gencd_problem* p, const CscView& a, const void* u_vec, bool u_is_double);
-int launch_propose_light(gencd_problem* p, const CscView& a, const void* u_vec);  // native u, light CSC
 // propose_plan.cu
 int build_propose_plan(gencd_problem* p);
 int launch_propose_plan(gencd_problem* p, const void* u_vec);

@@ -477,115 +477,6 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// Streaming propose over the light columns (a compact CSC, column map cmap):
-// a warp owns a tile of 32*ITEMS consecutive non-zeros, a lane ITEMS of them
-// (128-bit streaming loads; u gathered through the read-only path).  The
-// tile's column boundaries and column ids are staged in shared memory, so a
-// lane finds its first column and walks its segments without global loads.
-// Sums of columns that lie inside one lane are stored; sums cut by lane
-// boundaries are combined by a warp scan; only columns cut by a tile
-// boundary use atomic adds.
-template <typename V, typename U, typename G, int ITEMS>
-__global__ void __launch_bounds__(kThreads)
-    k_propose_light(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
-                    const V* __restrict__ val, const U* __restrict__ u, const int32_t* __restrict__ tile_col,
-                    int64_t nnz, int64_t ntiles, const int32_t* __restrict__ cmap, G* __restrict__ out) {
-  constexpr int TILE = 32 * ITEMS;
-  __shared__ int32_t s_end[kThreads / 32][TILE + 2];
-  __shared__ int32_t s_col[kThreads / 32][TILE + 2];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int32_t* ends = s_end[wid];
-  int32_t* cols = s_col[wid];
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t t = warp; t < ntiles; t += nwarps) {  // warp-uniform
-    const int64_t ts = t * TILE;
-    const int tile_len = (int)(nnz - ts < TILE ? nnz - ts : TILE);
-    const int32_t cA = __ldg(tile_col + t);
-    const int32_t cB = __ldg(tile_col + t + 1);
-    const int ncols = min(cB - cA + 1, TILE + 1);
-    const int32_t s0 = (int32_t)(__ldg(col_ptr + cA) - ts);
-    __syncwarp();
-    for (int m = lane; m < ncols; m += 32) {
-      const int64_t e = __ldg(col_ptr + cA + m + 1) - ts;
-      ends[m] = (int32_t)(e < TILE + 1 ? e : TILE + 1);
-      cols[m] = __ldg(cmap + cA + m);
-    }
-    const int a = lane * ITEMS;
-    const bool active = a < tile_len;
-    const int nv = active ? min(ITEMS, tile_len - a) : 0;
-    int32_t r[ITEMS];
-    V v[ITEMS];
-    U uu[ITEMS];
-    if (active) {
-      load_idx<ITEMS>(row_idx + ts + a, r);  // padded arrays: in bounds
-      load_val<ITEMS>(val + ts + a, v);
-#pragma unroll
-      for (int i = 0; i < ITEMS; ++i) uu[i] = i < nv ? __ldg(u + r[i]) : U(0);
-    }
-    __syncwarp();
-    V acc = V(0), head = V(0), right = V(0);
-    int m = 0, m0 = 0, cend = 0;
-    bool closed = false, open_left = false, open_right = false, through = false, starts = false;
-    if (active) {
-      int lo = 0, hi = ncols - 1;  // first column whose end is past a
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (ends[mid] > a)
-          hi = mid;
-        else
-          lo = mid + 1;
-      }
-      m = m0 = lo;
-      open_left = (m == 0 ? s0 : ends[m - 1]) < a;
-      cend = ends[m];
-#pragma unroll
-      for (int i = 0; i < ITEMS; ++i) {
-        if (i < nv) {
-          const int p = a + i;
-          while (p >= cend) {  // column m closes before p
-            if (!closed && open_left)
-              head = acc;  // its earlier part is in previous lanes
-            else
-              out[cols[m]] = (G)acc;  // complete inside this lane
-            closed = true;
-            ++m;
-            cend = ends[m];
-            acc = V(0);
-          }
-          acc = fma(v[i], (V)uu[i], acc);
-        }
-      }
-      open_right = cend > a + nv;
-      if (!closed) {  // one segment in this lane
-        through = open_left && open_right;
-        if (open_right) {
-          right = acc;
-          starts = !open_left;
-        } else if (open_left) {
-          head = acc;  // the chain ends at this lane's end
-        } else {
-          out[cols[m]] = (G)acc;
-        }
-      } else if (open_right) {
-        right = acc;
-        starts = true;
-      } else {
-        out[cols[m]] = (G)acc;
-      }
-    }
-    V cin, cout;
-    bool from_tile;
-    warp_chain_scan(right, through, starts, cin, from_tile, cout);
-    if (active && open_left && !through) {  // a chain ends in this lane
-      if (from_tile)
-        out[cols[m0]] = (G)(head + cin);
-      else
-        atomicAdd(out + cols[m0], (G)(head + cin));
-    }
-    if (active && open_right && a + nv >= tile_len) atomicAdd(out + cols[m], (G)cout);  // continues past the tile
-  }
-}
 
 template <int NT>
 __device__ __forceinline__ double block_sum(double v, double* sm) {
@@ -641,8 +532,8 @@ __global__ void k_objective_final(const double* __restrict__ red, int nblocks, d
 
 static int blocks_per_sm_cap(gencd_problem* p, int per_sm) { return p->num_sms * per_sm; }
 
-// Lane-segmented streaming pass over a CSC (the whole X, or the compact copy
-// of the light columns with its column map): out[col] += X_col^T u.  With u
+// Lane-segmented streaming pass over the whole CSC: out[col] += X_col^T u
+// (the path without a row-slab plan, and the setup passes).  With u
 // in the storage precision the sums go to the native accumulator (float in
 // FP32 mode), otherwise (power iteration in FP32 mode) to the FP64 gacc.
 int launch_propose_csc(gencd_problem* p, const CscView& a, const void* u_vec, bool u_is_double) {
@@ -683,21 +574,6 @@ int launch_propose_all(gencd_problem* p, const void* u_vec, bool u_is_double) {
     prof_end(p, e2);
   }
   prof_end(p, ev);
-  return GENCD_OK;
-}
-
-int launch_propose_light(gencd_problem* p, const CscView& a, const void* u_vec) {
-  if (a.ntiles == 0) return GENCD_OK;
-  const int grid = grid_for(a.ntiles * 32, kThreads, blocks_per_sm_cap(p, 8));
-  if (p->precision == GENCD_F64)
-    k_propose_light<double, double, double, kItemsF64><<<grid, kThreads, 0, p->stream>>>(
-        a.col_ptr, a.row_idx, (const double*)a.val, (const double*)u_vec, a.tile_col, a.nnz, a.ntiles, a.cmap,
-        (double*)p->gnat);
-  else
-    k_propose_light<float, float, float, kItemsF32><<<grid, kThreads, 0, p->stream>>>(
-        a.col_ptr, a.row_idx, (const float*)a.val, (const float*)u_vec, a.tile_col, a.nnz, a.ntiles, a.cmap,
-        (float*)p->gnat);
-  GENCD_CUDA_TRY(cudaGetLastError());
   return GENCD_OK;
 }
 

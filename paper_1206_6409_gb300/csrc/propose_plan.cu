@@ -29,7 +29,8 @@
 namespace gencd {
 
 constexpr int kSlabBytes = 192 * 1024;
-constexpr int kSlabThreads = 1024;
+constexpr int kSlabThreadsF32 = 1024;  // 32 warps, the next tile's loads in flight
+constexpr int kSlabThreadsF64 = 1024;  // 32 warps, loads issued tile by tile
 constexpr int kSlabItems = 8;
 constexpr int kSlabTile = 32 * kSlabItems;
 
@@ -106,8 +107,34 @@ __device__ __forceinline__ V lane_suffix_sum(V x, bool stop, int lane, bool& end
 // from the left (cont) and the run that leaves to the right (tail) are
 // combined across the warp by a segmented suffix sum, so only the tile's first
 // and last pairs take atomic adds.
-template <typename V, typename U, typename G>
-__global__ void __launch_bounds__(kSlabThreads, 1)
+// one tile's loads for one lane: 8 rows and values, the start bits, and the
+// pair of the tile's first entry
+template <typename V>
+struct TileStage {
+  LaneLoad<V> L;
+  uint32_t m, q0;
+};
+
+template <typename V>
+__device__ __forceinline__ void load_stage(const uint16_t* __restrict__ s_row, const V* __restrict__ s_val,
+                                           const uint8_t* __restrict__ pmask,
+                                           const uint32_t* __restrict__ tile_pair, int t, int t1, uint32_t base,
+                                           int tb, uint32_t slab_end, int lane, TileStage<V>& S) {
+  S.m = 0;
+  if (t < t1) {
+    S.q0 = __ldg(tile_pair + t);
+    const uint32_t a = base + (uint32_t)(t - tb) * kSlabTile + lane * kSlabItems;
+    if (a < slab_end) {
+      load_lane(s_row, s_val, a, S.L);
+      S.m = pmask[a >> 3];
+    }
+  }
+}
+
+// THREADS per CTA (one CTA per SM); DEPTH tiles of loads in flight per warp
+// beyond the one being processed
+template <typename V, typename U, typename G, int THREADS, int DEPTH>
+__global__ void __launch_bounds__(THREADS, 1)
     k_propose_slabs(const uint16_t* __restrict__ s_row, const V* __restrict__ s_val,
                     const uint8_t* __restrict__ pmask, const uint32_t* __restrict__ pair_slot,
                     const uint32_t* __restrict__ tile_start,
@@ -115,8 +142,6 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
                     const int32_t* __restrict__ tile_slab, const int32_t* __restrict__ slab_tile_begin,
                     const int32_t* __restrict__ cta_tile_begin, const U* __restrict__ u, int64_t n,
                     int32_t slab_rows, G* __restrict__ partial) {
-  // FP32 tiles are small enough to keep the next tile's loads in flight
-  constexpr bool kPrefetch = sizeof(V) == 4;
   const unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   U* s_u = reinterpret_cast<U*>(smem_raw);
@@ -125,51 +150,32 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
   int t0 = cta_tile_begin[blockIdx.x];
   while (t0 < t_end) {
     const int r = tile_slab[t0];
-    const int t1 = min(t_end, slab_tile_begin[r + 1]);
+    const int tb = slab_tile_begin[r], tnext = slab_tile_begin[r + 1];
+    const int t1 = min(t_end, tnext);
+    const uint32_t base = tile_start[tb], slab_end = tile_end[tnext - 1];  // the slab's entries
     const int64_t row0 = (int64_t)r * slab_rows;
     const int rows = (int)min((int64_t)slab_rows, n - row0);
     __syncthreads();  // the previous slab is no longer read
     for (int i = threadIdx.x; i < rows; i += blockDim.x) s_u[i] = u[row0 + i];
     __syncthreads();
-    LaneLoad<V> nxt;
-    uint32_t nts = 0, nte = 0, nq0 = 0, nm = 0;
+    TileStage<V> stg[DEPTH > 0 ? DEPTH : 1];
     int t = t0 + warp;
-    if (kPrefetch && t < t1) {
-      nts = tile_start[t];
-      nte = tile_end[t];
-      nq0 = tile_pair[t];
-      const uint32_t a = nts + lane * kSlabItems;
-      if (a < nte) {
-        load_lane(s_row, s_val, a, nxt);
-        nm = pmask[a >> 3];
-      }
-    }
+#pragma unroll
+    for (int d = 0; d < DEPTH; ++d) load_stage(s_row, s_val, pmask, tile_pair, t + d * nw, t1, base, tb, slab_end, lane, stg[d]);
     for (; t < t1; t += nw) {  // warp-uniform loop
-      uint32_t ts, te, q0, m;
-      LaneLoad<V> cur;
-      if (kPrefetch) {
-        ts = nts, te = nte, q0 = nq0, m = nm;
-        cur = nxt;
-        const int tn = t + nw;
-        if (tn < t1) {
-          nts = tile_start[tn];
-          nte = tile_end[tn];
-          nq0 = tile_pair[tn];
-          const uint32_t an = nts + lane * kSlabItems;
-          nm = 0;
-          if (an < nte) {
-            load_lane(s_row, s_val, an, nxt);
-            nm = pmask[an >> 3];
-          }
-        }
+      TileStage<V> cur;
+      if (DEPTH > 0) {
+        cur = stg[0];
+#pragma unroll
+        for (int d = 0; d + 1 < DEPTH; ++d) stg[d] = stg[d + 1];
+        load_stage(s_row, s_val, pmask, tile_pair, t + DEPTH * nw, t1, base, tb, slab_end, lane, stg[DEPTH - 1]);
       } else {
-        ts = tile_start[t], te = tile_end[t], q0 = tile_pair[t], m = 0;
-        const uint32_t a0 = ts + lane * kSlabItems;
-        if (a0 < te) {
-          load_lane(s_row, s_val, a0, cur);
-          m = pmask[a0 >> 3];
-        }
+        load_stage(s_row, s_val, pmask, tile_pair, t, t1, base, tb, slab_end, lane, cur);
       }
+      const uint32_t ts = base + (uint32_t)(t - tb) * kSlabTile;
+      const uint32_t te = slab_end - ts < (uint32_t)kSlabTile ? slab_end : ts + kSlabTile;
+      const uint32_t q0 = cur.q0;
+      uint32_t m = cur.m;
       const uint32_t a = ts + lane * kSlabItems;
       const bool active = a < te;  // tile ends are multiples of 8
       if (!active) m = 0;
@@ -190,7 +196,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
       V acc = V(0), cont = V(0), tail = V(0);
       bool has_tail = false;
       if (active) {
-        const uint32_t w4[4] = {cur.rr.x, cur.rr.y, cur.rr.z, cur.rr.w};
+        const uint32_t w4[4] = {cur.L.rr.x, cur.L.rr.y, cur.L.rr.z, cur.L.rr.w};
         U uu[8];
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
@@ -199,7 +205,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
         }
         if (m <= 1u) {  // no pair starts after the lane's first entry (the common case)
 #pragma unroll
-          for (int i = 0; i < kSlabItems; ++i) acc = fma(cur.v[i], (V)uu[i], acc);
+          for (int i = 0; i < kSlabItems; ++i) acc = fma(cur.L.v[i], (V)uu[i], acc);
         } else {
           bool first_run = true;
 #pragma unroll
@@ -213,7 +219,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
               acc = V(0);
               first_run = false;
             }
-            acc = fma(cur.v[i], (V)uu[i], acc);
+            acc = fma(cur.L.v[i], (V)uu[i], acc);
           }
           if (!first_run || (m & 1u)) {
             tail = acc;
@@ -264,8 +270,34 @@ __device__ __forceinline__ void load_rows8(const int32_t* __restrict__ p, int32_
   r[0] = a.x, r[1] = a.y, r[2] = a.z, r[3] = a.w, r[4] = b.x, r[5] = b.y, r[6] = b.z, r[7] = b.w;
 }
 
+// one lane's loads of a light tile: 8 rows, 8 values, the start bits, and the
+// light column of the tile's first entry
+template <typename V>
+struct LightStage {
+  int32_t r[8];
+  V v[8];
+  uint32_t m, lc0;
+};
+
+template <typename V>
+__device__ __forceinline__ void load_light_stage(const int32_t* __restrict__ row, const V* __restrict__ val,
+                                                 const uint8_t* __restrict__ lmask,
+                                                 const int32_t* __restrict__ tile_lc, int64_t t, int64_t ntiles,
+                                                 int64_t nnz, int lane, LightStage<V>& S) {
+  S.m = 0;
+  if (t < ntiles) {
+    S.lc0 = (uint32_t)__ldg(tile_lc + t);
+    const int64_t a = t * kLightTile + (int64_t)lane * kLightItems;
+    if (a < nnz) {  // the arrays are padded: a lane's 8 entries are in bounds
+      load_rows8(row + a, S.r);
+      load8<V>(val + a, S.v);
+      S.m = lmask[a >> 3];
+    }
+  }
+}
+
 template <typename V, typename U, typename G>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, 3)
     k_propose_light_runs(const int32_t* __restrict__ row, const V* __restrict__ val,
                          const uint8_t* __restrict__ lmask, const int32_t* __restrict__ tile_lc,
                          const int32_t* __restrict__ light_cols, const U* __restrict__ u, int64_t nnz,
@@ -274,18 +306,16 @@ __global__ void __launch_bounds__(kThreads, 4)
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  LightStage<V> nxt;
+  load_light_stage(row, val, lmask, tile_lc, warp, ntiles, nnz, lane, nxt);
   for (int64_t t = warp; t < ntiles; t += nwarps) {  // warp-uniform
+    const LightStage<V> cur = nxt;
+    load_light_stage(row, val, lmask, tile_lc, t + nwarps, ntiles, nnz, lane, nxt);  // next tile's loads in flight
     const int64_t a = t * kLightTile + (int64_t)lane * kLightItems;
-    const bool active = a < nnz;  // the arrays are padded: a lane's 8 entries are in bounds
-    int32_t r[8];
-    V v[8];
-    uint32_t m = 0;
-    if (active) {
-      load_rows8(row + a, r);
-      load8<V>(val + a, v);
-      m = lmask[a >> 3];
-    }
-    const uint32_t lc0 = (uint32_t)__ldg(tile_lc + t);
+    const bool active = a < nnz;
+    const uint32_t m = cur.m, lc0 = cur.lc0;
+    const int32_t* r = cur.r;
+    const V* v = cur.v;
     const uint32_t cnt = __popc(lane == 0 ? (m & 0xfeu) : m);
     uint32_t incl = cnt;
 #pragma unroll
@@ -370,7 +400,7 @@ int launch_propose_plan(gencd_problem* p, const void* u_vec) {
   if (P.nlight > 0) {
     cudaEvent_t e = nullptr;
     prof_begin(p, K_PROPOSE_LIGHT, &e);
-    const int grid = grid_for(P.light_ntiles * 32, kThreads, p->num_sms * 8);
+    const int grid = grid_for(P.light_ntiles * 32, kThreads, p->num_sms * 3);  // resident CTAs: persistent warps
     if (p->precision == GENCD_F64)
       k_propose_light_runs<double, double, double><<<grid, kThreads, 0, p->stream>>>(
           P.light_row, (const double*)P.light_val, P.lmask, P.light_tile_lc, P.light_cols, (const double*)u_vec,
@@ -388,11 +418,11 @@ int launch_propose_plan(gencd_problem* p, const void* u_vec) {
     cudaEvent_t e1 = nullptr, e2 = nullptr;
     prof_begin(p, K_PROPOSE_SLABS, &e1);
     if (p->precision == GENCD_F64)
-      k_propose_slabs<double, double, double><<<P.grid, kSlabThreads, smem, p->stream>>>(
+      k_propose_slabs<double, double, double, kSlabThreadsF64, 0><<<P.grid, kSlabThreadsF64, smem, p->stream>>>(
           P.s_row, (const double*)P.s_val, P.pmask, P.pair_slot, P.tile_start, P.tile_end, P.tile_pair, P.tile_slab,
           P.slab_tile_begin, P.cta_tile_begin, (const double*)u_vec, p->n, P.slab_rows, (double*)P.partial);
     else
-      k_propose_slabs<float, float, float><<<P.grid, kSlabThreads, smem, p->stream>>>(
+      k_propose_slabs<float, float, float, kSlabThreadsF32, 1><<<P.grid, kSlabThreadsF32, smem, p->stream>>>(
           P.s_row, (const float*)P.s_val, P.pmask, P.pair_slot, P.tile_start, P.tile_end, P.tile_pair, P.tile_slab,
           P.slab_tile_begin, P.cta_tile_begin, (const float*)u_vec, p->n, P.slab_rows, (float*)P.partial);
     prof_end(p, e1);
@@ -809,10 +839,11 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   GENCD_CUDA_TRY(cudaMemcpyAsync(P.cta_tile_begin, ctb.data(), 4 * (P.grid + 1), cudaMemcpyHostToDevice, st));
   const int smem = (int)((size_t)P.slab_rows * (f64 ? 8 : 4));
   if (f64)
-    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_slabs<double, double, double>,
+    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_slabs<double, double, double, kSlabThreadsF64, 0>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   else
-    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_slabs<float, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_slabs<float, float, float, kSlabThreadsF32, 1>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         smem));
   GENCD_CUDA_TRY(cudaStreamSynchronize(st));  // scratch is freed on return
   p->prof.launches[K_SETUP] += 10;
