@@ -61,20 +61,38 @@ __global__ void k_convert(const S* __restrict__ in, int64_t m, D* __restrict__ o
 }
 
 __global__ void k_inv_beta(const double* __restrict__ c, int64_t k, double beta, int beta_mode,
-                           double* __restrict__ bj, double* __restrict__ ib) {
+                           double* __restrict__ bj, double* __restrict__ ib, float* __restrict__ bj32,
+                           float* __restrict__ ib32) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) {
     const double b = beta_mode ? beta : beta * c[j];
     bj[j] = b;
     ib[j] = b > 0.0 ? 1.0 / b : 0.0;
+    if (bj32) {
+      bj32[j] = (float)b;
+      ib32[j] = b > 0.0 ? (float)(1.0 / b) : 0.0f;
+    }
   }
+}
+
+__global__ void k_mirror_w(const double* __restrict__ w, int64_t k, float* __restrict__ w32) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) w32[j] = w_mirror(w[j]);
+}
+
+int launch_mirror_w(gencd_problem* p) {
+  if (!p->w32) return GENCD_OK;
+  k_mirror_w<<<grid_for(p->k, kThreads, p->num_sms * 8), kThreads, 0, p->stream>>>(p->w, p->k, p->w32);
+  p->prof.launches[K_SETUP] += 1;
+  GENCD_CUDA_TRY(cudaGetLastError());
+  return GENCD_OK;
 }
 
 int launch_inv_beta(gencd_problem* p) {
   if (p->ib_mode == p->params.beta_mode) return GENCD_OK;
   const double beta = p->loss == GENCD_LOSS_SQUARED ? 1.0 : 0.25;
-  k_inv_beta<<<grid_for(p->k, kThreads, p->num_sms * 8), kThreads, 0, p->stream>>>(p->c, p->k, beta,
-                                                                                     p->params.beta_mode, p->bj, p->ib);
+  k_inv_beta<<<grid_for(p->k, kThreads, p->num_sms * 8), kThreads, 0, p->stream>>>(
+      p->c, p->k, beta, p->params.beta_mode, p->bj, p->ib, p->bj32, p->ib32);
   p->prof.launches[K_SETUP] += 1;
   GENCD_CUDA_TRY(cudaGetLastError());
   p->ib_mode = p->params.beta_mode;
@@ -320,7 +338,7 @@ static void free_problem(gencd_problem* p) {
   void* bufs[] = {p->col_ptr, p->row_idx, p->val, p->y, p->z, p->u, p->w, p->c, p->ib, p->tile_col, p->gacc,
                   p->delta, p->phi, p->list_j, p->list_d, p->dscal, p->red, p->perm, p->sort_tmp,
                   p->row_ptr, p->col_idx, p->csr_val, p->color, p->color_ptr, p->cols_by_color,
-                  p->slot_m, p->slot_d, p->slot_j, p->list_off, p->scan_tmp, p->bj};
+                  p->slot_m, p->slot_d, p->slot_j, p->list_off, p->scan_tmp, p->bj, p->w32, p->bj32, p->ib32};
   if (p->stream) cudaStreamSynchronize(p->stream);
   free_propose_plan(p);
   if (p->gnat && p->gnat != p->gacc) cudaFree(p->gnat);
@@ -353,6 +371,11 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
   GENCD_TRY(dalloc(&p->c, k));
   GENCD_TRY(dalloc(&p->ib, k));
   GENCD_TRY(dalloc(&p->bj, k));
+  if (p->precision == GENCD_F32) {
+    GENCD_TRY(dalloc(&p->w32, k));
+    GENCD_TRY(dalloc(&p->bj32, k));
+    GENCD_TRY(dalloc(&p->ib32, k));
+  }
   GENCD_TRY(dalloc(&p->tile_col, p->ntiles + 1));
   GENCD_TRY(dalloc(&p->gacc, k));
   if (p->precision == GENCD_F64) {
@@ -414,6 +437,7 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
 
   GENCD_CUDA_TRY(cudaMemsetAsync(p->z, 0, sizeof(double) * n, st));
   GENCD_CUDA_TRY(cudaMemsetAsync(p->w, 0, sizeof(double) * k, st));
+  if (p->w32) GENCD_CUDA_TRY(cudaMemsetAsync(p->w32, 0, sizeof(float) * k, st));
   GENCD_CUDA_TRY(cudaMemsetAsync(p->gacc, 0, sizeof(double) * k, st));
   if (p->gnat != p->gacc) GENCD_CUDA_TRY(cudaMemsetAsync(p->gnat, 0, sizeof(float) * k, st));
   GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal, 0, 8 * sizeof(double), st));
@@ -684,6 +708,7 @@ int gencd_set_w(gencd_problem* p, const double* w, int64_t k, int32_t memory) {
       if (!std::isfinite(w[j])) return fail(GENCD_EINVAL, "w[" + std::to_string(j) + "] is not finite");
   }
   GENCD_CUDA_TRY(cudaMemcpyAsync(p->w, w, sizeof(double) * k, kind_in(memory), p->stream));
+  GENCD_TRY(launch_mirror_w(p));
   GENCD_TRY(build_csr(p));
   GENCD_TRY(launch_csr_spmv(p, p->w, p->z));
   GENCD_TRY(launch_fill_u(p));

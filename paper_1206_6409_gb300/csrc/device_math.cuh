@@ -78,6 +78,39 @@ __device__ __forceinline__ void eq7_step(double g, double wj, double lam, double
   phi = bj > 0.0 ? d * fma(0.5 * bj, d, g) + lam * dabs : -lam * fabs(wj);
 }
 
+// FP32 copy of a coefficient that is 0 exactly when the coefficient is 0
+// (values below the float range keep their sign at the smallest denormal)
+__device__ __forceinline__ float w_mirror(double x) {
+  const float f = (float)x;
+  if (f != 0.0f || x == 0.0) return f;
+  return x < 0.0 ? -__int_as_float(1) : __int_as_float(1);
+}
+
+// Eq. 7 / Eq. 9 in FP32 (the same steps as eq7_step): the FP32 mode uses it
+// to rank the columns of a partition; the accepted column's step is then
+// recomputed with eq7_step.
+__device__ __forceinline__ void eq7_step_f32(float g, float wj, float lam, float bj, float ibj, float& d,
+                                             float& phi) {
+  if (bj > 0.0f) {
+    const float t = wj * bj;
+    const float lo = g - lam, hi = g + lam;
+    d = t < lo ? -lo * ibj : (t > hi ? -hi * ibj : -wj);
+  } else {
+    d = -wj;
+  }
+  const float x = wj + d;
+  const uint32_t sw = __float_as_uint(wj), sx = __float_as_uint(x);
+  const bool keep = (sw << 1) != 0 && (((sw ^ sx) >> 31) == 0 || (sx << 1) == 0);
+  const float dabs = keep ? ((sw >> 31) ? -d : d) : fabsf(x) - fabsf(wj);
+  phi = bj > 0.0f ? d * fmaf(0.5f * bj, d, g) + lam * dabs : -lam * fabsf(wj);
+}
+
+__device__ __forceinline__ float kkt_violation_f32(float g, float wj, float lam) {
+  const uint32_t sw = __float_as_uint(wj);
+  if ((sw << 1) == 0) return fmaxf(fabsf(g) - lam, 0.0f);
+  return fabsf(g + ((sw >> 31) ? -lam : lam));
+}
+
 // KKT violation of coordinate j: max(|g| - lam, 0) if w_j = 0, else
 // |g + lam sign(w_j)|.
 __device__ __forceinline__ double kkt_violation(double g, double wj, double lam) {

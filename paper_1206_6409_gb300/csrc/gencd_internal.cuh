@@ -175,6 +175,12 @@ struct gencd_problem {
   int32_t* slot_j = nullptr;
   int64_t slot_cap = 0;
 
+  // FP32 mode: float copies of w, beta_j and 1/beta_j for the per-column
+  // selection pass (w32[j] is 0 exactly when w[j] is); null in FP64 mode
+  float* w32 = nullptr;
+  float* bj32 = nullptr;
+  float* ib32 = nullptr;
+
   // device scalars: [0] kkt bits, [1] objective, [2] loss sum, [3] l1 sum,
   // [4] updates (int64), [5] nnz processed (int64), [6] scratch
   double* dscal = nullptr;
@@ -242,6 +248,7 @@ int launch_propose_list(gencd_problem* p, const int32_t* J, int64_t m, double* d
 int launch_objective(gencd_problem* p);
 int launch_col_sumsq(gencd_problem* p);  // gacc_j = sum_i X_ij^2
 int launch_inv_beta(gencd_problem* p);   // ib_j = 1 / beta_j for the current beta_mode
+int launch_mirror_w(gencd_problem* p);   // w32 from w (FP32 mode)
 
 // kernels_update.cu
 int launch_fill_u(gencd_problem* p);

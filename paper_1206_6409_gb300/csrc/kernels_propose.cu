@@ -355,6 +355,181 @@ __global__ void __launch_bounds__(kThreads)
   if (want_kkt) block_max_bits_to(kkt_out, vmax);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 mode: the per-column pass ranks the columns with Eq. 7 / Eq. 9 in FP32
+// (FP32 sums, the float copies of w, beta_j and 1/beta_j); only the accepted
+// column's step is recomputed in FP64 (eq7_step with the FP64 w), and it is
+// accepted when that proxy is negative.  GB300 runs FP64 at a small fraction
+// of its FP32 rate, so the per-column work stays on the FP32 pipe.
+
+__device__ __forceinline__ uint64_t candidate_mag32(float phi) {
+  const uint32_t b = __float_as_uint(phi);
+  const uint32_t m = b & 0x7fffffffu;
+  return ((b >> 31) && m != 0 && m <= 0x7f800000u) ? (uint64_t)m : 0ull;
+}
+
+// one round of 4 columns per thread: load, zero the sums, integer idle test,
+// queue the active columns (j, raw sum, w) in shared memory
+__device__ __forceinline__ int scan_round_f32(float* __restrict__ gacc, const float* __restrict__ w32, int64_t base,
+                                              int64_t hi, uint32_t lnb32, int* s_n, int32_t* s_j, float* s_g,
+                                              float* s_w) {
+  float ga[kColsPerThread], wv[kColsPerThread];
+#pragma unroll
+  for (int q = 0; q < kColsPerThread; ++q) {
+    const int64_t j = base + q * kThreads + threadIdx.x;
+    ga[q] = j < hi ? gacc[j] : 0.0f;
+    wv[q] = j < hi ? w32[j] : 0.0f;
+  }
+#pragma unroll
+  for (int q = 0; q < kColsPerThread; ++q) {
+    const int64_t j = base + q * kThreads + threadIdx.x;
+    if (j >= hi) continue;
+    gacc[j] = 0.0f;
+    const bool idle = (__float_as_uint(wv[q]) << 1) == 0 && (__float_as_uint(ga[q]) & 0x7fffffffu) <= lnb32;
+    if (!idle) {
+      const int slot = atomicAdd(s_n, 1);
+      s_j[slot] = (int32_t)j;
+      s_g[slot] = ga[q];
+      s_w[slot] = wv[q];
+    }
+  }
+  __syncthreads();
+  return *s_n;
+}
+
+// FP64 step and proxy of the ranked winner (raw sum ga): the accepted delta,
+// or no acceptance (false) when that proxy is not negative
+__device__ __forceinline__ bool accept_fp64(double ga, int32_t j, double inv_n, double lam,
+                                            const double* __restrict__ w, const double* __restrict__ bjs,
+                                            const double* __restrict__ ib, double& d) {
+  double f;
+  eq7_step(ga * inv_n, w[j], lam, bjs[j], ib[j], d, f);
+  return candidate_mag(f) != 0;
+}
+
+__device__ __forceinline__ uint64_t kkt_bits_f32(uint32_t vmax32) {
+  return (uint64_t)__double_as_longlong((double)__uint_as_float(vmax32));
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_finalize_accept_f32(float* __restrict__ gacc, const float* __restrict__ w32, const float* __restrict__ bj32,
+                          const float* __restrict__ ib32, const double* __restrict__ w,
+                          const double* __restrict__ bjs, const double* __restrict__ ib, int64_t k, float inv_nf,
+                          float lamf, double inv_n, double lam, uint32_t lnb32, int64_t B, int want_kkt,
+                          int32_t* __restrict__ list_j, double* __restrict__ list_d, double* __restrict__ kkt_out) {
+  __shared__ int s_n;
+  __shared__ int32_t s_j[kRoundCols];
+  __shared__ float s_g[kRoundCols], s_w[kRoundCols];
+  __shared__ int64_t s_lo, s_hi;
+  uint32_t vmax = 0;
+  for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
+    if (threadIdx.x == 0) {  // one thread does the 64-bit divisions
+      s_lo = b * k / B;
+      s_hi = (b + 1) * k / B;
+    }
+    __syncthreads();
+    const int64_t lo = s_lo, hi = s_hi;
+    uint64_t bm = 0;
+    int32_t bj = INT32_MAX;
+    float bga = 0.0f;
+    for (int64_t base = lo; base < hi; base += kRoundCols) {  // uniform across the CTA
+      if (threadIdx.x == 0) s_n = 0;
+      __syncthreads();
+      const int na = scan_round_f32(gacc, w32, base, hi, lnb32, &s_n, s_j, s_g, s_w);
+      for (int e = threadIdx.x; e < na; e += kThreads) {
+        const int32_t j = s_j[e];
+        const float g = s_g[e] * inv_nf;
+        float d, f;
+        eq7_step_f32(g, s_w[e], lamf, bj32[j], ib32[j], d, f);
+        if (want_kkt) {
+          const uint32_t v = __float_as_uint(kkt_violation_f32(g, s_w[e], lamf));
+          vmax = v > vmax ? v : vmax;
+        }
+        const uint64_t m = candidate_mag32(f);
+        if (cand_better(m, j, bm, bj)) {
+          bm = m;
+          bj = j;
+          bga = s_g[e];
+        }
+      }
+      __syncthreads();
+    }
+    double dga = (double)bga;
+    block_best(bm, bj, dga);
+    if (threadIdx.x == 0) {
+      double d = 0.0;
+      const bool ok = bm && accept_fp64(dga, bj, inv_n, lam, w, bjs, ib, d);
+      list_j[b] = ok ? bj : -1;
+      list_d[b] = ok ? d : 0.0;
+    }
+  }
+  if (want_kkt) block_max_bits_to(kkt_out, kkt_bits_f32(vmax));
+}
+
+// few partitions, stage 1 in FP32 (see k_finalize_chunks); slot_d carries the
+// winner's raw sum, and k_accept_slots computes its FP64 step
+__global__ void __launch_bounds__(kThreads)
+    k_finalize_chunks_f32(float* __restrict__ gacc, const float* __restrict__ w32, const float* __restrict__ bj32,
+                          const float* __restrict__ ib32, int64_t k, float inv_nf, float lamf, uint32_t lnb32,
+                          int64_t B, int64_t S, int64_t nchunks, int want_kkt, uint64_t* __restrict__ slot_m,
+                          int32_t* __restrict__ slot_j, double* __restrict__ slot_d, double* __restrict__ kkt_out) {
+  __shared__ int64_t s_b[3];
+  uint32_t vmax = 0;
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int64_t lo = ch * S, hi = lo + S < k ? lo + S : k;
+    if (threadIdx.x == 0) {  // one thread does the 64-bit divisions
+      s_b[0] = partition_of(lo, k, B);
+      s_b[1] = partition_of(hi - 1, k, B);
+      s_b[2] = (s_b[0] + 1) * k / B;  // first column after partition b0
+    }
+    __syncthreads();
+    const int64_t b0 = s_b[0], b1 = s_b[1], end0 = s_b[2];
+    uint64_t m0 = 0, m1 = 0;
+    int32_t j0 = INT32_MAX, j1 = INT32_MAX;
+    float g0 = 0.0f, g1 = 0.0f;
+    for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+      const float ga = gacc[j];
+      gacc[j] = 0.0f;
+      const float wj = w32[j];
+      if ((__float_as_uint(wj) << 1) == 0 && (__float_as_uint(ga) & 0x7fffffffu) <= lnb32) continue;
+      const float g = ga * inv_nf;
+      float d, f;
+      eq7_step_f32(g, wj, lamf, bj32[j], ib32[j], d, f);
+      if (want_kkt) {
+        const uint32_t v = __float_as_uint(kkt_violation_f32(g, wj, lamf));
+        vmax = v > vmax ? v : vmax;
+      }
+      const uint64_t m = candidate_mag32(f);
+      if (j < end0) {
+        if (cand_better(m, (int32_t)j, m0, j0)) {
+          m0 = m;
+          j0 = (int32_t)j;
+          g0 = ga;
+        }
+      } else if (cand_better(m, (int32_t)j, m1, j1)) {
+        m1 = m;
+        j1 = (int32_t)j;
+        g1 = ga;
+      }
+    }
+    double d0 = (double)g0, d1 = (double)g1;
+    block_best(m0, j0, d0);
+    block_best(m1, j1, d1);
+    if (threadIdx.x == 0) {
+      slot_m[ch + b0] = m0;
+      slot_j[ch + b0] = j0;
+      slot_d[ch + b0] = d0;
+      if (b1 != b0) {
+        slot_m[ch + b1] = m1;
+        slot_j[ch + b1] = j1;
+        slot_d[ch + b1] = d1;
+      }
+    }
+    __syncthreads();
+  }
+  if (want_kkt) block_max_bits_to(kkt_out, kkt_bits_f32(vmax));
+}
+
 // Thread-Greedy with few partitions (Greedy: B = 1), stage 1: one CTA per
 // chunk of S <= floor(k / B) columns, which meets at most two partitions;
 // the best candidate of (chunk c, partition b) goes to slot c + b.
@@ -418,10 +593,13 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // stage 2: partition b reduces its slots c + b for the chunks c it meets
+// (FP32 mode: slot_d holds raw sums and the winner's step is computed here
+// in FP64 from w, bjs, ib; FP64 mode: w is null and slot_d holds the steps)
 __global__ void __launch_bounds__(kThreads)
     k_accept_slots(const uint64_t* __restrict__ slot_m, const int32_t* __restrict__ slot_j,
                    const double* __restrict__ slot_d, int64_t k, int64_t B, int64_t S,
-                   int32_t* __restrict__ list_j, double* __restrict__ list_d) {
+                   int32_t* __restrict__ list_j, double* __restrict__ list_d, const double* __restrict__ w,
+                   const double* __restrict__ bjs, const double* __restrict__ ib, double inv_n, double lam) {
   __shared__ int64_t s_c[2];
   for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
     if (threadIdx.x == 0) {  // one thread does the 64-bit divisions (FP64 unit)
@@ -444,8 +622,10 @@ __global__ void __launch_bounds__(kThreads)
     }
     block_best(bm, bj, bd);
     if (threadIdx.x == 0) {
-      list_j[b] = bm ? bj : -1;
-      list_d[b] = bm ? bd : 0.0;
+      bool ok = bm != 0;
+      if (ok && w) ok = accept_fp64(bd, bj, inv_n, lam, w, bjs, ib, bd);
+      list_j[b] = ok ? bj : -1;
+      list_d[b] = ok ? bd : 0.0;
     }
     __syncthreads();
   }
@@ -633,9 +813,9 @@ int launch_finalize_accept(gencd_problem* p, int64_t B, bool want_kkt) {
                                                                   p->lambda, b64, b32, B, want_kkt ? 1 : 0, p->list_j,
                                                                   p->list_d, p->dscal + 0);
     else
-      k_finalize_accept<float><<<grid, kThreads, 0, p->stream>>>((float*)p->gnat, p->w, p->bj, p->ib, p->k, inv_n,
-                                                                 p->lambda, b64, b32, B, want_kkt ? 1 : 0, p->list_j,
-                                                                 p->list_d, p->dscal + 0);
+      k_finalize_accept_f32<<<grid, kThreads, 0, p->stream>>>(
+          (float*)p->gnat, p->w32, p->bj32, p->ib32, p->w, p->bj, p->ib, p->k, (float)inv_n, (float)p->lambda, inv_n,
+          p->lambda, b32, B, want_kkt ? 1 : 0, p->list_j, p->list_d, p->dscal + 0);
   } else {
     int64_t S = p->k / B;  // >= 1 since B <= k; a chunk meets at most two partitions
     if (S > 4096) S = 4096;
@@ -647,12 +827,13 @@ int launch_finalize_accept(gencd_problem* p, int64_t B, bool want_kkt) {
                                                                   p->lambda, b64, b32, B, S, nchunks, want_kkt ? 1 : 0,
                                                                   p->slot_m, p->slot_j, p->slot_d, p->dscal + 0);
     else
-      k_finalize_chunks<float><<<grid, kThreads, 0, p->stream>>>((float*)p->gnat, p->w, p->bj, p->ib, p->k, inv_n,
-                                                                 p->lambda, b64, b32, B, S, nchunks, want_kkt ? 1 : 0,
-                                                                 p->slot_m, p->slot_j, p->slot_d, p->dscal + 0);
+      k_finalize_chunks_f32<<<grid, kThreads, 0, p->stream>>>((float*)p->gnat, p->w32, p->bj32, p->ib32, p->k,
+                                                              (float)inv_n, (float)p->lambda, b32, B, S, nchunks,
+                                                              want_kkt ? 1 : 0, p->slot_m, p->slot_j, p->slot_d,
+                                                              p->dscal + 0);
     const int g2 = (int)(B < (int64_t)p->num_sms * 16 ? B : (int64_t)p->num_sms * 16);
     k_accept_slots<<<g2, kThreads, 0, p->stream>>>(p->slot_m, p->slot_j, p->slot_d, p->k, B, S, p->list_j,
-                                                   p->list_d);
+                                                   p->list_d, f64 ? nullptr : p->w, p->bj, p->ib, inv_n, p->lambda);
     p->prof.launches[K_ACCEPT] += 1;
   }
   prof_end(p, ev);

@@ -44,7 +44,7 @@ __global__ void k_list_len(const int64_t* __restrict__ col_ptr, const int32_t* _
 
 // w_j += delta_j for the applied entries (distinct columns), and the counters
 __global__ void k_apply_w(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ J,
-                          const double* __restrict__ D, int64_t m, double* __restrict__ w,
+                          const double* __restrict__ D, int64_t m, double* __restrict__ w, float* __restrict__ w32,
                           unsigned long long* __restrict__ counters) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   unsigned long long upd = 0, work = 0;
@@ -52,7 +52,9 @@ __global__ void k_apply_w(const int64_t* __restrict__ col_ptr, const int32_t* __
     const int32_t j = J[e];
     const double d = D[e];
     if (j < 0 || d == 0.0) continue;
-    w[j] += d;
+    const double wn = w[j] + d;
+    w[j] = wn;
+    if (w32) w32[j] = w_mirror(wn);
     upd += 1;
     work += (unsigned long long)(col_ptr[j + 1] - col_ptr[j]);
   }
@@ -74,7 +76,7 @@ constexpr int64_t kListPlanMax = (int64_t)kListPlanThreads * kListPlanPer;
 
 __global__ void __launch_bounds__(kListPlanThreads)
     k_list_plan(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ J, const double* __restrict__ D,
-                int64_t m, double* __restrict__ w, uint32_t* __restrict__ off,
+                int64_t m, double* __restrict__ w, float* __restrict__ w32, uint32_t* __restrict__ off,
                 unsigned long long* __restrict__ counters) {
   __shared__ uint32_t s_warp[kListPlanThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -89,7 +91,9 @@ __global__ void __launch_bounds__(kListPlanThreads)
       const double d = D[e];
       if (j >= 0 && d != 0.0) {
         len[q] = (uint32_t)(col_ptr[j + 1] - col_ptr[j]);
-        w[j] += d;  // the entries name distinct columns
+        const double wn = w[j] + d;  // the entries name distinct columns
+        w[j] = wn;
+        if (w32) w32[j] = w_mirror(wn);
         ++upd;
       }
     }
@@ -200,7 +204,8 @@ template <typename V, typename U>
 __global__ void __launch_bounds__(kThreads)
     k_coloring_iter(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
                     const V* __restrict__ val, U* __restrict__ u, double* __restrict__ w,
-                    const double* __restrict__ bjs, const double* __restrict__ ib, double* __restrict__ z,
+                    float* __restrict__ w32, const double* __restrict__ bjs, const double* __restrict__ ib,
+                    double* __restrict__ z,
                     const double* __restrict__ y, const int32_t* __restrict__ perm, int64_t q,
                     const int32_t* __restrict__ color_ptr, const int32_t* __restrict__ cols_by_color,
                     double n, double lam, int loss,
@@ -229,7 +234,10 @@ __global__ void __launch_bounds__(kThreads)
         z[i] = zi;
         u[i] = u_value<U>(loss, y[i], zi);
       }
-      if (lane == 0) w[j] = wj + d;
+      if (lane == 0) {
+        w[j] = wj + d;
+        if (w32) w32[j] = w_mirror(wj + d);
+      }
       upd += 1;
       work += (unsigned long long)(t - s);
     }
@@ -281,11 +289,11 @@ int launch_update_list(gencd_problem* p, const int32_t* J, const double* d, int6
   const bool one_cta = m <= kListPlanMax;
   prof_begin(p, K_UPDATE, &ev, one_cta ? 2 : 3);  // plan kernel(s) and the scatter (+ the scan)
   if (one_cta) {
-    k_list_plan<<<1, kListPlanThreads, 0, p->stream>>>(p->col_ptr, J, d, m, p->w, p->list_off, ctr);
+    k_list_plan<<<1, kListPlanThreads, 0, p->stream>>>(p->col_ptr, J, d, m, p->w, p->w32, p->list_off, ctr);
   } else {
     k_list_len<<<grid_for(m + 1, kThreads, g), kThreads, 0, p->stream>>>(p->col_ptr, J, d, m, p->list_off);
     GENCD_TRY(exclusive_scan(p, p->list_off, p->list_off, m + 1, p->scan_tmp));
-    k_apply_w<<<grid_for(m, kThreads, g), kThreads, 0, p->stream>>>(p->col_ptr, J, d, m, p->w, ctr);
+    k_apply_w<<<grid_for(m, kThreads, g), kThreads, 0, p->stream>>>(p->col_ptr, J, d, m, p->w, p->w32, ctr);
   }
   if (p->precision == GENCD_F64)
     k_update_flat<double><<<g, kThreads, 0, p->stream>>>(p->col_ptr, p->row_idx, (const double*)p->val, J, d,
@@ -323,11 +331,11 @@ int launch_coloring_iter(gencd_problem* p, int64_t q) {
   prof_begin(p, K_COLOR_ITER, &ev);
   if (p->precision == GENCD_F64)
     k_coloring_iter<double, double><<<grid, kThreads, 0, p->stream>>>(
-        p->col_ptr, p->row_idx, (const double*)p->val, (double*)p->u, p->w, p->bj, p->ib, p->z, p->y, p->perm, q,
+        p->col_ptr, p->row_idx, (const double*)p->val, (double*)p->u, p->w, p->w32, p->bj, p->ib, p->z, p->y, p->perm, q,
         p->color_ptr, p->cols_by_color, (double)p->n, p->lambda, p->loss, ctr);
   else
     k_coloring_iter<float, float><<<grid, kThreads, 0, p->stream>>>(
-        p->col_ptr, p->row_idx, (const float*)p->val, (float*)p->u, p->w, p->bj, p->ib, p->z, p->y, p->perm, q,
+        p->col_ptr, p->row_idx, (const float*)p->val, (float*)p->u, p->w, p->w32, p->bj, p->ib, p->z, p->y, p->perm, q,
         p->color_ptr, p->cols_by_color, (double)p->n, p->lambda, p->loss, ctr);
   prof_end(p, ev);
   GENCD_CUDA_TRY(cudaGetLastError());

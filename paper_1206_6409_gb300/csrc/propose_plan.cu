@@ -31,30 +31,31 @@ namespace gencd {
 constexpr int kSlabBytes = 192 * 1024;
 constexpr int kSlabThreadsF32 = 1024;  // 32 warps, the next tile's loads in flight
 constexpr int kSlabThreadsF64 = 1024;  // 32 warps, loads issued tile by tile
-constexpr int kSlabItems = 8;
-constexpr int kSlabTile = 32 * kSlabItems;
+constexpr int kSlabItemsF32 = 8;   // entries per lane and tile step
+constexpr int kSlabItemsF64 = 8;
+constexpr int kSlabPad = 16;       // slab entry ranges are padded to this
 
 // ---------------------------------------------------------------------------
 // the kernel
 
-template <typename V>
-__device__ __forceinline__ void load8(const V* __restrict__ p, V (&v)[8]);
-
-template <>
-__device__ __forceinline__ void load8<float>(const float* __restrict__ p, float (&v)[8]) {
-  const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
-  const float4 b = __ldcs(reinterpret_cast<const float4*>(p) + 1);
-  v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+template <typename V, int N>
+__device__ __forceinline__ void load_vals(const V* __restrict__ p, V (&v)[N]) {
+  constexpr int PER = 16 / (int)sizeof(V);  // values per 128-bit load
+#pragma unroll
+  for (int q = 0; q < N / PER; ++q) {
+    if (sizeof(V) == 4) {
+      const float4 x = __ldcs(reinterpret_cast<const float4*>(p) + q);
+      v[4 * q] = (V)x.x, v[4 * q + 1] = (V)x.y, v[4 * q + 2] = (V)x.z, v[4 * q + 3] = (V)x.w;
+    } else {
+      const double2 x = __ldcs(reinterpret_cast<const double2*>(p) + q);
+      v[2 * q] = (V)x.x, v[2 * q + 1] = (V)x.y;
+    }
+  }
 }
 
-template <>
-__device__ __forceinline__ void load8<double>(const double* __restrict__ p, double (&v)[8]) {
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const double2 x = __ldcs(reinterpret_cast<const double2*>(p) + q);
-    v[2 * q] = x.x;
-    v[2 * q + 1] = x.y;
-  }
+template <typename V>
+__device__ __forceinline__ void load8(const V* __restrict__ p, V (&v)[8]) {
+  load_vals<V, 8>(p, v);
 }
 
 template <typename G>
@@ -65,18 +66,26 @@ __device__ __forceinline__ void emit_pair(G* __restrict__ partial, uint32_t slot
     atomicAdd(partial + slot, s);
 }
 
-// the entries of one lane: 8 in-slab rows (one 128-bit load) and 8 values
-template <typename V>
+// the entries of one lane: ITEMS in-slab rows (128-bit loads of 8) and values
+template <typename V, int ITEMS>
 struct LaneLoad {
-  uint4 rr;
-  V v[8];
+  uint4 rr[ITEMS / 8];
+  V v[ITEMS];
 };
 
-template <typename V>
+template <typename V, int ITEMS>
 __device__ __forceinline__ void load_lane(const uint16_t* __restrict__ s_row, const V* __restrict__ s_val,
-                                          uint32_t a, LaneLoad<V>& L) {
-  L.rr = __ldcs(reinterpret_cast<const uint4*>(s_row + a));
-  load8<V>(s_val + a, L.v);
+                                          uint32_t a, LaneLoad<V, ITEMS>& L) {
+#pragma unroll
+  for (int h = 0; h < ITEMS / 8; ++h) L.rr[h] = __ldcs(reinterpret_cast<const uint4*>(s_row + a) + h);
+  load_vals<V, ITEMS>(s_val + a, L.v);
+}
+
+// start bits of a lane's ITEMS entries (one byte per 8 entries, little-endian)
+template <int ITEMS>
+__device__ __forceinline__ uint32_t lane_mask(const uint8_t* __restrict__ pmask, uint32_t a) {
+  if (ITEMS == 16) return reinterpret_cast<const uint16_t*>(pmask)[a >> 4];
+  return pmask[a >> 3];
 }
 
 // Segmented suffix sum over the lanes: T_L = x_L + x_{L+1} + ... + x_M where M
@@ -107,33 +116,34 @@ __device__ __forceinline__ V lane_suffix_sum(V x, bool stop, int lane, bool& end
 // from the left (cont) and the run that leaves to the right (tail) are
 // combined across the warp by a segmented suffix sum, so only the tile's first
 // and last pairs take atomic adds.
-// one tile's loads for one lane: 8 rows and values, the start bits, and the
-// pair of the tile's first entry
-template <typename V>
+// one tile's loads for one lane: ITEMS rows and values, the start bits, and
+// the pair of the tile's first entry
+template <typename V, int ITEMS>
 struct TileStage {
-  LaneLoad<V> L;
+  LaneLoad<V, ITEMS> L;
   uint32_t m, q0;
 };
 
-template <typename V>
+template <typename V, int ITEMS>
 __device__ __forceinline__ void load_stage(const uint16_t* __restrict__ s_row, const V* __restrict__ s_val,
                                            const uint8_t* __restrict__ pmask,
                                            const uint32_t* __restrict__ tile_pair, int t, int t1, uint32_t base,
-                                           int tb, uint32_t slab_end, int lane, TileStage<V>& S) {
+                                           int tb, uint32_t slab_end, int lane, TileStage<V, ITEMS>& S) {
   S.m = 0;
   if (t < t1) {
     S.q0 = __ldg(tile_pair + t);
-    const uint32_t a = base + (uint32_t)(t - tb) * kSlabTile + lane * kSlabItems;
+    const uint32_t a = base + (uint32_t)(t - tb) * (32 * ITEMS) + lane * ITEMS;
     if (a < slab_end) {
-      load_lane(s_row, s_val, a, S.L);
-      S.m = pmask[a >> 3];
+      load_lane<V, ITEMS>(s_row, s_val, a, S.L);
+      S.m = lane_mask<ITEMS>(pmask, a);
     }
   }
 }
 
-// THREADS per CTA (one CTA per SM); DEPTH tiles of loads in flight per warp
-// beyond the one being processed
-template <typename V, typename U, typename G, int THREADS, int DEPTH>
+// THREADS per CTA (one CTA per SM); ITEMS entries per lane (a tile is 32 *
+// ITEMS entries); DEPTH tiles of loads in flight per warp beyond the one
+// being processed
+template <typename V, typename U, typename G, int THREADS, int DEPTH, int ITEMS>
 __global__ void __launch_bounds__(THREADS, 1)
     k_propose_slabs(const uint16_t* __restrict__ s_row, const V* __restrict__ s_val,
                     const uint8_t* __restrict__ pmask, const uint32_t* __restrict__ pair_slot,
@@ -142,6 +152,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const int32_t* __restrict__ tile_slab, const int32_t* __restrict__ slab_tile_begin,
                     const int32_t* __restrict__ cta_tile_begin, const U* __restrict__ u, int64_t n,
                     int32_t slab_rows, G* __restrict__ partial) {
+  constexpr int TILE = 32 * ITEMS;
+  constexpr uint32_t NOT_FIRST = ((1u << ITEMS) - 1u) & ~1u;  // start bits after a lane's first entry
   const unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   U* s_u = reinterpret_cast<U*>(smem_raw);
@@ -158,29 +170,31 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncthreads();  // the previous slab is no longer read
     for (int i = threadIdx.x; i < rows; i += blockDim.x) s_u[i] = u[row0 + i];
     __syncthreads();
-    TileStage<V> stg[DEPTH > 0 ? DEPTH : 1];
+    TileStage<V, ITEMS> stg[DEPTH > 0 ? DEPTH : 1];
     int t = t0 + warp;
 #pragma unroll
-    for (int d = 0; d < DEPTH; ++d) load_stage(s_row, s_val, pmask, tile_pair, t + d * nw, t1, base, tb, slab_end, lane, stg[d]);
+    for (int d = 0; d < DEPTH; ++d)
+      load_stage<V, ITEMS>(s_row, s_val, pmask, tile_pair, t + d * nw, t1, base, tb, slab_end, lane, stg[d]);
     for (; t < t1; t += nw) {  // warp-uniform loop
-      TileStage<V> cur;
+      TileStage<V, ITEMS> cur;
       if (DEPTH > 0) {
         cur = stg[0];
 #pragma unroll
         for (int d = 0; d + 1 < DEPTH; ++d) stg[d] = stg[d + 1];
-        load_stage(s_row, s_val, pmask, tile_pair, t + DEPTH * nw, t1, base, tb, slab_end, lane, stg[DEPTH - 1]);
+        load_stage<V, ITEMS>(s_row, s_val, pmask, tile_pair, t + DEPTH * nw, t1, base, tb, slab_end, lane,
+                             stg[DEPTH - 1]);
       } else {
-        load_stage(s_row, s_val, pmask, tile_pair, t, t1, base, tb, slab_end, lane, cur);
+        load_stage<V, ITEMS>(s_row, s_val, pmask, tile_pair, t, t1, base, tb, slab_end, lane, cur);
       }
-      const uint32_t ts = base + (uint32_t)(t - tb) * kSlabTile;
-      const uint32_t te = slab_end - ts < (uint32_t)kSlabTile ? slab_end : ts + kSlabTile;
+      const uint32_t ts = base + (uint32_t)(t - tb) * TILE;
+      const uint32_t te = slab_end - ts < (uint32_t)TILE ? slab_end : ts + TILE;
       const uint32_t q0 = cur.q0;
       uint32_t m = cur.m;
-      const uint32_t a = ts + lane * kSlabItems;
-      const bool active = a < te;  // tile ends are multiples of 8
+      const uint32_t a = ts + lane * ITEMS;
+      const bool active = a < te;  // slab ends are multiples of ITEMS
       if (!active) m = 0;
       // pair of the lane's first entry: q0 + start bits in (ts, a] of the tile
-      const uint32_t cnt = __popc(lane == 0 ? (m & 0xfeu) : m);
+      const uint32_t cnt = __popc(lane == 0 ? (m & NOT_FIRST) : m);
       uint32_t incl = cnt;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
@@ -192,24 +206,33 @@ __global__ void __launch_bounds__(THREADS, 1)
       // tile's first pair (lane 0) and the pair of the lane's last run
       const bool lead = lane == 0 && active && !(m & 1u);
       const uint32_t slot0 = lead ? __ldg(pair_slot + q0) : 0u;
-      const uint32_t slot_last = (active && m != 0u) ? __ldg(pair_slot + q + __popc(m & 0xfeu)) : 0u;
+      const uint32_t slot_last = (active && m != 0u) ? __ldg(pair_slot + q + __popc(m & NOT_FIRST)) : 0u;
       V acc = V(0), cont = V(0), tail = V(0);
       bool has_tail = false;
       if (active) {
-        const uint32_t w4[4] = {cur.L.rr.x, cur.L.rr.y, cur.L.rr.z, cur.L.rr.w};
-        U uu[8];
+        U uu[ITEMS];
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          uu[2 * h] = s_u[w4[h] & 0xffffu];
-          uu[2 * h + 1] = s_u[w4[h] >> 16];
+        for (int h = 0; h < ITEMS / 8; ++h) {
+          const uint32_t w4[4] = {cur.L.rr[h].x, cur.L.rr[h].y, cur.L.rr[h].z, cur.L.rr[h].w};
+#pragma unroll
+          for (int k2 = 0; k2 < 4; ++k2) {
+            uu[8 * h + 2 * k2] = s_u[w4[k2] & 0xffffu];
+            uu[8 * h + 2 * k2 + 1] = s_u[w4[k2] >> 16];
+          }
         }
         if (m <= 1u) {  // no pair starts after the lane's first entry (the common case)
 #pragma unroll
-          for (int i = 0; i < kSlabItems; ++i) acc = fma(cur.L.v[i], (V)uu[i], acc);
+          for (int i = 0; i < ITEMS; ++i) acc = fma(cur.L.v[i], (V)uu[i], acc);
+          if (m == 1u) {  // one run, starting at the lane's first entry
+            tail = acc;
+            has_tail = true;
+          } else {
+            cont = acc;
+          }
         } else {
           bool first_run = true;
 #pragma unroll
-          for (int i = 0; i < kSlabItems; ++i) {
+          for (int i = 0; i < ITEMS; ++i) {
             if (i > 0 && ((m >> i) & 1u)) {
               if (first_run && !(m & 1u))
                 cont = acc;  // continues from the left
@@ -221,17 +244,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             acc = fma(cur.L.v[i], (V)uu[i], acc);
           }
-          if (!first_run || (m & 1u)) {
-            tail = acc;
-            has_tail = true;
-            acc = V(0);
-          }
-        }
-        if (m == 1u) {  // one run, starting at the lane's first entry
-          tail = acc;
+          tail = acc;  // the last run started inside the lane
           has_tail = true;
-        } else if (m == 0u) {
-          cont = acc;
         }
       }
       const bool stop = !active || m != 0u;
@@ -418,11 +432,11 @@ int launch_propose_plan(gencd_problem* p, const void* u_vec) {
     cudaEvent_t e1 = nullptr, e2 = nullptr;
     prof_begin(p, K_PROPOSE_SLABS, &e1);
     if (p->precision == GENCD_F64)
-      k_propose_slabs<double, double, double, kSlabThreadsF64, 0><<<P.grid, kSlabThreadsF64, smem, p->stream>>>(
+      k_propose_slabs<double, double, double, kSlabThreadsF64, 0, kSlabItemsF64><<<P.grid, kSlabThreadsF64, smem, p->stream>>>(
           P.s_row, (const double*)P.s_val, P.pmask, P.pair_slot, P.tile_start, P.tile_end, P.tile_pair, P.tile_slab,
           P.slab_tile_begin, P.cta_tile_begin, (const double*)u_vec, p->n, P.slab_rows, (double*)P.partial);
     else
-      k_propose_slabs<float, float, float, kSlabThreadsF32, 1><<<P.grid, kSlabThreadsF32, smem, p->stream>>>(
+      k_propose_slabs<float, float, float, kSlabThreadsF32, 1, kSlabItemsF32><<<P.grid, kSlabThreadsF32, smem, p->stream>>>(
           P.s_row, (const float*)P.s_val, P.pmask, P.pair_slot, P.tile_start, P.tile_end, P.tile_pair, P.tile_slab,
           P.slab_tile_begin, P.cta_tile_begin, (const float*)u_vec, p->n, P.slab_rows, (float*)P.partial);
     prof_end(p, e1);
@@ -585,7 +599,8 @@ __global__ void k_plan_lower_bounds(const uint32_t* __restrict__ sorted, int64_t
 }
 
 __global__ void k_plan_tiles(const int32_t* __restrict__ slab_tile_begin, const int64_t* __restrict__ pad_off,
-                             int32_t R, int64_t T, const uint32_t* __restrict__ pair_start, int64_t npairs,
+                             int32_t R, int64_t T, int64_t tile, const uint32_t* __restrict__ pair_start,
+                             int64_t npairs,
                              uint32_t* __restrict__ tile_start, uint32_t* __restrict__ tile_end,
                              uint32_t* __restrict__ tile_pair, int32_t* __restrict__ tile_slab) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -599,8 +614,8 @@ __global__ void k_plan_tiles(const int32_t* __restrict__ slab_tile_begin, const 
         hi = mid - 1;
     }
     const int32_t r = lo;
-    const int64_t s = pad_off[r] + (t - slab_tile_begin[r]) * (int64_t)kSlabTile;
-    const int64_t e = s + kSlabTile < pad_off[r + 1] ? s + kSlabTile : pad_off[r + 1];
+    const int64_t s = pad_off[r] + (t - slab_tile_begin[r]) * tile;
+    const int64_t e = s + tile < pad_off[r + 1] ? s + tile : pad_off[r + 1];
     tile_start[t] = (uint32_t)s;
     tile_end[t] = (uint32_t)e;
     tile_slab[t] = r;
@@ -759,7 +774,7 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   GENCD_CUDA_TRY(cudaMemcpyAsync(hb.data(), slab_begin, 8 * (R + 1), cudaMemcpyDeviceToHost, st));
   GENCD_CUDA_TRY(cudaStreamSynchronize(st));
   hp[0] = 0;
-  for (int r = 0; r < R; ++r) hp[r + 1] = hp[r] + ((hb[r + 1] - hb[r] + kSlabItems - 1) / kSlabItems) * kSlabItems;
+  for (int r = 0; r < R; ++r) hp[r + 1] = hp[r] + ((hb[r + 1] - hb[r] + kSlabPad - 1) / kSlabPad) * kSlabPad;
   P.entries = hp[R];
   if (P.entries >= (int64_t(1) << 32)) return fail_plan("heavy entries exceed 2^32");
   GENCD_CUDA_TRY(cudaMemcpyAsync(pad_off, hp.data(), 8 * (R + 1), cudaMemcpyHostToDevice, st));
@@ -820,7 +835,8 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   // tiles inside each slab, and contiguous runs of tiles per CTA
   std::vector<int32_t> tb(R + 1);
   tb[0] = 0;
-  for (int r = 0; r < R; ++r) tb[r + 1] = tb[r] + (int32_t)((hp[r + 1] - hp[r] + kSlabTile - 1) / kSlabTile);
+  const int64_t tile = 32LL * (f64 ? kSlabItemsF64 : kSlabItemsF32);  // the kernel's tile
+  for (int r = 0; r < R; ++r) tb[r + 1] = tb[r] + (int32_t)((hp[r + 1] - hp[r] + tile - 1) / tile);
   P.ntiles = tb[R];
   GENCD_TRY(palloc(&P.slab_tile_begin, R + 1));
   GENCD_TRY(palloc(&P.tile_start, P.ntiles));
@@ -828,7 +844,7 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   GENCD_TRY(palloc(&P.tile_pair, P.ntiles));
   GENCD_TRY(palloc(&P.tile_slab, P.ntiles));
   GENCD_CUDA_TRY(cudaMemcpyAsync(P.slab_tile_begin, tb.data(), 4 * (R + 1), cudaMemcpyHostToDevice, st));
-  k_plan_tiles<<<grid_for(P.ntiles, kThreads, g), kThreads, 0, st>>>(P.slab_tile_begin, pad_off, R, P.ntiles,
+  k_plan_tiles<<<grid_for(P.ntiles, kThreads, g), kThreads, 0, st>>>(P.slab_tile_begin, pad_off, R, P.ntiles, tile,
                                                                       pair_start, P.npairs, P.tile_start,
                                                                       P.tile_end, P.tile_pair, P.tile_slab);
   GENCD_CUDA_TRY(cudaGetLastError());
@@ -839,10 +855,10 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   GENCD_CUDA_TRY(cudaMemcpyAsync(P.cta_tile_begin, ctb.data(), 4 * (P.grid + 1), cudaMemcpyHostToDevice, st));
   const int smem = (int)((size_t)P.slab_rows * (f64 ? 8 : 4));
   if (f64)
-    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_slabs<double, double, double, kSlabThreadsF64, 0>,
+    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_slabs<double, double, double, kSlabThreadsF64, 0, kSlabItemsF64>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   else
-    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_slabs<float, float, float, kSlabThreadsF32, 1>,
+    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_slabs<float, float, float, kSlabThreadsF32, 1, kSlabItemsF32>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         smem));
   GENCD_CUDA_TRY(cudaStreamSynchronize(st));  // scratch is freed on return

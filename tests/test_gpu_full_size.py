@@ -57,7 +57,8 @@ def test_config2_propose_sampled(full, precision):
         d_l, f_l = p.propose_at(sample)
         assert_steps_close(prob, z, w, lam, sample, d_l, f_l, d_cpu, f_cpu, TOL[precision])
         # one Thread-Greedy iteration as the benchmark runs it: every accepted
-        # column is the best proxy of its partition, and w moved only there
+        # column is the best proxy of its partition (FP32 mode ranks with FP32
+        # proxies: best up to their rounding), and w moved only there
         p.iterate(1)
         w1 = p.w()
         moved = np.flatnonzero(w1 != w)
@@ -68,4 +69,9 @@ def test_config2_propose_sampled(full, precision):
         for j, b in zip(moved[:50], part[:50]):
             lo, hi = b * prob.k // B, (b + 1) * prob.k // B
             assert lo <= j < hi
-            assert f_all[j] == f_all[lo:hi].min() and f_all[j] < 0
+            fmin = f_all[lo:hi].min()
+            assert f_all[j] < 0
+            if precision == "f64":
+                assert f_all[j] == fmin
+            else:
+                assert f_all[j] <= fmin + 1e-4 * abs(fmin)

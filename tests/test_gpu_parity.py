@@ -262,6 +262,39 @@ def test_f32_solve_reaches_the_optimum(gb):
     assert r.objective == pytest.approx(orc.objective(w_opt), rel=1e-6)
 
 
+@pytest.mark.parametrize("variant,B", [("greedy", 1), ("thread_greedy", 7), ("thread_greedy", 1024)])
+def test_f32_accepts_the_best_proxy(gb, variant, B):
+    # FP32 mode ranks columns with FP32 proxies and applies the winner's FP64
+    # step: each partition's accepted column has the partition's best proxy up
+    # to FP32 rounding, its step is the FP64 Eq. 7 step, and nothing else moves
+    prob = workloads.config2_scaled(0.01, "logistic")
+    orc = oracle.Oracle(prob)
+    lam = 0.05 * orc.lambda_max()
+    orc.set_lambda(lam)
+    w = _state(prob, 11, frac=0.05, scale=0.3)
+    z = orc.fitted(w)
+    with gb.Problem(prob, precision="f32") as p:
+        p.set_lambda(lam)
+        p.set_params(variant=variant, blocks=B)
+        p.set_w(w)
+        _, f_all, _ = p.propose_all()
+        p.iterate(1)
+        w1 = p.w()
+    moved = np.flatnonzero(w1 != w)
+    Bp = 1 if variant == "greedy" else B
+    bounds = (np.arange(Bp + 1, dtype=np.int64) * prob.k) // Bp
+    part = np.searchsorted(bounds, moved, side="right") - 1
+    assert moved.size > 0 and np.unique(part).size == part.size
+    J = moved.astype(np.int32)
+    d_cpu, _ = orc.propose(w, z, J)
+    S, bj = _scales(prob, z, lam)
+    for j, b, dc in zip(moved, part, d_cpu):
+        fmin = f_all[bounds[b]:bounds[b + 1]].min()
+        assert f_all[j] < 0 and f_all[j] <= fmin + 1e-4 * abs(fmin)
+        sd = abs(dc) + (S[j] / bj[j] if bj[j] > 0 else abs(w[j]))
+        assert abs((w1[j] - w[j]) - dc) <= TOL["f32"] * sd
+
+
 def test_edge_cases(gb):
     # one column, one row, all-empty columns, lambda above lambda_max
     X = np.array([[2.0]])
