@@ -157,11 +157,13 @@ __device__ __forceinline__ bool cand_better(uint64_t ma, int32_t ja, uint64_t mb
   return ma > mb || (ma == mb && ma != 0 && ja < jb);
 }
 
-// block reduction of the best candidate (mag, j, delta); valid in thread 0
+// block reduction of the best candidate (mag, j, delta) over NT threads;
+// valid in thread 0
+template <int NT = kThreads>
 __device__ __forceinline__ void block_best(uint64_t& m, int32_t& j, double& d) {
-  __shared__ uint64_t s_m[kThreads / 32];
-  __shared__ double s_d[kThreads / 32];
-  __shared__ int32_t s_j[kThreads / 32];
+  __shared__ uint64_t s_m[NT / 32];
+  __shared__ double s_d[NT / 32];
+  __shared__ int32_t s_j[NT / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const uint64_t xm = __shfl_xor_sync(0xffffffffu, m, o);
@@ -182,7 +184,7 @@ __device__ __forceinline__ void block_best(uint64_t& m, int32_t& j, double& d) {
   }
   __syncthreads();
   if (threadIdx.x == 0)
-    for (int q = 1; q < kThreads / 32; ++q)
+    for (int q = 1; q < NT / 32; ++q)
       if (cand_better(s_m[q], s_j[q], m, j)) {
         m = s_m[q];
         j = s_j[q];
@@ -368,21 +370,21 @@ __device__ __forceinline__ uint64_t candidate_mag32(float phi) {
   return ((b >> 31) && m != 0 && m <= 0x7f800000u) ? (uint64_t)m : 0ull;
 }
 
-// one round of 4 columns per thread: load, zero the sums, integer idle test,
-// queue the active columns (j, raw sum, w) in shared memory
+// one round of 4 columns per thread of NT: load, zero the sums, integer idle
+// test, queue the active columns (j, raw sum) in shared memory
+template <int NT>
 __device__ __forceinline__ int scan_round_f32(float* __restrict__ gacc, const float* __restrict__ w32, int64_t base,
-                                              int64_t hi, uint32_t lnb32, int* s_n, int32_t* s_j, float* s_g,
-                                              float* s_w) {
+                                              int64_t hi, uint32_t lnb32, int* s_n, int32_t* s_j, float* s_g) {
   float ga[kColsPerThread], wv[kColsPerThread];
 #pragma unroll
   for (int q = 0; q < kColsPerThread; ++q) {
-    const int64_t j = base + q * kThreads + threadIdx.x;
+    const int64_t j = base + q * NT + threadIdx.x;
     ga[q] = j < hi ? gacc[j] : 0.0f;
     wv[q] = j < hi ? w32[j] : 0.0f;
   }
 #pragma unroll
   for (int q = 0; q < kColsPerThread; ++q) {
-    const int64_t j = base + q * kThreads + threadIdx.x;
+    const int64_t j = base + q * NT + threadIdx.x;
     if (j >= hi) continue;
     gacc[j] = 0.0f;
     const bool idle = (__float_as_uint(wv[q]) << 1) == 0 && (__float_as_uint(ga[q]) & 0x7fffffffu) <= lnb32;
@@ -390,7 +392,6 @@ __device__ __forceinline__ int scan_round_f32(float* __restrict__ gacc, const fl
       const int slot = atomicAdd(s_n, 1);
       s_j[slot] = (int32_t)j;
       s_g[slot] = ga[q];
-      s_w[slot] = wv[q];
     }
   }
   __syncthreads();
@@ -411,15 +412,18 @@ __device__ __forceinline__ uint64_t kkt_bits_f32(uint32_t vmax32) {
   return (uint64_t)__double_as_longlong((double)__uint_as_float(vmax32));
 }
 
-__global__ void __launch_bounds__(kThreads)
+constexpr int kFinThreads = 1024;  // one round of 4096 columns covers a partition of config 2
+
+__global__ void __launch_bounds__(kFinThreads)
     k_finalize_accept_f32(float* __restrict__ gacc, const float* __restrict__ w32, const float* __restrict__ bj32,
                           const float* __restrict__ ib32, const double* __restrict__ w,
                           const double* __restrict__ bjs, const double* __restrict__ ib, int64_t k, float inv_nf,
                           float lamf, double inv_n, double lam, uint32_t lnb32, int64_t B, int want_kkt,
                           int32_t* __restrict__ list_j, double* __restrict__ list_d, double* __restrict__ kkt_out) {
+  constexpr int ROUND = kColsPerThread * kFinThreads;
   __shared__ int s_n;
-  __shared__ int32_t s_j[kRoundCols];
-  __shared__ float s_g[kRoundCols], s_w[kRoundCols];
+  __shared__ int32_t s_j[ROUND];
+  __shared__ float s_g[ROUND];
   __shared__ int64_t s_lo, s_hi;
   uint32_t vmax = 0;
   for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
@@ -432,17 +436,17 @@ __global__ void __launch_bounds__(kThreads)
     uint64_t bm = 0;
     int32_t bj = INT32_MAX;
     float bga = 0.0f;
-    for (int64_t base = lo; base < hi; base += kRoundCols) {  // uniform across the CTA
+    for (int64_t base = lo; base < hi; base += ROUND) {  // uniform across the CTA
       if (threadIdx.x == 0) s_n = 0;
       __syncthreads();
-      const int na = scan_round_f32(gacc, w32, base, hi, lnb32, &s_n, s_j, s_g, s_w);
-      for (int e = threadIdx.x; e < na; e += kThreads) {
+      const int na = scan_round_f32<kFinThreads>(gacc, w32, base, hi, lnb32, &s_n, s_j, s_g);
+      for (int e = threadIdx.x; e < na; e += kFinThreads) {
         const int32_t j = s_j[e];
-        const float g = s_g[e] * inv_nf;
+        const float g = s_g[e] * inv_nf, wj = w32[j];
         float d, f;
-        eq7_step_f32(g, s_w[e], lamf, bj32[j], ib32[j], d, f);
+        eq7_step_f32(g, wj, lamf, bj32[j], ib32[j], d, f);
         if (want_kkt) {
-          const uint32_t v = __float_as_uint(kkt_violation_f32(g, s_w[e], lamf));
+          const uint32_t v = __float_as_uint(kkt_violation_f32(g, wj, lamf));
           vmax = v > vmax ? v : vmax;
         }
         const uint64_t m = candidate_mag32(f);
@@ -455,7 +459,7 @@ __global__ void __launch_bounds__(kThreads)
       __syncthreads();
     }
     double dga = (double)bga;
-    block_best(bm, bj, dga);
+    block_best<kFinThreads>(bm, bj, dga);
     if (threadIdx.x == 0) {
       double d = 0.0;
       const bool ok = bm && accept_fp64(dga, bj, inv_n, lam, w, bjs, ib, d);
@@ -813,7 +817,7 @@ int launch_finalize_accept(gencd_problem* p, int64_t B, bool want_kkt) {
                                                                   p->lambda, b64, b32, B, want_kkt ? 1 : 0, p->list_j,
                                                                   p->list_d, p->dscal + 0);
     else
-      k_finalize_accept_f32<<<grid, kThreads, 0, p->stream>>>(
+      k_finalize_accept_f32<<<grid, kFinThreads, 0, p->stream>>>(
           (float*)p->gnat, p->w32, p->bj32, p->ib32, p->w, p->bj, p->ib, p->k, (float)inv_n, (float)p->lambda, inv_n,
           p->lambda, b32, B, want_kkt ? 1 : 0, p->list_j, p->list_d, p->dscal + 0);
   } else {

@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const bool lead = lane == 0 && active && !(m & 1u);
       const uint32_t slot0 = lead ? __ldg(pair_slot + q0) : 0u;
       const uint32_t slot_last = (active && m != 0u) ? __ldg(pair_slot + q + __popc(m & NOT_FIRST)) : 0u;
-      V acc = V(0), cont = V(0), tail = V(0);
+      V cont = V(0), tail = V(0);
       bool has_tail = false;
       if (active) {
         U uu[ITEMS];
@@ -220,32 +220,46 @@ __global__ void __launch_bounds__(THREADS, 1)
             uu[8 * h + 2 * k2 + 1] = s_u[w4[k2] >> 16];
           }
         }
-        if (m <= 1u) {  // no pair starts after the lane's first entry (the common case)
+        // runs of the lane: the first (entries before the first start bit
+        // after entry 0), the last (from the last such start bit), and, with
+        // two or more start bits, the runs between them -- no divergence for
+        // the lanes with at most one start bit
+        const uint32_t inner = m & NOT_FIRST;
+        const int bf = inner ? __ffs(inner) - 1 : ITEMS;  // first start bit after entry 0
+        const int bl = inner ? 31 - __clz(inner) : ITEMS;  // last one
+        V x[ITEMS], first = V(0), last = V(0);
 #pragma unroll
-          for (int i = 0; i < ITEMS; ++i) acc = fma(cur.L.v[i], (V)uu[i], acc);
-          if (m == 1u) {  // one run, starting at the lane's first entry
-            tail = acc;
-            has_tail = true;
-          } else {
-            cont = acc;
-          }
-        } else {
-          bool first_run = true;
+        for (int i = 0; i < ITEMS; ++i) {
+          x[i] = cur.L.v[i] * (V)uu[i];
+          first += i < bf ? x[i] : V(0);
+          last += i >= bl ? x[i] : V(0);
+        }
+        if (inner & (inner - 1)) {  // runs that start and end inside the lane
+          uint32_t qi = q;
+          V sum = V(0);
 #pragma unroll
-          for (int i = 0; i < ITEMS; ++i) {
-            if (i > 0 && ((m >> i) & 1u)) {
-              if (first_run && !(m & 1u))
-                cont = acc;  // continues from the left
-              else
-                partial[__ldg(pair_slot + q)] = (G)acc;  // started and ended inside the lane
-              ++q;
-              acc = V(0);
-              first_run = false;
+          for (int i = 1; i < ITEMS; ++i) {
+            const bool start = (inner >> i) & 1u;
+            if (start && i > bf) {  // the run [previous start, i) is pair qi
+              partial[__ldg(pair_slot + qi)] = (G)sum;
+              sum = V(0);
             }
-            acc = fma(cur.L.v[i], (V)uu[i], acc);
+            if (start) ++qi;
+            if (i >= bf && i < bl) sum += x[i];
           }
-          tail = acc;  // the last run started inside the lane
+        }
+        if (inner) {
+          if (m & 1u)
+            partial[__ldg(pair_slot + q)] = (G)first;  // started at entry 0, ended inside
+          else
+            cont = first;  // continues from the left
+          tail = last;
           has_tail = true;
+        } else if (m & 1u) {  // one run, starting at the lane's first entry
+          tail = first;
+          has_tail = true;
+        } else {
+          cont = first;
         }
       }
       const bool stop = !active || m != 0u;
@@ -342,38 +356,49 @@ __global__ void __launch_bounds__(kThreads, 3)
     const bool lead = lane == 0 && active && !(m & 1u);
     const int32_t j0 = lead ? __ldg(light_cols + lc0) : 0;
     const int32_t jl = (active && m != 0u) ? __ldg(light_cols + q + __popc(m & 0xfeu)) : 0;
-    V acc = V(0), cont = V(0), tail = V(0);
+    V cont = V(0), tail = V(0);
     bool has_tail = false;
     if (active) {
       U uu[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) uu[i] = __ldg(u + r[i]);  // padding rows are 0, values 0
-      if (m <= 1u) {
+      // first run, last run and the whole columns between (see k_propose_slabs)
+      const uint32_t inner = m & 0xfeu;
+      const int bf = inner ? __ffs(inner) - 1 : 8;
+      const int bl = inner ? 31 - __clz(inner) : 8;
+      V x[8], first = V(0), last = V(0);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) acc = fma(v[i], (V)uu[i], acc);
-        if (m == 1u) {
-          tail = acc;
-          has_tail = true;
-        } else {
-          cont = acc;
-        }
-      } else {
-        bool first_run = true;
+      for (int i = 0; i < 8; ++i) {
+        x[i] = v[i] * (V)uu[i];
+        first += i < bf ? x[i] : V(0);
+        last += i >= bl ? x[i] : V(0);
+      }
+      if (inner & (inner - 1)) {
+        uint32_t qi = q;
+        V sum = V(0);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          if (i > 0 && ((m >> i) & 1u)) {
-            if (first_run && !(m & 1u))
-              cont = acc;
-            else
-              out[__ldg(light_cols + q)] = (G)acc;  // a whole column inside the lane
-            ++q;
-            acc = V(0);
-            first_run = false;
+        for (int i = 1; i < 8; ++i) {
+          const bool start = (inner >> i) & 1u;
+          if (start && i > bf) {  // the column [previous start, i) lies inside the lane
+            out[__ldg(light_cols + qi)] = (G)sum;
+            sum = V(0);
           }
-          acc = fma(v[i], (V)uu[i], acc);
+          if (start) ++qi;
+          if (i >= bf && i < bl) sum += x[i];
         }
-        tail = acc;
+      }
+      if (inner) {
+        if (m & 1u)
+          out[__ldg(light_cols + q)] = (G)first;  // started at entry 0, ended inside
+        else
+          cont = first;
+        tail = last;
         has_tail = true;
+      } else if (m & 1u) {
+        tail = first;
+        has_tail = true;
+      } else {
+        cont = first;
       }
     }
     const bool stop = !active || m != 0u;
