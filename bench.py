@@ -350,7 +350,7 @@ def run_gencd(args):
                        "nnz": prob.nnz, "n": prob.n, "k": prob.k,
                        "l2": "inputs larger than L2: each step streams all of X (%.2f GB)" % (bytes_per_launch / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": {"bound": "hbm", "kernel": "streaming propose (k_propose_all light pass + k_propose_slabs + "
+            "roofline": {"bound": "hbm", "kernel": "streaming propose (k_propose_light_runs + k_propose_slabs + "
                                                   "k_pairs_to_gacc)", "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / peak if achieved else None, "traffic": traffic,
