@@ -220,46 +220,38 @@ __global__ void __launch_bounds__(THREADS, 1)
             uu[8 * h + 2 * k2 + 1] = s_u[w4[k2] >> 16];
           }
         }
-        // runs of the lane: the first (entries before the first start bit
-        // after entry 0), the last (from the last such start bit), and, with
-        // two or more start bits, the runs between them -- no divergence for
-        // the lanes with at most one start bit
+        // one FMA chain over the lane's entries; at each start bit after
+        // entry 0 the running sum closes a run: the first run (continuing
+        // from the left, or a whole run when it began at entry 0) or a run
+        // between two start bits (whole: stored); the last run stays in acc
         const uint32_t inner = m & NOT_FIRST;
         const int bf = inner ? __ffs(inner) - 1 : ITEMS;  // first start bit after entry 0
-        const int bl = inner ? 31 - __clz(inner) : ITEMS;  // last one
-        V x[ITEMS], first = V(0), last = V(0);
+        V acc = V(0), first = V(0);
+        uint32_t qi = q;
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
-          x[i] = cur.L.v[i] * (V)uu[i];
-          first += i < bf ? x[i] : V(0);
-          last += i >= bl ? x[i] : V(0);
-        }
-        if (inner & (inner - 1)) {  // runs that start and end inside the lane
-          uint32_t qi = q;
-          V sum = V(0);
-#pragma unroll
-          for (int i = 1; i < ITEMS; ++i) {
-            const bool start = (inner >> i) & 1u;
-            if (start && i > bf) {  // the run [previous start, i) is pair qi
-              partial[__ldg(pair_slot + qi)] = (G)sum;
-              sum = V(0);
-            }
-            if (start) ++qi;
-            if (i >= bf && i < bl) sum += x[i];
+          if ((inner >> i) & 1u) {
+            if (i == bf)
+              first = acc;
+            else
+              partial[__ldg(pair_slot + qi)] = (G)acc;  // started and ended inside the lane
+            acc = V(0);
+            ++qi;
           }
+          acc = fma(cur.L.v[i], (V)uu[i], acc);
         }
         if (inner) {
           if (m & 1u)
             partial[__ldg(pair_slot + q)] = (G)first;  // started at entry 0, ended inside
           else
             cont = first;  // continues from the left
-          tail = last;
+          tail = acc;  // the last run started inside the lane
           has_tail = true;
         } else if (m & 1u) {  // one run, starting at the lane's first entry
-          tail = first;
+          tail = acc;
           has_tail = true;
         } else {
-          cont = first;
+          cont = acc;
         }
       }
       const bool stop = !active || m != 0u;
@@ -334,11 +326,17 @@ __global__ void __launch_bounds__(kThreads, 3)
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  constexpr bool kPrefetch = sizeof(V) == 4;  // FP64 stages are too large to double in registers
   LightStage<V> nxt;
-  load_light_stage(row, val, lmask, tile_lc, warp, ntiles, nnz, lane, nxt);
+  if (kPrefetch) load_light_stage(row, val, lmask, tile_lc, warp, ntiles, nnz, lane, nxt);
   for (int64_t t = warp; t < ntiles; t += nwarps) {  // warp-uniform
-    const LightStage<V> cur = nxt;
-    load_light_stage(row, val, lmask, tile_lc, t + nwarps, ntiles, nnz, lane, nxt);  // next tile's loads in flight
+    LightStage<V> cur;
+    if (kPrefetch) {
+      cur = nxt;
+      load_light_stage(row, val, lmask, tile_lc, t + nwarps, ntiles, nnz, lane, nxt);  // next tile's loads in flight
+    } else {
+      load_light_stage(row, val, lmask, tile_lc, t, ntiles, nnz, lane, cur);
+    }
     const int64_t a = t * kLightTile + (int64_t)lane * kLightItems;
     const bool active = a < nnz;
     const uint32_t m = cur.m, lc0 = cur.lc0;
@@ -365,40 +363,32 @@ __global__ void __launch_bounds__(kThreads, 3)
       // first run, last run and the whole columns between (see k_propose_slabs)
       const uint32_t inner = m & 0xfeu;
       const int bf = inner ? __ffs(inner) - 1 : 8;
-      const int bl = inner ? 31 - __clz(inner) : 8;
-      V x[8], first = V(0), last = V(0);
+      V acc = V(0), first = V(0);
+      uint32_t qi = q;
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        x[i] = v[i] * (V)uu[i];
-        first += i < bf ? x[i] : V(0);
-        last += i >= bl ? x[i] : V(0);
-      }
-      if (inner & (inner - 1)) {
-        uint32_t qi = q;
-        V sum = V(0);
-#pragma unroll
-        for (int i = 1; i < 8; ++i) {
-          const bool start = (inner >> i) & 1u;
-          if (start && i > bf) {  // the column [previous start, i) lies inside the lane
-            out[__ldg(light_cols + qi)] = (G)sum;
-            sum = V(0);
-          }
-          if (start) ++qi;
-          if (i >= bf && i < bl) sum += x[i];
+        if ((inner >> i) & 1u) {
+          if (i == bf)
+            first = acc;
+          else
+            out[__ldg(light_cols + qi)] = (G)acc;  // a whole column inside the lane
+          acc = V(0);
+          ++qi;
         }
+        acc = fma(v[i], (V)uu[i], acc);
       }
       if (inner) {
         if (m & 1u)
           out[__ldg(light_cols + q)] = (G)first;  // started at entry 0, ended inside
         else
           cont = first;
-        tail = last;
+        tail = acc;
         has_tail = true;
       } else if (m & 1u) {
-        tail = first;
+        tail = acc;
         has_tail = true;
       } else {
-        cont = first;
+        cont = acc;
       }
     }
     const bool stop = !active || m != 0u;
@@ -420,16 +410,25 @@ __global__ void __launch_bounds__(kThreads, 3)
 }
 
 // sum of each heavy column = its partials in slab order (the slots of column h
-// are hslot_ptr[h] .. hslot_ptr[h+1]); partials reset
+// are hslot_ptr[h] .. hslot_ptr[h+1], at most one per slab); partials reset.
+// The loads of up to 32 slots are issued together, then summed in order.
 template <typename G>
 __global__ void k_pairs_to_gacc(const uint32_t* __restrict__ hslot_ptr, const int32_t* __restrict__ heavy_cols,
                                 int64_t nheavy, G* __restrict__ partial, G* __restrict__ gacc) {
+  constexpr int CH = 32;
   const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= nheavy) return;
+  const uint32_t b = hslot_ptr[h], e = hslot_ptr[h + 1];
   G s = G(0);
-  for (uint32_t x = hslot_ptr[h]; x < hslot_ptr[h + 1]; ++x) {
-    s += partial[x];
-    partial[x] = G(0);
+  for (uint32_t base = b; base < e; base += CH) {
+    G v[CH];
+#pragma unroll
+    for (int i = 0; i < CH; ++i) v[i] = base + i < e ? partial[base + i] : G(0);
+#pragma unroll
+    for (int i = 0; i < CH; ++i) s += v[i];
+#pragma unroll
+    for (int i = 0; i < CH; ++i)
+      if (base + i < e) partial[base + i] = G(0);
   }
   gacc[heavy_cols[h]] = s;
 }
