@@ -247,8 +247,7 @@ static int enqueue_iteration(gencd_problem* p, int64_t* host_nnz, bool want_kkt)
   const int v = p->params.variant;
   if (v == GENCD_THREAD_GREEDY || v == GENCD_GREEDY) {
     const int B = effective_B(p);
-    GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal, 0, sizeof(double), p->stream));
-    GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal + 7, 0, sizeof(double), p->stream));
+    GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal, 0, sizeof(double), p->stream));  // KKT maximum
     GENCD_TRY(launch_propose_all(p, p->u, p->precision == GENCD_F64));  // Propose, all columns
     GENCD_TRY(launch_finalize_accept(p, B, want_kkt));  // step, proxy (+ KKT of the start state); Accept
     GENCD_TRY(launch_update_list(p, p->list_j, p->list_d, B, true));     // Update (atomic z)
@@ -264,7 +263,6 @@ static int enqueue_iteration(gencd_problem* p, int64_t* host_nnz, bool want_kkt)
     GENCD_TRY(ensure_selection(p, e, p->k));                             // Select, random subset
     const int64_t lo = q * P, m = (lo + P <= p->k ? P : p->k - lo);
     const int32_t* J = p->perm + lo;
-    GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal + 7, 0, sizeof(double), p->stream));
     GENCD_TRY(launch_propose_list(p, J, m, p->list_d, p->phi));          // Propose (Jacobi)
     GENCD_TRY(launch_update_list(p, J, p->list_d, m, false));            // Accept all, Update
     GENCD_TRY(launch_refresh_list(p, J, p->list_d, m, false));
@@ -338,7 +336,8 @@ static void free_problem(gencd_problem* p) {
   void* bufs[] = {p->col_ptr, p->row_idx, p->val, p->y, p->z, p->u, p->w, p->c, p->ib, p->tile_col, p->gacc,
                   p->delta, p->phi, p->list_j, p->list_d, p->dscal, p->red, p->perm, p->sort_tmp,
                   p->row_ptr, p->col_idx, p->csr_val, p->color, p->color_ptr, p->cols_by_color,
-                  p->slot_m, p->slot_d, p->slot_j, p->list_off, p->scan_tmp, p->bj, p->w32, p->bj32, p->ib32};
+                  p->slot_m, p->slot_d, p->slot_j, p->list_off, p->scan_tmp, p->bj, p->w32, p->bj32, p->ib32,
+                  p->part_lo};
   if (p->stream) cudaStreamSynchronize(p->stream);
   free_propose_plan(p);
   if (p->gnat && p->gnat != p->gacc) cudaFree(p->gnat);

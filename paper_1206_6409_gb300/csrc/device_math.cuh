@@ -78,6 +78,17 @@ __device__ __forceinline__ void eq7_step(double g, double wj, double lam, double
   phi = bj > 0.0 ? d * fma(0.5 * bj, d, g) + lam * dabs : -lam * fabs(wj);
 }
 
+// Accept candidates.  Only a proxy phi < 0 can be accepted; among negative
+// doubles the order of phi is the reverse of the order of |phi|'s bit pattern,
+// so "lowest phi, then lowest column" becomes "largest magnitude bits, then
+// lowest column" -- integer compares, no FP64 instructions.  mag = 0 means
+// "no candidate" (phi >= 0, -0, or NaN).
+__device__ __forceinline__ uint64_t candidate_mag(double phi) {
+  const uint64_t b = (uint64_t)__double_as_longlong(phi);
+  const uint64_t m = b & 0x7fffffffffffffffull;
+  return ((b >> 63) && m != 0 && m <= 0x7ff0000000000000ull) ? m : 0ull;
+}
+
 // FP32 copy of a coefficient that is 0 exactly when the coefficient is 0
 // (values below the float range keep their sign at the smallest denormal)
 __device__ __forceinline__ float w_mirror(double x) {

@@ -48,6 +48,11 @@ constexpr int kItemsF64 = 4;   // nnz per lane in the streaming propose (FP64 mo
 constexpr int kItemsF32 = 8;   // nnz per lane in the streaming propose (FP32 mode)
 constexpr int kPadNnz = 64;    // CSC arrays are padded to a multiple of this
 constexpr int kThreads = 256;  // default CTA size
+// the single-CTA plan of an update list (lengths, prefix, w) takes lists of at
+// most kListPlanMax entries
+constexpr int kListPlanThreads = 1024;
+constexpr int kListPlanPer = 4;
+constexpr int64_t kListPlanMax = (int64_t)kListPlanThreads * kListPlanPer;
 
 // kernel ids for launch counting / profiling
 enum KernelId {
@@ -168,6 +173,10 @@ struct gencd_problem {
   double* list_d = nullptr;
   uint32_t* list_off = nullptr;  // exclusive prefix of the listed columns' nnz (k + 2)
   uint32_t* scan_tmp = nullptr;  // scratch of the prefix sum
+
+  // Thread-Greedy partition bounds floor(b k / B), b = 0..part_B
+  int64_t* part_lo = nullptr;
+  int64_t part_B = 0, part_cap = 0;
 
   // accept candidates of (chunk, partition) pairs when partitions are few
   uint64_t* slot_m = nullptr;

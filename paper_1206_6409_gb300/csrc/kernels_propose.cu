@@ -142,17 +142,6 @@ __device__ __forceinline__ bool column_is_idle(double gacc, double wj, uint64_t 
 }
 
 
-// Accept candidates.  Only a proxy phi < 0 can be accepted; among negative
-// doubles the order of phi is the reverse of the order of |phi|'s bit pattern,
-// so "lowest phi, then lowest column" becomes "largest magnitude bits, then
-// lowest column" -- integer compares, no FP64 instructions.  mag = 0 means
-// "no candidate" (phi >= 0, -0, or NaN).
-__device__ __forceinline__ uint64_t candidate_mag(double phi) {
-  const uint64_t b = (uint64_t)__double_as_longlong(phi);
-  const uint64_t m = b & 0x7fffffffffffffffull;
-  return ((b >> 63) && m != 0 && m <= 0x7ff0000000000000ull) ? m : 0ull;
-}
-
 __device__ __forceinline__ bool cand_better(uint64_t ma, int32_t ja, uint64_t mb, int32_t jb) {
   return ma > mb || (ma == mb && ma != 0 && ja < jb);
 }
@@ -418,21 +407,16 @@ __global__ void __launch_bounds__(kFinThreads)
     k_finalize_accept_f32(float* __restrict__ gacc, const float* __restrict__ w32, const float* __restrict__ bj32,
                           const float* __restrict__ ib32, const double* __restrict__ w,
                           const double* __restrict__ bjs, const double* __restrict__ ib, int64_t k, float inv_nf,
-                          float lamf, double inv_n, double lam, uint32_t lnb32, int64_t B, int want_kkt,
-                          int32_t* __restrict__ list_j, double* __restrict__ list_d, double* __restrict__ kkt_out) {
+                          float lamf, double inv_n, double lam, uint32_t lnb32, int64_t B,
+                          const int64_t* __restrict__ part_lo, int want_kkt, int32_t* __restrict__ list_j,
+                          double* __restrict__ list_d, double* __restrict__ kkt_out) {
   constexpr int ROUND = kColsPerThread * kFinThreads;
   __shared__ int s_n;
   __shared__ int32_t s_j[ROUND];
   __shared__ float s_g[ROUND];
-  __shared__ int64_t s_lo, s_hi;
   uint32_t vmax = 0;
   for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
-    if (threadIdx.x == 0) {  // one thread does the 64-bit divisions
-      s_lo = b * k / B;
-      s_hi = (b + 1) * k / B;
-    }
-    __syncthreads();
-    const int64_t lo = s_lo, hi = s_hi;
+    const int64_t lo = part_lo[b], hi = part_lo[b + 1];  // precomputed: no 64-bit division here
     uint64_t bm = 0;
     int32_t bj = INT32_MAX;
     float bga = 0.0f;
@@ -466,6 +450,7 @@ __global__ void __launch_bounds__(kFinThreads)
       list_j[b] = ok ? bj : -1;
       list_d[b] = ok ? d : 0.0;
     }
+    __syncthreads();  // s_n and the queue are reused by the next partition
   }
   if (want_kkt) block_max_bits_to(kkt_out, kkt_bits_f32(vmax));
 }
@@ -802,6 +787,33 @@ int launch_finalize(gencd_problem* p, double lambda, bool write_steps) {
   return GENCD_OK;
 }
 
+__global__ void k_part_bounds(int64_t k, int64_t B, int64_t* __restrict__ lo) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= B; b += stride) lo[b] = b * k / B;
+}
+
+// part_lo[b] = floor(b k / B), b = 0..B (Thread-Greedy partitions, reading 4)
+static int ensure_part_bounds(gencd_problem* p, int64_t B) {
+  if (p->part_B == B && p->part_lo) return GENCD_OK;
+  if (p->part_cap < B + 1) {
+    GENCD_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    cudaFree(p->part_lo);
+    p->part_lo = nullptr;
+    p->part_cap = 0;
+    if (cudaMalloc((void**)&p->part_lo, sizeof(int64_t) * (size_t)(B + 1)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaMalloc of the partition bounds failed");
+      return GENCD_ENOMEM;
+    }
+    p->part_cap = B + 1;
+  }
+  k_part_bounds<<<grid_for(B + 1, kThreads, p->num_sms * 8), kThreads, 0, p->stream>>>(p->k, B, p->part_lo);
+  p->prof.launches[K_SETUP] += 1;
+  GENCD_CUDA_TRY(cudaGetLastError());
+  p->part_B = B;
+  return GENCD_OK;
+}
+
 int launch_finalize_accept(gencd_problem* p, int64_t B, bool want_kkt) {
   const double inv_n = 1.0 / (double)p->n;
   uint64_t b64;
@@ -816,10 +828,12 @@ int launch_finalize_accept(gencd_problem* p, int64_t B, bool want_kkt) {
       k_finalize_accept<double><<<grid, kThreads, 0, p->stream>>>((double*)p->gnat, p->w, p->bj, p->ib, p->k, inv_n,
                                                                   p->lambda, b64, b32, B, want_kkt ? 1 : 0, p->list_j,
                                                                   p->list_d, p->dscal + 0);
-    else
+    else {
+      GENCD_TRY(ensure_part_bounds(p, B));
       k_finalize_accept_f32<<<grid, kFinThreads, 0, p->stream>>>(
           (float*)p->gnat, p->w32, p->bj32, p->ib32, p->w, p->bj, p->ib, p->k, (float)inv_n, (float)p->lambda, inv_n,
-          p->lambda, b32, B, want_kkt ? 1 : 0, p->list_j, p->list_d, p->dscal + 0);
+          p->lambda, b32, B, p->part_lo, want_kkt ? 1 : 0, p->list_j, p->list_d, p->dscal + 0);
+    }
   } else {
     int64_t S = p->k / B;  // >= 1 since B <= k; a chunk meets at most two partitions
     if (S > 4096) S = 4096;

@@ -63,16 +63,12 @@ __global__ void k_apply_w(const int64_t* __restrict__ col_ptr, const int32_t* __
   if ((threadIdx.x & 31) == 0 && upd) {
     atomicAdd(counters + 0, upd);
     atomicAdd(counters + 1, work);
-    atomicAdd(counters + 3, work);  // touched this iteration
   }
 }
 
 // One CTA for lists of at most kListPlanMax entries: lengths of the applied
 // entries, their exclusive prefix (off[0..m]), w_j += delta_j and the counters
 // -- k_list_len, the scan and k_apply_w in one launch.
-constexpr int kListPlanThreads = 1024;
-constexpr int kListPlanPer = 4;
-constexpr int64_t kListPlanMax = (int64_t)kListPlanThreads * kListPlanPer;
 
 __global__ void __launch_bounds__(kListPlanThreads)
     k_list_plan(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ J, const double* __restrict__ D,
@@ -129,10 +125,7 @@ __global__ void __launch_bounds__(kListPlanThreads)
   if (tid == 0) off[m] = total;
   const unsigned long long u_all = warp_sum((unsigned long long)upd);
   if (lane == 0 && u_all) atomicAdd(counters + 0, u_all);
-  if (tid == 0 && total) {
-    atomicAdd(counters + 1, (unsigned long long)total);
-    atomicAdd(counters + 3, (unsigned long long)total);  // touched this iteration
-  }
+  if (tid == 0 && total) atomicAdd(counters + 1, (unsigned long long)total);
 }
 
 // last entry e in [0, m) with off[e] <= q
