@@ -61,6 +61,7 @@ def lib():
             "oracle_step": (None, [C.c_double, C.c_double, C.c_double, C.c_double, _f64p, _f64p]),
             "oracle_propose": (None, [vp, _f64p, _f64p, _i32p, C.c_int64, _f64p, _f64p]),
             "oracle_splitmix64": (C.c_uint64, [C.c_uint64, C.c_uint64]),
+            "oracle_stored_values": (C.c_int64, [C.c_int32, C.c_int64, _i64p, _f64p, _f64p]),
             "oracle_permutation": (None, [C.c_uint64, C.c_int64, C.c_int64, _i32p]),
             "oracle_spectral_radius": (C.c_double, [vp, C.c_int32, C.c_double, _i32p]),
             "oracle_pstar": (C.c_int64, [C.c_int64, C.c_double]),
@@ -230,6 +231,33 @@ def step(g, w_j, lam, beta_j):
     return d.value, f.value
 
 
+STORAGE = {"f64": 0, "f32": 1, "bf16": 2, "binary": 3}
+
+
+def stored_values(prob, mode):
+    """The values of X as storage mode ``mode`` holds them (R10), float64[nnz].
+
+    Raises ValueError for a binary column whose values differ, or a value
+    beyond the bfloat16 range."""
+    col_ptr = np.ascontiguousarray(prob.col_ptr, np.int64)
+    val = np.ascontiguousarray(prob.val, np.float64)
+    out = np.empty(val.size)
+    bad = lib().oracle_stored_values(STORAGE[mode], int(prob.k), _p(col_ptr, _i64p), _p(val, _f64p),
+                                     _p(out, _f64p))
+    if bad == -2:
+        raise ValueError("a value of X is beyond the bfloat16 range")
+    if bad >= 0:
+        raise ValueError(f"column {bad} has non-zeros of different values")
+    return out
+
+
+def stored_problem(prob, mode):
+    """``prob`` with X replaced by the values storage mode ``mode`` holds."""
+    import dataclasses
+
+    return dataclasses.replace(prob, val=stored_values(prob, mode))
+
+
 def splitmix64(s, i):
     return lib().oracle_splitmix64(s & ((1 << 64) - 1), i)
 
@@ -245,4 +273,5 @@ def pstar(k, rho):
 
 
 __all__ = ["Oracle", "loss", "dloss", "beta", "step", "splitmix64", "permutation", "pstar",
+           "stored_values", "stored_problem", "STORAGE",
            "SQUARED", "LOGISTIC"]

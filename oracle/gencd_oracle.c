@@ -36,6 +36,11 @@
  *  R8  The colouring is greedy first-fit over the columns in index order.
  *  R9  KKT violation: max(|g_j| - lambda, 0) if w_j == 0, else
  *      |g_j + lambda sign(w_j)|.
+ *  R10 Storage modes (not in the paper): a mode replaces each value of X by
+ *      the value it stores, and the method then runs on that X.  FP32 rounds
+ *      to nearest even; bfloat16 keeps the sign, the 8 exponent bits and the
+ *      top 7 mantissa bits of the FP32 value, rounded to nearest even;
+ *      binary stores one FP32 value per column.
  */
 #include "gencd_oracle.h"
 
@@ -435,4 +440,33 @@ int64_t oracle_solve(const oracle_problem* pr, const oracle_params* pa, double t
   }
   if (kkt_out) *kkt_out = kkt;
   return t;
+}
+
+/* R10: stored values.  bfloat16 rounding: with u the FP32 bit pattern, the
+ * discarded low 16 bits are compared with half of the kept last place; adding
+ * 0x7fff plus the kept last bit rounds up exactly when they exceed half, or
+ * equal half with an odd kept part (ties to even). */
+int64_t oracle_stored_values(int32_t mode, int64_t k, const int64_t* col_ptr, const double* val,
+                             double* out) {
+  const int64_t nnz = col_ptr[k];
+  for (int64_t q = 0; q < nnz; ++q) {
+    if (mode == 0) {
+      out[q] = val[q];
+      continue;
+    }
+    float f = (float)val[q];
+    if (mode == 2) {
+      uint32_t u;
+      memcpy(&u, &f, 4);
+      u = (u + 0x7fffu + ((u >> 16) & 1u)) & 0xffff0000u;
+      memcpy(&f, &u, 4);
+      if (!isfinite(f)) return -2;
+    }
+    out[q] = (double)f;
+  }
+  if (mode == 3)
+    for (int64_t j = 0; j < k; ++j)
+      for (int64_t q = col_ptr[j] + 1; q < col_ptr[j + 1]; ++q)
+        if (out[q] != out[col_ptr[j]]) return j;
+  return -1;
 }

@@ -78,6 +78,14 @@ void oracle_propose(const oracle_problem* pr, const double* w, const double* z,
 
 /* SplitMix64 (Steele, Lea, Flood 2014): output number i (i >= 0) of the
  * stream whose state starts at s. */
+/* Values of X as a storage mode holds them (R10): mode 0 FP64 (copy), 1 FP32,
+ * 2 bfloat16 from the FP32 value, 3 index-only binary (FP32; every column's
+ * values must be equal).  out[q] is the stored value of entry q, as a double.
+ * Returns -1, or the lowest column whose values differ (mode 3), or -2 for a
+ * value outside the bfloat16 range (mode 2). */
+int64_t oracle_stored_values(int32_t mode, int64_t k, const int64_t* col_ptr, const double* val,
+                             double* out);
+
 uint64_t oracle_splitmix64(uint64_t s, uint64_t i);
 /* Selection permutation of 0..m-1 for one epoch. */
 void oracle_permutation(uint64_t seed, int64_t epoch, int64_t m, int32_t* perm);

@@ -523,3 +523,53 @@ def test_empty_columns_and_rows_are_handled():
     assert o.kkt(w) <= 1e-12
     Pbf, wbf = _brute_force(X[:, [0, 2, 4]], y, "logistic", 0.05)
     np.testing.assert_allclose(w[[0, 2, 4]], wbf, atol=1e-8)
+
+
+
+def _one_column(vals):
+    vals = np.asarray(vals, np.float64)
+    return workloads.Problem(1, 1, np.array([0, vals.size], np.int64), np.zeros(vals.size, np.int32), vals,
+                             np.ones(1), "squared", np.zeros(1))
+
+
+def test_stored_values_bf16_rounds_to_nearest_even():
+    # R10: bfloat16 keeps 7 mantissa bits of the FP32 value; a halfway case
+    # goes to the even neighbour, anything above half rounds away from zero
+    h = 2.0 ** -8  # half of bfloat16's last place at 1
+    cases = [(1.0, 1.0), (1.0 + h, 1.0), (1.0 + 3 * h, 1.0 + 4 * h), (-(1.0 + h), -1.0),
+             (1.0 + h + 2.0 ** -20, 1.0 + 2 * h), (1.0 + h - 2.0 ** -20, 1.0), (0.0, 0.0),
+             (2.0 ** -130, 2.0 ** -130), (2.0 ** -140, 0.0), (-(2.0 ** 100) * (1 + 3 * h), -(2.0 ** 100) * (1 + 4 * h)),
+             # FP32 rounds first: 1 + h + 2^-30 is 1 + h in FP32, a tie that goes to 1
+             (1.0 + h + 2.0 ** -30, 1.0)]
+    out = oracle.stored_values(_one_column([c[0] for c in cases]), "bf16")
+    np.testing.assert_array_equal(out, [c[1] for c in cases])
+    with pytest.raises(ValueError, match="bfloat16 range"):
+        oracle.stored_values(_one_column([1.0, 3.4e38]), "bf16")
+
+
+def test_stored_values_match_library_conversions():
+    # FP32 storage is numpy's float32 cast; bfloat16 storage is PyTorch's CPU
+    # float32 -> bfloat16 conversion (round to nearest even)
+    import torch
+
+    rng = np.random.default_rng(3)
+    v = np.concatenate([rng.lognormal(0, 3, 20_000) * np.where(rng.random(20_000) < 0.5, -1, 1),
+                        rng.normal(size=1000) * 1e-39])
+    p = _one_column(v)
+    np.testing.assert_array_equal(oracle.stored_values(p, "f64"), v)
+    f32 = v.astype(np.float32)
+    np.testing.assert_array_equal(oracle.stored_values(p, "f32"), f32.astype(np.float64))
+    ref = torch.from_numpy(f32).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(oracle.stored_values(p, "bf16"), ref)
+
+
+def test_stored_values_binary_needs_one_value_per_column():
+    p = workloads.config3("ones")
+    np.testing.assert_array_equal(oracle.stored_values(p, "binary"), np.ones(p.nnz))
+    b = workloads.binarized(workloads.config2_scaled(0.002))
+    np.testing.assert_array_equal(oracle.stored_values(b, "binary"), b.val.astype(np.float32))
+    pm = workloads.config3("pm1")
+    first_mixed = next(j for j in range(pm.k)
+                       if np.unique(pm.val[pm.col_ptr[j]:pm.col_ptr[j + 1]]).size > 1)
+    with pytest.raises(ValueError, match=f"column {first_mixed} "):
+        oracle.stored_values(pm, "binary")

@@ -54,3 +54,29 @@ def test_distinct_rows_are_uniform_without_replacement():
     assert rows[15:].tolist() == list(range(10))
     with pytest.raises(ValueError):
         workloads.synthetic._distinct_rows(3, np.array([4]), rng)
+
+
+def test_cv_folds_are_balanced_and_seeded():
+    f = workloads.cv_folds(1003, 5, seed=4)
+    assert f.dtype == np.uint8 and set(np.unique(f)) == set(range(5))
+    assert np.bincount(f).max() - np.bincount(f).min() <= 1
+    np.testing.assert_array_equal(f, workloads.cv_folds(1003, 5, seed=4))
+
+
+def test_row_subset_is_the_dense_row_selection():
+    # trailing and inner empty columns, a row subset that empties some columns
+    X = np.zeros((7, 6))
+    X[0, 0], X[3, 0], X[1, 2], X[6, 2], X[2, 3], X[5, 3] = 1.0, -2.0, 0.5, 1.5, 3.0, -1.0
+    y = np.arange(7.0)
+    p = workloads.csc_from_dense(X, y, "squared")
+    rows = np.array([5, 0, 2, 6])
+    s = workloads.row_subset(p, rows)
+    np.testing.assert_array_equal(s.to_dense(), X[np.sort(rows)])
+    np.testing.assert_array_equal(s.y, y[np.sort(rows)])
+    assert s.col_ptr[-1] == s.nnz == int(np.count_nonzero(X[np.sort(rows)]))
+
+
+def test_lambda_grid_is_log_spaced():
+    g = workloads.lambda_grid(2.0, 32, 1e-3)
+    assert g.size == 32 and g[0] == 2.0 and abs(g[-1] - 2e-3) < 1e-15
+    np.testing.assert_allclose(g[1:] / g[:-1], (1e-3) ** (1 / 31))

@@ -13,6 +13,12 @@ from .synthetic import (  # noqa: F401
     config1,
     config2,
     config2_scaled,
+    config3,
+    binarized,
+    config4,
+    cv_folds,
+    lambda_grid,
+    row_subset,
     tiny_problem,
     csc_from_dense,
 )

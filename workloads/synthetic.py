@@ -231,6 +231,22 @@ def config2(loss=LOGISTIC, seed=0, cache_dir=None) -> Problem:
     return p
 
 
+def config3(values="lognormal", loss=LOGISTIC, seed=0) -> Problem:
+    """config1's shapes (n=2,000, k=5,000, 20 nnz/column at uniform rows) with
+    one of three value laws: "pm1" (exact in bfloat16), "ones" (binary) or
+    "lognormal" (LogNormal(0,1), unit-norm columns: bfloat16 rounds them)."""
+    return uniform_problem(2000, 5000, 20, values=values, n_planted=50, loss=loss, seed=seed,
+                           name=f"uniform-2000x5000-20nnz-{values}-{loss}")
+
+
+def binarized(prob: Problem) -> Problem:
+    """The same sparsity pattern and labels with binary, unit-norm columns:
+    every non-zero of column j becomes 1/sqrt(nnz_j) (no random draws)."""
+    counts = prob.col_nnz()
+    s = 1.0 / np.sqrt(np.maximum(counts, 1).astype(np.float64))
+    return dataclasses.replace(prob, val=np.repeat(s, counts), name=prob.name + "-binary")
+
+
 def config2_scaled(scale=0.02, loss=LOGISTIC, seed=0) -> Problem:
     """config2's structure at a fraction of its size (rows, columns, nnz and the
     column cap all scaled), for tests that must run in seconds."""
@@ -240,6 +256,47 @@ def config2_scaled(scale=0.02, loss=LOGISTIC, seed=0) -> Problem:
     cap = max(50, int(50_000 * scale))
     return zipf_problem(n, k, nnz, cap=cap, n_planted=max(10, int(2000 * scale)), loss=loss,
                         seed=seed, name=f"zipf1.1-{n}x{k}-{nnz}nnz-{loss}")
+
+
+def config4(loss=SQUARED, seed=0, scale=1.0) -> Problem:
+    """The regularisation-path workload: n=200,000, k=500,000, Zipf(1.1)
+    column lengths capped at 10,000 (4.0e7 nnz), LogNormal(0,1) values with
+    unit-norm columns, 1,000 planted weights (zipf_problem's law).  ``scale``
+    shrinks rows, columns, nnz and the cap together, for tests."""
+    n = max(1000, int(200_000 * scale))
+    k = max(1000, int(500_000 * scale))
+    nnz = int(40_000_000 * scale)
+    cap = max(50, int(10_000 * scale))
+    return zipf_problem(n, k, nnz, cap=cap, n_planted=max(10, int(1000 * scale)), loss=loss, seed=seed,
+                        name=f"zipf1.1-{n}x{k}-{nnz}nnz-{loss}")
+
+
+def cv_folds(n, nfolds=5, seed=0) -> np.ndarray:
+    """Row folds for cross-validation: a seeded permutation of the rows dealt
+    round-robin, so fold sizes differ by at most one (uint8[n])."""
+    perm = _rng(seed).permutation(n)
+    fold = np.empty(n, np.uint8)
+    fold[perm] = (np.arange(n) % nfolds).astype(np.uint8)
+    return fold
+
+
+def lambda_grid(lam_max, nlambda=32, ratio=1e-3) -> np.ndarray:
+    """nlambda values log-spaced from lam_max down to ratio * lam_max."""
+    return lam_max * np.logspace(0.0, np.log10(ratio), nlambda)
+
+
+def row_subset(prob: Problem, rows) -> Problem:
+    """The problem restricted to the given rows (renumbered in increasing
+    order), the same columns: the training problem of a cross-validation
+    fold."""
+    rows = np.sort(np.asarray(rows, np.int64))
+    new_id = np.full(prob.n, -1, np.int64)
+    new_id[rows] = np.arange(rows.size)
+    keep = new_id[prob.row_idx] >= 0
+    col_of = np.repeat(np.arange(prob.k), np.diff(prob.col_ptr))
+    counts = np.bincount(col_of[keep], minlength=prob.k).astype(np.int64)
+    return Problem(int(rows.size), prob.k, _col_ptr(counts), new_id[prob.row_idx[keep]].astype(np.int32),
+                   prob.val[keep].copy(), prob.y[rows].copy(), prob.loss, prob.w_star, prob.name + "-rows")
 
 
 def tiny_problem(n, k, density=0.6, loss=LOGISTIC, seed=0, max_tries=1000) -> Problem:
