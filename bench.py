@@ -51,7 +51,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gencd", choices=["gencd", "reference"])
-    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64", "bf16", "binary"],
+                    help="storage mode of X (bf16 and binary compute in FP32; binary runs on the "
+                         "workload's pattern with 1/sqrt(nnz_j) values)")
     ap.add_argument("--variant", default="thread_greedy", choices=["thread_greedy", "greedy"])
     ap.add_argument("--blocks", type=int, default=1024)
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the full workload (tests)")
@@ -64,10 +66,13 @@ def parse():
     return ap.parse_args()
 
 
-def load_problem(scale):
-    if scale >= 1.0:
-        return workloads.config2("logistic")
-    return workloads.config2_scaled(scale, "logistic")
+def load_problem(scale, precision="f32"):
+    prob = workloads.config2("logistic") if scale >= 1.0 else workloads.config2_scaled(scale, "logistic")
+    return workloads.binarized(prob) if precision == "binary" else prob
+
+
+# bytes of one stored value of X per storage mode
+VALUE_BYTES = {"f64": 8, "f32": 4, "bf16": 2, "binary": 0}
 
 
 def measured_peak():
@@ -211,8 +216,11 @@ def run_reference(args):
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return
-    prob = load_problem(args.scale)
+    prob = load_problem(args.scale, args.precision)
     import oracle
+
+    if args.precision != "f64":  # the oracle runs on the values the storage mode holds
+        prob = oracle.stored_problem(prob, args.precision)
 
     orc_full = oracle.Oracle(prob)
     lam = 0.05 * orc_full.lambda_max()
@@ -234,7 +242,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": "nnz processed/s", "value": value, "unit": "nnz/s", "n_gpus": world,
             "steps": steps, "warmup": warm, "ms_per_step": 1000.0 * el / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC, "variant": "thread_greedy", "precision": "f64"},
+            "config": {"workload": WORKLOAD_DESC + ("; binarized: every non-zero of column j is 1/sqrt(nnz_j)"
+                                                    if args.precision == "binary" else ""),
+                       "variant": "thread_greedy", "precision": args.precision, "oracle_arithmetic": "f64"},
             "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": "nnz/s",
                              "sample": "per step: " + sample},
             "e2e": {"value": value, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -253,9 +263,9 @@ def run_gencd(args):
     from paper_1206_6409_gb300 import binding as gb
 
     gb.lib()
-    prob = load_problem(args.scale)
+    prob = load_problem(args.scale, args.precision)
     stream = torch.cuda.current_stream()
-    val = prob.val.astype(np.float32) if args.precision == "f32" else prob.val
+    val = prob.val if args.precision == "f64" else prob.val.astype(np.float32)
 
     # ---- device-resident arm ----------------------------------------------
     p = gb.Problem(n=prob.n, k=prob.k, col_ptr=prob.col_ptr, row_idx=prob.row_idx, val=val, y=prob.y,
@@ -296,8 +306,10 @@ def run_gencd(args):
 
     # roofline of the dominant kernel (the streaming propose)
     pa_ms, _, pa_n = prof["propose_all"]  # one timed invocation of the family per step
-    sv = 4 if args.precision == "f32" else 8
-    bytes_per_launch = prob.nnz * (4 + sv) + 8 * (prob.k + 1) + 8 * prob.k
+    # row index + stored value per non-zero; column pointer and gradient per
+    # column; binary storage reads one FP32 value per column instead
+    sv = VALUE_BYTES[args.precision]
+    bytes_per_launch = prob.nnz * (4 + sv) + 8 * (prob.k + 1) + 8 * prob.k + (4 * prob.k if sv == 0 else 0)
     achieved = bytes_per_launch / (pa_ms / pa_n / 1000.0) / 1e9 if pa_n else None
     peak, peak_kind = measured_peak()
     csrc = os.path.join(ROOT, "paper_1206_6409_gb300", "csrc")
@@ -371,8 +383,11 @@ def run_gencd(args):
         line = {
             "metric": "nnz processed/s", "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC if args.scale >= 1.0 else f"scaled {args.scale}: {prob.name}",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "f64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": (WORKLOAD_DESC if args.scale >= 1.0 else f"scaled {args.scale}: {prob.name}")
+                       + ("; binarized: every non-zero of column j is 1/sqrt(nnz_j)"
+                          if args.precision == "binary" else ""),
                        "variant": args.variant, "blocks": args.blocks, "precision": args.precision,
                        "nnz": prob.nnz, "n": prob.n, "k": prob.k,
                        "l2": "inputs larger than L2: each step streams all of X (%.2f GB)" % (bytes_per_launch / 1e9),

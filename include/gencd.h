@@ -60,7 +60,16 @@ typedef enum {
   GENCD_COLORING = 3       /* Select: random colour class; Accept: all          */
 } gencd_variant;
 
-typedef enum { GENCD_F64 = 0, GENCD_F32 = 1 } gencd_precision;
+/* Storage and arithmetic of the hot path.  F64: X, u and the sums in FP64.
+ * F32: X and u in FP32, sums in FP32 (z, w, objective in FP64; Thread-Greedy
+ * ranks columns with FP32 proxies and applies the winner's FP64 step).
+ * BF16: as F32, with the values of X rounded to bfloat16 (round to nearest
+ * even) at create and streamed as bfloat16 by the propose over all columns.
+ * BINARY: as F32, index only: all non-zeros of a column must share one value
+ * s_j (GENCD_EINVAL otherwise); the propose over all columns streams row
+ * indices only and scales each column's sum of u by s_j.  Neither storage
+ * mode is in the paper; its data sets are binary or tf-idf (Section 5). */
+typedef enum { GENCD_F64 = 0, GENCD_F32 = 1, GENCD_BF16 = 2, GENCD_BINARY = 3 } gencd_precision;
 typedef enum { GENCD_HOST = 0, GENCD_DEVICE = 1 } gencd_memory;
 
 typedef struct gencd_problem gencd_problem; /* opaque, owned by the library */
@@ -100,8 +109,8 @@ typedef struct {
  *   row_idx  int32[nnz], strictly increasing within each column, in [0, n)
  *   val      nnz values, double (val_dtype 0) or float (val_dtype 1)
  *   y        double[n]; for logistic loss every y_i must be -1 or +1
- *   loss     gencd_loss;  precision  gencd_precision of the device copy of X
- *            and of u (FP32 mode accumulates X_j^T u in FP32 per thread)
+ *   loss     gencd_loss;  precision  gencd_precision (storage of X and u and
+ *            the precision of the sums X_j^T u; see gencd_precision)
  *   memory   where col_ptr/row_idx/val/y live; the library copies them into
  *            its own device buffers, so the caller may free them on return
  *   stream   cudaStream_t (may be NULL for the legacy default stream)

@@ -30,13 +30,13 @@ GENCD_ESTATE = -6
 
 GENCD_LOSS_SQUARED, GENCD_LOSS_LOGISTIC = 0, 1
 GENCD_SHOTGUN, GENCD_THREAD_GREEDY, GENCD_GREEDY, GENCD_COLORING = 0, 1, 2, 3
-GENCD_F64, GENCD_F32 = 0, 1
+GENCD_F64, GENCD_F32, GENCD_BF16, GENCD_BINARY = 0, 1, 2, 3
 GENCD_HOST, GENCD_DEVICE = 0, 1
 
 LOSSES = {"squared": GENCD_LOSS_SQUARED, "logistic": GENCD_LOSS_LOGISTIC}
 VARIANTS = {"shotgun": GENCD_SHOTGUN, "thread_greedy": GENCD_THREAD_GREEDY, "greedy": GENCD_GREEDY,
             "coloring": GENCD_COLORING}
-PRECISIONS = {"f64": GENCD_F64, "f32": GENCD_F32}
+PRECISIONS = {"f64": GENCD_F64, "f32": GENCD_F32, "bf16": GENCD_BF16, "binary": GENCD_BINARY}
 KERNELS = ["propose_all", "finalize", "accept", "update", "refresh", "propose_list", "coloring_iter",
            "objective", "setup", "propose_light", "propose_slabs", "pairs_reduce"]
 
@@ -47,7 +47,12 @@ EXPORTS = ["gencd_create", "gencd_destroy", "gencd_set_lambda", "gencd_lambda_ma
            "gencd_set_w", "gencd_get_z", "gencd_objective", "gencd_propose_at", "gencd_propose_all",
            "gencd_spectral_radius", "gencd_color", "gencd_get_colors", "gencd_set_colors",
            "gencd_permutation", "gencd_profile_enable", "gencd_profile_read", "gencd_profile_reset",
-           "gencd_last_error", "gencd_stats", "gencd_stats_reset", "gencd_propose_all_noalloc"]
+           "gencd_last_error", "gencd_stats", "gencd_stats_reset", "gencd_propose_all_noalloc",
+           # include/gencd_batch.h
+           "gencd_batch_create", "gencd_batch_destroy", "gencd_batch_slots", "gencd_batch_lambda_max",
+           "gencd_batch_set_params", "gencd_batch_set_slot", "gencd_batch_copy_slot", "gencd_batch_clear_slot",
+           "gencd_batch_get_w", "gencd_batch_iterate", "gencd_batch_objective", "gencd_batch_propose",
+           "gencd_batch_path"]
 
 
 class gencd_params(C.Structure):
@@ -63,6 +68,16 @@ class gencd_result(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class gencd_path(C.Structure):
+    _fields_ = [("nchains", C.c_int32), ("nlambda", C.c_int32), ("held_out", C.c_void_p), ("lambda_", C.c_void_p),
+                ("handoff", C.c_double), ("warm", C.c_int32), ("reserved", C.c_int32)]
+
+
+class gencd_path_solve(C.Structure):
+    _fields_ = [("status", C.c_int32), ("slot", C.c_int32), ("iters", C.c_int64), ("objective", C.c_double),
+                ("kkt", C.c_double), ("t_start", C.c_double), ("t_end", C.c_double)]
 
 
 class GencdError(RuntimeError):
@@ -115,6 +130,20 @@ def lib():
             "gencd_stats_reset": (C.c_int, [vp]),
             "gencd_propose_all_noalloc": (C.c_int, [i64, i64, i64, vp, vp, vp, vp, vp, vp, i32, f64, i32, vp, vp,
                                                     vp, vp]),
+            # include/gencd_batch.h
+            "gencd_batch_create": (C.c_int, [pp, i64, i64, i64, vp, vp, vp, i32, vp, i32, vp, i32, i32, i32, vp]),
+            "gencd_batch_destroy": (None, [vp]),
+            "gencd_batch_slots": (C.c_int, [vp, C.POINTER(i32)]),
+            "gencd_batch_lambda_max": (C.c_int, [vp, i32, C.POINTER(f64)]),
+            "gencd_batch_set_params": (C.c_int, [vp, C.POINTER(gencd_params)]),
+            "gencd_batch_set_slot": (C.c_int, [vp, i32, i32, f64, vp, i32]),
+            "gencd_batch_copy_slot": (C.c_int, [vp, i32, i32, i32, f64]),
+            "gencd_batch_clear_slot": (C.c_int, [vp, i32]),
+            "gencd_batch_get_w": (C.c_int, [vp, i32, vp, i64, i32]),
+            "gencd_batch_iterate": (C.c_int, [vp, i64, i32]),
+            "gencd_batch_objective": (C.c_int, [vp, vp, vp]),
+            "gencd_batch_propose": (C.c_int, [vp, vp, vp, i32]),
+            "gencd_batch_path": (C.c_int, [vp, C.POINTER(gencd_path), vp, vp, C.POINTER(gencd_result)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -452,3 +481,176 @@ class Problem:
 
     def stats_reset(self):
         gencd_stats_reset(self.h)
+
+
+# --- include/gencd_batch.h ----------------------------------------------------
+
+def gencd_batch_create(n, k, nnz, col_ptr, row_idx, val, y, loss="logistic", fold=None, nfolds=0, slots=32,
+                       stream=None):
+    """Opaque batch handle over one X (host numpy arrays or CUDA tensors)."""
+    if _is_cuda_tensor(val):
+        val_dtype = 0 if str(val.dtype) == "torch.float64" else 1
+        vdt = None
+    else:
+        vdt = np.float32 if np.asarray(val).dtype == np.float32 else np.float64
+        val_dtype = 0 if vdt == np.float64 else 1
+    cp, m0, k0 = _buf(col_ptr, np.int64)
+    ri, m1, k1 = _buf(row_idx, np.int32)
+    va, m2, k2 = _buf(val, vdt)
+    yy, m3, k3 = _buf(y, np.float64)
+    fo, m4, k4 = _buf(fold, np.uint8)
+    mems = {m0, m1, m2, m3} if nnz > 0 else {m0, m3}
+    if fold is not None:
+        mems.add(m4)
+    if len(mems) != 1:
+        raise ValueError("inputs must be all host arrays or all device tensors")
+    handle = C.c_void_p()
+    st = default_stream() if stream is None else int(stream)
+    _check(lib().gencd_batch_create(C.byref(handle), int(n), int(k), int(nnz), cp, ri, va, val_dtype, yy,
+                                    LOSSES.get(loss, loss), fo, int(nfolds), int(slots), mems.pop(),
+                                    C.c_void_p(st)))
+    del k0, k1, k2, k3, k4
+    return handle
+
+
+def gencd_batch_destroy(h):
+    lib().gencd_batch_destroy(h)
+
+
+def gencd_batch_slots(h) -> int:
+    v = C.c_int32()
+    _check(lib().gencd_batch_slots(h, C.byref(v)))
+    return v.value
+
+
+def gencd_batch_lambda_max(h, held_out=-1) -> float:
+    v = C.c_double()
+    _check(lib().gencd_batch_lambda_max(h, int(held_out), C.byref(v)))
+    return v.value
+
+
+def gencd_batch_set_params(h, params: gencd_params):
+    _check(lib().gencd_batch_set_params(h, C.byref(params)))
+
+
+def gencd_batch_set_slot(h, slot, held_out, lam, w=None):
+    ptr, mem, keep = _buf(w, np.float64)
+    _check(lib().gencd_batch_set_slot(h, int(slot), int(held_out), float(lam), ptr, mem))
+    del keep
+
+
+def gencd_batch_copy_slot(h, dst, src, held_out, lam):
+    _check(lib().gencd_batch_copy_slot(h, int(dst), int(src), int(held_out), float(lam)))
+
+
+def gencd_batch_clear_slot(h, slot):
+    _check(lib().gencd_batch_clear_slot(h, int(slot)))
+
+
+def gencd_batch_get_w(h, slot, k):
+    w = np.empty(int(k))
+    _check(lib().gencd_batch_get_w(h, int(slot), C.c_void_p(w.ctypes.data), int(k), GENCD_HOST))
+    return w
+
+
+def gencd_batch_iterate(h, iters, sync=True):
+    _check(lib().gencd_batch_iterate(h, int(iters), 1 if sync else 0))
+
+
+def gencd_batch_objective(h, slots):
+    o = np.empty(int(slots))
+    kk = np.empty(int(slots))
+    _check(lib().gencd_batch_objective(h, C.c_void_p(o.ctypes.data), C.c_void_p(kk.ctypes.data)))
+    return o, kk
+
+
+def gencd_batch_propose(h, slots, k):
+    d = np.empty((int(slots), int(k)))
+    f = np.empty((int(slots), int(k)))
+    _check(lib().gencd_batch_propose(h, C.c_void_p(d.ctypes.data), C.c_void_p(f.ctypes.data), GENCD_HOST))
+    return d, f
+
+
+def gencd_batch_path(h, held_out, lambdas, k, handoff=0.0, warm=True, want_w=False):
+    """Runs a path: held_out int[nchains], lambdas float[nchains, nlambda].
+    Returns (per-solve records as a list of dicts, w array [nchains, nlambda, k]
+    or None, totals gencd_result).  A solve that did not converge is reported
+    in its record's status, not raised."""
+    ho = np.ascontiguousarray(held_out, np.int32)
+    lam = np.ascontiguousarray(lambdas, np.float64)
+    C_, L = lam.shape
+    if ho.size != C_:
+        raise ValueError("one held-out fold per chain")
+    spec = gencd_path(nchains=C_, nlambda=L, held_out=C.c_void_p(ho.ctypes.data),
+                      lambda_=C.c_void_p(lam.ctypes.data), handoff=float(handoff), warm=1 if warm else 0)
+    recs = (gencd_path_solve * (C_ * L))()
+    w = np.empty((C_, L, int(k))) if want_w else None
+    r = gencd_result()
+    rc = lib().gencd_batch_path(h, C.byref(spec), C.cast(recs, C.c_void_p),
+                                C.c_void_p(w.ctypes.data) if want_w else None, C.byref(r))
+    _check(rc)
+    out = [{f: getattr(x, f) for f, _ in gencd_path_solve._fields_} for x in recs]
+    return out, w, r
+
+
+class Batch:
+    """Owns one batch handle; methods forward to the calls above."""
+
+    def __init__(self, prob, *, fold=None, nfolds=0, slots=32, loss=None, stream=None):
+        self.n, self.k, self.nnz = int(prob.n), int(prob.k), int(prob.nnz)
+        self.h = gencd_batch_create(prob.n, prob.k, prob.nnz, prob.col_ptr, prob.row_idx, prob.val, prob.y,
+                                    loss or prob.loss, fold, nfolds, slots, stream)
+        self.slots = gencd_batch_slots(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            gencd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def lambda_max(self, held_out=-1):
+        return gencd_batch_lambda_max(self.h, held_out)
+
+    def set_params(self, **kw):
+        p = gencd_default_params()
+        for key, v in kw.items():
+            if key == "variant" and isinstance(v, str):
+                v = VARIANTS[v]
+            setattr(p, key, v)
+        gencd_batch_set_params(self.h, p)
+        return p
+
+    def set_slot(self, slot, held_out, lam, w=None):
+        gencd_batch_set_slot(self.h, slot, held_out, lam, w)
+
+    def copy_slot(self, dst, src, held_out, lam):
+        gencd_batch_copy_slot(self.h, dst, src, held_out, lam)
+
+    def clear_slot(self, slot):
+        gencd_batch_clear_slot(self.h, slot)
+
+    def w(self, slot):
+        return gencd_batch_get_w(self.h, slot, self.k)
+
+    def iterate(self, iters, sync=True):
+        gencd_batch_iterate(self.h, iters, sync)
+
+    def objective(self):
+        return gencd_batch_objective(self.h, self.slots)
+
+    def propose(self):
+        return gencd_batch_propose(self.h, self.slots, self.k)
+
+    def path(self, held_out, lambdas, handoff=0.0, warm=True, want_w=False):
+        return gencd_batch_path(self.h, held_out, lambdas, self.k, handoff, warm, want_w)

@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgencd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "kernels_propose.cu", "kernels_update.cu", "kernels_setup.cu", "propose_plan.cu",
-           "noalloc.cu"]
+           "noalloc.cu", "batch.cu"]
 
 
 def _nvcc() -> str:
@@ -31,7 +31,7 @@ def _nvcc() -> str:
 
 
 def _deps():
-    out = [os.path.join(INCLUDE, "gencd.h")]
+    out = [os.path.join(INCLUDE, h) for h in os.listdir(INCLUDE) if h.endswith(".h")]
     for f in os.listdir(CSRC):
         out.append(os.path.join(CSRC, f))
     return out

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "device_math.cuh"
 #include "gencd_internal.cuh"
 
@@ -337,7 +339,7 @@ static void free_problem(gencd_problem* p) {
                   p->delta, p->phi, p->list_j, p->list_d, p->dscal, p->red, p->perm, p->sort_tmp,
                   p->row_ptr, p->col_idx, p->csr_val, p->color, p->color_ptr, p->cols_by_color,
                   p->slot_m, p->slot_d, p->slot_j, p->list_off, p->scan_tmp, p->bj, p->w32, p->bj32, p->ib32,
-                  p->part_lo};
+                  p->part_lo, p->col_val};
   if (p->stream) cudaStreamSynchronize(p->stream);
   free_propose_plan(p);
   if (p->gnat && p->gnat != p->gacc) cudaFree(p->gnat);
@@ -347,6 +349,63 @@ static void free_problem(gencd_problem* p) {
   for (cudaEvent_t e : p->prof.pool) cudaEventDestroy(e);
   cudaGetLastError();
   delete p;
+}
+
+// bfloat16 storage: the FP32 values rounded to bfloat16 (nearest even), in
+// place; *bad = 0 when a value leaves the bfloat16 range
+__global__ void k_round_bf16(float* __restrict__ v, int64_t m, unsigned long long* __restrict__ bad) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    const float r = __bfloat162float(__float2bfloat16_rn(v[i]));
+    if (!isfinite(r)) atomicMin(bad, 0ull);
+    v[i] = r;
+  }
+}
+
+// index-only storage: s_j = the value of column j's non-zeros (0 for an empty
+// column); *bad = the lowest column whose non-zeros differ
+__global__ void k_column_values(const int64_t* __restrict__ col_ptr, const float* __restrict__ val, int64_t k,
+                                float* __restrict__ col_val, unsigned long long* __restrict__ bad) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) {
+    const int64_t s = col_ptr[j], e = col_ptr[j + 1];
+    const float v0 = s < e ? val[s] : 0.0f;
+    col_val[j] = v0;
+    for (int64_t t = s + 1; t < e; ++t)
+      if (val[t] != v0) {
+        atomicMin(bad, (unsigned long long)j);
+        break;
+      }
+  }
+}
+
+// Converts the FP32 values to the storage mode's (bfloat16 rounding, or the
+// per-column values of binary storage).  *bad: -1 if the values fit the mode,
+// else the first offending column (binary) or 0 (a value beyond bfloat16).
+static int store_values(gencd_problem* p, int64_t* bad_out) {
+  *bad_out = -1;
+  if (p->vmode == kValPlain) return GENCD_OK;
+  if (p->vmode == kValNone) GENCD_TRY(dalloc(&p->col_val, p->k));
+  unsigned long long* bad = nullptr;
+  GENCD_TRY(dalloc(&bad, 1));
+  unsigned long long h = ~0ull;
+  int rc = GENCD_OK;
+  if (cudaMemcpyAsync(bad, &h, 8, cudaMemcpyHostToDevice, p->stream) != cudaSuccess) rc = GENCD_ECUDA;
+  if (rc == GENCD_OK) {
+    if (p->vmode == kValBf16)
+      k_round_bf16<<<grid_for(p->nnz, kThreads, p->num_sms * 8), kThreads, 0, p->stream>>>((float*)p->val, p->nnz,
+                                                                                          bad);
+    else
+      k_column_values<<<grid_for(p->k, kThreads, p->num_sms * 8), kThreads, 0, p->stream>>>(
+          p->col_ptr, (const float*)p->val, p->k, p->col_val, bad);
+    if (cudaMemcpyAsync(&h, bad, 8, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+        cudaStreamSynchronize(p->stream) != cudaSuccess)
+      rc = fail(GENCD_ECUDA, std::string("storage conversion: ") + cudaGetErrorString(cudaGetLastError()));
+  }
+  cudaFree(bad);
+  p->prof.launches[K_SETUP] += 1;
+  if (rc == GENCD_OK && h != ~0ull) *bad_out = (int64_t)h;
+  return rc;
 }
 
 static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* row_idx, const void* val,
@@ -365,7 +424,7 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
   GENCD_TRY(dalloc((char**)&p->val, vsz * p->nnz_pad));
   GENCD_TRY(dalloc(&p->y, n));
   GENCD_TRY(dalloc(&p->z, n));
-  GENCD_TRY(dalloc((char**)&p->u, vsz * n));
+  GENCD_TRY(dalloc((char**)&p->u, vsz * (n + 1)));  // u[n] = 0: the row that padding entries may gather
   GENCD_TRY(dalloc(&p->w, k));
   GENCD_TRY(dalloc(&p->c, k));
   GENCD_TRY(dalloc(&p->ib, k));
@@ -434,7 +493,15 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
     return fail(GENCD_EINVAL, "label y[" + std::to_string(bad_row) + "] is not finite" +
                                   (p->loss == GENCD_LOSS_LOGISTIC ? " or not -1/+1 (logistic loss)" : ""));
 
+  int64_t bad_store = -1;  // bfloat16 rounding, or binary storage's one value per column
+  GENCD_TRY(store_values(p, &bad_store));
+  if (bad_store >= 0)
+    return fail(GENCD_EINVAL, p->vmode == kValBf16 ? std::string("a value of X is beyond the bfloat16 range")
+                                                    : "column " + std::to_string(bad_store) +
+                                                          " has non-zeros of different values (binary storage "
+                                                          "holds one value per column)");
   GENCD_CUDA_TRY(cudaMemsetAsync(p->z, 0, sizeof(double) * n, st));
+  GENCD_CUDA_TRY(cudaMemsetAsync(p->u, 0, vsz * (n + 1), st));
   GENCD_CUDA_TRY(cudaMemsetAsync(p->w, 0, sizeof(double) * k, st));
   if (p->w32) GENCD_CUDA_TRY(cudaMemsetAsync(p->w32, 0, sizeof(float) * k, st));
   GENCD_CUDA_TRY(cudaMemsetAsync(p->gacc, 0, sizeof(double) * k, st));
@@ -495,7 +562,8 @@ int gencd_create(gencd_problem** out, int64_t n, int64_t k, int64_t nnz, const i
     return fail(GENCD_EINVAL, "a required input pointer is NULL");
   if (val_dtype != 0 && val_dtype != 1) return fail(GENCD_EINVAL, "val_dtype must be 0 (double) or 1 (float)");
   if (loss != GENCD_LOSS_SQUARED && loss != GENCD_LOSS_LOGISTIC) return fail(GENCD_EINVAL, "unknown loss");
-  if (precision != GENCD_F64 && precision != GENCD_F32) return fail(GENCD_EINVAL, "unknown precision");
+  if (precision != GENCD_F64 && precision != GENCD_F32 && precision != GENCD_BF16 && precision != GENCD_BINARY)
+    return fail(GENCD_EINVAL, "unknown precision");
   if (memory != GENCD_HOST && memory != GENCD_DEVICE) return fail(GENCD_EINVAL, "unknown memory kind");
   gencd_problem* p = new (std::nothrow) gencd_problem();
   if (!p) return fail(GENCD_ENOMEM, "host allocation failed");
@@ -503,7 +571,9 @@ int gencd_create(gencd_problem** out, int64_t n, int64_t k, int64_t nnz, const i
   p->k = k;
   p->nnz = nnz;
   p->loss = loss;
-  p->precision = precision;
+  p->user_precision = precision;
+  p->precision = precision == GENCD_F64 ? GENCD_F64 : GENCD_F32;  // BF16 and BINARY compute in FP32
+  p->vmode = precision == GENCD_BF16 ? kValBf16 : precision == GENCD_BINARY ? kValNone : kValPlain;
   p->stream = (cudaStream_t)stream;
   int rc = create_impl(p, col_ptr, row_idx, val, val_dtype, y, memory);
   if (rc != GENCD_OK) {

@@ -89,6 +89,13 @@ __device__ __forceinline__ uint64_t candidate_mag(double phi) {
   return ((b >> 63) && m != 0 && m <= 0x7ff0000000000000ull) ? m : 0ull;
 }
 
+// candidate_mag for an FP32 proxy (the same order on FP32 bit patterns)
+__device__ __forceinline__ uint32_t candidate_mag32(float phi) {
+  const uint32_t b = __float_as_uint(phi);
+  const uint32_t m = b & 0x7fffffffu;
+  return ((b >> 31) && m != 0 && m <= 0x7f800000u) ? m : 0u;
+}
+
 // FP32 copy of a coefficient that is 0 exactly when the coefficient is 0
 // (values below the float range keep their sign at the smallest denormal)
 __device__ __forceinline__ float w_mirror(double x) {

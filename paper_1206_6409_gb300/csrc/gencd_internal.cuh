@@ -48,6 +48,10 @@ constexpr int kItemsF64 = 4;   // nnz per lane in the streaming propose (FP64 mo
 constexpr int kItemsF32 = 8;   // nnz per lane in the streaming propose (FP32 mode)
 constexpr int kPadNnz = 64;    // CSC arrays are padded to a multiple of this
 constexpr int kThreads = 256;  // default CTA size
+// value storage of the streaming plan in FP32 arithmetic (gencd_problem::vmode)
+constexpr int kValPlain = 0;  // the storage precision's values
+constexpr int kValBf16 = 1;   // bfloat16 (GENCD_BF16)
+constexpr int kValNone = 2;   // index only, one value per column (GENCD_BINARY)
 // the single-CTA plan of an update list (lengths, prefix, w) takes lists of at
 // most kListPlanMax entries
 constexpr int kListPlanThreads = 1024;
@@ -110,6 +114,8 @@ struct ProposePlan {
   int32_t* light_row = nullptr;
   void* light_val = nullptr;
   int32_t* light_tile_lc = nullptr;  // light column of each 256-entry tile's first entry
+  float* light_scale = nullptr;      // index-only storage: the value of light column lc
+  float* heavy_scale = nullptr;      // index-only storage: the value of heavy column h
   uint8_t* lmask = nullptr;          // per 8 light entries: bit i = entry 8g + i starts a column
   // heavy columns
   int64_t nheavy = 0, entries = 0, npairs = 0, ntiles = 0;
@@ -138,7 +144,10 @@ struct gencd_problem {
   cudaStream_t stream = nullptr;
   int64_t n = 0, k = 0, nnz = 0, nnz_pad = 0;
   int32_t loss = GENCD_LOSS_LOGISTIC;
-  int32_t precision = GENCD_F64;
+  int32_t precision = GENCD_F64;  // arithmetic: GENCD_F64 or GENCD_F32 (BF16 and BINARY compute in FP32)
+  int32_t vmode = gencd::kValPlain;     // value storage of the streaming plan
+  int32_t user_precision = GENCD_F64;
+  float* col_val = nullptr;       // index-only storage: the value s_j shared by column j's non-zeros
   double lambda = 0.0;
   double lambda_max = 0.0;
   gencd_params params{};

@@ -353,11 +353,6 @@ __global__ void __launch_bounds__(kThreads)
 // accepted when that proxy is negative.  GB300 runs FP64 at a small fraction
 // of its FP32 rate, so the per-column work stays on the FP32 pipe.
 
-__device__ __forceinline__ uint64_t candidate_mag32(float phi) {
-  const uint32_t b = __float_as_uint(phi);
-  const uint32_t m = b & 0x7fffffffu;
-  return ((b >> 31) && m != 0 && m <= 0x7f800000u) ? (uint64_t)m : 0ull;
-}
 
 // one round of 4 columns per thread of NT: load, zero the sums, integer idle
 // test, queue the active columns (j, raw sum) in shared memory

@@ -20,7 +20,10 @@
 // pairs removes most atomics but costs more instructions than it saves in
 // this issue-bound kernel.)  Partial sums are kept in the storage precision
 // (FP32 atomics in FP32 mode).
+#include <cuda_bf16.h>
+
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "device_math.cuh"
@@ -34,6 +37,7 @@ constexpr int kSlabThreadsF64 = 1024;  // 32 warps, loads issued tile by tile
 constexpr int kSlabItemsF32 = 8;   // entries per lane and tile step
 constexpr int kSlabItemsF64 = 8;
 constexpr int kSlabPad = 16;       // slab entry ranges are padded to this
+constexpr int kSlabZeroSlot = 4;   // shared u slots past the slab (16 B); the first holds 0
 
 // ---------------------------------------------------------------------------
 // the kernel
@@ -66,19 +70,64 @@ __device__ __forceinline__ void emit_pair(G* __restrict__ partial, uint32_t slot
     atomicAdd(partial + slot, s);
 }
 
-// the entries of one lane: ITEMS in-slab rows (128-bit loads of 8) and values
-template <typename V, int ITEMS>
-struct LaneLoad {
-  uint4 rr[ITEMS / 8];
-  V v[ITEMS];
+// Values of a lane's entries as stored by the plan (SV): float or double,
+// bfloat16 (kept packed, two per register, widened on use), or none at all
+// (NoVal: index-only columns, every value 1; the column scale is applied to
+// the column's sum outside the streaming loop).
+struct NoVal {};
+
+template <typename SV, int N>
+struct ValRegs;
+
+template <int N>
+struct ValRegs<float, N> {
+  float v[N];
+  __device__ __forceinline__ void load(const float* __restrict__ p) { load_vals<float, N>(p, v); }
+  __device__ __forceinline__ float get(int i) const { return v[i]; }
 };
 
-template <typename V, int ITEMS>
-__device__ __forceinline__ void load_lane(const uint16_t* __restrict__ s_row, const V* __restrict__ s_val,
-                                          uint32_t a, LaneLoad<V, ITEMS>& L) {
+template <int N>
+struct ValRegs<double, N> {
+  double v[N];
+  __device__ __forceinline__ void load(const double* __restrict__ p) { load_vals<double, N>(p, v); }
+  __device__ __forceinline__ double get(int i) const { return v[i]; }
+};
+
+template <int N>
+struct ValRegs<__nv_bfloat16, N> {
+  uint32_t w[N / 2];  // value 2q in the low half of w[q], 2q + 1 in the high half
+  __device__ __forceinline__ void load(const __nv_bfloat16* __restrict__ p) {
+#pragma unroll
+    for (int q = 0; q < N / 8; ++q) {
+      const uint4 x = __ldcs(reinterpret_cast<const uint4*>(p) + q);
+      w[4 * q] = x.x, w[4 * q + 1] = x.y, w[4 * q + 2] = x.z, w[4 * q + 3] = x.w;
+    }
+  }
+  __device__ __forceinline__ float get(int i) const {  // bfloat16 -> float: the upper 16 bits
+    const uint32_t x = w[i >> 1];
+    return __uint_as_float((i & 1) ? (x & 0xffff0000u) : (x << 16));
+  }
+};
+
+template <int N>
+struct ValRegs<NoVal, N> {
+  __device__ __forceinline__ void load(const NoVal*) {}
+  __device__ __forceinline__ float get(int) const { return 1.0f; }
+};
+
+// the entries of one lane: ITEMS in-slab rows (128-bit loads of 8) and values
+template <typename SV, int ITEMS>
+struct LaneLoad {
+  uint4 rr[ITEMS / 8];
+  ValRegs<SV, ITEMS> val;
+};
+
+template <typename SV, int ITEMS>
+__device__ __forceinline__ void load_lane(const uint16_t* __restrict__ s_row, const SV* __restrict__ s_val,
+                                          uint32_t a, LaneLoad<SV, ITEMS>& L) {
 #pragma unroll
   for (int h = 0; h < ITEMS / 8; ++h) L.rr[h] = __ldcs(reinterpret_cast<const uint4*>(s_row + a) + h);
-  load_vals<V, ITEMS>(s_val + a, L.v);
+  L.val.load(s_val + a);
 }
 
 // start bits of a lane's ITEMS entries (one byte per 8 entries, little-endian)
@@ -118,23 +167,23 @@ __device__ __forceinline__ V lane_suffix_sum(V x, bool stop, int lane, bool& end
 // and last pairs take atomic adds.
 // one tile's loads for one lane: ITEMS rows and values, the start bits, and
 // the pair of the tile's first entry
-template <typename V, int ITEMS>
+template <typename SV, int ITEMS>
 struct TileStage {
-  LaneLoad<V, ITEMS> L;
+  LaneLoad<SV, ITEMS> L;
   uint32_t m, q0;
 };
 
-template <typename V, int ITEMS>
-__device__ __forceinline__ void load_stage(const uint16_t* __restrict__ s_row, const V* __restrict__ s_val,
+template <typename SV, int ITEMS>
+__device__ __forceinline__ void load_stage(const uint16_t* __restrict__ s_row, const SV* __restrict__ s_val,
                                            const uint8_t* __restrict__ pmask,
                                            const uint32_t* __restrict__ tile_pair, int t, int t1, uint32_t base,
-                                           int tb, uint32_t slab_end, int lane, TileStage<V, ITEMS>& S) {
+                                           int tb, uint32_t slab_end, int lane, TileStage<SV, ITEMS>& S) {
   S.m = 0;
   if (t < t1) {
     S.q0 = __ldg(tile_pair + t);
     const uint32_t a = base + (uint32_t)(t - tb) * (32 * ITEMS) + lane * ITEMS;
     if (a < slab_end) {
-      load_lane<V, ITEMS>(s_row, s_val, a, S.L);
+      load_lane<SV, ITEMS>(s_row, s_val, a, S.L);
       S.m = lane_mask<ITEMS>(pmask, a);
     }
   }
@@ -143,9 +192,9 @@ __device__ __forceinline__ void load_stage(const uint16_t* __restrict__ s_row, c
 // THREADS per CTA (one CTA per SM); ITEMS entries per lane (a tile is 32 *
 // ITEMS entries); DEPTH tiles of loads in flight per warp beyond the one
 // being processed
-template <typename V, typename U, typename G, int THREADS, int DEPTH, int ITEMS>
+template <typename V, typename U, typename G, int THREADS, int DEPTH, int ITEMS, typename SV>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_propose_slabs(const uint16_t* __restrict__ s_row, const V* __restrict__ s_val,
+    k_propose_slabs(const uint16_t* __restrict__ s_row, const SV* __restrict__ s_val,
                     const uint8_t* __restrict__ pmask, const uint32_t* __restrict__ pair_slot,
                     const uint32_t* __restrict__ tile_start,
                     const uint32_t* __restrict__ tile_end, const uint32_t* __restrict__ tile_pair,
@@ -158,6 +207,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   U* s_u = reinterpret_cast<U*>(smem_raw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) s_u[slab_rows] = U(0);  // the row of padding entries (index-only storage)
   const int t_end = cta_tile_begin[blockIdx.x + 1];
   int t0 = cta_tile_begin[blockIdx.x];
   while (t0 < t_end) {
@@ -170,21 +220,21 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncthreads();  // the previous slab is no longer read
     for (int i = threadIdx.x; i < rows; i += blockDim.x) s_u[i] = u[row0 + i];
     __syncthreads();
-    TileStage<V, ITEMS> stg[DEPTH > 0 ? DEPTH : 1];
+    TileStage<SV, ITEMS> stg[DEPTH > 0 ? DEPTH : 1];
     int t = t0 + warp;
 #pragma unroll
     for (int d = 0; d < DEPTH; ++d)
-      load_stage<V, ITEMS>(s_row, s_val, pmask, tile_pair, t + d * nw, t1, base, tb, slab_end, lane, stg[d]);
+      load_stage<SV, ITEMS>(s_row, s_val, pmask, tile_pair, t + d * nw, t1, base, tb, slab_end, lane, stg[d]);
     for (; t < t1; t += nw) {  // warp-uniform loop
-      TileStage<V, ITEMS> cur;
+      TileStage<SV, ITEMS> cur;
       if (DEPTH > 0) {
         cur = stg[0];
 #pragma unroll
         for (int d = 0; d + 1 < DEPTH; ++d) stg[d] = stg[d + 1];
-        load_stage<V, ITEMS>(s_row, s_val, pmask, tile_pair, t + DEPTH * nw, t1, base, tb, slab_end, lane,
-                             stg[DEPTH - 1]);
+        load_stage<SV, ITEMS>(s_row, s_val, pmask, tile_pair, t + DEPTH * nw, t1, base, tb, slab_end, lane,
+                              stg[DEPTH - 1]);
       } else {
-        load_stage<V, ITEMS>(s_row, s_val, pmask, tile_pair, t, t1, base, tb, slab_end, lane, cur);
+        load_stage<SV, ITEMS>(s_row, s_val, pmask, tile_pair, t, t1, base, tb, slab_end, lane, cur);
       }
       const uint32_t ts = base + (uint32_t)(t - tb) * TILE;
       const uint32_t te = slab_end - ts < (uint32_t)TILE ? slab_end : ts + TILE;
@@ -238,7 +288,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             acc = V(0);
             ++qi;
           }
-          acc = fma(cur.L.v[i], (V)uu[i], acc);
+          acc = fma((V)cur.L.val.get(i), (V)uu[i], acc);
         }
         if (inner) {
           if (m & 1u)
@@ -290,58 +340,59 @@ __device__ __forceinline__ void load_rows8(const int32_t* __restrict__ p, int32_
   r[0] = a.x, r[1] = a.y, r[2] = a.z, r[3] = a.w, r[4] = b.x, r[5] = b.y, r[6] = b.z, r[7] = b.w;
 }
 
-// one lane's loads of a light tile: 8 rows, 8 values, the start bits, and the
-// light column of the tile's first entry
-template <typename V>
+// one lane's loads of a light tile: 8 rows, 8 values (as stored), the start
+// bits, and the light column of the tile's first entry
+template <typename SV>
 struct LightStage {
   int32_t r[8];
-  V v[8];
+  ValRegs<SV, 8> val;
   uint32_t m, lc0;
 };
 
-template <typename V>
-__device__ __forceinline__ void load_light_stage(const int32_t* __restrict__ row, const V* __restrict__ val,
+template <typename SV>
+__device__ __forceinline__ void load_light_stage(const int32_t* __restrict__ row, const SV* __restrict__ val,
                                                  const uint8_t* __restrict__ lmask,
                                                  const int32_t* __restrict__ tile_lc, int64_t t, int64_t ntiles,
-                                                 int64_t nnz, int lane, LightStage<V>& S) {
+                                                 int64_t nnz, int lane, LightStage<SV>& S) {
   S.m = 0;
   if (t < ntiles) {
     S.lc0 = (uint32_t)__ldg(tile_lc + t);
     const int64_t a = t * kLightTile + (int64_t)lane * kLightItems;
     if (a < nnz) {  // the arrays are padded: a lane's 8 entries are in bounds
       load_rows8(row + a, S.r);
-      load8<V>(val + a, S.v);
+      S.val.load(val + a);
       S.m = lmask[a >> 3];
     }
   }
 }
 
-template <typename V, typename U, typename G>
+// lscale (index-only columns): each column's sum is scaled by its value
+template <typename V, typename U, typename G, typename SV>
 __global__ void __launch_bounds__(kThreads, 3)
-    k_propose_light_runs(const int32_t* __restrict__ row, const V* __restrict__ val,
+    k_propose_light_runs(const int32_t* __restrict__ row, const SV* __restrict__ val,
                          const uint8_t* __restrict__ lmask, const int32_t* __restrict__ tile_lc,
-                         const int32_t* __restrict__ light_cols, const U* __restrict__ u, int64_t nnz,
-                         int64_t ntiles, G* __restrict__ out) {
+                         const int32_t* __restrict__ light_cols, const float* __restrict__ lscale,
+                         const U* __restrict__ u, int64_t nnz, int64_t ntiles, G* __restrict__ out) {
   const unsigned FULL = 0xffffffffu;
+  constexpr bool kScaled = std::is_same<SV, NoVal>::value;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   constexpr bool kPrefetch = sizeof(V) == 4;  // FP64 stages are too large to double in registers
-  LightStage<V> nxt;
-  if (kPrefetch) load_light_stage(row, val, lmask, tile_lc, warp, ntiles, nnz, lane, nxt);
+  LightStage<SV> nxt;
+  if (kPrefetch) load_light_stage<SV>(row, val, lmask, tile_lc, warp, ntiles, nnz, lane, nxt);
   for (int64_t t = warp; t < ntiles; t += nwarps) {  // warp-uniform
-    LightStage<V> cur;
+    LightStage<SV> cur;
     if (kPrefetch) {
       cur = nxt;
-      load_light_stage(row, val, lmask, tile_lc, t + nwarps, ntiles, nnz, lane, nxt);  // next tile's loads in flight
+      load_light_stage<SV>(row, val, lmask, tile_lc, t + nwarps, ntiles, nnz, lane, nxt);  // next tile in flight
     } else {
-      load_light_stage(row, val, lmask, tile_lc, t, ntiles, nnz, lane, cur);
+      load_light_stage<SV>(row, val, lmask, tile_lc, t, ntiles, nnz, lane, cur);
     }
     const int64_t a = t * kLightTile + (int64_t)lane * kLightItems;
     const bool active = a < nnz;
     const uint32_t m = cur.m, lc0 = cur.lc0;
     const int32_t* r = cur.r;
-    const V* v = cur.v;
     const uint32_t cnt = __popc(lane == 0 ? (m & 0xfeu) : m);
     uint32_t incl = cnt;
 #pragma unroll
@@ -350,10 +401,16 @@ __global__ void __launch_bounds__(kThreads, 3)
       if (lane >= d) incl += y;
     }
     uint32_t q = lc0 + (incl - cnt) + (lane > 0 ? (m & 1u) : 0u);
-    // columns this lane may write, loaded early
+    // columns this lane may write (and their scales), loaded early
     const bool lead = lane == 0 && active && !(m & 1u);
+    const uint32_t ql = q + __popc(m & 0xfeu);
     const int32_t j0 = lead ? __ldg(light_cols + lc0) : 0;
-    const int32_t jl = (active && m != 0u) ? __ldg(light_cols + q + __popc(m & 0xfeu)) : 0;
+    const int32_t jl = (active && m != 0u) ? __ldg(light_cols + ql) : 0;
+    V s0 = V(1), sl = V(1);
+    if (kScaled) {
+      s0 = lead ? (V)__ldg(lscale + lc0) : V(1);
+      sl = (active && m != 0u) ? (V)__ldg(lscale + ql) : V(1);
+    }
     V cont = V(0), tail = V(0);
     bool has_tail = false;
     if (active) {
@@ -368,20 +425,24 @@ __global__ void __launch_bounds__(kThreads, 3)
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         if ((inner >> i) & 1u) {
-          if (i == bf)
+          if (i == bf) {
             first = acc;
-          else
-            out[__ldg(light_cols + qi)] = (G)acc;  // a whole column inside the lane
+          } else {  // a whole column inside the lane
+            const V sc = kScaled ? (V)__ldg(lscale + qi) : V(1);
+            out[__ldg(light_cols + qi)] = (G)(acc * sc);
+          }
           acc = V(0);
           ++qi;
         }
-        acc = fma(v[i], (V)uu[i], acc);
+        acc = fma((V)cur.val.get(i), (V)uu[i], acc);
       }
       if (inner) {
-        if (m & 1u)
-          out[__ldg(light_cols + q)] = (G)first;  // started at entry 0, ended inside
-        else
+        if (m & 1u) {  // started at entry 0, ended inside
+          const V sc = kScaled ? (V)__ldg(lscale + q) : V(1);
+          out[__ldg(light_cols + q)] = (G)(first * sc);
+        } else {
           cont = first;
+        }
         tail = acc;
         has_tail = true;
       } else if (m & 1u) {
@@ -394,16 +455,16 @@ __global__ void __launch_bounds__(kThreads, 3)
     const bool stop = !active || m != 0u;
     if (__ballot_sync(FULL, stop) == 0u) {
       const V sum = warp_sum(cont);  // the whole tile is inside column lc0
-      if (lane == 0) atomicAdd(out + j0, (G)sum);
+      if (lane == 0) atomicAdd(out + j0, (G)(sum * s0));
     } else {
       bool ended;
       const V tsum = lane_suffix_sum(cont, stop, lane, ended);
       const V t1s = __shfl_down_sync(FULL, tsum, 1);
       const bool e1 = __shfl_down_sync(FULL, (int)ended, 1) != 0;
-      if (lead) atomicAdd(out + j0, (G)tsum);  // column from the previous tile
+      if (lead) atomicAdd(out + j0, (G)(tsum * s0));  // column from the previous tile
       if (has_tail) {
         const V sum = tail + (lane < 31 ? t1s : V(0));
-        emit_pair<G>(out, (uint32_t)jl, (G)sum, lane < 31 && e1);
+        emit_pair<G>(out, (uint32_t)jl, (G)(sum * sl), lane < 31 && e1);
       }
     }
   }
@@ -412,9 +473,11 @@ __global__ void __launch_bounds__(kThreads, 3)
 // sum of each heavy column = its partials in slab order (the slots of column h
 // are hslot_ptr[h] .. hslot_ptr[h+1], at most one per slab); partials reset.
 // The loads of up to 32 slots are issued together, then summed in order.
+// hscale (index-only columns): the sum is scaled by the column's value
 template <typename G>
 __global__ void k_pairs_to_gacc(const uint32_t* __restrict__ hslot_ptr, const int32_t* __restrict__ heavy_cols,
-                                int64_t nheavy, G* __restrict__ partial, G* __restrict__ gacc) {
+                                int64_t nheavy, G* __restrict__ partial, G* __restrict__ gacc,
+                                const float* __restrict__ hscale) {
   constexpr int CH = 32;
   const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= nheavy) return;
@@ -430,51 +493,58 @@ __global__ void k_pairs_to_gacc(const uint32_t* __restrict__ hslot_ptr, const in
     for (int i = 0; i < CH; ++i)
       if (base + i < e) partial[base + i] = G(0);
   }
-  gacc[heavy_cols[h]] = s;
+  gacc[heavy_cols[h]] = hscale ? s * (G)hscale[h] : s;
 }
 
-int launch_propose_plan(gencd_problem* p, const void* u_vec) {
+// the two streaming passes and the partial reduction for one value storage SV
+// (V compute type, U type of u, G accumulator)
+template <typename V, typename U, typename G, typename SV, int THREADS, int DEPTH, int ITEMS>
+static int launch_plan_passes(gencd_problem* p, const void* u_vec) {
   ProposePlan& P = p->plan;
   if (P.nlight > 0) {
     cudaEvent_t e = nullptr;
     prof_begin(p, K_PROPOSE_LIGHT, &e);
     const int grid = grid_for(P.light_ntiles * 32, kThreads, p->num_sms * 3);  // resident CTAs: persistent warps
-    if (p->precision == GENCD_F64)
-      k_propose_light_runs<double, double, double><<<grid, kThreads, 0, p->stream>>>(
-          P.light_row, (const double*)P.light_val, P.lmask, P.light_tile_lc, P.light_cols, (const double*)u_vec,
-          P.light_nnz, P.light_ntiles, (double*)p->gnat);
-    else
-      k_propose_light_runs<float, float, float><<<grid, kThreads, 0, p->stream>>>(
-          P.light_row, (const float*)P.light_val, P.lmask, P.light_tile_lc, P.light_cols, (const float*)u_vec,
-          P.light_nnz, P.light_ntiles, (float*)p->gnat);
+    k_propose_light_runs<V, U, G, SV><<<grid, kThreads, 0, p->stream>>>(
+        P.light_row, (const SV*)P.light_val, P.lmask, P.light_tile_lc, P.light_cols, P.light_scale,
+        (const U*)u_vec, P.light_nnz, P.light_ntiles, (G*)p->gnat);
     prof_end(p, e);
     GENCD_CUDA_TRY(cudaGetLastError());
   }
   if (P.nheavy > 0) {
-    const size_t smem = (size_t)P.slab_rows * (p->precision == GENCD_F64 ? 8 : 4);
+    const size_t smem = (size_t)(P.slab_rows + kSlabZeroSlot) * sizeof(U);
     const int g2 = (int)((P.nheavy + kThreads - 1) / kThreads);  // one thread per heavy column
     cudaEvent_t e1 = nullptr, e2 = nullptr;
     prof_begin(p, K_PROPOSE_SLABS, &e1);
-    if (p->precision == GENCD_F64)
-      k_propose_slabs<double, double, double, kSlabThreadsF64, 0, kSlabItemsF64><<<P.grid, kSlabThreadsF64, smem, p->stream>>>(
-          P.s_row, (const double*)P.s_val, P.pmask, P.pair_slot, P.tile_start, P.tile_end, P.tile_pair, P.tile_slab,
-          P.slab_tile_begin, P.cta_tile_begin, (const double*)u_vec, p->n, P.slab_rows, (double*)P.partial);
-    else
-      k_propose_slabs<float, float, float, kSlabThreadsF32, 1, kSlabItemsF32><<<P.grid, kSlabThreadsF32, smem, p->stream>>>(
-          P.s_row, (const float*)P.s_val, P.pmask, P.pair_slot, P.tile_start, P.tile_end, P.tile_pair, P.tile_slab,
-          P.slab_tile_begin, P.cta_tile_begin, (const float*)u_vec, p->n, P.slab_rows, (float*)P.partial);
+    k_propose_slabs<V, U, G, THREADS, DEPTH, ITEMS, SV><<<P.grid, THREADS, smem, p->stream>>>(
+        P.s_row, (const SV*)P.s_val, P.pmask, P.pair_slot, P.tile_start, P.tile_end, P.tile_pair, P.tile_slab,
+        P.slab_tile_begin, P.cta_tile_begin, (const U*)u_vec, p->n, P.slab_rows, (G*)P.partial);
     prof_end(p, e1);
     prof_begin(p, K_PAIRS, &e2);
-    if (p->precision == GENCD_F64)
-      k_pairs_to_gacc<double><<<g2, kThreads, 0, p->stream>>>(P.hslot_ptr, P.heavy_cols, P.nheavy,
-                                                               (double*)P.partial, (double*)p->gnat);
-    else
-      k_pairs_to_gacc<float><<<g2, kThreads, 0, p->stream>>>(P.hslot_ptr, P.heavy_cols, P.nheavy,
-                                                              (float*)P.partial, (float*)p->gnat);
+    k_pairs_to_gacc<G><<<g2, kThreads, 0, p->stream>>>(P.hslot_ptr, P.heavy_cols, P.nheavy, (G*)P.partial,
+                                                        (G*)p->gnat, P.heavy_scale);
     prof_end(p, e2);
     GENCD_CUDA_TRY(cudaGetLastError());
   }
   return GENCD_OK;
+}
+
+template <typename V, typename U, typename G, typename SV, int THREADS, int DEPTH, int ITEMS>
+static int set_slab_smem(const ProposePlan& P) {
+  GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_slabs<V, U, G, THREADS, DEPTH, ITEMS, SV>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)((size_t)(P.slab_rows + kSlabZeroSlot) * sizeof(U))));
+  return GENCD_OK;
+}
+
+#define GENCD_PLAN_F64 double, double, double, double, kSlabThreadsF64, 0, kSlabItemsF64
+#define GENCD_PLAN_F32(SV) float, float, float, SV, kSlabThreadsF32, 1, kSlabItemsF32
+
+int launch_propose_plan(gencd_problem* p, const void* u_vec) {
+  if (p->precision == GENCD_F64) return launch_plan_passes<GENCD_PLAN_F64>(p, u_vec);
+  if (p->vmode == kValBf16) return launch_plan_passes<GENCD_PLAN_F32(__nv_bfloat16)>(p, u_vec);
+  if (p->vmode == kValNone) return launch_plan_passes<GENCD_PLAN_F32(NoVal)>(p, u_vec);
+  return launch_plan_passes<GENCD_PLAN_F32(float)>(p, u_vec);
 }
 
 // ---------------------------------------------------------------------------
@@ -528,6 +598,26 @@ __global__ void k_plan_copy_light(const int64_t* __restrict__ col_ptr, const int
       lval[loff[j] + t] = val[s + t];
     }
   }
+}
+
+// value storage of the plan: bfloat16 copies (the values are bfloat16-exact)
+__global__ void k_plan_to_bf16(const float* __restrict__ src, int64_t m, __nv_bfloat16* __restrict__ dst) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride)
+    dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+template <typename T>
+__global__ void k_plan_fill(T* __restrict__ a, int64_t m, T v) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) a[i] = v;
+}
+
+// index-only storage: scale[c] = col_val[cols[c]]
+__global__ void k_plan_gather_scales(const int32_t* __restrict__ cols, int64_t m, const float* __restrict__ col_val,
+                                     float* __restrict__ scale) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < m; c += stride) scale[c] = col_val[cols[c]];
 }
 
 // bit p % 32 of word p / 32 (= bit p % 8 of byte p / 8) for the first entry p of
@@ -657,7 +747,8 @@ __global__ void k_plan_tiles(const int32_t* __restrict__ slab_tile_begin, const 
 
 void free_propose_plan(gencd_problem* p) {
   ProposePlan& P = p->plan;
-  void* bufs[] = {P.light_cols, P.light_col_ptr, P.light_row, P.light_val, P.light_tile_lc, P.lmask, P.heavy_cols,
+  void* bufs[] = {P.light_cols, P.light_col_ptr, P.light_row, P.light_val, P.light_tile_lc, P.lmask, P.light_scale,
+                  P.heavy_scale, P.heavy_cols,
                   P.s_row, P.s_val, P.pmask, P.pair_slot, P.hslot_ptr, P.partial, P.tile_start,
                   P.tile_end, P.tile_pair, P.tile_slab, P.slab_tile_begin, P.cta_tile_begin};
   for (void* b : bufs)
@@ -742,6 +833,10 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
     GENCD_TRY(palloc((char**)&P.light_val, lpad * (int64_t)vsz));
     GENCD_CUDA_TRY(cudaMemsetAsync(P.light_row, 0, sizeof(int32_t) * lpad, st));
     GENCD_CUDA_TRY(cudaMemsetAsync(P.light_val, 0, vsz * lpad, st));
+    if (p->vmode == kValNone) {  // padding has no value to zero it: it gathers u[n] = 0 instead
+      k_plan_fill<int32_t><<<grid_for(lpad, kThreads, g), kThreads, 0, st>>>(P.light_row, lpad, (int32_t)n);
+      GENCD_CUDA_TRY(cudaGetLastError());
+    }
     const int64_t ln = P.light_nnz;
     GENCD_CUDA_TRY(cudaMemcpyAsync(P.light_col_ptr + P.nlight, &ln, 8, cudaMemcpyHostToDevice, st));
     if (f64)
@@ -751,6 +846,24 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
       k_plan_copy_light<float><<<grid_for(k * 32, kThreads, g), kThreads, 0, st>>>(
           p->col_ptr, p->row_idx, (const float*)p->val, k, P.heavy_min, loff, P.light_row, (float*)P.light_val);
     GENCD_CUDA_TRY(cudaGetLastError());
+    if (!f64 && p->vmode != kValPlain) {  // bfloat16 copy, or no values and a scale per column
+      if (p->vmode == kValBf16) {
+        __nv_bfloat16* b16 = nullptr;
+        GENCD_TRY(palloc(&b16, lpad));
+        k_plan_to_bf16<<<grid_for(lpad, kThreads, g), kThreads, 0, st>>>((const float*)P.light_val, lpad, b16);
+        GENCD_CUDA_TRY(cudaStreamSynchronize(st));
+        cudaFree(P.light_val);
+        P.light_val = b16;
+      } else {
+        GENCD_CUDA_TRY(cudaStreamSynchronize(st));
+        cudaFree(P.light_val);
+        P.light_val = nullptr;
+        GENCD_TRY(palloc(&P.light_scale, P.nlight));
+        k_plan_gather_scales<<<grid_for(P.nlight, kThreads, g), kThreads, 0, st>>>(P.light_cols, P.nlight, p->col_val,
+                                                                                    P.light_scale);
+      }
+      GENCD_CUDA_TRY(cudaGetLastError());
+    }
     P.light_ntiles = (P.light_nnz + kLightTile - 1) / kLightTile;
     GENCD_TRY(palloc(&P.light_tile_lc, P.light_ntiles + 1));
     GENCD_TRY(launch_tile_map_of(p, P.light_col_ptr, P.nlight, P.light_ntiles, P.light_tile_lc, kLightTile));
@@ -807,6 +920,11 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   GENCD_TRY(palloc((char**)&P.s_val, (P.entries + 8) * (int64_t)vsz));
   GENCD_CUDA_TRY(cudaMemsetAsync(P.s_row, 0, 2 * (P.entries + 8), st));
   GENCD_CUDA_TRY(cudaMemsetAsync(P.s_val, 0, vsz * (P.entries + 8), st));
+  if (p->vmode == kValNone) {  // padding reads the zero slot past the slab
+    k_plan_fill<uint16_t><<<grid_for(P.entries + 8, kThreads, g), kThreads, 0, st>>>(P.s_row, P.entries + 8,
+                                                                                     (uint16_t)P.slab_rows);
+    GENCD_CUDA_TRY(cudaGetLastError());
+  }
   // start bits: one byte per 8 entries, written as 32-bit words (entries + 8 bits, rounded up to words)
   const int64_t mask_words = (P.entries + 8 + 31) / 32;
   GENCD_TRY(palloc((uint32_t**)&P.pmask, mask_words));
@@ -822,6 +940,25 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
         sk, se, E, slab_begin, pad_off, P.slab_rows, hrow, hh, (const float*)hval, P.s_row, (float*)P.s_val, pidx,
         (uint32_t*)P.pmask);
   GENCD_CUDA_TRY(cudaGetLastError());
+  if (!f64 && p->vmode != kValPlain) {  // bfloat16 copy, or no values and a scale per column
+    if (p->vmode == kValBf16) {
+      __nv_bfloat16* b16 = nullptr;
+      GENCD_TRY(palloc(&b16, P.entries + 8));
+      k_plan_to_bf16<<<grid_for(P.entries + 8, kThreads, g), kThreads, 0, st>>>((const float*)P.s_val, P.entries + 8,
+                                                                                b16);
+      GENCD_CUDA_TRY(cudaStreamSynchronize(st));
+      cudaFree(P.s_val);
+      P.s_val = b16;
+    } else {
+      GENCD_CUDA_TRY(cudaStreamSynchronize(st));
+      cudaFree(P.s_val);
+      P.s_val = nullptr;
+      GENCD_TRY(palloc(&P.heavy_scale, P.nheavy));
+      k_plan_gather_scales<<<grid_for(P.nheavy, kThreads, g), kThreads, 0, st>>>(P.heavy_cols, P.nheavy, p->col_val,
+                                                                                  P.heavy_scale);
+    }
+    GENCD_CUDA_TRY(cudaGetLastError());
+  }
   uint32_t* ptmp;
   GENCD_TRY(S.get(&ptmp, scan_tmp_words(E + 1)));
   GENCD_TRY(exclusive_scan(p, pidx, pidx, E + 1, ptmp));
@@ -877,14 +1014,14 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   for (int b = 0; b <= P.grid; ++b) ctb[b] = (int32_t)((int64_t)b * P.ntiles / P.grid);
   GENCD_TRY(palloc(&P.cta_tile_begin, P.grid + 1));
   GENCD_CUDA_TRY(cudaMemcpyAsync(P.cta_tile_begin, ctb.data(), 4 * (P.grid + 1), cudaMemcpyHostToDevice, st));
-  const int smem = (int)((size_t)P.slab_rows * (f64 ? 8 : 4));
   if (f64)
-    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_slabs<double, double, double, kSlabThreadsF64, 0, kSlabItemsF64>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    GENCD_TRY(set_slab_smem<GENCD_PLAN_F64>(P));
+  else if (p->vmode == kValBf16)
+    GENCD_TRY(set_slab_smem<GENCD_PLAN_F32(__nv_bfloat16)>(P));
+  else if (p->vmode == kValNone)
+    GENCD_TRY(set_slab_smem<GENCD_PLAN_F32(NoVal)>(P));
   else
-    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_slabs<float, float, float, kSlabThreadsF32, 1, kSlabItemsF32>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        smem));
+    GENCD_TRY(set_slab_smem<GENCD_PLAN_F32(float)>(P));
   GENCD_CUDA_TRY(cudaStreamSynchronize(st));  // scratch is freed on return
   p->prof.launches[K_SETUP] += 10;
   return GENCD_OK;

@@ -1,4 +1,4 @@
-"""The C-ABI library builds, loads and exports every symbol include/gencd.h
+"""The C-ABI library builds, loads and exports every symbol include/*.h
 declares (no GPU needed: nothing here calls into CUDA)."""
 
 import ctypes
@@ -18,9 +18,13 @@ def libpath():
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "gencd.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(gencd_[a-z_0-9]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(gencd_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():

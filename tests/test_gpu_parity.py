@@ -13,10 +13,9 @@ import pytest
 
 import oracle
 import workloads
+from parity_tools import TOL, _scales, _state, _u, assert_steps_close  # noqa: F401
 
 pytestmark = pytest.mark.gpu
-
-TOL = {"f64": 1e-12, "f32": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -31,43 +30,6 @@ def gb():
 
     binding.lib()
     return binding
-
-
-def _u(prob, z):
-    if prob.loss == "squared":
-        return z - prob.y
-    return -prob.y / (1.0 + np.exp(prob.y * z))
-
-
-def _scales(prob, z, lam, beta_mode=0):
-    u = _u(prob, z)
-    counts = np.diff(prob.col_ptr)
-    a = np.abs(prob.val * u[prob.row_idx])
-    S = np.zeros(prob.k)
-    nz = counts > 0
-    S[nz] = np.add.reduceat(a, prob.col_ptr[:-1][nz]) / prob.n
-    beta = 1.0 if prob.loss == "squared" else 0.25
-    c = np.zeros(prob.k)
-    c[nz] = np.add.reduceat(prob.val ** 2, prob.col_ptr[:-1][nz]) / prob.n
-    bj = np.full(prob.k, beta) if beta_mode else beta * c
-    return S, bj
-
-
-def assert_steps_close(prob, z, w, lam, J, d_gpu, f_gpu, d_cpu, f_cpu, tol, beta_mode=0):
-    S, bj = _scales(prob, z, lam, beta_mode)
-    S, bj, wj = S[J], bj[J], w[J]
-    sd = np.abs(d_cpu) + np.where(bj > 0, S / np.where(bj > 0, bj, 1.0), np.abs(wj))
-    td = tol * sd + 1e-300
-    tf = tol * sd * (S + bj * sd + lam) + 1e-300
-    bad = np.flatnonzero(np.abs(d_gpu - d_cpu) > td)
-    assert bad.size == 0, (bad[:5], d_gpu[bad[:5]], d_cpu[bad[:5]], td[bad[:5]])
-    bad = np.flatnonzero(np.abs(f_gpu - f_cpu) > tf)
-    assert bad.size == 0, (bad[:5], f_gpu[bad[:5]], f_cpu[bad[:5]], tf[bad[:5]])
-
-
-def _state(prob, seed, frac=0.1, scale=0.5):
-    rng = np.random.default_rng(seed)
-    return np.where(rng.random(prob.k) < frac, rng.normal(0, scale, prob.k), 0.0)
 
 
 def ragged_problem(loss="logistic", seed=0):
@@ -394,3 +356,118 @@ def test_not_converged_and_diverged_are_reported(gb):
         p.set_params(variant="thread_greedy", beta_mode=1, max_iter=100000, check_every=10, tol_kkt=0.0)
         r = p.solve()
         assert r.status == gb.GENCD_EDIVERGED
+
+
+# --- storage modes: bfloat16 values and index-only binary columns -----------
+# The oracle runs on the values the mode stores (oracle.stored_values), so the
+# comparison isolates the FP32 arithmetic: the FP32 tolerance applies.
+
+STORAGE_CASES = {
+    "cfg3-lognormal-bf16": (lambda: workloads.config3("lognormal"), "bf16"),
+    "cfg3-pm1-bf16": (lambda: workloads.config3("pm1", "squared"), "bf16"),
+    "ragged-bf16": (lambda: ragged_problem("logistic", 2), "bf16"),
+    "zipf-slabs-bf16": (PROBLEMS["zipf-slabs-squared"], "bf16"),
+    "cfg3-ones-binary": (lambda: workloads.config3("ones"), "binary"),
+    "ragged-binary": (lambda: workloads.binarized(ragged_problem("squared", 3)), "binary"),
+    "zipf-binary": (lambda: workloads.binarized(workloads.config2_scaled(0.002, "logistic")), "binary"),
+    "zipf-slabs-binary": (lambda: workloads.binarized(PROBLEMS["zipf-slabs-squared"]()), "binary"),
+}
+
+
+@pytest.mark.parametrize("name", list(STORAGE_CASES))
+def test_storage_modes_match_oracle(gb, name):
+    make, mode = STORAGE_CASES[name]
+    prob = make()
+    sp = oracle.stored_problem(prob, mode)
+    orc = oracle.Oracle(sp)
+    lam = 0.05 * orc.lambda_max()
+    orc.set_lambda(lam)
+    w = _state(prob, 4)
+    z = orc.fitted(w)
+    rng = np.random.default_rng(6)
+    J = np.concatenate([np.arange(prob.k), rng.integers(0, prob.k, 300)]).astype(np.int32)
+    d_cpu, f_cpu = orc.propose(w, z, J)
+    with gb.Problem(prob, precision=mode) as p:
+        assert p.lambda_max() == pytest.approx(orc.lambda_max(), rel=TOL["f32"] * 10)
+        p.set_lambda(lam)
+        p.set_w(w)
+        np.testing.assert_allclose(p.z(), z, rtol=0, atol=1e-5 * max(1.0, np.abs(z).max()))
+        d_gpu, f_gpu = p.propose_at(J)
+        assert_steps_close(sp, z, w, lam, J, d_gpu, f_gpu, d_cpu, f_cpu, TOL["f32"])
+        d_all, f_all, kkt = p.propose_all()
+        assert_steps_close(sp, z, w, lam, np.arange(prob.k), d_all, f_all, d_cpu[:prob.k], f_cpu[:prob.k],
+                           TOL["f32"])
+        S, _ = _scales(sp, z, lam)
+        assert abs(kkt - orc.kkt(w, z)) <= TOL["f32"] * (S.max() + lam) * 10
+        obj, _ = p.objective()
+        assert obj == pytest.approx(orc.objective(w), rel=1e-6)
+
+
+@pytest.mark.parametrize("mode,values", [("bf16", "lognormal"), ("binary", "ones")])
+@pytest.mark.parametrize("loss,variant", [("logistic", "thread_greedy"), ("squared", "coloring")])
+def test_storage_solve_reaches_the_stored_optimum(gb, mode, values, loss, variant):
+    # Thread-Greedy has no convergence guarantee (Section 7): on the squared
+    # loss here the FP64 oracle diverges at B = 16 too.  Coloring converges.
+    prob = workloads.config3(values, loss)
+    orc = oracle.Oracle(oracle.stored_problem(prob, mode))
+    lam = 0.05 * orc.lambda_max()
+    orc.set_lambda(lam)
+    w_opt, _, _, _, _ = orc.solve("ccd", tol_kkt=1e-11)
+    with gb.Problem(prob, precision=mode) as p:
+        p.set_lambda(lam)
+        p.set_params(variant=variant, blocks=16, tol_kkt=1e-9, max_iter=200_000, check_every=50)
+        r = p.solve()
+        assert r.status == 0, r.as_dict()
+        w = p.w()
+    assert r.objective == pytest.approx(orc.objective(w_opt), rel=1e-6)
+    big = (np.abs(w_opt) > 1e-6) | (np.abs(w) > 1e-6)
+    np.testing.assert_array_equal(np.sign(w[big]), np.sign(w_opt[big]))
+
+
+def test_storage_modes_reject_what_they_cannot_hold(gb):
+    pm = workloads.config3("pm1")
+    with pytest.raises(ValueError) as ref:
+        oracle.stored_values(pm, "binary")
+    with pytest.raises(gb.GencdError) as e:
+        gb.Problem(pm, precision="binary")
+    assert e.value.code == gb.GENCD_EINVAL
+    col = str(ref.value).split()[1]
+    assert f"column {col} " in str(e.value)
+    big = workloads.config3("lognormal")
+    big.val[7] = 3.4e38
+    with pytest.raises(gb.GencdError) as e:
+        gb.Problem(big, precision="bf16")
+    assert e.value.code == gb.GENCD_EINVAL and "bfloat16" in str(e.value)
+
+
+def test_precision_sweep_config3(gb, capsys):
+    # Every storage mode against the FP64 oracle on the original X: each mode
+    # solves to its own KKT tolerance, and its w is scored by the original
+    # objective.  Exact storage (FP64; +-1 and binary values in any mode)
+    # reaches P* to the solve tolerance; bfloat16 of log-normal values solves a
+    # nearby problem.
+    rows = []
+    for values, modes in (("pm1", ["f64", "f32", "bf16"]), ("ones", ["f64", "f32", "bf16", "binary"]),
+                          ("lognormal", ["f64", "f32", "bf16"])):
+        prob = workloads.config3(values, "logistic")
+        orc = oracle.Oracle(prob)
+        lam = 0.01 * orc.lambda_max()
+        orc.set_lambda(lam)
+        w_opt, _, _, _, _ = orc.solve("ccd", tol_kkt=1e-11)
+        P_opt = orc.objective(w_opt)
+        for mode in modes:
+            with gb.Problem(prob, precision=mode) as p:
+                p.set_lambda(lam)
+                p.set_params(variant="thread_greedy", blocks=16, tol_kkt=1e-9, max_iter=400_000, check_every=50)
+                r = p.solve()
+                assert r.status == 0, (values, mode, r.as_dict())
+                w = p.w()
+            rel = (orc.objective(w) - P_opt) / P_opt
+            supp = int(np.sum((np.abs(w) > 1e-6) != (np.abs(w_opt) > 1e-6)))
+            rows.append((values, mode, rel, np.abs(w - w_opt).max(), supp))
+            exact = mode == "f64" or values != "lognormal"
+            assert abs(rel) <= (1e-6 if exact else 1e-2), rows[-1]
+    with capsys.disabled():
+        print("\nprecision sweep (config 3 shapes, logistic, lambda = 0.01 lambda_max)")
+        for values, mode, rel, dw, supp in rows:
+            print(f"  {values:9s} {mode:6s} (P(w)-P*)/P* = {rel:+.3e}  max|w-w*| = {dw:.3e}  support diff = {supp}")
