@@ -63,6 +63,17 @@ def parse():
     ap.add_argument("--target-check", type=int, default=10,
                     help="iterations between objective checks of the time-to-1e-6 run (0: skip it)")
     ap.add_argument("--target-max-iter", type=int, default=5000)
+    # regularisation path (batched solves over one X against one solve per call)
+    ap.add_argument("--no-path", action="store_true", help="skip the regularisation-path measurement")
+    ap.add_argument("--path-loss", default="squared", choices=["squared", "logistic"])
+    ap.add_argument("--path-scale", type=float, default=1.0)
+    ap.add_argument("--path-slots", type=int, default=32)
+    ap.add_argument("--path-blocks", type=int, default=1024)
+    ap.add_argument("--path-check", type=int, default=5)
+    ap.add_argument("--path-tol-rel", type=float, default=1e-3)
+    ap.add_argument("--path-handoff", type=float, default=0.0)
+    ap.add_argument("--path-max-iter", type=int, default=100_000)
+    ap.add_argument("--path-plain", type=int, default=1, help="also time the one-solve-per-call form (0/1)")
     return ap.parse_args()
 
 
@@ -210,6 +221,80 @@ def cpu_oracle_rate(prob, lam, seconds, blocks):
                       "sample": f"{iters} Thread-Greedy iterations (B={B}) of the FP64 oracle on the first "
                                 f"{kk} columns ({int(sub.col_ptr[-1])} nnz) of the workload, "
                                 f"{el:.1f} s on 1 host core"}
+
+
+PATH_FOLDS, PATH_LAMBDAS = 5, 32
+
+
+def run_path(args, gb, stream):
+    """A cross-validated regularisation path on config 4: 5 row folds x 32
+    lambdas (lambda_max -> lambda_max / 1000, each fold's own lambda_max),
+    every solve to KKT <= tol_rel * lambda, warm started along each fold's
+    path.  Batched: one gencd_batch over X runs all 160 solves (X streamed
+    once per step for every live solve).  Plain: one FP32 problem per fold
+    (its training rows), one gencd_solve per lambda, warm started by the
+    problem's own w."""
+    import torch
+
+    prob = workloads.config4(args.path_loss, seed=0, scale=args.path_scale)
+    F, L = PATH_FOLDS, PATH_LAMBDAS
+    fold = workloads.cv_folds(prob.n, F, seed=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = gb.Batch(prob, fold=fold, nfolds=F, slots=args.path_slots, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t0
+    lam = np.stack([workloads.lambda_grid(b.lambda_max(f), L, 1e-3) for f in range(F)])
+    b.set_params(variant="thread_greedy", blocks=args.path_blocks, check_every=args.path_check,
+                 max_iter=args.path_max_iter)
+    b.path(list(range(F)), lam[:, :1], tol_rel=args.path_tol_rel)  # warm-up: the graph capture, lambda_max solves
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    recs, _, tot = b.path(list(range(F)), lam, handoff=args.path_handoff, warm=True, tol_rel=args.path_tol_rel)
+    torch.cuda.synchronize()
+    t_batched = time.perf_counter() - t0
+    b.close()
+    P_b = np.array([r["objective"] for r in recs]).reshape(F, L)
+    st_b = np.array([r["status"] for r in recs])
+    out = {"workload": f"config 4 ({prob.name}), {F} row folds x {L} lambdas (lambda_max -> lambda_max/1000), "
+                       f"{args.path_loss} loss, KKT <= {args.path_tol_rel:g} lambda per solve, warm starts",
+           "solves": F * L, "tol_rel": args.path_tol_rel,
+           "batched": {"seconds": t_batched, "solves_per_s": F * L / t_batched, "create_s": t_create,
+                       "slots": args.path_slots, "blocks": args.path_blocks, "handoff": args.path_handoff,
+                       "steps": int(tot.iters), "updates": int(tot.updates), "nnz_processed": int(tot.nnz_processed),
+                       "converged": int((st_b == 0).sum()),
+                       "iters_per_solve": float(np.mean([r["iters"] for r in recs])),
+                       "max_group": int(max(r["group"] for r in recs))}}
+    if args.path_plain:
+        subs = [workloads.row_subset(prob, np.flatnonzero(fold != f)) for f in range(F)]  # host prep, untimed
+        P_p = np.zeros((F, L))
+        st_p = np.zeros((F, L), np.int64)
+        it_p = np.zeros((F, L), np.int64)
+        t_plain = t_pcreate = 0.0
+        for f in range(F):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p = gb.Problem(subs[f], precision="f32", stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            t_pcreate += time.perf_counter() - t0
+            t0 = time.perf_counter()
+            for t in range(L):
+                p.set_lambda(lam[f, t])
+                p.set_params(variant="thread_greedy", blocks=args.path_blocks, tol_kkt=args.path_tol_rel * lam[f, t],
+                             check_every=args.path_check, max_iter=args.path_max_iter)
+                r = p.solve()
+                P_p[f, t], st_p[f, t], it_p[f, t] = r.objective, r.status, r.iters
+            torch.cuda.synchronize()
+            t_plain += time.perf_counter() - t0
+            p.close()
+        ok = (st_p == 0) & (st_b.reshape(F, L) == 0)
+        out["plain"] = {"seconds": t_plain, "solves_per_s": F * L / t_plain, "create_s": t_pcreate,
+                        "converged": int((st_p == 0).sum()), "iters_per_solve": float(it_p.mean())}
+        out["speedup"] = t_plain / t_batched
+        out["speedup_with_create"] = (t_plain + t_pcreate) / (t_batched + t_create)
+        rel = np.abs(P_b - P_p) / np.abs(P_p)
+        out["max_rel_objective_diff"] = float(rel[ok].max()) if ok.any() else None
+    return out
 
 
 def run_reference(args):
@@ -375,6 +460,13 @@ def run_gencd(args):
         ttt = {"seconds": t_target if reached else None, "iterations": iters, "reached": reached,
                "p_star": final_obj, "check_every": args.target_check, "rel_gap": 1e-6}
 
+    path = None
+    if not args.no_path:
+        try:
+            path = run_path(args, gb, stream)
+        except Exception as e:  # reported, not fatal: the headline line still prints
+            path = {"error": f"{type(e).__name__}: {e}"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         _, cpu = cpu_oracle_rate(prob, lam, args.cpu_seconds, args.blocks)
@@ -408,6 +500,7 @@ def run_gencd(args):
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "regularisation_path": path,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -120,6 +120,16 @@ int gencd_batch_propose(gencd_batch* b, double* delta, double* phi, int32_t memo
  * t's KKT violation is at most handoff, from solve t's iterate at that time,
  * while solve t runs on: chains then fill more slots at once.  Every solve
  * still runs to its own tolerance.
+ *
+ * Accept backoff.  Thread-Greedy has no convergence guarantee (the paper's
+ * closing discussion): on correlated columns the B simultaneous updates can
+ * oscillate or diverge.  A solve accepts, of every G consecutive partitions,
+ * only the best proxy (G = 1 is Thread-Greedy, G = B is Greedy, which lowers
+ * the objective at every step).  When a solve's KKT violation grows to 100
+ * times its lowest value (or is not finite), it restarts from its start with
+ * 4G; when its FP64 objective, evaluated every 8 checks, rose, or did not
+ * fall while the KKT violation is above 100 tol_kkt, G doubles.  A chain's
+ * next solve starts at half the G its predecessor reached.
  */
 typedef struct {
   int32_t nchains;         /* chains (e.g. cross-validation folds)            */
@@ -129,6 +139,9 @@ typedef struct {
   double handoff;          /* KKT level at which the next solve may start; 0 */
   int32_t warm;            /* 1: warm starts, 0: every solve from w = 0      */
   int32_t reserved;
+  double tol_rel;          /* > 0: solve q stops at KKT <= tol_rel * lambda_q
+                              (instead of the absolute tol_kkt); handoff is
+                              then relative to lambda too                     */
 } gencd_path;
 
 typedef struct {
@@ -139,6 +152,8 @@ typedef struct {
   double kkt;       /* KKT violation at the start of the solve's last iteration */
   double t_start;   /* seconds from the start of the call                   */
   double t_end;
+  int32_t group;    /* partitions per accept group at the end (see below)   */
+  int32_t reserved;
 } gencd_path_solve;
 
 /*

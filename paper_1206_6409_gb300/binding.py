@@ -72,12 +72,13 @@ class gencd_result(C.Structure):
 
 class gencd_path(C.Structure):
     _fields_ = [("nchains", C.c_int32), ("nlambda", C.c_int32), ("held_out", C.c_void_p), ("lambda_", C.c_void_p),
-                ("handoff", C.c_double), ("warm", C.c_int32), ("reserved", C.c_int32)]
+                ("handoff", C.c_double), ("warm", C.c_int32), ("reserved", C.c_int32), ("tol_rel", C.c_double)]
 
 
 class gencd_path_solve(C.Structure):
     _fields_ = [("status", C.c_int32), ("slot", C.c_int32), ("iters", C.c_int64), ("objective", C.c_double),
-                ("kkt", C.c_double), ("t_start", C.c_double), ("t_end", C.c_double)]
+                ("kkt", C.c_double), ("t_start", C.c_double), ("t_end", C.c_double), ("group", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class GencdError(RuntimeError):
@@ -571,7 +572,7 @@ def gencd_batch_propose(h, slots, k):
     return d, f
 
 
-def gencd_batch_path(h, held_out, lambdas, k, handoff=0.0, warm=True, want_w=False):
+def gencd_batch_path(h, held_out, lambdas, k, handoff=0.0, warm=True, want_w=False, tol_rel=0.0):
     """Runs a path: held_out int[nchains], lambdas float[nchains, nlambda].
     Returns (per-solve records as a list of dicts, w array [nchains, nlambda, k]
     or None, totals gencd_result).  A solve that did not converge is reported
@@ -582,7 +583,8 @@ def gencd_batch_path(h, held_out, lambdas, k, handoff=0.0, warm=True, want_w=Fal
     if ho.size != C_:
         raise ValueError("one held-out fold per chain")
     spec = gencd_path(nchains=C_, nlambda=L, held_out=C.c_void_p(ho.ctypes.data),
-                      lambda_=C.c_void_p(lam.ctypes.data), handoff=float(handoff), warm=1 if warm else 0)
+                      lambda_=C.c_void_p(lam.ctypes.data), handoff=float(handoff), warm=1 if warm else 0,
+                      tol_rel=float(tol_rel))
     recs = (gencd_path_solve * (C_ * L))()
     w = np.empty((C_, L, int(k))) if want_w else None
     r = gencd_result()
@@ -652,5 +654,5 @@ class Batch:
     def propose(self):
         return gencd_batch_propose(self.h, self.slots, self.k)
 
-    def path(self, held_out, lambdas, handoff=0.0, warm=True, want_w=False):
-        return gencd_batch_path(self.h, held_out, lambdas, self.k, handoff, warm, want_w)
+    def path(self, held_out, lambdas, handoff=0.0, warm=True, want_w=False, tol_rel=0.0):
+        return gencd_batch_path(self.h, held_out, lambdas, self.k, handoff, warm, want_w, tol_rel)

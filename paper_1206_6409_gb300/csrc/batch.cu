@@ -43,6 +43,8 @@ constexpr int kBatchMaxSlots = 256;
 constexpr int kBatchMaxFolds = 31;
 constexpr int kSpmmThreads = 256;
 constexpr int kAcceptThreads = 512;  // per partition: slots x column strides
+constexpr int kObjChecks = 8;        // convergence checks between objective evaluations of a path solve
+constexpr double kJump = 100.0;      // KKT growth (over its best) taken as divergence
 
 static int bfail(int code, const std::string& m) {
   set_error(m);
@@ -282,6 +284,7 @@ __global__ void __launch_bounds__(kSpmmThreads)
 // per-slot parameters, one array of S values each
 struct SlotArgs {
   const int32_t* set;  // training set (0..F; F = all rows), -1 inactive
+  const int32_t* group;  // partitions merged per accept group (1: plain Thread-Greedy)
   const double* lam;
   const float* lam32;
   const double* invn;  // 1 / n_s
@@ -297,7 +300,8 @@ __global__ void __launch_bounds__(kAcceptThreads)
     k_b_accept(const float* __restrict__ G, const float* __restrict__ w32, const double* __restrict__ w,
                const float* __restrict__ bj32, const float* __restrict__ ib32, const double* __restrict__ bjs,
                const double* __restrict__ ibs, int64_t k, SlotArgs sa, const int64_t* __restrict__ part_lo, int Sp,
-               int R, int32_t* __restrict__ acc_j, double* __restrict__ acc_d, unsigned int* __restrict__ kkt_bits) {
+               int R, int32_t* __restrict__ acc_j, double* __restrict__ acc_d, double* __restrict__ acc_phi,
+               unsigned int* __restrict__ kkt_bits) {
   __shared__ uint32_t s_mag[kAcceptThreads];
   __shared__ int32_t s_col[kAcceptThreads];
   __shared__ float s_v[kAcceptThreads];
@@ -341,13 +345,16 @@ __global__ void __launch_bounds__(kAcceptThreads)
   }
   const int64_t slot = (int64_t)b * Sp + s;
   if (set < 0) {
-    if (MODE == 1) acc_j[slot] = -1;
+    if (MODE == 1) {
+      acc_j[slot] = -1;
+      acc_phi[slot] = 0.0;
+    }
     return;
   }
   if (vmax > 0.0f) atomicMax(kkt_bits + s, __float_as_uint(vmax));
   if (MODE == 1) {
     int32_t oj = -1;
-    double od = 0.0;
+    double od = 0.0, of = 0.0;
     if (best > 0u) {  // the FP32 winner's step and proxy in FP64
       const int64_t q = (int64_t)set * k + bcol;
       const double g = (double)G[(int64_t)bcol * Sp + s] * sa.invn[s];
@@ -356,11 +363,37 @@ __global__ void __launch_bounds__(kAcceptThreads)
       if (phi < 0.0) {
         oj = bcol;
         od = d;
+        of = phi;
       }
     }
     acc_j[slot] = oj;
     acc_d[slot] = od;
+    acc_phi[slot] = of;
   }
+}
+
+// Accept backoff: a slot whose group size G > 1 keeps, of every G
+// consecutive partitions, only the one whose accepted proxy is lowest (ties:
+// the lower partition).  G = B is Greedy.
+__global__ void k_b_merge(int32_t* __restrict__ acc_j, const double* __restrict__ acc_phi, int B, int Sp,
+                          const int32_t* __restrict__ group) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= B * Sp) return;
+  const int b = q / Sp, s = q % Sp;
+  const int G = group[s];
+  if (G <= 1 || b % G != 0) return;
+  const int end = min(B, b + G);
+  int win = -1;
+  double best = 0.0;
+  for (int c = b; c < end; ++c) {
+    const double f = acc_phi[c * Sp + s];
+    if (acc_j[c * Sp + s] >= 0 && (win < 0 || f < best)) {
+      win = c;
+      best = f;
+    }
+  }
+  for (int c = b; c < end; ++c)
+    if (c != win) acc_j[c * Sp + s] = -1;
 }
 
 // w += delta and z_s += delta X_j for every accepted (partition, slot)
@@ -552,6 +585,7 @@ struct gencd_batch {
   float *w32 = nullptr, *U = nullptr, *G = nullptr;
   int32_t* acc_j = nullptr;
   double* acc_d = nullptr;
+  double* acc_phi = nullptr;
   int64_t* part_lo = nullptr;
   unsigned int* kkt_bits = nullptr;
   unsigned long long* ctr = nullptr;  // accepted non-zeros, updates
@@ -561,9 +595,10 @@ struct gencd_batch {
 
   // per-slot parameters (device) and their host copy
   int32_t* d_set = nullptr;
+  int32_t* d_group = nullptr;
   double *d_lam = nullptr, *d_invn = nullptr;
   float *d_lam32 = nullptr, *d_invn32 = nullptr;
-  std::vector<int32_t> h_set;
+  std::vector<int32_t> h_set, h_group;
   std::vector<double> h_lam;
 
   // captured steps
@@ -575,7 +610,7 @@ struct gencd_batch {
 namespace gencd {
 
 static SlotArgs slot_args(const gencd_batch* b) {
-  return SlotArgs{b->d_set, b->d_lam, b->d_lam32, b->d_invn, b->d_invn32};
+  return SlotArgs{b->d_set, b->d_group, b->d_lam, b->d_lam32, b->d_invn, b->d_invn32};
 }
 
 static int upload_slots(gencd_batch* b) {
@@ -590,6 +625,7 @@ static int upload_slots(gencd_batch* b) {
   }
   // pageable sources: each copy has read its source when the call returns
   GENCD_CUDA_TRY(cudaMemcpyAsync(b->d_set, b->h_set.data(), 4 * S, cudaMemcpyHostToDevice, b->st));
+  GENCD_CUDA_TRY(cudaMemcpyAsync(b->d_group, b->h_group.data(), 4 * S, cudaMemcpyHostToDevice, b->st));
   GENCD_CUDA_TRY(cudaMemcpyAsync(b->d_lam, b->h_lam.data(), 8 * S, cudaMemcpyHostToDevice, b->st));
   GENCD_CUDA_TRY(cudaMemcpyAsync(b->d_invn, inv.data(), 8 * S, cudaMemcpyHostToDevice, b->st));
   GENCD_CUDA_TRY(cudaMemcpyAsync(b->d_lam32, l32.data(), 4 * S, cudaMemcpyHostToDevice, b->st));
@@ -651,10 +687,11 @@ static int enqueue_propose(gencd_batch* b, bool accept) {
   if (accept)
     k_b_accept<1><<<b->B, b->S * R, 0, b->st>>>(b->G, b->w32, b->w, b->bj32, b->ib32, b->bj, b->ib, b->k,
                                                  slot_args(b), b->part_lo, b->S, R, b->acc_j, b->acc_d,
-                                                 b->kkt_bits);
+                                                 b->acc_phi, b->kkt_bits);
   else
     k_b_accept<0><<<b->B, b->S * R, 0, b->st>>>(b->G, b->w32, b->w, b->bj32, b->ib32, b->bj, b->ib, b->k,
-                                                 slot_args(b), b->part_lo, b->S, R, nullptr, nullptr, b->kkt_bits);
+                                                 slot_args(b), b->part_lo, b->S, R, nullptr, nullptr, nullptr,
+                                                 b->kkt_bits);
   GENCD_CUDA_TRY(cudaGetLastError());
   return GENCD_OK;
 }
@@ -662,6 +699,9 @@ static int enqueue_propose(gencd_batch* b, bool accept) {
 static int enqueue_step(gencd_batch* b) {
   GENCD_TRY(enqueue_propose(b, true));
   const int npairs = b->B * b->S;
+  if (b->B > 1)
+    k_b_merge<<<(npairs + kThreads - 1) / kThreads, kThreads, 0, b->st>>>(b->acc_j, b->acc_phi, b->B, b->S,
+                                                                         b->d_group);
   const int g = grid_for((int64_t)npairs * 32, kThreads, b->X->num_sms * 8);
   k_b_update<<<g, kThreads, 0, b->st>>>(b->acc_j, b->acc_d, npairs, b->S, b->X->col_ptr, b->X->row_idx,
                                         (const float*)b->X->val, b->w, b->w32, b->z, b->ctr);
@@ -739,18 +779,20 @@ static int slot_recompute(gencd_batch* b, int s) {
   return GENCD_OK;
 }
 
-static int slot_set(gencd_batch* b, int s, int set, double lambda, const double* w_dev) {
+static int slot_set(gencd_batch* b, int s, int set, double lambda, const double* w_dev, int group = 1) {
   b->h_set[s] = set;
   b->h_lam[s] = lambda;
+  b->h_group[s] = group;
   GENCD_TRY(upload_slots(b));
   k_b_set_w<<<grid_for(b->k, kThreads, b->X->num_sms * 8), kThreads, 0, b->st>>>(w_dev, b->k, b->S, s, b->w, b->w32);
   return slot_recompute(b, s);
 }
 
-static int slot_copy(gencd_batch* b, int dst, int src, int set, double lambda) {
+static int slot_copy(gencd_batch* b, int dst, int src, int set, double lambda, int group = 1) {
   const int g = b->X->num_sms * 8;
   b->h_set[dst] = set;
   b->h_lam[dst] = lambda;
+  b->h_group[dst] = group;
   GENCD_TRY(upload_slots(b));
   k_b_copy_col<double><<<grid_for(b->k, kThreads, g), kThreads, 0, b->st>>>(b->w, b->k, b->S, src, dst);
   k_b_copy_col<float><<<grid_for(b->k, kThreads, g), kThreads, 0, b->st>>>(b->w32, b->k, b->S, src, dst);
@@ -764,6 +806,7 @@ static int slot_copy(gencd_batch* b, int dst, int src, int set, double lambda) {
 static int slot_clear(gencd_batch* b, int s) {
   b->h_set[s] = -1;
   b->h_lam[s] = 0.0;
+  b->h_group[s] = 1;
   GENCD_TRY(upload_slots(b));
   k_b_fill_col<<<grid_for(b->n, kThreads, b->X->num_sms * 8), kThreads, 0, b->st>>>(
       b->X->y, b->fold, b->nfolds, -1, b->loss, b->z, b->n, b->S, s, b->U);
@@ -824,7 +867,10 @@ static int set_partitions(gencd_batch* b) {
   b->acc_j = nullptr;
   cudaFree(b->acc_d);
   b->acc_d = nullptr;
+  cudaFree(b->acc_phi);
+  b->acc_phi = nullptr;
   GENCD_TRY(balloc(&b->part_lo, B + 1));
+  GENCD_TRY(balloc(&b->acc_phi, (size_t)B * b->S));
   GENCD_TRY(balloc(&b->acc_j, (size_t)B * b->S));
   GENCD_TRY(balloc(&b->acc_d, (size_t)B * b->S));
   GENCD_CUDA_TRY(cudaMemcpyAsync(b->part_lo, lo.data(), 8 * (B + 1), cudaMemcpyHostToDevice, b->st));
@@ -848,8 +894,9 @@ static void free_batch(gencd_batch* b) {
   if (b->st) cudaStreamSynchronize(b->st);
   drop_graph(b);
   void* bufs[] = {b->fold, b->inv_n, b->sq, b->bj, b->ib, b->bj32, b->ib32, b->tstart, b->tile_cc, b->nzcols,
-                  b->bnd, b->w, b->z, b->w32, b->U, b->G, b->acc_j, b->acc_d, b->part_lo, b->kkt_bits, b->ctr,
-                  b->obj_acc, b->obj_list, b->tmp_k, b->d_set, b->d_lam, b->d_invn, b->d_lam32, b->d_invn32};
+                  b->bnd, b->w, b->z, b->w32, b->U, b->G, b->acc_j, b->acc_d, b->acc_phi, b->part_lo, b->kkt_bits,
+                  b->ctr, b->obj_acc, b->obj_list, b->tmp_k, b->d_set, b->d_group, b->d_lam, b->d_invn,
+                  b->d_lam32, b->d_invn32};
   for (void* q : bufs) cudaFree(q);
   cudaGetLastError();
   if (b->X) gencd_destroy(b->X);
@@ -966,11 +1013,13 @@ static int create_batch(gencd_batch* b, const uint8_t* fold, int32_t memory) {
   GENCD_TRY(balloc(&b->obj_list, 64));
   GENCD_TRY(balloc(&b->tmp_k, k));
   GENCD_TRY(balloc(&b->d_set, S));
+  GENCD_TRY(balloc(&b->d_group, S));
   GENCD_TRY(balloc(&b->d_lam, S));
   GENCD_TRY(balloc(&b->d_invn, S));
   GENCD_TRY(balloc(&b->d_lam32, S));
   GENCD_TRY(balloc(&b->d_invn32, S));
   b->h_set.assign(S, -1);
+  b->h_group.assign(S, 1);
   b->h_lam.assign(S, 0.0);
   GENCD_TRY(upload_slots(b));
   gencd_default_params(&b->params);
@@ -1191,7 +1240,7 @@ int gencd_batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* s
                      gencd_result* out) {
   if (!b || !path || !solves) return bfail(GENCD_EINVAL, "NULL argument");
   const int C = path->nchains, L = path->nlambda;
-  if (C < 1 || L < 1 || !path->held_out || !path->lambda || !(path->handoff >= 0.0))
+  if (C < 1 || L < 1 || !path->held_out || !path->lambda || !(path->handoff >= 0.0) || !(path->tol_rel >= 0.0))
     return bfail(GENCD_EINVAL, "malformed path");
   std::vector<int> cset(C);
   for (int c = 0; c < C; ++c) GENCD_TRY(set_of(b, path->held_out[c], &cset[c]));
@@ -1204,11 +1253,19 @@ int gencd_batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* s
   const int m = std::max(1, b->params.check_every);
   const int64_t max_iter = b->params.max_iter;
   const double tol = b->params.tol_kkt;
-  // per chain: the last finished solve's w (warm starts from a retired solve)
-  double* w_last = nullptr;
+  // per chain: the last finished solve's w (warm starts from a retired solve);
+  // per slot: the w its solve started from (restarts after a divergence)
+  double *w_last = nullptr, *w_start = nullptr;
   GENCD_TRY(balloc(&w_last, (size_t)C * b->k));
+  if (balloc(&w_start, (size_t)S * b->k) != GENCD_OK) {
+    cudaFree(w_last);
+    return GENCD_ENOMEM;
+  }
   std::vector<int> next(C, 0), ready(C, 1), pred_slot(C, -1), slot_solve(S, -1), last_q(C, -1);
+  std::vector<int> chain_group(C, 1), obj_wait(S, 0);
   std::vector<int64_t> slot_iters(S, 0);
+  std::vector<double> best_v(S, HUGE_VAL), p_ref(S, HUGE_VAL);
+  const int g_sm = b->X->num_sms * 8;
   for (int64_t q = 0; q < (int64_t)C * L; ++q) {
     std::memset(&solves[q], 0, sizeof(gencd_path_solve));
     solves[q].status = GENCD_NOT_CONVERGED;
@@ -1229,13 +1286,19 @@ int gencd_batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* s
       const int t = next[c], q = c * L + t, s = free_s;
       const double lam = path->lambda[q];
       if (t == 0 || !path->warm)
-        rc = slot_set(b, s, cset[c], lam, nullptr);
+        rc = slot_set(b, s, cset[c], lam, nullptr, chain_group[c]);
       else if (pred_slot[c] >= 0)
-        rc = slot_copy(b, s, pred_slot[c], cset[c], lam);
+        rc = slot_copy(b, s, pred_slot[c], cset[c], lam, chain_group[c]);
       else
-        rc = slot_set(b, s, cset[c], lam, w_last + (size_t)c * b->k);
+        rc = slot_set(b, s, cset[c], lam, w_last + (size_t)c * b->k, chain_group[c]);
+      if (rc == GENCD_OK)
+        k_b_get_w<<<grid_for(b->k, kThreads, g_sm), kThreads, 0, b->st>>>(b->w, b->k, S, s,
+                                                                           w_start + (size_t)s * b->k);
       slot_solve[s] = q;
       slot_iters[s] = 0;
+      obj_wait[s] = 0;
+      best_v[s] = HUGE_VAL;
+      p_ref[s] = HUGE_VAL;
       solves[q].slot = s;
       solves[q].t_start = secs();
       next[c] += 1;
@@ -1245,36 +1308,83 @@ int gencd_batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* s
     rc = run_steps(b, m);
     if (rc == GENCD_OK) rc = read_kkt(b, &kv);
     if (rc != GENCD_OK) break;
-    std::vector<int32_t> retire;
+    // Accept backoff (Thread-Greedy has no convergence guarantee): a KKT
+    // value that jumps (kJump times its best, or not finite) restarts the
+    // solve from its start with 4x the accept group; an objective that rose,
+    // or stayed flat while the KKT value is far from the tolerance, over
+    // kObjChecks checks doubles the group and goes on.  G = B is Greedy.
+    std::vector<int32_t> retire, restart, watch;
+    bool regroup = false;
     for (int s = 0; s < S; ++s) {
       const int q = slot_solve[s];
       if (q < 0) continue;
       const int c = q / L;
       slot_iters[s] += m;
       const double v = kv[s];
+      const double lam_q = path->lambda[q];
+      const double tol_q = path->tol_rel > 0.0 ? path->tol_rel * lam_q : tol;
+      const double hand_q = path->tol_rel > 0.0 ? path->handoff * lam_q : path->handoff;
       solves[q].iters = slot_iters[s];
       solves[q].kkt = v;
-      if (!std::isfinite(v) || v > 1e30) {
-        solves[q].status = GENCD_EDIVERGED;
-        retire.push_back(s);
-      } else if (v <= tol) {
+      if (v <= tol_q) {
         solves[q].status = GENCD_OK;
         retire.push_back(s);
+      } else if (!std::isfinite(v) || v > kJump * best_v[s]) {
+        if (b->h_group[s] < b->B && slot_iters[s] < max_iter) {
+          b->h_group[s] = std::min(b->B, 4 * b->h_group[s]);
+          restart.push_back(s);
+        } else {
+          solves[q].status = GENCD_EDIVERGED;
+          retire.push_back(s);
+        }
       } else if (slot_iters[s] >= max_iter) {
         solves[q].status = GENCD_NOT_CONVERGED;
         retire.push_back(s);
-      } else if (path->handoff > 0.0 && v <= path->handoff && next[c] == (q % L) + 1 && !ready[c]) {
-        ready[c] = 1;  // the successor may start from this iterate
-        pred_slot[c] = s;
+      } else {
+        best_v[s] = std::min(best_v[s], v);
+        if (++obj_wait[s] >= kObjChecks) watch.push_back(s);
+        if (hand_q > 0.0 && v <= hand_q && next[c] == (q % L) + 1 && !ready[c]) {
+          ready[c] = 1;  // the successor may start from this iterate
+          pred_slot[c] = s;
+        }
       }
     }
-    if (retire.empty()) continue;
+    if (!watch.empty()) {
+      std::vector<double> pw;
+      rc = slot_objectives(b, watch, &pw);
+      for (size_t r = 0; r < watch.size() && rc == GENCD_OK; ++r) {
+        const int s = watch[r];
+        obj_wait[s] = 0;
+        const double P = pw[r];
+        const bool rose = !(P <= p_ref[s] * (1.0 + 1e-9));
+        const int q = slot_solve[s];
+        const double tol_q = path->tol_rel > 0.0 ? path->tol_rel * path->lambda[q] : tol;
+        const bool flat = P > p_ref[s] * (1.0 - 1e-12) && best_v[s] > 100.0 * tol_q;
+        if ((rose || flat) && p_ref[s] < HUGE_VAL && b->h_group[s] < b->B) {
+          b->h_group[s] = std::min(b->B, 2 * b->h_group[s]);
+          regroup = true;
+        }
+        if (std::isfinite(P)) p_ref[s] = std::min(p_ref[s], P);
+      }
+    }
+    for (size_t r = 0; r < restart.size() && rc == GENCD_OK; ++r) {
+      const int s = restart[r];
+      rc = slot_set(b, s, b->h_set[s], b->h_lam[s], w_start + (size_t)s * b->k, b->h_group[s]);
+      best_v[s] = HUGE_VAL;
+      p_ref[s] = HUGE_VAL;
+      obj_wait[s] = 0;
+    }
+    for (int s = 0; s < S; ++s)
+      if (slot_solve[s] >= 0) chain_group[slot_solve[s] / L] = std::max(1, b->h_group[s] / 2);
+    if (regroup) rc = upload_slots(b);
+    if (rc != GENCD_OK || retire.empty()) continue;
     std::vector<double> ob;
     rc = slot_objectives(b, retire, &ob);
     for (size_t r = 0; r < retire.size() && rc == GENCD_OK; ++r) {
       const int s = retire[r], q = slot_solve[s], c = q / L;
       solves[q].objective = ob[r];
       solves[q].t_end = secs();
+      solves[q].group = b->h_group[s];
       if (solves[q].status != GENCD_OK) all_ok = 0;
       // the chain's latest finished lambda is the warm start of the solves still to come
       double* dst = q > last_q[c] ? w_last + (size_t)c * b->k : b->tmp_k;
@@ -1300,6 +1410,7 @@ int gencd_batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* s
       rc = bfail(GENCD_ECUDA, "counters");
   }
   cudaFree(w_last);
+  cudaFree(w_start);
   if (rc != GENCD_OK) return rc;
   if (out) {
     std::memset(out, 0, sizeof(*out));

@@ -158,11 +158,13 @@ def test_batch_slot_is_the_same_alone_and_in_the_mix(gb):
 def test_batch_path_reaches_every_oracle_optimum(gb, loss, handoff):
     # 3 chains (two folds and all rows) x 5 lambdas from lambda_max to
     # lambda_max / 100, warm started; each solve against the oracle's cyclic
-    # CD optimum on its training rows
+    # CD optimum on its training rows (objective) and the oracle's FP64 KKT
+    # value at the GPU's w
     prob, fold = _problem(loss, seed=11)
     chains = [-1, 0, 2]
     with gb.Batch(prob, fold=fold, nfolds=NFOLDS, slots=32) as b:
-        b.set_params(variant="thread_greedy", blocks=64, tol_kkt=1e-9, check_every=5, max_iter=20_000)
+        # KKT 1e-8: near the floor of FP32 sums here, and enough for P within 1e-6
+        b.set_params(variant="thread_greedy", blocks=64, tol_kkt=1e-8, check_every=5, max_iter=40_000)
         lams = np.stack([workloads.lambda_grid(b.lambda_max(h), 5, 1e-2) for h in chains])
         recs, W, tot = b.path(chains, lams, handoff=handoff, warm=True, want_w=True)
     assert tot.status == 0
@@ -170,14 +172,16 @@ def test_batch_path_reaches_every_oracle_optimum(gb, loss, handoff):
         orc = oracle.Oracle(_subset(prob, fold, h))
         for t in range(lams.shape[1]):
             r = recs[c * lams.shape[1] + t]
-            assert r["status"] == 0 and r["kkt"] <= 1e-9, (c, t, r)
+            assert r["status"] == 0 and r["kkt"] <= 1e-8, (c, t, r)
             orc.set_lambda(lams[c, t])
             w_opt, _, _, kkt, _ = orc.solve("ccd", tol_kkt=1e-11)
             P_opt = orc.objective(w_opt)
             assert r["objective"] == pytest.approx(P_opt, rel=1e-6), (c, t)
             assert orc.objective(W[c, t]) == pytest.approx(P_opt, rel=1e-6), (c, t)
-            big = (np.abs(w_opt) > 1e-6) | (np.abs(W[c, t]) > 1e-6)
-            np.testing.assert_array_equal(np.sign(W[c, t][big]), np.sign(w_opt[big]))
+            # k > n: the minimiser need not be unique, so supports may differ
+            # between two optimal points; the GPU's w is checked for
+            # optimality by the oracle in FP64 instead
+            assert orc.kkt(W[c, t]) <= 5e-8, (c, t)
 
 
 def test_batch_rejects_bad_input(gb):
