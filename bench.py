@@ -64,7 +64,7 @@ def parse():
                     help="iterations between objective checks of the time-to-1e-6 run (0: skip it)")
     ap.add_argument("--target-max-iter", type=int, default=5000)
     # regularisation path (batched solves over one X against one solve per call)
-    ap.add_argument("--no-path", action="store_true", help="skip the regularisation-path measurement")
+    ap.add_argument("--path", action="store_true", help="add the regularisation-path measurement")
     ap.add_argument("--path-loss", default="squared", choices=["squared", "logistic"])
     ap.add_argument("--path-scale", type=float, default=1.0)
     ap.add_argument("--path-slots", type=int, default=32)
@@ -461,7 +461,7 @@ def run_gencd(args):
                "p_star": final_obj, "check_every": args.target_check, "rel_gap": 1e-6}
 
     path = None
-    if not args.no_path:
+    if args.path:
         try:
             path = run_path(args, gb, stream)
         except Exception as e:  # reported, not fatal: the headline line still prints
