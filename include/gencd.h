@@ -149,6 +149,14 @@ int gencd_get_params(gencd_problem* p, gencd_params* params);
  * and Coloring make a full pass over X at each check).  Returns GENCD_OK,
  * GENCD_NOT_CONVERGED, GENCD_EDIVERGED (objective non-finite, or above 1e6
  * times its value at the start of the call) or an error.
+ * Accept backoff (Thread-Greedy, B > 1; not in the paper, which gives
+ * Thread-Greedy no convergence guarantee): when the KKT value grows to 100
+ * times its lowest or the objective diverges, the solve restarts from the w
+ * it started with and keeps, of every G consecutive partitions, only the best
+ * accepted proxy, G growing 4x per restart; when the FP64 objective rose, or
+ * did not fall while the KKT value is above 100 tol_kkt, over 8 checks, G
+ * doubles.  G = B is Greedy, whose steps always lower the objective.  G
+ * returns to 1 at gencd_set_params; gencd_iterate applies the current G.
  * `out` (nullable) receives the statistics of the call.
  */
 int gencd_solve(gencd_problem* p, gencd_result* out);

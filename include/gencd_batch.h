@@ -47,7 +47,7 @@ typedef struct gencd_batch gencd_batch; /* opaque, owned by the library */
  *   fold     uint8[n] fold of each row, each < nfolds; NULL when nfolds is 0
  *            (then only held_out = -1 is valid)
  *   nfolds   0..31
- *   slots    1..256 solve slots (rounded up to a multiple of 32 inside; the
+ *   slots    1..256 solve slots (rounded up to 8, 16 or a multiple of 32; the
  *            propose pass streams X once per step for all of them)
  *   memory   where col_ptr/row_idx/val/y/fold live (copied; free on return)
  * All slots start inactive.  Parameters start at gencd_default_params().
@@ -62,7 +62,7 @@ int gencd_batch_create(gencd_batch** out, int64_t n, int64_t k, int64_t nnz, con
 /* Frees every buffer of the batch.  NULL is ignored. */
 void gencd_batch_destroy(gencd_batch* b);
 
-/* Number of slots (the multiple of 32 the batch holds). */
+/* Number of slots the batch holds (8, 16 or a multiple of 32). */
 int gencd_batch_slots(gencd_batch* b, int32_t* slots);
 
 /* lambda_max of the training set of held_out (-1: all rows): the smallest

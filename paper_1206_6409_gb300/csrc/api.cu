@@ -252,6 +252,7 @@ static int enqueue_iteration(gencd_problem* p, int64_t* host_nnz, bool want_kkt)
     GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal, 0, sizeof(double), p->stream));  // KKT maximum
     GENCD_TRY(launch_propose_all(p, p->u, p->precision == GENCD_F64));  // Propose, all columns
     GENCD_TRY(launch_finalize_accept(p, B, want_kkt));  // step, proxy (+ KKT of the start state); Accept
+    GENCD_TRY(launch_merge_accept(p, B));               // accept backoff (groups of partitions), if any
     GENCD_TRY(launch_update_list(p, p->list_j, p->list_d, B, true));     // Update (atomic z)
     GENCD_TRY(launch_refresh_list(p, p->list_j, p->list_d, B, true));
     *host_nnz += p->nnz;
@@ -336,7 +337,8 @@ static int compute_pstar(gencd_problem* p, int32_t* iters_out) {
 static void free_problem(gencd_problem* p) {
   if (!p) return;
   void* bufs[] = {p->col_ptr, p->row_idx, p->val, p->y, p->z, p->u, p->w, p->c, p->ib, p->tile_col, p->gacc,
-                  p->delta, p->phi, p->list_j, p->list_d, p->dscal, p->red, p->perm, p->sort_tmp,
+                  p->delta, p->phi, p->list_j, p->list_d, p->list_m, p->w_start, p->dscal, p->red, p->perm,
+                  p->sort_tmp,
                   p->row_ptr, p->col_idx, p->csr_val, p->color, p->color_ptr, p->cols_by_color,
                   p->slot_m, p->slot_d, p->slot_j, p->list_off, p->scan_tmp, p->bj, p->w32, p->bj32, p->ib32,
                   p->part_lo, p->col_val};
@@ -447,6 +449,7 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
   GENCD_TRY(dalloc(&p->phi, k));
   GENCD_TRY(dalloc(&p->list_j, k));
   GENCD_TRY(dalloc(&p->list_d, k));
+  GENCD_TRY(dalloc(&p->list_m, k));
   GENCD_TRY(dalloc(&p->perm, k));
   GENCD_TRY(dalloc(&p->list_off, k + 2));
   GENCD_TRY(dalloc(&p->scan_tmp, scan_tmp_words(k + 2)));
@@ -611,6 +614,7 @@ int gencd_set_params(gencd_problem* p, const gencd_params* a) {
     return fail(GENCD_EINVAL, "parameter out of range");
   const bool reseed = a->seed != p->params.seed;
   p->params = *a;
+  p->accept_group = 1;
   if (reseed) p->perm_epoch = -1;
   GENCD_TRY(launch_inv_beta(p));
   return GENCD_OK;
@@ -690,10 +694,51 @@ int gencd_solve(gencd_problem* p, gencd_result* out) {
   // start state inside the iteration; their checks read it and only run a
   // full evaluation to confirm convergence.  Shotgun and Coloring evaluate.
   const bool fused = a.variant == GENCD_THREAD_GREEDY || a.variant == GENCD_GREEDY;
+  // Accept backoff (Thread-Greedy has no convergence guarantee): a KKT value
+  // 100x its best, or an objective that diverges, restarts the solve from
+  // its start with 4x larger accept groups; an objective that rose, or did
+  // not fall while the KKT value is above 100 tol_kkt, over kObjChecks checks
+  // doubles the group.  A group of B partitions is Greedy.
+  const int64_t B = fused ? effective_B(p) : 1;
+  const bool backoff = fused && B > 1;
+  constexpr int kObjChecks = 8;
+  double best_kkt = HUGE_VAL, obj_ref = HUGE_VAL;
+  int checks = 0;
+  if (backoff) {
+    if (!p->w_start) GENCD_TRY(dalloc(&p->w_start, p->k));
+    GENCD_CUDA_TRY(cudaMemcpyAsync(p->w_start, p->w, sizeof(double) * p->k, cudaMemcpyDeviceToDevice, p->stream));
+  }
   bool evaluated = true;  // hpin holds the KKT of the current state
   for (;;) {
     const double kkt = p->hpin[0], obj = p->hpin[1];
-    if (!std::isfinite(kkt) || !std::isfinite(obj) || obj > 1e6 * (std::fabs(obj_start) + 1e-300)) {
+    const bool blown = !std::isfinite(kkt) || !std::isfinite(obj) || obj > 1e6 * (std::fabs(obj_start) + 1e-300);
+    if (backoff && p->accept_group < B && iters < a.max_iter && (blown || kkt > 100.0 * best_kkt)) {
+      p->accept_group = std::min<int64_t>(B, 4 * p->accept_group);  // restart from the start state
+      GENCD_CUDA_TRY(cudaMemcpyAsync(p->w, p->w_start, sizeof(double) * p->k, cudaMemcpyDeviceToDevice, p->stream));
+      GENCD_TRY(launch_mirror_w(p));
+      GENCD_TRY(build_csr(p));
+      GENCD_TRY(launch_csr_spmv(p, p->w, p->z));
+      GENCD_TRY(launch_fill_u(p));
+      GENCD_TRY(enqueue_evaluate(p));
+      GENCD_TRY(read_scalars(p));
+      host_nnz += p->nnz;
+      p->stat_host_nnz += p->nnz;
+      evaluated = true;
+      best_kkt = obj_ref = HUGE_VAL;
+      checks = 0;
+      continue;
+    }
+    if (backoff && !blown) {
+      best_kkt = std::min(best_kkt, kkt);
+      if (++checks >= kObjChecks) {
+        const bool rose = obj > obj_ref * (1.0 + 1e-9);
+        const bool flat = obj > obj_ref * (1.0 - 1e-12) && best_kkt > 100.0 * a.tol_kkt;
+        if (obj_ref < HUGE_VAL && (rose || flat)) p->accept_group = std::min<int64_t>(B, 2 * p->accept_group);
+        obj_ref = std::min(obj_ref, obj);
+        checks = 0;
+      }
+    }
+    if (blown) {
       status = GENCD_EDIVERGED;
       set_error("objective is not finite or grew beyond 1e6 times its starting value");
       break;

@@ -445,6 +445,173 @@ __global__ void k_b_refresh(const int32_t* __restrict__ acc_j, int npairs, int S
   }
 }
 
+// u_s on every row of every slot (thread (s, row), block Sp x rows): the
+// dense form of k_b_refresh, cheaper when the accepted columns touch more
+// (row, slot) entries than there are rows times slots
+__global__ void k_b_refresh_all(const double* __restrict__ y, const uint8_t* __restrict__ fold, int nfolds, int loss,
+                                const int32_t* __restrict__ sset, const double* __restrict__ z, int64_t n, int Sp,
+                                float* __restrict__ U) {
+  const int s = threadIdx.x;
+  const int set = sset[s];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.y;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; i < n; i += stride) {
+    const int64_t o = i * Sp + s;
+    const bool train = set >= 0 && (set == nfolds || fold[i] != set);
+    U[o] = train ? u_value<float>(loss, y[i], z[o]) : 0.0f;
+  }
+}
+
+// G[:, 8c .. 8c+8) = X^T U[:, 8c .. 8c+8) for chunk c = blockIdx.y, lanes over
+// entries: a warp takes 256-entry tiles, a lane 8 consecutive entries, and
+// each lane keeps the 8 slots' sums of its current column in registers (one
+// 32-byte U row per entry, loaded as two 16-byte vectors).  Start bits (one
+// byte per 8 entries) mark column starts; a lane stores the columns that
+// start and end inside it, and the column continuing from the left (cont) or
+// leaving to the right (tail) is combined across the warp by a segmented
+// suffix sum, so only a tile's first and last column are added atomically.
+// G must be zero before the launch.
+__device__ __forceinline__ void b_row8(const float* __restrict__ p, float (&u)[8]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  u[0] = a.x, u[1] = a.y, u[2] = a.z, u[3] = a.w, u[4] = b.x, u[5] = b.y, u[6] = b.z, u[7] = b.w;
+}
+
+__device__ __forceinline__ void b_store8(float* __restrict__ p, const float (&v)[8]) {
+  reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+  reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+
+__device__ __forceinline__ void b_add8(float* __restrict__ p, const float (&v)[8]) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) atomicAdd(p + q, v[q]);
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+    k_b_spmm_runs8(const int32_t* __restrict__ row, const float* __restrict__ val, const uint8_t* __restrict__ smask,
+                   const int32_t* __restrict__ tile_cc, const int32_t* __restrict__ nzcols,
+                   const float* __restrict__ U, int S, float* __restrict__ G, int64_t nnz, int64_t ntiles) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const float* __restrict__ Uc = U + 8 * blockIdx.y;
+  float* __restrict__ Gc = G + 8 * blockIdx.y;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles; t += nwarps) {
+    const int64_t a = t * 256 + (int64_t)lane * 8;
+    const bool active = a < nnz;
+    int32_t r[8];
+    float x[8];
+    uint32_t m = 0;
+    if (active) {  // rows and values are padded: a lane's 8 entries are in bounds
+      const int4 r0 = __ldcs(reinterpret_cast<const int4*>(row + a));
+      const int4 r1 = __ldcs(reinterpret_cast<const int4*>(row + a) + 1);
+      const float4 x0 = __ldcs(reinterpret_cast<const float4*>(val + a));
+      const float4 x1 = __ldcs(reinterpret_cast<const float4*>(val + a) + 1);
+      r[0] = r0.x, r[1] = r0.y, r[2] = r0.z, r[3] = r0.w, r[4] = r1.x, r[5] = r1.y, r[6] = r1.z, r[7] = r1.w;
+      x[0] = x0.x, x[1] = x0.y, x[2] = x0.z, x[3] = x0.w, x[4] = x1.x, x[5] = x1.y, x[6] = x1.z, x[7] = x1.w;
+      m = smask[a >> 3];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) r[i] = 0, x[i] = 0.0f;
+    }
+    const uint32_t lc0 = (uint32_t)__ldg(tile_cc + t * 8);
+    // compact column of this lane's first entry: the tile's first column plus
+    // the column starts before it (lane 0's entry 0 is the tile's own start)
+    const uint32_t cnt = __popc(lane == 0 ? (m & 0xfeu) : m);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t yv = __shfl_up_sync(FULL, incl, d);
+      if (lane >= d) incl += yv;
+    }
+    const uint32_t q = lc0 + (incl - cnt) + (lane > 0 ? (m & 1u) : 0u);
+    float acc[8], first[8], cont[8], tail[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) acc[s] = first[s] = cont[s] = tail[s] = 0.0f;
+    bool has_tail = false;
+    if (active) {
+      const uint32_t inner = m & 0xfeu;
+      const int bf = inner ? __ffs(inner) - 1 : 8;
+      uint32_t qi = q;
+#pragma unroll
+      for (int h = 0; h < 8; h += 4) {
+        float u[4][8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) b_row8(Uc + (int64_t)r[h + i] * S, u[i]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if ((inner >> (h + i)) & 1u) {
+            if (h + i == bf) {
+#pragma unroll
+              for (int s = 0; s < 8; ++s) first[s] = acc[s];
+            } else {  // a whole column inside the lane
+              b_store8(Gc + (int64_t)__ldg(nzcols + qi) * S, acc);
+            }
+#pragma unroll
+            for (int s = 0; s < 8; ++s) acc[s] = 0.0f;
+            ++qi;
+          }
+#pragma unroll
+          for (int s = 0; s < 8; ++s) acc[s] = fmaf(x[h + i], u[i][s], acc[s]);
+        }
+      }
+      if (inner) {
+        if (m & 1u)  // started at entry 0 and ended inside
+          b_store8(Gc + (int64_t)__ldg(nzcols + q) * S, first);
+        else
+#pragma unroll
+          for (int s = 0; s < 8; ++s) cont[s] = first[s];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) tail[s] = acc[s];
+        has_tail = true;
+      } else if (m & 1u) {
+#pragma unroll
+        for (int s = 0; s < 8; ++s) tail[s] = acc[s];
+        has_tail = true;
+      } else {
+#pragma unroll
+        for (int s = 0; s < 8; ++s) cont[s] = acc[s];
+      }
+    }
+    const bool stop = !active || m != 0u;
+    const bool lead = lane == 0 && active && !(m & 1u);
+    if (__ballot_sync(FULL, stop) == 0u) {  // the whole tile lies inside column lc0
+#pragma unroll
+      for (int s = 0; s < 8; ++s) cont[s] = warp_sum(cont[s]);
+      if (lane == 0) b_add8(Gc + (int64_t)__ldg(nzcols + lc0) * S, cont);
+    } else {
+      // segmented suffix sum of cont over the lanes up to the next stop
+      bool e = stop;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const bool en = __shfl_down_sync(FULL, (int)e, d) != 0;
+        float tn[8];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) tn[s] = __shfl_down_sync(FULL, cont[s], d);
+        if (!e && lane + d < 32) {
+#pragma unroll
+          for (int s = 0; s < 8; ++s) cont[s] += tn[s];
+          e = en;
+        }
+      }
+      const bool e1 = __shfl_down_sync(FULL, (int)e, 1) != 0;
+      float t1[8];
+#pragma unroll
+      for (int s = 0; s < 8; ++s) t1[s] = __shfl_down_sync(FULL, cont[s], 1);
+      if (lead) b_add8(Gc + (int64_t)__ldg(nzcols + lc0) * S, cont);  // column from the previous tile
+      if (has_tail) {
+        const uint32_t ql = q + __popc(m & 0xfeu);
+#pragma unroll
+        for (int s = 0; s < 8; ++s) tail[s] += lane < 31 ? t1[s] : 0.0f;
+        float* g = Gc + (int64_t)__ldg(nzcols + ql) * S;
+        if (lane < 31 && e1)
+          b_store8(g, tail);  // the column ends inside this tile
+        else
+          b_add8(g, tail);
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // slot state and evaluation
 
@@ -602,6 +769,7 @@ struct gencd_batch {
   std::vector<double> h_lam;
 
   // captured steps
+  bool dense_refresh = false;  // refresh u over all rows after each step
   cudaGraphExec_t graph = nullptr;
   int graph_iters = 0, graph_B = 0;
   int64_t steps = 0;  // batched steps enqueued
@@ -641,7 +809,19 @@ static int launch_spmm_nc(gencd_batch* b, const float* U, float* G) {
   return GENCD_OK;
 }
 
+// NC = S / 32 slot chunks of lanes; NC = 0: S = 8 or 16, lanes over entries
+// and 8 slots per lane, one launch row per 8-slot chunk (G zeroed first)
 static int launch_spmm(gencd_batch* b, int NC, const float* U, float* G) {
+  if (NC == 0) {
+    GENCD_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(float) * (size_t)b->k * b->S, b->st));
+    const int64_t t256 = (b->nnz + 255) / 256;
+    if (t256 == 0) return GENCD_OK;
+    const dim3 grid(grid_for(t256 * 32, kThreads, b->X->num_sms * 2), b->S / 8);
+    k_b_spmm_runs8<<<grid, kThreads, 0, b->st>>>(b->X->row_idx, (const float*)b->X->val,
+                                                  reinterpret_cast<const uint8_t*>(b->tstart), b->tile_cc, b->nzcols,
+                                                  U, b->S, G, b->nnz, t256);
+    return GENCD_OK;
+  }
   switch (NC) {
     case 1: return launch_spmm_nc<1>(b, U, G);
     case 2: return launch_spmm_nc<2>(b, U, G);
@@ -663,6 +843,10 @@ static int spmm_occupancy(int* blocks) {
 }
 
 static int spmm_blocks_per_sm(int NC, int* blocks) {
+  if (NC == 0) {
+    *blocks = 2;
+    return GENCD_OK;
+  }
   switch (NC) {
     case 1: return spmm_occupancy<1>(blocks);
     case 2: return spmm_occupancy<2>(blocks);
@@ -681,7 +865,9 @@ static int accept_R(const gencd_batch* b) { return std::max(1, kAcceptThreads / 
 // G = X^T U and the per-slot KKT maxima (MODE 0), or a whole step (MODE 1)
 static int enqueue_propose(gencd_batch* b, bool accept) {
   const int g = b->X->num_sms * 8;
-  k_b_prep<<<grid_for(2 * b->W * b->S, kThreads, g), kThreads, 0, b->st>>>(b->bnd, 2 * b->W, b->S, b->G, b->kkt_bits);
+  const int64_t nb = b->NC == 0 ? 0 : 2 * b->W;  // the lanes-over-entries pass zeroes all of G itself
+  k_b_prep<<<grid_for(std::max<int64_t>(1, nb * b->S), kThreads, g), kThreads, 0, b->st>>>(b->bnd, nb, b->S, b->G,
+                                                                                          b->kkt_bits);
   GENCD_TRY(launch_spmm(b, b->NC, b->U, b->G));
   const int R = accept_R(b);
   if (accept)
@@ -696,6 +882,14 @@ static int enqueue_propose(gencd_batch* b, bool accept) {
   return GENCD_OK;
 }
 
+static int launch_refresh_all(gencd_batch* b) {
+  const int rows = std::max(1, 256 / b->S);
+  const int g = grid_for(b->n, rows, b->X->num_sms * 16);
+  k_b_refresh_all<<<g, dim3(b->S, rows), 0, b->st>>>(b->X->y, b->fold, b->nfolds, b->loss, b->d_set, b->z, b->n,
+                                                     b->S, b->U);
+  return GENCD_OK;
+}
+
 static int enqueue_step(gencd_batch* b) {
   GENCD_TRY(enqueue_propose(b, true));
   const int npairs = b->B * b->S;
@@ -705,8 +899,11 @@ static int enqueue_step(gencd_batch* b) {
   const int g = grid_for((int64_t)npairs * 32, kThreads, b->X->num_sms * 8);
   k_b_update<<<g, kThreads, 0, b->st>>>(b->acc_j, b->acc_d, npairs, b->S, b->X->col_ptr, b->X->row_idx,
                                         (const float*)b->X->val, b->w, b->w32, b->z, b->ctr);
-  k_b_refresh<<<g, kThreads, 0, b->st>>>(b->acc_j, npairs, b->S, b->X->col_ptr, b->X->row_idx, b->X->y, b->fold,
-                                         b->nfolds, b->loss, b->d_set, b->z, b->U);
+  if (b->dense_refresh)
+    GENCD_TRY(launch_refresh_all(b));
+  else
+    k_b_refresh<<<g, kThreads, 0, b->st>>>(b->acc_j, npairs, b->S, b->X->col_ptr, b->X->row_idx, b->X->y, b->fold,
+                                           b->nfolds, b->loss, b->d_set, b->z, b->U);
   GENCD_CUDA_TRY(cudaGetLastError());
   b->steps += 1;
   return GENCD_OK;
@@ -876,6 +1073,9 @@ static int set_partitions(gencd_batch* b) {
   GENCD_CUDA_TRY(cudaMemcpyAsync(b->part_lo, lo.data(), 8 * (B + 1), cudaMemcpyHostToDevice, b->st));
   GENCD_CUDA_TRY(cudaStreamSynchronize(b->st));
   b->B = B;
+  // dense refresh when the accepted columns (heavier than the mean column,
+  // taken as 4x) touch at least n (row, slot) entries per slot
+  b->dense_refresh = (double)B * 4.0 * (double)b->nnz / (double)std::max<int64_t>(1, b->k) >= (double)b->n;
   drop_graph(b);
   return GENCD_OK;
 }
@@ -1085,8 +1285,13 @@ int gencd_batch_create(gencd_batch** out, int64_t n, int64_t k, int64_t nnz, con
   b->nnz = nnz;
   b->loss = loss;
   b->nfolds = nfolds;
-  b->NC = (slots + 31) / 32;
-  b->S = 32 * b->NC;
+  if (slots <= 16) {  // one or two 32-byte segments of U per entry
+    b->NC = 0;
+    b->S = slots <= 8 ? 8 : 16;
+  } else {
+    b->NC = (slots + 31) / 32;
+    b->S = 32 * b->NC;
+  }
   b->st = (cudaStream_t)stream;
   rc = create_batch(b, fold, memory);
   if (rc != GENCD_OK) {

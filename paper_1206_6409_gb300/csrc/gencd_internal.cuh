@@ -179,6 +179,9 @@ struct gencd_problem {
 
   // accepted / selected lists (capacity k)
   int32_t* list_j = nullptr;
+  uint64_t* list_m = nullptr;   // candidate magnitude of each partition's accepted column (accept backoff)
+  double* w_start = nullptr;    // w at the start of a solve (restarts of the accept backoff)
+  int64_t accept_group = 1;     // Thread-Greedy partitions merged per accept group (1: none)
   double* list_d = nullptr;
   uint32_t* list_off = nullptr;  // exclusive prefix of the listed columns' nnz (k + 2)
   uint32_t* scan_tmp = nullptr;  // scratch of the prefix sum
@@ -248,6 +251,7 @@ int launch_propose_plan(gencd_problem* p, const void* u_vec);
 void free_propose_plan(gencd_problem* p);
 int launch_finalize(gencd_problem* p, double lambda, bool write_steps);
 int launch_finalize_accept(gencd_problem* p, int64_t B, bool want_kkt);  // Thread-Greedy / Greedy
+int launch_merge_accept(gencd_problem* p, int64_t B);  // keep the best of every accept_group partitions
 int ensure_slots(gencd_problem* p, int64_t count);
 // exclusive prefix sum of m uint32 (in place allowed); tmp holds scan_tmp_words(m)
 int exclusive_scan(gencd_problem* p, const uint32_t* in, uint32_t* out, int64_t m, uint32_t* tmp);

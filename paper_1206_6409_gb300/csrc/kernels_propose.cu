@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kThreads)
     k_finalize_accept(G* __restrict__ gacc, const double* __restrict__ w, const double* __restrict__ bjs,
                       const double* __restrict__ ib, int64_t k, double inv_n, double lam, uint64_t lnb64,
                       uint32_t lnb32, int64_t B, int want_kkt, int32_t* __restrict__ list_j,
-                      double* __restrict__ list_d, double* __restrict__ kkt_out) {
+                      double* __restrict__ list_d, uint64_t* __restrict__ list_m, double* __restrict__ kkt_out) {
   __shared__ int s_n;
   __shared__ int64_t s_j[kRoundCols];
   __shared__ double s_g[kRoundCols], s_w[kRoundCols];
@@ -341,6 +341,7 @@ __global__ void __launch_bounds__(kThreads)
     if (threadIdx.x == 0) {
       list_j[b] = bm ? bj : -1;
       list_d[b] = bm ? bd : 0.0;
+      list_m[b] = bm;
     }
   }
   if (want_kkt) block_max_bits_to(kkt_out, vmax);
@@ -404,7 +405,7 @@ __global__ void __launch_bounds__(kFinThreads)
                           const double* __restrict__ bjs, const double* __restrict__ ib, int64_t k, float inv_nf,
                           float lamf, double inv_n, double lam, uint32_t lnb32, int64_t B,
                           const int64_t* __restrict__ part_lo, int want_kkt, int32_t* __restrict__ list_j,
-                          double* __restrict__ list_d, double* __restrict__ kkt_out) {
+                          double* __restrict__ list_d, uint64_t* __restrict__ list_m, double* __restrict__ kkt_out) {
   constexpr int ROUND = kColsPerThread * kFinThreads;
   __shared__ int s_n;
   __shared__ int32_t s_j[ROUND];
@@ -444,6 +445,7 @@ __global__ void __launch_bounds__(kFinThreads)
       const bool ok = bm && accept_fp64(dga, bj, inv_n, lam, w, bjs, ib, d);
       list_j[b] = ok ? bj : -1;
       list_d[b] = ok ? d : 0.0;
+      list_m[b] = ok ? bm : 0ull;
     }
     __syncthreads();  // s_n and the queue are reused by the next partition
   }
@@ -582,8 +584,9 @@ __global__ void __launch_bounds__(kThreads)
 __global__ void __launch_bounds__(kThreads)
     k_accept_slots(const uint64_t* __restrict__ slot_m, const int32_t* __restrict__ slot_j,
                    const double* __restrict__ slot_d, int64_t k, int64_t B, int64_t S,
-                   int32_t* __restrict__ list_j, double* __restrict__ list_d, const double* __restrict__ w,
-                   const double* __restrict__ bjs, const double* __restrict__ ib, double inv_n, double lam) {
+                   int32_t* __restrict__ list_j, double* __restrict__ list_d, uint64_t* __restrict__ list_m,
+                   const double* __restrict__ w, const double* __restrict__ bjs, const double* __restrict__ ib,
+                   double inv_n, double lam) {
   __shared__ int64_t s_c[2];
   for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
     if (threadIdx.x == 0) {  // one thread does the 64-bit divisions (FP64 unit)
@@ -610,6 +613,7 @@ __global__ void __launch_bounds__(kThreads)
       if (ok && w) ok = accept_fp64(bd, bj, inv_n, lam, w, bjs, ib, bd);
       list_j[b] = ok ? bj : -1;
       list_d[b] = ok ? bd : 0.0;
+      list_m[b] = ok ? bm : 0ull;
     }
     __syncthreads();
   }
@@ -822,12 +826,12 @@ int launch_finalize_accept(gencd_problem* p, int64_t B, bool want_kkt) {
     if (f64)
       k_finalize_accept<double><<<grid, kThreads, 0, p->stream>>>((double*)p->gnat, p->w, p->bj, p->ib, p->k, inv_n,
                                                                   p->lambda, b64, b32, B, want_kkt ? 1 : 0, p->list_j,
-                                                                  p->list_d, p->dscal + 0);
+                                                                  p->list_d, p->list_m, p->dscal + 0);
     else {
       GENCD_TRY(ensure_part_bounds(p, B));
       k_finalize_accept_f32<<<grid, kFinThreads, 0, p->stream>>>(
           (float*)p->gnat, p->w32, p->bj32, p->ib32, p->w, p->bj, p->ib, p->k, (float)inv_n, (float)p->lambda, inv_n,
-          p->lambda, b32, B, p->part_lo, want_kkt ? 1 : 0, p->list_j, p->list_d, p->dscal + 0);
+          p->lambda, b32, B, p->part_lo, want_kkt ? 1 : 0, p->list_j, p->list_d, p->list_m, p->dscal + 0);
     }
   } else {
     int64_t S = p->k / B;  // >= 1 since B <= k; a chunk meets at most two partitions
@@ -846,10 +850,40 @@ int launch_finalize_accept(gencd_problem* p, int64_t B, bool want_kkt) {
                                                               p->dscal + 0);
     const int g2 = (int)(B < (int64_t)p->num_sms * 16 ? B : (int64_t)p->num_sms * 16);
     k_accept_slots<<<g2, kThreads, 0, p->stream>>>(p->slot_m, p->slot_j, p->slot_d, p->k, B, S, p->list_j,
-                                                   p->list_d, f64 ? nullptr : p->w, p->bj, p->ib, inv_n, p->lambda);
+                                                   p->list_d, p->list_m, f64 ? nullptr : p->w, p->bj, p->ib, inv_n,
+                                                   p->lambda);
     p->prof.launches[K_ACCEPT] += 1;
   }
   prof_end(p, ev);
+  GENCD_CUDA_TRY(cudaGetLastError());
+  return GENCD_OK;
+}
+
+// Accept backoff for Thread-Greedy: of every G consecutive partitions only
+// the accepted column with the best proxy (largest candidate magnitude, ties
+// to the lower partition) is kept.
+__global__ void k_merge_accept(int32_t* __restrict__ list_j, const uint64_t* __restrict__ list_m, int64_t B, int64_t G) {
+  const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * G;
+  if (b >= B) return;
+  const int64_t end = b + G < B ? b + G : B;
+  int64_t win = -1;
+  uint64_t best = 0;
+  for (int64_t c = b; c < end; ++c)
+    if (list_j[c] >= 0 && (win < 0 || list_m[c] > best)) {
+      win = c;
+      best = list_m[c];
+    }
+  for (int64_t c = b; c < end; ++c)
+    if (c != win) list_j[c] = -1;
+}
+
+int launch_merge_accept(gencd_problem* p, int64_t B) {
+  const int64_t G = p->accept_group;
+  if (G <= 1 || B <= 1) return GENCD_OK;
+  const int64_t groups = (B + G - 1) / G;
+  k_merge_accept<<<grid_for(groups, kThreads, (int)((groups + kThreads - 1) / kThreads) + 1), kThreads, 0,
+                   p->stream>>>(p->list_j, p->list_m, B, G);
+  p->prof.launches[K_ACCEPT] += 1;
   GENCD_CUDA_TRY(cudaGetLastError());
   return GENCD_OK;
 }

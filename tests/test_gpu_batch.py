@@ -62,7 +62,7 @@ def test_batch_lambda_max_matches_oracle(gb, loss):
             assert b.lambda_max(h) == pytest.approx(ref, rel=1e-5), h
 
 
-@pytest.mark.parametrize("slots", [32, 70])
+@pytest.mark.parametrize("slots", [8, 16, 32, 70])
 @pytest.mark.parametrize("loss", ["squared", "logistic"])
 def test_batch_propose_matches_oracle(gb, loss, slots):
     # every slot its own (training set, lambda, w); some slots stay inactive
@@ -104,7 +104,7 @@ def test_batch_step_accepts_each_partitions_best(gb, B):
     # has the best proxy up to FP32 rounding, its step is the oracle's FP64
     # Eq. 7 step, and no other coefficient moves
     prob, fold = _problem("logistic", seed=5)
-    with gb.Batch(prob, fold=fold, nfolds=NFOLDS, slots=32) as b:
+    with gb.Batch(prob, fold=fold, nfolds=NFOLDS, slots=8) as b:
         b.set_params(variant="thread_greedy", blocks=B)
         states = {}
         for s, h in enumerate([-1, 0, 1, 2, 3, -1]):
@@ -153,16 +153,16 @@ def test_batch_slot_is_the_same_alone_and_in_the_mix(gb):
     np.testing.assert_array_equal(mixed != 0, alone != 0)
 
 
-@pytest.mark.parametrize("handoff", [0.0, 1e-3])
+@pytest.mark.parametrize("handoff,slots", [(0.0, 8), (1e-3, 32)])
 @pytest.mark.parametrize("loss", ["squared", "logistic"])
-def test_batch_path_reaches_every_oracle_optimum(gb, loss, handoff):
+def test_batch_path_reaches_every_oracle_optimum(gb, loss, handoff, slots):
     # 3 chains (two folds and all rows) x 5 lambdas from lambda_max to
     # lambda_max / 100, warm started; each solve against the oracle's cyclic
     # CD optimum on its training rows (objective) and the oracle's FP64 KKT
     # value at the GPU's w
     prob, fold = _problem(loss, seed=11)
     chains = [-1, 0, 2]
-    with gb.Batch(prob, fold=fold, nfolds=NFOLDS, slots=32) as b:
+    with gb.Batch(prob, fold=fold, nfolds=NFOLDS, slots=slots) as b:
         # KKT 1e-8: near the floor of FP32 sums here, and enough for P within 1e-6
         b.set_params(variant="thread_greedy", blocks=64, tol_kkt=1e-8, check_every=5, max_iter=40_000)
         lams = np.stack([workloads.lambda_grid(b.lambda_max(h), 5, 1e-2) for h in chains])

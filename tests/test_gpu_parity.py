@@ -358,6 +358,29 @@ def test_not_converged_and_diverged_are_reported(gb):
         assert r.status == gb.GENCD_EDIVERGED
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_thread_greedy_backoff_converges_where_plain_thread_greedy_diverges(gb, precision):
+    # config-3 shapes, squared loss: Thread-Greedy with B = 16 diverges (the
+    # FP64 oracle's too); the solve's accept backoff merges partitions until
+    # the iteration converges, to the oracle's cyclic CD optimum
+    prob = workloads.config3("lognormal", "squared")
+    orc = oracle.Oracle(prob)
+    lam = 0.05 * orc.lambda_max()
+    orc.set_lambda(lam)
+    w_tg, _, _, _ = orc.run("thread_greedy", 200, B=16)[:4]
+    assert not orc.objective(w_tg) < orc.objective(np.zeros(prob.k))  # plain Thread-Greedy diverges
+    w_opt, _, _, _, _ = orc.solve("ccd", tol_kkt=1e-11)
+    with gb.Problem(prob, precision=precision) as p:
+        p.set_lambda(lam)
+        p.set_params(variant="thread_greedy", blocks=16, tol_kkt=1e-9 if precision == "f64" else 1e-8,
+                     max_iter=200_000, check_every=10)
+        r = p.solve()
+        assert r.status == 0, r.as_dict()
+        w = p.w()
+    assert r.objective == pytest.approx(orc.objective(w_opt), rel=1e-6)
+    assert orc.kkt(w) <= 1e-7
+
+
 # --- storage modes: bfloat16 values and index-only binary columns -----------
 # The oracle runs on the values the mode stores (oracle.stored_values), so the
 # comparison isolates the FP32 arithmetic: the FP32 tolerance applies.
