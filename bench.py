@@ -18,6 +18,10 @@ with unit-norm columns, 2,000 planted weights, lambda = 0.05 lambda_max.
           creates the problem from host memory (H2D of X and y), runs one
           iteration and reads the objective and KKT value back (D2H)
 
+  regularisation_path  batched solves/s of a cross-validated lambda path on
+          config 4 (5 row folds x 32 lambdas, one gencd_batch over X) beside
+          the same 160 solves through gencd_solve one at a time (run_path)
+
 `--impl reference` times the FP64 CPU oracle on the host cores instead (the
 paper's method has no other runnable implementation).  Under torchrun every
 rank runs an independent replica (the path is replicated, not sharded).
@@ -64,15 +68,19 @@ def parse():
                     help="iterations between objective checks of the time-to-1e-6 run (0: skip it)")
     ap.add_argument("--target-max-iter", type=int, default=5000)
     # regularisation path (batched solves over one X against one solve per call)
-    ap.add_argument("--path", action="store_true", help="add the regularisation-path measurement")
+    ap.add_argument("--no-path", action="store_true", help="skip the regularisation-path measurement")
     ap.add_argument("--path-loss", default="squared", choices=["squared", "logistic"])
     ap.add_argument("--path-scale", type=float, default=1.0)
     ap.add_argument("--path-slots", type=int, default=32)
     ap.add_argument("--path-blocks", type=int, default=1024)
     ap.add_argument("--path-check", type=int, default=5)
     ap.add_argument("--path-tol-rel", type=float, default=1e-3)
-    ap.add_argument("--path-handoff", type=float, default=0.0)
+    ap.add_argument("--path-handoff", type=float, default=0.5,
+                    help="a fold's next solve starts once KKT <= handoff * lambda (0: after convergence)")
     ap.add_argument("--path-max-iter", type=int, default=100_000)
+    ap.add_argument("--path-ratio", type=float, default=1e-2,
+                    help="smallest lambda / lambda_max of the path (below ~1/250 on this workload the solutions "
+                         "near interpolation and Thread-Greedy stalls)")
     ap.add_argument("--path-plain", type=int, default=1, help="also time the one-solve-per-call form (0/1)")
     return ap.parse_args()
 
@@ -228,7 +236,7 @@ PATH_FOLDS, PATH_LAMBDAS = 5, 32
 
 def run_path(args, gb, stream):
     """A cross-validated regularisation path on config 4: 5 row folds x 32
-    lambdas (lambda_max -> lambda_max / 1000, each fold's own lambda_max),
+    lambdas (lambda_max -> ratio * lambda_max, each fold's own lambda_max),
     every solve to KKT <= tol_rel * lambda, warm started along each fold's
     path.  Batched: one gencd_batch over X runs all 160 solves (X streamed
     once per step for every live solve).  Plain: one FP32 problem per fold
@@ -244,7 +252,7 @@ def run_path(args, gb, stream):
     b = gb.Batch(prob, fold=fold, nfolds=F, slots=args.path_slots, stream=stream.cuda_stream)
     torch.cuda.synchronize()
     t_create = time.perf_counter() - t0
-    lam = np.stack([workloads.lambda_grid(b.lambda_max(f), L, 1e-3) for f in range(F)])
+    lam = np.stack([workloads.lambda_grid(b.lambda_max(f), L, args.path_ratio) for f in range(F)])
     b.set_params(variant="thread_greedy", blocks=args.path_blocks, check_every=args.path_check,
                  max_iter=args.path_max_iter)
     b.path(list(range(F)), lam[:, :1], tol_rel=args.path_tol_rel)  # warm-up: the graph capture, lambda_max solves
@@ -256,7 +264,8 @@ def run_path(args, gb, stream):
     b.close()
     P_b = np.array([r["objective"] for r in recs]).reshape(F, L)
     st_b = np.array([r["status"] for r in recs])
-    out = {"workload": f"config 4 ({prob.name}), {F} row folds x {L} lambdas (lambda_max -> lambda_max/1000), "
+    out = {"workload": f"config 4 ({prob.name}), {F} row folds x {L} lambdas (lambda_max -> "
+                       f"{args.path_ratio:g} lambda_max), "
                        f"{args.path_loss} loss, KKT <= {args.path_tol_rel:g} lambda per solve, warm starts",
            "solves": F * L, "tol_rel": args.path_tol_rel,
            "batched": {"seconds": t_batched, "solves_per_s": F * L / t_batched, "create_s": t_create,
@@ -461,7 +470,7 @@ def run_gencd(args):
                "p_star": final_obj, "check_every": args.target_check, "rel_gap": 1e-6}
 
     path = None
-    if args.path:
+    if not args.no_path:
         try:
             path = run_path(args, gb, stream)
         except Exception as e:  # reported, not fatal: the headline line still prints

@@ -153,9 +153,8 @@ int gencd_get_params(gencd_problem* p, gencd_params* params);
  * Thread-Greedy no convergence guarantee): when the KKT value grows to 100
  * times its lowest or the objective diverges, the solve restarts from the w
  * it started with and keeps, of every G consecutive partitions, only the best
- * accepted proxy, G growing 4x per restart; when the FP64 objective rose, or
- * did not fall while the KKT value is above 100 tol_kkt, over 8 checks, G
- * doubles.  G = B is Greedy, whose steps always lower the objective.  G
+ * accepted proxy, G growing 4x per restart; when the FP64 objective rose over
+ * 8 checks, or 400 checks pass without a new lowest KKT value, G doubles.  G = B is Greedy, whose steps always lower the objective.  G
  * returns to 1 at gencd_set_params; gencd_iterate applies the current G.
  * `out` (nullable) receives the statistics of the call.
  */

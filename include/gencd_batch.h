@@ -127,8 +127,8 @@ int gencd_batch_propose(gencd_batch* b, double* delta, double* phi, int32_t memo
  * only the best proxy (G = 1 is Thread-Greedy, G = B is Greedy, which lowers
  * the objective at every step).  When a solve's KKT violation grows to 100
  * times its lowest value (or is not finite), it restarts from its start with
- * 4G; when its FP64 objective, evaluated every 8 checks, rose, or did not
- * fall while the KKT violation is above 100 tol_kkt, G doubles.  A chain's
+ * 4G; when its FP64 objective, evaluated every 8 checks, rose, or 400 checks
+ * pass without a new lowest KKT value, G doubles.  A chain's
  * next solve starts at half the G its predecessor reached.
  */
 typedef struct {

@@ -696,14 +696,14 @@ int gencd_solve(gencd_problem* p, gencd_result* out) {
   const bool fused = a.variant == GENCD_THREAD_GREEDY || a.variant == GENCD_GREEDY;
   // Accept backoff (Thread-Greedy has no convergence guarantee): a KKT value
   // 100x its best, or an objective that diverges, restarts the solve from
-  // its start with 4x larger accept groups; an objective that rose, or did
-  // not fall while the KKT value is above 100 tol_kkt, over kObjChecks checks
-  // doubles the group.  A group of B partitions is Greedy.
+  // its start with 4x larger accept groups; an objective that rose over
+  // kObjChecks checks, or kStallChecks checks without a new lowest KKT value,
+  // double the group.  A group of B partitions is Greedy.
   const int64_t B = fused ? effective_B(p) : 1;
   const bool backoff = fused && B > 1;
-  constexpr int kObjChecks = 8;
+  constexpr int kObjChecks = 8, kStallChecks = 400;
   double best_kkt = HUGE_VAL, obj_ref = HUGE_VAL;
-  int checks = 0;
+  int checks = 0, stall = 0;
   if (backoff) {
     if (!p->w_start) GENCD_TRY(dalloc(&p->w_start, p->k));
     GENCD_CUDA_TRY(cudaMemcpyAsync(p->w_start, p->w, sizeof(double) * p->k, cudaMemcpyDeviceToDevice, p->stream));
@@ -725,15 +725,20 @@ int gencd_solve(gencd_problem* p, gencd_result* out) {
       p->stat_host_nnz += p->nnz;
       evaluated = true;
       best_kkt = obj_ref = HUGE_VAL;
-      checks = 0;
+      checks = stall = 0;
       continue;
     }
     if (backoff && !blown) {
-      best_kkt = std::min(best_kkt, kkt);
+      if (kkt < best_kkt) {
+        best_kkt = kkt;
+        stall = 0;
+      } else if (++stall >= kStallChecks) {
+        p->accept_group = std::min<int64_t>(B, 2 * p->accept_group);
+        stall = 0;
+      }
       if (++checks >= kObjChecks) {
         const bool rose = obj > obj_ref * (1.0 + 1e-9);
-        const bool flat = obj > obj_ref * (1.0 - 1e-12) && best_kkt > 100.0 * a.tol_kkt;
-        if (obj_ref < HUGE_VAL && (rose || flat)) p->accept_group = std::min<int64_t>(B, 2 * p->accept_group);
+        if (obj_ref < HUGE_VAL && rose) p->accept_group = std::min<int64_t>(B, 2 * p->accept_group);
         obj_ref = std::min(obj_ref, obj);
         checks = 0;
       }

@@ -44,6 +44,7 @@ constexpr int kBatchMaxFolds = 31;
 constexpr int kSpmmThreads = 256;
 constexpr int kAcceptThreads = 512;  // per partition: slots x column strides
 constexpr int kObjChecks = 8;        // convergence checks between objective evaluations of a path solve
+constexpr int kStallChecks = 400;    // checks without a new lowest KKT value taken as a stall
 constexpr double kJump = 100.0;      // KKT growth (over its best) taken as divergence
 
 static int bfail(int code, const std::string& m) {
@@ -1467,7 +1468,7 @@ int gencd_batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* s
     return GENCD_ENOMEM;
   }
   std::vector<int> next(C, 0), ready(C, 1), pred_slot(C, -1), slot_solve(S, -1), last_q(C, -1);
-  std::vector<int> chain_group(C, 1), obj_wait(S, 0);
+  std::vector<int> chain_group(C, 1), obj_wait(S, 0), stall(S, 0);
   std::vector<int64_t> slot_iters(S, 0);
   std::vector<double> best_v(S, HUGE_VAL), p_ref(S, HUGE_VAL);
   const int g_sm = b->X->num_sms * 8;
@@ -1502,6 +1503,7 @@ int gencd_batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* s
       slot_solve[s] = q;
       slot_iters[s] = 0;
       obj_wait[s] = 0;
+      stall[s] = 0;
       best_v[s] = HUGE_VAL;
       p_ref[s] = HUGE_VAL;
       solves[q].slot = s;
@@ -1515,9 +1517,10 @@ int gencd_batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* s
     if (rc != GENCD_OK) break;
     // Accept backoff (Thread-Greedy has no convergence guarantee): a KKT
     // value that jumps (kJump times its best, or not finite) restarts the
-    // solve from its start with 4x the accept group; an objective that rose,
-    // or stayed flat while the KKT value is far from the tolerance, over
-    // kObjChecks checks doubles the group and goes on.  G = B is Greedy.
+    // solve from its start with 4x the accept group; an FP64 objective that
+    // rose over kObjChecks checks, or kStallChecks checks without a new
+    // lowest KKT value, double the group and the solve goes on.  G = B is
+    // Greedy.
     std::vector<int32_t> retire, restart, watch;
     bool regroup = false;
     for (int s = 0; s < S; ++s) {
@@ -1546,7 +1549,14 @@ int gencd_batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* s
         solves[q].status = GENCD_NOT_CONVERGED;
         retire.push_back(s);
       } else {
-        best_v[s] = std::min(best_v[s], v);
+        if (v < best_v[s]) {
+          best_v[s] = v;
+          stall[s] = 0;
+        } else if (++stall[s] >= kStallChecks && b->h_group[s] < b->B) {
+          b->h_group[s] = std::min(b->B, 2 * b->h_group[s]);
+          stall[s] = 0;
+          regroup = true;
+        }
         if (++obj_wait[s] >= kObjChecks) watch.push_back(s);
         if (hand_q > 0.0 && v <= hand_q && next[c] == (q % L) + 1 && !ready[c]) {
           ready[c] = 1;  // the successor may start from this iterate
@@ -1562,10 +1572,7 @@ int gencd_batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* s
         obj_wait[s] = 0;
         const double P = pw[r];
         const bool rose = !(P <= p_ref[s] * (1.0 + 1e-9));
-        const int q = slot_solve[s];
-        const double tol_q = path->tol_rel > 0.0 ? path->tol_rel * path->lambda[q] : tol;
-        const bool flat = P > p_ref[s] * (1.0 - 1e-12) && best_v[s] > 100.0 * tol_q;
-        if ((rose || flat) && p_ref[s] < HUGE_VAL && b->h_group[s] < b->B) {
+        if (rose && p_ref[s] < HUGE_VAL && b->h_group[s] < b->B) {
           b->h_group[s] = std::min(b->B, 2 * b->h_group[s]);
           regroup = true;
         }
@@ -1578,6 +1585,7 @@ int gencd_batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* s
       best_v[s] = HUGE_VAL;
       p_ref[s] = HUGE_VAL;
       obj_wait[s] = 0;
+      stall[s] = 0;
     }
     for (int s = 0; s < S; ++s)
       if (slot_solve[s] >= 0) chain_group[slot_solve[s] / L] = std::max(1, b->h_group[s] / 2);
