@@ -82,6 +82,8 @@ def parse():
                     help="smallest lambda / lambda_max of the path (below ~1/250 on this workload the solutions "
                          "near interpolation and Thread-Greedy stalls)")
     ap.add_argument("--path-plain", type=int, default=1, help="also time the one-solve-per-call form (0/1)")
+    ap.add_argument("--batch-step", type=int, default=0, metavar="SLOTS",
+                    help="time only the batched step on config 4 with SLOTS active slots (profiling entry point)")
     return ap.parse_args()
 
 
@@ -306,6 +308,37 @@ def run_path(args, gb, stream):
     return out
 
 
+def run_batch_step(args):
+    """The batched Thread-Greedy step alone: config 4 (scaled by --path-scale),
+    5 folds, every slot active (fold s mod 5, lambda = 0.05 lambda_max of
+    the fold, w = 0), --warmup untimed then --steps timed steps (CUDA events
+    on the library's stream)."""
+    import torch
+
+    from paper_1206_6409_gb300 import binding as gb
+
+    gb.lib()
+    prob = workloads.config4(args.path_loss, seed=0, scale=args.path_scale)
+    fold = workloads.cv_folds(prob.n, PATH_FOLDS, seed=0)
+    st = torch.cuda.current_stream()
+    with gb.Batch(prob, fold=fold, nfolds=PATH_FOLDS, slots=args.batch_step, stream=st.cuda_stream) as b:
+        b.set_params(variant="thread_greedy", blocks=args.path_blocks)
+        for s in range(b.slots):
+            h = s % PATH_FOLDS
+            b.set_slot(s, h, 0.05 * b.lambda_max(h), None)
+        b.iterate(args.warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        b.iterate(args.steps, sync=False)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / max(1, args.steps)
+        print(json.dumps({"metric": "batched Thread-Greedy step", "workload": prob.name, "slots": b.slots,
+                          "blocks": args.path_blocks, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": ms, "us_per_solve_step": 1000.0 * ms / b.slots}), flush=True)
+
+
 def run_reference(args):
     world, rank, _ = dist_setup(args)
     if rank != 0:
@@ -520,6 +553,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.batch_step > 0:
+        run_batch_step(args)
     else:
         run_gencd(args)
 
