@@ -18,6 +18,8 @@ with unit-norm columns, 2,000 planted weights, lambda = 0.05 lambda_max.
           creates the problem from host memory (H2D of X and y), runs one
           iteration and reads the objective and KKT value back (D2H)
 
+  serving  p50/p99 latency and solves/s of a config-5 request stream served
+          with concurrent requests and one at a time (run_serve)
   regularisation_path  batched solves/s of a cross-validated lambda path on
           config 4 (5 row folds x 32 lambdas, one gencd_batch over X) beside
           the same 160 solves through gencd_solve one at a time (run_path)
@@ -82,6 +84,9 @@ def parse():
                     help="smallest lambda / lambda_max of the path (below ~1/250 on this workload the solutions "
                          "near interpolation and Thread-Greedy stalls)")
     ap.add_argument("--path-plain", type=int, default=1, help="also time the one-solve-per-call form (0/1)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-stream measurement")
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--batch-step", type=int, default=0, metavar="SLOTS",
                     help="time only the batched step on config 4 with SLOTS active slots (profiling entry point)")
     return ap.parse_args()
@@ -308,6 +313,34 @@ def run_path(args, gb, stream):
     return out
 
 
+def run_serve(args, gb):
+    """Config 5: independent requests arriving as a Poisson process at 200/s
+    (n in [1e3, 2e5], k in [1e3, 1e6] log-uniform, 5-100 nnz per column,
+    squared or logistic loss, lambda = U[0.01, 0.3] lambda_max), FP32, each
+    solved to KKT <= 1e-7 by Thread-Greedy; served with --serve-workers
+    concurrent requests (admission by free HBM) and one at a time."""
+    problems, fracs, arrivals = workloads.serving_stream(args.serve_requests, rate=200.0, seed=0)
+    params = dict(variant="thread_greedy", blocks=1024, tol_kkt=1e-7, max_iter=100_000, check_every=10)
+
+    def summary(res):
+        lat = np.array([r["end"] - r["arrival"] for r in res])
+        span = max(r["end"] for r in res) - min(r["arrival"] for r in res)
+        return {"solves_per_s": len(res) / span, "p50_ms": 1000.0 * float(np.percentile(lat, 50)),
+                "p99_ms": 1000.0 * float(np.percentile(lat, 99)), "seconds": span,
+                "converged": int(sum(r["status"] == 0 for r in res))}
+
+    gb.gencd_serve(problems[:2], fracs[:2], arrivals[:2] * 0, workers=2, **params)  # warm-up
+    mix, _ = gb.gencd_serve(problems, fracs, arrivals, workers=args.serve_workers, hbm_fraction=0.5, **params)
+    one, _ = gb.gencd_serve(problems, fracs, arrivals, workers=1, hbm_fraction=0.5, **params)
+    rel = [abs(a["objective"] - b["objective"]) / abs(b["objective"]) for a, b in zip(mix, one)
+           if a["status"] == 0 and b["status"] == 0]
+    return {"workload": f"config 5: {len(problems)} requests, Poisson 200/s, "
+                        f"{sum(p.nnz for p in problems) / 1e6:.0f}M nnz in total, FP32, KKT <= 1e-7",
+            "concurrent": dict(summary(mix), workers=args.serve_workers),
+            "one_at_a_time": summary(one),
+            "max_rel_objective_diff": max(rel) if rel else None}
+
+
 def run_batch_step(args):
     """The batched Thread-Greedy step alone: config 4 (scaled by --path-scale),
     5 folds, every slot active (fold s mod 5, lambda = 0.05 lambda_max of
@@ -509,6 +542,13 @@ def run_gencd(args):
         except Exception as e:  # reported, not fatal: the headline line still prints
             path = {"error": f"{type(e).__name__}: {e}"}
 
+    serve = None
+    if not args.no_serve:
+        try:
+            serve = run_serve(args, gb)
+        except Exception as e:  # reported, not fatal
+            serve = {"error": f"{type(e).__name__}: {e}"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         _, cpu = cpu_oracle_rate(prob, lam, args.cpu_seconds, args.blocks)
@@ -543,6 +583,7 @@ def run_gencd(args):
             "e2e": e2e,
             "cpu_baseline": cpu,
             "regularisation_path": path,
+            "serving": serve,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -150,11 +150,11 @@ int gencd_get_params(gencd_problem* p, gencd_params* params);
  * GENCD_NOT_CONVERGED, GENCD_EDIVERGED (objective non-finite, or above 1e6
  * times its value at the start of the call) or an error.
  * Accept backoff (Thread-Greedy, B > 1; not in the paper, which gives
- * Thread-Greedy no convergence guarantee): when the KKT value grows to 100
- * times its lowest or the objective diverges, the solve restarts from the w
+ * Thread-Greedy no convergence guarantee): when the objective is not finite
+ * or above its value at the start of the call, the solve restarts from the w
  * it started with and keeps, of every G consecutive partitions, only the best
- * accepted proxy, G growing 4x per restart; when the FP64 objective rose over
- * 8 checks, or 400 checks pass without a new lowest KKT value, G doubles.  G = B is Greedy, whose steps always lower the objective.  G
+ * accepted proxy, G growing 4x per restart.  G = B is Greedy, whose steps
+ * always lower the objective.  A solve that converges never restarts.  G
  * returns to 1 at gencd_set_params; gencd_iterate applies the current G.
  * `out` (nullable) receives the statistics of the call.
  */

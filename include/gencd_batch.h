@@ -125,11 +125,12 @@ int gencd_batch_propose(gencd_batch* b, double* delta, double* phi, int32_t memo
  * closing discussion): on correlated columns the B simultaneous updates can
  * oscillate or diverge.  A solve accepts, of every G consecutive partitions,
  * only the best proxy (G = 1 is Thread-Greedy, G = B is Greedy, which lowers
- * the objective at every step).  When a solve's KKT violation grows to 100
+ * the objective at every step).  When a solve's KKT violation grows to 10^6
  * times its lowest value (or is not finite), it restarts from its start with
- * 4G; when its FP64 objective, evaluated every 8 checks, rose, or 400 checks
- * pass without a new lowest KKT value, G doubles.  A chain's
- * next solve starts at half the G its predecessor reached.
+ * 4G; when 400 checks pass without a new lowest KKT value and its FP64
+ * objective (evaluated every 8 checks) fell by less than 1e-9 of itself over
+ * them, G doubles.  A chain's next solve starts at half the G its
+ * predecessor reached.
  */
 typedef struct {
   int32_t nchains;         /* chains (e.g. cross-validation folds)            */

@@ -52,7 +52,9 @@ EXPORTS = ["gencd_create", "gencd_destroy", "gencd_set_lambda", "gencd_lambda_ma
            "gencd_batch_create", "gencd_batch_destroy", "gencd_batch_slots", "gencd_batch_lambda_max",
            "gencd_batch_set_params", "gencd_batch_set_slot", "gencd_batch_copy_slot", "gencd_batch_clear_slot",
            "gencd_batch_get_w", "gencd_batch_iterate", "gencd_batch_objective", "gencd_batch_propose",
-           "gencd_batch_path"]
+           "gencd_batch_path",
+           # include/gencd_serve.h
+           "gencd_serve"]
 
 
 class gencd_params(C.Structure):
@@ -68,6 +70,23 @@ class gencd_result(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class gencd_request(C.Structure):
+    _fields_ = [("n", C.c_int64), ("k", C.c_int64), ("nnz", C.c_int64), ("col_ptr", C.c_void_p),
+                ("row_idx", C.c_void_p), ("val", C.c_void_p), ("val_dtype", C.c_int32), ("loss", C.c_int32),
+                ("y", C.c_void_p), ("lambda_frac", C.c_double), ("arrival", C.c_double)]
+
+
+class gencd_serve_params(C.Structure):
+    _fields_ = [("workers", C.c_int32), ("precision", C.c_int32), ("hbm_fraction", C.c_double),
+                ("params", gencd_params)]
+
+
+class gencd_response(C.Structure):
+    _fields_ = [("status", C.c_int32), ("worker", C.c_int32), ("iters", C.c_int64), ("lambda_", C.c_double),
+                ("objective", C.c_double), ("kkt", C.c_double), ("arrival", C.c_double), ("start", C.c_double),
+                ("end", C.c_double), ("bytes", C.c_int64)]
 
 
 class gencd_path(C.Structure):
@@ -145,6 +164,8 @@ def lib():
             "gencd_batch_objective": (C.c_int, [vp, vp, vp]),
             "gencd_batch_propose": (C.c_int, [vp, vp, vp, i32]),
             "gencd_batch_path": (C.c_int, [vp, C.POINTER(gencd_path), vp, vp, C.POINTER(gencd_result)]),
+            # include/gencd_serve.h
+            "gencd_serve": (C.c_int, [vp, i64, C.POINTER(gencd_serve_params), vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -656,3 +677,39 @@ class Batch:
 
     def path(self, held_out, lambdas, handoff=0.0, warm=True, want_w=False, tol_rel=0.0):
         return gencd_batch_path(self.h, held_out, lambdas, self.k, handoff, warm, want_w, tol_rel)
+
+
+# --- include/gencd_serve.h ----------------------------------------------------
+
+def gencd_serve(problems, lambda_fracs, arrivals, workers=4, precision="f32", hbm_fraction=0.5, want_w=False,
+                **params):
+    """Serves a stream of independent problems (workloads.Problem, host
+    arrays) arriving at `arrivals` seconds; lambda = lambda_frac * lambda_max
+    per problem.  Returns (responses as dicts, list of w arrays or None)."""
+    keep = []
+    reqs = (gencd_request * len(problems))()
+    for q, (p, lf, at) in enumerate(zip(problems, lambda_fracs, arrivals)):
+        cp = np.ascontiguousarray(p.col_ptr, np.int64)
+        ri = np.ascontiguousarray(p.row_idx, np.int32)
+        va = np.ascontiguousarray(p.val)
+        if va.dtype not in (np.float32, np.float64):
+            va = va.astype(np.float64)
+        yy = np.ascontiguousarray(p.y, np.float64)
+        keep += [cp, ri, va, yy]
+        reqs[q] = gencd_request(n=p.n, k=p.k, nnz=p.nnz, col_ptr=cp.ctypes.data, row_idx=ri.ctypes.data,
+                                val=va.ctypes.data, val_dtype=0 if va.dtype == np.float64 else 1,
+                                loss=LOSSES[p.loss], y=yy.ctypes.data, lambda_frac=float(lf), arrival=float(at))
+    pr = gencd_default_params()
+    for key, v in params.items():
+        if key == "variant" and isinstance(v, str):
+            v = VARIANTS[v]
+        setattr(pr, key, v)
+    sp = gencd_serve_params(workers=int(workers), precision=PRECISIONS.get(precision, precision),
+                            hbm_fraction=float(hbm_fraction), params=pr)
+    out = (gencd_response * len(problems))()
+    ws = [np.empty(p.k) for p in problems] if want_w else None
+    wp = (C.c_void_p * len(problems))(*[w.ctypes.data for w in ws]) if want_w else None
+    _check(lib().gencd_serve(C.cast(reqs, C.c_void_p), len(problems), C.byref(sp), C.cast(out, C.c_void_p),
+                             C.cast(wp, C.c_void_p) if want_w else None))
+    del keep
+    return [{f: getattr(x, f) for f, _ in gencd_response._fields_} for x in out], ws

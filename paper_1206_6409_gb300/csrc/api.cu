@@ -694,16 +694,13 @@ int gencd_solve(gencd_problem* p, gencd_result* out) {
   // start state inside the iteration; their checks read it and only run a
   // full evaluation to confirm convergence.  Shotgun and Coloring evaluate.
   const bool fused = a.variant == GENCD_THREAD_GREEDY || a.variant == GENCD_GREEDY;
-  // Accept backoff (Thread-Greedy has no convergence guarantee): a KKT value
-  // 100x its best, or an objective that diverges, restarts the solve from
-  // its start with 4x larger accept groups; an objective that rose over
-  // kObjChecks checks, or kStallChecks checks without a new lowest KKT value,
-  // double the group.  A group of B partitions is Greedy.
+  // Accept backoff (Thread-Greedy has no convergence guarantee): an
+  // objective that is not finite or above its value at the start restarts
+  // the solve from its start with 4x larger accept groups (of every G
+  // partitions only the best proxy is applied; G = B is Greedy).
   const int64_t B = fused ? effective_B(p) : 1;
   const bool backoff = fused && B > 1;
-  constexpr int kObjChecks = 8, kStallChecks = 400;
-  double best_kkt = HUGE_VAL, obj_ref = HUGE_VAL;
-  int checks = 0, stall = 0;
+
   if (backoff) {
     if (!p->w_start) GENCD_TRY(dalloc(&p->w_start, p->k));
     GENCD_CUDA_TRY(cudaMemcpyAsync(p->w_start, p->w, sizeof(double) * p->k, cudaMemcpyDeviceToDevice, p->stream));
@@ -712,7 +709,9 @@ int gencd_solve(gencd_problem* p, gencd_result* out) {
   for (;;) {
     const double kkt = p->hpin[0], obj = p->hpin[1];
     const bool blown = !std::isfinite(kkt) || !std::isfinite(obj) || obj > 1e6 * (std::fabs(obj_start) + 1e-300);
-    if (backoff && p->accept_group < B && iters < a.max_iter && (blown || kkt > 100.0 * best_kkt)) {
+    // divergence: the objective is not finite or above its value at the start
+    const bool above = !(obj <= obj_start * (1.0 + 1e-6) + 1e-300);
+    if (backoff && p->accept_group < B && iters < a.max_iter && (blown || above)) {
       p->accept_group = std::min<int64_t>(B, 4 * p->accept_group);  // restart from the start state
       GENCD_CUDA_TRY(cudaMemcpyAsync(p->w, p->w_start, sizeof(double) * p->k, cudaMemcpyDeviceToDevice, p->stream));
       GENCD_TRY(launch_mirror_w(p));
@@ -724,24 +723,7 @@ int gencd_solve(gencd_problem* p, gencd_result* out) {
       host_nnz += p->nnz;
       p->stat_host_nnz += p->nnz;
       evaluated = true;
-      best_kkt = obj_ref = HUGE_VAL;
-      checks = stall = 0;
       continue;
-    }
-    if (backoff && !blown) {
-      if (kkt < best_kkt) {
-        best_kkt = kkt;
-        stall = 0;
-      } else if (++stall >= kStallChecks) {
-        p->accept_group = std::min<int64_t>(B, 2 * p->accept_group);
-        stall = 0;
-      }
-      if (++checks >= kObjChecks) {
-        const bool rose = obj > obj_ref * (1.0 + 1e-9);
-        if (obj_ref < HUGE_VAL && rose) p->accept_group = std::min<int64_t>(B, 2 * p->accept_group);
-        obj_ref = std::min(obj_ref, obj);
-        checks = 0;
-      }
     }
     if (blown) {
       status = GENCD_EDIVERGED;

@@ -45,7 +45,7 @@ constexpr int kSpmmThreads = 256;
 constexpr int kAcceptThreads = 512;  // per partition: slots x column strides
 constexpr int kObjChecks = 8;        // convergence checks between objective evaluations of a path solve
 constexpr int kStallChecks = 400;    // checks without a new lowest KKT value taken as a stall
-constexpr double kJump = 100.0;      // KKT growth (over its best) taken as divergence
+constexpr double kJump = 1e6;        // KKT growth (over its best) taken as divergence
 
 static int bfail(int code, const std::string& m) {
   set_error(m);
@@ -1517,10 +1517,10 @@ int gencd_batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* s
     if (rc != GENCD_OK) break;
     // Accept backoff (Thread-Greedy has no convergence guarantee): a KKT
     // value that jumps (kJump times its best, or not finite) restarts the
-    // solve from its start with 4x the accept group; an FP64 objective that
-    // rose over kObjChecks checks, or kStallChecks checks without a new
-    // lowest KKT value, double the group and the solve goes on.  G = B is
-    // Greedy.
+    // solve from its start with 4x the accept group; kStallChecks checks
+    // without a new lowest KKT value over which the FP64 objective (evaluated
+    // every kObjChecks checks) fell by less than 1e-9 of itself double the
+    // group and the solve goes on.  G = B is Greedy.
     std::vector<int32_t> retire, restart, watch;
     bool regroup = false;
     for (int s = 0; s < S; ++s) {
@@ -1552,10 +1552,8 @@ int gencd_batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* s
         if (v < best_v[s]) {
           best_v[s] = v;
           stall[s] = 0;
-        } else if (++stall[s] >= kStallChecks && b->h_group[s] < b->B) {
-          b->h_group[s] = std::min(b->B, 2 * b->h_group[s]);
-          stall[s] = 0;
-          regroup = true;
+        } else {
+          stall[s] += 1;
         }
         if (++obj_wait[s] >= kObjChecks) watch.push_back(s);
         if (hand_q > 0.0 && v <= hand_q && next[c] == (q % L) + 1 && !ready[c]) {
@@ -1571,12 +1569,16 @@ int gencd_batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* s
         const int s = watch[r];
         obj_wait[s] = 0;
         const double P = pw[r];
-        const bool rose = !(P <= p_ref[s] * (1.0 + 1e-9));
-        if (rose && p_ref[s] < HUGE_VAL && b->h_group[s] < b->B) {
-          b->h_group[s] = std::min(b->B, 2 * b->h_group[s]);
-          regroup = true;
+        if (stall[s] >= kStallChecks) {  // no new lowest KKT value for kStallChecks checks
+          const bool flat = !(P < p_ref[s] * (1.0 - 1e-9));
+          if (flat && b->h_group[s] < b->B) {
+            b->h_group[s] = std::min(b->B, 2 * b->h_group[s]);
+            regroup = true;
+          }
+          stall[s] = 0;
+          p_ref[s] = HUGE_VAL;  // the next window starts here
         }
-        if (std::isfinite(P)) p_ref[s] = std::min(p_ref[s], P);
+        if (std::isfinite(P) && p_ref[s] == HUGE_VAL) p_ref[s] = P;  // objective at the window's start
       }
     }
     for (size_t r = 0; r < restart.size() && rc == GENCD_OK; ++r) {

@@ -19,6 +19,7 @@ from .synthetic import (  # noqa: F401
     cv_folds,
     lambda_grid,
     row_subset,
+    serving_stream,
     tiny_problem,
     csc_from_dense,
 )

@@ -299,6 +299,33 @@ def row_subset(prob: Problem, rows) -> Problem:
                    prob.val[keep].copy(), prob.y[rows].copy(), prob.loss, prob.w_star, prob.name + "-rows")
 
 
+def serving_stream(nreq, rate=200.0, seed=0, n_range=(1_000, 200_000), k_range=(1_000, 1_000_000),
+                   nnz_range=(5, 100)):
+    """Independent requests arriving as a Poisson process of ``rate`` per
+    second: n and k log-uniform over their ranges, a column length uniform in
+    ``nnz_range`` (at most n), squared or logistic loss with probability 1/2,
+    lambda / lambda_max uniform in [0.01, 0.3]; each X from uniform_problem
+    with log-normal unit-norm columns and min(50, k) planted weights.
+
+    Draw order: inter-arrival gaps, then per request n, k, column length,
+    loss, lambda fraction and the request's own seed.  Returns (problems,
+    lambda_fracs, arrivals in seconds from the first arrival)."""
+    rng = _rng(seed)
+    gaps = rng.exponential(1.0 / rate, nreq)
+    arrivals = np.cumsum(gaps) - gaps[0] if nreq else np.zeros(0)
+    problems, fracs = [], []
+    for _ in range(nreq):
+        n = int(round(np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1])))))
+        k = int(round(np.exp(rng.uniform(np.log(k_range[0]), np.log(k_range[1])))))
+        npc = int(min(n, rng.integers(nnz_range[0], nnz_range[1] + 1)))
+        loss = SQUARED if rng.random() < 0.5 else LOGISTIC
+        fracs.append(float(rng.uniform(0.01, 0.3)))
+        s = int(rng.integers(0, 2**31 - 1))
+        problems.append(uniform_problem(n, k, npc, values="lognormal", n_planted=min(50, k), loss=loss, seed=s,
+                                        name=f"request-{n}x{k}-{npc}nnz-{loss}"))
+    return problems, np.array(fracs), arrivals
+
+
 def tiny_problem(n, k, density=0.6, loss=LOGISTIC, seed=0, max_tries=1000) -> Problem:
     """A small problem with n >= k and full column rank (so the l1 optimum is
     unique), for brute-force checks.  Values are N(0,1) on a random pattern."""
