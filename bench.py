@@ -70,7 +70,7 @@ def parse():
                     help="iterations between objective checks of the time-to-1e-6 run (0: skip it)")
     ap.add_argument("--target-max-iter", type=int, default=5000)
     # regularisation path (batched solves over one X against one solve per call)
-    ap.add_argument("--no-path", action="store_true", help="skip the regularisation-path measurement")
+    ap.add_argument("--path", action="store_true", help="add the regularisation-path measurement (minutes)")
     ap.add_argument("--path-loss", default="squared", choices=["squared", "logistic"])
     ap.add_argument("--path-scale", type=float, default=1.0)
     ap.add_argument("--path-slots", type=int, default=32)
@@ -84,7 +84,7 @@ def parse():
                     help="smallest lambda / lambda_max of the path (below ~1/250 on this workload the solutions "
                          "near interpolation and Thread-Greedy stalls)")
     ap.add_argument("--path-plain", type=int, default=1, help="also time the one-solve-per-call form (0/1)")
-    ap.add_argument("--no-serve", action="store_true", help="skip the serving-stream measurement")
+    ap.add_argument("--serve", action="store_true", help="add the serving-stream measurement (minutes)")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--batch-step", type=int, default=0, metavar="SLOTS",
@@ -536,14 +536,14 @@ def run_gencd(args):
                "p_star": final_obj, "check_every": args.target_check, "rel_gap": 1e-6}
 
     path = None
-    if not args.no_path:
+    if args.path:
         try:
             path = run_path(args, gb, stream)
         except Exception as e:  # reported, not fatal: the headline line still prints
             path = {"error": f"{type(e).__name__}: {e}"}
 
     serve = None
-    if not args.no_serve:
+    if args.serve:
         try:
             serve = run_serve(args, gb)
         except Exception as e:  # reported, not fatal
