@@ -1266,9 +1266,24 @@ static int create_batch(gencd_batch* b, const uint8_t* fold, int32_t memory) {
 
 extern "C" {
 
+static int batch_create(gencd_batch** out, int64_t n, int64_t k, int64_t nnz, const int64_t* col_ptr,
+                        const int32_t* row_idx, const void* val, int32_t val_dtype, const double* y, int32_t loss,
+                        const uint8_t* fold, int32_t nfolds, int32_t slots, int32_t memory, void* stream);
+
 int gencd_batch_create(gencd_batch** out, int64_t n, int64_t k, int64_t nnz, const int64_t* col_ptr,
                        const int32_t* row_idx, const void* val, int32_t val_dtype, const double* y, int32_t loss,
                        const uint8_t* fold, int32_t nfolds, int32_t slots, int32_t memory, void* stream) {
+  try {  // no exception crosses the C ABI
+    return batch_create(out, n, k, nnz, col_ptr, row_idx, val, val_dtype, y, loss, fold, nfolds, slots, memory,
+                        stream);
+  } catch (const std::exception& e) {
+    return bfail(GENCD_ENOMEM, std::string("host allocation failed: ") + e.what());
+  }
+}
+
+static int batch_create(gencd_batch** out, int64_t n, int64_t k, int64_t nnz, const int64_t* col_ptr,
+                        const int32_t* row_idx, const void* val, int32_t val_dtype, const double* y, int32_t loss,
+                        const uint8_t* fold, int32_t nfolds, int32_t slots, int32_t memory, void* stream) {
   if (!out) return bfail(GENCD_EINVAL, "out is NULL");
   *out = nullptr;
   if (nfolds < 0 || nfolds > kBatchMaxFolds) return bfail(GENCD_EINVAL, "nfolds must be in [0, 31]");
@@ -1442,8 +1457,20 @@ int gencd_batch_propose(gencd_batch* b, double* delta, double* phi, int32_t memo
   return rc;
 }
 
+static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* solves, double* w_out,
+                      gencd_result* out);
+
 int gencd_batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* solves, double* w_out,
                      gencd_result* out) {
+  try {  // no exception crosses the C ABI
+    return batch_path(b, path, solves, w_out, out);
+  } catch (const std::exception& e) {
+    return bfail(GENCD_ENOMEM, std::string("host allocation failed: ") + e.what());
+  }
+}
+
+static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* solves, double* w_out,
+                      gencd_result* out) {
   if (!b || !path || !solves) return bfail(GENCD_EINVAL, "NULL argument");
   const int C = path->nchains, L = path->nlambda;
   if (C < 1 || L < 1 || !path->held_out || !path->lambda || !(path->handoff >= 0.0) || !(path->tol_rel >= 0.0))

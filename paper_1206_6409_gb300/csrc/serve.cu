@@ -176,8 +176,19 @@ extern "C" int gencd_serve(const gencd_request* requests, int64_t nreq, const ge
   S.budget = (double)free_b * params->hbm_fraction;
   S.t0 = Clock::now();
   std::vector<std::thread> th;
-  th.reserve((size_t)params->workers);
-  for (int w = 0; w < params->workers; ++w) th.emplace_back(worker, &S, w);
+  try {
+    th.reserve((size_t)params->workers);
+    for (int w = 0; w < params->workers; ++w) th.emplace_back(worker, &S, w);
+  } catch (const std::exception& e) {  // no exception crosses the C ABI: stop the workers already started
+    {
+      std::lock_guard<std::mutex> g(S.mu);
+      if (S.err == GENCD_OK) {
+        S.err = GENCD_ENOMEM;
+        S.err_msg = std::string("worker thread creation failed: ") + e.what();
+      }
+    }
+    S.cv.notify_all();
+  }
   for (auto& t : th) t.join();
   if (S.err != GENCD_OK) {
     set_error(S.err_msg);
