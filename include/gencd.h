@@ -128,6 +128,12 @@ void gencd_destroy(gencd_problem* p);
 /* Sets the l1 weight lambda >= 0 of Eq. 1 (state w, z is kept). */
 int gencd_set_lambda(gencd_problem* p, double lambda);
 
+/* Changes the loss (gencd_loss) of the problem; for logistic loss every y_i
+ * must be -1 or +1 (GENCD_EINVAL otherwise, and the loss is unchanged).  The
+ * state w, z and lambda are kept; u, beta_j and lambda_max follow the new
+ * loss. */
+int gencd_set_loss(gencd_problem* p, int32_t loss);
+
 /* lambda_max = max_j |g_j(w = 0)|, the smallest lambda for which w = 0 is
  * optimal.  Computed on the GPU at create time. */
 int gencd_lambda_max(gencd_problem* p, double* lambda_max);

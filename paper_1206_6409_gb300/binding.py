@@ -41,7 +41,7 @@ KERNELS = ["propose_all", "finalize", "accept", "update", "refresh", "propose_li
            "objective", "setup", "propose_light", "propose_slabs", "pairs_reduce"]
 
 # every symbol include/gencd.h declares
-EXPORTS = ["gencd_create", "gencd_destroy", "gencd_set_lambda", "gencd_lambda_max",
+EXPORTS = ["gencd_create", "gencd_destroy", "gencd_set_lambda", "gencd_set_loss", "gencd_lambda_max",
            "gencd_default_params", "gencd_set_params", "gencd_get_params", "gencd_solve",
            "gencd_iterate", "gencd_set_iteration", "gencd_get_iteration", "gencd_get_w",
            "gencd_set_w", "gencd_get_z", "gencd_objective", "gencd_propose_at", "gencd_propose_all",
@@ -123,6 +123,7 @@ def lib():
             "gencd_create": (C.c_int, [pp, i64, i64, i64, vp, vp, vp, i32, vp, i32, i32, i32, vp]),
             "gencd_destroy": (None, [vp]),
             "gencd_set_lambda": (C.c_int, [vp, f64]),
+            "gencd_set_loss": (C.c_int, [vp, i32]),
             "gencd_lambda_max": (C.c_int, [vp, C.POINTER(f64)]),
             "gencd_default_params": (C.c_int, [C.POINTER(gencd_params)]),
             "gencd_set_params": (C.c_int, [vp, C.POINTER(gencd_params)]),
@@ -242,6 +243,10 @@ def gencd_destroy(h):
 
 def gencd_set_lambda(h, lam):
     _check(lib().gencd_set_lambda(h, float(lam)))
+
+
+def gencd_set_loss(h, loss):
+    _check(lib().gencd_set_loss(h, LOSSES.get(loss, loss)))
 
 
 def gencd_lambda_max(h) -> float:
@@ -446,6 +451,9 @@ class Problem:
 
     def lambda_max(self):
         return gencd_lambda_max(self.h)
+
+    def set_loss(self, loss):
+        gencd_set_loss(self.h, loss)
 
     def set_params(self, **kw):
         p = gencd_get_params(self.h)

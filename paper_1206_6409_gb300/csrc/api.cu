@@ -598,6 +598,33 @@ int gencd_set_lambda(gencd_problem* p, double lambda) {
   return GENCD_OK;
 }
 
+int gencd_set_loss(gencd_problem* p, int32_t loss) {
+  GENCD_CHECK_HANDLE(p);
+  if (loss != GENCD_LOSS_SQUARED && loss != GENCD_LOSS_LOGISTIC) return fail(GENCD_EINVAL, "unknown loss");
+  if (loss == p->loss) return GENCD_OK;
+  const int32_t old = p->loss;
+  p->loss = loss;
+  if (loss == GENCD_LOSS_LOGISTIC) {  // labels must be -1 / +1
+    int64_t bad_col = -1, bad_row = -1;
+    int stage = 0;
+    const int rc = validate_input(p, &bad_col, &bad_row, &stage);
+    if (rc != GENCD_OK || bad_row >= 0) {
+      p->loss = old;
+      return rc != GENCD_OK ? rc
+                            : fail(GENCD_EINVAL, "label y[" + std::to_string(bad_row) +
+                                                     "] is not -1/+1 (logistic loss)");
+    }
+  }
+  // l'(y, 0) is -y (squared) and -y/2 (logistic): lambda_max scales by exactly 2
+  p->lambda_max = loss == GENCD_LOSS_LOGISTIC ? 0.5 * p->lambda_max : 2.0 * p->lambda_max;
+  p->ib_mode = -1;  // beta_j depends on the loss
+  GENCD_TRY(launch_inv_beta(p));
+  GENCD_TRY(launch_fill_u(p));
+  p->accept_group = 1;
+  GENCD_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return GENCD_OK;
+}
+
 int gencd_lambda_max(gencd_problem* p, double* lambda_max) {
   GENCD_CHECK_HANDLE(p);
   if (!lambda_max) return fail(GENCD_EINVAL, "lambda_max is NULL");

@@ -381,6 +381,41 @@ def test_thread_greedy_backoff_converges_where_plain_thread_greedy_diverges(gb, 
     assert orc.kkt(w) <= 1e-7
 
 
+def test_set_loss_switches_the_problem(gb):
+    # +-1 labels are valid for both losses: a problem switched to the squared
+    # loss equals a problem created with it, in the same state, and back
+    prob = workloads.config1("logistic")
+    sq = prob.with_loss("squared", prob.y)
+    w = _state(prob, 21)
+    J = np.arange(prob.k, dtype=np.int32)
+    with gb.Problem(prob) as p, gb.Problem(sq) as q:
+        lm_logistic = p.lambda_max()
+        lam = 0.05 * q.lambda_max()
+        for h in (p, q):
+            h.set_w(w)
+            h.set_lambda(lam)
+        p.set_loss("squared")
+        assert p.lambda_max() == pytest.approx(q.lambda_max(), rel=1e-14)
+        d1, f1 = p.propose_at(J)
+        d2, f2 = q.propose_at(J)
+        np.testing.assert_allclose(d1, d2, rtol=1e-12, atol=1e-300)
+        np.testing.assert_allclose(f1, f2, rtol=1e-12, atol=1e-300)
+        assert p.objective()[0] == pytest.approx(q.objective()[0], rel=1e-14)
+        p.set_loss("logistic")
+        assert p.lambda_max() == pytest.approx(lm_logistic, rel=1e-14)
+        orc = oracle.Oracle(prob)
+        orc.set_lambda(lam)
+        assert p.objective()[0] == pytest.approx(orc.objective(w), rel=1e-13)
+    # real-valued labels cannot take the logistic loss; the problem is unchanged
+    lasso = workloads.config1("squared")
+    with gb.Problem(lasso) as p:
+        lm = p.lambda_max()
+        with pytest.raises(gb.GencdError) as e:
+            p.set_loss("logistic")
+        assert e.value.code == gb.GENCD_EINVAL and "-1/+1" in str(e.value)
+        assert p.lambda_max() == lm
+
+
 # --- storage modes: bfloat16 values and index-only binary columns -----------
 # The oracle runs on the values the mode stores (oracle.stored_values), so the
 # comparison isolates the FP32 arithmetic: the FP32 tolerance applies.
