@@ -70,6 +70,16 @@ typedef struct {
 int gencd_serve(const gencd_request* requests, int64_t nreq, const gencd_serve_params* params, gencd_response* out,
                 double* const* w_out);
 
+/*
+ * The same admission policy without a GPU, for capacity planning: request q
+ * holds a worker for service_s[q] seconds (no GPU work, the X arrays are not
+ * read), the budget is hbm_fraction * budget_bytes and each request's HBM
+ * estimate is computed as gencd_serve does.  Fills worker, arrival, start,
+ * end and bytes of every response (status GENCD_OK).
+ */
+int gencd_serve_dry_run(const gencd_request* requests, int64_t nreq, const gencd_serve_params* params,
+                        double budget_bytes, const double* service_s, gencd_response* out);
+
 #ifdef __cplusplus
 }
 #endif

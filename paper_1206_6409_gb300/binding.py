@@ -54,7 +54,7 @@ EXPORTS = ["gencd_create", "gencd_destroy", "gencd_set_lambda", "gencd_set_loss"
            "gencd_batch_get_w", "gencd_batch_iterate", "gencd_batch_objective", "gencd_batch_propose",
            "gencd_batch_path",
            # include/gencd_serve.h
-           "gencd_serve"]
+           "gencd_serve", "gencd_serve_dry_run"]
 
 
 class gencd_params(C.Structure):
@@ -167,6 +167,7 @@ def lib():
             "gencd_batch_path": (C.c_int, [vp, C.POINTER(gencd_path), vp, vp, C.POINTER(gencd_result)]),
             # include/gencd_serve.h
             "gencd_serve": (C.c_int, [vp, i64, C.POINTER(gencd_serve_params), vp, vp]),
+            "gencd_serve_dry_run": (C.c_int, [vp, i64, C.POINTER(gencd_serve_params), f64, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -721,3 +722,19 @@ def gencd_serve(problems, lambda_fracs, arrivals, workers=4, precision="f32", hb
                              C.cast(wp, C.c_void_p) if want_w else None))
     del keep
     return [{f: getattr(x, f) for f, _ in gencd_response._fields_} for x in out], ws
+
+
+def gencd_serve_dry_run(sizes, arrivals, service_s, budget_bytes, workers=4, hbm_fraction=1.0):
+    """The serving admission policy without a GPU: sizes are (n, k, nnz) per
+    request, service_s the seconds each request holds its worker.  Returns the
+    responses as dicts (worker, arrival, start, end, bytes)."""
+    reqs = (gencd_request * len(sizes))()
+    for q, ((n, k, nnz), at) in enumerate(zip(sizes, arrivals)):
+        reqs[q] = gencd_request(n=int(n), k=int(k), nnz=int(nnz), lambda_frac=0.1, arrival=float(at))
+    svc = np.ascontiguousarray(service_s, np.float64)
+    sp = gencd_serve_params(workers=int(workers), precision=GENCD_F32, hbm_fraction=float(hbm_fraction),
+                            params=gencd_default_params())
+    out = (gencd_response * len(sizes))()
+    _check(lib().gencd_serve_dry_run(C.cast(reqs, C.c_void_p), len(sizes), C.byref(sp), float(budget_bytes),
+                                     C.c_void_p(svc.ctypes.data), C.cast(out, C.c_void_p)))
+    return [{f: getattr(x, f) for f, _ in gencd_response._fields_} for x in out]

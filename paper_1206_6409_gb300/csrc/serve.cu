@@ -38,6 +38,7 @@ struct Server {
   int running = 0;
   int err = GENCD_OK;
   std::string err_msg;
+  const double* service = nullptr;  // dry run: seconds each request holds its worker (no GPU work)
 
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 };
@@ -81,10 +82,17 @@ void solve_one(Server* S, int wid, int64_t q, cudaStream_t st) {
   o.end = S->now();
 }
 
+void dry_one(Server* S, int wid, int64_t q) {
+  std::this_thread::sleep_for(std::chrono::duration<double>(S->service[q]));
+  S->out[q].worker = wid;
+  S->out[q].status = GENCD_OK;
+  S->out[q].end = S->now();
+}
+
 void worker(Server* S, int wid) {
-  cudaSetDevice(S->device);
   cudaStream_t st = nullptr;
-  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+  if (!S->service) cudaSetDevice(S->device);
+  if (!S->service && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
     std::lock_guard<std::mutex> g(S->mu);
     S->err = GENCD_ECUDA;
     S->err_msg = "worker stream creation failed";
@@ -118,7 +126,10 @@ void worker(Server* S, int wid) {
       }
     }
     if (q < 0) break;
-    solve_one(S, wid, q, st);
+    if (S->service)
+      dry_one(S, wid, q);
+    else
+      solve_one(S, wid, q, st);
     {
       std::lock_guard<std::mutex> g(S->mu);
       S->held -= need;
@@ -126,17 +137,10 @@ void worker(Server* S, int wid) {
     }
     S->cv.notify_all();
   }
-  cudaStreamDestroy(st);
+  if (st) cudaStreamDestroy(st);
 }
 
-}  // namespace
-
-}  // namespace gencd
-
-using namespace gencd;
-
-extern "C" int gencd_serve(const gencd_request* requests, int64_t nreq, const gencd_serve_params* params,
-                           gencd_response* out, double* const* w_out) {
+int check_stream(const gencd_request* requests, int64_t nreq, const gencd_serve_params* params, gencd_response* out) {
   if (nreq < 0 || (nreq > 0 && (!requests || !out)) || !params) {
     set_error("bad requests / params / out");
     return GENCD_EINVAL;
@@ -157,6 +161,43 @@ extern "C" int gencd_serve(const gencd_request* requests, int64_t nreq, const ge
       return GENCD_EINVAL;
     }
   }
+  return GENCD_OK;
+}
+
+// runs the workers to the end of the stream; S is filled but for t0
+int run_workers(Server& S, int workers) {
+  S.t0 = Clock::now();
+  std::vector<std::thread> th;
+  try {
+    th.reserve((size_t)workers);
+    for (int w = 0; w < workers; ++w) th.emplace_back(worker, &S, w);
+  } catch (const std::exception& e) {  // no exception crosses the C ABI: stop the workers already started
+    {
+      std::lock_guard<std::mutex> g(S.mu);
+      if (S.err == GENCD_OK) {
+        S.err = GENCD_ENOMEM;
+        S.err_msg = std::string("worker thread creation failed: ") + e.what();
+      }
+    }
+    S.cv.notify_all();
+  }
+  for (auto& t : th) t.join();
+  if (S.err != GENCD_OK) {
+    set_error(S.err_msg);
+    return S.err;
+  }
+  return GENCD_OK;
+}
+
+}  // namespace
+
+}  // namespace gencd
+
+using namespace gencd;
+
+extern "C" int gencd_serve(const gencd_request* requests, int64_t nreq, const gencd_serve_params* params,
+                           gencd_response* out, double* const* w_out) {
+  GENCD_TRY(check_stream(requests, nreq, params, out));
   std::memset(out, 0, sizeof(gencd_response) * (size_t)nreq);
   Server S;
   S.req = requests;
@@ -174,25 +215,28 @@ extern "C" int gencd_serve(const gencd_request* requests, int64_t nreq, const ge
     return GENCD_ECUDA;
   }
   S.budget = (double)free_b * params->hbm_fraction;
-  S.t0 = Clock::now();
-  std::vector<std::thread> th;
-  try {
-    th.reserve((size_t)params->workers);
-    for (int w = 0; w < params->workers; ++w) th.emplace_back(worker, &S, w);
-  } catch (const std::exception& e) {  // no exception crosses the C ABI: stop the workers already started
-    {
-      std::lock_guard<std::mutex> g(S.mu);
-      if (S.err == GENCD_OK) {
-        S.err = GENCD_ENOMEM;
-        S.err_msg = std::string("worker thread creation failed: ") + e.what();
-      }
+  return run_workers(S, params->workers);
+}
+
+extern "C" int gencd_serve_dry_run(const gencd_request* requests, int64_t nreq, const gencd_serve_params* params,
+                                   double budget_bytes, const double* service_s, gencd_response* out) {
+  GENCD_TRY(check_stream(requests, nreq, params, out));
+  if (!(budget_bytes > 0.0) || (nreq > 0 && !service_s)) {
+    set_error("budget_bytes must be > 0 and service_s given");
+    return GENCD_EINVAL;
+  }
+  for (int64_t q = 0; q < nreq; ++q)
+    if (!(service_s[q] >= 0.0) || !std::isfinite(service_s[q])) {
+      set_error("service_s[" + std::to_string(q) + "] must be finite and >= 0");
+      return GENCD_EINVAL;
     }
-    S.cv.notify_all();
-  }
-  for (auto& t : th) t.join();
-  if (S.err != GENCD_OK) {
-    set_error(S.err_msg);
-    return S.err;
-  }
-  return GENCD_OK;
+  std::memset(out, 0, sizeof(gencd_response) * (size_t)nreq);
+  Server S;
+  S.req = requests;
+  S.nreq = nreq;
+  S.sp = *params;
+  S.out = out;
+  S.budget = budget_bytes * params->hbm_fraction;
+  S.service = service_s;
+  return run_workers(S, params->workers);
 }
