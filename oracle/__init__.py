@@ -35,7 +35,7 @@ class _Problem(C.Structure):
 
 class _Params(C.Structure):
     _fields_ = [("variant", C.c_int32), ("B", C.c_int32), ("P", C.c_int64), ("seed", C.c_uint64),
-                ("colors", _i32p), ("ncolors", C.c_int32)]
+                ("colors", _i32p), ("ncolors", C.c_int32), ("improve_steps", C.c_int32)]
 
 
 _lib = None
@@ -60,6 +60,7 @@ def lib():
             "oracle_lambda_max": (C.c_double, [vp]),
             "oracle_step": (None, [C.c_double, C.c_double, C.c_double, C.c_double, _f64p, _f64p]),
             "oracle_propose": (None, [vp, _f64p, _f64p, _i32p, C.c_int64, _f64p, _f64p]),
+            "oracle_improve": (C.c_double, [vp, _f64p, _f64p, C.c_int64, C.c_double, C.c_int32]),
             "oracle_splitmix64": (C.c_uint64, [C.c_uint64, C.c_uint64]),
             "oracle_stored_values": (C.c_int64, [C.c_int32, C.c_int64, _i64p, _f64p, _f64p]),
             "oracle_permutation": (None, [C.c_uint64, C.c_int64, C.c_int64, _i32p]),
@@ -161,6 +162,13 @@ class Oracle:
                              _p(d, _f64p), _p(f, _f64p))
         return d, f
 
+    def improve(self, w, z, j, d, steps):
+        """R11: the increment d of column j improved by up to `steps` Eq. 7
+        steps on coordinate j alone (Algorithm 3's Improve)."""
+        w = np.ascontiguousarray(w, np.float64)
+        z = np.ascontiguousarray(z, np.float64)
+        return lib().oracle_improve(self._ptr, _p(w, _f64p), _p(z, _f64p), int(j), float(d), int(steps))
+
     def spectral_radius(self, max_iter=100, rel_tol=1e-6):
         it = C.c_int32(0)
         rho = lib().oracle_spectral_radius(self._ptr, max_iter, rel_tol, C.byref(it))
@@ -172,10 +180,11 @@ class Oracle:
         return c, nc
 
     # --- iterations ----------------------------------------------------------
-    def _params(self, variant, B=1, P=1, seed=0, colors=None):
+    def _params(self, variant, B=1, P=1, seed=0, colors=None, improve_steps=0):
         pa = _Params()
         pa.variant = _VARIANT[variant] if isinstance(variant, str) else int(variant)
         pa.B, pa.P, pa.seed = int(B), int(P), int(seed) & ((1 << 64) - 1)
+        pa.improve_steps = int(improve_steps)
         if colors is not None:
             colors = np.ascontiguousarray(colors, np.int32)
             pa.colors = _p(colors, _i32p)
@@ -183,11 +192,11 @@ class Oracle:
         return pa, colors
 
     def run(self, variant, iters, w=None, z=None, t0=0, B=1, P=1, seed=0, colors=None,
-            trace=False):
+            trace=False, improve_steps=0):
         """Runs iterations t0..t0+iters-1; returns (w, z, trace, stats)."""
         w = np.zeros(self.k) if w is None else np.array(w, np.float64)
         z = self.fitted(w) if z is None else np.array(z, np.float64)
-        pa, keep = self._params(variant, B, P, seed, colors)
+        pa, keep = self._params(variant, B, P, seed, colors, improve_steps)
         tr = np.empty(iters) if trace else None
         st = np.zeros(3, np.int64)
         rc = lib().oracle_run(self._ptr, C.byref(pa), t0, iters, _p(w, _f64p), _p(z, _f64p),
@@ -198,13 +207,13 @@ class Oracle:
         return w, z, tr, st
 
     def solve(self, variant="ccd", tol_kkt=1e-10, max_iter=10**8, check_every=None, w=None,
-              B=1, P=1, seed=0, colors=None):
+              B=1, P=1, seed=0, colors=None, improve_steps=0):
         """Iterates until KKT <= tol_kkt; returns (w, z, iters, kkt, stats)."""
         w = np.zeros(self.k) if w is None else np.array(w, np.float64)
         z = self.fitted(w)
         if check_every is None:
             check_every = self.k if variant == "ccd" else 10
-        pa, keep = self._params(variant, B, P, seed, colors)
+        pa, keep = self._params(variant, B, P, seed, colors, improve_steps)
         kkt = C.c_double(0.0)
         st = np.zeros(3, np.int64)
         it = lib().oracle_solve(self._ptr, C.byref(pa), tol_kkt, max_iter, check_every,

@@ -36,6 +36,15 @@
  *  R8  The colouring is greedy first-fit over the columns in index order.
  *  R9  KKT violation: max(|g_j| - lambda, 0) if w_j == 0, else
  *      |g_j + lambda sign(w_j)|.
+ *  R11 "Improve delta_j" (Algorithm 3; Section 4.1 adds "500 steps using the
+ *      quadratic approximation" per accepted proposal, without further
+ *      detail): the Eq. 7 step is repeated on coordinate j alone, each time
+ *      from w_j + d with g_j recomputed at z + d X_j, until the step is 0 or
+ *      the step budget ends; every accepted proposal is improved from the
+ *      iteration-start state (R5) before any update is applied.  This is a
+ *      majorise-minimise iteration on the one-coordinate problem, so it
+ *      reaches that coordinate's exact minimiser; for the squared loss with
+ *      beta_mode 0 the first step already is (Eq. 4).
  *  R10 Storage modes (not in the paper): a mode replaces each value of X by
  *      the value it stores, and the method then runs on that X.  FP32 rounds
  *      to nearest even; bfloat16 keeps the sign, the 8 exponent bits and the
@@ -201,6 +210,30 @@ void oracle_propose(const oracle_problem* pr, const double* w, const double* z, 
   }
 }
 
+/* R11: g_j at z + d X_j, only column j's rows moved */
+static double column_gradient_moved(const oracle_problem* pr, const double* z, int64_t j, double d) {
+  double s = 0.0;
+  for (int64_t p = pr->col_ptr[j]; p < pr->col_ptr[j + 1]; ++p) {
+    int32_t i = pr->row_idx[p];
+    s += pr->val[p] * oracle_dloss(pr->loss, pr->y[i], z[i] + d * pr->val[p]);
+  }
+  return s / (double)pr->n;
+}
+
+double oracle_improve(const oracle_problem* pr, const double* w, const double* z, int64_t j, double d,
+                      int32_t steps) {
+  double beta_j = beta_of(pr, j);
+  if (!(beta_j > 0.0)) return d; /* R2: the step already is the exact minimiser */
+  for (int32_t s = 0; s < steps; ++s) {
+    double g = column_gradient_moved(pr, z, j, d);
+    double step, phi;
+    oracle_step(g, w[j] + d, pr->lambda, beta_j, &step, &phi);
+    if (step == 0.0) break;
+    d += step;
+  }
+  return d;
+}
+
 /* ---- R6: selection randomness ------------------------------------------ */
 
 uint64_t oracle_splitmix64(uint64_t s, uint64_t i) {
@@ -355,6 +388,7 @@ int oracle_run(const oracle_problem* pr, const oracle_params* pa, int64_t t0, in
   int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * (size_t)k);
   double* delta = (double*)malloc(sizeof(double) * (size_t)k);
   double* phi = (double*)malloc(sizeof(double) * (size_t)k);
+  int64_t* acc = (int64_t*)malloc(sizeof(int64_t) * (size_t)k);
   int64_t perm_epoch = -1;
   int64_t n_updates = 0, n_nnz = 0;
 
@@ -391,7 +425,8 @@ int oracle_run(const oracle_problem* pr, const oracle_params* pa, int64_t t0, in
     oracle_propose(pr, w, z, J, m, delta, phi);
     for (int64_t a = 0; a < m; ++a) n_nnz += col_len(pr, J[a]);
 
-    /* Accept (Section 2.3) and Update (Algorithm 3) */
+    /* Accept (Section 2.3): the positions a of the accepted proposals */
+    int64_t na = 0;
     if (v == ORACLE_THREAD_GREEDY || v == ORACLE_GREEDY) {
       int64_t B = v == ORACLE_GREEDY ? 1 : pa->B;
       for (int64_t b = 0; b < B; ++b) {
@@ -399,18 +434,20 @@ int oracle_run(const oracle_problem* pr, const oracle_params* pa, int64_t t0, in
         int64_t best = -1;
         for (int64_t a = lo; a < hi; ++a)
           if (best < 0 || phi[a] < phi[best]) best = a; /* strict: ties keep the lower j */
-        if (best >= 0 && phi[best] < 0.0) {
-          apply_update(pr, J[best], delta[best], w, z);
-          n_updates += 1;
-          n_nnz += col_len(pr, J[best]);
-        }
+        if (best >= 0 && phi[best] < 0.0) acc[na++] = best;
       }
     } else { /* Shotgun, Coloring, CCD accept every proposal */
-      for (int64_t a = 0; a < m; ++a) {
-        apply_update(pr, J[a], delta[a], w, z);
-        n_updates += 1;
-        n_nnz += col_len(pr, J[a]);
-      }
+      for (int64_t a = 0; a < m; ++a) acc[na++] = a;
+    }
+    /* Update (Algorithm 3): improve every accepted increment from the
+     * iteration-start state (R11), then apply them in ascending j (R5) */
+    if (pa->improve_steps > 0)
+      for (int64_t r = 0; r < na; ++r)
+        delta[acc[r]] = oracle_improve(pr, w, z, J[acc[r]], delta[acc[r]], pa->improve_steps);
+    for (int64_t r = 0; r < na; ++r) {
+      apply_update(pr, J[acc[r]], delta[acc[r]], w, z);
+      n_updates += 1;
+      n_nnz += col_len(pr, J[acc[r]]);
     }
     if (obj_trace) obj_trace[t - t0] = oracle_objective_z(pr, w, z);
   }
@@ -423,6 +460,7 @@ int oracle_run(const oracle_problem* pr, const oracle_params* pa, int64_t t0, in
   free(perm);
   free(delta);
   free(phi);
+  free(acc);
   return 0;
 }
 

@@ -48,6 +48,7 @@ typedef struct {
   uint64_t seed;         /* selection stream seed                            */
   const int32_t* colors; /* Coloring: colour of each column, 0..ncolors-1    */
   int32_t ncolors;
+  int32_t improve_steps; /* R11: "Improve delta_j" steps per accepted proposal (0: off) */
 } oracle_params;
 
 /* Section 1 losses and their derivative in the fitted value t. */
@@ -85,6 +86,14 @@ void oracle_propose(const oracle_problem* pr, const double* w, const double* z,
  * value outside the bfloat16 range (mode 2). */
 int64_t oracle_stored_values(int32_t mode, int64_t k, const int64_t* col_ptr, const double* val,
                              double* out);
+
+/* R11, "Improve delta_j" (Algorithm 3, Section 4.1): starting from the
+ * proposal d of column j, repeat the Eq. 7 step on coordinate j at w_j + d
+ * with g_j evaluated at z + d X_j (every other coordinate held at the state
+ * (w, z)), at most `steps` times or until a step is 0.  Returns the improved
+ * increment. */
+double oracle_improve(const oracle_problem* pr, const double* w, const double* z, int64_t j, double d,
+                      int32_t steps);
 
 uint64_t oracle_splitmix64(uint64_t s, uint64_t i);
 /* Selection permutation of 0..m-1 for one epoch. */

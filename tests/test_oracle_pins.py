@@ -573,3 +573,76 @@ def test_stored_values_binary_needs_one_value_per_column():
                        if np.unique(pm.val[pm.col_ptr[j]:pm.col_ptr[j + 1]]).size > 1)
     with pytest.raises(ValueError, match=f"column {first_mixed} "):
         oracle.stored_values(pm, "binary")
+
+
+# --- R11: "Improve delta_j" (Algorithm 3, Section 4.1) ----------------------
+
+def _coordinate_objective(orc, w, j):
+    def h(d):
+        w2 = w.copy()
+        w2[j] += d
+        return orc.objective(w2)
+    return h
+
+
+def test_improve_keeps_the_exact_squared_loss_step():
+    # squared loss, beta_j = c_j: the Eq. 7 step is the coordinate's exact
+    # minimiser (Eq. 4), so the improvement stops at once
+    p = workloads.tiny_problem(30, 12, loss="squared", seed=4)
+    orc = oracle.Oracle(p)
+    orc.set_lambda(0.05 * orc.lambda_max())
+    w = np.random.default_rng(4).normal(0, 0.5, p.k)
+    z = orc.fitted(w)
+    d0, _ = orc.propose(w, z, np.arange(p.k, dtype=np.int32))
+    for j in range(p.k):
+        assert orc.improve(w, z, j, d0[j], 500) == pytest.approx(d0[j], rel=1e-12, abs=1e-15)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_improve_reaches_the_logistic_coordinate_minimiser(seed):
+    from scipy.optimize import minimize_scalar
+
+    p = workloads.tiny_problem(40, 10, loss="logistic", seed=seed)
+    orc = oracle.Oracle(p)
+    orc.set_lambda(0.02 * orc.lambda_max())
+    w = np.random.default_rng(seed).normal(0, 1.0, p.k) * (np.random.default_rng(seed + 9).random(p.k) < 0.5)
+    z = orc.fitted(w)
+    d0, _ = orc.propose(w, z, np.arange(p.k, dtype=np.int32))
+    for j in range(p.k):
+        h = _coordinate_objective(orc, w, j)
+        d = orc.improve(w, z, j, d0[j], 500)
+        span = 10 * abs(d0[j]) + 5.0
+        ref = minimize_scalar(h, bounds=(-w[j] - span, -w[j] + span), method="bounded",
+                              options={"xatol": 1e-12, "maxiter": 2000})
+        assert h(d) <= h(d0[j]) + 1e-15 <= h(0.0) + 2e-15  # never worse than the plain step
+        assert h(d) <= ref.fun + 1e-13
+        assert d == pytest.approx(ref.x, abs=1e-5)
+
+
+def test_thread_greedy_applies_the_improved_increments_from_the_start_state():
+    # Jacobi (R5): every accepted increment is improved at the start state,
+    # then all are applied
+    p = workloads.uniform_problem(300, 120, 8, values="lognormal", loss="logistic", seed=6)
+    orc = oracle.Oracle(p)
+    orc.set_lambda(0.05 * orc.lambda_max())
+    w0 = np.random.default_rng(6).normal(0, 0.3, p.k) * (np.random.default_rng(7).random(p.k) < 0.3)
+    z0 = orc.fitted(w0)
+    w_plain, _, _, _ = orc.run("thread_greedy", 1, w=w0, B=8)
+    w_imp, z_imp, _, _ = orc.run("thread_greedy", 1, w=w0, B=8, improve_steps=500)
+    moved = np.flatnonzero(w_plain != w0)
+    np.testing.assert_array_equal(np.flatnonzero(w_imp != w0), moved)
+    for j in moved:
+        d = orc.improve(w0, z0, j, w_plain[j] - w0[j], 500)
+        assert w_imp[j] - w0[j] == pytest.approx(d, rel=1e-12, abs=1e-15)
+    np.testing.assert_allclose(z_imp, orc.fitted(w_imp), rtol=0, atol=1e-12)
+
+
+def test_cyclic_cd_with_improve_reaches_the_same_optimum():
+    p = workloads.config1("logistic")
+    orc = oracle.Oracle(p)
+    orc.set_lambda(0.05 * orc.lambda_max())
+    w_a, _, it_a, kkt_a, _ = orc.solve("ccd", tol_kkt=1e-10)
+    w_b, _, it_b, kkt_b, _ = orc.solve("ccd", tol_kkt=1e-10, improve_steps=500)
+    assert kkt_a <= 1e-10 and kkt_b <= 1e-10
+    assert orc.objective(w_b) == pytest.approx(orc.objective(w_a), rel=1e-10)
+    assert it_b <= it_a  # exact coordinate minimisation needs no more sweeps
