@@ -17,9 +17,9 @@ import numpy as np
 from . import build as _build
 
 SQUARED, LOGISTIC = 0, 1
-SHOTGUN, THREAD_GREEDY, GREEDY, COLORING, CCD = 0, 1, 2, 3, 4
+SHOTGUN, THREAD_GREEDY, GREEDY, COLORING, CCD, TOP_GREEDY = 0, 1, 2, 3, 4, 5
 _LOSS = {"squared": SQUARED, "logistic": LOGISTIC, SQUARED: SQUARED, LOGISTIC: LOGISTIC}
-_VARIANT = {"shotgun": SHOTGUN, "thread_greedy": THREAD_GREEDY, "greedy": GREEDY,
+_VARIANT = {"shotgun": SHOTGUN, "thread_greedy": THREAD_GREEDY, "greedy": GREEDY, "top_greedy": TOP_GREEDY,
             "coloring": COLORING, "ccd": CCD}
 
 _i64p = C.POINTER(C.c_int64)

@@ -36,6 +36,11 @@
  *  R8  The colouring is greedy first-fit over the columns in index order.
  *  R9  KKT violation: max(|g_j| - lambda, 0) if w_j == 0, else
  *      |g_j + lambda sign(w_j)|.
+ *  R12 Thread-Greedy with a global top-|J'| Accept (Section 7 leaves it as
+ *      an extension): every column is proposed, as for Thread-Greedy, and
+ *      the B proposals with the lowest proxies are accepted (only proxies
+ *      < 0; equal proxies go to the lower column), whichever partition they
+ *      fall in.  B = 1 is Greedy.
  *  R11 "Improve delta_j" (Algorithm 3; Section 4.1 adds "500 steps using the
  *      quadratic approximation" per accepted proposal, without further
  *      detail): the Eq. 7 step is repeated on coordinate j alone, each time
@@ -367,6 +372,20 @@ static int cmp_i32(const void* a, const void* b) {
   return (x > y) - (x < y);
 }
 
+/* R12: positions ordered by proxy, equal proxies by position (= column) */
+static const double* qsort_ctx_phi = NULL; /* the oracle is single-threaded */
+static int cmp_by_phi(const void* a, const void* b) {
+  int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+  double px = qsort_ctx_phi[x], py = qsort_ctx_phi[y];
+  if (px < py) return -1;
+  if (px > py) return 1;
+  return (x > y) - (x < y);
+}
+static int cmp_i64(const void* a, const void* b) {
+  int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+  return (x > y) - (x < y);
+}
+
 /* Update (Algorithm 3) for one accepted proposal: w_j += delta, z += delta X_j. */
 static void apply_update(const oracle_problem* pr, int64_t j, double delta, double* w, double* z) {
   w[j] += delta;
@@ -381,7 +400,7 @@ int oracle_run(const oracle_problem* pr, const oracle_params* pa, int64_t t0, in
   if (k <= 0) return -1;
   int v = pa->variant;
   if (v == ORACLE_SHOTGUN && (pa->P < 1)) return -1;
-  if (v == ORACLE_THREAD_GREEDY && pa->B < 1) return -1;
+  if ((v == ORACLE_THREAD_GREEDY || v == ORACLE_TOP_GREEDY) && pa->B < 1) return -1;
   if (v == ORACLE_COLORING && (pa->colors == NULL || pa->ncolors < 1)) return -1;
 
   int32_t* J = (int32_t*)malloc(sizeof(int32_t) * (size_t)k);
@@ -417,7 +436,7 @@ int oracle_run(const oracle_problem* pr, const oracle_params* pa, int64_t t0, in
       int32_t colour = perm[q];
       for (int64_t j = 0; j < k; ++j)
         if (pa->colors[j] == colour) J[m++] = (int32_t)j;
-    } else { /* Thread-Greedy and Greedy select all columns */
+    } else { /* Thread-Greedy, Greedy and top-greedy select all columns */
       for (int64_t j = 0; j < k; ++j) J[m++] = (int32_t)j;
     }
 
@@ -436,6 +455,13 @@ int oracle_run(const oracle_problem* pr, const oracle_params* pa, int64_t t0, in
           if (best < 0 || phi[a] < phi[best]) best = a; /* strict: ties keep the lower j */
         if (best >= 0 && phi[best] < 0.0) acc[na++] = best;
       }
+    } else if (v == ORACLE_TOP_GREEDY) { /* R12: the B lowest proxies < 0 */
+      for (int64_t a = 0; a < m; ++a)
+        if (phi[a] < 0.0) acc[na++] = a;
+      qsort_ctx_phi = phi;
+      qsort(acc, (size_t)na, sizeof(int64_t), cmp_by_phi);
+      if (na > pa->B) na = pa->B;
+      qsort(acc, (size_t)na, sizeof(int64_t), cmp_i64); /* R5: ascending application */
     } else { /* Shotgun, Coloring, CCD accept every proposal */
       for (int64_t a = 0; a < m; ++a) acc[na++] = a;
     }

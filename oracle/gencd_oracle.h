@@ -27,7 +27,8 @@ enum {
   ORACLE_THREAD_GREEDY = 1, /* Table 2: all, best proxy per partition        */
   ORACLE_GREEDY = 2,        /* Table 2: all, single best proxy               */
   ORACLE_COLORING = 3,      /* Table 2: random colour, accept all            */
-  ORACLE_CCD = 4            /* Section 2.1: cyclic singleton                 */
+  ORACLE_CCD = 4,           /* Section 2.1: cyclic singleton                 */
+  ORACLE_TOP_GREEDY = 5     /* Section 7 (R12): all, the best B proxies      */
 };
 
 typedef struct {
@@ -43,7 +44,7 @@ typedef struct {
 
 typedef struct {
   int32_t variant;       /* ORACLE_* variant                                 */
-  int32_t B;             /* Thread-Greedy partitions (>= 1)                  */
+  int32_t B;             /* Thread-Greedy partitions; top-greedy: |J'| (>= 1) */
   int64_t P;             /* Shotgun subset size (>= 1)                       */
   uint64_t seed;         /* selection stream seed                            */
   const int32_t* colors; /* Coloring: colour of each column, 0..ncolors-1    */

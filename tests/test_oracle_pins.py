@@ -646,3 +646,31 @@ def test_cyclic_cd_with_improve_reaches_the_same_optimum():
     assert kkt_a <= 1e-10 and kkt_b <= 1e-10
     assert orc.objective(w_b) == pytest.approx(orc.objective(w_a), rel=1e-10)
     assert it_b <= it_a  # exact coordinate minimisation needs no more sweeps
+
+
+# --- R12: Thread-Greedy with a global top-|J'| Accept (Section 7) ----------
+
+def test_top_greedy_with_one_accept_is_greedy():
+    p = workloads.uniform_problem(200, 80, 6, values="lognormal", loss="logistic", seed=12)
+    orc = oracle.Oracle(p)
+    orc.set_lambda(0.05 * orc.lambda_max())
+    w_a, _, _, _ = orc.run("greedy", 25)
+    w_b, _, _, _ = orc.run("top_greedy", 25, B=1)
+    np.testing.assert_array_equal(w_a, w_b)
+
+
+@pytest.mark.parametrize("B", [3, 17, 10_000])
+def test_top_greedy_accepts_the_lowest_proxies(B):
+    p = workloads.uniform_problem(300, 150, 8, values="pm1", loss="squared", seed=13)
+    orc = oracle.Oracle(p)
+    orc.set_lambda(0.05 * orc.lambda_max())
+    w0 = np.random.default_rng(13).normal(0, 0.2, p.k) * (np.random.default_rng(14).random(p.k) < 0.2)
+    z0 = orc.fitted(w0)
+    d, f = orc.propose(w0, z0, np.arange(p.k, dtype=np.int32))
+    neg = np.flatnonzero(f < 0)
+    order = neg[np.lexsort((neg, f[neg]))]  # proxy ascending, then column
+    want = np.sort(order[:B])
+    w1, _, _, st = orc.run("top_greedy", 1, w=w0, B=B)
+    np.testing.assert_array_equal(np.flatnonzero(w1 != w0), want)
+    np.testing.assert_allclose(w1[want] - w0[want], d[want], rtol=1e-13, atol=0)
+    assert st[0] == want.size
