@@ -225,6 +225,20 @@ int gencd_spectral_radius(gencd_problem* p, double* rho, int64_t* pstar, int32_t
  * greedy first-fit in column order.  *ncolors receives the colour count.
  */
 int gencd_color(gencd_problem* p, int32_t* ncolors);
+/*
+ * Balanced distance-2 colouring on the host (preprocessing, no GPU work):
+ * the paper notes that the fewest colours need not give the most parallelism
+ * and that balanced colour classes are preferable (Section 7).  Columns in
+ * index order; column j takes, among the colours no lower-index column
+ * sharing a row with it uses, the one with the fewest columns so far that is
+ * still below `cap` (ties: the lower colour), or a new colour.  cap <= 0:
+ * ceil(k / C), C the first-fit colour count of gencd_color.  col_ptr
+ * int64[k+1] and row_idx int32[nnz] are host arrays (validated as by
+ * gencd_create); colors int32[k] receives the colours, *ncolors their count.
+ * Install them with gencd_set_colors to run the Coloring variant on them.
+ */
+int gencd_color_balanced_csc(int64_t n, int64_t k, const int64_t* col_ptr, const int32_t* row_idx, int64_t cap,
+                             int32_t* colors, int32_t* ncolors);
 /* Copies the colours (int32[k]) out, or installs caller colours (validated:
  * columns sharing a row must differ; colours in [0, k)). */
 int gencd_get_colors(gencd_problem* p, int32_t* colors, int64_t k, int32_t memory);

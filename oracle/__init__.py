@@ -67,6 +67,7 @@ def lib():
             "oracle_spectral_radius": (C.c_double, [vp, C.c_int32, C.c_double, _i32p]),
             "oracle_pstar": (C.c_int64, [C.c_int64, C.c_double]),
             "oracle_color": (C.c_int32, [vp, _i32p]),
+            "oracle_color_balanced": (C.c_int32, [vp, C.c_int64, _i32p]),
             "oracle_run": (C.c_int, [vp, vp, C.c_int64, C.c_int64, _f64p, _f64p, _f64p, _i64p]),
             "oracle_solve": (C.c_int64, [vp, vp, C.c_double, C.c_int64, C.c_int64, _f64p, _f64p,
                                          _f64p, _i64p]),
@@ -178,6 +179,12 @@ class Oracle:
         c = np.empty(self.k, np.int32)
         nc = lib().oracle_color(self._ptr, _p(c, _i32p))
         return c, nc
+
+    def color_balanced(self, cap=0):
+        """R13: balanced distance-2 colouring; returns (colors, ncolors)."""
+        c = np.empty(self.k, np.int32)
+        nc = lib().oracle_color_balanced(self._ptr, int(cap), _p(c, _i32p))
+        return c, int(nc)
 
     # --- iterations ----------------------------------------------------------
     def _params(self, variant, B=1, P=1, seed=0, colors=None, improve_steps=0):

@@ -36,6 +36,10 @@
  *  R8  The colouring is greedy first-fit over the columns in index order.
  *  R9  KKT violation: max(|g_j| - lambda, 0) if w_j == 0, else
  *      |g_j + lambda sign(w_j)|.
+ *  R13 Balanced colouring (Section 7: fewer colours need not mean more
+ *      parallelism; a balanced distribution is preferable): greedy in column
+ *      order, each column taking the least-used admissible colour below a
+ *      size cap (default ceil(k / C_first-fit)), a new colour if none.
  *  R12 Thread-Greedy with a global top-|J'| Accept (Section 7 leaves it as
  *      an extension): every column is proposed, as for Thread-Greedy, and
  *      the B proposals with the lowest proxies are accepted (only proxies
@@ -362,6 +366,45 @@ int32_t oracle_color(const oracle_problem* pr, int32_t* colors) {
   free(rc);
   free(fill);
   free(mark);
+  return ncolors;
+}
+
+int32_t oracle_color_balanced(const oracle_problem* pr, int64_t cap, int32_t* colors) {
+  int64_t n = pr->n, k = pr->k, nnz = pr->col_ptr[k];
+  if (k == 0) return 0;
+  if (cap <= 0) {
+    int32_t c0 = oracle_color(pr, colors);
+    cap = (k + c0 - 1) / c0;
+  }
+  int64_t* rp = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  int32_t* rc = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  for (int64_t p = 0; p < nnz; ++p) rp[pr->row_idx[p] + 1] += 1;
+  for (int64_t i = 0; i < n; ++i) rp[i + 1] += rp[i];
+  for (int64_t i = 0; i < n; ++i) fill[i] = rp[i];
+  for (int64_t j = 0; j < k; ++j)
+    for (int64_t p = pr->col_ptr[j]; p < pr->col_ptr[j + 1]; ++p) rc[fill[pr->row_idx[p]]++] = (int32_t)j;
+  int64_t* mark = (int64_t*)calloc((size_t)k + 1, sizeof(int64_t));
+  int64_t* size = (int64_t*)calloc((size_t)k + 1, sizeof(int64_t));
+  int32_t ncolors = 0;
+  for (int64_t j = 0; j < k; ++j) {
+    for (int64_t p = pr->col_ptr[j]; p < pr->col_ptr[j + 1]; ++p) {
+      int32_t i = pr->row_idx[p];
+      for (int64_t q = rp[i]; q < rp[i + 1]; ++q)
+        if (rc[q] < j) mark[colors[rc[q]]] = j + 1;
+    }
+    int32_t best = -1;
+    for (int32_t c = 0; c < ncolors; ++c)
+      if (mark[c] != j + 1 && size[c] < cap && (best < 0 || size[c] < size[best])) best = c;
+    if (best < 0) best = ncolors++;
+    colors[j] = best;
+    size[best] += 1;
+  }
+  free(rp);
+  free(rc);
+  free(fill);
+  free(mark);
+  free(size);
   return ncolors;
 }
 

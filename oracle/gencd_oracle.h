@@ -110,6 +110,13 @@ int64_t oracle_pstar(int64_t k, double rho);
 /* Greedy first-fit partial distance-2 colouring of the columns in index
  * order.  Returns the number of colours. */
 int32_t oracle_color(const oracle_problem* pr, int32_t* colors);
+/* R13: balanced distance-2 colouring (Section 7 asks for balanced colour
+ * classes rather than the fewest colours).  Columns in index order; column j
+ * takes, among the colours not used by lower-index columns sharing a row with
+ * it, the one with the fewest columns so far that is still below `cap`
+ * (ties: the lower colour), or a new colour when none is.  cap <= 0 means
+ * ceil(k / C), C the first-fit colour count (R8).  Returns the colour count. */
+int32_t oracle_color_balanced(const oracle_problem* pr, int64_t cap, int32_t* colors);
 
 /* Runs GenCD iterations t0 .. t0+iters-1 (Algorithm 1) from (w, z), updating
  * both in place.  obj_trace (nullable) receives P(w) after every iteration.

@@ -45,7 +45,7 @@ EXPORTS = ["gencd_create", "gencd_destroy", "gencd_set_lambda", "gencd_set_loss"
            "gencd_default_params", "gencd_set_params", "gencd_get_params", "gencd_solve",
            "gencd_iterate", "gencd_set_iteration", "gencd_get_iteration", "gencd_get_w",
            "gencd_set_w", "gencd_get_z", "gencd_objective", "gencd_propose_at", "gencd_propose_all",
-           "gencd_spectral_radius", "gencd_color", "gencd_get_colors", "gencd_set_colors",
+           "gencd_spectral_radius", "gencd_color", "gencd_color_balanced_csc", "gencd_get_colors", "gencd_set_colors",
            "gencd_permutation", "gencd_profile_enable", "gencd_profile_read", "gencd_profile_reset",
            "gencd_last_error", "gencd_stats", "gencd_stats_reset", "gencd_propose_all_noalloc",
            # include/gencd_batch.h
@@ -140,6 +140,7 @@ def lib():
             "gencd_propose_all": (C.c_int, [vp, vp, vp, i32, C.POINTER(f64)]),
             "gencd_spectral_radius": (C.c_int, [vp, C.POINTER(f64), C.POINTER(i64), C.POINTER(i32)]),
             "gencd_color": (C.c_int, [vp, C.POINTER(i32)]),
+            "gencd_color_balanced_csc": (C.c_int, [i64, i64, vp, vp, i64, vp, C.POINTER(i32)]),
             "gencd_get_colors": (C.c_int, [vp, vp, i64, i32]),
             "gencd_set_colors": (C.c_int, [vp, vp, i64, i32]),
             "gencd_permutation": (C.c_int, [vp, C.c_uint64, i64, i64, vp]),
@@ -367,6 +368,18 @@ def gencd_color(h) -> int:
     c = C.c_int32()
     _check(lib().gencd_color(h, C.byref(c)))
     return c.value
+
+
+def gencd_color_balanced_csc(n, k, col_ptr, row_idx, cap=0):
+    """Balanced distance-2 colouring of a host CSC (no GPU work); returns
+    (colors int32[k], ncolors)."""
+    cp = np.ascontiguousarray(col_ptr, np.int64)
+    ri = np.ascontiguousarray(row_idx, np.int32)
+    c = np.empty(int(k), np.int32)
+    nc = C.c_int32()
+    _check(lib().gencd_color_balanced_csc(int(n), int(k), C.c_void_p(cp.ctypes.data), C.c_void_p(ri.ctypes.data),
+                                          int(cap), C.c_void_p(c.ctypes.data), C.byref(nc)))
+    return c, nc.value
 
 
 def gencd_get_colors(h, k):

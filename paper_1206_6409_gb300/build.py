@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgencd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "kernels_propose.cu", "kernels_update.cu", "kernels_setup.cu", "propose_plan.cu",
-           "noalloc.cu", "batch.cu", "serve.cu"]
+           "noalloc.cu", "batch.cu", "serve.cu", "color_balanced.cu"]
 
 
 def _nvcc() -> str:

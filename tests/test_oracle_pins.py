@@ -674,3 +674,65 @@ def test_top_greedy_accepts_the_lowest_proxies(B):
     np.testing.assert_array_equal(np.flatnonzero(w1 != w0), want)
     np.testing.assert_allclose(w1[want] - w0[want], d[want], rtol=1e-13, atol=0)
     assert st[0] == want.size
+
+
+# --- R13: balanced colouring (Section 7) -------------------------------------
+
+def _csc(cols, n):
+    """CSC problem from per-column row lists (values 1)."""
+    X = np.zeros((n, len(cols)))
+    for j, rows in enumerate(cols):
+        X[rows, j] = 1.0
+    return workloads.csc_from_dense(X, np.ones(n), "squared")
+
+
+def _valid_distance2(p, colors):
+    rows_of = [set(p.row_idx[p.col_ptr[j]:p.col_ptr[j + 1]]) for j in range(p.k)]
+    for a in range(p.k):
+        for b in range(a + 1, p.k):
+            if rows_of[a] & rows_of[b] and colors[a] == colors[b]:
+                return False
+    return True
+
+
+def test_balanced_colouring_hand_examples():
+    # six columns in separate rows: first-fit needs one colour; the default
+    # cap ceil(6/1) keeps them together, a cap of 2 deals them out in order
+    free = _csc([[0], [1], [2], [3], [4], [5]], 6)
+    o = oracle.Oracle(free)
+    assert o.color()[1] == 1
+    np.testing.assert_array_equal(o.color_balanced()[0], [0] * 6)
+    np.testing.assert_array_equal(o.color_balanced(cap=2)[0], [0, 0, 1, 1, 2, 2])
+    # columns 0-2 share row 0, columns 3-5 are free: first-fit gives class
+    # sizes 4, 1, 1; the balanced rule (cap ceil(6/3) = 2) gives 2, 2, 2
+    tri = _csc([[0, 1], [0, 2], [0, 3], [4], [5], [6]], 7)
+    o = oracle.Oracle(tri)
+    ff, c0 = o.color()
+    np.testing.assert_array_equal(ff, [0, 1, 2, 0, 0, 0])
+    bal, c1 = o.color_balanced()
+    np.testing.assert_array_equal(bal, [0, 1, 2, 0, 1, 2])
+    assert c0 == c1 == 3
+
+
+def test_balanced_colouring_is_valid_capped_and_flatter():
+    p = workloads.zipf_problem(400, 600, 6000, cap=80, n_planted=10, seed=8)
+    o = oracle.Oracle(p)
+    ff, c0 = o.color()
+    bal, c1 = o.color_balanced()
+    cap = -(-p.k // c0)
+    assert _valid_distance2(p, bal)
+    sizes_ff = np.bincount(ff, minlength=c0)
+    sizes = np.bincount(bal, minlength=c1)
+    assert sizes.max() <= cap and c1 >= c0
+    assert sizes.max() < sizes_ff.max() and sizes.std() < sizes_ff.std()
+
+
+def test_coloring_with_balanced_colours_reaches_the_optimum():
+    p = workloads.config1("squared")
+    o = oracle.Oracle(p)
+    o.set_lambda(0.05 * o.lambda_max())
+    bal, _ = o.color_balanced()
+    w_ref, _, _, _, _ = o.solve("ccd", tol_kkt=1e-11)
+    w, _, _, kkt, _ = o.solve("coloring", tol_kkt=1e-10, colors=bal, seed=3, max_iter=10**6)
+    assert kkt <= 1e-10
+    assert o.objective(w) == pytest.approx(o.objective(w_ref), rel=1e-9)
