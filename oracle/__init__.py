@@ -17,9 +17,10 @@ import numpy as np
 from . import build as _build
 
 SQUARED, LOGISTIC = 0, 1
-SHOTGUN, THREAD_GREEDY, GREEDY, COLORING, CCD, TOP_GREEDY = 0, 1, 2, 3, 4, 5
+SHOTGUN, THREAD_GREEDY, GREEDY, COLORING, CCD, TOP_GREEDY, SHOTGUN_BLOCKS = 0, 1, 2, 3, 4, 5, 6
 _LOSS = {"squared": SQUARED, "logistic": LOGISTIC, SQUARED: SQUARED, LOGISTIC: LOGISTIC}
 _VARIANT = {"shotgun": SHOTGUN, "thread_greedy": THREAD_GREEDY, "greedy": GREEDY, "top_greedy": TOP_GREEDY,
+            "shotgun_blocks": SHOTGUN_BLOCKS,
             "coloring": COLORING, "ccd": CCD}
 
 _i64p = C.POINTER(C.c_int64)
@@ -35,7 +36,8 @@ class _Problem(C.Structure):
 
 class _Params(C.Structure):
     _fields_ = [("variant", C.c_int32), ("B", C.c_int32), ("P", C.c_int64), ("seed", C.c_uint64),
-                ("colors", _i32p), ("ncolors", C.c_int32), ("improve_steps", C.c_int32)]
+                ("colors", _i32p), ("ncolors", C.c_int32), ("improve_steps", C.c_int32),
+                ("block_P", _i64p)]
 
 
 _lib = None
@@ -66,6 +68,7 @@ def lib():
             "oracle_permutation": (None, [C.c_uint64, C.c_int64, C.c_int64, _i32p]),
             "oracle_spectral_radius": (C.c_double, [vp, C.c_int32, C.c_double, _i32p]),
             "oracle_pstar": (C.c_int64, [C.c_int64, C.c_double]),
+            "oracle_block_pstar": (None, [vp, C.c_int32, C.c_int32, C.c_double, _i64p]),
             "oracle_color": (C.c_int32, [vp, _i32p]),
             "oracle_color_balanced": (C.c_int32, [vp, C.c_int64, _i32p]),
             "oracle_run": (C.c_int, [vp, vp, C.c_int64, C.c_int64, _f64p, _f64p, _f64p, _i64p]),
@@ -163,6 +166,12 @@ class Oracle:
                              _p(d, _f64p), _p(f, _f64p))
         return d, f
 
+    def block_pstar(self, B, max_iter=100, rel_tol=1e-6):
+        """R14: P*_b of each of B contiguous column blocks."""
+        out = np.empty(int(B), np.int64)
+        lib().oracle_block_pstar(self._ptr, int(B), int(max_iter), float(rel_tol), _p(out, _i64p))
+        return out
+
     def improve(self, w, z, j, d, steps):
         """R11: the increment d of column j improved by up to `steps` Eq. 7
         steps on coordinate j alone (Algorithm 3's Improve)."""
@@ -187,7 +196,7 @@ class Oracle:
         return c, int(nc)
 
     # --- iterations ----------------------------------------------------------
-    def _params(self, variant, B=1, P=1, seed=0, colors=None, improve_steps=0):
+    def _params(self, variant, B=1, P=1, seed=0, colors=None, improve_steps=0, block_P=None):
         pa = _Params()
         pa.variant = _VARIANT[variant] if isinstance(variant, str) else int(variant)
         pa.B, pa.P, pa.seed = int(B), int(P), int(seed) & ((1 << 64) - 1)
@@ -196,14 +205,17 @@ class Oracle:
             colors = np.ascontiguousarray(colors, np.int32)
             pa.colors = _p(colors, _i32p)
             pa.ncolors = int(colors.max()) + 1 if colors.size else 0
-        return pa, colors
+        if block_P is not None:
+            block_P = np.ascontiguousarray(block_P, np.int64)
+            pa.block_P = _p(block_P, _i64p)
+        return pa, (colors, block_P)
 
     def run(self, variant, iters, w=None, z=None, t0=0, B=1, P=1, seed=0, colors=None,
-            trace=False, improve_steps=0):
+            trace=False, improve_steps=0, block_P=None):
         """Runs iterations t0..t0+iters-1; returns (w, z, trace, stats)."""
         w = np.zeros(self.k) if w is None else np.array(w, np.float64)
         z = self.fitted(w) if z is None else np.array(z, np.float64)
-        pa, keep = self._params(variant, B, P, seed, colors, improve_steps)
+        pa, keep = self._params(variant, B, P, seed, colors, improve_steps, block_P)
         tr = np.empty(iters) if trace else None
         st = np.zeros(3, np.int64)
         rc = lib().oracle_run(self._ptr, C.byref(pa), t0, iters, _p(w, _f64p), _p(z, _f64p),
@@ -214,13 +226,13 @@ class Oracle:
         return w, z, tr, st
 
     def solve(self, variant="ccd", tol_kkt=1e-10, max_iter=10**8, check_every=None, w=None,
-              B=1, P=1, seed=0, colors=None, improve_steps=0):
+              B=1, P=1, seed=0, colors=None, improve_steps=0, block_P=None):
         """Iterates until KKT <= tol_kkt; returns (w, z, iters, kkt, stats)."""
         w = np.zeros(self.k) if w is None else np.array(w, np.float64)
         z = self.fitted(w)
         if check_every is None:
             check_every = self.k if variant == "ccd" else 10
-        pa, keep = self._params(variant, B, P, seed, colors, improve_steps)
+        pa, keep = self._params(variant, B, P, seed, colors, improve_steps, block_P)
         kkt = C.c_double(0.0)
         st = np.zeros(3, np.int64)
         it = lib().oracle_solve(self._ptr, C.byref(pa), tol_kkt, max_iter, check_every,

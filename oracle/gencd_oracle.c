@@ -36,6 +36,12 @@
  *  R8  The colouring is greedy first-fit over the columns in index order.
  *  R9  KKT violation: max(|g_j| - lambda, 0) if w_j == 0, else
  *      |g_j + lambda sign(w_j)|.
+ *  R14 Block Shotgun (Section 7: partition the columns into blocks and
+ *      compute a P*_b per block): B contiguous column blocks; P*_b is P* of
+ *      the block's own normalised Gram matrix; an iteration takes, from
+ *      every block, the next P*_b columns of that block's per-epoch
+ *      permutation (block b's stream seeded with seed + b, so one block is
+ *      Shotgun at P*) and accepts them all.
  *  R13 Balanced colouring (Section 7: fewer colours need not mean more
  *      parallelism; a balanced distribution is preferable): greedy in column
  *      order, each column taking the least-used admissible colour below a
@@ -333,6 +339,16 @@ int64_t oracle_pstar(int64_t k, double rho) {
   return (int64_t)p;
 }
 
+void oracle_block_pstar(const oracle_problem* pr, int32_t B, int32_t max_iter, double rel_tol, int64_t* Pb) {
+  for (int32_t b = 0; b < B; ++b) {
+    int64_t lo = pr->k * b / B, hi = pr->k * (b + 1) / B;
+    oracle_problem view = *pr; /* the block's columns; offsets stay absolute */
+    view.col_ptr = pr->col_ptr + lo;
+    view.k = hi - lo;
+    Pb[b] = hi > lo ? oracle_pstar(hi - lo, oracle_spectral_radius(&view, max_iter, rel_tol, NULL)) : 0;
+  }
+}
+
 /* ---- R8: greedy first-fit partial distance-2 colouring ------------------ */
 
 int32_t oracle_color(const oracle_problem* pr, int32_t* colors) {
@@ -444,6 +460,7 @@ int oracle_run(const oracle_problem* pr, const oracle_params* pa, int64_t t0, in
   int v = pa->variant;
   if (v == ORACLE_SHOTGUN && (pa->P < 1)) return -1;
   if ((v == ORACLE_THREAD_GREEDY || v == ORACLE_TOP_GREEDY) && pa->B < 1) return -1;
+  if (v == ORACLE_SHOTGUN_BLOCKS && (pa->B < 1 || pa->block_P == NULL)) return -1;
   if (v == ORACLE_COLORING && (pa->colors == NULL || pa->ncolors < 1)) return -1;
 
   int32_t* J = (int32_t*)malloc(sizeof(int32_t) * (size_t)k);
@@ -468,6 +485,17 @@ int oracle_run(const oracle_problem* pr, const oracle_params* pa, int64_t t0, in
         perm_epoch = e;
       }
       for (int64_t a = q * P; a < k && a < (q + 1) * P; ++a) J[m++] = perm[a];
+      qsort(J, (size_t)m, sizeof(int32_t), cmp_i32); /* R5: ascending application */
+    } else if (v == ORACLE_SHOTGUN_BLOCKS) { /* R14: P*_b columns from every block */
+      for (int32_t b = 0; b < pa->B; ++b) {
+        int64_t lo = k * b / pa->B, hi = k * (b + 1) / pa->B, kb = hi - lo;
+        if (kb == 0) continue;
+        int64_t P = pa->block_P[b] < 1 ? 1 : (pa->block_P[b] < kb ? pa->block_P[b] : kb);
+        int64_t per_epoch = (kb + P - 1) / P;
+        int64_t e = t / per_epoch, q = t % per_epoch;
+        oracle_permutation(pa->seed + (uint64_t)b, e, kb, perm);
+        for (int64_t a = q * P; a < kb && a < (q + 1) * P; ++a) J[m++] = (int32_t)(lo + perm[a]);
+      }
       qsort(J, (size_t)m, sizeof(int32_t), cmp_i32); /* R5: ascending application */
     } else if (v == ORACLE_COLORING) {
       int64_t C = pa->ncolors;

@@ -28,7 +28,8 @@ enum {
   ORACLE_GREEDY = 2,        /* Table 2: all, single best proxy               */
   ORACLE_COLORING = 3,      /* Table 2: random colour, accept all            */
   ORACLE_CCD = 4,           /* Section 2.1: cyclic singleton                 */
-  ORACLE_TOP_GREEDY = 5     /* Section 7 (R12): all, the best B proxies      */
+  ORACLE_TOP_GREEDY = 5,    /* Section 7 (R12): all, the best B proxies      */
+  ORACLE_SHOTGUN_BLOCKS = 6 /* Section 7 (R14): Shotgun with P*_b per block  */
 };
 
 typedef struct {
@@ -50,6 +51,7 @@ typedef struct {
   const int32_t* colors; /* Coloring: colour of each column, 0..ncolors-1    */
   int32_t ncolors;
   int32_t improve_steps; /* R11: "Improve delta_j" steps per accepted proposal (0: off) */
+  const int64_t* block_P; /* R14: subset size of each of the B column blocks   */
 } oracle_params;
 
 /* Section 1 losses and their derivative in the fitted value t. */
@@ -106,6 +108,11 @@ double oracle_spectral_radius(const oracle_problem* pr, int32_t max_iter, double
                               int32_t* iters_out);
 /* Shotgun's P* = max(1, floor(k / (2 rho))) (Section 4.1). */
 int64_t oracle_pstar(int64_t k, double rho);
+
+/* R14: P*_b of each of B contiguous column blocks (block b = columns
+ * floor(b k / B) .. floor((b+1) k / B) - 1): oracle_pstar of the block's own
+ * spectral radius (power iteration as oracle_spectral_radius). */
+void oracle_block_pstar(const oracle_problem* pr, int32_t B, int32_t max_iter, double rel_tol, int64_t* Pb);
 
 /* Greedy first-fit partial distance-2 colouring of the columns in index
  * order.  Returns the number of colours. */

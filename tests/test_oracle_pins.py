@@ -736,3 +736,57 @@ def test_coloring_with_balanced_colours_reaches_the_optimum():
     w, _, _, kkt, _ = o.solve("coloring", tol_kkt=1e-10, colors=bal, seed=3, max_iter=10**6)
     assert kkt <= 1e-10
     assert o.objective(w) == pytest.approx(o.objective(w_ref), rel=1e-9)
+
+
+# --- R14: block Shotgun, a P*_b per column block (Section 7) ----------------
+
+def test_block_shotgun_with_one_block_is_shotgun_at_pstar():
+    p = workloads.uniform_problem(200, 120, 5, values="lognormal", loss="logistic", seed=15)
+    o = oracle.Oracle(p)
+    o.set_lambda(0.05 * o.lambda_max())
+    rho, _ = o.spectral_radius(max_iter=1000, rel_tol=1e-12)
+    pstar = oracle.pstar(p.k, rho)
+    Pb = o.block_pstar(1, max_iter=1000, rel_tol=1e-12)
+    assert list(Pb) == [pstar]
+    w_a, _, _, _ = o.run("shotgun", 30, P=pstar, seed=5)
+    w_b, _, _, _ = o.run("shotgun_blocks", 30, B=1, block_P=Pb, seed=5)
+    np.testing.assert_array_equal(w_a, w_b)
+
+
+def test_block_pstar_is_each_blocks_own_bound():
+    p = workloads.uniform_problem(60, 45, 6, values="pm1", loss="squared", seed=16)
+    o = oracle.Oracle(p)
+    B = 4
+    Pb = o.block_pstar(B, max_iter=5000, rel_tol=1e-14)
+    X = p.to_dense()
+    for b in range(B):
+        lo, hi = p.k * b // B, p.k * (b + 1) // B
+        Xb = X[:, lo:hi]
+        nb = np.sqrt((Xb * Xb).sum(0))
+        M = (Xb / nb).T @ (Xb / nb)
+        rho = np.linalg.eigvalsh(M)[-1]
+        assert Pb[b] == max(1, int(np.floor((hi - lo) / (2 * rho))))
+    # one iteration takes P*_b columns from every block and accepts them all
+    o.set_lambda(0.01 * o.lambda_max())
+    _, _, _, st = o.run("shotgun_blocks", 1, B=B, block_P=Pb, seed=2)
+    assert st[0] == int(np.minimum(Pb, [p.k * (b + 1) // B - p.k * b // B for b in range(B)]).sum())
+
+
+def test_block_shotgun_converges_on_orthogonal_blocks():
+    # block-diagonal X: the blocks are independent problems that share the loss
+    rng = np.random.default_rng(17)
+    n, kb, B = 240, 40, 3
+    X = np.zeros((n, kb * B))
+    for b in range(B):
+        rows = slice(b * n // B, (b + 1) * n // B)
+        Xb = rng.normal(size=(n // B, kb)) * (rng.random((n // B, kb)) < 0.2)
+        X[rows, b * kb:(b + 1) * kb] = Xb
+    y = X @ (rng.normal(size=kb * B) * (rng.random(kb * B) < 0.1)) + 0.01 * rng.normal(size=n)
+    p = workloads.csc_from_dense(X, y, "squared")
+    o = oracle.Oracle(p)
+    o.set_lambda(0.05 * o.lambda_max())
+    Pb = o.block_pstar(B)
+    w_ref, _, _, _, _ = o.solve("ccd", tol_kkt=1e-11)
+    w, _, _, kkt, _ = o.solve("shotgun_blocks", tol_kkt=1e-10, B=B, block_P=Pb, seed=1, max_iter=10**6)
+    assert kkt <= 1e-10
+    assert o.objective(w) == pytest.approx(o.objective(w_ref), rel=1e-9)
