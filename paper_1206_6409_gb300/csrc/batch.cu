@@ -1034,7 +1034,8 @@ static int slot_objectives(gencd_batch* b, const std::vector<int32_t>& slots, st
     GENCD_CUDA_TRY(cudaStreamSynchronize(b->st));
     for (int q = 0; q < m; ++q) {
       const int s = slots[q0 + q], set = b->h_set[s];
-      (*obj)[q0 + q] = h[q] / (double)b->set_rows[set] + b->h_lam[s] * h[m + q];
+      const double rows = (double)b->set_rows[set];  // an empty training set has no loss term
+      (*obj)[q0 + q] = (rows > 0.0 ? h[q] / rows : 0.0) + b->h_lam[s] * h[m + q];
     }
   }
   return GENCD_OK;
