@@ -87,6 +87,12 @@ typedef struct {
   int32_t beta_mode;   /* 0: beta_j = beta * ||X_j||^2 / n (default);
                           1: the literal beta of Eq. 7 (1 squared, 1/4 logistic) */
   double timeout_s;    /* wall-clock cap of gencd_solve in seconds; 0 = none    */
+  int32_t improve_steps; /* "Improve delta_j" (Algorithm 3, Section 4.1): up to
+                            this many Eq. 7 steps refine each accepted increment
+                            on its own coordinate from the iteration-start state
+                            (Thread-Greedy, Greedy, Shotgun; 0 = off, at most
+                            100000)                                              */
+  int32_t reserved;
 } gencd_params;
 
 typedef struct {

@@ -60,7 +60,8 @@ EXPORTS = ["gencd_create", "gencd_destroy", "gencd_set_lambda", "gencd_set_loss"
 class gencd_params(C.Structure):
     _fields_ = [("variant", C.c_int32), ("blocks", C.c_int32), ("P", C.c_int64), ("seed", C.c_uint64),
                 ("max_iter", C.c_int64), ("tol_kkt", C.c_double), ("check_every", C.c_int32),
-                ("beta_mode", C.c_int32), ("timeout_s", C.c_double)]
+                ("beta_mode", C.c_int32), ("timeout_s", C.c_double), ("improve_steps", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class gencd_result(C.Structure):

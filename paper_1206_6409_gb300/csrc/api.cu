@@ -253,6 +253,7 @@ static int enqueue_iteration(gencd_problem* p, int64_t* host_nnz, bool want_kkt)
     GENCD_TRY(launch_propose_all(p, p->u, p->precision == GENCD_F64));  // Propose, all columns
     GENCD_TRY(launch_finalize_accept(p, B, want_kkt));  // step, proxy (+ KKT of the start state); Accept
     GENCD_TRY(launch_merge_accept(p, B));               // accept backoff (groups of partitions), if any
+    GENCD_TRY(launch_improve_list(p, p->list_j, p->list_d, B));  // Improve delta_j (Algorithm 3), if asked
     GENCD_TRY(launch_update_list(p, p->list_j, p->list_d, B, true));     // Update (atomic z)
     GENCD_TRY(launch_refresh_list(p, p->list_j, p->list_d, B, true));
     *host_nnz += p->nnz;
@@ -267,6 +268,7 @@ static int enqueue_iteration(gencd_problem* p, int64_t* host_nnz, bool want_kkt)
     const int64_t lo = q * P, m = (lo + P <= p->k ? P : p->k - lo);
     const int32_t* J = p->perm + lo;
     GENCD_TRY(launch_propose_list(p, J, m, p->list_d, p->phi));          // Propose (Jacobi)
+    GENCD_TRY(launch_improve_list(p, J, p->list_d, m));                  // Improve delta_j, if asked
     GENCD_TRY(launch_update_list(p, J, p->list_d, m, false));            // Accept all, Update
     GENCD_TRY(launch_refresh_list(p, J, p->list_d, m, false));
   } else if (v == GENCD_COLORING) {
@@ -637,7 +639,8 @@ int gencd_set_params(gencd_problem* p, const gencd_params* a) {
   if (!a) return fail(GENCD_EINVAL, "params is NULL");
   if (a->variant < 0 || a->variant > 3) return fail(GENCD_EINVAL, "unknown variant");
   if (a->blocks < 0 || a->P < 0 || a->max_iter < 0 || !(a->tol_kkt >= 0.0) || a->check_every < 1 ||
-      (a->beta_mode != 0 && a->beta_mode != 1) || !(a->timeout_s >= 0.0))
+      (a->beta_mode != 0 && a->beta_mode != 1) || !(a->timeout_s >= 0.0) || a->improve_steps < 0 ||
+      a->improve_steps > 100000)
     return fail(GENCD_EINVAL, "parameter out of range");
   const bool reseed = a->seed != p->params.seed;
   p->params = *a;

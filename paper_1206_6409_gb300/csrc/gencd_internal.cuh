@@ -252,6 +252,9 @@ void free_propose_plan(gencd_problem* p);
 int launch_finalize(gencd_problem* p, double lambda, bool write_steps);
 int launch_finalize_accept(gencd_problem* p, int64_t B, bool want_kkt);  // Thread-Greedy / Greedy
 int launch_merge_accept(gencd_problem* p, int64_t B);  // keep the best of every accept_group partitions
+// Improve delta_j (Algorithm 3): refine the accepted steps D[e] of columns
+// J[e] >= 0 in place (params.improve_steps Eq. 7 steps each; 0: nothing)
+int launch_improve_list(gencd_problem* p, const int32_t* J, double* D, int64_t m);
 int ensure_slots(gencd_problem* p, int64_t count);
 // exclusive prefix sum of m uint32 (in place allowed); tmp holds scan_tmp_words(m)
 int exclusive_scan(gencd_problem* p, const uint32_t* in, uint32_t* out, int64_t m, uint32_t* tmp);

@@ -261,6 +261,63 @@ __global__ void __launch_bounds__(kThreads)
 // ---------------------------------------------------------------------------
 // launchers
 
+// Improve delta_j (Algorithm 3; Section 4.1: further steps of the quadratic
+// approximation per accepted increment): one warp per accepted column j
+// repeats the Eq. 7 step on coordinate j from w_j + d, with g_j at
+// z + d X_j (the iteration-start z: every accepted increment is improved
+// before any is applied), until a step is 0 or `steps` steps.  FP64 in both
+// storage modes.
+template <typename V>
+__global__ void k_improve_list(const int32_t* __restrict__ J, double* __restrict__ D, int64_t m,
+                               const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
+                               const V* __restrict__ val, const double* __restrict__ y, const double* __restrict__ z,
+                               const double* __restrict__ w, const double* __restrict__ bjs,
+                               const double* __restrict__ ibs, int loss, double lam, double inv_n, int steps) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < m; e += nw) {
+    const int32_t j = J[e];
+    if (j < 0) continue;
+    const double bj = bjs[j];
+    if (!(bj > 0.0)) continue;  // a column without entries: its step is already exact
+    const double wj = w[j], ibj = ibs[j];
+    const int64_t a = col_ptr[j], b = col_ptr[j + 1];
+    double d = D[e];
+    for (int s = 0; s < steps; ++s) {  // warp-uniform: g is the same in every lane
+      double acc = 0.0;
+      for (int64_t t = a + lane; t < b; t += 32) {
+        const double x = (double)val[t];
+        const int32_t i = row_idx[t];
+        acc += x * loss_deriv(loss, y[i], z[i] + d * x);
+      }
+      const double g = warp_sum(acc) * inv_n;
+      double step, phi;
+      eq7_step(g, wj + d, lam, bj, ibj, step, phi);
+      if (step == 0.0) break;
+      d += step;
+    }
+    if (lane == 0) D[e] = d;
+  }
+}
+
+int launch_improve_list(gencd_problem* p, const int32_t* J, double* D, int64_t m) {
+  const int steps = p->params.improve_steps;
+  if (steps <= 0 || m <= 0) return GENCD_OK;
+  const int grid = grid_for(m * 32, kThreads, p->num_sms * 8);
+  const double inv_n = 1.0 / (double)p->n;
+  if (p->precision == GENCD_F64)
+    k_improve_list<double><<<grid, kThreads, 0, p->stream>>>(J, D, m, p->col_ptr, p->row_idx, (const double*)p->val,
+                                                             p->y, p->z, p->w, p->bj, p->ib, p->loss, p->lambda,
+                                                             inv_n, steps);
+  else
+    k_improve_list<float><<<grid, kThreads, 0, p->stream>>>(J, D, m, p->col_ptr, p->row_idx, (const float*)p->val,
+                                                            p->y, p->z, p->w, p->bj, p->ib, p->loss, p->lambda, inv_n,
+                                                            steps);
+  p->prof.launches[K_UPDATE] += 1;
+  GENCD_CUDA_TRY(cudaGetLastError());
+  return GENCD_OK;
+}
+
 int launch_fill_u(gencd_problem* p) {
   if (p->n == 0) return GENCD_OK;
   const int grid = grid_for(p->n, kThreads, p->num_sms * 8);

@@ -381,6 +381,27 @@ def test_thread_greedy_backoff_converges_where_plain_thread_greedy_diverges(gb, 
     assert orc.kkt(w) <= 1e-7
 
 
+@pytest.mark.parametrize("variant,B,P", [("thread_greedy", 64, 0), ("greedy", 1, 0), ("shotgun", 0, 200)])
+def test_improve_steps_match_the_oracle(gb, variant, B, P):
+    # Improve delta_j (Algorithm 3, reading R11): every accepted increment
+    # refined on its own coordinate before the update
+    prob = workloads.config1("logistic")
+    orc = oracle.Oracle(prob)
+    lam = 0.05 * orc.lambda_max()
+    orc.set_lambda(lam)
+    iters = 15
+    w_plain, _, _, _ = orc.run(variant, iters, B=B or 1, P=P or 1, seed=4)
+    w_cpu, _, _, _ = orc.run(variant, iters, B=B or 1, P=P or 1, seed=4, improve_steps=500)
+    assert np.abs(w_cpu - w_plain).max() > 1e-6  # the step changes the trajectory
+    with gb.Problem(prob) as p:
+        p.set_lambda(lam)
+        p.set_params(variant=variant, blocks=B, P=P, seed=4, improve_steps=500)
+        p.iterate(iters)
+        w_gpu = p.w()
+    np.testing.assert_array_equal(w_gpu != 0, w_cpu != 0)
+    np.testing.assert_allclose(w_gpu, w_cpu, rtol=0, atol=1e-9)
+
+
 def test_set_loss_switches_the_problem(gb):
     # +-1 labels are valid for both losses: a problem switched to the squared
     # loss equals a problem created with it, in the same state, and back
