@@ -57,7 +57,10 @@ typedef enum {
   GENCD_SHOTGUN = 0,       /* Select: random subset of P columns; Accept: all   */
   GENCD_THREAD_GREEDY = 1, /* Select: all; Accept: best proxy per partition     */
   GENCD_GREEDY = 2,        /* Select: all; Accept: the single best proxy        */
-  GENCD_COLORING = 3       /* Select: random colour class; Accept: all          */
+  GENCD_COLORING = 3,      /* Select: random colour class; Accept: all          */
+  GENCD_TOP_GREEDY = 4     /* Select: all; Accept: the `blocks` lowest proxies
+                              of all columns, wherever they fall (Section 7's
+                              extension of Thread-Greedy)                       */
 } gencd_variant;
 
 /* Storage and arithmetic of the hot path.  F64: X, u and the sums in FP64.

@@ -29,13 +29,13 @@ GENCD_EDIVERGED = -5
 GENCD_ESTATE = -6
 
 GENCD_LOSS_SQUARED, GENCD_LOSS_LOGISTIC = 0, 1
-GENCD_SHOTGUN, GENCD_THREAD_GREEDY, GENCD_GREEDY, GENCD_COLORING = 0, 1, 2, 3
+GENCD_SHOTGUN, GENCD_THREAD_GREEDY, GENCD_GREEDY, GENCD_COLORING, GENCD_TOP_GREEDY = 0, 1, 2, 3, 4
 GENCD_F64, GENCD_F32, GENCD_BF16, GENCD_BINARY = 0, 1, 2, 3
 GENCD_HOST, GENCD_DEVICE = 0, 1
 
 LOSSES = {"squared": GENCD_LOSS_SQUARED, "logistic": GENCD_LOSS_LOGISTIC}
 VARIANTS = {"shotgun": GENCD_SHOTGUN, "thread_greedy": GENCD_THREAD_GREEDY, "greedy": GENCD_GREEDY,
-            "coloring": GENCD_COLORING}
+            "coloring": GENCD_COLORING, "top_greedy": GENCD_TOP_GREEDY}
 PRECISIONS = {"f64": GENCD_F64, "f32": GENCD_F32, "bf16": GENCD_BF16, "binary": GENCD_BINARY}
 KERNELS = ["propose_all", "finalize", "accept", "update", "refresh", "propose_list", "coloring_iter",
            "objective", "setup", "propose_light", "propose_slabs", "pairs_reduce"]

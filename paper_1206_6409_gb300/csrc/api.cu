@@ -244,6 +244,63 @@ static int ensure_selection(gencd_problem* p, int64_t epoch, int64_t m) {
   return GENCD_OK;
 }
 
+// Global top-|J'| Accept (Section 7): the B columns with the lowest proxies
+// below 0 (ties: the lower column).  Keys are the proxies' candidate
+// magnitudes, inverted so that ascending order is best first (non-candidates
+// last); two stable 32-bit radix passes (low half, then high half) order all
+// k columns by the 64-bit key with the column index breaking ties.
+__global__ void k_top_keys(const double* __restrict__ phi, int64_t k, uint32_t* __restrict__ hi,
+                           uint32_t* __restrict__ lo, uint32_t* __restrict__ idx) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) {
+    const uint64_t m = candidate_mag(phi[j]);
+    const uint64_t key = m ? ~m : ~0ull;
+    hi[j] = (uint32_t)(key >> 32);
+    lo[j] = (uint32_t)key;
+    idx[j] = (uint32_t)j;
+  }
+}
+
+__global__ void k_top_gather(const uint32_t* __restrict__ hi, const uint32_t* __restrict__ idx, int64_t k,
+                             uint32_t* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < k; e += stride) out[e] = hi[idx[e]];
+}
+
+__global__ void k_top_take(const uint32_t* __restrict__ order, const double* __restrict__ phi,
+                           const double* __restrict__ delta, int64_t B, int32_t* __restrict__ list_j,
+                           double* __restrict__ list_d) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < B; e += stride) {
+    const uint32_t j = order[e];
+    const bool ok = candidate_mag(phi[j]) != 0ull;
+    list_j[e] = ok ? (int32_t)j : -1;
+    list_d[e] = ok ? delta[j] : 0.0;
+  }
+}
+
+static int launch_top_accept(gencd_problem* p, int64_t B) {
+  const int64_t k = p->k;
+  if (!p->top_buf) GENCD_TRY(dalloc(&p->top_buf, 6 * (size_t)k));
+  uint32_t *lo = p->top_buf, *idx = lo + k, *lo_alt = lo + 2 * k, *idx_alt = lo + 3 * k, *hi = lo + 4 * k,
+           *hi_g = lo + 5 * k;
+  const int g = grid_for(k, kThreads, p->num_sms * 8);
+  k_top_keys<<<g, kThreads, 0, p->stream>>>(p->phi, k, hi, lo, idx);
+  GENCD_CUDA_TRY(cudaGetLastError());
+  bool alt1 = false, alt2 = false;
+  GENCD_TRY(radix_sort_pairs(p, lo, idx, k, 32, lo_alt, idx_alt, &alt1));  // by the low half
+  uint32_t* idx1 = alt1 ? idx_alt : idx;
+  k_top_gather<<<g, kThreads, 0, p->stream>>>(hi, idx1, k, hi_g);
+  uint32_t *free_k = alt1 ? lo : lo_alt, *free_v = alt1 ? idx : idx_alt;  // the pair the first pass left free
+  GENCD_TRY(radix_sort_pairs(p, hi_g, idx1, k, 32, free_k, free_v, &alt2));  // then by the high half, stably
+  const uint32_t* order = alt2 ? free_v : idx1;
+  k_top_take<<<grid_for(B, kThreads, p->num_sms * 8), kThreads, 0, p->stream>>>(order, p->phi, p->delta, B,
+                                                                                p->list_j, p->list_d);
+  p->prof.launches[K_ACCEPT] += 3;
+  GENCD_CUDA_TRY(cudaGetLastError());
+  return GENCD_OK;
+}
+
 // one GenCD iteration (Algorithm 1) of the configured variant, enqueued
 static int enqueue_iteration(gencd_problem* p, int64_t* host_nnz, bool want_kkt) {
   const int v = p->params.variant;
@@ -255,6 +312,17 @@ static int enqueue_iteration(gencd_problem* p, int64_t* host_nnz, bool want_kkt)
     GENCD_TRY(launch_merge_accept(p, B));               // accept backoff (groups of partitions), if any
     GENCD_TRY(launch_improve_list(p, p->list_j, p->list_d, B));  // Improve delta_j (Algorithm 3), if asked
     GENCD_TRY(launch_update_list(p, p->list_j, p->list_d, B, true));     // Update (atomic z)
+    GENCD_TRY(launch_refresh_list(p, p->list_j, p->list_d, B, true));
+    *host_nnz += p->nnz;
+    p->stat_host_nnz += p->nnz;
+  } else if (v == GENCD_TOP_GREEDY) {
+    const int B = effective_B(p);  // |J'|
+    GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal, 0, sizeof(double), p->stream));  // KKT maximum
+    GENCD_TRY(launch_propose_all(p, p->u, p->precision == GENCD_F64));  // Propose, all columns
+    GENCD_TRY(launch_finalize(p, p->lambda, true));    // delta, phi of every column (+ KKT of the start state)
+    GENCD_TRY(launch_top_accept(p, B));                 // Accept: the B lowest proxies
+    GENCD_TRY(launch_improve_list(p, p->list_j, p->list_d, B));
+    GENCD_TRY(launch_update_list(p, p->list_j, p->list_d, B, true));  // Update (atomic z)
     GENCD_TRY(launch_refresh_list(p, p->list_j, p->list_d, B, true));
     *host_nnz += p->nnz;
     p->stat_host_nnz += p->nnz;
@@ -339,7 +407,7 @@ static int compute_pstar(gencd_problem* p, int32_t* iters_out) {
 static void free_problem(gencd_problem* p) {
   if (!p) return;
   void* bufs[] = {p->col_ptr, p->row_idx, p->val, p->y, p->z, p->u, p->w, p->c, p->ib, p->tile_col, p->gacc,
-                  p->delta, p->phi, p->list_j, p->list_d, p->list_m, p->w_start, p->dscal, p->red, p->perm,
+                  p->delta, p->phi, p->list_j, p->list_d, p->list_m, p->w_start, p->top_buf, p->dscal, p->red, p->perm,
                   p->sort_tmp,
                   p->row_ptr, p->col_idx, p->csr_val, p->color, p->color_ptr, p->cols_by_color,
                   p->slot_m, p->slot_d, p->slot_j, p->list_off, p->scan_tmp, p->bj, p->w32, p->bj32, p->ib32,
@@ -637,7 +705,7 @@ int gencd_lambda_max(gencd_problem* p, double* lambda_max) {
 int gencd_set_params(gencd_problem* p, const gencd_params* a) {
   GENCD_CHECK_HANDLE(p);
   if (!a) return fail(GENCD_EINVAL, "params is NULL");
-  if (a->variant < 0 || a->variant > 3) return fail(GENCD_EINVAL, "unknown variant");
+  if (a->variant < 0 || a->variant > 4) return fail(GENCD_EINVAL, "unknown variant");
   if (a->blocks < 0 || a->P < 0 || a->max_iter < 0 || !(a->tol_kkt >= 0.0) || a->check_every < 1 ||
       (a->beta_mode != 0 && a->beta_mode != 1) || !(a->timeout_s >= 0.0) || a->improve_steps < 0 ||
       a->improve_steps > 100000)
@@ -723,13 +791,14 @@ int gencd_solve(gencd_problem* p, gencd_result* out) {
   // Thread-Greedy and Greedy compute the KKT violation of each iteration's
   // start state inside the iteration; their checks read it and only run a
   // full evaluation to confirm convergence.  Shotgun and Coloring evaluate.
-  const bool fused = a.variant == GENCD_THREAD_GREEDY || a.variant == GENCD_GREEDY;
+  const bool tg = a.variant == GENCD_THREAD_GREEDY || a.variant == GENCD_GREEDY;
+  const bool fused = tg || a.variant == GENCD_TOP_GREEDY;
   // Accept backoff (Thread-Greedy has no convergence guarantee): an
   // objective that is not finite or above its value at the start restarts
   // the solve from its start with 4x larger accept groups (of every G
   // partitions only the best proxy is applied; G = B is Greedy).
-  const int64_t B = fused ? effective_B(p) : 1;
-  const bool backoff = fused && B > 1;
+  const int64_t B = tg ? effective_B(p) : 1;
+  const bool backoff = tg && B > 1;
 
   if (backoff) {
     if (!p->w_start) GENCD_TRY(dalloc(&p->w_start, p->k));

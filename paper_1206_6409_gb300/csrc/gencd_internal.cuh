@@ -180,6 +180,7 @@ struct gencd_problem {
   // accepted / selected lists (capacity k)
   int32_t* list_j = nullptr;
   uint64_t* list_m = nullptr;   // candidate magnitude of each partition's accepted column (accept backoff)
+  uint32_t* top_buf = nullptr;  // global top-|J'| Accept: sort keys and indices (6 k words)
   double* w_start = nullptr;    // w at the start of a solve (restarts of the accept backoff)
   int64_t accept_group = 1;     // Thread-Greedy partitions merged per accept group (1: none)
   double* list_d = nullptr;

@@ -402,6 +402,26 @@ def test_improve_steps_match_the_oracle(gb, variant, B, P):
     np.testing.assert_allclose(w_gpu, w_cpu, rtol=0, atol=1e-9)
 
 
+@pytest.mark.parametrize("B", [17, 200])
+def test_top_greedy_iterations_match(gb, B):
+    # Section 7's global top-|J'| Accept (reading R12): the B lowest proxies
+    prob = workloads.config1("logistic")
+    orc = oracle.Oracle(prob)
+    lam = 0.05 * orc.lambda_max()
+    orc.set_lambda(lam)
+    iters = 15
+    w_cpu, _, _, st = orc.run("top_greedy", iters, B=B)
+    with gb.Problem(prob) as p:
+        p.set_lambda(lam)
+        p.set_params(variant="top_greedy", blocks=B)
+        p.stats_reset()
+        p.iterate(iters)
+        w_gpu = p.w()
+        assert p.stats().updates == st[0]
+    np.testing.assert_array_equal(w_gpu != 0, w_cpu != 0)
+    np.testing.assert_allclose(w_gpu, w_cpu, rtol=0, atol=1e-10)
+
+
 def test_set_loss_switches_the_problem(gb):
     # +-1 labels are valid for both losses: a problem switched to the squared
     # loss equals a problem created with it, in the same state, and back
