@@ -402,8 +402,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": "nnz processed/s", "value": value, "unit": "nnz/s", "n_gpus": world,
             "steps": steps, "warmup": warm, "ms_per_step": 1000.0 * el / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC + ("; binarized: every non-zero of column j is 1/sqrt(nnz_j)"
-                                                    if args.precision == "binary" else ""),
+            "config": {"workload": (WORKLOAD_DESC if args.scale >= 1.0 else f"scaled {args.scale}: {prob.name}")
+                       + ("; binarized: every non-zero of column j is 1/sqrt(nnz_j)"
+                          if args.precision == "binary" else ""),
                        "variant": "thread_greedy", "precision": args.precision, "oracle_arithmetic": "f64"},
             "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": "nnz/s",
                              "sample": "per step: " + sample},
