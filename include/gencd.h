@@ -164,13 +164,15 @@ int gencd_get_params(gencd_problem* p, gencd_params* params);
  * and Coloring make a full pass over X at each check).  Returns GENCD_OK,
  * GENCD_NOT_CONVERGED, GENCD_EDIVERGED (objective non-finite, or above 1e6
  * times its value at the start of the call) or an error.
- * Accept backoff (Thread-Greedy, B > 1; not in the paper, which gives
- * Thread-Greedy no convergence guarantee): when the objective is not finite
- * or above its value at the start of the call, the solve restarts from the w
- * it started with and keeps, of every G consecutive partitions, only the best
- * accepted proxy, G growing 4x per restart.  G = B is Greedy, whose steps
- * always lower the objective.  A solve that converges never restarts.  G
- * returns to 1 at gencd_set_params; gencd_iterate applies the current G.
+ * Accept backoff (Thread-Greedy and the global top-|J'| Accept with B > 1;
+ * not in the paper, which gives them no convergence guarantee): when the
+ * objective is not finite or above its value at the start of the call, the
+ * solve restarts from the w it started with and, G growing 4x per restart,
+ * Thread-Greedy keeps of every G consecutive partitions only the best
+ * accepted proxy while top-|J'| accepts the max(1, B/G) lowest proxies.
+ * G = B is Greedy, whose steps always lower the objective.  A solve that
+ * converges never restarts.  G returns to 1 at gencd_set_params;
+ * gencd_iterate applies the current G.
  * `out` (nullable) receives the statistics of the call.
  */
 int gencd_solve(gencd_problem* p, gencd_result* out);
@@ -281,12 +283,13 @@ int gencd_profile_reset(gencd_problem* p);
  * paper has no counterpart; this is a deployment entry point.
  *
  * It allocates nothing: no problem handle, no cudaMalloc/cudaFree, no
- * allocating library call.  Its scratch is a fixed device array of 8.5 MB
- * (every GPU that loads this library holds it until the process exits), which
+ * allocating library call.  Its scratch is a fixed device array of 9.44 MB
+ * (9,437,192 bytes; every GPU that loads this library holds it until the
+ * process exits), which
  * bounds the input: k <= 524,288 columns and nnz <= 33,554,432 non-zeros;
- * larger inputs return GENCD_EINVAL.  The first call on each device looks up
- * the scratch's device address (cudaGetSymbolAddress); make that first call
- * before capturing any stream.  All calls on a device share the scratch and
+ * larger inputs, a non-finite or negative lambda return GENCD_EINVAL.  The
+ * first call on each device looks up the scratch's device address
+ * (cudaGetSymbolAddress); make that first call before capturing any stream.  All calls on a device share the scratch and
  * each clears what it accumulates into, so calls that overlap on the GPU
  * (no stream ordering between them) race.
  *

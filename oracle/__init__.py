@@ -60,6 +60,8 @@ def lib():
             "oracle_objective_z": (C.c_double, [vp, _f64p, _f64p]),
             "oracle_kkt": (C.c_double, [vp, _f64p, _f64p]),
             "oracle_lambda_max": (C.c_double, [vp]),
+            "oracle_conjugate": (C.c_double, [C.c_int32, C.c_double, C.c_double]),
+            "oracle_duality_gap": (C.c_double, [vp, _f64p, _f64p]),
             "oracle_step": (None, [C.c_double, C.c_double, C.c_double, C.c_double, _f64p, _f64p]),
             "oracle_propose": (None, [vp, _f64p, _f64p, _i32p, C.c_int64, _f64p, _f64p]),
             "oracle_improve": (C.c_double, [vp, _f64p, _f64p, C.c_int64, C.c_double, C.c_int32]),
@@ -156,6 +158,12 @@ class Oracle:
     def lambda_max(self):
         return lib().oracle_lambda_max(self._ptr)
 
+    def duality_gap(self, w, z=None):
+        """P(w) - D(s u): an upper bound on P(w) - P* (Fenchel duality)."""
+        w = np.ascontiguousarray(w, np.float64)
+        z = self.fitted(w) if z is None else np.ascontiguousarray(z, np.float64)
+        return lib().oracle_duality_gap(self._ptr, _p(w, _f64p), _p(z, _f64p))
+
     def propose(self, w, z, J):
         w = np.ascontiguousarray(w, np.float64)
         z = np.ascontiguousarray(z, np.float64)
@@ -249,6 +257,11 @@ def dloss(loss_id, y, t):
     return lib().oracle_dloss(_LOSS[loss_id], y, t)
 
 
+def conjugate(loss_id, y, v):
+    """l*(y, v) = sup_t (v t - l(y, t))."""
+    return lib().oracle_conjugate(_LOSS[loss_id], y, v)
+
+
 def beta(loss_id):
     return lib().oracle_beta(_LOSS[loss_id])
 
@@ -300,6 +313,6 @@ def pstar(k, rho):
     return lib().oracle_pstar(k, rho)
 
 
-__all__ = ["Oracle", "loss", "dloss", "beta", "step", "splitmix64", "permutation", "pstar",
+__all__ = ["Oracle", "loss", "dloss", "conjugate", "beta", "step", "splitmix64", "permutation", "pstar",
            "stored_values", "stored_problem", "STORAGE",
            "SQUARED", "LOGISTIC"]

@@ -177,6 +177,34 @@ double oracle_lambda_max(const oracle_problem* pr) {
   return m;
 }
 
+/* ---- a certificate of P(w) - P*: the Fenchel duality gap of Eq. 1 -------- */
+
+/* l*(y, v) = sup_t (v t - l(y, t)).  Squared: the sup is at t = y + v.
+ * Logistic: with s = y t and p = -y v the sup of -p s - log(1 + e^-s) is at
+ * e^-s / (1 + e^-s) = p, which gives p log p + (1 - p) log(1 - p). */
+double oracle_conjugate(int32_t loss, double y, double v) {
+  if (loss == ORACLE_SQUARED) return v * y + 0.5 * v * v;
+  double p = -y * v;
+  if (p < 0.0 || p > 1.0) return HUGE_VAL;
+  double a = p > 0.0 ? p * log(p) : 0.0;
+  double b = p < 1.0 ? (1.0 - p) * log1p(-p) : 0.0;
+  return a + b;
+}
+
+double oracle_duality_gap(const oracle_problem* pr, const double* w, const double* z) {
+  double gmax = 0.0;
+  for (int64_t j = 0; j < pr->k; ++j) {
+    double g = fabs(column_gradient(pr, z, j));
+    if (g > gmax) gmax = g;
+  }
+  double s = gmax > pr->lambda ? pr->lambda / gmax : 1.0;
+  double dual = 0.0;
+  for (int64_t i = 0; i < pr->n; ++i)
+    dual -= oracle_conjugate(pr->loss, pr->y[i], s * oracle_dloss(pr->loss, pr->y[i], z[i]));
+  if (pr->n > 0) dual /= (double)pr->n;
+  return oracle_objective_z(pr, w, z) - dual;
+}
+
 /* ---- Section 3.2-3.3: the step of Eq. 7 and the proxy of Eq. 9 ---------- */
 
 /* |w + d| - |w| of Eq. 9.  When w + d keeps the sign of w the difference is

@@ -74,6 +74,19 @@ double oracle_kkt(const oracle_problem* pr, const double* w, const double* z);
 /* lambda_max = max_j |g_j(0)|: the smallest lambda with w = 0 optimal. */
 double oracle_lambda_max(const oracle_problem* pr);
 
+/* Convex conjugate of the loss in its second argument,
+ * l*(y, v) = sup_t (v t - l(y, t)):  squared  v y + v^2 / 2;  logistic
+ * p log p + (1 - p) log(1 - p) with p = -y v, finite for p in [0, 1]
+ * (0 log 0 = 0; HUGE_VAL outside). */
+double oracle_conjugate(int32_t loss, double y, double v);
+/* Duality gap of (w, z = Xw) for Eq. 1 (Fenchel duality; the paper states
+ * no stopping rule, this is a certificate of P(w) - P*):  P(w) - D(s u) with
+ * u = l'(y, z), g = X^T u / n, s = min(1, lambda / max_j |g_j|) (s = 1 when
+ * g = 0), D(nu) = -(1/n) sum_i l*(y_i, nu_i).  s u is dual feasible
+ * (||X^T s u|| / n <= lambda), so by weak duality the gap is >= P(w) - P*, and
+ * it is 0 at the optimum. */
+double oracle_duality_gap(const oracle_problem* pr, const double* w, const double* z);
+
 /* Eq. 7 step and Eq. 9 proxy for one coordinate. */
 void oracle_step(double g, double w_j, double lambda, double beta_j, double* delta, double* phi);
 /* Algorithm 4 over the columns J[0..m) at the state (w, z). */

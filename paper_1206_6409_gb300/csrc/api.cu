@@ -281,18 +281,21 @@ __global__ void k_top_take(const uint32_t* __restrict__ order, const double* __r
 
 static int launch_top_accept(gencd_problem* p, int64_t B) {
   const int64_t k = p->k;
-  if (!p->top_buf) GENCD_TRY(dalloc(&p->top_buf, 6 * (size_t)k));
+  // keys, indices, their alternates, the high halves and the radix scratch:
+  // sized once, so the Accept allocates nothing per iteration
+  if (!p->top_buf) GENCD_TRY(dalloc(&p->top_buf, 6 * (size_t)k + radix_tmp_words(k)));
   uint32_t *lo = p->top_buf, *idx = lo + k, *lo_alt = lo + 2 * k, *idx_alt = lo + 3 * k, *hi = lo + 4 * k,
-           *hi_g = lo + 5 * k;
+           *hi_g = lo + 5 * k, *rtmp = lo + 6 * k;
   const int g = grid_for(k, kThreads, p->num_sms * 8);
   k_top_keys<<<g, kThreads, 0, p->stream>>>(p->phi, k, hi, lo, idx);
   GENCD_CUDA_TRY(cudaGetLastError());
   bool alt1 = false, alt2 = false;
-  GENCD_TRY(radix_sort_pairs(p, lo, idx, k, 32, lo_alt, idx_alt, &alt1));  // by the low half
+  GENCD_TRY(radix_sort_with_tmp(p, lo, idx, k, 32, lo_alt, idx_alt, rtmp, &alt1));  // by the low half
   uint32_t* idx1 = alt1 ? idx_alt : idx;
   k_top_gather<<<g, kThreads, 0, p->stream>>>(hi, idx1, k, hi_g);
   uint32_t *free_k = alt1 ? lo : lo_alt, *free_v = alt1 ? idx : idx_alt;  // the pair the first pass left free
-  GENCD_TRY(radix_sort_pairs(p, hi_g, idx1, k, 32, free_k, free_v, &alt2));  // then by the high half, stably
+  GENCD_TRY(radix_sort_with_tmp(p, hi_g, idx1, k, 32, free_k, free_v, rtmp, &alt2));  // then by the high half,
+                                                                                   // stably
   const uint32_t* order = alt2 ? free_v : idx1;
   k_top_take<<<grid_for(B, kThreads, p->num_sms * 8), kThreads, 0, p->stream>>>(order, p->phi, p->delta, B,
                                                                                 p->list_j, p->list_d);
@@ -316,7 +319,8 @@ static int enqueue_iteration(gencd_problem* p, int64_t* host_nnz, bool want_kkt)
     *host_nnz += p->nnz;
     p->stat_host_nnz += p->nnz;
   } else if (v == GENCD_TOP_GREEDY) {
-    const int B = effective_B(p);  // |J'|
+    // |J'|; the accept backoff of a solve divides it by the accept group
+    const int64_t B = std::max<int64_t>(1, effective_B(p) / p->accept_group);
     GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal, 0, sizeof(double), p->stream));  // KKT maximum
     GENCD_TRY(launch_propose_all(p, p->u, p->precision == GENCD_F64));  // Propose, all columns
     GENCD_TRY(launch_finalize(p, p->lambda, true));    // delta, phi of every column (+ KKT of the start state)
@@ -792,13 +796,15 @@ int gencd_solve(gencd_problem* p, gencd_result* out) {
   // start state inside the iteration; their checks read it and only run a
   // full evaluation to confirm convergence.  Shotgun and Coloring evaluate.
   const bool tg = a.variant == GENCD_THREAD_GREEDY || a.variant == GENCD_GREEDY;
-  const bool fused = tg || a.variant == GENCD_TOP_GREEDY;
-  // Accept backoff (Thread-Greedy has no convergence guarantee): an
-  // objective that is not finite or above its value at the start restarts
-  // the solve from its start with 4x larger accept groups (of every G
-  // partitions only the best proxy is applied; G = B is Greedy).
-  const int64_t B = tg ? effective_B(p) : 1;
-  const bool backoff = tg && B > 1;
+  const bool top = a.variant == GENCD_TOP_GREEDY;
+  const bool fused = tg || top;
+  // Accept backoff (neither Thread-Greedy nor the global top-|J'| Accept has
+  // a convergence guarantee): an objective that is not finite or above its
+  // value at the start restarts the solve from its start with 4x larger
+  // accept groups.  Thread-Greedy applies only the best proxy of every G
+  // partitions; top-|J'| accepts the |J'|/G lowest proxies.  G = B is Greedy.
+  const int64_t B = fused ? effective_B(p) : 1;
+  const bool backoff = fused && B > 1;
 
   if (backoff) {
     if (!p->w_start) GENCD_TRY(dalloc(&p->w_start, p->k));

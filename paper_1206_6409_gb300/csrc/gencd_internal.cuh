@@ -286,8 +286,6 @@ int launch_csr_spmv(gencd_problem* p, const double* x, double* out);  // out = X
 // kernels_setup.cu
 int launch_col_scale(gencd_problem* p);
 int launch_tile_map(gencd_problem* p);
-int radix_sort_pairs(gencd_problem* p, uint32_t* keys, uint32_t* vals, int64_t m, int bits,
-                     uint32_t* keys_alt, uint32_t* vals_alt, bool* result_in_alt);
 int make_permutation(gencd_problem* p, uint64_t seed, int64_t epoch, int64_t m, int32_t* out);
 int build_csr(gencd_problem* p);
 int run_coloring(gencd_problem* p);

@@ -261,7 +261,7 @@ size_t radix_tmp_words(int64_t m) {
 
 // Sorts (keys, vals) by the low `bits` bits of the keys, stably.  Ping-pongs
 // with (keys_alt, vals_alt); *result_in_alt tells where the result is.
-// Needs radix_tmp_words(m) words at the start of p->sort_tmp... provided by caller
+// Needs radix_tmp_words(m) words of scratch at tmp (provided by the caller).
 int radix_sort_with_tmp(gencd_problem* p, uint32_t* keys, uint32_t* vals, int64_t m, int bits,
                         uint32_t* keys_alt, uint32_t* vals_alt, uint32_t* tmp, bool* result_in_alt) {
   *result_in_alt = false;
@@ -285,17 +285,6 @@ int radix_sort_with_tmp(gencd_problem* p, uint32_t* keys, uint32_t* vals, int64_
   }
   *result_in_alt = alt;
   return GENCD_OK;
-}
-
-int radix_sort_pairs(gencd_problem* p, uint32_t* keys, uint32_t* vals, int64_t m, int bits,
-                     uint32_t* keys_alt, uint32_t* vals_alt, bool* result_in_alt) {
-  // the caller's four arrays must not overlap p->sort_tmp
-  uint32_t* tmp = nullptr;
-  const size_t words = radix_tmp_words(m);
-  GENCD_CUDA_TRY(cudaMallocAsync((void**)&tmp, words * 4, p->stream));
-  int rc = radix_sort_with_tmp(p, keys, vals, m, bits, keys_alt, vals_alt, tmp, result_in_alt);
-  cudaFreeAsync(tmp, p->stream);
-  return rc;
 }
 
 // ---------------------------------------------------------------------------

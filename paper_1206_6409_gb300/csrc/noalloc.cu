@@ -29,7 +29,8 @@ constexpr int64_t kNoAllocMaxNnz = int64_t(1) << 25;   // non-zeros
 constexpr int64_t kNoAllocMaxTiles = kNoAllocMaxNnz / kNoAllocTile;
 
 // layout: [0, K) column sums X_j^T u, [K, 2K) sums of X_ij^2, then the tile map
-// (int32, max tiles + 1 entries); 2 K + (max tiles + 2) / 2 doubles = 8.5 MB
+// (int32, max tiles + 1 entries); 2 K + (max tiles + 2) / 2 = 1,179,649 doubles
+// = 9,437,192 bytes (9.44 MB, 9.0 MiB)
 static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocMaxCols + (kNoAllocMaxTiles + 2) / 2];
 
 __global__ void k_na_clear(double* __restrict__ sums, int64_t k, double* __restrict__ kkt) {
@@ -165,7 +166,8 @@ extern "C" int gencd_propose_all_noalloc(int64_t n, int64_t k, int64_t nnz, cons
   if (!col_ptr || !y || !z || !w || !delta || !phi || !kkt || (nnz > 0 && (!row_idx || !val)))
     return fail_plan("a required pointer is NULL");
   if (loss != GENCD_LOSS_SQUARED && loss != GENCD_LOSS_LOGISTIC) return fail_plan("unknown loss");
-  if (!(lambda >= 0.0) || (beta_mode != 0 && beta_mode != 1)) return fail_plan("bad lambda or beta_mode");
+  if (!(lambda >= 0.0) || !std::isfinite(lambda) || (beta_mode != 0 && beta_mode != 1))
+    return fail_plan("lambda must be finite and >= 0, beta_mode 0 or 1");
   double* scratch = nullptr;
   GENCD_TRY(noalloc_scratch(&scratch));
   double* sums = scratch;

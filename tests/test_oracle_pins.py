@@ -790,3 +790,85 @@ def test_block_shotgun_converges_on_orthogonal_blocks():
     w, _, _, kkt, _ = o.solve("shotgun_blocks", tol_kkt=1e-10, B=B, block_P=Pb, seed=1, max_iter=10**6)
     assert kkt <= 1e-10
     assert o.objective(w) == pytest.approx(o.objective(w_ref), rel=1e-9)
+
+
+# --- the duality gap: a certificate of P(w) - P* (the paper has no stopping rule) ----
+
+def _golden_max(f, lo, hi, iters=300):
+    """Maximiser of a concave function on [lo, hi] by golden-section search."""
+    r = (np.sqrt(5.0) - 1.0) / 2.0
+    a, b = lo, hi
+    c, d = b - r * (b - a), a + r * (b - a)
+    fc, fd = f(c), f(d)
+    for _ in range(iters):
+        if fc > fd:
+            b, d, fd = d, c, fc
+            c = b - r * (b - a)
+            fc = f(c)
+        else:
+            a, c, fc = c, d, fd
+            d = a + r * (b - a)
+            fd = f(d)
+    return 0.5 * (a + b)
+
+
+@pytest.mark.parametrize("loss", ["squared", "logistic"])
+def test_conjugate_is_the_sup_over_t(loss):
+    # l*(y, v) = sup_t (v t - l(y, t)): the supremum found by search on the
+    # concave function of t, for labels and dual values across the domain
+    rng = np.random.default_rng(3)
+    for _ in range(300):
+        if loss == "logistic":
+            y = float(rng.choice([-1.0, 1.0]))
+            v = -y * float(rng.uniform(1e-3, 1.0 - 1e-3))
+        else:
+            y, v = float(rng.normal(0, 2)), float(rng.normal(0, 2))
+        f = lambda t: v * t - oracle.loss(loss, y, t)
+        t_star = _golden_max(f, -60.0, 60.0)
+        assert oracle.conjugate(loss, y, v) == pytest.approx(f(t_star), abs=1e-12)
+    if loss == "logistic":  # the ends of the domain, and outside it
+        assert oracle.conjugate(loss, 1.0, 0.0) == 0.0 and oracle.conjugate(loss, 1.0, -1.0) == 0.0
+        assert oracle.conjugate(loss, 1.0, 0.5) == float("inf")
+        assert oracle.conjugate(loss, -1.0, -0.1) == float("inf")
+
+
+@pytest.mark.parametrize("loss", ["squared", "logistic"])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_duality_gap_bounds_the_suboptimality(loss, seed):
+    # weak duality: gap(w) >= P(w) - P* for every w, with P* from brute force;
+    # and the gap closes at the optimum
+    p = workloads.tiny_problem(8, 4, loss=loss, seed=seed)
+    X = p.to_dense()
+    o = oracle.Oracle(p)
+    lam = 0.2 * o.lambda_max()
+    o.set_lambda(lam)
+    Pbf, wbf = _brute_force(X, p.y, loss, lam)
+    rng = np.random.default_rng(seed + 10)
+    gaps = []
+    for scale in (1e-4, 1e-2, 0.3, 3.0):
+        for _ in range(25):
+            w = wbf + rng.normal(0, scale, 4) * (rng.random(4) < 0.7)
+            gap = o.duality_gap(w)
+            sub = _dense_objective(X, p.y, loss, lam, w) - Pbf
+            assert gap >= sub - 1e-13, (gap, sub)
+            gaps.append(gap)
+    assert min(gaps) >= -1e-13
+    w, _, _, kkt, _ = o.solve("ccd", tol_kkt=1e-13, max_iter=10**7)
+    assert o.duality_gap(w) <= 1e-12
+
+
+@pytest.mark.parametrize("loss", ["squared", "logistic"])
+def test_duality_gap_closes_along_cyclic_cd(loss):
+    # a sparse problem with k > n: the gap is non-negative along the solve and
+    # shrinks with the KKT violation
+    p = workloads.uniform_problem(200, 300, 6, values="lognormal", loss=loss, n_planted=10, seed=4)
+    o = oracle.Oracle(p)
+    o.set_lambda(0.1 * o.lambda_max())
+    last = np.inf
+    for tol in (1e-3, 1e-6, 1e-9, 1e-12):
+        w, _, _, kkt, _ = o.solve("ccd", tol_kkt=tol, max_iter=10**8)
+        gap = o.duality_gap(w)
+        assert 0.0 <= gap <= last + 1e-15
+        last = gap
+    # at KKT violation eps the dual scaling moves D by about eps ||w||_1
+    assert last <= 4e-12 * (1.0 + np.abs(w).sum())

@@ -80,3 +80,30 @@ def test_lambda_grid_is_log_spaced():
     g = workloads.lambda_grid(2.0, 32, 1e-3)
     assert g.size == 32 and g[0] == 2.0 and abs(g[-1] - 2e-3) < 1e-15
     np.testing.assert_allclose(g[1:] / g[:-1], (1e-3) ** (1 / 31))
+
+
+def test_generators_draw_no_repeated_row_sets():
+    # duplicate columns would make the l1 minimiser non-unique: every
+    # generator redraws a column whose row set repeats a lower-index column's
+    dup = workloads.synthetic._duplicate_columns
+    cp = np.array([0, 1, 3, 4, 6, 9, 10], np.int64)
+    ri = np.array([5, 1, 2, 5, 1, 2, 0, 1, 2, 7], np.int32)
+    assert dup(10, cp, ri).tolist() == [2, 3]  # planted repeats of columns 0 and 1
+    for p in (workloads.config1(), workloads.config3("ones"), workloads.config2_scaled(0.002),
+              workloads.uniform_problem(50, 40, 1, values="ones", n_planted=5, seed=3),
+              workloads.zipf_problem(5000, 2000, 6000, cap=100, n_planted=5, seed=2)):
+        _check_csc(p)
+        assert dup(p.n, p.col_ptr, p.row_idx).size == 0, p.name
+    # 40 one-entry columns in 50 rows: the first draw repeats rows, the redraws do not
+    p = workloads.uniform_problem(50, 40, 1, values="ones", n_planted=5, seed=3)
+    assert np.unique(p.row_idx).size == 40
+    with pytest.raises(ValueError):
+        workloads.uniform_problem(10, 11, 1, values="ones", n_planted=2, seed=0)
+
+
+def test_no_redraw_leaves_the_first_draw():
+    # without repeated row sets the generator's bytes are those of the plain draw
+    counts = np.full(300, 20, np.int64)
+    a = workloads.synthetic._distinct_rows(2000, counts, workloads.synthetic._rng(5))
+    b = workloads.synthetic._distinct_columns(2000, counts, workloads.synthetic._rng(5))
+    np.testing.assert_array_equal(a, b)

@@ -92,6 +92,61 @@ def _distinct_rows(n: int, counts: np.ndarray, rng: np.random.Generator) -> np.n
     return (key - col * n).astype(np.int32)
 
 
+def _row_set_hash(col_ptr: np.ndarray, row_idx: np.ndarray) -> np.ndarray:
+    """A 64-bit fingerprint of each column's row set (equal sets, equal
+    fingerprints), from a SplitMix64-style mix of every row summed per column."""
+    with np.errstate(over="ignore"):
+        x = row_idx.astype(np.uint64) + np.uint64(0x9E3779B97F4A7C15)
+        x = (x ^ (x >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        x = (x ^ (x >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        x = x ^ (x >> np.uint64(31))
+    counts = np.diff(col_ptr)
+    h = np.zeros(counts.size, np.uint64)
+    nz = counts > 0
+    if nz.any():
+        h[nz] = np.add.reduceat(x, col_ptr[:-1][nz])
+    return h
+
+
+def _duplicate_columns(n: int, col_ptr: np.ndarray, row_idx: np.ndarray) -> np.ndarray:
+    """Columns whose row set equals that of a lower-index column (ascending)."""
+    counts = np.diff(col_ptr)
+    h = _row_set_hash(col_ptr, row_idx)
+    order = np.lexsort((np.arange(counts.size), h, counts))
+    key_c, key_h = counts[order], h[order]
+    starts = np.flatnonzero(np.r_[True, (key_c[1:] != key_c[:-1]) | (key_h[1:] != key_h[:-1])])
+    ends = np.r_[starts[1:], order.size]
+    dups = []
+    for a, b in zip(starts[ends - starts > 1], ends[ends - starts > 1]):
+        group = order[a:b]  # equal fingerprints, ascending column index
+        rows = [row_idx[col_ptr[j]:col_ptr[j + 1]] for j in group]
+        for q in range(1, len(group)):
+            if any(np.array_equal(rows[q], rows[r]) for r in range(q)):
+                dups.append(group[q])
+    return np.sort(np.asarray(dups, np.int64))
+
+
+def _distinct_columns(n: int, counts: np.ndarray, rng: np.random.Generator) -> np.ndarray:
+    """Rows of every column as _distinct_rows draws them, then the rows of each
+    column whose row set repeats a lower-index column's are drawn again, until
+    no two columns share a row set.  Duplicate columns would make the l1
+    minimiser non-unique (weight can move freely between them), so the
+    generators never produce them.  When no column repeats, no extra draw is
+    made: the arrays are those of _distinct_rows."""
+    counts = np.asarray(counts, np.int64)
+    col_ptr = _col_ptr(counts)
+    row_idx = _distinct_rows(n, counts, rng)
+    for _ in range(1000):
+        dup = _duplicate_columns(n, col_ptr, row_idx)
+        if dup.size == 0:
+            return row_idx
+        fresh = _distinct_rows(n, counts[dup], rng)
+        fp = _col_ptr(counts[dup])
+        for q, j in enumerate(dup):
+            row_idx[col_ptr[j]:col_ptr[j + 1]] = fresh[fp[q]:fp[q + 1]]
+    raise ValueError("cannot draw columns with distinct row sets (too many short columns for n rows)")
+
+
 def _col_ptr(counts: np.ndarray) -> np.ndarray:
     cp = np.zeros(len(counts) + 1, np.int64)
     np.cumsum(counts, out=cp[1:])
@@ -125,14 +180,15 @@ def uniform_problem(n, k, nnz_per_col, *, values="pm1", n_planted=50, loss=LOGIS
                     noise_sd=None, seed=0, name="") -> Problem:
     """Every column holds ``nnz_per_col`` distinct rows drawn uniformly.
 
-    Draw order: rows, values, planted support, planted weights, label noise.
+    Draw order: rows (with redraws of repeated row sets, see
+    _distinct_columns), values, planted support, planted weights, label noise.
     ``values``: "pm1" (+-1 at p=1/2), "ones" (binary, DOROTHEA-like) or
     "lognormal" (LogNormal(0,1) then unit-norm columns, tf-idf-like).
     """
     rng = _rng(seed)
     counts = np.full(k, nnz_per_col, np.int64)
     col_ptr = _col_ptr(counts)
-    row_idx = _distinct_rows(n, counts, rng)
+    row_idx = _distinct_columns(n, counts, rng)
     nnz = int(col_ptr[-1])
     if values == "pm1":
         val = np.where(rng.random(nnz) < 0.5, -1.0, 1.0)
@@ -186,7 +242,8 @@ def zipf_problem(n, k, nnz_total, *, s=1.1, cap=50_000, n_planted=2000, loss=LOG
     """Zipf(s) column lengths assigned to columns by a seeded permutation, rows
     uniform without replacement, LogNormal(0,1) values, unit-norm columns.
 
-    Draw order: rank-to-column permutation, rows, values, planted support,
+    Draw order: rank-to-column permutation, rows (with redraws of repeated
+    row sets, see _distinct_columns), values, planted support,
     planted weights, label noise.  Labels: y = sign(Xw* + eps) with
     eps ~ N(0, (0.1 rms(Xw*))^2) (logistic), y = Xw* + eps (squared).
     """
@@ -196,7 +253,7 @@ def zipf_problem(n, k, nnz_total, *, s=1.1, cap=50_000, n_planted=2000, loss=LOG
     counts = np.empty(k, np.int64)
     counts[perm] = by_rank
     col_ptr = _col_ptr(counts)
-    row_idx = _distinct_rows(n, counts, rng)
+    row_idx = _distinct_columns(n, counts, rng)
     val = _normalise_columns(col_ptr, rng.lognormal(0.0, 1.0, int(col_ptr[-1])))
     w_star = np.zeros(k)
     support = rng.choice(k, size=min(n_planted, k), replace=False)
