@@ -7,6 +7,7 @@ import pytest
 
 import oracle
 import workloads
+from parity_tools import assert_support_matches
 
 pytestmark = pytest.mark.gpu
 
@@ -44,6 +45,10 @@ def test_serve_results_are_the_same_alone_and_in_the_mix(gb, stream):
         assert a["lambda_"] == pytest.approx(b["lambda_"], rel=1e-6)
         assert a["objective"] == pytest.approx(b["objective"], rel=1e-7), q
         assert a["end"] >= a["start"] >= a["arrival"] - 1e-6
+        # the same support alone and in the mix, outside the columns fragile at
+        # the two points' KKT accuracy (FP64 atomics add in arrival order)
+        assert_support_matches(oracle.stored_problem(problems[q], "f32"), b["lambda_"], w_mix[q], w_alone[q],
+                               label=f"request {q} alone / mix")
     # the smaller requests against the oracle on the same problem
     order = np.argsort([p.nnz for p in problems])[:4]
     for q in order:
@@ -54,6 +59,8 @@ def test_serve_results_are_the_same_alone_and_in_the_mix(gb, stream):
         w_opt, _, _, _, _ = orc.solve("ccd", tol_kkt=1e-11)
         assert mix[q]["objective"] == pytest.approx(orc.objective(w_opt), rel=1e-6), q
         assert orc.kkt(w_mix[q]) <= 5e-8
+        assert_support_matches(oracle.stored_problem(p, "f32"), mix[q]["lambda_"], w_mix[q], w_opt,
+                               label=f"request {q}")
 
 
 def test_serve_admits_by_the_hbm_budget(gb, stream):
