@@ -64,7 +64,11 @@ def parse():
     ap.add_argument("--blocks", type=int, default=1024)
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the full workload (tests)")
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--legs", type=int, default=1,
+                    help="also time config 2 in the other storage modes and variants, and config 1 (0/1)")
+    ap.add_argument("--leg-steps", type=int, default=30, help="timed iterations of each config-2 leg")
+    ap.add_argument("--ref-seconds", type=float, default=90.0,
+                    help="time limit of the FP64 reference solve that gives P* for the time-to-1e-6 run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--target-check", type=int, default=10,
                     help="iterations between objective checks of the time-to-1e-6 run (0: skip it)")
@@ -99,6 +103,47 @@ def load_problem(scale, precision="f32"):
 
 # bytes of one stored value of X per storage mode
 VALUE_BYTES = {"f64": 8, "f32": 4, "bf16": 2, "binary": 0}
+
+
+def stored_values_host(val, precision):
+    """The values of X as the storage mode holds them, as float64 (numpy /
+    PyTorch CPU conversions: FP32 round to nearest even, then bfloat16 round
+    to nearest even).  Used to give the FP64 reference solve the same X as the
+    timed run."""
+    if precision == "f64":
+        return np.asarray(val, np.float64)
+    v32 = np.asarray(val, np.float32)
+    if precision == "bf16":
+        import torch
+
+        return torch.from_numpy(v32).to(torch.bfloat16).to(torch.float64).numpy()
+    return v32.astype(np.float64)
+
+
+def host_info():
+    """Host cores and CPU model of the machine the CPU baseline runs on."""
+    info = {"nproc": os.cpu_count(), "affinity": len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity")
+            else os.cpu_count(), "machine": os.uname().machine, "cpu_model": None}
+    try:
+        import subprocess
+
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        fields = {line.split(":", 1)[0].strip(): line.split(":", 1)[1].strip()
+                  for line in out.splitlines() if ":" in line}
+        info["cpu_model"] = fields.get("Model name") or fields.get("Vendor ID")
+        if fields.get("Vendor ID") and fields.get("Model name"):
+            info["cpu_model"] = fields["Vendor ID"] + " " + fields["Model name"]
+    except (OSError, ValueError):
+        pass
+    if info["cpu_model"] is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    info["cpu_model"] = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return info
 
 
 def measured_peak():
@@ -208,34 +253,51 @@ def dist_setup(args):
     return world, rank, local
 
 
-def cpu_oracle_rate(prob, lam, seconds, blocks):
-    """The FP64 oracle (single thread, as it stands) running Thread-Greedy
-    iterations on a column slice of the workload for about `seconds`."""
+def cpu_omp_rate(sp, lam, blocks, iters, threads, orc=None):
+    """Thread-Greedy iterations (B partitions) of the OpenMP baseline
+    (Section 4.2's design, FP64) from w = 0 on the full stored workload `sp`
+    with `threads` threads; returns (nnz/s, seconds, iterations)."""
     import oracle
 
-    # contiguous slice of the first columns holding ~2e7 non-zeros
-    kk = int(np.searchsorted(prob.col_ptr, 20_000_000))
-    kk = max(1, min(kk, prob.k))
-    sub = workloads.Problem(prob.n, kk, prob.col_ptr[:kk + 1].copy(), prob.row_idx[:prob.col_ptr[kk]],
-                            prob.val[:prob.col_ptr[kk]], prob.y, prob.loss, prob.w_star[:kk], "slice")
-    orc = oracle.Oracle(sub, lam)
-    B = max(1, int(round(blocks * kk / prob.k)))
-    w = np.zeros(kk)
-    z = np.zeros(prob.n)
+    orc = orc or oracle.Oracle(sp, lam)
+    s = oracle.OmpSolver(orc, threads=threads)
     t0 = time.perf_counter()
-    nnz = 0
-    iters = 0
-    while True:
-        w, z, _, st = orc.run("thread_greedy", 1, w=w, z=z, t0=iters, B=B)
-        nnz += int(st[1])
-        iters += 1
-        el = time.perf_counter() - t0
-        if el >= seconds:
-            break
-    return nnz / el, {"kind": "oracle", "cores": 1, "value": nnz / el, "unit": "nnz/s",
-                      "sample": f"{iters} Thread-Greedy iterations (B={B}) of the FP64 oracle on the first "
-                                f"{kk} columns ({int(sub.col_ptr[-1])} nnz) of the workload, "
-                                f"{el:.1f} s on 1 host core"}
+    _, nnz, it = s.iterate(iters, B=blocks)
+    el = time.perf_counter() - t0
+    s.close()
+    return nnz / el, el, it
+
+
+def cpu_baseline_leg(sp, lam, blocks, w_ref):
+    """The CPU baseline (rank 0, one GPU): the OpenMP baseline timed on the
+    host's cores, at 1 thread and at all of them, on the whole workload; and
+    the oracle's FP64 certificate (KKT violation, duality gap) of the
+    reference point the time-to-1e-6 run measured against."""
+    import oracle
+
+    info = host_info()
+    orc = oracle.Oracle(sp, lam)
+    out = {"kind": "oracle", "impl": "OpenMP Thread-Greedy (Section 4.2: static schedule, atomic z), FP64",
+           "unit": "nnz/s", "same_config": True, **info}
+    try:
+        threads = oracle.omp_lib().omp_solver_max_threads()
+        r1, el1, it1 = cpu_omp_rate(sp, lam, blocks, 2, 1, orc)
+        rT, elT, itT = cpu_omp_rate(sp, lam, blocks, 6, threads, orc)
+        out.update({"value": rT, "cores": int(threads), "value_1_thread": r1,
+                    "sample": f"{itT} Thread-Greedy iterations (B={blocks}) of the whole workload from w = 0 "
+                              f"on {threads} threads in {elT:.1f} s; {it1} on 1 thread in {el1:.1f} s"})
+    except Exception as e:  # noqa: BLE001 -- e.g. no OpenMP on the host
+        out.update({"value": None, "cores": None, "unavailable": f"{type(e).__name__}: {e}"})
+    cert = None
+    if w_ref is not None:
+        t0 = time.perf_counter()
+        z = orc.fitted(w_ref)
+        P = orc.objective(w_ref, z)
+        kkt = orc.kkt(w_ref, z)
+        gap = orc.duality_gap(w_ref, z)
+        cert = {"objective": P, "kkt": kkt, "kkt_over_lambda": kkt / lam, "duality_gap": gap,
+                "rel_gap": gap / P, "seconds": time.perf_counter() - t0}
+    return out, cert
 
 
 PATH_FOLDS, PATH_LAMBDAS = 5, 32
@@ -373,43 +435,230 @@ def run_batch_step(args):
 
 
 def run_reference(args):
+    """The reference arm: the paper's method has no runnable implementation,
+    so the OpenMP baseline (Section 4.2's design, FP64) runs the workload on
+    the host's cores: one step = one Thread-Greedy iteration over the whole
+    workload (stored values of the storage mode), continuing from the last."""
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return
     prob = load_problem(args.scale, args.precision)
     import oracle
 
-    if args.precision != "f64":  # the oracle runs on the values the storage mode holds
-        prob = oracle.stored_problem(prob, args.precision)
-
-    orc_full = oracle.Oracle(prob)
-    lam = 0.05 * orc_full.lambda_max()
-    steps, warm = args.steps, args.warmup
-    # each step: a bounded sample of oracle work on a column slice, sized so
-    # that the whole run stays within about three minutes
-    per_step = min(1.0, max(0.05, 150.0 / max(1, steps + warm)))
-    for _ in range(warm):
-        cpu_oracle_rate(prob, lam, per_step * 0.25, args.blocks)
-    rates = []
-    sample = None
+    sp = oracle.stored_problem(prob, args.precision) if args.precision != "f64" else prob
+    orc = oracle.Oracle(sp)
+    lam = 0.05 * orc.lambda_max()
+    orc.set_lambda(lam)
+    info = host_info()
+    s = oracle.OmpSolver(orc)
+    s.iterate(args.warmup, B=args.blocks)
     t0 = time.perf_counter()
-    for _ in range(steps):
-        r, info = cpu_oracle_rate(prob, lam, per_step, args.blocks)
-        rates.append(r)
-        sample = info["sample"]
+    _, nnz, _ = s.iterate(args.steps, B=args.blocks)
     el = time.perf_counter() - t0
-    value = statistics.mean(rates)
+    s.close()
+    value = nnz / el
     line = {"impl": "reference", "metric": "nnz processed/s", "value": value, "unit": "nnz/s", "n_gpus": world,
-            "steps": steps, "warmup": warm, "ms_per_step": 1000.0 * el / steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": (WORKLOAD_DESC if args.scale >= 1.0 else f"scaled {args.scale}: {prob.name}")
                        + ("; binarized: every non-zero of column j is 1/sqrt(nnz_j)"
                           if args.precision == "binary" else ""),
-                       "variant": "thread_greedy", "precision": args.precision, "oracle_arithmetic": "f64"},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": "nnz/s",
-                             "sample": "per step: " + sample},
+                       "variant": "thread_greedy", "blocks": args.blocks, "precision": args.precision,
+                       "oracle_arithmetic": "f64"},
+            "cpu_baseline": {"kind": "oracle", "impl": "OpenMP Thread-Greedy (Section 4.2: static schedule, "
+                                                       "atomic z), FP64", "cores": s.threads, "value": value,
+                             "unit": "nnz/s", "same_config": True, **info,
+                             "sample": f"{args.steps} Thread-Greedy iterations (B={args.blocks}) of the whole "
+                                       f"workload after {args.warmup} warm-up iterations, {el:.1f} s on "
+                                       f"{s.threads} threads"},
             "e2e": {"value": value, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _event_ms(fn, stream):
+    """Device time (ms) of the work fn enqueues on `stream` (CUDA events)."""
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def time_to_target(args, gb, prob, val, lam, stream):
+    """Time to a 1e-6 relative objective gap from w = 0 (reading 10).
+
+    P* comes from a reference solve of the same problem (the stored values of
+    the storage mode) in FP64 arithmetic: Thread-Greedy with the accept
+    backoff, to KKT <= 1e-6 lambda or --ref-seconds.  The CPU-baseline leg
+    certifies that point with the oracle (KKT violation and duality gap in
+    FP64).  The timed run is the benchmark's own configuration from w = 0, with
+    an objective check every --target-check iterations inside the clock."""
+    import torch
+
+    ref_val = stored_values_host(val, args.precision)
+    q = gb.Problem(n=prob.n, k=prob.k, col_ptr=prob.col_ptr, row_idx=prob.row_idx, val=ref_val, y=prob.y,
+                   loss="logistic", precision="f64", stream=stream.cuda_stream)
+    q.set_lambda(lam)
+    q.set_params(variant="thread_greedy", blocks=args.blocks, seed=0, tol_kkt=1e-6 * lam, max_iter=10_000_000,
+                 check_every=20, timeout_s=args.ref_seconds)
+    r = q.solve()
+    w_ref = q.w()
+    p_star, ref_kkt = q.objective()
+    q.close()
+    ref = {"objective": p_star, "kkt": ref_kkt, "kkt_over_lambda": ref_kkt / lam, "status": int(r.status),
+           "iterations": int(r.iters), "seconds": r.seconds,
+           "w_sha256": hashlib.sha256(np.ascontiguousarray(w_ref).tobytes()).hexdigest()[:16],
+           "w_nonzeros": int(np.count_nonzero(w_ref)),
+           "how": "FP64 Thread-Greedy (B=%d, accept backoff) on the stored values to KKT <= 1e-6 lambda or %g s"
+                  % (args.blocks, args.ref_seconds)}
+    p = gb.Problem(n=prob.n, k=prob.k, col_ptr=prob.col_ptr, row_idx=prob.row_idx, val=val, y=prob.y,
+                   loss="logistic", precision=args.precision, stream=stream.cuda_stream)
+    p.set_lambda(lam)
+    p.set_params(variant=args.variant, blocks=args.blocks, seed=0)
+    p.stats_reset()
+    torch.cuda.synchronize()
+    target = p_star * (1.0 + 1e-6)
+    t0 = time.perf_counter()
+    iters, reached, obj = 0, False, None
+    while iters < args.target_max_iter and time.perf_counter() - t0 < 60.0:
+        p.iterate(args.target_check, sync=False)
+        iters += args.target_check
+        obj, _ = p.objective()
+        if obj <= target:
+            reached = True
+            break
+    el = time.perf_counter() - t0
+    st = p.stats()
+    p.close()
+    out = {"seconds": el if reached else None, "iterations": iters, "reached": reached, "rel_gap": 1e-6,
+           "objective": obj, "rel_gap_at_end": (obj - p_star) / p_star if obj is not None else None,
+           "check_every": args.target_check, "updates": int(st.updates),
+           "updates_per_s": st.updates / el if el > 0 else None, "p_star": p_star, "reference": ref}
+    return out, w_ref
+
+
+def _step_leg(gb, prob, val, precision, lam, stream, steps, variant="thread_greedy", blocks=1024, warm=3,
+              extra=None):
+    """Times `steps` iterations of one configuration on config 2 (CUDA events
+    on the library's stream, after `warm` untimed ones)."""
+    p = gb.Problem(n=prob.n, k=prob.k, col_ptr=prob.col_ptr, row_idx=prob.row_idx, val=val, y=prob.y,
+                   loss="logistic", precision=precision, stream=stream.cuda_stream)
+    try:
+        p.set_lambda(lam)
+        out = {}
+        if extra:
+            out.update(extra(p))
+        p.set_params(variant=variant, blocks=blocks, seed=0)
+        p.iterate(warm, sync=False)
+        gb.gencd_profile_reset(p.h)
+        p.stats_reset()
+        gb.gencd_profile_enable(p.h, True)
+        ms = _event_ms(lambda: p.iterate(steps, sync=False), stream)
+        st = p.stats()
+        prof = {name: gb.gencd_profile_read(p.h, name) for name in gb.KERNELS}
+        gb.gencd_profile_enable(p.h, False)
+        out.update({"ms_per_step": ms / steps, "us_per_iteration": 1000.0 * ms / steps,
+                    "nnz_per_s": st.nnz_processed / (ms / 1000.0), "updates_per_s": st.updates / (ms / 1000.0),
+                    "updates_per_step": st.updates / steps, "steps": steps,
+                    "kernel_ms_per_call": {k: v[0] / v[2] for k, v in prof.items() if v[2]}})
+        return out, prof
+    finally:
+        p.close()
+
+
+def leg_storage_modes(args, gb, prob, stream):
+    """Config 2, one Thread-Greedy step in the storage modes the headline does
+    not run: ms/step, nnz/s and the streaming propose's roofline fraction."""
+    out = {}
+    peak, _ = measured_peak()
+    for mode in ("f32", "f64", "bf16", "binary"):
+        if mode == args.precision:
+            continue
+        src = workloads.binarized(prob) if mode == "binary" else prob
+        val = src.val if mode == "f64" else src.val.astype(np.float32)
+        try:
+            lm_probe = gb.Problem(n=src.n, k=src.k, col_ptr=src.col_ptr, row_idx=src.row_idx, val=val, y=src.y,
+                                  loss="logistic", precision=mode, stream=stream.cuda_stream)
+            lam = 0.05 * lm_probe.lambda_max()
+            lm_probe.close()
+            r, prof = _step_leg(gb, src, val, mode, lam, stream, args.leg_steps, blocks=args.blocks)
+            sv = VALUE_BYTES[mode]
+            byts = src.nnz * (4 + sv) + 8 * (src.k + 1) + 8 * src.k + (4 * src.k if sv == 0 else 0)
+            pa_ms, _, pa_n = prof["propose_all"]
+            if pa_n:
+                r["roofline"] = {"achieved_gbs": byts / (pa_ms / pa_n / 1000.0) / 1e9,
+                                 "frac": byts / (pa_ms / pa_n / 1000.0) / 1e9 / peak,
+                                 "algorithmic_bytes_per_launch": byts, "launch_ms": pa_ms / pa_n}
+            out[mode] = r
+        except Exception as e:  # noqa: BLE001 -- reported, the headline still prints
+            out[mode] = {"error": f"{type(e).__name__}: {e}"}
+    return out
+
+
+def leg_variants(args, gb, prob, val, lam, stream):
+    """Config 2 in the benchmark's storage mode with the other variants of
+    Table 2: Coloring (one colour class per iteration, after the distance-2
+    colouring) and Shotgun (P* columns per iteration, after the power
+    iteration): time per iteration, nnz/s, updates/s and the one-time cost."""
+    import torch
+
+    out = {}
+
+    def colouring(p):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nc = p.color()
+        torch.cuda.synchronize()
+        return {"setup_s": time.perf_counter() - t0, "ncolors": int(nc)}
+
+    def pstar(p):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rho, ps, it = p.spectral_radius()
+        torch.cuda.synchronize()
+        return {"setup_s": time.perf_counter() - t0, "rho": rho, "P_star": int(ps), "power_iterations": int(it)}
+
+    for name, variant, extra, steps in (("coloring", "coloring", colouring, 200), ("shotgun", "shotgun", pstar, 200)):
+        try:
+            out[name], _ = _step_leg(gb, prob, val, args.precision, lam, stream, steps, variant=variant,
+                                     extra=extra)
+        except Exception as e:  # noqa: BLE001
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+    return out
+
+
+def leg_config1(args, gb, stream):
+    """Config 1 (n = 2,000, k = 5,000, +-1 values, FP64), both losses,
+    lambda = 0.01 lambda_max: Shotgun at P* and Coloring solved from w = 0 to
+    KKT <= 1e-9 (latency: wall time, iterations, us per iteration, nnz/s)."""
+    out = {}
+    for loss in ("logistic", "squared"):
+        prob = workloads.config1(loss)
+        for variant in ("shotgun", "coloring"):
+            try:
+                with gb.Problem(prob, precision="f64", stream=stream.cuda_stream) as p:
+                    p.set_lambda(0.01 * p.lambda_max())
+                    if variant == "shotgun":
+                        p.spectral_radius()
+                    else:
+                        p.color()
+                    p.set_params(variant=variant, tol_kkt=1e-9, max_iter=5_000_000, check_every=200, seed=0)
+                    p.solve()  # warm-up (kernel loading), then the same solve from w = 0
+                    p.set_w(np.zeros(prob.k))
+                    p.set_iteration(0)
+                    r = p.solve()
+                out[f"{variant}_{loss}"] = {"status": int(r.status), "seconds": r.seconds, "iterations": int(r.iters),
+                                            "us_per_iteration": 1e6 * r.seconds / max(1, r.iters),
+                                            "nnz_per_s": r.nnz_processed / r.seconds if r.seconds > 0 else None,
+                                            "updates_per_s": r.updates / r.seconds if r.seconds > 0 else None,
+                                            "objective": r.objective, "kkt": r.kkt}
+            except Exception as e:  # noqa: BLE001
+                out[f"{variant}_{loss}"] = {"error": f"{type(e).__name__}: {e}"}
+    return out
 
 
 def run_gencd(args):
@@ -513,28 +762,16 @@ def run_gencd(args):
         e2e["value"] = nnz_sum / t_max
 
     # ---- time to a 1e-6 relative objective gap from w = 0 -------------------
-    # P* is the objective the timed run converged to (its KKT is printed with
-    # it); the clock covers the iterations and the objective checks.
-    ttt = None
+    ttt, w_ref = None, None
     if args.target_check > 0:
-        q = gb.Problem(n=prob.n, k=prob.k, col_ptr=prob.col_ptr, row_idx=prob.row_idx, val=val, y=prob.y,
-                       loss="logistic", precision=args.precision, stream=stream.cuda_stream)
-        q.set_lambda(lam)
-        q.set_params(variant=args.variant, blocks=args.blocks, seed=0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        iters, reached = 0, False
-        while iters < args.target_max_iter:
-            q.iterate(args.target_check, sync=False)
-            iters += args.target_check
-            obj, _ = q.objective()
-            if obj <= final_obj * (1.0 + 1e-6):
-                reached = True
-                break
-        t_target = time.perf_counter() - t0
-        q.close()
-        ttt = {"seconds": t_target if reached else None, "iterations": iters, "reached": reached,
-               "p_star": final_obj, "check_every": args.target_check, "rel_gap": 1e-6}
+        ttt, w_ref = time_to_target(args, gb, prob, val, lam, stream)
+
+    # ---- the other storage modes and variants of config 2, config 1 --------
+    legs = {}
+    if args.legs:
+        legs["storage_modes"] = leg_storage_modes(args, gb, prob, stream)
+        legs["variants"] = leg_variants(args, gb, prob, val, lam, stream)
+        legs["config1"] = leg_config1(args, gb, stream)
 
     path = None
     if args.path:
@@ -552,7 +789,12 @@ def run_gencd(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        _, cpu = cpu_oracle_rate(prob, lam, args.cpu_seconds, args.blocks)
+        import oracle
+
+        sp = prob if args.precision == "f64" else oracle.stored_problem(prob, args.precision)
+        cpu, cert = cpu_baseline_leg(sp, lam, args.blocks, w_ref)
+        if ttt is not None:
+            ttt["p_star_certificate"] = cert
 
     if rank == 0:
         line = {
@@ -579,6 +821,7 @@ def run_gencd(args):
             "updates_per_step": st.updates / args.steps,
             "updates_per_s": st.updates / (ms / 1000.0),
             "time_to_1e-6": ttt,
+            "legs": legs,
             "objective": final_obj, "kkt": final_kkt, "w_nonzeros": w_nonzeros,
             "clocks": clk,
             "e2e": e2e,

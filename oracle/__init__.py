@@ -299,6 +299,62 @@ def stored_problem(prob, mode):
     return dataclasses.replace(prob, val=stored_values(prob, mode))
 
 
+_omp_lib = None
+
+
+def omp_lib():
+    """The OpenMP baseline library (Section 4.2's design), built on first use."""
+    global _omp_lib
+    if _omp_lib is None:
+        L = C.CDLL(_build.build_omp())
+        vp = C.c_void_p
+        L.omp_solver_max_threads.restype = C.c_int32
+        L.omp_solver_create.restype = vp
+        L.omp_solver_create.argtypes = [vp, _f64p, _f64p, C.c_int32]
+        L.omp_solver_iterate.restype = C.c_int
+        L.omp_solver_iterate.argtypes = [vp, C.c_int32, C.c_int32, C.c_int64, _i64p]
+        L.omp_solver_get.restype = None
+        L.omp_solver_get.argtypes = [vp, _f64p, _f64p]
+        L.omp_solver_destroy.restype = None
+        L.omp_solver_destroy.argtypes = [vp]
+        _omp_lib = L
+    return _omp_lib
+
+
+class OmpSolver:
+    """Thread-Greedy / Greedy with OpenMP (static schedule, atomic z, critical
+    section for Greedy) on an Oracle's problem, from (w, z = Xw)."""
+
+    def __init__(self, orc: Oracle, w=None, threads=0):
+        self.orc = orc  # keeps the problem arrays alive
+        w = np.zeros(orc.k) if w is None else np.ascontiguousarray(w, np.float64)
+        z = orc.fitted(w)
+        self.threads = int(threads) if threads > 0 else int(omp_lib().omp_solver_max_threads())
+        self.h = omp_lib().omp_solver_create(orc._ptr, _p(w, _f64p), _p(z, _f64p), self.threads)
+        if not self.h:
+            raise MemoryError("omp_solver_create failed")
+
+    def iterate(self, iters, B=1024, greedy=False):
+        """Runs iterations; returns (updates, nnz processed, iterations)."""
+        st = np.zeros(3, np.int64)
+        if omp_lib().omp_solver_iterate(self.h, int(B), int(bool(greedy)), int(iters), _p(st, _i64p)) != 0:
+            raise ValueError("omp_solver_iterate rejected its parameters")
+        return tuple(int(x) for x in st)
+
+    def state(self):
+        w, z = np.empty(self.orc.k), np.empty(self.orc.n)
+        omp_lib().omp_solver_get(self.h, _p(w, _f64p), _p(z, _f64p))
+        return w, z
+
+    def close(self):
+        if getattr(self, "h", None):
+            omp_lib().omp_solver_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
 def splitmix64(s, i):
     return lib().oracle_splitmix64(s & ((1 << 64) - 1), i)
 
@@ -313,6 +369,6 @@ def pstar(k, rho):
     return lib().oracle_pstar(k, rho)
 
 
-__all__ = ["Oracle", "loss", "dloss", "conjugate", "beta", "step", "splitmix64", "permutation", "pstar",
+__all__ = ["Oracle", "OmpSolver", "loss", "dloss", "conjugate", "beta", "step", "splitmix64", "permutation", "pstar",
            "stored_values", "stored_problem", "STORAGE",
            "SQUARED", "LOGISTIC"]
