@@ -683,6 +683,10 @@ def run_gencd(args):
     lam = 0.05 * p.lambda_max()
     p.set_lambda(lam)
     p.set_params(variant=args.variant, blocks=args.blocks, seed=0)
+    split, tuned = gb.gencd_propose_schedule(p.h)
+    schedule = {"fused_split": split, "candidates_ms": tuned,
+                "form": "separate light and slab kernels" if split == 0 else
+                f"one kernel, {split} of 32 warps per SM start on the row slabs"}
     for _ in range(args.warmup):
         p.iterate(1, sync=False)
     torch.cuda.synchronize()
@@ -809,12 +813,14 @@ def run_gencd(args):
                        "nnz": prob.nnz, "n": prob.n, "k": prob.k,
                        "l2": "inputs larger than L2: each step streams all of X (%.2f GB)" % (bytes_per_launch / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": {"bound": "hbm", "kernel": "streaming propose (k_propose_light_runs + k_propose_slabs + "
-                                                  "k_pairs_to_gacc)", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "hbm", "kernel": "streaming propose (k_propose_fused or k_propose_light_runs + "
+                                                  "k_propose_slabs, then k_pairs_to_gacc)", "achieved": achieved,
+                         "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / peak if achieved else None, "traffic": traffic,
                          "algorithmic_bytes_per_launch": bytes_per_launch,
                          "launch_ms": pa_ms / pa_n if pa_n else None, "source_sha256": src_hash},
+            "propose_schedule": schedule,
             "kernel_ms_per_call": {k: v[0] / v[2] for k, v in prof.items() if v[2]},
             "kernel_launches": {k: v[1] for k, v in prof.items() if v[1]},
             "gpu_launches": launches,

@@ -58,9 +58,15 @@ typedef enum {
   GENCD_THREAD_GREEDY = 1, /* Select: all; Accept: best proxy per partition     */
   GENCD_GREEDY = 2,        /* Select: all; Accept: the single best proxy        */
   GENCD_COLORING = 3,      /* Select: random colour class; Accept: all          */
-  GENCD_TOP_GREEDY = 4     /* Select: all; Accept: the `blocks` lowest proxies
+  GENCD_TOP_GREEDY = 4,    /* Select: all; Accept: the `blocks` lowest proxies
                               of all columns, wherever they fall (Section 7's
                               extension of Thread-Greedy)                       */
+  GENCD_SHOTGUN_BLOCKS = 5 /* Section 7's block Shotgun: `blocks` contiguous
+                              column blocks (0 => 16, at most 1024), each with
+                              its own P*_b (gencd_block_pstar); Select: the
+                              next P*_b columns of every block's per-epoch
+                              permutation (block b's stream seeded with
+                              seed + b); Accept: all                            */
 } gencd_variant;
 
 /* Storage and arithmetic of the hot path.  F64: X, u and the sums in FP64.
@@ -230,6 +236,14 @@ int gencd_propose_all(gencd_problem* p, double* delta, double* phi, int32_t memo
  * P* = max(1, floor(k / (2 rho))) (Section 4.1). */
 int gencd_spectral_radius(gencd_problem* p, double* rho, int64_t* pstar, int32_t* iters);
 
+/* Block Shotgun's subset sizes (Section 7): for the B contiguous column
+ * blocks [floor(b k / B), floor((b+1) k / B)), rho_b is the spectral radius
+ * of the block's D^-1/2 X_b^T X_b D^-1/2 (power iteration as
+ * gencd_spectral_radius, from the block's all-ones vector) and
+ * P*_b = max(1, floor(k_b / (2 rho_b))).  pstar int64[B] and rho double[B]
+ * (nullable) are host buffers; 1 <= B <= min(k, 1024). */
+int gencd_block_pstar(gencd_problem* p, int32_t B, int64_t* pstar, double* rho);
+
 /*
  * Partial distance-2 colouring of the columns (Section 4.1: columns that
  * share a row get different colours), computed on the GPU.  The result equals
@@ -265,14 +279,27 @@ int gencd_permutation(gencd_problem* p, uint64_t seed, int64_t epoch, int64_t m,
 
 /* Kernel launch counts and, when profiling is enabled, summed device time
  * (ms, CUDA events on the problem's stream) and number of timed invocations
- * per kernel family: 0 streaming propose (the whole family 9 + 10 + 11),
- * 1 finalize, 2 accept, 3 update, 4 refresh, 5 list propose, 6 Coloring
- * iteration, 7 objective, 8 setup/selection, 9 light-column pass, 10 row-slab
- * pass, 11 partial-sum reduction.  ms / calls is the mean duration of one
+ * per kernel family: 0 streaming propose (the whole family 9 + 10 + 11, or
+ * 12 + 11), 1 finalize, 2 accept, 3 update, 4 refresh, 5 list propose,
+ * 6 Coloring iteration, 7 objective, 8 setup/selection, 9 light-column pass,
+ * 10 row-slab pass, 11 partial-sum reduction, 12 row-slab and light-column
+ * passes in one kernel.  ms / calls is the mean duration of one
  * invocation; ms, launches, calls may be NULL. */
 int gencd_profile_enable(gencd_problem* p, int32_t enable);
 int gencd_profile_read(gencd_problem* p, int32_t kernel, double* ms, int64_t* launches, int64_t* calls);
 int gencd_profile_reset(gencd_problem* p);
+
+/*
+ * Schedule of the streaming propose over all columns, chosen at create by the
+ * library's autotuner (not in the paper): the row-slab pass over the heavy
+ * columns and the light-column pass run as two kernels (*split = 0) or as one
+ * kernel whose first *split of 32 warps per SM start on the row slabs and the
+ * rest on a shared pool of light tiles.  ms[0..nms) receives the autotuner's
+ * mean time per invocation (ms) of the two kernels, then of the splits 16,
+ * 20, 24 and 28 (-1 where a form was not timed: FP64 arithmetic, or no light
+ * or no heavy columns).  split and ms may be NULL.
+ */
+int gencd_propose_schedule(gencd_problem* p, int32_t* split, double* ms, int32_t nms);
 
 /*
  * gencd_propose_all_noalloc -- the streaming Propose over all k columns

@@ -29,16 +29,17 @@ GENCD_EDIVERGED = -5
 GENCD_ESTATE = -6
 
 GENCD_LOSS_SQUARED, GENCD_LOSS_LOGISTIC = 0, 1
-GENCD_SHOTGUN, GENCD_THREAD_GREEDY, GENCD_GREEDY, GENCD_COLORING, GENCD_TOP_GREEDY = 0, 1, 2, 3, 4
+GENCD_SHOTGUN, GENCD_THREAD_GREEDY, GENCD_GREEDY, GENCD_COLORING, GENCD_TOP_GREEDY, GENCD_SHOTGUN_BLOCKS = \
+    0, 1, 2, 3, 4, 5
 GENCD_F64, GENCD_F32, GENCD_BF16, GENCD_BINARY = 0, 1, 2, 3
 GENCD_HOST, GENCD_DEVICE = 0, 1
 
 LOSSES = {"squared": GENCD_LOSS_SQUARED, "logistic": GENCD_LOSS_LOGISTIC}
 VARIANTS = {"shotgun": GENCD_SHOTGUN, "thread_greedy": GENCD_THREAD_GREEDY, "greedy": GENCD_GREEDY,
-            "coloring": GENCD_COLORING, "top_greedy": GENCD_TOP_GREEDY}
+            "coloring": GENCD_COLORING, "top_greedy": GENCD_TOP_GREEDY, "shotgun_blocks": GENCD_SHOTGUN_BLOCKS}
 PRECISIONS = {"f64": GENCD_F64, "f32": GENCD_F32, "bf16": GENCD_BF16, "binary": GENCD_BINARY}
 KERNELS = ["propose_all", "finalize", "accept", "update", "refresh", "propose_list", "coloring_iter",
-           "objective", "setup", "propose_light", "propose_slabs", "pairs_reduce"]
+           "objective", "setup", "propose_light", "propose_slabs", "pairs_reduce", "propose_fused"]
 
 # every symbol include/gencd.h declares
 EXPORTS = ["gencd_create", "gencd_destroy", "gencd_set_lambda", "gencd_set_loss", "gencd_lambda_max",
@@ -48,6 +49,7 @@ EXPORTS = ["gencd_create", "gencd_destroy", "gencd_set_lambda", "gencd_set_loss"
            "gencd_spectral_radius", "gencd_color", "gencd_color_balanced_csc", "gencd_get_colors", "gencd_set_colors",
            "gencd_permutation", "gencd_profile_enable", "gencd_profile_read", "gencd_profile_reset",
            "gencd_last_error", "gencd_stats", "gencd_stats_reset", "gencd_propose_all_noalloc",
+           "gencd_propose_schedule", "gencd_block_pstar",
            # include/gencd_batch.h
            "gencd_batch_create", "gencd_batch_destroy", "gencd_batch_slots", "gencd_batch_lambda_max",
            "gencd_batch_set_params", "gencd_batch_set_slot", "gencd_batch_copy_slot", "gencd_batch_clear_slot",
@@ -141,6 +143,7 @@ def lib():
             "gencd_propose_all": (C.c_int, [vp, vp, vp, i32, C.POINTER(f64)]),
             "gencd_spectral_radius": (C.c_int, [vp, C.POINTER(f64), C.POINTER(i64), C.POINTER(i32)]),
             "gencd_color": (C.c_int, [vp, C.POINTER(i32)]),
+            "gencd_block_pstar": (C.c_int, [vp, i32, vp, vp]),
             "gencd_color_balanced_csc": (C.c_int, [i64, i64, vp, vp, i64, vp, C.POINTER(i32)]),
             "gencd_get_colors": (C.c_int, [vp, vp, i64, i32]),
             "gencd_set_colors": (C.c_int, [vp, vp, i64, i32]),
@@ -148,6 +151,7 @@ def lib():
             "gencd_profile_enable": (C.c_int, [vp, i32]),
             "gencd_profile_read": (C.c_int, [vp, i32, C.POINTER(f64), C.POINTER(i64), C.POINTER(i64)]),
             "gencd_profile_reset": (C.c_int, [vp]),
+            "gencd_propose_schedule": (C.c_int, [vp, C.POINTER(i32), C.POINTER(f64), i32]),
             "gencd_last_error": (C.c_char_p, []),
             "gencd_stats": (C.c_int, [vp, C.POINTER(gencd_result)]),
             "gencd_stats_reset": (C.c_int, [vp]),
@@ -405,6 +409,24 @@ def gencd_profile_enable(h, enable=True):
     _check(lib().gencd_profile_enable(h, 1 if enable else 0))
 
 
+def gencd_block_pstar(h, B):
+    """(P*_b int64[B], rho_b float64[B]) of block Shotgun's B column blocks."""
+    P = np.zeros(int(B), np.int64)
+    rho = np.zeros(int(B), np.float64)
+    _check(lib().gencd_block_pstar(h, int(B), P.ctypes.data_as(C.c_void_p), rho.ctypes.data_as(C.c_void_p)))
+    return P, rho
+
+
+def gencd_propose_schedule(h):
+    """(split, {form: mean ms}) of the streaming propose's autotuner: split 0
+    is the two separate kernels, else the fused kernel's slab warps."""
+    split = C.c_int32()
+    ms = (C.c_double * 5)()
+    _check(lib().gencd_propose_schedule(h, C.byref(split), ms, 5))
+    forms = ["separate", "fused16", "fused20", "fused24", "fused28"]
+    return int(split.value), {f: float(v) for f, v in zip(forms, ms) if v >= 0}
+
+
 def gencd_profile_read(h, kernel):
     """(summed ms, kernel launches, timed invocations) of a kernel family."""
     kid = KERNELS.index(kernel) if isinstance(kernel, str) else int(kernel)
@@ -508,6 +530,9 @@ class Problem:
 
     def color(self):
         return gencd_color(self.h)
+
+    def block_pstar(self, B):
+        return gencd_block_pstar(self.h, B)
 
     def colors(self):
         return gencd_get_colors(self.h, self.k)

@@ -101,26 +101,29 @@ int launch_inv_beta(gencd_problem* p) {
   return GENCD_OK;
 }
 
-__global__ void k_dinv(const double* __restrict__ c, int64_t k, double n, double* __restrict__ dinv,
-                       double* __restrict__ v) {
+// D^-1/2 and the start vector of the power iteration on the columns
+// [lo, hi): v_j = 1 / sqrt(hi - lo) there, 0 elsewhere
+__global__ void k_dinv(const double* __restrict__ c, int64_t k, double n, int64_t lo, int64_t hi,
+                       double* __restrict__ dinv, double* __restrict__ v) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const double v0 = 1.0 / sqrt((double)k);
+  const double v0 = 1.0 / sqrt((double)(hi - lo));
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) {
     const double s = c[j] * n;  // ||X_j||^2
     dinv[j] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
-    v[j] = v0;
+    v[j] = (j >= lo && j < hi) ? v0 : 0.0;
   }
 }
 
-// t_j = dinv_j * gacc_j (gacc reset to 0); red[block] = sum of t_j^2
+// t_j = dinv_j * gacc_j on the columns [lo, hi), 0 elsewhere (gacc reset to
+// 0); red[block] = sum of t_j^2
 __global__ void __launch_bounds__(kThreads)
-    k_power_finish(double* __restrict__ gacc, const double* __restrict__ dinv, int64_t k,
+    k_power_finish(double* __restrict__ gacc, const double* __restrict__ dinv, int64_t k, int64_t lo, int64_t hi,
                    double* __restrict__ t, double* __restrict__ red) {
   __shared__ double sm[kThreads / 32];
   double s = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += stride) {
-    const double x = dinv[j] * gacc[j];
+    const double x = (j >= lo && j < hi) ? dinv[j] * gacc[j] : 0.0;
     gacc[j] = 0.0;
     t[j] = x;
     s = fma(x, x, s);
@@ -235,6 +238,9 @@ static int read_scalars(gencd_problem* p) {
 }
 
 static int compute_pstar(gencd_problem* p, int32_t* iters_out);
+static int compute_block_pstar(gencd_problem* p, int32_t B);
+__global__ void k_block_select(int64_t t, int32_t B, const int64_t* __restrict__ blo, const int64_t* __restrict__ bP,
+                               const int32_t* __restrict__ perm, int32_t* __restrict__ J);
 
 static int ensure_selection(gencd_problem* p, int64_t epoch, int64_t m) {
   if (p->perm_epoch == epoch && p->perm_m == m) return GENCD_OK;
@@ -343,6 +349,29 @@ static int enqueue_iteration(gencd_problem* p, int64_t* host_nnz, bool want_kkt)
     GENCD_TRY(launch_improve_list(p, J, p->list_d, m));                  // Improve delta_j, if asked
     GENCD_TRY(launch_update_list(p, J, p->list_d, m, false));            // Accept all, Update
     GENCD_TRY(launch_refresh_list(p, J, p->list_d, m, false));
+  } else if (v == GENCD_SHOTGUN_BLOCKS) {
+    const int32_t B = (int32_t)std::min<int64_t>(p->params.blocks > 0 ? p->params.blocks : 16, p->k);
+    GENCD_TRY(compute_block_pstar(p, B));
+    int64_t m = 0;
+    for (int32_t b = 0; b < B; ++b) {  // Select: each block's next P*_b columns (block b's stream: seed + b)
+      const int64_t lo = p->hblock_lo[b], kb = p->hblock_lo[b + 1] - lo;
+      if (kb == 0) continue;
+      const int64_t P = std::min<int64_t>(std::max<int64_t>(p->hblock_P[b], 1), kb);
+      const int64_t per_epoch = (kb + P - 1) / P, e = p->t / per_epoch, q = p->t % per_epoch;
+      if (p->hblock_epoch[b] != e) {
+        GENCD_TRY(make_permutation(p, p->params.seed + (uint64_t)b, e, kb, p->perm + lo));
+        p->hblock_epoch[b] = e;
+      }
+      m += std::min<int64_t>(P, kb - q * P);
+    }
+    p->perm_epoch = -1;  // perm now holds the blocks' permutations
+    k_block_select<<<1, kThreads, 0, p->stream>>>(p->t, B, p->block_lo, p->block_P, p->perm, p->list_j);
+    p->prof.launches[K_SETUP] += 1;
+    GENCD_CUDA_TRY(cudaGetLastError());
+    GENCD_TRY(launch_propose_list(p, p->list_j, m, p->list_d, p->phi));  // Propose (Jacobi)
+    GENCD_TRY(launch_improve_list(p, p->list_j, p->list_d, m));         // Improve delta_j, if asked
+    GENCD_TRY(launch_update_list(p, p->list_j, p->list_d, m, false));   // Accept all, Update
+    GENCD_TRY(launch_refresh_list(p, p->list_j, p->list_d, m, false));
   } else if (v == GENCD_COLORING) {
     if (!p->color) GENCD_TRY(run_coloring(p));
     const int64_t C = p->ncolors;
@@ -357,7 +386,11 @@ static int enqueue_iteration(gencd_problem* p, int64_t* host_nnz, bool want_kkt)
   return GENCD_OK;
 }
 
-static int compute_pstar(gencd_problem* p, int32_t* iters_out) {
+// Spectral radius of D^-1/2 X_b^T X_b D^-1/2 for the columns b = [lo, hi)
+// (all columns: Shotgun's rho; one block: block Shotgun's rho_b) by power
+// iteration from the block's all-ones vector, at most 100 iterations or a
+// relative change below 1e-6 (Section 4.1)
+static int power_radius(gencd_problem* p, int64_t lo, int64_t hi, double* rho_out, int32_t* iters_out) {
   GENCD_TRY(build_csr(p));
   const int64_t k = p->k;
   double *dinv = nullptr, *v = nullptr, *s = nullptr, *t = nullptr, *r = nullptr;
@@ -372,13 +405,13 @@ static int compute_pstar(gencd_problem* p, int32_t* iters_out) {
     return rc;
   }
   const int g = p->num_sms * 8;
-  k_dinv<<<grid_for(k, kThreads, g), kThreads, 0, p->stream>>>(p->c, k, (double)p->n, dinv, v);
+  k_dinv<<<grid_for(k, kThreads, g), kThreads, 0, p->stream>>>(p->c, k, (double)p->n, lo, hi, dinv, v);
   double rho = 0.0;
   int it = 0;
   const int nb = grid_for(k, kThreads, kRedBlocks);
   for (it = 1; it <= 100 && rc == GENCD_OK; ++it) {
     if ((rc = launch_power_step(p, v, dinv, r, s)) != GENCD_OK) break;
-    k_power_finish<<<nb, kThreads, 0, p->stream>>>(p->gacc, dinv, k, t, p->red);
+    k_power_finish<<<nb, kThreads, 0, p->stream>>>(p->gacc, dinv, k, lo, hi, t, p->red);
     k_sum_partials<<<1, 32, 0, p->stream>>>(p->red, nb, p->dscal + 6);
     p->prof.launches[K_SETUP] += 2;
     if ((rc = read_scalars(p)) != GENCD_OK) break;
@@ -399,13 +432,89 @@ static int compute_pstar(gencd_problem* p, int32_t* iters_out) {
   cudaFree(t);
   cudaFree(r);
   if (rc != GENCD_OK) return rc;
-  p->rho = rho;
-  double ps = rho > 0.0 ? std::floor((double)k / (2.0 * rho)) : (double)k;
-  if (ps < 1.0) ps = 1.0;
-  if (ps > (double)k) ps = (double)k;
-  p->pstar = (int64_t)ps;
+  *rho_out = rho;
   if (iters_out) *iters_out = it;
   return GENCD_OK;
+}
+
+// P* = max(1, floor(m / (2 rho))), at most m (Section 4.1)
+static int64_t pstar_of(int64_t m, double rho) {
+  double ps = rho > 0.0 ? std::floor((double)m / (2.0 * rho)) : (double)m;
+  if (ps < 1.0) ps = 1.0;
+  if (ps > (double)m) ps = (double)m;
+  return (int64_t)ps;
+}
+
+static int compute_pstar(gencd_problem* p, int32_t* iters_out) {
+  double rho = 0.0;
+  GENCD_TRY(power_radius(p, 0, p->k, &rho, iters_out));
+  p->rho = rho;
+  p->pstar = pstar_of(p->k, rho);
+  return GENCD_OK;
+}
+
+// Block Shotgun (Section 7): B contiguous column blocks [floor(b k / B),
+// floor((b+1) k / B)) and each block's P*_b from its own spectral radius
+static int compute_block_pstar(gencd_problem* p, int32_t B) {
+  if (p->block_B == B && !p->hblock_P.empty()) return GENCD_OK;
+  std::vector<int64_t> lo(B + 1), P(B);
+  std::vector<double> rho(B);
+  for (int32_t b = 0; b <= B; ++b) lo[b] = p->k * b / B;
+  for (int32_t b = 0; b < B; ++b) {
+    rho[b] = 0.0;
+    if (lo[b + 1] > lo[b]) GENCD_TRY(power_radius(p, lo[b], lo[b + 1], &rho[b], nullptr));
+    P[b] = lo[b + 1] > lo[b] ? pstar_of(lo[b + 1] - lo[b], rho[b]) : 0;
+  }
+  cudaFree(p->block_lo);
+  cudaFree(p->block_P);
+  p->block_lo = nullptr;
+  p->block_P = nullptr;
+  p->block_B = 0;
+  GENCD_TRY(dalloc(&p->block_lo, B + 1));
+  GENCD_TRY(dalloc(&p->block_P, B));
+  GENCD_CUDA_TRY(cudaMemcpyAsync(p->block_lo, lo.data(), sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice,
+                                 p->stream));
+  GENCD_CUDA_TRY(cudaMemcpyAsync(p->block_P, P.data(), sizeof(int64_t) * B, cudaMemcpyHostToDevice, p->stream));
+  GENCD_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  p->hblock_lo = lo;
+  p->hblock_P = P;
+  p->hblock_rho = rho;
+  p->hblock_epoch.assign(B, -1);
+  p->block_B = B;
+  return GENCD_OK;
+}
+
+// Select of block Shotgun for iteration t: from every block b the next
+// m_b = min(P_b, k_b - q P_b) columns of its epoch permutation (q = t mod
+// ceil(k_b / P_b)), laid end to end in block order.  One CTA; the blocks'
+// offsets by a prefix sum in shared memory (B <= kMaxShotgunBlocks).
+__global__ void __launch_bounds__(kThreads)
+    k_block_select(int64_t t, int32_t B, const int64_t* __restrict__ blo, const int64_t* __restrict__ bP,
+                   const int32_t* __restrict__ perm, int32_t* __restrict__ J) {
+  __shared__ int64_t off[kMaxShotgunBlocks + 1];
+  __shared__ int64_t start[kMaxShotgunBlocks];
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const int64_t kb = blo[b + 1] - blo[b];
+    int64_t m = 0, q0 = 0;
+    if (kb > 0) {
+      const int64_t P = bP[b] < 1 ? 1 : (bP[b] < kb ? bP[b] : kb);
+      const int64_t per_epoch = (kb + P - 1) / P;
+      q0 = (t % per_epoch) * P;
+      m = kb - q0 < P ? kb - q0 : P;
+    }
+    off[b + 1] = m;
+    start[b] = q0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    off[0] = 0;
+    for (int b = 0; b < B; ++b) off[b + 1] += off[b];
+  }
+  __syncthreads();
+  for (int b = 0; b < B; ++b) {
+    const int64_t lo = blo[b], m = off[b + 1] - off[b];
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) J[off[b] + i] = (int32_t)(lo + perm[lo + start[b] + i]);
+  }
 }
 
 static void free_problem(gencd_problem* p) {
@@ -415,7 +524,7 @@ static void free_problem(gencd_problem* p) {
                   p->sort_tmp,
                   p->row_ptr, p->col_idx, p->csr_val, p->color, p->color_ptr, p->cols_by_color,
                   p->slot_m, p->slot_d, p->slot_j, p->list_off, p->scan_tmp, p->bj, p->w32, p->bj32, p->ib32,
-                  p->part_lo, p->col_val};
+                  p->part_lo, p->col_val, p->block_lo, p->block_P};
   if (p->stream) cudaStreamSynchronize(p->stream);
   free_propose_plan(p);
   if (p->gnat && p->gnat != p->gacc) cudaFree(p->gnat);
@@ -709,7 +818,9 @@ int gencd_lambda_max(gencd_problem* p, double* lambda_max) {
 int gencd_set_params(gencd_problem* p, const gencd_params* a) {
   GENCD_CHECK_HANDLE(p);
   if (!a) return fail(GENCD_EINVAL, "params is NULL");
-  if (a->variant < 0 || a->variant > 4) return fail(GENCD_EINVAL, "unknown variant");
+  if (a->variant < 0 || a->variant > 5) return fail(GENCD_EINVAL, "unknown variant");
+  if (a->variant == GENCD_SHOTGUN_BLOCKS && a->blocks > kMaxShotgunBlocks)
+    return fail(GENCD_EINVAL, "block Shotgun takes at most " + std::to_string(kMaxShotgunBlocks) + " blocks");
   if (a->blocks < 0 || a->P < 0 || a->max_iter < 0 || !(a->tol_kkt >= 0.0) || a->check_every < 1 ||
       (a->beta_mode != 0 && a->beta_mode != 1) || !(a->timeout_s >= 0.0) || a->improve_steps < 0 ||
       a->improve_steps > 100000)
@@ -717,7 +828,10 @@ int gencd_set_params(gencd_problem* p, const gencd_params* a) {
   const bool reseed = a->seed != p->params.seed;
   p->params = *a;
   p->accept_group = 1;
-  if (reseed) p->perm_epoch = -1;
+  if (reseed) {
+    p->perm_epoch = -1;
+    std::fill(p->hblock_epoch.begin(), p->hblock_epoch.end(), int64_t(-1));
+  }
   GENCD_TRY(launch_inv_beta(p));
   return GENCD_OK;
 }
@@ -985,6 +1099,18 @@ int gencd_spectral_radius(gencd_problem* p, double* rho, int64_t* pstar, int32_t
   return GENCD_OK;
 }
 
+int gencd_block_pstar(gencd_problem* p, int32_t B, int64_t* pstar, double* rho) {
+  GENCD_CHECK_HANDLE(p);
+  if (B < 1 || B > kMaxShotgunBlocks || B > p->k)
+    return fail(GENCD_EINVAL, "B must be in [1, min(k, " + std::to_string(kMaxShotgunBlocks) + ")]");
+  GENCD_TRY(compute_block_pstar(p, B));
+  for (int32_t b = 0; b < B; ++b) {
+    if (pstar) pstar[b] = p->hblock_P[b];
+    if (rho) rho[b] = p->hblock_rho[b];
+  }
+  return GENCD_OK;
+}
+
 int gencd_color(gencd_problem* p, int32_t* ncolors) {
   GENCD_CHECK_HANDLE(p);
   GENCD_TRY(run_coloring(p));
@@ -1076,6 +1202,15 @@ int gencd_profile_read(gencd_problem* p, int32_t kernel, double* ms, int64_t* la
   if (ms) *ms = p->prof.ms[kernel];
   if (launches) *launches = p->prof.launches[kernel];
   if (calls) *calls = p->prof.calls[kernel];
+  return GENCD_OK;
+}
+
+int gencd_propose_schedule(gencd_problem* p, int32_t* split, double* ms, int32_t nms) {
+  GENCD_CHECK_HANDLE(p);
+  if (nms < 0 || (nms > 0 && !ms)) return fail(GENCD_EINVAL, "ms must hold nms >= 0 values");
+  if (split) *split = p->plan.fused_split;
+  const bool timed = p->plan.built && p->plan.light_counter != nullptr;
+  for (int32_t i = 0; i < nms; ++i) ms[i] = (timed && i < 5) ? p->plan.tuned_ms[i] : -1.0;
   return GENCD_OK;
 }
 

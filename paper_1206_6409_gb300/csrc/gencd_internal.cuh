@@ -57,6 +57,7 @@ constexpr int kValNone = 2;   // index only, one value per column (GENCD_BINARY)
 constexpr int kListPlanThreads = 1024;
 constexpr int kListPlanPer = 4;
 constexpr int64_t kListPlanMax = (int64_t)kListPlanThreads * kListPlanPer;
+constexpr int32_t kMaxShotgunBlocks = 1024;  // column blocks of block Shotgun (one selection CTA)
 
 // kernel ids for launch counting / profiling
 enum KernelId {
@@ -72,6 +73,7 @@ enum KernelId {
   K_PROPOSE_LIGHT,    // streaming propose: lane-segmented pass over the light columns
   K_PROPOSE_SLABS,    // streaming propose: row-slab pass over the heavy columns
   K_PAIRS,            // streaming propose: sum of each heavy column's partials
+  K_PROPOSE_FUSED,    // streaming propose: row-slab and light passes in one kernel
   K_NUM
 };
 
@@ -133,6 +135,14 @@ struct ProposePlan {
   int32_t* slab_tile_begin = nullptr;  // nslabs + 1
   int32_t* cta_tile_begin = nullptr;   // grid + 1
   int grid = 0;
+  // both passes in one kernel (k_propose_fused) when fused_split > 0 (the
+  // number of warps that start on the row slabs; 0: two kernels), chosen by
+  // the plan's autotuner (tuned_ms: mean ms of the separate kernels, then of
+  // each split); light tiles are taken from a pool whose counter the partial
+  // reduction resets after each launch
+  int fused_split = 0;
+  double tuned_ms[8] = {-1.0};
+  unsigned int* light_counter = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -234,6 +244,15 @@ struct gencd_problem {
   double rho = 0.0;
   int64_t pstar = 0;
 
+  // block Shotgun (Section 7): block_B contiguous column blocks, their
+  // bounds (B + 1) and P*_b on the device and the host, rho_b, and the epoch
+  // whose permutation each block's part of perm holds
+  int32_t block_B = 0;
+  int64_t* block_lo = nullptr;
+  int64_t* block_P = nullptr;
+  std::vector<int64_t> hblock_lo, hblock_P, hblock_epoch;
+  std::vector<double> hblock_rho;
+
   gencd::Profiler prof;
   gencd::ProposePlan plan;
 };
@@ -249,6 +268,7 @@ int launch_propose_csc(gencd_problem* p, const CscView& a, const void* u_vec, bo
 // propose_plan.cu
 int build_propose_plan(gencd_problem* p);
 int launch_propose_plan(gencd_problem* p, const void* u_vec);
+int tune_propose_plan(gencd_problem* p);  // picks the fastest form of the streaming propose
 void free_propose_plan(gencd_problem* p);
 int launch_finalize(gencd_problem* p, double lambda, bool write_steps);
 int launch_finalize_accept(gencd_problem* p, int64_t B, bool want_kkt);  // Thread-Greedy / Greedy

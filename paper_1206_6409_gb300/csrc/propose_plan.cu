@@ -189,27 +189,37 @@ __device__ __forceinline__ void load_stage(const uint16_t* __restrict__ s_row, c
   }
 }
 
-// THREADS per CTA (one CTA per SM); ITEMS entries per lane (a tile is 32 *
-// ITEMS entries); DEPTH tiles of loads in flight per warp beyond the one
-// being processed
-template <typename V, typename U, typename G, int THREADS, int DEPTH, int ITEMS, typename SV>
-__global__ void __launch_bounds__(THREADS, 1)
-    k_propose_slabs(const uint16_t* __restrict__ s_row, const SV* __restrict__ s_val,
-                    const uint8_t* __restrict__ pmask, const uint32_t* __restrict__ pair_slot,
-                    const uint32_t* __restrict__ tile_start,
-                    const uint32_t* __restrict__ tile_end, const uint32_t* __restrict__ tile_pair,
-                    const int32_t* __restrict__ tile_slab, const int32_t* __restrict__ slab_tile_begin,
-                    const int32_t* __restrict__ cta_tile_begin, const U* __restrict__ u, int64_t n,
-                    int32_t slab_rows, G* __restrict__ partial) {
+// Barrier of the warps that share a CTA's u slab: the whole CTA (BAR_THREADS
+// = 0), or the first BAR_THREADS threads on named barrier 1 when other warps
+// of the CTA do other work (the fused pass below).
+template <int BAR_THREADS>
+__device__ __forceinline__ void slab_barrier() {
+  if (BAR_THREADS == 0)
+    __syncthreads();
+  else
+    asm volatile("bar.sync 1, %0;" ::"n"(BAR_THREADS) : "memory");
+}
+
+// The row-slab pass of one CTA's contiguous run of tiles [t0, t_end), by the
+// warps warp = 0 .. nw - 1 of the slab group (ITEMS entries per lane, a tile
+// is 32 * ITEMS entries; DEPTH tiles of loads in flight per warp beyond the
+// one being processed).
+template <typename V, typename U, typename G, int DEPTH, int ITEMS, typename SV, int BAR_THREADS>
+__device__ __forceinline__ void slab_pass(const uint16_t* __restrict__ s_row, const SV* __restrict__ s_val,
+                                          const uint8_t* __restrict__ pmask, const uint32_t* __restrict__ pair_slot,
+                                          const uint32_t* __restrict__ tile_start,
+                                          const uint32_t* __restrict__ tile_end,
+                                          const uint32_t* __restrict__ tile_pair,
+                                          const int32_t* __restrict__ tile_slab,
+                                          const int32_t* __restrict__ slab_tile_begin, int t0, const int t_end,
+                                          const U* __restrict__ u, int64_t n, int32_t slab_rows,
+                                          G* __restrict__ partial, U* s_u, const int warp, const int nw,
+                                          const int gtid, const int gthreads) {
   constexpr int TILE = 32 * ITEMS;
   constexpr uint32_t NOT_FIRST = ((1u << ITEMS) - 1u) & ~1u;  // start bits after a lane's first entry
   const unsigned FULL = 0xffffffffu;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  U* s_u = reinterpret_cast<U*>(smem_raw);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (threadIdx.x == 0) s_u[slab_rows] = U(0);  // the row of padding entries (index-only storage)
-  const int t_end = cta_tile_begin[blockIdx.x + 1];
-  int t0 = cta_tile_begin[blockIdx.x];
+  const int lane = threadIdx.x & 31;
+  if (gtid == 0) s_u[slab_rows] = U(0);  // the row of padding entries (index-only storage)
   while (t0 < t_end) {
     const int r = tile_slab[t0];
     const int tb = slab_tile_begin[r], tnext = slab_tile_begin[r + 1];
@@ -217,9 +227,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t base = tile_start[tb], slab_end = tile_end[tnext - 1];  // the slab's entries
     const int64_t row0 = (int64_t)r * slab_rows;
     const int rows = (int)min((int64_t)slab_rows, n - row0);
-    __syncthreads();  // the previous slab is no longer read
-    for (int i = threadIdx.x; i < rows; i += blockDim.x) s_u[i] = u[row0 + i];
-    __syncthreads();
+    slab_barrier<BAR_THREADS>();  // the previous slab is no longer read
+    for (int i = gtid; i < rows; i += gthreads) s_u[i] = u[row0 + i];
+    slab_barrier<BAR_THREADS>();
     TileStage<SV, ITEMS> stg[DEPTH > 0 ? DEPTH : 1];
     int t = t0 + warp;
 #pragma unroll
@@ -325,6 +335,24 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
+// THREADS per CTA (one CTA per SM); see slab_pass
+template <typename V, typename U, typename G, int THREADS, int DEPTH, int ITEMS, typename SV>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_propose_slabs(const uint16_t* __restrict__ s_row, const SV* __restrict__ s_val,
+                    const uint8_t* __restrict__ pmask, const uint32_t* __restrict__ pair_slot,
+                    const uint32_t* __restrict__ tile_start,
+                    const uint32_t* __restrict__ tile_end, const uint32_t* __restrict__ tile_pair,
+                    const int32_t* __restrict__ tile_slab, const int32_t* __restrict__ slab_tile_begin,
+                    const int32_t* __restrict__ cta_tile_begin, const U* __restrict__ u, int64_t n,
+                    int32_t slab_rows, G* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  U* s_u = reinterpret_cast<U*>(smem_raw);
+  slab_pass<V, U, G, DEPTH, ITEMS, SV, 0>(s_row, s_val, pmask, pair_slot, tile_start, tile_end, tile_pair, tile_slab,
+                                          slab_tile_begin, cta_tile_begin[blockIdx.x],
+                                          cta_tile_begin[blockIdx.x + 1], u, n, slab_rows, partial, s_u,
+                                          threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x, blockDim.x);
+}
+
 // ---------------------------------------------------------------------------
 // the light columns: a compact CSC copy streamed in 256-entry tiles, u gathered
 // from L2.  Column starts are marked like pair starts above (one byte per 8
@@ -366,15 +394,101 @@ __device__ __forceinline__ void load_light_stage(const int32_t* __restrict__ row
   }
 }
 
-// lscale (index-only columns): each column's sum is scaled by its value
+// One light tile's sums from its loads `cur` (lscale: index-only columns,
+// each column's sum scaled by its value); results go to out[light_cols[lc]].
+template <typename V, typename U, typename G, typename SV>
+__device__ __forceinline__ void light_tile(const LightStage<SV>& cur, int64_t t, int64_t nnz,
+                                           const int32_t* __restrict__ light_cols,
+                                           const float* __restrict__ lscale, const U* __restrict__ u,
+                                           G* __restrict__ out, int lane) {
+  const unsigned FULL = 0xffffffffu;
+  constexpr bool kScaled = std::is_same<SV, NoVal>::value;
+  const int64_t a = t * kLightTile + (int64_t)lane * kLightItems;
+  const bool active = a < nnz;
+  const uint32_t m = cur.m, lc0 = cur.lc0;
+  const int32_t* r = cur.r;
+  const uint32_t cnt = __popc(lane == 0 ? (m & 0xfeu) : m);
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, incl, d);
+    if (lane >= d) incl += y;
+  }
+  uint32_t q = lc0 + (incl - cnt) + (lane > 0 ? (m & 1u) : 0u);
+  // columns this lane may write (and their scales), loaded early
+  const bool lead = lane == 0 && active && !(m & 1u);
+  const uint32_t ql = q + __popc(m & 0xfeu);
+  const int32_t j0 = lead ? __ldg(light_cols + lc0) : 0;
+  const int32_t jl = (active && m != 0u) ? __ldg(light_cols + ql) : 0;
+  V s0 = V(1), sl = V(1);
+  if (kScaled) {
+    s0 = lead ? (V)__ldg(lscale + lc0) : V(1);
+    sl = (active && m != 0u) ? (V)__ldg(lscale + ql) : V(1);
+  }
+  V cont = V(0), tail = V(0);
+  bool has_tail = false;
+  if (active) {
+    U uu[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) uu[i] = __ldg(u + r[i]);  // padding rows are 0, values 0
+    // first run, last run and the whole columns between (see k_propose_slabs)
+    const uint32_t inner = m & 0xfeu;
+    const int bf = inner ? __ffs(inner) - 1 : 8;
+    V acc = V(0), first = V(0);
+    uint32_t qi = q;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if ((inner >> i) & 1u) {
+        if (i == bf) {
+          first = acc;
+        } else {  // a whole column inside the lane
+          const V sc = kScaled ? (V)__ldg(lscale + qi) : V(1);
+          out[__ldg(light_cols + qi)] = (G)(acc * sc);
+        }
+        acc = V(0);
+        ++qi;
+      }
+      acc = fma((V)cur.val.get(i), (V)uu[i], acc);
+    }
+    if (inner) {
+      if (m & 1u) {  // started at entry 0, ended inside
+        const V sc = kScaled ? (V)__ldg(lscale + q) : V(1);
+        out[__ldg(light_cols + q)] = (G)(first * sc);
+      } else {
+        cont = first;
+      }
+      tail = acc;
+      has_tail = true;
+    } else if (m & 1u) {
+      tail = acc;
+      has_tail = true;
+    } else {
+      cont = acc;
+    }
+  }
+  const bool stop = !active || m != 0u;
+  if (__ballot_sync(FULL, stop) == 0u) {
+    const V sum = warp_sum(cont);  // the whole tile is inside column lc0
+    if (lane == 0) atomicAdd(out + j0, (G)(sum * s0));
+  } else {
+    bool ended;
+    const V tsum = lane_suffix_sum(cont, stop, lane, ended);
+    const V t1s = __shfl_down_sync(FULL, tsum, 1);
+    const bool e1 = __shfl_down_sync(FULL, (int)ended, 1) != 0;
+    if (lead) atomicAdd(out + j0, (G)(tsum * s0));  // column from the previous tile
+    if (has_tail) {
+      const V sum = tail + (lane < 31 ? t1s : V(0));
+      emit_pair<G>(out, (uint32_t)jl, (G)(sum * sl), lane < 31 && e1);
+    }
+  }
+}
+
 template <typename V, typename U, typename G, typename SV>
 __global__ void __launch_bounds__(kThreads, 3)
     k_propose_light_runs(const int32_t* __restrict__ row, const SV* __restrict__ val,
                          const uint8_t* __restrict__ lmask, const int32_t* __restrict__ tile_lc,
                          const int32_t* __restrict__ light_cols, const float* __restrict__ lscale,
                          const U* __restrict__ u, int64_t nnz, int64_t ntiles, G* __restrict__ out) {
-  const unsigned FULL = 0xffffffffu;
-  constexpr bool kScaled = std::is_same<SV, NoVal>::value;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -389,97 +503,87 @@ __global__ void __launch_bounds__(kThreads, 3)
     } else {
       load_light_stage<SV>(row, val, lmask, tile_lc, t, ntiles, nnz, lane, cur);
     }
-    const int64_t a = t * kLightTile + (int64_t)lane * kLightItems;
-    const bool active = a < nnz;
-    const uint32_t m = cur.m, lc0 = cur.lc0;
-    const int32_t* r = cur.r;
-    const uint32_t cnt = __popc(lane == 0 ? (m & 0xfeu) : m);
-    uint32_t incl = cnt;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(FULL, incl, d);
-      if (lane >= d) incl += y;
-    }
-    uint32_t q = lc0 + (incl - cnt) + (lane > 0 ? (m & 1u) : 0u);
-    // columns this lane may write (and their scales), loaded early
-    const bool lead = lane == 0 && active && !(m & 1u);
-    const uint32_t ql = q + __popc(m & 0xfeu);
-    const int32_t j0 = lead ? __ldg(light_cols + lc0) : 0;
-    const int32_t jl = (active && m != 0u) ? __ldg(light_cols + ql) : 0;
-    V s0 = V(1), sl = V(1);
-    if (kScaled) {
-      s0 = lead ? (V)__ldg(lscale + lc0) : V(1);
-      sl = (active && m != 0u) ? (V)__ldg(lscale + ql) : V(1);
-    }
-    V cont = V(0), tail = V(0);
-    bool has_tail = false;
-    if (active) {
-      U uu[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) uu[i] = __ldg(u + r[i]);  // padding rows are 0, values 0
-      // first run, last run and the whole columns between (see k_propose_slabs)
-      const uint32_t inner = m & 0xfeu;
-      const int bf = inner ? __ffs(inner) - 1 : 8;
-      V acc = V(0), first = V(0);
-      uint32_t qi = q;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        if ((inner >> i) & 1u) {
-          if (i == bf) {
-            first = acc;
-          } else {  // a whole column inside the lane
-            const V sc = kScaled ? (V)__ldg(lscale + qi) : V(1);
-            out[__ldg(light_cols + qi)] = (G)(acc * sc);
-          }
-          acc = V(0);
-          ++qi;
-        }
-        acc = fma((V)cur.val.get(i), (V)uu[i], acc);
-      }
-      if (inner) {
-        if (m & 1u) {  // started at entry 0, ended inside
-          const V sc = kScaled ? (V)__ldg(lscale + q) : V(1);
-          out[__ldg(light_cols + q)] = (G)(first * sc);
-        } else {
-          cont = first;
-        }
-        tail = acc;
-        has_tail = true;
-      } else if (m & 1u) {
-        tail = acc;
-        has_tail = true;
-      } else {
-        cont = acc;
-      }
-    }
-    const bool stop = !active || m != 0u;
-    if (__ballot_sync(FULL, stop) == 0u) {
-      const V sum = warp_sum(cont);  // the whole tile is inside column lc0
-      if (lane == 0) atomicAdd(out + j0, (G)(sum * s0));
-    } else {
-      bool ended;
-      const V tsum = lane_suffix_sum(cont, stop, lane, ended);
-      const V t1s = __shfl_down_sync(FULL, tsum, 1);
-      const bool e1 = __shfl_down_sync(FULL, (int)ended, 1) != 0;
-      if (lead) atomicAdd(out + j0, (G)(tsum * s0));  // column from the previous tile
-      if (has_tail) {
-        const V sum = tail + (lane < 31 ? t1s : V(0));
-        emit_pair<G>(out, (uint32_t)jl, (G)(sum * sl), lane < 31 && e1);
-      }
-    }
+    light_tile<V, U, G, SV>(cur, t, nnz, light_cols, lscale, u, out, lane);
   }
+}
+
+// The light tiles as a shared pool: warps take kLightChunk tiles at a time
+// from a global counter (reset to 0 by k_pairs_to_gacc after every launch),
+// the next tile's loads in flight while one is summed.
+constexpr int kLightChunk = 2;
+
+template <typename V, typename U, typename G, typename SV>
+__device__ __forceinline__ void light_pool(const int32_t* __restrict__ row, const SV* __restrict__ val,
+                                           const uint8_t* __restrict__ lmask, const int32_t* __restrict__ tile_lc,
+                                           const int32_t* __restrict__ light_cols,
+                                           const float* __restrict__ lscale, const U* __restrict__ u, int64_t nnz,
+                                           int64_t ntiles, G* __restrict__ out, unsigned int* counter) {
+  const int lane = threadIdx.x & 31;
+  auto grab = [&](int64_t& t, int64_t& t_end) {
+    unsigned int b = 0;
+    if (lane == 0) b = atomicAdd(counter, (unsigned int)kLightChunk);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    t = (int64_t)b;
+    t_end = t + kLightChunk < ntiles ? t + kLightChunk : ntiles;
+  };
+  int64_t t, t_end;
+  grab(t, t_end);
+  if (t >= ntiles) return;
+  LightStage<SV> nxt;
+  load_light_stage<SV>(row, val, lmask, tile_lc, t, ntiles, nnz, lane, nxt);
+  for (;;) {  // warp-uniform
+    const LightStage<SV> cur = nxt;
+    const int64_t tc = t;
+    if (++t >= t_end) grab(t, t_end);
+    const bool more = t < ntiles;
+    if (more) load_light_stage<SV>(row, val, lmask, tile_lc, t, ntiles, nnz, lane, nxt);  // next tile in flight
+    light_tile<V, U, G, SV>(cur, tc, nnz, light_cols, lscale, u, out, lane);
+    if (!more) break;
+  }
+}
+
+// Both streaming passes in one persistent kernel, one CTA per SM: warps
+// 0 .. SLAB_WARPS - 1 run the CTA's row-slab tiles (u slab in shared memory,
+// synchronised on named barrier 1), the other warps take light tiles from
+// the pool, and the slab warps join the pool when their tiles are done.  The
+// slab pass waits on memory latency and the light pass on L1 gathers, so
+// running them side by side on every SM overlaps the two.
+template <typename V, typename U, typename G, int THREADS, int SLAB_WARPS, int DEPTH, int ITEMS, typename SV>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_propose_fused(const uint16_t* __restrict__ s_row, const SV* __restrict__ s_val,
+                    const uint8_t* __restrict__ pmask, const uint32_t* __restrict__ pair_slot,
+                    const uint32_t* __restrict__ tile_start, const uint32_t* __restrict__ tile_end,
+                    const uint32_t* __restrict__ tile_pair, const int32_t* __restrict__ tile_slab,
+                    const int32_t* __restrict__ slab_tile_begin, const int32_t* __restrict__ cta_tile_begin,
+                    const int32_t* __restrict__ lrow, const SV* __restrict__ lval,
+                    const uint8_t* __restrict__ lmask, const int32_t* __restrict__ tile_lc,
+                    const int32_t* __restrict__ light_cols, const float* __restrict__ lscale, int64_t lnnz,
+                    int64_t lntiles, unsigned int* counter, const U* __restrict__ u, int64_t n, int32_t slab_rows,
+                    G* __restrict__ partial, G* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  U* s_u = reinterpret_cast<U*>(smem_raw);
+  const int warp = threadIdx.x >> 5;
+  if (warp < SLAB_WARPS)
+    slab_pass<V, U, G, DEPTH, ITEMS, SV, 32 * SLAB_WARPS>(
+        s_row, s_val, pmask, pair_slot, tile_start, tile_end, tile_pair, tile_slab, slab_tile_begin,
+        cta_tile_begin[blockIdx.x], cta_tile_begin[blockIdx.x + 1], u, n, slab_rows, partial, s_u, warp, SLAB_WARPS,
+        threadIdx.x, 32 * SLAB_WARPS);
+  light_pool<V, U, G, SV>(lrow, lval, lmask, tile_lc, light_cols, lscale, u, lnnz, lntiles, out, counter);
 }
 
 // sum of each heavy column = its partials in slab order (the slots of column h
 // are hslot_ptr[h] .. hslot_ptr[h+1], at most one per slab); partials reset.
 // The loads of up to 32 slots are issued together, then summed in order.
 // hscale (index-only columns): the sum is scaled by the column's value
+// light_counter (nullable): the light-tile pool of k_propose_fused, reset
+// here for the next launch (this kernel runs after it on the same stream)
 template <typename G>
 __global__ void k_pairs_to_gacc(const uint32_t* __restrict__ hslot_ptr, const int32_t* __restrict__ heavy_cols,
                                 int64_t nheavy, G* __restrict__ partial, G* __restrict__ gacc,
-                                const float* __restrict__ hscale) {
+                                const float* __restrict__ hscale, unsigned int* __restrict__ light_counter) {
   constexpr int CH = 32;
   const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (light_counter && h == 0) *light_counter = 0u;
   if (h >= nheavy) return;
   const uint32_t b = hslot_ptr[h], e = hslot_ptr[h + 1];
   G s = G(0);
@@ -498,9 +602,45 @@ __global__ void k_pairs_to_gacc(const uint32_t* __restrict__ hslot_ptr, const in
 
 // the two streaming passes and the partial reduction for one value storage SV
 // (V compute type, U type of u, G accumulator)
+constexpr int kFusedThreads = 1024;
+// candidate splits of the fused kernel's 32 warps: warps that start on the
+// row slabs (the rest start on the light pool); the plan's autotuner times
+// each, and the two separate kernels, on the problem at hand
+constexpr int kFusedSplits[] = {16, 20, 24, 28};
+constexpr int kNumFusedSplits = 4;
+
+template <typename V, typename U, typename G, typename SV, int DEPTH, int ITEMS, int SW>
+static void launch_fused(gencd_problem* p, const void* u_vec, size_t smem) {
+  ProposePlan& P = p->plan;
+  k_propose_fused<V, U, G, kFusedThreads, SW, DEPTH, ITEMS, SV><<<P.grid, kFusedThreads, smem, p->stream>>>(
+      P.s_row, (const SV*)P.s_val, P.pmask, P.pair_slot, P.tile_start, P.tile_end, P.tile_pair, P.tile_slab,
+      P.slab_tile_begin, P.cta_tile_begin, P.light_row, (const SV*)P.light_val, P.lmask, P.light_tile_lc,
+      P.light_cols, P.light_scale, P.light_nnz, P.light_ntiles, P.light_counter, (const U*)u_vec, p->n,
+      P.slab_rows, (G*)P.partial, (G*)p->gnat);
+}
+
 template <typename V, typename U, typename G, typename SV, int THREADS, int DEPTH, int ITEMS>
 static int launch_plan_passes(gencd_problem* p, const void* u_vec) {
   ProposePlan& P = p->plan;
+  if (P.fused_split > 0) {  // both passes in one kernel, then the heavy columns' partials
+    const size_t smem = (size_t)(P.slab_rows + kSlabZeroSlot) * sizeof(U);
+    const int g2 = (int)((P.nheavy + kThreads - 1) / kThreads);
+    cudaEvent_t e1 = nullptr, e2 = nullptr;
+    prof_begin(p, K_PROPOSE_FUSED, &e1);
+    switch (P.fused_split) {
+      case 16: launch_fused<V, U, G, SV, DEPTH, ITEMS, 16>(p, u_vec, smem); break;
+      case 20: launch_fused<V, U, G, SV, DEPTH, ITEMS, 20>(p, u_vec, smem); break;
+      case 24: launch_fused<V, U, G, SV, DEPTH, ITEMS, 24>(p, u_vec, smem); break;
+      default: launch_fused<V, U, G, SV, DEPTH, ITEMS, 28>(p, u_vec, smem); break;
+    }
+    prof_end(p, e1);
+    prof_begin(p, K_PAIRS, &e2);
+    k_pairs_to_gacc<G><<<g2, kThreads, 0, p->stream>>>(P.hslot_ptr, P.heavy_cols, P.nheavy, (G*)P.partial,
+                                                        (G*)p->gnat, P.heavy_scale, P.light_counter);
+    prof_end(p, e2);
+    GENCD_CUDA_TRY(cudaGetLastError());
+    return GENCD_OK;
+  }
   if (P.nlight > 0) {
     cudaEvent_t e = nullptr;
     prof_begin(p, K_PROPOSE_LIGHT, &e);
@@ -522,7 +662,7 @@ static int launch_plan_passes(gencd_problem* p, const void* u_vec) {
     prof_end(p, e1);
     prof_begin(p, K_PAIRS, &e2);
     k_pairs_to_gacc<G><<<g2, kThreads, 0, p->stream>>>(P.hslot_ptr, P.heavy_cols, P.nheavy, (G*)P.partial,
-                                                        (G*)p->gnat, P.heavy_scale);
+                                                        (G*)p->gnat, P.heavy_scale, nullptr);
     prof_end(p, e2);
     GENCD_CUDA_TRY(cudaGetLastError());
   }
@@ -531,9 +671,19 @@ static int launch_plan_passes(gencd_problem* p, const void* u_vec) {
 
 template <typename V, typename U, typename G, typename SV, int THREADS, int DEPTH, int ITEMS>
 static int set_slab_smem(const ProposePlan& P) {
+  const int smem = (int)((size_t)(P.slab_rows + kSlabZeroSlot) * sizeof(U));
   GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_slabs<V, U, G, THREADS, DEPTH, ITEMS, SV>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)((size_t)(P.slab_rows + kSlabZeroSlot) * sizeof(U))));
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  if (P.light_counter) {
+    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_fused<V, U, G, kFusedThreads, 16, DEPTH, ITEMS, SV>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_fused<V, U, G, kFusedThreads, 20, DEPTH, ITEMS, SV>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_fused<V, U, G, kFusedThreads, 24, DEPTH, ITEMS, SV>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_fused<V, U, G, kFusedThreads, 28, DEPTH, ITEMS, SV>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  }
   return GENCD_OK;
 }
 
@@ -750,7 +900,7 @@ void free_propose_plan(gencd_problem* p) {
   void* bufs[] = {P.light_cols, P.light_col_ptr, P.light_row, P.light_val, P.light_tile_lc, P.lmask, P.light_scale,
                   P.heavy_scale, P.heavy_cols,
                   P.s_row, P.s_val, P.pmask, P.pair_slot, P.hslot_ptr, P.partial, P.tile_start,
-                  P.tile_end, P.tile_pair, P.tile_slab, P.slab_tile_begin, P.cta_tile_begin};
+                  P.tile_end, P.tile_pair, P.tile_slab, P.slab_tile_begin, P.cta_tile_begin, P.light_counter};
   for (void* b : bufs)
     if (b) cudaFree(b);
   P = ProposePlan();
@@ -1010,6 +1160,14 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
                                                                       P.tile_end, P.tile_pair, P.tile_slab);
   GENCD_CUDA_TRY(cudaGetLastError());
   P.grid = p->num_sms;
+  // both passes may run in one kernel when there are light and heavy columns
+  // (FP32 arithmetic: FP64 stages do not fit the fused kernel's registers);
+  // the autotuner below decides
+  P.fused_split = 0;
+  if (!f64 && P.nlight > 0 && P.nheavy > 0) {
+    GENCD_TRY(palloc(&P.light_counter, 1));
+    GENCD_CUDA_TRY(cudaMemsetAsync(P.light_counter, 0, sizeof(unsigned int), st));
+  }
   std::vector<int32_t> ctb(P.grid + 1);
   for (int b = 0; b <= P.grid; ++b) ctb[b] = (int32_t)((int64_t)b * P.ntiles / P.grid);
   GENCD_TRY(palloc(&P.cta_tile_begin, P.grid + 1));
@@ -1040,6 +1198,51 @@ int build_propose_plan(gencd_problem* p) {
     return rc;
   }
   p->plan.built = true;
+  return tune_propose_plan(p);
+}
+
+// Autotuner of the streaming propose: times the separate light and slab
+// kernels and every split of the fused kernel on this problem (three
+// launches each, CUDA events, u as it stands) and keeps the fastest.  All
+// candidates compute the same sums; the scratch they leave is cleared.
+int tune_propose_plan(gencd_problem* p) {
+  ProposePlan& P = p->plan;
+  P.tuned_ms[0] = -1.0;
+  if (!P.built || !P.light_counter) return GENCD_OK;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  GENCD_CUDA_TRY(cudaEventCreate(&ev[0]));
+  if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+    cudaEventDestroy(ev[0]);
+    return fail_plan("cudaEventCreate failed");
+  }
+  const bool prof = p->prof.enabled;
+  p->prof.enabled = false;
+  int rc = GENCD_OK;
+  float best_ms = 0.f;
+  int best = 0;
+  for (int c = 0; c <= kNumFusedSplits && rc == GENCD_OK; ++c) {
+    P.fused_split = c == 0 ? 0 : kFusedSplits[c - 1];
+    if ((rc = launch_propose_plan(p, p->u)) != GENCD_OK) break;  // warm-up
+    cudaEventRecord(ev[0], p->stream);
+    for (int r = 0; r < 3 && rc == GENCD_OK; ++r) rc = launch_propose_plan(p, p->u);
+    cudaEventRecord(ev[1], p->stream);
+    if (rc != GENCD_OK || cudaEventSynchronize(ev[1]) != cudaSuccess) {
+      rc = rc != GENCD_OK ? rc : fail_plan("autotuning the streaming propose failed");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    P.tuned_ms[c] = ms / 3.0;
+    if (c == 0 || ms < best_ms) best_ms = ms, best = P.fused_split;
+  }
+  p->prof.enabled = prof;
+  P.fused_split = best;
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (rc != GENCD_OK) return rc;
+  // the candidates' sums are scratch: the hot path expects them zero
+  const size_t gsz = p->precision == GENCD_F64 ? sizeof(double) : sizeof(float);
+  GENCD_CUDA_TRY(cudaMemsetAsync(p->gnat, 0, gsz * (size_t)p->k, p->stream));
   return GENCD_OK;
 }
 

@@ -620,3 +620,47 @@ def test_precision_sweep_config3(gb, capsys):
         for values, mode, rel, bound, rel_s, dw, supp, ndiff, nfrag, eps, it in rows:
             print(f"  {values:9s} {mode:6s} {rel:+.3e}  {bound:.1e} | {rel_s:+.2e}  {ndiff:3d} ({nfrag:3d})  "
                   f"{eps:.1e} | {dw:.2e}  {supp:3d}  {it}")
+
+
+@pytest.mark.parametrize("loss", ["logistic", "squared"])
+def test_block_shotgun_matches_the_oracle(gb, loss):
+    # Section 7's block Shotgun (reading R14): 7 uneven column blocks, each
+    # with its own P*_b from the block's spectral radius; the GPU's P*_b equal
+    # the oracle's and 40 iterations follow the oracle's trajectory
+    prob = workloads.config1(loss)
+    orc = oracle.Oracle(prob)
+    lam = 0.05 * orc.lambda_max()
+    orc.set_lambda(lam)
+    B = 7
+    Pb_cpu = orc.block_pstar(B)
+    with gb.Problem(prob) as p:
+        p.set_lambda(lam)
+        Pb, rho = p.block_pstar(B)
+        np.testing.assert_array_equal(Pb, Pb_cpu)
+        p.set_params(variant="shotgun_blocks", blocks=B, seed=4)
+        p.stats_reset()
+        p.iterate(40)
+        w_gpu = p.w()
+        upd = p.stats().updates
+    w_cpu, _, _, st = orc.run("shotgun_blocks", 40, B=B, block_P=Pb_cpu, seed=4)
+    assert upd == st[0]
+    np.testing.assert_array_equal(w_gpu != 0, w_cpu != 0)
+    np.testing.assert_allclose(w_gpu, w_cpu, rtol=0, atol=1e-10)
+
+
+def test_block_shotgun_solve_reaches_the_optimum(gb):
+    prob = workloads.uniform_problem(1000, 2000, 10, values="pm1", loss="logistic", n_planted=30, seed=21)
+    orc = oracle.Oracle(prob)
+    lam = 0.05 * orc.lambda_max()
+    orc.set_lambda(lam)
+    w_opt, _, _, kkt, _ = orc.solve("ccd", tol_kkt=1e-11)
+    with gb.Problem(prob) as p:
+        p.set_lambda(lam)
+        p.set_params(variant="shotgun_blocks", blocks=16, tol_kkt=1e-10, max_iter=2_000_000, check_every=100)
+        r = p.solve()
+        assert r.status == 0, r.as_dict()
+        w = p.w()
+        with pytest.raises(gb.GencdError):
+            p.set_params(variant="shotgun_blocks", blocks=1025)
+    assert r.objective == pytest.approx(orc.objective(w_opt), rel=1e-6)
+    assert_support_matches(prob, lam, w, w_opt, label="block shotgun")
