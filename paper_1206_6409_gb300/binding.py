@@ -83,7 +83,7 @@ class gencd_request(C.Structure):
 
 class gencd_serve_params(C.Structure):
     _fields_ = [("workers", C.c_int32), ("precision", C.c_int32), ("hbm_fraction", C.c_double),
-                ("params", gencd_params)]
+                ("params", gencd_params), ("tol_rel", C.c_double)]
 
 
 class gencd_response(C.Structure):
@@ -730,10 +730,12 @@ class Batch:
 # --- include/gencd_serve.h ----------------------------------------------------
 
 def gencd_serve(problems, lambda_fracs, arrivals, workers=4, precision="f32", hbm_fraction=0.5, want_w=False,
-                **params):
+                tol_rel=0.0, **params):
     """Serves a stream of independent problems (workloads.Problem, host
-    arrays) arriving at `arrivals` seconds; lambda = lambda_frac * lambda_max
-    per problem.  Returns (responses as dicts, list of w arrays or None)."""
+    arrays) arriving at `arrivals` seconds in up to `workers` slots; lambda =
+    lambda_frac * lambda_max per problem, and with tol_rel > 0 each solve
+    stops at KKT <= tol_rel * lambda.  Returns (responses as dicts, list of w
+    arrays or None)."""
     keep = []
     reqs = (gencd_request * len(problems))()
     for q, (p, lf, at) in enumerate(zip(problems, lambda_fracs, arrivals)):
@@ -753,7 +755,7 @@ def gencd_serve(problems, lambda_fracs, arrivals, workers=4, precision="f32", hb
             v = VARIANTS[v]
         setattr(pr, key, v)
     sp = gencd_serve_params(workers=int(workers), precision=PRECISIONS.get(precision, precision),
-                            hbm_fraction=float(hbm_fraction), params=pr)
+                            hbm_fraction=float(hbm_fraction), params=pr, tol_rel=float(tol_rel))
     out = (gencd_response * len(problems))()
     ws = [np.empty(p.k) for p in problems] if want_w else None
     wp = (C.c_void_p * len(problems))(*[w.ctypes.data for w in ws]) if want_w else None

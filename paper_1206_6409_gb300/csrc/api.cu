@@ -179,31 +179,39 @@ static cudaMemcpyKind kind_out(int32_t memory) {
   return memory == GENCD_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
 }
 
-template <typename T>
-static int dalloc(T** ptr, size_t count) {
+int dev_alloc_bytes(gencd_problem* p, void** ptr, size_t bytes) {
   *ptr = nullptr;
-  if (count == 0) count = 1;
-  if (cudaMalloc((void**)ptr, sizeof(T) * count) != cudaSuccess) {
+  const cudaError_t e = p->pool ? cudaMallocFromPoolAsync(ptr, bytes, p->pool, p->stream) : cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     *ptr = nullptr;
-    return fail(GENCD_ENOMEM, "cudaMalloc of " + std::to_string(sizeof(T) * count) + " bytes failed");
+    return fail(GENCD_ENOMEM, std::string(p->pool ? "allocation from the memory pool" : "cudaMalloc") + " of " +
+                                  std::to_string(bytes) + " bytes failed");
   }
   return GENCD_OK;
+}
+
+void dev_free(gencd_problem* p, void* ptr) {
+  if (!ptr) return;
+  if (p->pool)
+    cudaFreeAsync(ptr, p->stream);
+  else
+    cudaFree(ptr);
 }
 
 int ensure_slots(gencd_problem* p, int64_t count) {
   if (count <= p->slot_cap) return GENCD_OK;
   GENCD_CUDA_TRY(cudaStreamSynchronize(p->stream));
-  cudaFree(p->slot_m);
-  cudaFree(p->slot_d);
-  cudaFree(p->slot_j);
+  dev_free(p, p->slot_m);
+  dev_free(p, p->slot_d);
+  dev_free(p, p->slot_j);
   p->slot_m = nullptr;
   p->slot_d = nullptr;
   p->slot_j = nullptr;
   p->slot_cap = 0;
-  GENCD_TRY(dalloc(&p->slot_m, count));
-  GENCD_TRY(dalloc(&p->slot_d, count));
-  GENCD_TRY(dalloc(&p->slot_j, count));
+  GENCD_TRY(dev_alloc(p, &p->slot_m, count));
+  GENCD_TRY(dev_alloc(p, &p->slot_d, count));
+  GENCD_TRY(dev_alloc(p, &p->slot_j, count));
   p->slot_cap = count;
   return GENCD_OK;
 }
@@ -234,6 +242,13 @@ static int enqueue_evaluate(gencd_problem* p) {
 static int read_scalars(gencd_problem* p) {
   GENCD_CUDA_TRY(cudaMemcpyAsync(p->hpin, p->dscal, 8 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
   GENCD_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return GENCD_OK;
+}
+
+// the device scalars to hpin without waiting; ev_scalars marks their arrival
+static int read_scalars_async(gencd_problem* p) {
+  GENCD_CUDA_TRY(cudaMemcpyAsync(p->hpin, p->dscal, 8 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  GENCD_CUDA_TRY(cudaEventRecord(p->ev_scalars, p->stream));
   return GENCD_OK;
 }
 
@@ -289,7 +304,7 @@ static int launch_top_accept(gencd_problem* p, int64_t B) {
   const int64_t k = p->k;
   // keys, indices, their alternates, the high halves and the radix scratch:
   // sized once, so the Accept allocates nothing per iteration
-  if (!p->top_buf) GENCD_TRY(dalloc(&p->top_buf, 6 * (size_t)k + radix_tmp_words(k)));
+  if (!p->top_buf) GENCD_TRY(dev_alloc(p, &p->top_buf, 6 * (size_t)k + radix_tmp_words(k)));
   uint32_t *lo = p->top_buf, *idx = lo + k, *lo_alt = lo + 2 * k, *idx_alt = lo + 3 * k, *hi = lo + 4 * k,
            *hi_g = lo + 5 * k, *rtmp = lo + 6 * k;
   const int g = grid_for(k, kThreads, p->num_sms * 8);
@@ -395,13 +410,13 @@ static int power_radius(gencd_problem* p, int64_t lo, int64_t hi, double* rho_ou
   const int64_t k = p->k;
   double *dinv = nullptr, *v = nullptr, *s = nullptr, *t = nullptr, *r = nullptr;
   int rc = GENCD_OK;
-  if ((rc = dalloc(&dinv, k)) || (rc = dalloc(&v, k)) || (rc = dalloc(&s, k)) || (rc = dalloc(&t, k)) ||
-      (rc = dalloc(&r, p->n))) {
-    cudaFree(dinv);
-    cudaFree(v);
-    cudaFree(s);
-    cudaFree(t);
-    cudaFree(r);
+  if ((rc = dev_alloc(p, &dinv, k)) || (rc = dev_alloc(p, &v, k)) || (rc = dev_alloc(p, &s, k)) || (rc = dev_alloc(p, &t, k)) ||
+      (rc = dev_alloc(p, &r, p->n))) {
+    dev_free(p, dinv);
+    dev_free(p, v);
+    dev_free(p, s);
+    dev_free(p, t);
+    dev_free(p, r);
     return rc;
   }
   const int g = p->num_sms * 8;
@@ -426,11 +441,11 @@ static int power_radius(gencd_problem* p, int64_t lo, int64_t hi, double* rho_ou
     if (done) break;
   }
   if (it > 100) it = 100;
-  cudaFree(dinv);
-  cudaFree(v);
-  cudaFree(s);
-  cudaFree(t);
-  cudaFree(r);
+  dev_free(p, dinv);
+  dev_free(p, v);
+  dev_free(p, s);
+  dev_free(p, t);
+  dev_free(p, r);
   if (rc != GENCD_OK) return rc;
   *rho_out = rho;
   if (iters_out) *iters_out = it;
@@ -465,13 +480,13 @@ static int compute_block_pstar(gencd_problem* p, int32_t B) {
     if (lo[b + 1] > lo[b]) GENCD_TRY(power_radius(p, lo[b], lo[b + 1], &rho[b], nullptr));
     P[b] = lo[b + 1] > lo[b] ? pstar_of(lo[b + 1] - lo[b], rho[b]) : 0;
   }
-  cudaFree(p->block_lo);
-  cudaFree(p->block_P);
+  dev_free(p, p->block_lo);
+  dev_free(p, p->block_P);
   p->block_lo = nullptr;
   p->block_P = nullptr;
   p->block_B = 0;
-  GENCD_TRY(dalloc(&p->block_lo, B + 1));
-  GENCD_TRY(dalloc(&p->block_P, B));
+  GENCD_TRY(dev_alloc(p, &p->block_lo, B + 1));
+  GENCD_TRY(dev_alloc(p, &p->block_P, B));
   GENCD_CUDA_TRY(cudaMemcpyAsync(p->block_lo, lo.data(), sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice,
                                  p->stream));
   GENCD_CUDA_TRY(cudaMemcpyAsync(p->block_P, P.data(), sizeof(int64_t) * B, cudaMemcpyHostToDevice, p->stream));
@@ -527,10 +542,11 @@ static void free_problem(gencd_problem* p) {
                   p->part_lo, p->col_val, p->block_lo, p->block_P};
   if (p->stream) cudaStreamSynchronize(p->stream);
   free_propose_plan(p);
-  if (p->gnat && p->gnat != p->gacc) cudaFree(p->gnat);
+  if (p->gnat && p->gnat != p->gacc) dev_free(p, p->gnat);
   for (void* b : bufs)
-    if (b) cudaFree(b);
-  if (p->hpin) cudaFreeHost(p->hpin);
+    if (b) dev_free(p, b);
+  if (p->hpin && p->own_hpin) cudaFreeHost(p->hpin);
+  if (p->ev_scalars) cudaEventDestroy(p->ev_scalars);
   for (cudaEvent_t e : p->prof.pool) cudaEventDestroy(e);
   cudaGetLastError();
   delete p;
@@ -570,9 +586,9 @@ __global__ void k_column_values(const int64_t* __restrict__ col_ptr, const float
 static int store_values(gencd_problem* p, int64_t* bad_out) {
   *bad_out = -1;
   if (p->vmode == kValPlain) return GENCD_OK;
-  if (p->vmode == kValNone) GENCD_TRY(dalloc(&p->col_val, p->k));
+  if (p->vmode == kValNone) GENCD_TRY(dev_alloc(p, &p->col_val, p->k));
   unsigned long long* bad = nullptr;
-  GENCD_TRY(dalloc(&bad, 1));
+  GENCD_TRY(dev_alloc(p, &bad, 1));
   unsigned long long h = ~0ull;
   int rc = GENCD_OK;
   if (cudaMemcpyAsync(bad, &h, 8, cudaMemcpyHostToDevice, p->stream) != cudaSuccess) rc = GENCD_ECUDA;
@@ -587,7 +603,7 @@ static int store_values(gencd_problem* p, int64_t* bad_out) {
         cudaStreamSynchronize(p->stream) != cudaSuccess)
       rc = fail(GENCD_ECUDA, std::string("storage conversion: ") + cudaGetErrorString(cudaGetLastError()));
   }
-  cudaFree(bad);
+  dev_free(p, bad);
   p->prof.launches[K_SETUP] += 1;
   if (rc == GENCD_OK && h != ~0ull) *bad_out = (int64_t)h;
   return rc;
@@ -604,41 +620,42 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
   p->ntiles = (nnz + tile - 1) / tile;
   const size_t vsz = p->precision == GENCD_F64 ? 8 : 4;
 
-  GENCD_TRY(dalloc(&p->col_ptr, k + 1));
-  GENCD_TRY(dalloc(&p->row_idx, p->nnz_pad));
-  GENCD_TRY(dalloc((char**)&p->val, vsz * p->nnz_pad));
-  GENCD_TRY(dalloc(&p->y, n));
-  GENCD_TRY(dalloc(&p->z, n));
-  GENCD_TRY(dalloc((char**)&p->u, vsz * (n + 1)));  // u[n] = 0: the row that padding entries may gather
-  GENCD_TRY(dalloc(&p->w, k));
-  GENCD_TRY(dalloc(&p->c, k));
-  GENCD_TRY(dalloc(&p->ib, k));
-  GENCD_TRY(dalloc(&p->bj, k));
+  GENCD_TRY(dev_alloc(p, &p->col_ptr, k + 1));
+  GENCD_TRY(dev_alloc(p, &p->row_idx, p->nnz_pad));
+  GENCD_TRY(dev_alloc(p, (char**)&p->val, vsz * p->nnz_pad));
+  GENCD_TRY(dev_alloc(p, &p->y, n));
+  GENCD_TRY(dev_alloc(p, &p->z, n));
+  GENCD_TRY(dev_alloc(p, (char**)&p->u, vsz * (n + 1)));  // u[n] = 0: the row that padding entries may gather
+  GENCD_TRY(dev_alloc(p, &p->w, k));
+  GENCD_TRY(dev_alloc(p, &p->c, k));
+  GENCD_TRY(dev_alloc(p, &p->ib, k));
+  GENCD_TRY(dev_alloc(p, &p->bj, k));
   if (p->precision == GENCD_F32) {
-    GENCD_TRY(dalloc(&p->w32, k));
-    GENCD_TRY(dalloc(&p->bj32, k));
-    GENCD_TRY(dalloc(&p->ib32, k));
+    GENCD_TRY(dev_alloc(p, &p->w32, k));
+    GENCD_TRY(dev_alloc(p, &p->bj32, k));
+    GENCD_TRY(dev_alloc(p, &p->ib32, k));
   }
-  GENCD_TRY(dalloc(&p->tile_col, p->ntiles + 1));
-  GENCD_TRY(dalloc(&p->gacc, k));
+  GENCD_TRY(dev_alloc(p, &p->tile_col, p->ntiles + 1));
+  GENCD_TRY(dev_alloc(p, &p->gacc, k));
   if (p->precision == GENCD_F64) {
     p->gnat = p->gacc;
   } else {
     float* gf = nullptr;
-    GENCD_TRY(dalloc(&gf, k));
+    GENCD_TRY(dev_alloc(p, &gf, k));
     p->gnat = gf;
   }
-  GENCD_TRY(dalloc(&p->delta, k));
-  GENCD_TRY(dalloc(&p->phi, k));
-  GENCD_TRY(dalloc(&p->list_j, k));
-  GENCD_TRY(dalloc(&p->list_d, k));
-  GENCD_TRY(dalloc(&p->list_m, k));
-  GENCD_TRY(dalloc(&p->perm, k));
-  GENCD_TRY(dalloc(&p->list_off, k + 2));
-  GENCD_TRY(dalloc(&p->scan_tmp, scan_tmp_words(k + 2)));
-  GENCD_TRY(dalloc(&p->dscal, 8));
-  GENCD_TRY(dalloc(&p->red, 2 * kRedBlocks));
-  if (cudaMallocHost((void**)&p->hpin, 8 * sizeof(double)) != cudaSuccess) {
+  GENCD_TRY(dev_alloc(p, &p->delta, k));
+  GENCD_TRY(dev_alloc(p, &p->phi, k));
+  GENCD_TRY(dev_alloc(p, &p->list_j, k));
+  GENCD_TRY(dev_alloc(p, &p->list_d, k));
+  GENCD_TRY(dev_alloc(p, &p->list_m, k));
+  GENCD_TRY(dev_alloc(p, &p->perm, k));
+  GENCD_TRY(dev_alloc(p, &p->list_off, k + 2));
+  GENCD_TRY(dev_alloc(p, &p->scan_tmp, scan_tmp_words(k + 2)));
+  GENCD_TRY(dev_alloc(p, &p->dscal, 8));
+  GENCD_TRY(dev_alloc(p, &p->red, 2 * kRedBlocks));
+  GENCD_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_scalars, cudaEventDisableTiming));
+  if (!p->hpin && cudaMallocHost((void**)&p->hpin, 8 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return fail(GENCD_ENOMEM, "pinned host allocation failed");
   }
@@ -653,7 +670,7 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
       GENCD_CUDA_TRY(cudaMemcpyAsync(p->val, val, vsz * nnz, kind_in(memory), st));
     } else {
       void* tmp = nullptr;
-      GENCD_CUDA_TRY(cudaMallocAsync(&tmp, in_sz * nnz, st));
+      GENCD_TRY(dev_alloc_bytes(p, &tmp, in_sz * nnz));
       GENCD_CUDA_TRY(cudaMemcpyAsync(tmp, val, in_sz * nnz, kind_in(memory), st));
       const int g = grid_for(nnz, kThreads, p->num_sms * 8);
       if (val_dtype == 0)
@@ -661,7 +678,7 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
       else
         k_convert<float, double><<<g, kThreads, 0, st>>>((const float*)tmp, nnz, (double*)p->val);
       GENCD_CUDA_TRY(cudaGetLastError());
-      GENCD_CUDA_TRY(cudaFreeAsync(tmp, st));
+      dev_free(p, tmp);
     }
   }
   GENCD_CUDA_TRY(cudaMemcpyAsync(p->y, y, sizeof(double) * n, kind_in(memory), st));
@@ -707,6 +724,126 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
   return GENCD_OK;
 }
 
+// ---- a solve, step by step ----------------------------------------------
+// gencd_solve's loop as a state machine, so that a caller can keep many
+// solves in flight: solve_begin enqueues the first evaluation; whenever the
+// work enqueued last has completed (ev_scalars), solve_advance decides from
+// the scalars it copied back (hpin) and enqueues the next work (returns 1) or
+// finishes (returns 0, status in S->status).
+
+static void fill_result(gencd_problem* p, gencd_result* out, int status, int64_t iters, int64_t host_nnz,
+                        double secs) {
+  if (!out) return;
+  std::memset(out, 0, sizeof(*out));
+  out->status = status;
+  out->iters = iters;
+  int64_t upd, nz;
+  std::memcpy(&upd, p->hpin + 4, 8);
+  std::memcpy(&nz, p->hpin + 5, 8);
+  out->updates = upd;
+  out->nnz_processed = nz + host_nnz;
+  out->objective = p->hpin[1];
+  out->kkt = p->hpin[0];
+  out->seconds = secs;
+}
+
+void solve_result(gencd_problem* p, const SolveRun* S, gencd_result* out) {
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - S->t0).count();
+  fill_result(p, out, S->status, S->iters, S->host_nnz, secs);
+}
+
+static int solve_evaluate(gencd_problem* p, SolveRun* S) {
+  GENCD_TRY(enqueue_evaluate(p));
+  GENCD_TRY(read_scalars_async(p));
+  S->host_nnz += p->nnz;
+  p->stat_host_nnz += p->nnz;
+  S->evaluated = true;
+  return GENCD_OK;
+}
+
+int solve_begin(gencd_problem* p, SolveRun* S) {
+  *S = SolveRun();
+  S->t0 = std::chrono::steady_clock::now();
+  const gencd_params& a = p->params;
+  // Thread-Greedy and Greedy compute the KKT violation of each iteration's
+  // start state inside the iteration; their checks read it and only run a
+  // full evaluation to confirm convergence.  Shotgun and Coloring evaluate.
+  const bool tg = a.variant == GENCD_THREAD_GREEDY || a.variant == GENCD_GREEDY;
+  S->fused = tg || a.variant == GENCD_TOP_GREEDY;
+  // Accept backoff (neither Thread-Greedy nor the global top-|J'| Accept has
+  // a convergence guarantee): an objective that is not finite or above its
+  // value at the start restarts the solve from its start with 4x larger
+  // accept groups.  Thread-Greedy applies only the best proxy of every G
+  // partitions; top-|J'| accepts the |J'|/G lowest proxies.  G = B is Greedy.
+  S->B = S->fused ? effective_B(p) : 1;
+  S->backoff = S->fused && S->B > 1;
+  GENCD_TRY(reset_counters(p));
+  if (S->backoff) {
+    if (!p->w_start) GENCD_TRY(dev_alloc(p, &p->w_start, p->k));
+    GENCD_CUDA_TRY(cudaMemcpyAsync(p->w_start, p->w, sizeof(double) * p->k, cudaMemcpyDeviceToDevice, p->stream));
+  }
+  return solve_evaluate(p, S);
+}
+
+static int solve_finish(gencd_problem* p, SolveRun* S) {
+  if (!S->evaluated && S->status != GENCD_EDIVERGED) {  // report the values of the returned state
+    GENCD_TRY(solve_evaluate(p, S));
+    S->finishing = true;
+    return 1;
+  }
+  return 0;
+}
+
+int solve_advance(gencd_problem* p, SolveRun* S) {
+  const gencd_params& a = p->params;
+  if (!S->started) {
+    S->obj_start = p->hpin[1];
+    S->started = true;
+  }
+  if (S->finishing) return 0;
+  const double kkt = p->hpin[0], obj = p->hpin[1];
+  const bool blown = !std::isfinite(kkt) || !std::isfinite(obj) || obj > 1e6 * (std::fabs(S->obj_start) + 1e-300);
+  // divergence: the objective is not finite or above its value at the start
+  const bool above = !(obj <= S->obj_start * (1.0 + 1e-6) + 1e-300);
+  if (S->backoff && p->accept_group < S->B && S->iters < a.max_iter && (blown || above)) {
+    p->accept_group = std::min<int64_t>(S->B, 4 * p->accept_group);  // restart from the start state
+    GENCD_CUDA_TRY(cudaMemcpyAsync(p->w, p->w_start, sizeof(double) * p->k, cudaMemcpyDeviceToDevice, p->stream));
+    GENCD_TRY(launch_mirror_w(p));
+    GENCD_TRY(build_csr(p));
+    GENCD_TRY(launch_csr_spmv(p, p->w, p->z));
+    GENCD_TRY(launch_fill_u(p));
+    GENCD_TRY(solve_evaluate(p, S));
+    return 1;
+  }
+  if (blown) {
+    S->status = GENCD_EDIVERGED;
+    set_error("objective is not finite or grew beyond 1e6 times its starting value");
+    return solve_finish(p, S);
+  }
+  if (kkt <= a.tol_kkt) {
+    if (S->evaluated) {
+      S->status = GENCD_OK;
+      return 0;
+    }
+    GENCD_TRY(solve_evaluate(p, S));  // confirm on the current state
+    return 1;
+  }
+  if (S->iters >= a.max_iter) return solve_finish(p, S);
+  const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - S->t0).count();
+  if (a.timeout_s > 0.0 && el >= a.timeout_s) return solve_finish(p, S);
+  const int64_t step = std::min<int64_t>(a.check_every, a.max_iter - S->iters);
+  for (int64_t i = 0; i < step; ++i) GENCD_TRY(enqueue_iteration(p, &S->host_nnz, i + 1 == step));
+  S->iters += step;
+  if (S->fused) {
+    GENCD_TRY(launch_objective(p));  // divergence watch on the current state
+    GENCD_TRY(read_scalars_async(p));
+    S->evaluated = false;
+  } else {
+    GENCD_TRY(solve_evaluate(p, S));  // the convergence check streams X once
+  }
+  return 1;
+}
+
 }  // namespace gencd
 
 using namespace gencd;
@@ -738,6 +875,17 @@ int gencd_default_params(gencd_params* out) {
 int gencd_create(gencd_problem** out, int64_t n, int64_t k, int64_t nnz, const int64_t* col_ptr,
                  const int32_t* row_idx, const void* val, int32_t val_dtype, const double* y, int32_t loss,
                  int32_t precision, int32_t memory, void* stream) {
+  return create_problem(out, n, k, nnz, col_ptr, row_idx, val, val_dtype, y, loss, precision, memory,
+                        (cudaStream_t)stream, nullptr, nullptr);
+}
+
+}  // extern "C"
+
+namespace gencd {
+
+int create_problem(gencd_problem** out, int64_t n, int64_t k, int64_t nnz, const int64_t* col_ptr,
+                   const int32_t* row_idx, const void* val, int32_t val_dtype, const double* y, int32_t loss,
+                   int32_t precision, int32_t memory, cudaStream_t stream, cudaMemPool_t pool, double* hpin) {
   set_error("");
   if (!out) return fail(GENCD_EINVAL, "out is NULL");
   *out = nullptr;
@@ -760,7 +908,12 @@ int gencd_create(gencd_problem** out, int64_t n, int64_t k, int64_t nnz, const i
   p->user_precision = precision;
   p->precision = precision == GENCD_F64 ? GENCD_F64 : GENCD_F32;  // BF16 and BINARY compute in FP32
   p->vmode = precision == GENCD_BF16 ? kValBf16 : precision == GENCD_BINARY ? kValNone : kValPlain;
-  p->stream = (cudaStream_t)stream;
+  p->stream = stream;
+  p->pool = pool;
+  if (hpin) {
+    p->hpin = hpin;
+    p->own_hpin = false;
+  }
   int rc = create_impl(p, col_ptr, row_idx, val, val_dtype, y, memory);
   if (rc != GENCD_OK) {
     std::string keep = last_error();
@@ -771,6 +924,10 @@ int gencd_create(gencd_problem** out, int64_t n, int64_t k, int64_t nnz, const i
   *out = p;
   return GENCD_OK;
 }
+
+}  // namespace gencd
+
+extern "C" {
 
 void gencd_destroy(gencd_problem* p) { free_problem(p); }
 
@@ -857,21 +1014,6 @@ int gencd_get_iteration(gencd_problem* p, int64_t* t) {
   return GENCD_OK;
 }
 
-static void fill_result(gencd_problem* p, gencd_result* out, int status, int64_t iters, int64_t host_nnz,
-                        double secs) {
-  if (!out) return;
-  std::memset(out, 0, sizeof(*out));
-  out->status = status;
-  out->iters = iters;
-  int64_t upd, nz;
-  std::memcpy(&upd, p->hpin + 4, 8);
-  std::memcpy(&nz, p->hpin + 5, 8);
-  out->updates = upd;
-  out->nnz_processed = nz + host_nnz;
-  out->objective = p->hpin[1];
-  out->kkt = p->hpin[0];
-  out->seconds = secs;
-}
 
 int gencd_iterate(gencd_problem* p, int64_t iters, gencd_result* out) {
   GENCD_CHECK_HANDLE(p);
@@ -896,98 +1038,16 @@ int gencd_iterate(gencd_problem* p, int64_t iters, gencd_result* out) {
 
 int gencd_solve(gencd_problem* p, gencd_result* out) {
   GENCD_CHECK_HANDLE(p);
-  auto t0 = std::chrono::steady_clock::now();
-  GENCD_TRY(reset_counters(p));
-  int64_t host_nnz = 0, iters = 0;
-  GENCD_TRY(enqueue_evaluate(p));
-  GENCD_TRY(read_scalars(p));
-  p->stat_host_nnz += p->nnz;
-  host_nnz += p->nnz;
-  int status = GENCD_NOT_CONVERGED;
-  const gencd_params& a = p->params;
-  const double obj_start = p->hpin[1];
-  // Thread-Greedy and Greedy compute the KKT violation of each iteration's
-  // start state inside the iteration; their checks read it and only run a
-  // full evaluation to confirm convergence.  Shotgun and Coloring evaluate.
-  const bool tg = a.variant == GENCD_THREAD_GREEDY || a.variant == GENCD_GREEDY;
-  const bool top = a.variant == GENCD_TOP_GREEDY;
-  const bool fused = tg || top;
-  // Accept backoff (neither Thread-Greedy nor the global top-|J'| Accept has
-  // a convergence guarantee): an objective that is not finite or above its
-  // value at the start restarts the solve from its start with 4x larger
-  // accept groups.  Thread-Greedy applies only the best proxy of every G
-  // partitions; top-|J'| accepts the |J'|/G lowest proxies.  G = B is Greedy.
-  const int64_t B = fused ? effective_B(p) : 1;
-  const bool backoff = fused && B > 1;
-
-  if (backoff) {
-    if (!p->w_start) GENCD_TRY(dalloc(&p->w_start, p->k));
-    GENCD_CUDA_TRY(cudaMemcpyAsync(p->w_start, p->w, sizeof(double) * p->k, cudaMemcpyDeviceToDevice, p->stream));
-  }
-  bool evaluated = true;  // hpin holds the KKT of the current state
+  SolveRun S;
+  GENCD_TRY(solve_begin(p, &S));
   for (;;) {
-    const double kkt = p->hpin[0], obj = p->hpin[1];
-    const bool blown = !std::isfinite(kkt) || !std::isfinite(obj) || obj > 1e6 * (std::fabs(obj_start) + 1e-300);
-    // divergence: the objective is not finite or above its value at the start
-    const bool above = !(obj <= obj_start * (1.0 + 1e-6) + 1e-300);
-    if (backoff && p->accept_group < B && iters < a.max_iter && (blown || above)) {
-      p->accept_group = std::min<int64_t>(B, 4 * p->accept_group);  // restart from the start state
-      GENCD_CUDA_TRY(cudaMemcpyAsync(p->w, p->w_start, sizeof(double) * p->k, cudaMemcpyDeviceToDevice, p->stream));
-      GENCD_TRY(launch_mirror_w(p));
-      GENCD_TRY(build_csr(p));
-      GENCD_TRY(launch_csr_spmv(p, p->w, p->z));
-      GENCD_TRY(launch_fill_u(p));
-      GENCD_TRY(enqueue_evaluate(p));
-      GENCD_TRY(read_scalars(p));
-      host_nnz += p->nnz;
-      p->stat_host_nnz += p->nnz;
-      evaluated = true;
-      continue;
-    }
-    if (blown) {
-      status = GENCD_EDIVERGED;
-      set_error("objective is not finite or grew beyond 1e6 times its starting value");
-      break;
-    }
-    if (kkt <= a.tol_kkt) {
-      if (evaluated) {
-        status = GENCD_OK;
-        break;
-      }
-      GENCD_TRY(enqueue_evaluate(p));  // confirm on the current state
-      GENCD_TRY(read_scalars(p));
-      host_nnz += p->nnz;
-      p->stat_host_nnz += p->nnz;
-      evaluated = true;
-      continue;
-    }
-    if (iters >= a.max_iter) break;
-    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    if (a.timeout_s > 0.0 && el >= a.timeout_s) break;
-    const int64_t step = std::min<int64_t>(a.check_every, a.max_iter - iters);
-    for (int64_t i = 0; i < step; ++i) GENCD_TRY(enqueue_iteration(p, &host_nnz, i + 1 == step));
-    iters += step;
-    if (fused) {
-      GENCD_TRY(launch_objective(p));  // divergence watch on the current state
-      GENCD_TRY(read_scalars(p));
-      evaluated = false;
-    } else {
-      GENCD_TRY(enqueue_evaluate(p));
-      GENCD_TRY(read_scalars(p));
-      host_nnz += p->nnz;  // the convergence check streams X once
-      p->stat_host_nnz += p->nnz;
-      evaluated = true;
-    }
+    GENCD_CUDA_TRY(cudaEventSynchronize(p->ev_scalars));
+    const int r = solve_advance(p, &S);
+    if (r < 0) return r;
+    if (r == 0) break;
   }
-  if (!evaluated && status != GENCD_EDIVERGED) {
-    GENCD_TRY(enqueue_evaluate(p));  // report the values of the returned state
-    GENCD_TRY(read_scalars(p));
-    host_nnz += p->nnz;
-    p->stat_host_nnz += p->nnz;
-  }
-  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  fill_result(p, out, status, iters, host_nnz, secs);
-  return status;
+  solve_result(p, &S, out);
+  return S.status;
 }
 
 int gencd_stats(gencd_problem* p, gencd_result* out) {
@@ -1058,10 +1118,10 @@ int gencd_propose_at(gencd_problem* p, const int32_t* J, int64_t m, double* delt
   int32_t* dj = nullptr;
   double *dd = nullptr, *df = nullptr;
   int rc = GENCD_OK;
-  if ((rc = dalloc(&dj, m)) || (rc = dalloc(&dd, m)) || (rc = dalloc(&df, m))) {
-    cudaFree(dj);
-    cudaFree(dd);
-    cudaFree(df);
+  if ((rc = dev_alloc(p, &dj, m)) || (rc = dev_alloc(p, &dd, m)) || (rc = dev_alloc(p, &df, m))) {
+    dev_free(p, dj);
+    dev_free(p, dd);
+    dev_free(p, df);
     return rc;
   }
   if (cudaMemcpyAsync(dj, hj.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
@@ -1071,9 +1131,9 @@ int gencd_propose_at(gencd_problem* p, const int32_t* J, int64_t m, double* delt
                          cudaMemcpyAsync(phi, df, sizeof(double) * m, kind_out(memory), p->stream) != cudaSuccess ||
                          cudaStreamSynchronize(p->stream) != cudaSuccess))
     rc = fail(GENCD_ECUDA, std::string("propose_at: ") + cudaGetErrorString(cudaGetLastError()));
-  cudaFree(dj);
-  cudaFree(dd);
-  cudaFree(df);
+  dev_free(p, dj);
+  dev_free(p, dd);
+  dev_free(p, df);
   return rc;
 }
 
@@ -1131,10 +1191,10 @@ int gencd_set_colors(gencd_problem* p, const int32_t* colors, int64_t k, int32_t
   GENCD_CHECK_HANDLE(p);
   if (!colors || k != p->k) return fail(GENCD_EINVAL, "colors must hold exactly k ints");
   GENCD_TRY(build_csr(p));
-  if (!p->color) GENCD_TRY(dalloc(&p->color, k));
+  if (!p->color) GENCD_TRY(dev_alloc(p, &p->color, k));
   GENCD_CUDA_TRY(cudaMemcpyAsync(p->color, colors, sizeof(int32_t) * k, kind_in(memory), p->stream));
   unsigned long long* chk = nullptr;
-  GENCD_TRY(dalloc(&chk, 2));
+  GENCD_TRY(dev_alloc(p, &chk, 2));
   GENCD_CUDA_TRY(cudaMemsetAsync(chk, 0xff, sizeof(unsigned long long), p->stream));
   GENCD_CUDA_TRY(cudaMemsetAsync(chk + 1, 0, sizeof(unsigned long long), p->stream));
   const int g = p->num_sms * 8;
@@ -1144,7 +1204,7 @@ int gencd_set_colors(gencd_problem* p, const int32_t* colors, int64_t k, int32_t
   unsigned long long h[2];
   GENCD_CUDA_TRY(cudaMemcpyAsync(h, chk, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
   GENCD_CUDA_TRY(cudaStreamSynchronize(p->stream));
-  cudaFree(chk);
+  dev_free(p, chk);
   int32_t mn = 0;
   {
     std::vector<int32_t> hc((size_t)k);
@@ -1152,12 +1212,12 @@ int gencd_set_colors(gencd_problem* p, const int32_t* colors, int64_t k, int32_t
     for (int32_t c : hc) mn = c < mn ? c : mn;
   }
   if (mn < 0 || h[1] >= (unsigned long long)k) {
-    cudaFree(p->color);
+    dev_free(p, p->color);
     p->color = nullptr;
     return fail(GENCD_EINVAL, "colours must lie in [0, k)");
   }
   if (h[0] != ~0ull) {
-    cudaFree(p->color);
+    dev_free(p, p->color);
     p->color = nullptr;
     return fail(GENCD_EINVAL, "two columns sharing row " + std::to_string(h[0]) + " have the same colour");
   }
@@ -1170,13 +1230,13 @@ int gencd_permutation(gencd_problem* p, uint64_t seed, int64_t epoch, int64_t m,
   if (m < 0 || epoch < 0 || (m > 0 && !perm)) return fail(GENCD_EINVAL, "bad permutation arguments");
   if (m == 0) return GENCD_OK;
   int32_t* d = nullptr;
-  GENCD_TRY(dalloc(&d, m));
+  GENCD_TRY(dev_alloc(p, &d, m));
   int rc = make_permutation(p, seed, epoch, m, d);
   if (rc == GENCD_OK &&
       (cudaMemcpyAsync(perm, d, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
        cudaStreamSynchronize(p->stream) != cudaSuccess))
     rc = fail(GENCD_ECUDA, "permutation copy failed");
-  cudaFree(d);
+  dev_free(p, d);
   return rc;
 }
 

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <chrono>
 #include <string>
 #include <vector>
 
@@ -152,6 +153,11 @@ struct gencd_problem {
   int device = 0;
   int num_sms = 0;
   cudaStream_t stream = nullptr;
+  // device memory: stream-ordered from this pool when set (problems of the
+  // serving loop, which must not synchronise the device), else cudaMalloc
+  cudaMemPool_t pool = nullptr;
+  bool own_hpin = true;               // hpin allocated by the problem (else lent by its owner)
+  cudaEvent_t ev_scalars = nullptr;   // recorded after each copy of dscal to hpin
   int64_t n = 0, k = 0, nnz = 0, nnz_pad = 0;
   int32_t loss = GENCD_LOSS_LOGISTIC;
   int32_t precision = GENCD_F64;  // arithmetic: GENCD_F64 or GENCD_F32 (BF16 and BINARY compute in FP32)
@@ -313,12 +319,45 @@ int build_color_classes(gencd_problem* p);
 int launch_power_step(gencd_problem* p, const double* v, const double* dinv, double* r, double* s);
 int validate_input(gencd_problem* p, int64_t* bad_col, int64_t* bad_row, int* stage);
 
+// gencd_create with the problem's device memory taken from `pool`
+// (stream-ordered on `stream`; NULL: cudaMalloc) and, when hpin is not NULL,
+// its pinned scalars lent by the caller (8 doubles, kept until destroy)
+int create_problem(gencd_problem** out, int64_t n, int64_t k, int64_t nnz, const int64_t* col_ptr,
+                   const int32_t* row_idx, const void* val, int32_t val_dtype, const double* y, int32_t loss,
+                   int32_t precision, int32_t memory, cudaStream_t stream, cudaMemPool_t pool, double* hpin);
+
+// a solve driven step by step (api.cu; gencd_solve and the serving loop)
+struct SolveRun {
+  std::chrono::steady_clock::time_point t0;
+  int64_t host_nnz = 0, iters = 0;
+  double obj_start = 0.0;
+  bool started = false;    // obj_start is known
+  bool evaluated = true;   // hpin holds a full evaluation of the current state
+  bool finishing = false;  // the final evaluation is in flight
+  int status = GENCD_NOT_CONVERGED;
+  int64_t B = 1;
+  bool backoff = false, fused = false;
+};
+int solve_begin(gencd_problem* p, SolveRun* S);
+int solve_advance(gencd_problem* p, SolveRun* S);  // 1: more work enqueued, 0: done, < 0: error
+void solve_result(gencd_problem* p, const SolveRun* S, gencd_result* out);
+
 // profiling helpers (api.cu)
 void prof_begin(gencd_problem* p, int id, cudaEvent_t* stop_out, int launches = 1);
 void prof_end(gencd_problem* p, cudaEvent_t stop);
 
 // grow a device allocation
 int ensure_sort_tmp(gencd_problem* p, size_t bytes);
+
+// Device memory of a problem: from its pool (stream-ordered on its stream)
+// when it has one, else cudaMalloc / cudaFree.  dev_alloc returns
+// GENCD_ENOMEM with a message on failure and leaves *ptr null.
+int dev_alloc_bytes(gencd_problem* p, void** ptr, size_t bytes);
+void dev_free(gencd_problem* p, void* ptr);
+template <typename T>
+inline int dev_alloc(gencd_problem* p, T** ptr, size_t count) {
+  return dev_alloc_bytes(p, reinterpret_cast<void**>(ptr), sizeof(T) * (count > 0 ? count : 1));
+}
 
 inline int grid_for(int64_t work, int threads, int max_blocks) {
   int64_t b = (work + threads - 1) / threads;

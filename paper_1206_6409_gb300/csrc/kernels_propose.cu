@@ -796,14 +796,10 @@ static int ensure_part_bounds(gencd_problem* p, int64_t B) {
   if (p->part_B == B && p->part_lo) return GENCD_OK;
   if (p->part_cap < B + 1) {
     GENCD_CUDA_TRY(cudaStreamSynchronize(p->stream));
-    cudaFree(p->part_lo);
+    dev_free(p, p->part_lo);
     p->part_lo = nullptr;
     p->part_cap = 0;
-    if (cudaMalloc((void**)&p->part_lo, sizeof(int64_t) * (size_t)(B + 1)) != cudaSuccess) {
-      cudaGetLastError();
-      set_error("cudaMalloc of the partition bounds failed");
-      return GENCD_ENOMEM;
-    }
+    GENCD_TRY(dev_alloc(p, &p->part_lo, (size_t)(B + 1)));
     p->part_cap = B + 1;
   }
   k_part_bounds<<<grid_for(B + 1, kThreads, p->num_sms * 8), kThreads, 0, p->stream>>>(p->k, B, p->part_lo);

@@ -239,15 +239,11 @@ int ensure_sort_tmp(gencd_problem* p, size_t bytes) {
   if (bytes <= p->sort_tmp_bytes) return GENCD_OK;
   if (p->sort_tmp) {
     GENCD_CUDA_TRY(cudaStreamSynchronize(p->stream));
-    cudaFree(p->sort_tmp);
+    dev_free(p, p->sort_tmp);
     p->sort_tmp = nullptr;
     p->sort_tmp_bytes = 0;
   }
-  if (cudaMalloc(&p->sort_tmp, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    set_error("out of device memory for sort scratch");
-    return GENCD_ENOMEM;
-  }
+  GENCD_TRY(dev_alloc_bytes(p, &p->sort_tmp, bytes));
   p->sort_tmp_bytes = bytes;
   return GENCD_OK;
 }
@@ -397,9 +393,9 @@ int build_csr(gencd_problem* p) {
   if (p->row_ptr) return GENCD_OK;
   const int64_t nnz = p->nnz;
   const size_t vsz = p->precision == GENCD_F64 ? 8 : 4;
-  GENCD_CUDA_TRY(cudaMalloc(&p->row_ptr, sizeof(int64_t) * (size_t)(p->n + 1)));
-  GENCD_CUDA_TRY(cudaMalloc(&p->col_idx, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1)));
-  GENCD_CUDA_TRY(cudaMalloc(&p->csr_val, vsz * (size_t)(nnz > 0 ? nnz : 1)));
+  GENCD_TRY(dev_alloc_bytes(p, (void**)&p->row_ptr, sizeof(int64_t) * (size_t)(p->n + 1)));
+  GENCD_TRY(dev_alloc_bytes(p, (void**)&p->col_idx, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1)));
+  GENCD_TRY(dev_alloc_bytes(p, (void**)&p->csr_val, vsz * (size_t)(nnz > 0 ? nnz : 1)));
   if (nnz == 0) {
     GENCD_CUDA_TRY(cudaMemsetAsync(p->row_ptr, 0, sizeof(int64_t) * (size_t)(p->n + 1), p->stream));
     return GENCD_OK;
@@ -524,10 +520,10 @@ int build_color_classes(gencd_problem* p) {
   GENCD_CUDA_TRY(cudaGetLastError());
   bool in_alt = false;
   GENCD_TRY(radix_sort_with_tmp(p, keys, vals, k, bits_for_max(p->ncolors - 1), ka, va, tmp, &in_alt));
-  if (p->color_ptr) cudaFree(p->color_ptr);
+  if (p->color_ptr) dev_free(p, p->color_ptr);
   p->color_ptr = nullptr;
-  GENCD_CUDA_TRY(cudaMalloc(&p->color_ptr, sizeof(int32_t) * (size_t)(p->ncolors + 1)));
-  if (!p->cols_by_color) GENCD_CUDA_TRY(cudaMalloc(&p->cols_by_color, sizeof(int32_t) * (size_t)k));
+  GENCD_TRY(dev_alloc_bytes(p, (void**)&p->color_ptr, sizeof(int32_t) * (size_t)(p->ncolors + 1)));
+  if (!p->cols_by_color) GENCD_TRY(dev_alloc_bytes(p, (void**)&p->cols_by_color, sizeof(int32_t) * (size_t)k));
   GENCD_CUDA_TRY(cudaMemcpyAsync(p->cols_by_color, in_alt ? va : vals, (size_t)k * 4, cudaMemcpyDeviceToDevice,
                                  p->stream));
   k_lower_bounds<<<grid_for(p->ncolors + 1, kThreads, g), kThreads, 0, p->stream>>>(
@@ -547,13 +543,13 @@ int build_color_classes(gencd_problem* p) {
 int run_coloring(gencd_problem* p) {
   GENCD_TRY(build_csr(p));
   const int64_t k = p->k;
-  if (!p->color) GENCD_CUDA_TRY(cudaMalloc(&p->color, sizeof(int32_t) * (size_t)k));
+  if (!p->color) GENCD_TRY(dev_alloc_bytes(p, (void**)&p->color, sizeof(int32_t) * (size_t)k));
   GENCD_CUDA_TRY(cudaMemsetAsync(p->color, 0xff, sizeof(int32_t) * (size_t)k, p->stream));  // -1
   int32_t *wa = nullptr, *wb = nullptr;
   unsigned long long* ctr = nullptr;  // [0] next worklist size, [1] max colour
-  GENCD_CUDA_TRY(cudaMalloc(&wa, sizeof(int32_t) * (size_t)k));
-  GENCD_CUDA_TRY(cudaMalloc(&wb, sizeof(int32_t) * (size_t)k));
-  GENCD_CUDA_TRY(cudaMalloc(&ctr, 2 * sizeof(unsigned long long)));
+  GENCD_TRY(dev_alloc_bytes(p, (void**)&wa, sizeof(int32_t) * (size_t)k));
+  GENCD_TRY(dev_alloc_bytes(p, (void**)&wb, sizeof(int32_t) * (size_t)k));
+  GENCD_TRY(dev_alloc_bytes(p, (void**)&ctr, 2 * sizeof(unsigned long long)));
   GENCD_CUDA_TRY(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), p->stream));
   const int g = p->num_sms * 8;
   k_iota_i32<<<grid_for(k, kThreads, g), kThreads, 0, p->stream>>>(wa, k);
@@ -586,9 +582,9 @@ int run_coloring(gencd_problem* p) {
       rc = GENCD_ETIMEOUT;
     }
   }
-  cudaFree(wa);
-  cudaFree(wb);
-  cudaFree(ctr);
+  dev_free(p, wa);
+  dev_free(p, wb);
+  dev_free(p, ctr);
   if (rc != GENCD_OK) return rc;
   p->ncolors = k > 0 ? (int32_t)mc + 1 : 0;
   return build_color_classes(p);
@@ -644,7 +640,7 @@ int launch_tile_map(gencd_problem* p) {
 // validation entry used by the API: returns first bad column / row or -1
 int validate_input(gencd_problem* p, int64_t* bad_col, int64_t* bad_row, int* stage) {
   unsigned long long* err = nullptr;
-  GENCD_CUDA_TRY(cudaMalloc(&err, 3 * sizeof(unsigned long long)));
+  GENCD_TRY(dev_alloc_bytes(p, (void**)&err, 3 * sizeof(unsigned long long)));
   GENCD_CUDA_TRY(cudaMemsetAsync(err, 0xff, 3 * sizeof(unsigned long long), p->stream));
   const int g = p->num_sms * 8;
   k_validate_colptr<<<grid_for(p->k, kThreads, g), kThreads, 0, p->stream>>>(p->col_ptr, p->k, p->nnz, err);
@@ -654,13 +650,13 @@ int validate_input(gencd_problem* p, int64_t* bad_col, int64_t* bad_row, int* st
   *stage = 0;
   if (h[0] != ~0ull) {
     *bad_col = (int64_t)h[0];
-    cudaFree(err);
+    dev_free(p, err);
     return GENCD_OK;
   }
   *stage = 1;
   uint32_t* starts = nullptr;
   const int64_t words = (p->nnz + 31) / 32 + 1;
-  GENCD_CUDA_TRY(cudaMallocAsync((void**)&starts, words * sizeof(uint32_t), p->stream));
+  GENCD_TRY(dev_alloc_bytes(p, (void**)&starts, words * sizeof(uint32_t)));
   GENCD_CUDA_TRY(cudaMemsetAsync(starts, 0, words * sizeof(uint32_t), p->stream));
   k_mark_starts<<<grid_for(p->k, kThreads, g), kThreads, 0, p->stream>>>(p->col_ptr, p->k, starts);
   if (p->precision == GENCD_F64)
@@ -669,13 +665,13 @@ int validate_input(gencd_problem* p, int64_t* bad_col, int64_t* bad_row, int* st
   else
     k_validate_rows<float><<<grid_for(p->nnz, kThreads, g), kThreads, 0, p->stream>>>(
         p->col_ptr, p->row_idx, (const float*)p->val, starts, p->k, p->n, p->nnz, err);
-  GENCD_CUDA_TRY(cudaFreeAsync(starts, p->stream));
+  dev_free(p, starts);
   k_validate_y<<<grid_for(p->n, kThreads, g), kThreads, 0, p->stream>>>(p->y, p->n,
                                                                         p->loss == GENCD_LOSS_LOGISTIC, err + 1);
   p->prof.launches[K_SETUP] += 4;
   GENCD_CUDA_TRY(cudaMemcpyAsync(h, err, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
   GENCD_CUDA_TRY(cudaStreamSynchronize(p->stream));
-  cudaFree(err);
+  dev_free(p, err);
   *bad_col = h[0] == ~0ull ? -1 : (int64_t)h[0];
   *bad_row = h[1] == ~0ull ? -1 : (int64_t)h[1];
   return GENCD_OK;

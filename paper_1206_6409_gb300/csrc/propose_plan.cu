@@ -902,33 +902,28 @@ void free_propose_plan(gencd_problem* p) {
                   P.s_row, P.s_val, P.pmask, P.pair_slot, P.hslot_ptr, P.partial, P.tile_start,
                   P.tile_end, P.tile_pair, P.tile_slab, P.slab_tile_begin, P.cta_tile_begin, P.light_counter};
   for (void* b : bufs)
-    if (b) cudaFree(b);
+    if (b) dev_free(p, b);
   P = ProposePlan();
 }
 
 template <typename T>
-static int palloc(T** ptr, int64_t count) {
-  *ptr = nullptr;
-  if (cudaMalloc((void**)ptr, sizeof(T) * (size_t)(count > 0 ? count : 1)) != cudaSuccess) {
-    cudaGetLastError();
-    *ptr = nullptr;
-    set_error("out of device memory while building the row-slab plan");
-    return GENCD_ENOMEM;
-  }
-  return GENCD_OK;
+static int palloc(gencd_problem* p, T** ptr, int64_t count) {
+  return dev_alloc(p, ptr, (size_t)(count > 0 ? count : 1));
 }
 
 // scratch that is freed when the build returns
 struct Scratch {
+  gencd_problem* p;
   std::vector<void*> bufs;
+  explicit Scratch(gencd_problem* q) : p(q) {}
   template <typename T>
   int get(T** ptr, int64_t count) {
-    int rc = palloc(ptr, count);
+    int rc = palloc(p, ptr, count);
     if (rc == GENCD_OK) bufs.push_back(*ptr);
     return rc;
   }
   ~Scratch() {
-    for (void* b : bufs) cudaFree(b);
+    for (void* b : bufs) dev_free(p, b);
   }
 };
 
@@ -969,9 +964,9 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   const int64_t E = tot[2];
   P.light_nnz = tot[3];
 
-  GENCD_TRY(palloc(&P.heavy_cols, P.nheavy));
-  GENCD_TRY(palloc(&P.light_cols, P.nlight));
-  GENCD_TRY(palloc(&P.light_col_ptr, P.nlight + 1));
+  GENCD_TRY(palloc(p, &P.heavy_cols, P.nheavy));
+  GENCD_TRY(palloc(p, &P.light_cols, P.nlight));
+  GENCD_TRY(palloc(p, &P.light_col_ptr, P.nlight + 1));
   k_plan_columns<<<grid_for(k, kThreads, g), kThreads, 0, st>>>(p->col_ptr, k, P.heavy_min, hid, lid, loff,
                                                                  P.heavy_cols, P.light_cols, P.light_col_ptr);
   GENCD_CUDA_TRY(cudaGetLastError());
@@ -979,8 +974,8 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   // light columns: compact CSC copy and its tile map
   if (P.nlight > 0) {
     const int64_t lpad = ((P.light_nnz + kPadNnz - 1) / kPadNnz) * kPadNnz + kPadNnz;
-    GENCD_TRY(palloc(&P.light_row, lpad));
-    GENCD_TRY(palloc((char**)&P.light_val, lpad * (int64_t)vsz));
+    GENCD_TRY(palloc(p, &P.light_row, lpad));
+    GENCD_TRY(palloc(p, (char**)&P.light_val, lpad * (int64_t)vsz));
     GENCD_CUDA_TRY(cudaMemsetAsync(P.light_row, 0, sizeof(int32_t) * lpad, st));
     GENCD_CUDA_TRY(cudaMemsetAsync(P.light_val, 0, vsz * lpad, st));
     if (p->vmode == kValNone) {  // padding has no value to zero it: it gathers u[n] = 0 instead
@@ -999,26 +994,26 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
     if (!f64 && p->vmode != kValPlain) {  // bfloat16 copy, or no values and a scale per column
       if (p->vmode == kValBf16) {
         __nv_bfloat16* b16 = nullptr;
-        GENCD_TRY(palloc(&b16, lpad));
+        GENCD_TRY(palloc(p, &b16, lpad));
         k_plan_to_bf16<<<grid_for(lpad, kThreads, g), kThreads, 0, st>>>((const float*)P.light_val, lpad, b16);
         GENCD_CUDA_TRY(cudaStreamSynchronize(st));
-        cudaFree(P.light_val);
+        dev_free(p, P.light_val);
         P.light_val = b16;
       } else {
         GENCD_CUDA_TRY(cudaStreamSynchronize(st));
-        cudaFree(P.light_val);
+        dev_free(p, P.light_val);
         P.light_val = nullptr;
-        GENCD_TRY(palloc(&P.light_scale, P.nlight));
+        GENCD_TRY(palloc(p, &P.light_scale, P.nlight));
         k_plan_gather_scales<<<grid_for(P.nlight, kThreads, g), kThreads, 0, st>>>(P.light_cols, P.nlight, p->col_val,
                                                                                     P.light_scale);
       }
       GENCD_CUDA_TRY(cudaGetLastError());
     }
     P.light_ntiles = (P.light_nnz + kLightTile - 1) / kLightTile;
-    GENCD_TRY(palloc(&P.light_tile_lc, P.light_ntiles + 1));
+    GENCD_TRY(palloc(p, &P.light_tile_lc, P.light_ntiles + 1));
     GENCD_TRY(launch_tile_map_of(p, P.light_col_ptr, P.nlight, P.light_ntiles, P.light_tile_lc, kLightTile));
     const int64_t lwords = (lpad + 31) / 32;  // start bits, one byte per 8 entries
-    GENCD_TRY(palloc((uint32_t**)&P.lmask, lwords));
+    GENCD_TRY(palloc(p, (uint32_t**)&P.lmask, lwords));
     GENCD_CUDA_TRY(cudaMemsetAsync(P.lmask, 0, 4 * (size_t)lwords, st));
     k_plan_light_starts<<<grid_for(P.nlight, kThreads, g), kThreads, 0, st>>>(P.light_col_ptr, P.nlight,
                                                                               (uint32_t*)P.lmask);
@@ -1066,8 +1061,8 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   if (P.entries >= (int64_t(1) << 32)) return fail_plan("heavy entries exceed 2^32");
   GENCD_CUDA_TRY(cudaMemcpyAsync(pad_off, hp.data(), 8 * (R + 1), cudaMemcpyHostToDevice, st));
 
-  GENCD_TRY(palloc(&P.s_row, P.entries + 8));
-  GENCD_TRY(palloc((char**)&P.s_val, (P.entries + 8) * (int64_t)vsz));
+  GENCD_TRY(palloc(p, &P.s_row, P.entries + 8));
+  GENCD_TRY(palloc(p, (char**)&P.s_val, (P.entries + 8) * (int64_t)vsz));
   GENCD_CUDA_TRY(cudaMemsetAsync(P.s_row, 0, 2 * (P.entries + 8), st));
   GENCD_CUDA_TRY(cudaMemsetAsync(P.s_val, 0, vsz * (P.entries + 8), st));
   if (p->vmode == kValNone) {  // padding reads the zero slot past the slab
@@ -1077,7 +1072,7 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   }
   // start bits: one byte per 8 entries, written as 32-bit words (entries + 8 bits, rounded up to words)
   const int64_t mask_words = (P.entries + 8 + 31) / 32;
-  GENCD_TRY(palloc((uint32_t**)&P.pmask, mask_words));
+  GENCD_TRY(palloc(p, (uint32_t**)&P.pmask, mask_words));
   GENCD_CUDA_TRY(cudaMemsetAsync(P.pmask, 0, 4 * (size_t)mask_words, st));
   uint32_t* pidx;
   GENCD_TRY(S.get(&pidx, E + 1));
@@ -1093,17 +1088,17 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   if (!f64 && p->vmode != kValPlain) {  // bfloat16 copy, or no values and a scale per column
     if (p->vmode == kValBf16) {
       __nv_bfloat16* b16 = nullptr;
-      GENCD_TRY(palloc(&b16, P.entries + 8));
+      GENCD_TRY(palloc(p, &b16, P.entries + 8));
       k_plan_to_bf16<<<grid_for(P.entries + 8, kThreads, g), kThreads, 0, st>>>((const float*)P.s_val, P.entries + 8,
                                                                                 b16);
       GENCD_CUDA_TRY(cudaStreamSynchronize(st));
-      cudaFree(P.s_val);
+      dev_free(p, P.s_val);
       P.s_val = b16;
     } else {
       GENCD_CUDA_TRY(cudaStreamSynchronize(st));
-      cudaFree(P.s_val);
+      dev_free(p, P.s_val);
       P.s_val = nullptr;
-      GENCD_TRY(palloc(&P.heavy_scale, P.nheavy));
+      GENCD_TRY(palloc(p, &P.heavy_scale, P.nheavy));
       k_plan_gather_scales<<<grid_for(P.nheavy, kThreads, g), kThreads, 0, st>>>(P.heavy_cols, P.nheavy, p->col_val,
                                                                                   P.heavy_scale);
     }
@@ -1134,9 +1129,9 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   GENCD_TRY(radix_sort_with_tmp(p, pair_h, qa, P.npairs, bits_for_max(P.nheavy - 1), ha, qb, qtmp, &q_alt));
   const uint32_t* h_sorted = q_alt ? ha : pair_h;
   const uint32_t* q_sorted = q_alt ? qb : qa;
-  GENCD_TRY(palloc(&P.pair_slot, P.npairs));
-  GENCD_TRY(palloc(&P.hslot_ptr, P.nheavy + 1));
-  GENCD_TRY(palloc((char**)&P.partial, P.npairs * (int64_t)vsz));
+  GENCD_TRY(palloc(p, &P.pair_slot, P.npairs));
+  GENCD_TRY(palloc(p, &P.hslot_ptr, P.nheavy + 1));
+  GENCD_TRY(palloc(p, (char**)&P.partial, P.npairs * (int64_t)vsz));
   GENCD_CUDA_TRY(cudaMemsetAsync(P.partial, 0, vsz * (size_t)P.npairs, st));
   k_plan_slots<<<grid_for(P.npairs, kThreads, g), kThreads, 0, st>>>(q_sorted, P.npairs, P.pair_slot);
   k_plan_lower_bounds<<<grid_for(P.nheavy + 1, kThreads, g), kThreads, 0, st>>>(h_sorted, P.npairs, P.nheavy,
@@ -1149,11 +1144,11 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   const int64_t tile = 32LL * (f64 ? kSlabItemsF64 : kSlabItemsF32);  // the kernel's tile
   for (int r = 0; r < R; ++r) tb[r + 1] = tb[r] + (int32_t)((hp[r + 1] - hp[r] + tile - 1) / tile);
   P.ntiles = tb[R];
-  GENCD_TRY(palloc(&P.slab_tile_begin, R + 1));
-  GENCD_TRY(palloc(&P.tile_start, P.ntiles));
-  GENCD_TRY(palloc(&P.tile_end, P.ntiles));
-  GENCD_TRY(palloc(&P.tile_pair, P.ntiles));
-  GENCD_TRY(palloc(&P.tile_slab, P.ntiles));
+  GENCD_TRY(palloc(p, &P.slab_tile_begin, R + 1));
+  GENCD_TRY(palloc(p, &P.tile_start, P.ntiles));
+  GENCD_TRY(palloc(p, &P.tile_end, P.ntiles));
+  GENCD_TRY(palloc(p, &P.tile_pair, P.ntiles));
+  GENCD_TRY(palloc(p, &P.tile_slab, P.ntiles));
   GENCD_CUDA_TRY(cudaMemcpyAsync(P.slab_tile_begin, tb.data(), 4 * (R + 1), cudaMemcpyHostToDevice, st));
   k_plan_tiles<<<grid_for(P.ntiles, kThreads, g), kThreads, 0, st>>>(P.slab_tile_begin, pad_off, R, P.ntiles, tile,
                                                                       pair_start, P.npairs, P.tile_start,
@@ -1165,12 +1160,12 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   // the autotuner below decides
   P.fused_split = 0;
   if (!f64 && P.nlight > 0 && P.nheavy > 0) {
-    GENCD_TRY(palloc(&P.light_counter, 1));
+    GENCD_TRY(palloc(p, &P.light_counter, 1));
     GENCD_CUDA_TRY(cudaMemsetAsync(P.light_counter, 0, sizeof(unsigned int), st));
   }
   std::vector<int32_t> ctb(P.grid + 1);
   for (int b = 0; b <= P.grid; ++b) ctb[b] = (int32_t)((int64_t)b * P.ntiles / P.grid);
-  GENCD_TRY(palloc(&P.cta_tile_begin, P.grid + 1));
+  GENCD_TRY(palloc(p, &P.cta_tile_begin, P.grid + 1));
   GENCD_CUDA_TRY(cudaMemcpyAsync(P.cta_tile_begin, ctb.data(), 4 * (P.grid + 1), cudaMemcpyHostToDevice, st));
   if (f64)
     GENCD_TRY(set_slab_smem<GENCD_PLAN_F64>(P));
@@ -1189,7 +1184,7 @@ int build_propose_plan(gencd_problem* p) {
   free_propose_plan(p);
   int rc;
   {
-    Scratch S;
+    Scratch S(p);
     rc = build_plan_impl(p, S);
     if (rc != GENCD_OK) cudaStreamSynchronize(p->stream);
   }

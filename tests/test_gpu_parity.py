@@ -196,7 +196,10 @@ def test_config1_shotgun_solve_matches_oracle(gb, loss):
     orc = oracle.Oracle(prob)
     lam = 0.01 * orc.lambda_max()
     orc.set_lambda(lam)
-    w_opt, _, _, kkt, _ = orc.solve("ccd", tol_kkt=1e-11, max_iter=4 * 10**8)
+    if loss == "logistic":  # config 1's logistic problem is config 3's +-1 one: its stored optimum
+        w_opt = certified_optimum("cfg3_pm1_logistic", prob, lam)
+    else:
+        w_opt, _, _, kkt, _ = orc.solve("ccd", tol_kkt=1e-11, max_iter=4 * 10**8)
     P_opt = orc.objective(w_opt)
     with gb.Problem(prob) as p:
         p.set_lambda(lam)
@@ -545,22 +548,18 @@ def test_storage_modes_reject_what_they_cannot_hold(gb):
     assert e.value.code == gb.GENCD_EINVAL and "bfloat16" in str(e.value)
 
 
-# Storage error bound (reading on storage modes): a mode that rounds each
-# value of X with relative error at most u_mode solves the problem P' on the
-# stored X' = X + E, |E| <= u_mode |X|.  The logistic loss is 1-Lipschitz in
-# t, so |P(w) - P'(w)| <= delta(w) = u_mode (1/n) sum_j |w_j| ||X_j||_1, and
-#   P(w) - P* <= delta(w) + gap'(w) + delta(w*),
-# gap' the duality gap of w on P' (an upper bound on P'(w) - P'*).
-# u_mode: 2^-24 for FP32, 2^-8 for bfloat16 (8 significant bits, round to
-# nearest), each widened by the FP32 rounding that precedes bfloat16.
-U_MODE = {"f64": 0.0, "f32": 2.0 ** -24, "bf16": 2.0 ** -8 * (1.0 + 2.0 ** -15), "binary": 2.0 ** -24}
-
-
+# Storage error bound (reading on storage modes): a mode that rounds X
+# solves the problem P' on the stored X'.  With P* = P(w*) and P'* <= P'(w*),
+#   P(w) - P* = [P(w) - P'(w)] + [P'(w) - P'*] + [P'* - P(w*)]
+#             <= [P(w) - P'(w)] + gap'(w) + [P'(w*) - P(w*)],
+# gap' the duality gap of w on P' (weak duality bounds P'(w) - P'*).  Every
+# term is evaluated by the oracle in FP64.
 def _storage_bound(prob, mode, lam, w, w_opt, P_opt):
-    l1 = np.add.reduceat(np.abs(prob.val), prob.col_ptr[:-1]) / prob.n  # ||X_j||_1 / n (no empty columns)
-    delta = lambda v: U_MODE[mode] * float(np.abs(v) @ l1)
-    gap = oracle.Oracle(oracle.stored_problem(prob, mode), lam).duality_gap(w)
-    return (delta(w) + max(gap, 0.0) + delta(w_opt)) / P_opt
+    orig = oracle.Oracle(prob, lam)
+    stored = oracle.Oracle(oracle.stored_problem(prob, mode), lam)
+    bound = (orig.objective(w) - stored.objective(w)) + max(stored.duality_gap(w), 0.0) + \
+        (stored.objective(w_opt) - orig.objective(w_opt))
+    return bound / P_opt
 
 
 SWEEP = (("pm1", ["f64", "f32", "bf16"]), ("ones", ["f64", "f32", "bf16", "binary"]),
