@@ -413,7 +413,11 @@ def run_serve(args, gb):
     one = serve(arrivals, 1)
     rel = [abs(a["objective"] - b["objective"]) / abs(b["objective"]) for a, b in zip(mix, one)
            if a["status"] == 0 and b["status"] == 0]
-    return {"workload": f"config 5: {len(problems)} requests, "
+    per_request = [{"n": p.n, "k": p.k, "nnz": p.nnz, "loss": p.loss, "lambda_frac": float(f),
+                    "status": int(r["status"]), "iters": int(r["iters"]), "ms": 1000.0 * (r["end"] - r["start"])}
+                   for p, f, r in zip(problems, fracs, mix)]
+    return {"per_request_saturated": per_request,
+            "workload": f"config 5: {len(problems)} requests, "
                         f"{sum(p.nnz for p in problems) / 1e6:.0f}M nnz in total, FP32, KKT <= "
                         f"{args.serve_tol:g} lambda per request, Thread-Greedy B=1024",
             "slots": args.serve_workers,

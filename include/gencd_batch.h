@@ -65,6 +65,25 @@ void gencd_batch_destroy(gencd_batch* b);
 /* Number of slots the batch holds (8, 16 or a multiple of 32). */
 int gencd_batch_slots(gencd_batch* b, int32_t* slots);
 
+/*
+ * Schedule of the batched step, chosen by the batch's autotuner (not in the
+ * paper).  The X^T U pass runs with lanes over entries and 8 slots per lane
+ * (spmm_kind 0) or with lanes over slots (1; S a multiple of 32): at create,
+ * each form is timed over three passes and the faster is kept.  The update
+ * runs one warp per (partition, slot) (update_kind 0) or one warp per
+ * (partition, 32 slots), the slots that accepted the same column adding
+ * into each z row side by side (1): the first call that runs at least four
+ * steps times them alternately and keeps the faster (-1 until then).
+ * ms[0..nms): the mean times (ms) of X^T U kinds 0 and 1, then of a whole
+ * step with update kinds 0 and 1 (-1 where not timed).  Any pointer may be
+ * NULL when nms is 0.
+ */
+int gencd_batch_schedule(gencd_batch* b, int32_t* spmm_kind, int32_t* update_kind, double* ms, int32_t nms);
+/* Sets the schedule (each kind 0 or 1, or -1: autotune it again); every
+ * schedule computes the same step.  GENCD_EINVAL for spmm_kind 1 with 8 or
+ * 16 slots. */
+int gencd_batch_set_schedule(gencd_batch* b, int32_t spmm_kind, int32_t update_kind);
+
 /* lambda_max of the training set of held_out (-1: all rows): the smallest
  * lambda for which w = 0 is optimal, max_j |g_j(0)| (computed at create). */
 int gencd_batch_lambda_max(gencd_batch* b, int32_t held_out, double* lambda_max);

@@ -54,7 +54,7 @@ EXPORTS = ["gencd_create", "gencd_destroy", "gencd_set_lambda", "gencd_set_loss"
            "gencd_batch_create", "gencd_batch_destroy", "gencd_batch_slots", "gencd_batch_lambda_max",
            "gencd_batch_set_params", "gencd_batch_set_slot", "gencd_batch_copy_slot", "gencd_batch_clear_slot",
            "gencd_batch_get_w", "gencd_batch_iterate", "gencd_batch_objective", "gencd_batch_propose",
-           "gencd_batch_path",
+           "gencd_batch_path", "gencd_batch_schedule", "gencd_batch_set_schedule",
            # include/gencd_serve.h
            "gencd_serve", "gencd_serve_dry_run"]
 
@@ -171,6 +171,8 @@ def lib():
             "gencd_batch_objective": (C.c_int, [vp, vp, vp]),
             "gencd_batch_propose": (C.c_int, [vp, vp, vp, i32]),
             "gencd_batch_path": (C.c_int, [vp, C.POINTER(gencd_path), vp, vp, C.POINTER(gencd_result)]),
+            "gencd_batch_schedule": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(f64), i32]),
+            "gencd_batch_set_schedule": (C.c_int, [vp, i32, i32]),
             # include/gencd_serve.h
             "gencd_serve": (C.c_int, [vp, i64, C.POINTER(gencd_serve_params), vp, vp]),
             "gencd_serve_dry_run": (C.c_int, [vp, i64, C.POINTER(gencd_serve_params), f64, vp, vp]),
@@ -664,6 +666,19 @@ def gencd_batch_path(h, held_out, lambdas, k, handoff=0.0, warm=True, want_w=Fal
     return out, w, r
 
 
+def gencd_batch_schedule(h):
+    """(spmm_kind, update_kind, {form: mean ms}) of the batch's autotuner."""
+    a, u = C.c_int32(), C.c_int32()
+    ms = (C.c_double * 4)()
+    _check(lib().gencd_batch_schedule(h, C.byref(a), C.byref(u), ms, 4))
+    forms = ["spmm_entries", "spmm_slots", "step_update_pairs", "step_update_grouped"]
+    return int(a.value), int(u.value), {f: float(v) for f, v in zip(forms, ms) if v >= 0}
+
+
+def gencd_batch_set_schedule(h, spmm_kind=-1, update_kind=-1):
+    _check(lib().gencd_batch_set_schedule(h, int(spmm_kind), int(update_kind)))
+
+
 class Batch:
     """Owns one batch handle; methods forward to the calls above."""
 
@@ -689,6 +704,12 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+    def schedule(self):
+        return gencd_batch_schedule(self.h)
+
+    def set_schedule(self, spmm_kind=-1, update_kind=-1):
+        gencd_batch_set_schedule(self.h, spmm_kind, update_kind)
 
     def lambda_max(self, held_out=-1):
         return gencd_batch_lambda_max(self.h, held_out)

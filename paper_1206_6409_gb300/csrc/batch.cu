@@ -422,6 +422,72 @@ __global__ void k_b_update(const int32_t* __restrict__ acc_j, const double* __re
   }
 }
 
+// The same update with the slots that accepted the same column grouped: one
+// warp per (partition, 32-slot chunk), lane = slot.  A column accepted by at
+// least kGroupMin slots of the chunk is walked once, entry by entry, and the
+// slots add into the entry's z row side by side (their S values are
+// contiguous, so the atomics of one entry share a few L2 lines); a column
+// accepted by fewer slots is walked by the lanes, one slot after another.
+constexpr int kGroupMin = 4;
+
+__global__ void k_b_update_grouped(const int32_t* __restrict__ acc_j, const double* __restrict__ acc_d, int B,
+                                   int Sp, const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ row,
+                                   const float* __restrict__ val, double* __restrict__ w, float* __restrict__ w32,
+                                   double* __restrict__ z, unsigned long long* __restrict__ ctr) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int per = (Sp + 31) / 32;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < (int64_t)B * per; q += nw) {
+    const int b = (int)(q / per), c = (int)(q % per);
+    const int s = 32 * c + lane;
+    const bool in = s < Sp;
+    const int32_t j = in ? acc_j[(int64_t)b * Sp + s] : -1;
+    const double d = in ? acc_d[(int64_t)b * Sp + s] : 0.0;
+    int64_t a = 0, e = 0;
+    if (j >= 0) {
+      a = col_ptr[j];
+      e = col_ptr[j + 1];
+      const int64_t o = (int64_t)j * Sp + s;
+      const double nwj = w[o] + d;
+      w[o] = nwj;
+      w32[o] = w_mirror(nwj);
+      atomicAdd(ctr, (unsigned long long)(e - a));
+      atomicAdd(ctr + 1, 1ull);
+    }
+    unsigned pending = __ballot_sync(FULL, j >= 0);
+    while (pending) {  // warp-uniform: one accepted column at a time
+      const int leader = __ffs(pending) - 1;
+      const int32_t jl = __shfl_sync(FULL, j, leader);
+      const unsigned mask = __ballot_sync(FULL, j == jl) & pending;
+      pending &= ~mask;
+      const int64_t al = __shfl_sync(FULL, a, leader), el = __shfl_sync(FULL, e, leader);
+      if (__popc(mask) >= kGroupMin) {
+        for (int64_t t0 = al; t0 < el; t0 += 32) {
+          const int64_t t = t0 + lane;
+          const int32_t r = t < el ? row[t] : 0;
+          const float v = t < el ? val[t] : 0.0f;
+          const int cnt = (int)(el - t0 < 32 ? el - t0 : 32);
+          for (int i = 0; i < cnt; ++i) {
+            const int32_t ri = __shfl_sync(FULL, r, i);
+            const float vi = __shfl_sync(FULL, v, i);
+            if ((mask >> lane) & 1u) atomicAdd(z + (int64_t)ri * Sp + s, d * (double)vi);
+          }
+        }
+      } else {
+        unsigned m = mask;
+        while (m) {
+          const int l = __ffs(m) - 1;
+          m &= m - 1;
+          const double dl = __shfl_sync(FULL, d, l);
+          const int sl = 32 * c + l;
+          for (int64_t t = al + lane; t < el; t += 32) atomicAdd(z + (int64_t)row[t] * Sp + sl, dl * (double)val[t]);
+        }
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ bool b_train(const uint8_t* __restrict__ fold, int64_t i, int set, int nfolds) {
   return set == nfolds || fold[i] != set;
 }
@@ -769,6 +835,16 @@ struct gencd_batch {
   std::vector<int32_t> h_set, h_group;
   std::vector<double> h_lam;
 
+  // schedule of the step, chosen by the autotuner (or set): the X^T U pass
+  // as lanes over slots (1, k_b_spmm; S a multiple of 32) or lanes over
+  // entries with 8 slots per lane (0, k_b_spmm_runs8), and the update per
+  // (partition, slot) (0) or grouped by column (1); tuned_ms: mean ms of the
+  // candidates (X^T U: kinds 0, 1; a whole step: update kinds 0, 1), -1 if
+  // not timed
+  int spmm_kind = 0, update_kind = 0;
+  bool spmm_forced = false, update_forced = false, update_tuned = false;
+  double tuned_ms[4] = {-1.0, -1.0, -1.0, -1.0};
+
   // captured steps
   bool dense_refresh = false;  // refresh u over all rows after each step
   cudaGraphExec_t graph = nullptr;
@@ -810,10 +886,12 @@ static int launch_spmm_nc(gencd_batch* b, const float* U, float* G) {
   return GENCD_OK;
 }
 
-// NC = S / 32 slot chunks of lanes; NC = 0: S = 8 or 16, lanes over entries
-// and 8 slots per lane, one launch row per 8-slot chunk (G zeroed first)
-static int launch_spmm(gencd_batch* b, int NC, const float* U, float* G) {
-  if (NC == 0) {
+// kind 1: lanes over slots, NC = S / 32 slot chunks of lanes; kind 0: lanes
+// over entries and 8 slots per lane, one launch row per 8-slot chunk (G
+// zeroed first)
+static int launch_spmm(gencd_batch* b, int kind, const float* U, float* G) {
+  const int NC = b->NC;
+  if (kind == 0 || NC == 0) {
     GENCD_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(float) * (size_t)b->k * b->S, b->st));
     const int64_t t256 = (b->nnz + 255) / 256;
     if (t256 == 0) return GENCD_OK;
@@ -866,10 +944,11 @@ static int accept_R(const gencd_batch* b) { return std::max(1, kAcceptThreads / 
 // G = X^T U and the per-slot KKT maxima (MODE 0), or a whole step (MODE 1)
 static int enqueue_propose(gencd_batch* b, bool accept) {
   const int g = b->X->num_sms * 8;
-  const int64_t nb = b->NC == 0 ? 0 : 2 * b->W;  // the lanes-over-entries pass zeroes all of G itself
+  // the lanes-over-entries pass zeroes all of G itself
+  const int64_t nb = (b->NC == 0 || b->spmm_kind == 0) ? 0 : 2 * b->W;
   k_b_prep<<<grid_for(std::max<int64_t>(1, nb * b->S), kThreads, g), kThreads, 0, b->st>>>(b->bnd, nb, b->S, b->G,
                                                                                           b->kkt_bits);
-  GENCD_TRY(launch_spmm(b, b->NC, b->U, b->G));
+  GENCD_TRY(launch_spmm(b, b->spmm_kind, b->U, b->G));
   const int R = accept_R(b);
   if (accept)
     k_b_accept<1><<<b->B, b->S * R, 0, b->st>>>(b->G, b->w32, b->w, b->bj32, b->ib32, b->bj, b->ib, b->k,
@@ -898,8 +977,15 @@ static int enqueue_step(gencd_batch* b) {
     k_b_merge<<<(npairs + kThreads - 1) / kThreads, kThreads, 0, b->st>>>(b->acc_j, b->acc_phi, b->B, b->S,
                                                                          b->d_group);
   const int g = grid_for((int64_t)npairs * 32, kThreads, b->X->num_sms * 8);
-  k_b_update<<<g, kThreads, 0, b->st>>>(b->acc_j, b->acc_d, npairs, b->S, b->X->col_ptr, b->X->row_idx,
-                                        (const float*)b->X->val, b->w, b->w32, b->z, b->ctr);
+  if (b->update_kind == 1) {
+    const int per = (b->S + 31) / 32;
+    k_b_update_grouped<<<grid_for((int64_t)b->B * per * 32, kThreads, b->X->num_sms * 8), kThreads, 0, b->st>>>(
+        b->acc_j, b->acc_d, b->B, b->S, b->X->col_ptr, b->X->row_idx, (const float*)b->X->val, b->w, b->w32, b->z,
+        b->ctr);
+  } else {
+    k_b_update<<<g, kThreads, 0, b->st>>>(b->acc_j, b->acc_d, npairs, b->S, b->X->col_ptr, b->X->row_idx,
+                                          (const float*)b->X->val, b->w, b->w32, b->z, b->ctr);
+  }
   if (b->dense_refresh)
     GENCD_TRY(launch_refresh_all(b));
   else
@@ -918,8 +1004,48 @@ static void drop_graph(gencd_batch* b) {
 
 // `iters` steps as one CUDA graph (captured once per (iters, B)); streams that
 // cannot be captured (the legacy default stream) launch the kernels directly
+// Autotuner of the update: the first time at least 4 steps run, they run
+// one by one with the update per (partition, slot) and grouped by column
+// alternately, each timed with CUDA events; the faster form is kept.  Every
+// step is a correct step either way.
+static int tune_update(gencd_batch* b, int* done) {
+  *done = 0;
+  if (b->update_tuned || b->update_forced) return GENCD_OK;
+  cudaEvent_t e[5];
+  for (int i = 0; i < 5; ++i)
+    if (cudaEventCreate(&e[i]) != cudaSuccess) {
+      for (int q = 0; q < i; ++q) cudaEventDestroy(e[q]);
+      return bfail(GENCD_ECUDA, "cudaEventCreate failed");
+    }
+  int rc = GENCD_OK;
+  cudaEventRecord(e[0], b->st);
+  for (int i = 0; i < 4 && rc == GENCD_OK; ++i) {
+    b->update_kind = i & 1;
+    rc = enqueue_step(b);
+    cudaEventRecord(e[i + 1], b->st);
+  }
+  if (rc == GENCD_OK && cudaEventSynchronize(e[4]) != cudaSuccess) rc = bfail(GENCD_ECUDA, "tuning steps failed");
+  float ms[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int i = 0; rc == GENCD_OK && i < 4; ++i) cudaEventElapsedTime(&ms[i], e[i], e[i + 1]);
+  for (int i = 0; i < 5; ++i) cudaEventDestroy(e[i]);
+  if (rc != GENCD_OK) return rc;
+  b->tuned_ms[2] = 0.5 * (ms[0] + ms[2]);
+  b->tuned_ms[3] = 0.5 * (ms[1] + ms[3]);
+  b->update_kind = b->tuned_ms[3] < b->tuned_ms[2] ? 1 : 0;
+  b->update_tuned = true;
+  drop_graph(b);
+  *done = 4;
+  return GENCD_OK;
+}
+
 static int run_steps(gencd_batch* b, int iters) {
   if (iters <= 0) return GENCD_OK;
+  if (iters >= 4) {
+    int done = 0;
+    GENCD_TRY(tune_update(b, &done));
+    iters -= done;
+    if (iters <= 0) return GENCD_OK;
+  }
   if (b->st != nullptr && (b->graph_iters != iters || b->graph_B != b->B)) {
     drop_graph(b);
     cudaGraph_t gr = nullptr;
@@ -1105,6 +1231,41 @@ static void free_batch(gencd_batch* b) {
   delete b;
 }
 
+// Autotuner of the X^T U pass: with S a multiple of 32 both forms apply;
+// each is timed over three launches on the current U and the faster kept.
+static int tune_spmm(gencd_batch* b) {
+  if (b->spmm_forced) return GENCD_OK;
+  if (b->NC == 0) {
+    b->spmm_kind = 0;
+    return GENCD_OK;
+  }
+  cudaEvent_t e0, e1;
+  GENCD_CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return bfail(GENCD_ECUDA, "cudaEventCreate failed");
+  }
+  int rc = GENCD_OK;
+  for (int kind = 0; kind < 2 && rc == GENCD_OK; ++kind) {
+    b->spmm_kind = kind;
+    rc = enqueue_propose(b, false);  // warm-up
+    cudaEventRecord(e0, b->st);
+    for (int r = 0; r < 3 && rc == GENCD_OK; ++r) rc = enqueue_propose(b, false);
+    cudaEventRecord(e1, b->st);
+    float ms = 0.f;
+    if (rc == GENCD_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+      b->tuned_ms[kind] = ms / 3.0;
+    else if (rc == GENCD_OK)
+      rc = bfail(GENCD_ECUDA, "timing the X^T U pass failed");
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != GENCD_OK) return rc;
+  b->spmm_kind = b->tuned_ms[1] <= b->tuned_ms[0] ? 1 : 0;
+  drop_graph(b);
+  return GENCD_OK;
+}
+
 static int create_batch(gencd_batch* b, const uint8_t* fold, int32_t memory) {
   const int64_t n = b->n, k = b->k, nnz = b->nnz;
   const int F = b->nfolds, S = b->S;
@@ -1241,7 +1402,7 @@ static int create_batch(gencd_batch* b, const uint8_t* fold, int32_t memory) {
       cudaMemsetAsync(G0, 0, 4 * (size_t)k * 32, st);
       cudaMemsetAsync(bits, 0, 4 * 32, st);
       k_b_prep<<<grid_for(2 * b->W * 32, kThreads, g), kThreads, 0, st>>>(b->bnd, 2 * b->W, 32, G0, nullptr);
-      rc = launch_spmm(b, 1, U0, G0);
+      rc = launch_spmm_nc<1>(b, U0, G0);  // 32 columns of U0: the training sets
     }
     if (rc == GENCD_OK) {
       k_b_absmax<<<grid_for(k * 32, kThreads, g), kThreads, 0, st>>>(G0, k, F + 1, bits);
@@ -1259,6 +1420,7 @@ static int create_batch(gencd_batch* b, const uint8_t* fold, int32_t memory) {
       b->lam_max[f] = (double)v * inv[f];
     }
   }
+  GENCD_TRY(tune_spmm(b));
   GENCD_CUDA_TRY(cudaStreamSynchronize(st));
   return GENCD_OK;
 }
@@ -1322,6 +1484,33 @@ static int batch_create(gencd_batch** out, int64_t n, int64_t k, int64_t nnz, co
 }
 
 void gencd_batch_destroy(gencd_batch* b) { free_batch(b); }
+
+int gencd_batch_schedule(gencd_batch* b, int32_t* spmm_kind, int32_t* update_kind, double* ms, int32_t nms) {
+  if (!b) return bfail(GENCD_EINVAL, "batch handle is NULL");
+  if (nms < 0 || (nms > 0 && !ms)) return bfail(GENCD_EINVAL, "ms must hold nms >= 0 values");
+  if (spmm_kind) *spmm_kind = b->spmm_kind;
+  if (update_kind) *update_kind = b->update_tuned || b->update_forced ? b->update_kind : -1;
+  for (int32_t i = 0; i < nms; ++i) ms[i] = i < 4 ? b->tuned_ms[i] : -1.0;
+  return GENCD_OK;
+}
+
+int gencd_batch_set_schedule(gencd_batch* b, int32_t spmm_kind, int32_t update_kind) {
+  if (!b) return bfail(GENCD_EINVAL, "batch handle is NULL");
+  if (spmm_kind < -1 || spmm_kind > 1 || update_kind < -1 || update_kind > 1)
+    return bfail(GENCD_EINVAL, "schedule kinds are -1 (autotune), 0 or 1");
+  if (spmm_kind == 1 && b->NC == 0) return bfail(GENCD_EINVAL, "lanes over slots need a multiple of 32 slots");
+  b->spmm_forced = spmm_kind >= 0;
+  if (spmm_kind >= 0) {
+    b->spmm_kind = spmm_kind;
+  } else {
+    GENCD_TRY(tune_spmm(b));
+  }
+  b->update_forced = update_kind >= 0;
+  if (update_kind >= 0) b->update_kind = update_kind;
+  else b->update_tuned = false;
+  drop_graph(b);
+  return GENCD_OK;
+}
 
 int gencd_batch_slots(gencd_batch* b, int32_t* slots) {
   if (!b || !slots) return bfail(GENCD_EINVAL, "NULL argument");

@@ -198,3 +198,60 @@ def test_batch_rejects_bad_input(gb):
                      lambda: b.set_params(variant="shotgun")):
             with pytest.raises(gb.GencdError):
                 call()
+
+
+@pytest.mark.parametrize("slots,spmm_kind", [(16, 0), (32, 0), (32, 1), (64, 1)])
+def test_every_schedule_proposes_like_the_oracle(gb, slots, spmm_kind):
+    # the autotuner's candidates for the X^T U pass compute the same proposals
+    prob, fold = _problem("logistic", seed=13)
+    with gb.Batch(prob, fold=fold, nfolds=NFOLDS, slots=slots) as b:
+        kind, _, tuned = b.schedule()
+        assert kind in (0, 1) and "spmm_entries" in tuned or b.slots < 32
+        b.set_schedule(spmm_kind, -1)
+        assert b.schedule()[0] == spmm_kind
+        cases = {}
+        for s in range(0, b.slots, 3):
+            h = s % (NFOLDS + 1) - 1
+            lam = b.lambda_max(h) * 0.05
+            w = _state(prob, 400 + s, frac=0.05, scale=0.3)
+            b.set_slot(s, h, lam, w)
+            cases[s] = (h, lam, w)
+        d_all, f_all = b.propose()
+        for s, (h, lam, w) in cases.items():
+            sp = _subset(prob, fold, h)
+            orc = oracle.Oracle(sp)
+            orc.set_lambda(lam)
+            z = orc.fitted(w)
+            J = np.arange(prob.k, dtype=np.int32)
+            d_cpu, f_cpu = orc.propose(w, z, J)
+            assert_steps_close(sp, z, w, lam, J, d_all[s], f_all[s], d_cpu, f_cpu, TOL["f32"])
+    with pytest.raises(gb.GencdError):
+        with gb.Batch(prob, fold=fold, nfolds=NFOLDS, slots=16) as b:
+            b.set_schedule(1, -1)  # lanes over slots need a multiple of 32 slots
+
+
+@pytest.mark.parametrize("update_kind", [0, 1])
+def test_every_update_schedule_keeps_z_equal_to_xw(gb, update_kind):
+    # after steps with either update form, each slot's fitted values are X w
+    # (its FP64 objective equals the oracle's at its w) and w moved only where
+    # the proposals allowed; slots share columns (the same training set and
+    # lambda in groups of four), so the grouped form's shared walks are taken
+    prob, fold = _problem("squared", seed=17)
+    with gb.Batch(prob, fold=fold, nfolds=NFOLDS, slots=32) as b:
+        b.set_params(variant="thread_greedy", blocks=64)
+        b.set_schedule(-1, update_kind)
+        cases = {}
+        for s in range(b.slots):
+            h = (s // 4) % (NFOLDS + 1) - 1
+            lam = b.lambda_max(h) * (0.05 if s % 8 < 4 else 0.02)
+            b.set_slot(s, h, lam, None)
+            cases[s] = (h, lam)
+        b.iterate(12)
+        obj, _ = b.objective()
+        for s, (h, lam) in cases.items():
+            orc = oracle.Oracle(oracle.stored_problem(_subset(prob, fold, h), "f32"))  # the batch stores X in FP32
+            orc.set_lambda(lam)
+            w = b.w(s)
+            assert np.count_nonzero(w) > 0
+            assert obj[s] == pytest.approx(orc.objective(w), rel=1e-12)
+            assert orc.objective(w) < orc.objective(np.zeros(prob.k))
