@@ -102,6 +102,11 @@ typedef struct {
                             (Thread-Greedy, Greedy, Shotgun; 0 = off, at most
                             100000)                                              */
   int32_t reserved;
+  double tol_gap;      /* > 0: gencd_solve also stops when the duality gap of a
+                          full evaluation (gencd_duality_gap) is at most
+                          tol_gap * |P(w)|, which bounds the relative objective
+                          error (P(w) - P*) / P(w); every convergence check is
+                          then a full evaluation.  0 = off (default)            */
 } gencd_params;
 
 typedef struct {
@@ -155,7 +160,7 @@ int gencd_lambda_max(gencd_problem* p, double* lambda_max);
 
 /* Fills *out with the default parameters (Thread-Greedy, B = 0 (auto),
  * P = 0 (auto), seed 0, max_iter 100000, tol_kkt 1e-8, check_every 10,
- * beta_mode 0, no timeout). */
+ * beta_mode 0, no timeout, tol_gap 0). */
 int gencd_default_params(gencd_params* out);
 
 /* Validates and stores the iteration parameters. */
@@ -215,6 +220,21 @@ int gencd_get_z(gencd_problem* p, double* z, int64_t n, int32_t memory);
 
 /* Objective P(w) of Eq. 1 and the KKT violation at the current state. */
 int gencd_objective(gencd_problem* p, double* objective, double* kkt);
+
+/*
+ * Duality gap at the current state (not in the paper, which states no
+ * stopping rule; a certificate of the objective error).  With
+ * u = l'(y, Xw) in FP64, g = X^T u / n and s = min(1, lambda / max_j |g_j|),
+ * s u is a feasible point of the Fenchel dual of Eq. 1,
+ *     D(v) = -(1/n) sum_i l*(y_i, v_i)  subject to  ||X^T v|| / n <= lambda,
+ * with l*(y, v) = sup_t (v t - l(y, t)) the conjugate of the loss (squared:
+ * v y + v^2 / 2; logistic: p log p + (1 - p) log(1 - p), p = -y v), so
+ * gap = P(w) - D(s u) >= P(w) - P* by weak duality, and it is 0 at the
+ * optimum.  The sums g are those of the problem's arithmetic: in the FP32
+ * storage modes the dual point's feasibility, hence the bound, holds to the
+ * FP32 rounding of g.  Any output pointer may be NULL.
+ */
+int gencd_duality_gap(gencd_problem* p, double* gap, double* primal, double* dual);
 
 /*
  * Parity hook for Algorithm 4: for the m columns J[0..m) (int32, in [0, k),

@@ -89,9 +89,13 @@ int gencd_batch_set_schedule(gencd_batch* b, int32_t spmm_kind, int32_t update_k
 int gencd_batch_lambda_max(gencd_batch* b, int32_t held_out, double* lambda_max);
 
 /* Iteration parameters (include/gencd.h): variant THREAD_GREEDY or GREEDY,
- * blocks (B partitions, 0 = min(k, 1024)), tol_kkt, check_every and max_iter
- * (per solve, gencd_batch_path), beta_mode.  P, seed and timeout_s are
- * ignored.  GENCD_EINVAL for another variant or a value out of range. */
+ * blocks (B partitions, 0 = min(k, 1024)), tol_kkt, tol_gap, check_every and
+ * max_iter (per solve, gencd_batch_path), beta_mode.  P, seed and timeout_s
+ * are ignored.  GENCD_EINVAL for another variant or a value out of range.
+ * tol_gap > 0: gencd_batch_path also ends a solve when its duality gap
+ * (include/gencd.h, gencd_duality_gap; the dual point's scale from the FP32
+ * sums) is at most tol_gap * |P(w)|, checked when the solve's objective is
+ * evaluated (every 8 checks). */
 int gencd_batch_set_params(gencd_batch* b, const gencd_params* params);
 
 /*

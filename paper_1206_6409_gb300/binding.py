@@ -49,7 +49,7 @@ EXPORTS = ["gencd_create", "gencd_destroy", "gencd_set_lambda", "gencd_set_loss"
            "gencd_spectral_radius", "gencd_color", "gencd_color_balanced_csc", "gencd_get_colors", "gencd_set_colors",
            "gencd_permutation", "gencd_profile_enable", "gencd_profile_read", "gencd_profile_reset",
            "gencd_last_error", "gencd_stats", "gencd_stats_reset", "gencd_propose_all_noalloc",
-           "gencd_propose_schedule", "gencd_block_pstar",
+           "gencd_propose_schedule", "gencd_block_pstar", "gencd_duality_gap",
            # include/gencd_batch.h
            "gencd_batch_create", "gencd_batch_destroy", "gencd_batch_slots", "gencd_batch_lambda_max",
            "gencd_batch_set_params", "gencd_batch_set_slot", "gencd_batch_copy_slot", "gencd_batch_clear_slot",
@@ -63,7 +63,7 @@ class gencd_params(C.Structure):
     _fields_ = [("variant", C.c_int32), ("blocks", C.c_int32), ("P", C.c_int64), ("seed", C.c_uint64),
                 ("max_iter", C.c_int64), ("tol_kkt", C.c_double), ("check_every", C.c_int32),
                 ("beta_mode", C.c_int32), ("timeout_s", C.c_double), ("improve_steps", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("reserved", C.c_int32), ("tol_gap", C.c_double)]
 
 
 class gencd_result(C.Structure):
@@ -139,6 +139,7 @@ def lib():
             "gencd_set_w": (C.c_int, [vp, vp, i64, i32]),
             "gencd_get_z": (C.c_int, [vp, vp, i64, i32]),
             "gencd_objective": (C.c_int, [vp, C.POINTER(f64), C.POINTER(f64)]),
+            "gencd_duality_gap": (C.c_int, [vp, C.POINTER(f64), C.POINTER(f64), C.POINTER(f64)]),
             "gencd_propose_at": (C.c_int, [vp, vp, i64, vp, vp, i32]),
             "gencd_propose_all": (C.c_int, [vp, vp, vp, i32, C.POINTER(f64)]),
             "gencd_spectral_radius": (C.c_int, [vp, C.POINTER(f64), C.POINTER(i64), C.POINTER(i32)]),
@@ -411,6 +412,13 @@ def gencd_profile_enable(h, enable=True):
     _check(lib().gencd_profile_enable(h, 1 if enable else 0))
 
 
+def gencd_duality_gap(h):
+    """(gap, primal P(w), dual D) at the current state."""
+    g, pr, du = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().gencd_duality_gap(h, C.byref(g), C.byref(pr), C.byref(du)))
+    return g.value, pr.value, du.value
+
+
 def gencd_block_pstar(h, B):
     """(P*_b int64[B], rho_b float64[B]) of block Shotgun's B column blocks."""
     P = np.zeros(int(B), np.int64)
@@ -520,6 +528,9 @@ class Problem:
 
     def objective(self):
         return gencd_objective(self.h)
+
+    def duality_gap(self):
+        return gencd_duality_gap(self.h)
 
     def propose_at(self, J):
         return gencd_propose_at(self.h, J)

@@ -231,23 +231,26 @@ static int effective_B(const gencd_problem* p) {
 }
 
 // KKT violation (dscal[0]) and objective (dscal[1]) of the current state
+// KKT violation (dscal[0]), objective (dscal[1]) and duality gap (dscal[9])
+// of the current state
 static int enqueue_evaluate(gencd_problem* p) {
   GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal, 0, sizeof(double), p->stream));
+  GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal + 7, 0, sizeof(double), p->stream));
   GENCD_TRY(launch_propose_all(p, p->u, p->precision == GENCD_F64));
   GENCD_TRY(launch_finalize(p, p->lambda, false));
-  GENCD_TRY(launch_objective(p));
+  GENCD_TRY(launch_objective(p, true));
   return GENCD_OK;
 }
 
 static int read_scalars(gencd_problem* p) {
-  GENCD_CUDA_TRY(cudaMemcpyAsync(p->hpin, p->dscal, 8 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  GENCD_CUDA_TRY(cudaMemcpyAsync(p->hpin, p->dscal, kScalars * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
   GENCD_CUDA_TRY(cudaStreamSynchronize(p->stream));
   return GENCD_OK;
 }
 
 // the device scalars to hpin without waiting; ev_scalars marks their arrival
 static int read_scalars_async(gencd_problem* p) {
-  GENCD_CUDA_TRY(cudaMemcpyAsync(p->hpin, p->dscal, 8 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  GENCD_CUDA_TRY(cudaMemcpyAsync(p->hpin, p->dscal, kScalars * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
   GENCD_CUDA_TRY(cudaEventRecord(p->ev_scalars, p->stream));
   return GENCD_OK;
 }
@@ -652,10 +655,10 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
   GENCD_TRY(dev_alloc(p, &p->perm, k));
   GENCD_TRY(dev_alloc(p, &p->list_off, k + 2));
   GENCD_TRY(dev_alloc(p, &p->scan_tmp, scan_tmp_words(k + 2)));
-  GENCD_TRY(dev_alloc(p, &p->dscal, 8));
-  GENCD_TRY(dev_alloc(p, &p->red, 2 * kRedBlocks));
+  GENCD_TRY(dev_alloc(p, &p->dscal, kScalars));
+  GENCD_TRY(dev_alloc(p, &p->red, 3 * kRedBlocks));
   GENCD_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_scalars, cudaEventDisableTiming));
-  if (!p->hpin && cudaMallocHost((void**)&p->hpin, 8 * sizeof(double)) != cudaSuccess) {
+  if (!p->hpin && cudaMallocHost((void**)&p->hpin, kScalars * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return fail(GENCD_ENOMEM, "pinned host allocation failed");
   }
@@ -709,7 +712,7 @@ static int create_impl(gencd_problem* p, const int64_t* col_ptr, const int32_t* 
   if (p->w32) GENCD_CUDA_TRY(cudaMemsetAsync(p->w32, 0, sizeof(float) * k, st));
   GENCD_CUDA_TRY(cudaMemsetAsync(p->gacc, 0, sizeof(double) * k, st));
   if (p->gnat != p->gacc) GENCD_CUDA_TRY(cudaMemsetAsync(p->gnat, 0, sizeof(float) * k, st));
-  GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal, 0, 8 * sizeof(double), st));
+  GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal, 0, kScalars * sizeof(double), st));
   GENCD_TRY(launch_tile_map(p));
   GENCD_TRY(launch_col_scale(p));
   GENCD_TRY(build_propose_plan(p));
@@ -820,7 +823,10 @@ int solve_advance(gencd_problem* p, SolveRun* S) {
     set_error("objective is not finite or grew beyond 1e6 times its starting value");
     return solve_finish(p, S);
   }
-  if (kkt <= a.tol_kkt) {
+  // converged: the KKT violation, or (tol_gap > 0) the relative duality gap
+  // of a full evaluation, within tolerance
+  const bool gap_ok = a.tol_gap > 0.0 && S->evaluated && p->hpin[9] <= a.tol_gap * std::fabs(obj);
+  if (kkt <= a.tol_kkt || gap_ok) {
     if (S->evaluated) {
       S->status = GENCD_OK;
       return 0;
@@ -834,8 +840,8 @@ int solve_advance(gencd_problem* p, SolveRun* S) {
   const int64_t step = std::min<int64_t>(a.check_every, a.max_iter - S->iters);
   for (int64_t i = 0; i < step; ++i) GENCD_TRY(enqueue_iteration(p, &S->host_nnz, i + 1 == step));
   S->iters += step;
-  if (S->fused) {
-    GENCD_TRY(launch_objective(p));  // divergence watch on the current state
+  if (S->fused && !(a.tol_gap > 0.0)) {
+    GENCD_TRY(launch_objective(p, false));  // divergence watch on the current state
     GENCD_TRY(read_scalars_async(p));
     S->evaluated = false;
   } else {
@@ -978,7 +984,8 @@ int gencd_set_params(gencd_problem* p, const gencd_params* a) {
   if (a->variant < 0 || a->variant > 5) return fail(GENCD_EINVAL, "unknown variant");
   if (a->variant == GENCD_SHOTGUN_BLOCKS && a->blocks > kMaxShotgunBlocks)
     return fail(GENCD_EINVAL, "block Shotgun takes at most " + std::to_string(kMaxShotgunBlocks) + " blocks");
-  if (a->blocks < 0 || a->P < 0 || a->max_iter < 0 || !(a->tol_kkt >= 0.0) || a->check_every < 1 ||
+  if (a->blocks < 0 || a->P < 0 || a->max_iter < 0 || !(a->tol_kkt >= 0.0) || !(a->tol_gap >= 0.0) ||
+      a->check_every < 1 ||
       (a->beta_mode != 0 && a->beta_mode != 1) || !(a->timeout_s >= 0.0) || a->improve_steps < 0 ||
       a->improve_steps > 100000)
     return fail(GENCD_EINVAL, "parameter out of range");
@@ -1093,6 +1100,16 @@ int gencd_set_w(gencd_problem* p, const double* w, int64_t k, int32_t memory) {
   GENCD_TRY(launch_csr_spmv(p, p->w, p->z));
   GENCD_TRY(launch_fill_u(p));
   GENCD_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return GENCD_OK;
+}
+
+int gencd_duality_gap(gencd_problem* p, double* gap, double* primal, double* dual) {
+  GENCD_CHECK_HANDLE(p);
+  GENCD_TRY(enqueue_evaluate(p));
+  GENCD_TRY(read_scalars(p));
+  if (gap) *gap = p->hpin[9];
+  if (primal) *primal = p->hpin[1];
+  if (dual) *dual = p->hpin[1] - p->hpin[9];
   return GENCD_OK;
 }
 

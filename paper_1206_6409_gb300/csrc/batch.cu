@@ -203,7 +203,7 @@ __global__ void k_b_prep(const int32_t* __restrict__ bnd, int64_t nb, int Sp, fl
     if (j >= 0) G[(int64_t)j * Sp + (q % Sp)] = 0.0f;
   }
   if (kkt_bits && blockIdx.x == 0)
-    for (int s = threadIdx.x; s < Sp; s += blockDim.x) kkt_bits[s] = 0u;
+    for (int s = threadIdx.x; s < 2 * Sp; s += blockDim.x) kkt_bits[s] = 0u;  // KKT and max |g| per slot
 }
 
 template <int NC>
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(kAcceptThreads)
   const int set = live ? sa.set[s] : -1;
   uint32_t best = 0u;
   int32_t bcol = INT_MAX;
-  float vmax = 0.0f;
+  float vmax = 0.0f, gmax = 0.0f;
   if (set >= 0) {
     const int64_t lo = part_lo[b], hi = part_lo[b + 1];
     const float lam = sa.lam32[s], invn = sa.invn32[s];
@@ -329,20 +329,29 @@ __global__ void __launch_bounds__(kAcceptThreads)
         bcol = (int32_t)j;
       }
       vmax = fmaxf(vmax, kkt_violation_f32(g, wj, lam));
+      gmax = fmaxf(gmax, fabsf(g));
     }
   }
   s_mag[threadIdx.x] = best;
   s_col[threadIdx.x] = bcol;
   s_v[threadIdx.x] = vmax;
   __syncthreads();
+  float gm = 0.0f;  // max |g| over the partition (reusing s_v)
+  if (live) {
+    for (int q = 1; q < R; ++q) vmax = fmaxf(vmax, s_v[q * Sp + s]);
+  }
+  __syncthreads();
+  s_v[threadIdx.x] = gmax;
+  __syncthreads();
   if (r != 0 || s >= Sp) return;
+  gm = gmax;
   for (int q = 1; q < R; ++q) {
     const int o = q * Sp + s;
     if (s_mag[o] > best || (s_mag[o] == best && s_col[o] < bcol)) {
       best = s_mag[o];
       bcol = s_col[o];
     }
-    vmax = fmaxf(vmax, s_v[o]);
+    gm = fmaxf(gm, s_v[o]);
   }
   const int64_t slot = (int64_t)b * Sp + s;
   if (set < 0) {
@@ -353,6 +362,7 @@ __global__ void __launch_bounds__(kAcceptThreads)
     return;
   }
   if (vmax > 0.0f) atomicMax(kkt_bits + s, __float_as_uint(vmax));
+  if (gm > 0.0f) atomicMax(kkt_bits + Sp + s, __float_as_uint(gm));
   if (MODE == 1) {
     int32_t oj = -1;
     double od = 0.0, of = 0.0;
@@ -735,30 +745,43 @@ __global__ void k_b_fill_col(const double* __restrict__ y, const uint8_t* __rest
 
 // acc[q] += loss sum over slot list[q]'s training rows; acc[m + q] += ||w_s||_1
 // (block: 32 x 8 threads, threadIdx.x = list position)
+// dual_scale (nullable): per listed slot, s = lambda_s / max(lambda_s,
+// max_j |g_js|); then acc[2m + q] += the slot's sum over its training rows of
+// l*(y_i, s u_is) (u from the FP64 fitted values): the duality gap's dual
+// point (reading on the duality gap)
 __global__ void k_b_objective(const double* __restrict__ y, const double* __restrict__ z,
                               const uint8_t* __restrict__ fold, int nfolds, int loss, int64_t n,
                               const double* __restrict__ w, int64_t k, int Sp, const int32_t* __restrict__ list,
-                              const int32_t* __restrict__ list_set, int m, double* __restrict__ acc) {
-  __shared__ double red[2][8][33];
+                              const int32_t* __restrict__ list_set, int m, const double* __restrict__ dual_scale,
+                              double* __restrict__ acc) {
+  __shared__ double red[3][8][33];
   const int q = threadIdx.x;
-  double sl = 0.0, s1 = 0.0;
+  double sl = 0.0, s1 = 0.0, sc = 0.0;
   if (q < m) {
     const int s = list[q], set = list_set[q];
+    const double sc_s = dual_scale ? dual_scale[q] : 0.0;
     const int64_t stride = (int64_t)gridDim.x * 8;
     for (int64_t i = (int64_t)blockIdx.x * 8 + threadIdx.y; i < n; i += stride)
-      if (b_train(fold, i, set, nfolds)) sl += loss_value(loss, y[i], z[i * Sp + s]);
+      if (b_train(fold, i, set, nfolds)) {
+        const double zi = z[i * Sp + s];
+        sl += loss_value(loss, y[i], zi);
+        if (dual_scale) sc += loss_conjugate(loss, y[i], sc_s * loss_deriv(loss, y[i], zi));
+      }
     for (int64_t j = (int64_t)blockIdx.x * 8 + threadIdx.y; j < k; j += stride) s1 += fabs(w[j * Sp + s]);
   }
   red[0][threadIdx.y][q] = sl;
   red[1][threadIdx.y][q] = s1;
+  red[2][threadIdx.y][q] = sc;
   __syncthreads();
   if (threadIdx.y == 0 && q < m) {
     for (int r = 1; r < 8; ++r) {
       sl += red[0][r][q];
       s1 += red[1][r][q];
+      sc += red[2][r][q];
     }
     atomicAdd(acc + q, sl);
     atomicAdd(acc + m + q, s1);
+    if (dual_scale) atomicAdd(acc + 2 * m + q, sc);
   }
 }
 
@@ -1138,9 +1161,19 @@ static int slot_clear(gencd_batch* b, int s) {
   return GENCD_OK;
 }
 
-// objectives of the listed slots (FP64), synchronising
-static int slot_objectives(gencd_batch* b, const std::vector<int32_t>& slots, std::vector<double>* obj) {
+// objectives of the listed slots (FP64), synchronising; gap (nullable): their
+// duality gaps, which need the max |g_js| of the slots' current state (a
+// propose pass over the current state must have run since the last step)
+static int slot_objectives(gencd_batch* b, const std::vector<int32_t>& slots, std::vector<double>* obj,
+                           std::vector<double>* gap = nullptr) {
   obj->assign(slots.size(), 0.0);
+  if (gap) gap->assign(slots.size(), 0.0);
+  std::vector<unsigned int> gbits;
+  if (gap) {
+    gbits.resize(b->S);
+    GENCD_CUDA_TRY(cudaMemcpyAsync(gbits.data(), b->kkt_bits + b->S, 4 * b->S, cudaMemcpyDeviceToHost, b->st));
+    GENCD_CUDA_TRY(cudaStreamSynchronize(b->st));
+  }
   for (size_t q0 = 0; q0 < slots.size(); q0 += 32) {
     const int m = (int)std::min<size_t>(32, slots.size() - q0);
     std::vector<int32_t> lst(64);
@@ -1149,19 +1182,34 @@ static int slot_objectives(gencd_batch* b, const std::vector<int32_t>& slots, st
       lst[32 + q] = b->h_set[slots[q0 + q]];
     }
     GENCD_CUDA_TRY(cudaMemcpyAsync(b->obj_list, lst.data(), 4 * 64, cudaMemcpyHostToDevice, b->st));
-    GENCD_CUDA_TRY(cudaMemsetAsync(b->obj_acc, 0, sizeof(double) * 64, b->st));
+    GENCD_CUDA_TRY(cudaMemsetAsync(b->obj_acc, 0, sizeof(double) * 96, b->st));
+    std::vector<double> scale(32, 0.0);
+    if (gap) {  // s = lambda / max(lambda, max_j |g_j|): the dual point s u is feasible
+      for (int q = 0; q < m; ++q) {
+        const int s = slots[q0 + q];
+        float gm;
+        std::memcpy(&gm, &gbits[s], 4);
+        const double lam = b->h_lam[s];
+        scale[q] = (double)gm > lam ? lam / (double)gm : 1.0;
+      }
+      GENCD_CUDA_TRY(cudaMemcpyAsync(b->obj_acc + 96, scale.data(), sizeof(double) * 32, cudaMemcpyHostToDevice,
+                                     b->st));
+    }
     const int64_t work = std::max(b->n, b->k);
     const int grid = (int)std::min<int64_t>((work + 7) / 8, (int64_t)b->X->num_sms * 8);
     k_b_objective<<<grid, dim3(32, 8), 0, b->st>>>(b->X->y, b->z, b->fold, b->nfolds, b->loss, b->n, b->w, b->k, b->S,
-                                                  b->obj_list, b->obj_list + 32, m, b->obj_acc);
+                                                  b->obj_list, b->obj_list + 32, m, gap ? b->obj_acc + 96 : nullptr,
+                                                  b->obj_acc);
     GENCD_CUDA_TRY(cudaGetLastError());
-    double h[64];
-    GENCD_CUDA_TRY(cudaMemcpyAsync(h, b->obj_acc, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, b->st));
+    double h[96];
+    GENCD_CUDA_TRY(cudaMemcpyAsync(h, b->obj_acc, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, b->st));
     GENCD_CUDA_TRY(cudaStreamSynchronize(b->st));
     for (int q = 0; q < m; ++q) {
       const int s = slots[q0 + q], set = b->h_set[s];
       const double rows = (double)b->set_rows[set];  // an empty training set has no loss term
-      (*obj)[q0 + q] = (rows > 0.0 ? h[q] / rows : 0.0) + b->h_lam[s] * h[m + q];
+      const double P = (rows > 0.0 ? h[q] / rows : 0.0) + b->h_lam[s] * h[m + q];
+      (*obj)[q0 + q] = P;
+      if (gap) (*gap)[q0 + q] = P + (rows > 0.0 ? h[2 * m + q] / rows : 0.0);
     }
   }
   return GENCD_OK;
@@ -1369,10 +1417,10 @@ static int create_batch(gencd_batch* b, const uint8_t* fold, int32_t memory) {
   GENCD_CUDA_TRY(cudaMemsetAsync(b->G, 0, 4 * (size_t)k * S, st));
   GENCD_CUDA_TRY(cudaMemsetAsync(b->z, 0, 8 * (size_t)n * S, st));
   GENCD_CUDA_TRY(cudaMemsetAsync(b->U, 0, 4 * (size_t)n * S, st));
-  GENCD_TRY(balloc(&b->kkt_bits, S));
+  GENCD_TRY(balloc(&b->kkt_bits, 2 * S));  // KKT and max |g| per slot
   GENCD_TRY(balloc(&b->ctr, 2));
   GENCD_CUDA_TRY(cudaMemsetAsync(b->ctr, 0, 16, st));
-  GENCD_TRY(balloc(&b->obj_acc, 64));
+  GENCD_TRY(balloc(&b->obj_acc, 128));
   GENCD_TRY(balloc(&b->obj_list, 64));
   GENCD_TRY(balloc(&b->tmp_k, k));
   GENCD_TRY(balloc(&b->d_set, S));
@@ -1530,7 +1578,7 @@ int gencd_batch_set_params(gencd_batch* b, const gencd_params* a) {
   if (!b || !a) return bfail(GENCD_EINVAL, "NULL argument");
   if (a->variant != GENCD_THREAD_GREEDY && a->variant != GENCD_GREEDY)
     return bfail(GENCD_EINVAL, "the batch runs Thread-Greedy or Greedy");
-  if (a->blocks < 0 || a->max_iter < 0 || !(a->tol_kkt >= 0.0) || a->check_every < 1 ||
+  if (a->blocks < 0 || a->max_iter < 0 || !(a->tol_kkt >= 0.0) || !(a->tol_gap >= 0.0) || a->check_every < 1 ||
       (a->beta_mode != 0 && a->beta_mode != 1))
     return bfail(GENCD_EINVAL, "parameter out of range");
   const bool betas = a->beta_mode != b->params.beta_mode;
@@ -1780,12 +1828,21 @@ static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* 
       }
     }
     if (!watch.empty()) {
-      std::vector<double> pw;
-      rc = slot_objectives(b, watch, &pw);
+      // with tol_gap, the watched slots' duality gaps: a propose pass over the
+      // current state gives max_j |g_j| (the step's own pass saw its start)
+      const bool gaps = b->params.tol_gap > 0.0;
+      std::vector<double> pw, pg;
+      if (gaps) rc = enqueue_propose(b, false);
+      if (rc == GENCD_OK) rc = slot_objectives(b, watch, &pw, gaps ? &pg : nullptr);
       for (size_t r = 0; r < watch.size() && rc == GENCD_OK; ++r) {
         const int s = watch[r];
         obj_wait[s] = 0;
         const double P = pw[r];
+        if (gaps && pg[r] <= b->params.tol_gap * std::fabs(P)) {  // certified within tol_gap of its optimum
+          solves[slot_solve[s]].status = GENCD_OK;
+          retire.push_back(s);
+          continue;
+        }
         if (stall[s] >= kStallChecks) {  // no new lowest KKT value for kStallChecks checks
           const bool flat = !(P < p_ref[s] * (1.0 - 1e-9));
           if (flat && b->h_group[s] < b->B) {

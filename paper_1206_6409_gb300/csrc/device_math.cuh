@@ -28,6 +28,19 @@ __device__ __forceinline__ double loss_deriv(int loss, double y, double t) {
   return -y / (1.0 + exp(m));
 }
 
+// Convex conjugate of the loss in t, l*(y, v) = sup_t (v t - l(y, t)) (the
+// dual of Eq. 1, for the duality gap): squared v y + v^2 / 2; logistic
+// p log p + (1 - p) log(1 - p) with p = -y v in [0, 1] (0 log 0 = 0; the
+// dual points used here keep p in [0, 1]).
+__device__ __forceinline__ double loss_conjugate(int loss, double y, double v) {
+  if (loss == 0) return v * y + 0.5 * v * v;
+  double p = -y * v;
+  p = p < 0.0 ? 0.0 : (p > 1.0 ? 1.0 : p);
+  const double a = p > 0.0 ? p * log(p) : 0.0;
+  const double b = p < 1.0 ? (1.0 - p) * log1p(-p) : 0.0;
+  return a + b;
+}
+
 // u_i in the storage precision of u: FP64 mode evaluates l' in FP64; FP32 mode
 // evaluates the logistic derivative in FP32 arithmetic (its result is stored
 // in FP32 anyway), from the FP64 fitted value.

@@ -59,6 +59,7 @@ constexpr int kListPlanThreads = 1024;
 constexpr int kListPlanPer = 4;
 constexpr int64_t kListPlanMax = (int64_t)kListPlanThreads * kListPlanPer;
 constexpr int32_t kMaxShotgunBlocks = 1024;  // column blocks of block Shotgun (one selection CTA)
+constexpr int kScalars = 16;  // device scalars of a problem (dscal / hpin)
 
 // kernel ids for launch counting / profiling
 enum KernelId {
@@ -219,8 +220,11 @@ struct gencd_problem {
   float* bj32 = nullptr;
   float* ib32 = nullptr;
 
-  // device scalars: [0] kkt bits, [1] objective, [2] loss sum, [3] l1 sum,
-  // [4] updates (int64), [5] nnz processed (int64), [6] scratch
+  // device scalars (kScalars doubles, mirrored to hpin): [0] kkt bits,
+  // [1] objective, [2] loss sum, [3] l1 sum, [4] updates (int64), [5] nnz
+  // processed (int64), [6] scratch, [7] max_j |g_j| of the last full
+  // evaluation (bits; idle columns count as lambda), [8] the duality gap's
+  // sum of conjugates, [9] the duality gap P(w) - D
   double* dscal = nullptr;
   double* red = nullptr;  // per-block partial sums (2 * kRedBlocks)
   double* hpin = nullptr; // pinned host mirror of dscal
@@ -297,7 +301,7 @@ int fail_plan(const char* msg);
 int launch_tile_map_of(gencd_problem* p, const int64_t* col_ptr, int64_t k, int64_t ntiles, int32_t* tile_col,
                        int64_t tile);
 int launch_propose_list(gencd_problem* p, const int32_t* J, int64_t m, double* delta, double* phi);
-int launch_objective(gencd_problem* p);
+int launch_objective(gencd_problem* p, bool gap);  // P(w); with gap also the duality gap (after a finalize)
 int launch_col_sumsq(gencd_problem* p);  // gacc_j = sum_i X_ij^2
 int launch_inv_beta(gencd_problem* p);   // ib_j = 1 / beta_j for the current beta_mode
 int launch_mirror_w(gencd_problem* p);   // w32 from w (FP32 mode)
@@ -321,7 +325,7 @@ int validate_input(gencd_problem* p, int64_t* bad_col, int64_t* bad_row, int* st
 
 // gencd_create with the problem's device memory taken from `pool`
 // (stream-ordered on `stream`; NULL: cudaMalloc) and, when hpin is not NULL,
-// its pinned scalars lent by the caller (8 doubles, kept until destroy)
+// its pinned scalars lent by the caller (kScalars doubles, kept until destroy)
 int create_problem(gencd_problem** out, int64_t n, int64_t k, int64_t nnz, const int64_t* col_ptr,
                    const int32_t* row_idx, const void* val, int32_t val_dtype, const double* y, int32_t loss,
                    int32_t precision, int32_t memory, cudaStream_t stream, cudaMemPool_t pool, double* hpin);

@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ int s_n;
   __shared__ int64_t s_j[kRoundCols];
   __shared__ double s_g[kRoundCols], s_w[kRoundCols];
-  uint64_t vmax = 0;
+  uint64_t vmax = 0, gmax = 0;
   for (int64_t base = (int64_t)blockIdx.x * kRoundCols; base < k; base += (int64_t)gridDim.x * kRoundCols) {
     if (threadIdx.x == 0) s_n = 0;
     __syncthreads();
@@ -280,6 +280,7 @@ __global__ void __launch_bounds__(kThreads)
       double g, d, f;
       active_step(s_g[e], inv_n, s_w[e], lam, bjs[j], ib[j], g, d, f);
       max_bits(vmax, kkt_violation(g, s_w[e], lam));
+      max_bits(gmax, fabs(g));
       if (write_steps) {
         delta[j] = d;
         phi[j] = f;
@@ -288,6 +289,7 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();  // the queue is reused
   }
   block_max_bits_to(kkt_out, vmax);
+  block_max_bits_to(kkt_out + 7, gmax);  // max |g_j| over the active columns (idle ones have |g_j| <= lambda)
 }
 
 // Thread-Greedy with many partitions: one CTA per partition computes the
@@ -659,39 +661,62 @@ __device__ __forceinline__ double block_sum(double v, double* sm) {
   return s;
 }
 
+// Per-block partial sums of the loss and of |w_j|; with gap, also of the
+// conjugates l*(y_i, s u_i) of the dual point s u (u_i = l'(y_i, z_i) in
+// FP64, s = lambda / max(lambda, max_j |g_j|) from the finalize that ran
+// before: dscal[7]), so that ||X^T s u|| / n <= lambda.
 __global__ void __launch_bounds__(kThreads)
     k_objective_partial(const double* __restrict__ y, const double* __restrict__ z, int64_t n,
-                        const double* __restrict__ w, int64_t k, int loss, double* __restrict__ red) {
+                        const double* __restrict__ w, int64_t k, int loss, double lam, int gap,
+                        const double* __restrict__ dscal, double* __restrict__ red) {
   __shared__ double sm[kThreads / 32];
-  double sl = 0.0, sw = 0.0;
+  double sl = 0.0, sw = 0.0, sc = 0.0;
+  double scale = 1.0;
+  if (gap) {
+    const double gm = dscal[7];
+    scale = gm > lam ? lam / gm : 1.0;
+  }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (int64_t i = i0; i < n; i += stride) sl += loss_value(loss, y[i], z[i]);
+  for (int64_t i = i0; i < n; i += stride) {
+    sl += loss_value(loss, y[i], z[i]);
+    if (gap) sc += loss_conjugate(loss, y[i], scale * loss_deriv(loss, y[i], z[i]));
+  }
   for (int64_t j = i0; j < k; j += stride) sw += fabs(w[j]);
   sl = block_sum<kThreads>(sl, sm);
   sw = block_sum<kThreads>(sw, sm);
+  if (gap) sc = block_sum<kThreads>(sc, sm);
   if (threadIdx.x == 0) {
     red[blockIdx.x] = sl;
     red[kRedBlocks + blockIdx.x] = sw;
+    if (gap) red[2 * kRedBlocks + blockIdx.x] = sc;
   }
 }
 
 // fixed-order reduction of the per-block partials: lane l sums blocks
-// l, l+32, ...; then a fixed butterfly
-__global__ void k_objective_final(const double* __restrict__ red, int nblocks, double n, double lam,
+// l, l+32, ...; then a fixed butterfly.  gap: D = -(1/n) sum of conjugates
+// and dscal[9] = P(w) - D
+__global__ void k_objective_final(const double* __restrict__ red, int nblocks, double n, double lam, int gap,
                                   double* __restrict__ dscal) {
   const int lane = threadIdx.x & 31;
-  double sl = 0.0, sw = 0.0;
+  double sl = 0.0, sw = 0.0, sc = 0.0;
   for (int b = lane; b < nblocks; b += 32) {
     sl += red[b];
     sw += red[kRedBlocks + b];
+    if (gap) sc += red[2 * kRedBlocks + b];
   }
   sl = warp_sum(sl);
   sw = warp_sum(sw);
+  if (gap) sc = warp_sum(sc);
   if (threadIdx.x == 0) {
-    dscal[1] = (n > 0 ? sl / n : 0.0) + lam * sw;
+    const double P = (n > 0 ? sl / n : 0.0) + lam * sw;
+    dscal[1] = P;
     dscal[2] = sl;
     dscal[3] = sw;
+    if (gap) {
+      dscal[8] = sc;
+      dscal[9] = P + (n > 0 ? sc / n : 0.0);
+    }
   }
 }
 
@@ -903,14 +928,14 @@ int launch_propose_list(gencd_problem* p, const int32_t* J, int64_t m, double* d
   return GENCD_OK;
 }
 
-int launch_objective(gencd_problem* p) {
+int launch_objective(gencd_problem* p, bool gap) {
   const int64_t work = p->n > p->k ? p->n : p->k;
   const int grid = grid_for(work, kThreads, kRedBlocks);
   cudaEvent_t ev = nullptr;
   prof_begin(p, K_OBJECTIVE, &ev);
-  k_objective_partial<<<grid, kThreads, 0, p->stream>>>(p->y, p->z, p->n, p->w, p->k, p->loss,
-                                                        p->red);
-  k_objective_final<<<1, 32, 0, p->stream>>>(p->red, grid, (double)p->n, p->lambda, p->dscal);
+  k_objective_partial<<<grid, kThreads, 0, p->stream>>>(p->y, p->z, p->n, p->w, p->k, p->loss, p->lambda,
+                                                        gap ? 1 : 0, p->dscal, p->red);
+  k_objective_final<<<1, 32, 0, p->stream>>>(p->red, grid, (double)p->n, p->lambda, gap ? 1 : 0, p->dscal);
   prof_end(p, ev);
   p->prof.launches[K_OBJECTIVE] += 1;  // two launches per objective
   GENCD_CUDA_TRY(cudaGetLastError());

@@ -43,7 +43,7 @@ enum SlotState { kFree = 0, kLoading = 1, kRunning = 2 };
 struct Slot {
   int state = kFree;
   cudaStream_t st = nullptr;
-  double* hpin = nullptr;  // 8 pinned doubles lent to the slot's problem
+  double* hpin = nullptr;  // kScalars pinned doubles lent to the slot's problem
   gencd_problem* p = nullptr;
   SolveRun S;
   int64_t q = -1;
@@ -319,10 +319,10 @@ int run(Server& S) {
 int setup(Server& S, int slots) {
   S.slots.resize((size_t)slots);
   if (S.service) return GENCD_OK;
-  GENCD_CUDA_TRY(cudaMallocHost((void**)&S.pinned, sizeof(double) * 8 * (size_t)slots));
+  GENCD_CUDA_TRY(cudaMallocHost((void**)&S.pinned, sizeof(double) * kScalars * (size_t)slots));
   for (int i = 0; i < slots; ++i) {
     GENCD_CUDA_TRY(cudaStreamCreateWithFlags(&S.slots[(size_t)i].st, cudaStreamNonBlocking));
-    S.slots[(size_t)i].hpin = S.pinned + 8 * i;
+    S.slots[(size_t)i].hpin = S.pinned + kScalars * i;
   }
   cudaMemPoolProps props;
   std::memset(&props, 0, sizeof(props));

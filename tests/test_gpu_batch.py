@@ -255,3 +255,22 @@ def test_every_update_schedule_keeps_z_equal_to_xw(gb, update_kind):
             assert np.count_nonzero(w) > 0
             assert obj[s] == pytest.approx(orc.objective(w), rel=1e-12)
             assert orc.objective(w) < orc.objective(np.zeros(prob.k))
+
+
+def test_batch_path_to_a_duality_gap(gb):
+    # solves that stop at a relative duality gap of 1e-7 (the dual point's
+    # scale from FP32 sums) are certified by the oracle's FP64 gap to 1e-6
+    prob, fold = _problem("logistic", seed=11)
+    chains = [-1, 1]
+    with gb.Batch(prob, fold=fold, nfolds=NFOLDS, slots=32) as b:
+        b.set_params(variant="thread_greedy", blocks=64, tol_kkt=0.0, tol_gap=1e-7, check_every=5, max_iter=40_000)
+        lams = np.stack([workloads.lambda_grid(b.lambda_max(h), 4, 1e-2) for h in chains])
+        recs, W, tot = b.path(chains, lams, handoff=0.0, warm=True, want_w=True)
+    assert tot.status == 0, recs
+    for c, h in enumerate(chains):
+        sp = oracle.stored_problem(_subset(prob, fold, h), "f32")
+        for t in range(lams.shape[1]):
+            orc = oracle.Oracle(sp, lams[c, t])
+            P = orc.objective(W[c, t])
+            assert recs[c * lams.shape[1] + t]["objective"] == pytest.approx(P, rel=1e-9)
+            assert orc.duality_gap(W[c, t]) <= 1e-6 * P, (c, t)

@@ -665,3 +665,51 @@ def test_block_shotgun_solve_reaches_the_optimum(gb):
             p.set_params(variant="shotgun_blocks", blocks=1025)
     assert r.objective == pytest.approx(orc.objective(w_opt), rel=1e-6)
     assert_support_matches(prob, lam, w, w_opt, label="block shotgun")
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("name", ["cfg1-logistic", "cfg1-squared", "ragged-logistic", "zipf-slabs-squared"])
+def test_duality_gap_matches_the_oracle(gb, name, precision):
+    # the device's duality gap (objective, dual point from the FP64 loss
+    # derivative scaled by lambda / max |g|) against the oracle's at the same w
+    prob = PROBLEMS[name]()
+    orc = oracle.Oracle(prob)
+    lam = 0.05 * orc.lambda_max()
+    orc.set_lambda(lam)
+    w = _state(prob, 31)
+    with gb.Problem(prob, precision=precision) as p:
+        p.set_lambda(lam)
+        p.set_w(w)
+        gap, primal, dual = p.duality_gap()
+    sp = prob if precision == "f64" else oracle.stored_problem(prob, "f32")
+    o_s = oracle.Oracle(sp, lam)
+    gap_cpu = o_s.duality_gap(w)
+    P = o_s.objective(w)
+    assert primal == pytest.approx(P, rel=1e-13 if precision == "f64" else 1e-9)
+    # P and D are each accurate to their sums' rounding; the scale of D's
+    # dual point comes from max |g| in the problem's arithmetic
+    tol = 1e-11 if precision == "f64" else 1e-5
+    assert abs(gap - gap_cpu) <= tol * (abs(P) + abs(P - gap_cpu))
+    assert gap_cpu >= 0.0
+
+
+@pytest.mark.parametrize("loss", ["logistic", "squared"])
+def test_solve_to_a_duality_gap_certifies_the_objective(gb, loss):
+    # stopping at a relative duality gap of 1e-9 bounds (P(w) - P*) / P(w)
+    prob = workloads.uniform_problem(1000, 2000, 10, values="pm1", loss=loss, n_planted=30, seed=21)
+    orc = oracle.Oracle(prob)
+    lam = 0.05 * orc.lambda_max()
+    orc.set_lambda(lam)
+    w_opt, _, _, kkt, _ = orc.solve("ccd", tol_kkt=1e-11)
+    P_opt = orc.objective(w_opt)
+    with gb.Problem(prob) as p:
+        p.set_lambda(lam)
+        p.set_params(variant="thread_greedy", blocks=16, tol_kkt=0.0, tol_gap=1e-9, max_iter=400_000,
+                     check_every=50)
+        r = p.solve()
+        assert r.status == 0, r.as_dict()
+        w = p.w()
+        gap, primal, _ = p.duality_gap()
+    assert gap <= 1e-9 * abs(primal) * (1 + 1e-6)
+    assert orc.duality_gap(w) <= 1e-9 * abs(primal) * (1 + 1e-3)
+    assert (orc.objective(w) - P_opt) / P_opt <= 1e-9 * (1 + 1e-3)
