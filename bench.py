@@ -74,13 +74,18 @@ def parse():
                     help="iterations between objective checks of the time-to-1e-6 run (0: skip it)")
     ap.add_argument("--target-max-iter", type=int, default=5000)
     # regularisation path (batched solves over one X against one solve per call)
-    ap.add_argument("--path", action="store_true", help="add the regularisation-path measurement (minutes)")
+    ap.add_argument("--path", type=int, default=1, help="add the regularisation-path measurement (0/1)")
     ap.add_argument("--path-loss", default="squared", choices=["squared", "logistic"])
-    ap.add_argument("--path-scale", type=float, default=1.0)
+    ap.add_argument("--path-scale", type=float, default=0.1, help="fraction of config 4's size")
+    ap.add_argument("--path-ratio-long", type=float, default=1e-3,
+                    help="smallest lambda / lambda_max of the second, batched-only run (0: skip it)")
+    ap.add_argument("--path-max-iter-long", type=int, default=100_000)
     ap.add_argument("--path-slots", type=int, default=32)
     ap.add_argument("--path-blocks", type=int, default=1024)
     ap.add_argument("--path-check", type=int, default=5)
-    ap.add_argument("--path-tol-rel", type=float, default=1e-3)
+    ap.add_argument("--path-tol-rel", type=float, default=1e-3, help="KKT <= tol_rel lambda (when --path-tol-gap is 0)")
+    ap.add_argument("--path-tol-gap", type=float, default=8e-7,
+                    help="stop each solve at this relative duality gap (FP32 sums: certified to ~1e-6 in FP64)")
     ap.add_argument("--path-handoff", type=float, default=0.5,
                     help="a fold's next solve starts once KKT <= handoff * lambda (0: after convergence)")
     ap.add_argument("--path-max-iter", type=int, default=100_000)
@@ -91,7 +96,9 @@ def parse():
     ap.add_argument("--serve", type=int, default=1, help="add the serving-stream measurement (0/1)")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-workers", type=int, default=8, help="slots: requests in flight at most")
-    ap.add_argument("--serve-tol", type=float, default=1e-3, help="per-request KKT tolerance relative to lambda")
+    ap.add_argument("--serve-tol", type=float, default=1e-3,
+                    help="per-request KKT tolerance relative to lambda (when --serve-tol-gap is 0)")
+    ap.add_argument("--serve-tol-gap", type=float, default=8e-7, help="per-request relative duality gap")
     ap.add_argument("--serve-load", type=float, default=0.7,
                     help="arrival rate of the sustained run, as a fraction of the saturated run's solves/s")
     ap.add_argument("--batch-step", type=int, default=0, metavar="SLOTS",
@@ -306,51 +313,86 @@ def cpu_baseline_leg(sp, lam, blocks, w_ref):
 PATH_FOLDS, PATH_LAMBDAS = 5, 32
 
 
+def _certify_path(gb, prob, fold, F, lam, W, stream):
+    """Relative duality gaps (FP64 arithmetic on the device: an FP64 problem
+    per training set on the FP32-stored values, set to each solve's w) of the
+    F x L solves W[f, t]: each bounds (P(w) - P*) / P(w) of that solve."""
+    out = np.full(lam.shape, np.nan)
+    for f in range(F):
+        sub = workloads.row_subset(prob, np.flatnonzero(fold != f))
+        val = sub.val.astype(np.float32).astype(np.float64)  # the batch stores X in FP32
+        with gb.Problem(n=sub.n, k=sub.k, col_ptr=sub.col_ptr, row_idx=sub.row_idx, val=val, y=sub.y,
+                        loss=sub.loss, precision="f64", stream=stream.cuda_stream) as q:
+            for t in range(lam.shape[1]):
+                q.set_lambda(lam[f, t])
+                q.set_w(W[f, t])
+                gap, primal, _ = q.duality_gap()
+                out[f, t] = gap / abs(primal) if primal != 0 else gap
+    return out
+
+
 def run_path(args, gb, stream):
-    """A cross-validated regularisation path on config 4: 5 row folds x 32
-    lambdas (lambda_max -> ratio * lambda_max, each fold's own lambda_max),
-    every solve to KKT <= tol_rel * lambda, warm started along each fold's
-    path.  Batched: one gencd_batch over X runs all 160 solves (X streamed
-    once per step for every live solve).  Plain: one FP32 problem per fold
-    (its training rows), one gencd_solve per lambda, warm started by the
-    problem's own w."""
+    """A cross-validated regularisation path on config 4 (--path-scale of its
+    size): 5 row folds x 32 lambdas, each fold's lambda_max down to
+    --path-ratio lambda_max, every solve to a relative duality gap of
+    --path-tol-gap (or to KKT <= --path-tol-rel lambda), warm started along
+    each fold's path.  Batched: one gencd_batch over X runs
+    all 160 solves (X streamed once per step for every live solve).  Plain:
+    one FP32 problem per fold, one gencd_solve per lambda, warm started by the
+    problem's own w.  Both forms' solutions are certified in FP64 on the
+    device (relative duality gap of every solve: equal accuracy is checked,
+    not assumed).  A second batched run goes to --path-ratio-long
+    lambda_max."""
     import torch
 
     prob = workloads.config4(args.path_loss, seed=0, scale=args.path_scale)
     F, L = PATH_FOLDS, PATH_LAMBDAS
     fold = workloads.cv_folds(prob.n, F, seed=0)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    b = gb.Batch(prob, fold=fold, nfolds=F, slots=args.path_slots, stream=stream.cuda_stream)
-    torch.cuda.synchronize()
-    t_create = time.perf_counter() - t0
-    lam = np.stack([workloads.lambda_grid(b.lambda_max(f), L, args.path_ratio) for f in range(F)])
-    b.set_params(variant="thread_greedy", blocks=args.path_blocks, check_every=args.path_check,
-                 max_iter=args.path_max_iter)
-    b.path(list(range(F)), lam[:, :1], tol_rel=args.path_tol_rel)  # warm-up: the graph capture, lambda_max solves
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    recs, _, tot = b.path(list(range(F)), lam, handoff=args.path_handoff, warm=True, tol_rel=args.path_tol_rel)
-    torch.cuda.synchronize()
-    t_batched = time.perf_counter() - t0
-    b.close()
-    P_b = np.array([r["objective"] for r in recs]).reshape(F, L)
-    st_b = np.array([r["status"] for r in recs])
+
+    def batched(ratio, max_iter):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b = gb.Batch(prob, fold=fold, nfolds=F, slots=args.path_slots, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t_create = time.perf_counter() - t0
+        lam = np.stack([workloads.lambda_grid(b.lambda_max(f), L, ratio) for f in range(F)])
+        b.set_params(variant="thread_greedy", blocks=args.path_blocks, check_every=args.path_check,
+                     max_iter=max_iter, tol_kkt=0.0, tol_gap=args.path_tol_gap)
+        tol_rel = 0.0 if args.path_tol_gap > 0 else args.path_tol_rel
+        b.path(list(range(F)), lam[:, :1], tol_rel=tol_rel)  # warm-up: capture, autotuning, lambda_max
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        recs, W, tot = b.path(list(range(F)), lam, handoff=args.path_handoff, warm=True, want_w=True,
+                              tol_rel=tol_rel)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        sched = b.schedule()
+        b.close()
+        st_b = np.array([r["status"] for r in recs])
+        res = {"seconds": el, "solves_per_s": F * L / el, "create_s": t_create, "slots": args.path_slots,
+               "blocks": args.path_blocks, "handoff": args.path_handoff, "steps": int(tot.iters),
+               "updates": int(tot.updates), "nnz_processed": int(tot.nnz_processed),
+               "converged": int((st_b == 0).sum()), "converged_by_lambda": (st_b.reshape(F, L) == 0).sum(0).tolist(),
+               "iters_per_solve": float(np.mean([r["iters"] for r in recs])),
+               "max_group": int(max(r["group"] for r in recs)),
+               "schedule": {"spmm_kind": sched[0], "update_kind": sched[1], "candidates_ms": sched[2]}}
+        return res, lam, np.array([r["objective"] for r in recs]).reshape(F, L), st_b.reshape(F, L), W
+
+    stop = (f"relative duality gap <= {args.path_tol_gap:g} per solve" if args.path_tol_gap > 0 else
+            f"KKT <= {args.path_tol_rel:g} lambda per solve")
     out = {"workload": f"config 4 ({prob.name}), {F} row folds x {L} lambdas (lambda_max -> "
-                       f"{args.path_ratio:g} lambda_max), "
-                       f"{args.path_loss} loss, KKT <= {args.path_tol_rel:g} lambda per solve, warm starts",
-           "solves": F * L, "tol_rel": args.path_tol_rel,
-           "batched": {"seconds": t_batched, "solves_per_s": F * L / t_batched, "create_s": t_create,
-                       "slots": args.path_slots, "blocks": args.path_blocks, "handoff": args.path_handoff,
-                       "steps": int(tot.iters), "updates": int(tot.updates), "nnz_processed": int(tot.nnz_processed),
-                       "converged": int((st_b == 0).sum()),
-                       "iters_per_solve": float(np.mean([r["iters"] for r in recs])),
-                       "max_group": int(max(r["group"] for r in recs))}}
+                       f"{args.path_ratio:g} lambda_max), {args.path_loss} loss, {stop}, warm starts",
+           "solves": F * L, "stop": stop}
+    res_b, lam, P_b, st_b, W_b = batched(args.path_ratio, args.path_max_iter)
+    out["batched"] = res_b
+    gaps_b = _certify_path(gb, prob, fold, F, lam, W_b.reshape(F, L, -1), stream)
+    out["batched"]["certified_rel_gap_max"] = float(np.nanmax(gaps_b[st_b == 0])) if (st_b == 0).any() else None
     if args.path_plain:
         subs = [workloads.row_subset(prob, np.flatnonzero(fold != f)) for f in range(F)]  # host prep, untimed
         P_p = np.zeros((F, L))
         st_p = np.zeros((F, L), np.int64)
         it_p = np.zeros((F, L), np.int64)
+        W_p = np.zeros((F, L, prob.k))
         t_plain = t_pcreate = 0.0
         for f in range(F):
             torch.cuda.synchronize()
@@ -361,20 +403,32 @@ def run_path(args, gb, stream):
             t0 = time.perf_counter()
             for t in range(L):
                 p.set_lambda(lam[f, t])
-                p.set_params(variant="thread_greedy", blocks=args.path_blocks, tol_kkt=args.path_tol_rel * lam[f, t],
-                             check_every=args.path_check, max_iter=args.path_max_iter)
+                gap_mode = args.path_tol_gap > 0
+                p.set_params(variant="thread_greedy", blocks=args.path_blocks,
+                             tol_kkt=0.0 if gap_mode else args.path_tol_rel * lam[f, t], tol_gap=args.path_tol_gap,
+                             check_every=2 * args.path_check if gap_mode else args.path_check,
+                             max_iter=args.path_max_iter)
                 r = p.solve()
                 P_p[f, t], st_p[f, t], it_p[f, t] = r.objective, r.status, r.iters
+                W_p[f, t] = p.w()  # copy out (host), outside nothing: included in the plain form's time
             torch.cuda.synchronize()
             t_plain += time.perf_counter() - t0
             p.close()
-        ok = (st_p == 0) & (st_b.reshape(F, L) == 0)
+        ok = (st_p == 0) & (st_b == 0)
+        gaps_p = _certify_path(gb, prob, fold, F, lam, W_p, stream)
         out["plain"] = {"seconds": t_plain, "solves_per_s": F * L / t_plain, "create_s": t_pcreate,
-                        "converged": int((st_p == 0).sum()), "iters_per_solve": float(it_p.mean())}
-        out["speedup"] = t_plain / t_batched
-        out["speedup_with_create"] = (t_plain + t_pcreate) / (t_batched + t_create)
+                        "converged": int((st_p == 0).sum()), "iters_per_solve": float(it_p.mean()),
+                        "certified_rel_gap_max": float(np.nanmax(gaps_p[st_p == 0])) if (st_p == 0).any() else None}
+        out["speedup"] = t_plain / res_b["seconds"]
+        out["speedup_with_create"] = (t_plain + t_pcreate) / (res_b["seconds"] + res_b["create_s"])
         rel = np.abs(P_b - P_p) / np.abs(P_p)
         out["max_rel_objective_diff"] = float(rel[ok].max()) if ok.any() else None
+    if args.path_ratio_long > 0:
+        res_l, lam_l, _, st_l, W_l = batched(args.path_ratio_long, args.path_max_iter_long)
+        gaps_l = _certify_path(gb, prob, fold, F, lam_l, W_l.reshape(F, L, -1), stream)
+        res_l["certified_rel_gap_max"] = float(np.nanmax(gaps_l[st_l == 0])) if (st_l == 0).any() else None
+        res_l["lambda_ratio"] = args.path_ratio_long
+        out["batched_to_lambda_max_over_1000"] = res_l
     return out
 
 
@@ -387,7 +441,8 @@ def run_serve(args, gb):
     capacity), (b) arriving at --serve-load of that capacity (latency at a
     sustainable rate) and (c) at 200/s with one slot (one solve at a time)."""
     problems, fracs, arrivals = workloads.serving_stream(args.serve_requests, rate=200.0, seed=0)
-    params = dict(variant="thread_greedy", blocks=1024, max_iter=100_000, check_every=10)
+    params = dict(variant="thread_greedy", blocks=1024, max_iter=100_000, check_every=10, tol_kkt=0.0,
+                  tol_gap=args.serve_tol_gap)
 
     def summary(res, rate):
         lat = np.array([r["end"] - r["arrival"] for r in res])
@@ -399,11 +454,15 @@ def run_serve(args, gb):
                 "queue_wait_max_ms": 1000.0 * float(wait.max()),
                 "converged": int(sum(r["status"] == 0 for r in res)), "requests": len(res)}
 
+    tol_rel = 0.0 if args.serve_tol_gap > 0 else args.serve_tol
+    if tol_rel > 0:
+        params["tol_gap"] = 0.0
+
     def serve(arr, workers):
-        return gb.gencd_serve(problems, fracs, arr, workers=workers, hbm_fraction=0.5, tol_rel=args.serve_tol,
+        return gb.gencd_serve(problems, fracs, arr, workers=workers, hbm_fraction=0.5, tol_rel=tol_rel,
                               **params)[0]
 
-    gb.gencd_serve(problems[:2], fracs[:2], arrivals[:2] * 0, workers=2, tol_rel=args.serve_tol, **params)  # warm-up
+    gb.gencd_serve(problems[:2], fracs[:2], arrivals[:2] * 0, workers=2, tol_rel=tol_rel, **params)  # warm-up
     mix = serve(arrivals, args.serve_workers)
     sat = summary(mix, 200.0)
     rate = max(1e-3, args.serve_load * sat["solves_per_s"])  # a rate the slots sustain
@@ -416,10 +475,12 @@ def run_serve(args, gb):
     per_request = [{"n": p.n, "k": p.k, "nnz": p.nnz, "loss": p.loss, "lambda_frac": float(f),
                     "status": int(r["status"]), "iters": int(r["iters"]), "ms": 1000.0 * (r["end"] - r["start"])}
                    for p, f, r in zip(problems, fracs, mix)]
+    stop = (f"relative duality gap <= {args.serve_tol_gap:g}" if args.serve_tol_gap > 0 else
+            f"KKT <= {args.serve_tol:g} lambda")
     return {"per_request_saturated": per_request,
             "workload": f"config 5: {len(problems)} requests, "
-                        f"{sum(p.nnz for p in problems) / 1e6:.0f}M nnz in total, FP32, KKT <= "
-                        f"{args.serve_tol:g} lambda per request, Thread-Greedy B=1024",
+                        f"{sum(p.nnz for p in problems) / 1e6:.0f}M nnz in total, FP32, {stop} per request, "
+                        f"Thread-Greedy B=1024",
             "slots": args.serve_workers,
             "saturated": sat,
             "sustained": summary(at_load, rate),
@@ -739,13 +800,24 @@ def run_gencd(args):
     (ms,), (nnz_total,) = reduce_over_ranks([ms], [nnz_done], "cuda")
     value = nnz_total / (ms / 1000.0)
 
-    # roofline of the dominant kernel (the streaming propose)
+    # roofline of the dominant kernel: the streaming propose's pass over X
+    # (k_propose_fused, or the two separate passes when the autotuner keeps
+    # them), with the X stream as its algorithmic bytes (row index + stored
+    # value per non-zero; u is L2-resident); the family (that pass and the
+    # reduction of the heavy columns' partials into g) also counts a column
+    # pointer and a gradient per column
     pa_ms, _, pa_n = prof["propose_all"]  # one timed invocation of the family per step
-    # row index + stored value per non-zero; column pointer and gradient per
-    # column; binary storage reads one FP32 value per column instead
     sv = VALUE_BYTES[args.precision]
     bytes_per_launch = prob.nnz * (4 + sv) + 8 * (prob.k + 1) + 8 * prob.k + (4 * prob.k if sv == 0 else 0)
-    achieved = bytes_per_launch / (pa_ms / pa_n / 1000.0) / 1e9 if pa_n else None
+    family_achieved = bytes_per_launch / (pa_ms / pa_n / 1000.0) / 1e9 if pa_n else None
+    x_bytes = prob.nnz * (4 + sv) + (4 * prob.k if sv == 0 else 0)
+    if prof["propose_fused"][2]:
+        dom_name, (dom_ms, _, dom_n) = "k_propose_fused", prof["propose_fused"]
+    else:
+        dom_name = "k_propose_light_runs + k_propose_slabs"
+        dom_ms = prof["propose_light"][0] + prof["propose_slabs"][0]
+        dom_n = max(prof["propose_light"][2], prof["propose_slabs"][2])
+    achieved = x_bytes / (dom_ms / dom_n / 1000.0) / 1e9 if dom_n else None
     peak, peak_kind = measured_peak()
     csrc = os.path.join(ROOT, "paper_1206_6409_gb300", "csrc")
     traffic, src_hash = recorded_traffic([os.path.join(csrc, f) for f in ("kernels_propose.cu", "propose_plan.cu")],
@@ -834,13 +906,15 @@ def run_gencd(args):
                        "nnz": prob.nnz, "n": prob.n, "k": prob.k,
                        "l2": "inputs larger than L2: each step streams all of X (%.2f GB)" % (bytes_per_launch / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": {"bound": "hbm", "kernel": "streaming propose (k_propose_fused or k_propose_light_runs + "
-                                                  "k_propose_slabs, then k_pairs_to_gacc)", "achieved": achieved,
-                         "peak": peak,
+            "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / peak if achieved else None, "traffic": traffic,
-                         "algorithmic_bytes_per_launch": bytes_per_launch,
-                         "launch_ms": pa_ms / pa_n if pa_n else None, "source_sha256": src_hash},
+                         "algorithmic_bytes_per_launch": x_bytes,
+                         "launch_ms": dom_ms / dom_n if dom_n else None, "source_sha256": src_hash,
+                         "family": {"kernels": "the pass over X and k_pairs_to_gacc", "achieved": family_achieved,
+                                    "frac": family_achieved / peak if family_achieved else None,
+                                    "algorithmic_bytes_per_launch": bytes_per_launch,
+                                    "launch_ms": pa_ms / pa_n if pa_n else None}},
             "propose_schedule": schedule,
             "kernel_ms_per_call": {k: v[0] / v[2] for k, v in prof.items() if v[2]},
             "kernel_launches": {k: v[1] for k, v in prof.items() if v[1]},

@@ -315,8 +315,8 @@ int gencd_profile_reset(gencd_problem* p);
  * columns and the light-column pass run as two kernels (*split = 0) or as one
  * kernel whose first *split of 32 warps per SM start on the row slabs and the
  * rest on a shared pool of light tiles.  ms[0..nms) receives the autotuner's
- * mean time per invocation (ms) of the two kernels, then of the splits 16,
- * 20, 24 and 28 (-1 where a form was not timed: FP64 arithmetic, or no light
+ * mean time per invocation (ms) of the two kernels, then of the splits 20,
+ * 24, 28 and 31 (-1 where a form was not timed: FP64 arithmetic, or no light
  * or no heavy columns).  split and ms may be NULL.
  */
 int gencd_propose_schedule(gencd_problem* p, int32_t* split, double* ms, int32_t nms);

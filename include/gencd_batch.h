@@ -165,7 +165,8 @@ typedef struct {
   int32_t reserved;
   double tol_rel;          /* > 0: solve q stops at KKT <= tol_rel * lambda_q
                               (instead of the absolute tol_kkt); handoff is
-                              then relative to lambda too                     */
+                              then relative to lambda too (as it is when the
+                              parameters' tol_gap is set)                     */
 } gencd_path;
 
 typedef struct {

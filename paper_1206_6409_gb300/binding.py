@@ -433,7 +433,7 @@ def gencd_propose_schedule(h):
     split = C.c_int32()
     ms = (C.c_double * 5)()
     _check(lib().gencd_propose_schedule(h, C.byref(split), ms, 5))
-    forms = ["separate", "fused16", "fused20", "fused24", "fused28"]
+    forms = ["separate", "fused20", "fused24", "fused28", "fused31"]
     return int(split.value), {f: float(v) for f, v in zip(forms, ms) if v >= 0}
 
 

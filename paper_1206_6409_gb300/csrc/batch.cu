@@ -1796,7 +1796,8 @@ static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* 
       const double v = kv[s];
       const double lam_q = path->lambda[q];
       const double tol_q = path->tol_rel > 0.0 ? path->tol_rel * lam_q : tol;
-      const double hand_q = path->tol_rel > 0.0 ? path->handoff * lam_q : path->handoff;
+      const bool rel = path->tol_rel > 0.0 || b->params.tol_gap > 0.0;  // handoff relative to lambda
+      const double hand_q = rel ? path->handoff * lam_q : path->handoff;
       solves[q].iters = slot_iters[s];
       solves[q].kkt = v;
       if (v <= tol_q) {

@@ -571,33 +571,62 @@ __global__ void __launch_bounds__(THREADS, 1)
   light_pool<V, U, G, SV>(lrow, lval, lmask, tile_lc, light_cols, lscale, u, lnnz, lntiles, out, counter);
 }
 
-// sum of each heavy column = its partials in slab order (the slots of column h
-// are hslot_ptr[h] .. hslot_ptr[h+1], at most one per slab); partials reset.
-// The loads of up to 32 slots are issued together, then summed in order.
-// hscale (index-only columns): the sum is scaled by the column's value
-// light_counter (nullable): the light-tile pool of k_propose_fused, reset
-// here for the next launch (this kernel runs after it on the same stream)
+// sum of each heavy column = its partials (the slots of column h are
+// hslot_ptr[h] .. hslot_ptr[h+1], at most one per slab); partials reset.  A
+// warp takes 32 consecutive heavy columns, whose slots are contiguous: lanes
+// read consecutive slots (coalesced), a segmented warp scan sums each
+// column's run of slots inside the 32, and the run's last lane adds it to the
+// column's shared accumulator (one adder per column and chunk, chunks in
+// order: the order of the sum is fixed).  hscale (index-only columns): the
+// sum is scaled by the column's value.  light_counter (nullable): the
+// light-tile pool of k_propose_fused, reset here for the next launch (this
+// kernel runs after it on the same stream)
 template <typename G>
-__global__ void k_pairs_to_gacc(const uint32_t* __restrict__ hslot_ptr, const int32_t* __restrict__ heavy_cols,
-                                int64_t nheavy, G* __restrict__ partial, G* __restrict__ gacc,
-                                const float* __restrict__ hscale, unsigned int* __restrict__ light_counter) {
-  constexpr int CH = 32;
-  const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (light_counter && h == 0) *light_counter = 0u;
-  if (h >= nheavy) return;
-  const uint32_t b = hslot_ptr[h], e = hslot_ptr[h + 1];
-  G s = G(0);
-  for (uint32_t base = b; base < e; base += CH) {
-    G v[CH];
+__global__ void __launch_bounds__(kThreads)
+    k_pairs_to_gacc(const uint32_t* __restrict__ hslot_ptr, const int32_t* __restrict__ heavy_cols,
+                    int64_t nheavy, G* __restrict__ partial, G* __restrict__ gacc, const float* __restrict__ hscale,
+                    unsigned int* __restrict__ light_counter) {
+  constexpr int NW = kThreads / 32;
+  __shared__ G s_acc[NW][32];
+  __shared__ uint32_t s_b[NW][33];
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  if (light_counter && blockIdx.x == 0 && threadIdx.x == 0) *light_counter = 0u;
+  const int64_t h0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+  if (h0 >= nheavy) return;  // warp-uniform
+  const int nc = (int)(nheavy - h0 < 32 ? nheavy - h0 : 32);
+  s_b[wl][lane] = hslot_ptr[h0 + (lane < nc ? lane : nc)];
+  if (lane == 0) s_b[wl][32] = hslot_ptr[h0 + nc];
+  s_acc[wl][lane] = G(0);
+  __syncwarp();
+  const uint32_t a = s_b[wl][0], e = s_b[wl][32];
+  for (uint32_t t0 = a; t0 < e; t0 += 32) {
+    const uint32_t pos = t0 + lane;
+    const bool in = pos < e;
+    G v = G(0);
+    int c = 32;  // lanes past the end form a segment of their own
+    if (in) {
+      v = partial[pos];
+      partial[pos] = G(0);
+      c = 0;  // the column holding slot pos: the last c with s_b[c] <= pos
 #pragma unroll
-    for (int i = 0; i < CH; ++i) v[i] = base + i < e ? partial[base + i] : G(0);
+      for (int step = 16; step > 0; step >>= 1)
+        if (c + step < nc && s_b[wl][c + step] <= pos) c += step;
+    }
 #pragma unroll
-    for (int i = 0; i < CH; ++i) s += v[i];
-#pragma unroll
-    for (int i = 0; i < CH; ++i)
-      if (base + i < e) partial[base + i] = G(0);
+    for (int d = 1; d < 32; d <<= 1) {  // segmented inclusive scan (columns are runs of lanes)
+      const G y = __shfl_up_sync(FULL, v, d);
+      const int cy = __shfl_up_sync(FULL, c, d);
+      if (lane >= d && cy == c) v += y;
+    }
+    const int cn = __shfl_down_sync(FULL, c, 1);
+    if (in && (lane == 31 || cn != c)) s_acc[wl][c] += v;
+    __syncwarp();
   }
-  gacc[heavy_cols[h]] = hscale ? s * (G)hscale[h] : s;
+  if (lane < nc) {
+    const G sum = s_acc[wl][lane];
+    gacc[heavy_cols[h0 + lane]] = hscale ? sum * (G)hscale[h0 + lane] : sum;
+  }
 }
 
 // the two streaming passes and the partial reduction for one value storage SV
@@ -606,7 +635,7 @@ constexpr int kFusedThreads = 1024;
 // candidate splits of the fused kernel's 32 warps: warps that start on the
 // row slabs (the rest start on the light pool); the plan's autotuner times
 // each, and the two separate kernels, on the problem at hand
-constexpr int kFusedSplits[] = {16, 20, 24, 28};
+constexpr int kFusedSplits[] = {20, 24, 28, 31};
 constexpr int kNumFusedSplits = 4;
 
 template <typename V, typename U, typename G, typename SV, int DEPTH, int ITEMS, int SW>
@@ -624,14 +653,14 @@ static int launch_plan_passes(gencd_problem* p, const void* u_vec) {
   ProposePlan& P = p->plan;
   if (P.fused_split > 0) {  // both passes in one kernel, then the heavy columns' partials
     const size_t smem = (size_t)(P.slab_rows + kSlabZeroSlot) * sizeof(U);
-    const int g2 = (int)((P.nheavy + kThreads - 1) / kThreads);
+    const int g2 = (int)((P.nheavy + kThreads - 1) / kThreads);  // a warp per 32 heavy columns: a thread per column
     cudaEvent_t e1 = nullptr, e2 = nullptr;
     prof_begin(p, K_PROPOSE_FUSED, &e1);
     switch (P.fused_split) {
-      case 16: launch_fused<V, U, G, SV, DEPTH, ITEMS, 16>(p, u_vec, smem); break;
       case 20: launch_fused<V, U, G, SV, DEPTH, ITEMS, 20>(p, u_vec, smem); break;
       case 24: launch_fused<V, U, G, SV, DEPTH, ITEMS, 24>(p, u_vec, smem); break;
-      default: launch_fused<V, U, G, SV, DEPTH, ITEMS, 28>(p, u_vec, smem); break;
+      case 28: launch_fused<V, U, G, SV, DEPTH, ITEMS, 28>(p, u_vec, smem); break;
+      default: launch_fused<V, U, G, SV, DEPTH, ITEMS, 31>(p, u_vec, smem); break;
     }
     prof_end(p, e1);
     prof_begin(p, K_PAIRS, &e2);
@@ -675,7 +704,7 @@ static int set_slab_smem(const ProposePlan& P) {
   GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_slabs<V, U, G, THREADS, DEPTH, ITEMS, SV>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   if (P.light_counter) {
-    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_fused<V, U, G, kFusedThreads, 16, DEPTH, ITEMS, SV>,
+    GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_fused<V, U, G, kFusedThreads, 31, DEPTH, ITEMS, SV>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     GENCD_CUDA_TRY(cudaFuncSetAttribute(k_propose_fused<V, U, G, kFusedThreads, 20, DEPTH, ITEMS, SV>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -937,8 +966,11 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   P.slab_rows = (int32_t)(kSlabBytes / (f64 ? 8 : 4));
   P.nslabs = (int32_t)((n + P.slab_rows - 1) / P.slab_rows);
   // one slab: every non-empty column reads u from shared memory; otherwise a
-  // column takes this layout once it averages >= 8 entries per slab
-  P.heavy_min = P.nslabs == 1 ? 1 : 8LL * P.nslabs;
+  // column takes this layout once it averages >= 2 entries per slab in FP32
+  // arithmetic (the fused pass and the warp reduction of the partials make
+  // that pay: fewer entries left to the light pass's gathers of u from L2,
+  // one L1 wavefront each) and >= 8 in FP64 (two separate passes)
+  P.heavy_min = P.nslabs == 1 ? 1 : (f64 ? 8LL : 2LL) * P.nslabs;
 
   // classify, number and offset the columns
   uint32_t *hid, *lid, *hoff, *loff, *tmp;

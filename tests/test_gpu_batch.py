@@ -233,9 +233,10 @@ def test_every_schedule_proposes_like_the_oracle(gb, slots, spmm_kind):
 @pytest.mark.parametrize("update_kind", [0, 1])
 def test_every_update_schedule_keeps_z_equal_to_xw(gb, update_kind):
     # after steps with either update form, each slot's fitted values are X w
-    # (its FP64 objective equals the oracle's at its w) and w moved only where
-    # the proposals allowed; slots share columns (the same training set and
-    # lambda in groups of four), so the grouped form's shared walks are taken
+    # (its FP64 objective equals the oracle's at its w, whatever the steps
+    # did: plain Thread-Greedy may diverge here); slots share columns (the same
+    # training set and lambda in groups of four), so the grouped form's shared
+    # walks are taken
     prob, fold = _problem("squared", seed=17)
     with gb.Batch(prob, fold=fold, nfolds=NFOLDS, slots=32) as b:
         b.set_params(variant="thread_greedy", blocks=64)
@@ -254,7 +255,6 @@ def test_every_update_schedule_keeps_z_equal_to_xw(gb, update_kind):
             w = b.w(s)
             assert np.count_nonzero(w) > 0
             assert obj[s] == pytest.approx(orc.objective(w), rel=1e-12)
-            assert orc.objective(w) < orc.objective(np.zeros(prob.k))
 
 
 def test_batch_path_to_a_duality_gap(gb):
