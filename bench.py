@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--blocks", type=int, default=1024)
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the full workload (tests)")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--propose-split", type=int, default=-1,
+                    help="streaming propose schedule (-1: the autotuner's; 0: two kernels; 20-31: fused split), "
+                         "e.g. to profile one form under ncu, whose replays distort the autotuner's timings")
     ap.add_argument("--legs", type=int, default=1,
                     help="also time config 2 in the other storage modes and variants, and config 1 (0/1)")
     ap.add_argument("--leg-steps", type=int, default=30, help="timed iterations of each config-2 leg")
@@ -92,7 +95,8 @@ def parse():
     ap.add_argument("--path-ratio", type=float, default=1e-2,
                     help="smallest lambda / lambda_max of the path (below ~1/250 on this workload the solutions "
                          "near interpolation and Thread-Greedy stalls)")
-    ap.add_argument("--path-plain", type=int, default=1, help="also time the one-solve-per-call form (0/1)")
+    ap.add_argument("--path-plain", type=int, default=2,
+                    help="also time the one-solve-per-call form on this many folds' chains (0: skip it)")
     ap.add_argument("--serve", type=int, default=1, help="add the serving-stream measurement (0/1)")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-workers", type=int, default=8, help="slots: requests in flight at most")
@@ -388,13 +392,16 @@ def run_path(args, gb, stream):
     gaps_b = _certify_path(gb, prob, fold, F, lam, W_b.reshape(F, L, -1), stream)
     out["batched"]["certified_rel_gap_max"] = float(np.nanmax(gaps_b[st_b == 0])) if (st_b == 0).any() else None
     if args.path_plain:
-        subs = [workloads.row_subset(prob, np.flatnonzero(fold != f)) for f in range(F)]  # host prep, untimed
-        P_p = np.zeros((F, L))
-        st_p = np.zeros((F, L), np.int64)
-        it_p = np.zeros((F, L), np.int64)
-        W_p = np.zeros((F, L, prob.k))
+        # the plain form on the first --path-plain folds' chains (its solves/s
+        # is per solve, so a subset keeps the benchmark short)
+        Fp = max(1, min(F, args.path_plain))
+        subs = [workloads.row_subset(prob, np.flatnonzero(fold != f)) for f in range(Fp)]  # host prep, untimed
+        P_p = np.zeros((Fp, L))
+        st_p = np.zeros((Fp, L), np.int64)
+        it_p = np.zeros((Fp, L), np.int64)
+        W_p = np.zeros((Fp, L, prob.k))
         t_plain = t_pcreate = 0.0
-        for f in range(F):
+        for f in range(Fp):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             p = gb.Problem(subs[f], precision="f32", stream=stream.cuda_stream)
@@ -414,14 +421,17 @@ def run_path(args, gb, stream):
             torch.cuda.synchronize()
             t_plain += time.perf_counter() - t0
             p.close()
-        ok = (st_p == 0) & (st_b == 0)
-        gaps_p = _certify_path(gb, prob, fold, F, lam, W_p, stream)
-        out["plain"] = {"seconds": t_plain, "solves_per_s": F * L / t_plain, "create_s": t_pcreate,
-                        "converged": int((st_p == 0).sum()), "iters_per_solve": float(it_p.mean()),
-                        "certified_rel_gap_max": float(np.nanmax(gaps_p[st_p == 0])) if (st_p == 0).any() else None}
-        out["speedup"] = t_plain / res_b["seconds"]
-        out["speedup_with_create"] = (t_plain + t_pcreate) / (res_b["seconds"] + res_b["create_s"])
-        rel = np.abs(P_b - P_p) / np.abs(P_p)
+        ok = (st_p == 0) & (st_b[:Fp] == 0)
+        gaps_p = _certify_path(gb, prob, fold, Fp, lam[:Fp], W_p, stream)
+        out["plain"] = {"seconds": t_plain, "solves": Fp * L, "solves_per_s": Fp * L / t_plain,
+                        "create_s": t_pcreate, "converged": int((st_p == 0).sum()),
+                        "iters_per_solve": float(it_p.mean()),
+                        "certified_rel_gap_max": float(np.nanmax(gaps_p[st_p == 0])) if (st_p == 0).any() else None,
+                        "folds": Fp}
+        out["speedup"] = res_b["solves_per_s"] / out["plain"]["solves_per_s"]
+        out["speedup_with_create"] = (F * L / (res_b["seconds"] + res_b["create_s"])) / \
+            (Fp * L / (t_plain + t_pcreate))
+        rel = np.abs(P_b[:Fp] - P_p) / np.abs(P_p)
         out["max_rel_objective_diff"] = float(rel[ok].max()) if ok.any() else None
     if args.path_ratio_long > 0:
         res_l, lam_l, _, st_l, W_l = batched(args.path_ratio_long, args.path_max_iter_long)
@@ -728,7 +738,9 @@ def leg_config1(args, gb, stream):
                         p.spectral_radius()
                     else:
                         p.color()
-                    p.set_params(variant=variant, tol_kkt=1e-9, max_iter=5_000_000, check_every=200, seed=0)
+                    # Coloring takes about 1.5e6 iterations to 1e-9 on the logistic problem: capped
+                    p.set_params(variant=variant, tol_kkt=1e-9, max_iter=300_000 if variant == "coloring" else 5_000_000,
+                                 check_every=200, seed=0)
                     p.solve()  # warm-up (kernel loading), then the same solve from w = 0
                     p.set_w(np.zeros(prob.k))
                     p.set_iteration(0)
@@ -765,6 +777,8 @@ def run_gencd(args):
     lam = 0.05 * p.lambda_max()
     p.set_lambda(lam)
     p.set_params(variant=args.variant, blocks=args.blocks, seed=0)
+    if args.propose_split >= 0:
+        gb.gencd_set_propose_schedule(p.h, args.propose_split)
     split, tuned = gb.gencd_propose_schedule(p.h)
     schedule = {"fused_split": split, "candidates_ms": tuned,
                 "form": "separate light and slab kernels" if split == 0 else

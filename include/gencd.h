@@ -182,8 +182,10 @@ int gencd_get_params(gencd_problem* p, gencd_params* params);
  * Thread-Greedy keeps of every G consecutive partitions only the best
  * accepted proxy while top-|J'| accepts the max(1, B/G) lowest proxies.
  * G = B is Greedy, whose steps always lower the objective.  A solve that
- * converges never restarts.  G returns to 1 at gencd_set_params;
- * gencd_iterate applies the current G.
+ * converges never restarts.  A solve that oscillates below its start value
+ * (no new lowest KKT violation over 50 checks while the objective fell by
+ * less than 1e-9 of itself over them) doubles G without a restart.  G returns
+ * to 1 at gencd_set_params; gencd_iterate applies the current G.
  * `out` (nullable) receives the statistics of the call.
  */
 int gencd_solve(gencd_problem* p, gencd_result* out);
@@ -320,6 +322,11 @@ int gencd_profile_reset(gencd_problem* p);
  * or no heavy columns).  split and ms may be NULL.
  */
 int gencd_propose_schedule(gencd_problem* p, int32_t* split, double* ms, int32_t nms);
+/* Sets that schedule (every form computes the same sums): 0 the two kernels,
+ * 20, 24, 28 or 31 the fused kernel with that many slab warps, -1 runs the
+ * autotuner again.  GENCD_EINVAL for another value, or a fused split on a
+ * problem whose propose has one form only. */
+int gencd_set_propose_schedule(gencd_problem* p, int32_t split);
 
 /*
  * gencd_propose_all_noalloc -- the streaming Propose over all k columns

@@ -49,7 +49,7 @@ EXPORTS = ["gencd_create", "gencd_destroy", "gencd_set_lambda", "gencd_set_loss"
            "gencd_spectral_radius", "gencd_color", "gencd_color_balanced_csc", "gencd_get_colors", "gencd_set_colors",
            "gencd_permutation", "gencd_profile_enable", "gencd_profile_read", "gencd_profile_reset",
            "gencd_last_error", "gencd_stats", "gencd_stats_reset", "gencd_propose_all_noalloc",
-           "gencd_propose_schedule", "gencd_block_pstar", "gencd_duality_gap",
+           "gencd_propose_schedule", "gencd_set_propose_schedule", "gencd_block_pstar", "gencd_duality_gap",
            # include/gencd_batch.h
            "gencd_batch_create", "gencd_batch_destroy", "gencd_batch_slots", "gencd_batch_lambda_max",
            "gencd_batch_set_params", "gencd_batch_set_slot", "gencd_batch_copy_slot", "gencd_batch_clear_slot",
@@ -153,6 +153,7 @@ def lib():
             "gencd_profile_read": (C.c_int, [vp, i32, C.POINTER(f64), C.POINTER(i64), C.POINTER(i64)]),
             "gencd_profile_reset": (C.c_int, [vp]),
             "gencd_propose_schedule": (C.c_int, [vp, C.POINTER(i32), C.POINTER(f64), i32]),
+            "gencd_set_propose_schedule": (C.c_int, [vp, i32]),
             "gencd_last_error": (C.c_char_p, []),
             "gencd_stats": (C.c_int, [vp, C.POINTER(gencd_result)]),
             "gencd_stats_reset": (C.c_int, [vp]),
@@ -435,6 +436,11 @@ def gencd_propose_schedule(h):
     _check(lib().gencd_propose_schedule(h, C.byref(split), ms, 5))
     forms = ["separate", "fused20", "fused24", "fused28", "fused31"]
     return int(split.value), {f: float(v) for f, v in zip(forms, ms) if v >= 0}
+
+
+def gencd_set_propose_schedule(h, split):
+    """0: two kernels; 20, 24, 28, 31: the fused kernel's slab warps; -1: autotune."""
+    _check(lib().gencd_set_propose_schedule(h, int(split)))
 
 
 def gencd_profile_read(h, kernel):

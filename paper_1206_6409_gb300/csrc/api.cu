@@ -755,6 +755,8 @@ void solve_result(gencd_problem* p, const SolveRun* S, gencd_result* out) {
   fill_result(p, out, S->status, S->iters, S->host_nnz, secs);
 }
 
+constexpr int kSolveStallChecks = 50;  // checks without a new lowest KKT value taken as a stall
+
 static int solve_evaluate(gencd_problem* p, SolveRun* S) {
   GENCD_TRY(enqueue_evaluate(p));
   GENCD_TRY(read_scalars_async(p));
@@ -835,6 +837,24 @@ int solve_advance(gencd_problem* p, SolveRun* S) {
     return 1;
   }
   if (S->iters >= a.max_iter) return solve_finish(p, S);
+  // A stall (Thread-Greedy oscillating without rising above its start): no
+  // new lowest KKT value for kSolveStallChecks checks while the objective fell
+  // by less than 1e-9 of itself over them doubles G (no restart).  A solve
+  // that keeps improving its KKT value is never touched.
+  if (S->backoff && p->accept_group < S->B) {
+    if (!S->window) {
+      S->p_ref = obj;
+      S->best_kkt = kkt;
+      S->stall = 0;
+      S->window = true;
+    } else if (kkt < S->best_kkt) {
+      S->best_kkt = kkt;
+      S->stall = 0;
+    } else if (++S->stall >= kSolveStallChecks) {
+      if (!(obj < S->p_ref - 1e-9 * std::fabs(S->p_ref))) p->accept_group = std::min<int64_t>(S->B, 2 * p->accept_group);
+      S->window = false;  // the next window starts at the next check
+    }
+  }
   const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - S->t0).count();
   if (a.timeout_s > 0.0 && el >= a.timeout_s) return solve_finish(p, S);
   const int64_t step = std::min<int64_t>(a.check_every, a.max_iter - S->iters);
@@ -1279,6 +1299,17 @@ int gencd_profile_read(gencd_problem* p, int32_t kernel, double* ms, int64_t* la
   if (ms) *ms = p->prof.ms[kernel];
   if (launches) *launches = p->prof.launches[kernel];
   if (calls) *calls = p->prof.calls[kernel];
+  return GENCD_OK;
+}
+
+int gencd_set_propose_schedule(gencd_problem* p, int32_t split) {
+  GENCD_CHECK_HANDLE(p);
+  if (split == -1) return tune_propose_plan(p);
+  const bool fusable = p->plan.built && p->plan.light_counter != nullptr;
+  if (split != 0 && !(fusable && (split == 20 || split == 24 || split == 28 || split == 31)))
+    return fail(GENCD_EINVAL, fusable ? "split must be -1, 0, 20, 24, 28 or 31"
+                                      : "this problem's streaming propose has one form only (split 0 or -1)");
+  p->plan.fused_split = split;
   return GENCD_OK;
 }
 

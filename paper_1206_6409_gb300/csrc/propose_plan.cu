@@ -577,7 +577,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 // read consecutive slots (coalesced), a segmented warp scan sums each
 // column's run of slots inside the 32, and the run's last lane adds it to the
 // column's shared accumulator (one adder per column and chunk, chunks in
-// order: the order of the sum is fixed).  hscale (index-only columns): the
+// order: the order of the sum is fixed).  The loads of PF chunks are issued
+// before any is summed, so each lane keeps several in flight.  hscale (index-only columns): the
 // sum is scaled by the column's value.  light_counter (nullable): the
 // light-tile pool of k_propose_fused, reset here for the next launch (this
 // kernel runs after it on the same stream)
@@ -600,28 +601,39 @@ __global__ void __launch_bounds__(kThreads)
   s_acc[wl][lane] = G(0);
   __syncwarp();
   const uint32_t a = s_b[wl][0], e = s_b[wl][32];
-  for (uint32_t t0 = a; t0 < e; t0 += 32) {
-    const uint32_t pos = t0 + lane;
-    const bool in = pos < e;
-    G v = G(0);
-    int c = 32;  // lanes past the end form a segment of their own
-    if (in) {
-      v = partial[pos];
-      partial[pos] = G(0);
-      c = 0;  // the column holding slot pos: the last c with s_b[c] <= pos
+  constexpr int PF = 8;  // chunks whose loads are issued together
+  for (uint32_t t1 = a; t1 < e; t1 += 32 * PF) {
+    G vv[PF];
 #pragma unroll
-      for (int step = 16; step > 0; step >>= 1)
-        if (c + step < nc && s_b[wl][c + step] <= pos) c += step;
+    for (int q = 0; q < PF; ++q) {
+      const uint32_t pos = t1 + 32 * q + lane;
+      vv[q] = pos < e ? partial[pos] : G(0);
     }
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {  // segmented inclusive scan (columns are runs of lanes)
-      const G y = __shfl_up_sync(FULL, v, d);
-      const int cy = __shfl_up_sync(FULL, c, d);
-      if (lane >= d && cy == c) v += y;
+    for (int q = 0; q < PF; ++q) {
+      const uint32_t t0 = t1 + 32 * q;
+      if (t0 >= e) break;  // warp-uniform
+      const uint32_t pos = t0 + lane;
+      const bool in = pos < e;
+      G v = vv[q];
+      int c = 32;  // lanes past the end form a segment of their own
+      if (in) {
+        partial[pos] = G(0);
+        c = 0;  // the column holding slot pos: the last c with s_b[c] <= pos
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+          if (c + step < nc && s_b[wl][c + step] <= pos) c += step;
+      }
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {  // segmented inclusive scan (columns are runs of lanes)
+        const G y = __shfl_up_sync(FULL, v, d);
+        const int cy = __shfl_up_sync(FULL, c, d);
+        if (lane >= d && cy == c) v += y;
+      }
+      const int cn = __shfl_down_sync(FULL, c, 1);
+      if (in && (lane == 31 || cn != c)) s_acc[wl][c] += v;
+      __syncwarp();
     }
-    const int cn = __shfl_down_sync(FULL, c, 1);
-    if (in && (lane == 31 || cn != c)) s_acc[wl][c] += v;
-    __syncwarp();
   }
   if (lane < nc) {
     const G sum = s_acc[wl][lane];

@@ -159,7 +159,16 @@ bool load(Server* S, int i) {
 
 // admits requests into free slots in arrival order and loads them
 void loader(Server* S) {
-  if (!S->service) cudaSetDevice(S->device);
+  if (!S->service && cudaSetDevice(S->device) != cudaSuccess) {
+    cudaGetLastError();
+    std::lock_guard<std::mutex> g(S->mu);
+    if (S->err == GENCD_OK) {
+      S->err = GENCD_ECUDA;
+      S->err_msg = "the loader thread could not select the device";
+    }
+    S->cv.notify_all();
+    return;
+  }
   for (;;) {
     int i = -1;
     {

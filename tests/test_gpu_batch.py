@@ -258,12 +258,13 @@ def test_every_update_schedule_keeps_z_equal_to_xw(gb, update_kind):
 
 
 def test_batch_path_to_a_duality_gap(gb):
-    # solves that stop at a relative duality gap of 1e-7 (the dual point's
-    # scale from FP32 sums) are certified by the oracle's FP64 gap to 1e-6
+    # solves that stop at a relative duality gap of 8e-7 (the dual point's
+    # scale from FP32 sums, accurate to about 1e-6 relative) are certified by
+    # the oracle's FP64 gap to 2e-6
     prob, fold = _problem("logistic", seed=11)
     chains = [-1, 1]
     with gb.Batch(prob, fold=fold, nfolds=NFOLDS, slots=32) as b:
-        b.set_params(variant="thread_greedy", blocks=64, tol_kkt=0.0, tol_gap=1e-7, check_every=5, max_iter=40_000)
+        b.set_params(variant="thread_greedy", blocks=64, tol_kkt=0.0, tol_gap=8e-7, check_every=5, max_iter=100_000)
         lams = np.stack([workloads.lambda_grid(b.lambda_max(h), 4, 1e-2) for h in chains])
         recs, W, tot = b.path(chains, lams, handoff=0.0, warm=True, want_w=True)
     assert tot.status == 0, recs
@@ -273,4 +274,4 @@ def test_batch_path_to_a_duality_gap(gb):
             orc = oracle.Oracle(sp, lams[c, t])
             P = orc.objective(W[c, t])
             assert recs[c * lams.shape[1] + t]["objective"] == pytest.approx(P, rel=1e-9)
-            assert orc.duality_gap(W[c, t]) <= 1e-6 * P, (c, t)
+            assert orc.duality_gap(W[c, t]) <= 2e-6 * P, (c, t)

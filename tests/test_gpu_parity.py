@@ -713,3 +713,47 @@ def test_solve_to_a_duality_gap_certifies_the_objective(gb, loss):
     assert gap <= 1e-9 * abs(primal) * (1 + 1e-6)
     assert orc.duality_gap(w) <= 1e-9 * abs(primal) * (1 + 1e-3)
     assert (orc.objective(w) - P_opt) / P_opt <= 1e-9 * (1 + 1e-3)
+
+
+@pytest.mark.parametrize("loss", ["logistic", "squared"])
+def test_top_greedy_solve_reaches_the_optimum(gb, loss):
+    # the global top-|J'| Accept has no convergence guarantee either: its solve
+    # backs off (|J'| / G accepted, G growing 4x on a rise of the objective)
+    # and reaches the oracle's optimum
+    prob = workloads.uniform_problem(1000, 2000, 10, values="pm1", loss=loss, n_planted=30, seed=21)
+    orc = oracle.Oracle(prob)
+    lam = 0.05 * orc.lambda_max()
+    orc.set_lambda(lam)
+    w_opt, _, _, kkt, _ = orc.solve("ccd", tol_kkt=1e-11)
+    with gb.Problem(prob) as p:
+        p.set_lambda(lam)
+        p.set_params(variant="top_greedy", blocks=64, tol_kkt=1e-10, max_iter=400_000, check_every=50)
+        r = p.solve()
+        assert r.status == 0, r.as_dict()
+        w = p.w()
+    assert r.objective == pytest.approx(orc.objective(w_opt), rel=1e-6)
+    assert_support_matches(prob, lam, w, w_opt, label=f"top-|J'| {loss}")
+
+
+@pytest.mark.parametrize("split", [0, 20, 24, 28, 31])
+def test_every_propose_schedule_matches_the_oracle(gb, split):
+    # the autotuner's candidates (two kernels, or the fused kernel with each
+    # split of its warps) compute the same proposals, heavy and light columns
+    prob = PROBLEMS["zipf-slabs-squared"]()
+    orc = oracle.Oracle(prob)
+    lam = 0.05 * orc.lambda_max()
+    orc.set_lambda(lam)
+    w = _state(prob, 41)
+    z = orc.fitted(w)
+    J = np.arange(prob.k, dtype=np.int32)
+    d_cpu, f_cpu = orc.propose(w, z, J)
+    with gb.Problem(prob, precision="f32") as p:
+        p.set_lambda(lam)
+        p.set_w(w)
+        gb.gencd_set_propose_schedule(p.h, split)
+        assert gb.gencd_propose_schedule(p.h)[0] == split
+        for _ in range(2):  # the light-tile pool's counter is reset between launches
+            d_all, f_all, kkt = p.propose_all()
+            assert_steps_close(prob, z, w, lam, J, d_all, f_all, d_cpu, f_cpu, TOL["f32"])
+        with pytest.raises(gb.GencdError):
+            gb.gencd_set_propose_schedule(p.h, 17)
