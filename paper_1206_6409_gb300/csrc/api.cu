@@ -231,14 +231,15 @@ static int effective_B(const gencd_problem* p) {
 }
 
 // KKT violation (dscal[0]) and objective (dscal[1]) of the current state
-// KKT violation (dscal[0]), objective (dscal[1]) and duality gap (dscal[9])
-// of the current state
-static int enqueue_evaluate(gencd_problem* p) {
+// KKT violation (dscal[0]), objective (dscal[1]) and, with gap, the duality
+// gap (dscal[9]) of the current state (the gap's conjugates cost FP64
+// transcendentals on every row: only where a gap is asked for)
+static int enqueue_evaluate(gencd_problem* p, bool gap = false) {
   GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal, 0, sizeof(double), p->stream));
   GENCD_CUDA_TRY(cudaMemsetAsync(p->dscal + 7, 0, sizeof(double), p->stream));
   GENCD_TRY(launch_propose_all(p, p->u, p->precision == GENCD_F64));
   GENCD_TRY(launch_finalize(p, p->lambda, false));
-  GENCD_TRY(launch_objective(p, true));
+  GENCD_TRY(launch_objective(p, gap));
   return GENCD_OK;
 }
 
@@ -758,7 +759,7 @@ void solve_result(gencd_problem* p, const SolveRun* S, gencd_result* out) {
 constexpr int kSolveStallChecks = 50;  // checks without a new lowest KKT value taken as a stall
 
 static int solve_evaluate(gencd_problem* p, SolveRun* S) {
-  GENCD_TRY(enqueue_evaluate(p));
+  GENCD_TRY(enqueue_evaluate(p, p->params.tol_gap > 0.0));
   GENCD_TRY(read_scalars_async(p));
   S->host_nnz += p->nnz;
   p->stat_host_nnz += p->nnz;
@@ -1125,7 +1126,7 @@ int gencd_set_w(gencd_problem* p, const double* w, int64_t k, int32_t memory) {
 
 int gencd_duality_gap(gencd_problem* p, double* gap, double* primal, double* dual) {
   GENCD_CHECK_HANDLE(p);
-  GENCD_TRY(enqueue_evaluate(p));
+  GENCD_TRY(enqueue_evaluate(p, true));
   GENCD_TRY(read_scalars(p));
   if (gap) *gap = p->hpin[9];
   if (primal) *primal = p->hpin[1];

@@ -44,8 +44,7 @@ constexpr int kBatchMaxFolds = 31;
 constexpr int kSpmmThreads = 256;
 constexpr int kAcceptThreads = 512;  // per partition: slots x column strides
 constexpr int kObjChecks = 8;        // convergence checks between objective evaluations of a path solve
-constexpr int kStallChecks = 400;    // checks without a new lowest KKT value taken as a stall
-constexpr double kJump = 1e6;        // KKT growth (over its best) taken as divergence
+constexpr int kStallChecks = 50;     // checks without a new lowest KKT value taken as a stall
 
 static int bfail(int code, const std::string& m) {
   set_error(m);
@@ -1735,7 +1734,7 @@ static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* 
   std::vector<int> next(C, 0), ready(C, 1), pred_slot(C, -1), slot_solve(S, -1), last_q(C, -1);
   std::vector<int> chain_group(C, 1), obj_wait(S, 0), stall(S, 0);
   std::vector<int64_t> slot_iters(S, 0);
-  std::vector<double> best_v(S, HUGE_VAL), p_ref(S, HUGE_VAL);
+  std::vector<double> best_v(S, HUGE_VAL), p_ref(S, HUGE_VAL), p_start(S, HUGE_VAL);
   const int g_sm = b->X->num_sms * 8;
   for (int64_t q = 0; q < (int64_t)C * L; ++q) {
     std::memset(&solves[q], 0, sizeof(gencd_path_solve));
@@ -1748,6 +1747,7 @@ static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* 
   const int64_t steps0 = b->steps;
   int done = 0, all_ok = 1;
   std::vector<double> kv;
+  std::vector<int32_t> started;
   while (rc == GENCD_OK && done < C * L) {
     // start ready solves in free slots, chains in turn
     for (int c = 0, free_s = 0; c < C && rc == GENCD_OK; ++c) {
@@ -1775,17 +1775,26 @@ static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* 
       solves[q].t_start = secs();
       next[c] += 1;
       ready[c] = 0;
+      started.push_back(s);
     }
     if (rc != GENCD_OK) break;
+    if (!started.empty()) {  // the objective each new solve starts from (the backoff's reference)
+      std::vector<double> p0;
+      rc = slot_objectives(b, started, &p0);
+      for (size_t r = 0; r < started.size() && rc == GENCD_OK; ++r) p_start[started[r]] = p0[r];
+      started.clear();
+      if (rc != GENCD_OK) break;
+    }
     rc = run_steps(b, m);
     if (rc == GENCD_OK) rc = read_kkt(b, &kv);
     if (rc != GENCD_OK) break;
-    // Accept backoff (Thread-Greedy has no convergence guarantee): a KKT
-    // value that jumps (kJump times its best, or not finite) restarts the
-    // solve from its start with 4x the accept group; kStallChecks checks
-    // without a new lowest KKT value over which the FP64 objective (evaluated
-    // every kObjChecks checks) fell by less than 1e-9 of itself double the
-    // group and the solve goes on.  G = B is Greedy.
+    // Accept backoff (Thread-Greedy has no convergence guarantee), the rules
+    // of gencd_solve: an objective (evaluated every kObjChecks checks) that is
+    // not finite or above the solve's start value, or a KKT value that is not
+    // finite, restarts the solve from its start with 4x the accept group;
+    // kStallChecks checks without a new lowest KKT value over which the
+    // objective fell by less than 1e-9 of itself double the group and the
+    // solve goes on.  G = B is Greedy.
     std::vector<int32_t> retire, restart, watch;
     bool regroup = false;
     for (int s = 0; s < S; ++s) {
@@ -1803,7 +1812,7 @@ static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* 
       if (v <= tol_q) {
         solves[q].status = GENCD_OK;
         retire.push_back(s);
-      } else if (!std::isfinite(v) || v > kJump * best_v[s]) {
+      } else if (!std::isfinite(v)) {
         if (b->h_group[s] < b->B && slot_iters[s] < max_iter) {
           b->h_group[s] = std::min(b->B, 4 * b->h_group[s]);
           restart.push_back(s);
@@ -1842,6 +1851,16 @@ static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* 
         if (gaps && pg[r] <= b->params.tol_gap * std::fabs(P)) {  // certified within tol_gap of its optimum
           solves[slot_solve[s]].status = GENCD_OK;
           retire.push_back(s);
+          continue;
+        }
+        if (!std::isfinite(P) || !(P <= p_start[s] * (1.0 + 1e-6) + 1e-300)) {  // above its start: restart
+          if (b->h_group[s] < b->B && slot_iters[s] < max_iter) {
+            b->h_group[s] = std::min(b->B, 4 * b->h_group[s]);
+            restart.push_back(s);
+          } else if (!std::isfinite(P)) {
+            solves[slot_solve[s]].status = GENCD_EDIVERGED;
+            retire.push_back(s);
+          }
           continue;
         }
         if (stall[s] >= kStallChecks) {  // no new lowest KKT value for kStallChecks checks

@@ -757,3 +757,28 @@ def test_every_propose_schedule_matches_the_oracle(gb, split):
             assert_steps_close(prob, z, w, lam, J, d_all, f_all, d_cpu, f_cpu, TOL["f32"])
         with pytest.raises(gb.GencdError):
             gb.gencd_set_propose_schedule(p.h, 17)
+
+
+@pytest.mark.parametrize("precision,tol_rel", [("f32", 1e-3), ("f64", 1e-6)])
+def test_config2_at_one_percent_solves_to_a_certified_point(gb, precision, tol_rel):
+    # config 2's law at 1/100 of its size (n = 10,000, k = 40,000, 2e6 nnz),
+    # the benchmark's Thread-Greedy (B = 1024): solved to KKT <= tol_rel lambda,
+    # the oracle's FP64 KKT value and duality gap at the GPU's w certify it
+    prob = workloads.config2_scaled(0.01, "logistic")
+    orc = oracle.Oracle(prob)
+    lam = 0.05 * orc.lambda_max()
+    orc.set_lambda(lam)
+    with gb.Problem(prob, precision=precision) as p:
+        p.set_lambda(lam)
+        p.set_params(variant="thread_greedy", blocks=1024, tol_kkt=tol_rel * lam, max_iter=200_000, check_every=10)
+        r = p.solve()
+        assert r.status == 0, r.as_dict()
+        w = p.w()
+    sp = prob if precision == "f64" else oracle.stored_problem(prob, "f32")
+    o_s = oracle.Oracle(sp, lam)
+    kkt = o_s.kkt(w)
+    # FP32 sums: the oracle's KKT value may exceed the device's by their rounding
+    assert kkt <= tol_rel * lam * (1.0 if precision == "f64" else 1.5) + (0 if precision == "f64" else 1e-9), kkt
+    P = o_s.objective(w)
+    assert o_s.duality_gap(w) <= (1e-5 if precision == "f64" else 1e-2) * P
+    assert r.objective == pytest.approx(P, rel=1e-9)
