@@ -148,12 +148,14 @@ int gencd_batch_propose(gencd_batch* b, double* delta, double* phi, int32_t memo
  * closing discussion): on correlated columns the B simultaneous updates can
  * oscillate or diverge.  A solve accepts, of every G consecutive partitions,
  * only the best proxy (G = 1 is Thread-Greedy, G = B is Greedy, which lowers
- * the objective at every step).  When a solve's KKT violation grows to 10^6
- * times its lowest value (or is not finite), it restarts from its start with
- * 4G; when 400 checks pass without a new lowest KKT value and its FP64
- * objective (evaluated every 8 checks) fell by less than 1e-9 of itself over
- * them, G doubles.  A chain's next solve starts at half the G its
- * predecessor reached.
+ * the objective at every step).  The rules are gencd_solve's: when a
+ * solve's FP64 objective (evaluated every 8 checks) is not finite or above
+ * its value at the solve's start, or its KKT violation is not finite, it
+ * restarts from its start with 4G; 50 checks in a row with neither a new
+ * lowest objective (by 1e-12 of itself) nor a KKT violation 1% below the
+ * lowest since the (re)start double G while the violation is at least
+ * 1e-3 lambda.  A chain's next solve starts at half the G its predecessor
+ * reached.
  */
 typedef struct {
   int32_t nchains;         /* chains (e.g. cross-validation folds)            */

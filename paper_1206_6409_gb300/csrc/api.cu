@@ -757,6 +757,9 @@ void solve_result(gencd_problem* p, const SolveRun* S, gencd_result* out) {
 }
 
 constexpr int kSolveStallChecks = 50;  // checks without a new lowest KKT value taken as a stall
+constexpr double kStallGain = 1e-2;    // a new lowest KKT value is 1% below the previous one
+constexpr double kObjGain = 1e-12;     // a new lowest objective is this far (relative) below the previous one
+constexpr double kStallKkt = 1e-3;     // stalls count while the KKT value is at least this times lambda
 
 static int solve_evaluate(gencd_problem* p, SolveRun* S) {
   GENCD_TRY(enqueue_evaluate(p, p->params.tol_gap > 0.0));
@@ -813,6 +816,8 @@ int solve_advance(gencd_problem* p, SolveRun* S) {
   const bool above = !(obj <= S->obj_start * (1.0 + 1e-6) + 1e-300);
   if (S->backoff && p->accept_group < S->B && S->iters < a.max_iter && (blown || above)) {
     p->accept_group = std::min<int64_t>(S->B, 4 * p->accept_group);  // restart from the start state
+    S->best_kkt = S->best_obj = HUGE_VAL;
+    S->stall = 0;
     GENCD_CUDA_TRY(cudaMemcpyAsync(p->w, p->w_start, sizeof(double) * p->k, cudaMemcpyDeviceToDevice, p->stream));
     GENCD_TRY(launch_mirror_w(p));
     GENCD_TRY(build_csr(p));
@@ -838,22 +843,29 @@ int solve_advance(gencd_problem* p, SolveRun* S) {
     return 1;
   }
   if (S->iters >= a.max_iter) return solve_finish(p, S);
-  // A stall (Thread-Greedy oscillating without rising above its start): no
-  // new lowest KKT value for kSolveStallChecks checks while the objective fell
-  // by less than 1e-9 of itself over them doubles G (no restart).  A solve
-  // that keeps improving its KKT value is never touched.
+  // A stall (Thread-Greedy cycling below its start): kSolveStallChecks checks
+  // in a row that set neither a new lowest objective (by kObjGain of itself)
+  // nor a KKT value kStallGain below the lowest so far double G (no
+  // restart), if the KKT value is still above kStallKkt * lambda.  The
+  // lowest values are kept from the solve's (re)start, so the phases of a
+  // cycle do not pass for progress, and a solve whose objective keeps falling
+  // is never touched.  Near the optimum both values stop improving at the
+  // rounding level of the FP32 sums, where fewer updates would not help.
   if (S->backoff && p->accept_group < S->B) {
-    if (!S->window) {
-      S->p_ref = obj;
+    bool progress = false;
+    if (obj < S->best_obj * (1.0 - kObjGain)) {  // P >= 0 for both losses
+      S->best_obj = obj;
+      progress = true;
+    }
+    if (kkt < S->best_kkt * (1.0 - kStallGain)) {
       S->best_kkt = kkt;
-      S->stall = 0;
-      S->window = true;
-    } else if (kkt < S->best_kkt) {
-      S->best_kkt = kkt;
+      progress = true;
+    }
+    if (progress) {
       S->stall = 0;
     } else if (++S->stall >= kSolveStallChecks) {
-      if (!(obj < S->p_ref - 1e-9 * std::fabs(S->p_ref))) p->accept_group = std::min<int64_t>(S->B, 2 * p->accept_group);
-      S->window = false;  // the next window starts at the next check
+      if (kkt >= kStallKkt * p->lambda) p->accept_group = std::min<int64_t>(S->B, 2 * p->accept_group);
+      S->stall = 0;
     }
   }
   const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - S->t0).count();

@@ -45,6 +45,9 @@ constexpr int kSpmmThreads = 256;
 constexpr int kAcceptThreads = 512;  // per partition: slots x column strides
 constexpr int kObjChecks = 8;        // convergence checks between objective evaluations of a path solve
 constexpr int kStallChecks = 50;     // checks without a new lowest KKT value taken as a stall
+constexpr double kStallGain = 1e-2;  // a new lowest KKT value is 1% below the previous one
+constexpr double kObjGain = 1e-12;   // a new lowest objective is this far (relative) below the previous one
+constexpr double kStallKkt = 1e-3;   // stalls count while the KKT value is at least this times lambda
 
 static int bfail(int code, const std::string& m) {
   set_error(m);
@@ -1734,7 +1737,7 @@ static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* 
   std::vector<int> next(C, 0), ready(C, 1), pred_slot(C, -1), slot_solve(S, -1), last_q(C, -1);
   std::vector<int> chain_group(C, 1), obj_wait(S, 0), stall(S, 0);
   std::vector<int64_t> slot_iters(S, 0);
-  std::vector<double> best_v(S, HUGE_VAL), p_ref(S, HUGE_VAL), p_start(S, HUGE_VAL);
+  std::vector<double> best_v(S, HUGE_VAL), best_p(S, HUGE_VAL), p_start(S, HUGE_VAL);
   const int g_sm = b->X->num_sms * 8;
   for (int64_t q = 0; q < (int64_t)C * L; ++q) {
     std::memset(&solves[q], 0, sizeof(gencd_path_solve));
@@ -1770,7 +1773,7 @@ static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* 
       obj_wait[s] = 0;
       stall[s] = 0;
       best_v[s] = HUGE_VAL;
-      p_ref[s] = HUGE_VAL;
+      best_p[s] = HUGE_VAL;
       solves[q].slot = s;
       solves[q].t_start = secs();
       next[c] += 1;
@@ -1792,9 +1795,10 @@ static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* 
     // of gencd_solve: an objective (evaluated every kObjChecks checks) that is
     // not finite or above the solve's start value, or a KKT value that is not
     // finite, restarts the solve from its start with 4x the accept group;
-    // kStallChecks checks without a new lowest KKT value over which the
-    // objective fell by less than 1e-9 of itself double the group and the
-    // solve goes on.  G = B is Greedy.
+    // kStallChecks checks in a row that set neither a KKT value kStallGain
+    // below the lowest since the (re)start nor (at an objective evaluation) a
+    // new lowest objective double the group, while the KKT value is above
+    // kStallKkt * lambda, and the solve goes on.  G = B is Greedy.
     std::vector<int32_t> retire, restart, watch;
     bool regroup = false;
     for (int s = 0; s < S; ++s) {
@@ -1824,7 +1828,7 @@ static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* 
         solves[q].status = GENCD_NOT_CONVERGED;
         retire.push_back(s);
       } else {
-        if (v < best_v[s]) {
+        if (v < best_v[s] * (1.0 - kStallGain)) {
           best_v[s] = v;
           stall[s] = 0;
         } else {
@@ -1863,23 +1867,23 @@ static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* 
           }
           continue;
         }
-        if (stall[s] >= kStallChecks) {  // no new lowest KKT value for kStallChecks checks
-          const bool flat = !(P < p_ref[s] * (1.0 - 1e-9));
-          if (flat && b->h_group[s] < b->B) {
+        if (P < best_p[s] * (1.0 - kObjGain)) {  // P >= 0 for both losses
+          best_p[s] = P;
+          stall[s] = 0;
+        } else if (stall[s] >= kStallChecks) {  // neither value improved for kStallChecks checks
+          if (b->h_group[s] < b->B && kv[s] >= kStallKkt * b->h_lam[s]) {
             b->h_group[s] = std::min(b->B, 2 * b->h_group[s]);
             regroup = true;
           }
           stall[s] = 0;
-          p_ref[s] = HUGE_VAL;  // the next window starts here
         }
-        if (std::isfinite(P) && p_ref[s] == HUGE_VAL) p_ref[s] = P;  // objective at the window's start
       }
     }
     for (size_t r = 0; r < restart.size() && rc == GENCD_OK; ++r) {
       const int s = restart[r];
       rc = slot_set(b, s, b->h_set[s], b->h_lam[s], w_start + (size_t)s * b->k, b->h_group[s]);
       best_v[s] = HUGE_VAL;
-      p_ref[s] = HUGE_VAL;
+      best_p[s] = HUGE_VAL;
       obj_wait[s] = 0;
       stall[s] = 0;
     }

@@ -16,6 +16,7 @@
 #include <stdint.h>
 
 #include <chrono>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -341,12 +342,10 @@ struct SolveRun {
   int status = GENCD_NOT_CONVERGED;
   int64_t B = 1;
   bool backoff = false, fused = false;
-  // stall watch of the accept backoff: checks since the lowest KKT value, and
-  // the objective at the start of the current window
-  double best_kkt = 0.0;
+  // stall watch of the accept backoff: the lowest KKT value and objective
+  // since the solve's (re)start, and the checks since either last improved
+  double best_kkt = HUGE_VAL, best_obj = HUGE_VAL;
   int stall = 0;
-  double p_ref = 0.0;
-  bool window = false;
 };
 int solve_begin(gencd_problem* p, SolveRun* S);
 int solve_advance(gencd_problem* p, SolveRun* S);  // 1: more work enqueued, 0: done, < 0: error

@@ -399,7 +399,7 @@ __device__ __forceinline__ uint64_t kkt_bits_f32(uint32_t vmax32) {
   return (uint64_t)__double_as_longlong((double)__uint_as_float(vmax32));
 }
 
-constexpr int kFinThreads = 1024;  // one round of 4096 columns covers a partition of config 2
+constexpr int kFinThreads = 256;  // small CTAs: every partition of config 2 (3,906 columns, 4 rounds) resident at once
 
 __global__ void __launch_bounds__(kFinThreads)
     k_finalize_accept_f32(float* __restrict__ gacc, const float* __restrict__ w32, const float* __restrict__ bj32,

@@ -430,7 +430,8 @@ __device__ __forceinline__ void light_tile(const LightStage<SV>& cur, int64_t t,
   if (active) {
     U uu[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) uu[i] = __ldg(u + r[i]);  // padding rows are 0, values 0
+    // gathers of u through L2 without allocating in L1 (no reuse to keep)
+    for (int i = 0; i < 8; ++i) uu[i] = __ldcg(u + r[i]);  // padding rows are 0, values 0
     // first run, last run and the whole columns between (see k_propose_slabs)
     const uint32_t inner = m & 0xfeu;
     const int bf = inner ? __ffs(inner) - 1 : 8;
@@ -510,7 +511,7 @@ __global__ void __launch_bounds__(kThreads, 3)
 // The light tiles as a shared pool: warps take kLightChunk tiles at a time
 // from a global counter (reset to 0 by k_pairs_to_gacc after every launch),
 // the next tile's loads in flight while one is summed.
-constexpr int kLightChunk = 2;
+constexpr int kLightChunk = 4;
 
 template <typename V, typename U, typename G, typename SV>
 __device__ __forceinline__ void light_pool(const int32_t* __restrict__ row, const SV* __restrict__ val,
