@@ -228,7 +228,15 @@ __device__ __forceinline__ void slab_pass(const uint16_t* __restrict__ s_row, co
     const int64_t row0 = (int64_t)r * slab_rows;
     const int rows = (int)min((int64_t)slab_rows, n - row0);
     slab_barrier<BAR_THREADS>();  // the previous slab is no longer read
-    for (int i = gtid; i < rows; i += gthreads) s_u[i] = u[row0 + i];
+    {  // 16-byte loads, four in flight per thread, when u + row0 is 16-byte aligned
+      const bool al = (reinterpret_cast<uintptr_t>(u + row0) & 15u) == 0;
+      const int nvec = al ? (int)(((int64_t)rows * (int64_t)sizeof(U)) / 16) : 0;
+      const uint4* src = reinterpret_cast<const uint4*>(u + row0);
+      uint4* dst = reinterpret_cast<uint4*>(s_u);
+#pragma unroll 4
+      for (int i = gtid; i < nvec; i += gthreads) dst[i] = __ldcg(src + i);
+      for (int i = (int)((int64_t)nvec * 16 / (int64_t)sizeof(U)) + gtid; i < rows; i += gthreads) s_u[i] = u[row0 + i];
+    }
     slab_barrier<BAR_THREADS>();
     TileStage<SV, ITEMS> stg[DEPTH > 0 ? DEPTH : 1];
     int t = t0 + warp;
