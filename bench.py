@@ -816,15 +816,17 @@ def run_gencd(args):
 
     # roofline of the dominant kernel: the streaming propose's pass over X
     # (k_propose_fused, or the two separate passes when the autotuner keeps
-    # them), with the X stream as its algorithmic bytes (row index + stored
-    # value per non-zero; u is L2-resident); the family (that pass and the
-    # reduction of the heavy columns' partials into g) also counts a column
-    # pointer and a gradient per column
+    # them), with what it must move as its algorithmic bytes: the X stream
+    # (row index + stored value per non-zero; u is L2-resident) and the
+    # gradient it writes (one g_j per column, FP32 or FP64); the family (every
+    # kernel of the propose over all columns) counts a column pointer and an
+    # FP64-sized gradient per column instead
     pa_ms, _, pa_n = prof["propose_all"]  # one timed invocation of the family per step
     sv = VALUE_BYTES[args.precision]
     bytes_per_launch = prob.nnz * (4 + sv) + 8 * (prob.k + 1) + 8 * prob.k + (4 * prob.k if sv == 0 else 0)
     family_achieved = bytes_per_launch / (pa_ms / pa_n / 1000.0) / 1e9 if pa_n else None
-    x_bytes = prob.nnz * (4 + sv) + (4 * prob.k if sv == 0 else 0)
+    g_bytes = 8 if args.precision == "f64" else 4
+    x_bytes = prob.nnz * (4 + sv) + (4 * prob.k if sv == 0 else 0) + g_bytes * prob.k
     if prof["propose_fused"][2]:
         dom_name, (dom_ms, _, dom_n) = "k_propose_fused", prof["propose_fused"]
     else:
@@ -925,7 +927,7 @@ def run_gencd(args):
                          "frac": achieved / peak if achieved else None, "traffic": traffic,
                          "algorithmic_bytes_per_launch": x_bytes,
                          "launch_ms": dom_ms / dom_n if dom_n else None, "source_sha256": src_hash,
-                         "family": {"kernels": "the pass over X and k_pairs_to_gacc", "achieved": family_achieved,
+                         "family": {"kernels": "every kernel of the propose over all columns", "achieved": family_achieved,
                                     "frac": family_achieved / peak if family_achieved else None,
                                     "algorithmic_bytes_per_launch": bytes_per_launch,
                                     "launch_ms": pa_ms / pa_n if pa_n else None}},

@@ -183,10 +183,10 @@ int gencd_get_params(gencd_problem* p, gencd_params* params);
  * accepted proxy while top-|J'| accepts the max(1, B/G) lowest proxies.
  * G = B is Greedy, whose steps always lower the objective.  A solve that
  * converges never restarts.  A solve that cycles below its start value
- * (50 checks in a row with neither a new lowest objective, by 1e-12 of
- * itself, nor a KKT violation 1% below the lowest since the start or the
- * last restart, while the violation is at least 1e-3 lambda) doubles G
- * without a restart.  G returns to 1 at gencd_set_params; gencd_iterate
+ * (checks covering 500 iterations in a row with neither a new lowest
+ * objective, by 1e-12 of itself, nor a KKT violation 1% below the lowest
+ * since the start or the last restart, while the violation is at least
+ * 1e-3 lambda) doubles G without a restart.  G returns to 1 at gencd_set_params; gencd_iterate
  * applies the current G.
  * `out` (nullable) receives the statistics of the call.
  */

@@ -151,10 +151,10 @@ int gencd_batch_propose(gencd_batch* b, double* delta, double* phi, int32_t memo
  * the objective at every step).  The rules are gencd_solve's: when a
  * solve's FP64 objective (evaluated every 8 checks) is not finite or above
  * its value at the solve's start, or its KKT violation is not finite, it
- * restarts from its start with 4G; 50 checks in a row with neither a new
- * lowest objective (by 1e-12 of itself) nor a KKT violation 1% below the
- * lowest since the (re)start double G while the violation is at least
- * 1e-3 lambda.  A chain's next solve starts at half the G its predecessor
+ * restarts from its start with 4G; checks covering 500 iterations in a row
+ * with neither a new lowest objective (by 1e-12 of itself) nor a KKT
+ * violation 1% below the lowest since the (re)start double G while the
+ * violation is at least 1e-3 lambda.  A chain's next solve starts at half the G its predecessor
  * reached.
  */
 typedef struct {

@@ -756,7 +756,7 @@ void solve_result(gencd_problem* p, const SolveRun* S, gencd_result* out) {
   fill_result(p, out, S->status, S->iters, S->host_nnz, secs);
 }
 
-constexpr int kSolveStallChecks = 50;  // checks without a new lowest KKT value taken as a stall
+constexpr int64_t kStallIters = 500;   // iterations without progress taken as a stall (50 checks of 10)
 constexpr double kStallGain = 1e-2;    // a new lowest KKT value is 1% below the previous one
 constexpr double kObjGain = 1e-12;     // a new lowest objective is this far (relative) below the previous one
 constexpr double kStallKkt = 1e-3;     // stalls count while the KKT value is at least this times lambda
@@ -843,10 +843,11 @@ int solve_advance(gencd_problem* p, SolveRun* S) {
     return 1;
   }
   if (S->iters >= a.max_iter) return solve_finish(p, S);
-  // A stall (Thread-Greedy cycling below its start): kSolveStallChecks checks
-  // in a row that set neither a new lowest objective (by kObjGain of itself)
-  // nor a KKT value kStallGain below the lowest so far double G (no
-  // restart), if the KKT value is still above kStallKkt * lambda.  The
+  // A stall (Thread-Greedy cycling below its start): checks covering
+  // kStallIters iterations in a row that set neither a new lowest objective
+  // (by kObjGain of itself) nor a KKT value kStallGain below the lowest so
+  // far double G (no restart), if the KKT value is still above kStallKkt *
+  // lambda.  The
   // lowest values are kept from the solve's (re)start, so the phases of a
   // cycle do not pass for progress, and a solve whose objective keeps falling
   // is never touched.  Near the optimum both values stop improving at the
@@ -863,7 +864,7 @@ int solve_advance(gencd_problem* p, SolveRun* S) {
     }
     if (progress) {
       S->stall = 0;
-    } else if (++S->stall >= kSolveStallChecks) {
+    } else if (++S->stall >= std::max<int64_t>(1, (kStallIters + a.check_every - 1) / a.check_every)) {
       if (kkt >= kStallKkt * p->lambda) p->accept_group = std::min<int64_t>(S->B, 2 * p->accept_group);
       S->stall = 0;
     }

@@ -44,7 +44,7 @@ constexpr int kBatchMaxFolds = 31;
 constexpr int kSpmmThreads = 256;
 constexpr int kAcceptThreads = 512;  // per partition: slots x column strides
 constexpr int kObjChecks = 8;        // convergence checks between objective evaluations of a path solve
-constexpr int kStallChecks = 50;     // checks without a new lowest KKT value taken as a stall
+constexpr int kStallIters = 500;     // iterations without progress taken as a stall (as gencd_solve)
 constexpr double kStallGain = 1e-2;  // a new lowest KKT value is 1% below the previous one
 constexpr double kObjGain = 1e-12;   // a new lowest objective is this far (relative) below the previous one
 constexpr double kStallKkt = 1e-3;   // stalls count while the KKT value is at least this times lambda
@@ -1724,6 +1724,7 @@ static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* 
   auto secs = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
   const int S = b->S;
   const int m = std::max(1, b->params.check_every);
+  const int stall_checks = std::max(1, (kStallIters + m - 1) / m);
   const int64_t max_iter = b->params.max_iter;
   const double tol = b->params.tol_kkt;
   // per chain: the last finished solve's w (warm starts from a retired solve);
@@ -1795,10 +1796,11 @@ static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* 
     // of gencd_solve: an objective (evaluated every kObjChecks checks) that is
     // not finite or above the solve's start value, or a KKT value that is not
     // finite, restarts the solve from its start with 4x the accept group;
-    // kStallChecks checks in a row that set neither a KKT value kStallGain
-    // below the lowest since the (re)start nor (at an objective evaluation) a
-    // new lowest objective double the group, while the KKT value is above
-    // kStallKkt * lambda, and the solve goes on.  G = B is Greedy.
+    // checks covering kStallIters iterations in a row that set neither a KKT
+    // value kStallGain below the lowest since the (re)start nor (at an
+    // objective evaluation) a new lowest objective double the group, while
+    // the KKT value is above kStallKkt * lambda, and the solve goes on.
+    // G = B is Greedy.
     std::vector<int32_t> retire, restart, watch;
     bool regroup = false;
     for (int s = 0; s < S; ++s) {
@@ -1870,7 +1872,7 @@ static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* 
         if (P < best_p[s] * (1.0 - kObjGain)) {  // P >= 0 for both losses
           best_p[s] = P;
           stall[s] = 0;
-        } else if (stall[s] >= kStallChecks) {  // neither value improved for kStallChecks checks
+        } else if (stall[s] >= stall_checks) {  // neither value improved for kStallIters iterations
           if (b->h_group[s] < b->B && kv[s] >= kStallKkt * b->h_lam[s]) {
             b->h_group[s] = std::min(b->B, 2 * b->h_group[s]);
             regroup = true;

@@ -75,7 +75,7 @@ enum KernelId {
   K_SETUP,            // one-time and selection kernels
   K_PROPOSE_LIGHT,    // streaming propose: lane-segmented pass over the light columns
   K_PROPOSE_SLABS,    // streaming propose: row-slab pass over the heavy columns
-  K_PAIRS,            // streaming propose: sum of each heavy column's partials
+  K_PAIRS,            // (not launched: the row-slab pass adds each partial into g_j itself)
   K_PROPOSE_FUSED,    // streaming propose: row-slab and light passes in one kernel
   K_NUM
 };
@@ -105,9 +105,9 @@ struct CscView {
 // slab_rows rows, small enough that a slab of u fits in shared memory.
 // Heavy columns (>= heavy_min non-zeros) are stored slab by slab: for each
 // slab, the entries of every heavy column with rows in it (a "pair"), row as
-// a 16-bit offset inside the slab.  Each pair yields one partial sum; a
-// column's partials are contiguous (slot order) and summed into gacc.  Light
-// columns keep a compact CSC copy for the lane-segmented pass.
+// a 16-bit offset inside the slab.  Each pair yields one partial sum, added
+// atomically into the column's g_j (zero before the pass).  Light columns keep
+// a compact CSC copy for the lane-segmented pass.
 struct ProposePlan {
   bool built = false;
   int32_t slab_rows = 0, nslabs = 0;
@@ -120,7 +120,6 @@ struct ProposePlan {
   void* light_val = nullptr;
   int32_t* light_tile_lc = nullptr;  // light column of each 256-entry tile's first entry
   float* light_scale = nullptr;      // index-only storage: the value of light column lc
-  float* heavy_scale = nullptr;      // index-only storage: the value of heavy column h
   uint8_t* lmask = nullptr;          // per 8 light entries: bit i = entry 8g + i starts a column
   // heavy columns
   int64_t nheavy = 0, entries = 0, npairs = 0, ntiles = 0;
@@ -128,9 +127,7 @@ struct ProposePlan {
   uint16_t* s_row = nullptr;       // slab-local row of each entry
   void* s_val = nullptr;           // value of each entry (padding: 0)
   uint8_t* pmask = nullptr;        // per 8 entries: bit i = entry 8g + i starts a pair (pairs in entry order)
-  uint32_t* pair_slot = nullptr;   // partial slot of each pair: column-major, each column's in slab order
-  uint32_t* hslot_ptr = nullptr;   // heavy column h owns slots hslot_ptr[h] .. hslot_ptr[h+1]
-  void* partial = nullptr;         // one partial sum per slot (storage precision), zero between launches
+  uint32_t* pair_col = nullptr;    // the column j of each pair (its run sums go to g_j)
   uint32_t* tile_start = nullptr;  // tiles of 32*ITEMS entries inside one slab
   uint32_t* tile_end = nullptr;
   uint32_t* tile_pair = nullptr;   // pair holding the tile's first entry
@@ -141,8 +138,9 @@ struct ProposePlan {
   // both passes in one kernel (k_propose_fused) when fused_split > 0 (the
   // number of warps that start on the row slabs; 0: two kernels), chosen by
   // the plan's autotuner (tuned_ms: mean ms of the separate kernels, then of
-  // each split); light tiles are taken from a pool whose counter the partial
-  // reduction resets after each launch
+  // each split); light tiles are taken from a pool: light_counter[0] counts
+  // the tiles taken, light_counter[1] the warps finished, and the last warp
+  // of a launch resets both
   int fused_split = 0;
   double tuned_ms[8] = {-1.0};
   unsigned int* light_counter = nullptr;

@@ -8,18 +8,19 @@
 // once and gathers from there.  Only columns with at least heavy_min
 // non-zeros use this layout (their entries are regrouped slab by slab, with
 // 16-bit in-slab rows); every (slab, column) "pair" produces one partial sum,
-// and the partials of a column are added in slab order afterwards.  Columns
-// with fewer non-zeros would produce about one partial per non-zero, so they
-// keep a compact CSC copy and the lane-segmented pass with gathers from L2.
+// added atomically into the column's g_j.  Columns with fewer non-zeros would
+// produce about one partial per non-zero, so they keep a compact CSC copy and
+// the lane-segmented pass with gathers from L2.
 //
 // Within a slab the kernel works like the CSC pass: a warp owns a tile of
 // 256 consecutive entries, a lane 8 of them (128-bit loads of rows and
-// values), a lane sums its entries pair by pair in registers and emits each
-// partial with a store (pair inside the lane) or an atomic add; a full tile
-// inside one pair is reduced by the warp first.  (A warp scan over lane-cut
-// pairs removes most atomics but costs more instructions than it saves in
-// this issue-bound kernel.)  Partial sums are kept in the storage precision
-// (FP32 atomics in FP32 mode).
+// values), a lane sums its entries pair by pair in registers and adds each
+// run's sum into g_j (an atomic add that returns nothing: other slabs and
+// tiles add to the same column); a run cut by lane boundaries is combined by
+// a segmented warp suffix sum first, and a full tile inside one pair is
+// reduced by the warp.  Sums are kept in the storage precision (FP32 atomics
+// in FP32 mode), so the order of a heavy column's additions, and with it the
+// last bits of g_j, can differ between launches.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -63,11 +64,11 @@ __device__ __forceinline__ void load8(const V* __restrict__ p, V (&v)[8]) {
 }
 
 template <typename G>
-__device__ __forceinline__ void emit_pair(G* __restrict__ partial, uint32_t slot, G s, bool whole) {
+__device__ __forceinline__ void emit_pair(G* __restrict__ out, uint32_t slot, G s, bool whole) {
   if (whole)
-    partial[slot] = s;
+    out[slot] = s;
   else
-    atomicAdd(partial + slot, s);
+    atomicAdd(out + slot, s);
 }
 
 // Values of a lane's entries as stored by the plan (SV): float or double,
@@ -75,6 +76,14 @@ __device__ __forceinline__ void emit_pair(G* __restrict__ partial, uint32_t slot
 // (NoVal: index-only columns, every value 1; the column scale is applied to
 // the column's sum outside the streaming loop).
 struct NoVal {};
+
+// a heavy column's run sum into g_j: other slabs and tiles add to the same
+// column, so always atomically; index-only storage scales by the column's value
+template <typename G, typename SV>
+__device__ __forceinline__ void add_col(G* __restrict__ gacc, const float* __restrict__ cscale, uint32_t j, G v) {
+  if (std::is_same<SV, NoVal>::value) v *= (G)__ldg(cscale + j);
+  atomicAdd(gacc + j, v);
+}
 
 template <typename SV, int N>
 struct ValRegs;
@@ -206,14 +215,15 @@ __device__ __forceinline__ void slab_barrier() {
 // one being processed).
 template <typename V, typename U, typename G, int DEPTH, int ITEMS, typename SV, int BAR_THREADS>
 __device__ __forceinline__ void slab_pass(const uint16_t* __restrict__ s_row, const SV* __restrict__ s_val,
-                                          const uint8_t* __restrict__ pmask, const uint32_t* __restrict__ pair_slot,
+                                          const uint8_t* __restrict__ pmask, const uint32_t* __restrict__ pair_col,
                                           const uint32_t* __restrict__ tile_start,
                                           const uint32_t* __restrict__ tile_end,
                                           const uint32_t* __restrict__ tile_pair,
                                           const int32_t* __restrict__ tile_slab,
                                           const int32_t* __restrict__ slab_tile_begin, int t0, const int t_end,
                                           const U* __restrict__ u, int64_t n, int32_t slab_rows,
-                                          G* __restrict__ partial, U* s_u, const int warp, const int nw,
+                                          G* __restrict__ gacc, const float* __restrict__ cscale, U* s_u,
+                                          const int warp, const int nw,
                                           const int gtid, const int gthreads) {
   constexpr int TILE = 32 * ITEMS;
   constexpr uint32_t NOT_FIRST = ((1u << ITEMS) - 1u) & ~1u;  // start bits after a lane's first entry
@@ -270,11 +280,11 @@ __device__ __forceinline__ void slab_pass(const uint16_t* __restrict__ s_row, co
         if (lane >= d) incl += y;
       }
       uint32_t q = q0 + (incl - cnt) + (lane > 0 ? (m & 1u) : 0u);
-      // column-major slots of the pairs this lane may emit, loaded early: the
-      // tile's first pair (lane 0) and the pair of the lane's last run
+      // columns of the pairs this lane may emit, loaded early: the tile's
+      // first pair (lane 0) and the pair of the lane's last run
       const bool lead = lane == 0 && active && !(m & 1u);
-      const uint32_t slot0 = lead ? __ldg(pair_slot + q0) : 0u;
-      const uint32_t slot_last = (active && m != 0u) ? __ldg(pair_slot + q + __popc(m & NOT_FIRST)) : 0u;
+      const uint32_t col0 = lead ? __ldg(pair_col + q0) : 0u;
+      const uint32_t col_last = (active && m != 0u) ? __ldg(pair_col + q + __popc(m & NOT_FIRST)) : 0u;
       V cont = V(0), tail = V(0);
       bool has_tail = false;
       if (active) {
@@ -302,7 +312,7 @@ __device__ __forceinline__ void slab_pass(const uint16_t* __restrict__ s_row, co
             if (i == bf)
               first = acc;
             else
-              partial[__ldg(pair_slot + qi)] = (G)acc;  // started and ended inside the lane
+              add_col<G, SV>(gacc, cscale, __ldg(pair_col + qi), (G)acc);  // started and ended inside the lane
             acc = V(0);
             ++qi;
           }
@@ -310,7 +320,7 @@ __device__ __forceinline__ void slab_pass(const uint16_t* __restrict__ s_row, co
         }
         if (inner) {
           if (m & 1u)
-            partial[__ldg(pair_slot + q)] = (G)first;  // started at entry 0, ended inside
+            add_col<G, SV>(gacc, cscale, __ldg(pair_col + q), (G)first);  // started at entry 0, ended inside
           else
             cont = first;  // continues from the left
           tail = acc;  // the last run started inside the lane
@@ -326,17 +336,13 @@ __device__ __forceinline__ void slab_pass(const uint16_t* __restrict__ s_row, co
       if (__ballot_sync(FULL, stop) == 0u) {
         // the whole tile lies inside pair q0
         const V sum = warp_sum(cont);
-        if (lane == 0) atomicAdd(partial + slot0, (G)sum);
+        if (lane == 0) add_col<G, SV>(gacc, cscale, col0, (G)sum);
       } else {
         bool ended;
         const V tsum = lane_suffix_sum(cont, stop, lane, ended);
         const V t1s = __shfl_down_sync(FULL, tsum, 1);
-        const bool e1 = __shfl_down_sync(FULL, (int)ended, 1) != 0;
-        if (lead) atomicAdd(partial + slot0, (G)tsum);  // pair from the previous tile
-        if (has_tail) {
-          const V sum = tail + (lane < 31 ? t1s : V(0));
-          emit_pair<G>(partial, slot_last, (G)sum, lane < 31 && e1);
-        }
+        if (lead) add_col<G, SV>(gacc, cscale, col0, (G)tsum);  // pair from the previous tile
+        if (has_tail) add_col<G, SV>(gacc, cscale, col_last, (G)(tail + (lane < 31 ? t1s : V(0))));
       }
     }
     t0 = t1;
@@ -347,17 +353,17 @@ __device__ __forceinline__ void slab_pass(const uint16_t* __restrict__ s_row, co
 template <typename V, typename U, typename G, int THREADS, int DEPTH, int ITEMS, typename SV>
 __global__ void __launch_bounds__(THREADS, 1)
     k_propose_slabs(const uint16_t* __restrict__ s_row, const SV* __restrict__ s_val,
-                    const uint8_t* __restrict__ pmask, const uint32_t* __restrict__ pair_slot,
+                    const uint8_t* __restrict__ pmask, const uint32_t* __restrict__ pair_col,
                     const uint32_t* __restrict__ tile_start,
                     const uint32_t* __restrict__ tile_end, const uint32_t* __restrict__ tile_pair,
                     const int32_t* __restrict__ tile_slab, const int32_t* __restrict__ slab_tile_begin,
                     const int32_t* __restrict__ cta_tile_begin, const U* __restrict__ u, int64_t n,
-                    int32_t slab_rows, G* __restrict__ partial) {
+                    int32_t slab_rows, G* __restrict__ gacc, const float* __restrict__ cscale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   U* s_u = reinterpret_cast<U*>(smem_raw);
-  slab_pass<V, U, G, DEPTH, ITEMS, SV, 0>(s_row, s_val, pmask, pair_slot, tile_start, tile_end, tile_pair, tile_slab,
+  slab_pass<V, U, G, DEPTH, ITEMS, SV, 0>(s_row, s_val, pmask, pair_col, tile_start, tile_end, tile_pair, tile_slab,
                                           slab_tile_begin, cta_tile_begin[blockIdx.x],
-                                          cta_tile_begin[blockIdx.x + 1], u, n, slab_rows, partial, s_u,
+                                          cta_tile_begin[blockIdx.x + 1], u, n, slab_rows, gacc, cscale, s_u,
                                           threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x, blockDim.x);
 }
 
@@ -560,7 +566,7 @@ __device__ __forceinline__ void light_pool(const int32_t* __restrict__ row, cons
 template <typename V, typename U, typename G, int THREADS, int SLAB_WARPS, int DEPTH, int ITEMS, typename SV>
 __global__ void __launch_bounds__(THREADS, 1)
     k_propose_fused(const uint16_t* __restrict__ s_row, const SV* __restrict__ s_val,
-                    const uint8_t* __restrict__ pmask, const uint32_t* __restrict__ pair_slot,
+                    const uint8_t* __restrict__ pmask, const uint32_t* __restrict__ pair_col,
                     const uint32_t* __restrict__ tile_start, const uint32_t* __restrict__ tile_end,
                     const uint32_t* __restrict__ tile_pair, const int32_t* __restrict__ tile_slab,
                     const int32_t* __restrict__ slab_tile_begin, const int32_t* __restrict__ cta_tile_begin,
@@ -568,90 +574,30 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const uint8_t* __restrict__ lmask, const int32_t* __restrict__ tile_lc,
                     const int32_t* __restrict__ light_cols, const float* __restrict__ lscale, int64_t lnnz,
                     int64_t lntiles, unsigned int* counter, const U* __restrict__ u, int64_t n, int32_t slab_rows,
-                    G* __restrict__ partial, G* __restrict__ out) {
+                    G* __restrict__ gacc, const float* __restrict__ cscale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   U* s_u = reinterpret_cast<U*>(smem_raw);
   const int warp = threadIdx.x >> 5;
   if (warp < SLAB_WARPS)
     slab_pass<V, U, G, DEPTH, ITEMS, SV, 32 * SLAB_WARPS>(
-        s_row, s_val, pmask, pair_slot, tile_start, tile_end, tile_pair, tile_slab, slab_tile_begin,
-        cta_tile_begin[blockIdx.x], cta_tile_begin[blockIdx.x + 1], u, n, slab_rows, partial, s_u, warp, SLAB_WARPS,
+        s_row, s_val, pmask, pair_col, tile_start, tile_end, tile_pair, tile_slab, slab_tile_begin,
+        cta_tile_begin[blockIdx.x], cta_tile_begin[blockIdx.x + 1], u, n, slab_rows, gacc, cscale, s_u, warp, SLAB_WARPS,
         threadIdx.x, 32 * SLAB_WARPS);
-  light_pool<V, U, G, SV>(lrow, lval, lmask, tile_lc, light_cols, lscale, u, lnnz, lntiles, out, counter);
-}
-
-// sum of each heavy column = its partials (the slots of column h are
-// hslot_ptr[h] .. hslot_ptr[h+1], at most one per slab); partials reset.  A
-// warp takes 32 consecutive heavy columns, whose slots are contiguous: lanes
-// read consecutive slots (coalesced), a segmented warp scan sums each
-// column's run of slots inside the 32, and the run's last lane adds it to the
-// column's shared accumulator (one adder per column and chunk, chunks in
-// order: the order of the sum is fixed).  The loads of PF chunks are issued
-// before any is summed, so each lane keeps several in flight.  hscale (index-only columns): the
-// sum is scaled by the column's value.  light_counter (nullable): the
-// light-tile pool of k_propose_fused, reset here for the next launch (this
-// kernel runs after it on the same stream)
-template <typename G>
-__global__ void __launch_bounds__(kThreads)
-    k_pairs_to_gacc(const uint32_t* __restrict__ hslot_ptr, const int32_t* __restrict__ heavy_cols,
-                    int64_t nheavy, G* __restrict__ partial, G* __restrict__ gacc, const float* __restrict__ hscale,
-                    unsigned int* __restrict__ light_counter) {
-  constexpr int NW = kThreads / 32;
-  __shared__ G s_acc[NW][32];
-  __shared__ uint32_t s_b[NW][33];
-  const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  if (light_counter && blockIdx.x == 0 && threadIdx.x == 0) *light_counter = 0u;
-  const int64_t h0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
-  if (h0 >= nheavy) return;  // warp-uniform
-  const int nc = (int)(nheavy - h0 < 32 ? nheavy - h0 : 32);
-  s_b[wl][lane] = hslot_ptr[h0 + (lane < nc ? lane : nc)];
-  if (lane == 0) s_b[wl][32] = hslot_ptr[h0 + nc];
-  s_acc[wl][lane] = G(0);
-  __syncwarp();
-  const uint32_t a = s_b[wl][0], e = s_b[wl][32];
-  constexpr int PF = 8;  // chunks whose loads are issued together
-  for (uint32_t t1 = a; t1 < e; t1 += 32 * PF) {
-    G vv[PF];
-#pragma unroll
-    for (int q = 0; q < PF; ++q) {
-      const uint32_t pos = t1 + 32 * q + lane;
-      vv[q] = pos < e ? partial[pos] : G(0);
+  light_pool<V, U, G, SV>(lrow, lval, lmask, tile_lc, light_cols, lscale, u, lnnz, lntiles, gacc, counter);
+  // the last warp out resets the pool for the next launch: every warp has
+  // taken its last tiles when it gets here (counter[1] counts the exits)
+  if ((threadIdx.x & 31) == 0) {
+    const unsigned int warps = gridDim.x * (THREADS / 32);
+    __threadfence();  // this warp's takes from the pool are performed before its exit counts
+    if (atomicAdd(counter + 1, 1u) == warps - 1) {
+      counter[0] = 0u;
+      counter[1] = 0u;
     }
-#pragma unroll
-    for (int q = 0; q < PF; ++q) {
-      const uint32_t t0 = t1 + 32 * q;
-      if (t0 >= e) break;  // warp-uniform
-      const uint32_t pos = t0 + lane;
-      const bool in = pos < e;
-      G v = vv[q];
-      int c = 32;  // lanes past the end form a segment of their own
-      if (in) {
-        partial[pos] = G(0);
-        c = 0;  // the column holding slot pos: the last c with s_b[c] <= pos
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1)
-          if (c + step < nc && s_b[wl][c + step] <= pos) c += step;
-      }
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {  // segmented inclusive scan (columns are runs of lanes)
-        const G y = __shfl_up_sync(FULL, v, d);
-        const int cy = __shfl_up_sync(FULL, c, d);
-        if (lane >= d && cy == c) v += y;
-      }
-      const int cn = __shfl_down_sync(FULL, c, 1);
-      if (in && (lane == 31 || cn != c)) s_acc[wl][c] += v;
-      __syncwarp();
-    }
-  }
-  if (lane < nc) {
-    const G sum = s_acc[wl][lane];
-    gacc[heavy_cols[h0 + lane]] = hscale ? sum * (G)hscale[h0 + lane] : sum;
   }
 }
 
-// the two streaming passes and the partial reduction for one value storage SV
-// (V compute type, U type of u, G accumulator)
+// the two streaming passes for one value storage SV (V compute type, U type
+// of u, G accumulator)
 constexpr int kFusedThreads = 1024;
 // candidate splits of the fused kernel's 32 warps: warps that start on the
 // row slabs (the rest start on the light pool); the plan's autotuner times
@@ -663,19 +609,18 @@ template <typename V, typename U, typename G, typename SV, int DEPTH, int ITEMS,
 static void launch_fused(gencd_problem* p, const void* u_vec, size_t smem) {
   ProposePlan& P = p->plan;
   k_propose_fused<V, U, G, kFusedThreads, SW, DEPTH, ITEMS, SV><<<P.grid, kFusedThreads, smem, p->stream>>>(
-      P.s_row, (const SV*)P.s_val, P.pmask, P.pair_slot, P.tile_start, P.tile_end, P.tile_pair, P.tile_slab,
+      P.s_row, (const SV*)P.s_val, P.pmask, P.pair_col, P.tile_start, P.tile_end, P.tile_pair, P.tile_slab,
       P.slab_tile_begin, P.cta_tile_begin, P.light_row, (const SV*)P.light_val, P.lmask, P.light_tile_lc,
       P.light_cols, P.light_scale, P.light_nnz, P.light_ntiles, P.light_counter, (const U*)u_vec, p->n,
-      P.slab_rows, (G*)P.partial, (G*)p->gnat);
+      P.slab_rows, (G*)p->gnat, p->col_val);
 }
 
 template <typename V, typename U, typename G, typename SV, int THREADS, int DEPTH, int ITEMS>
 static int launch_plan_passes(gencd_problem* p, const void* u_vec) {
   ProposePlan& P = p->plan;
-  if (P.fused_split > 0) {  // both passes in one kernel, then the heavy columns' partials
+  if (P.fused_split > 0) {  // both passes in one kernel
     const size_t smem = (size_t)(P.slab_rows + kSlabZeroSlot) * sizeof(U);
-    const int g2 = (int)((P.nheavy + kThreads - 1) / kThreads);  // a warp per 32 heavy columns: a thread per column
-    cudaEvent_t e1 = nullptr, e2 = nullptr;
+    cudaEvent_t e1 = nullptr;
     prof_begin(p, K_PROPOSE_FUSED, &e1);
     switch (P.fused_split) {
       case 20: launch_fused<V, U, G, SV, DEPTH, ITEMS, 20>(p, u_vec, smem); break;
@@ -684,10 +629,6 @@ static int launch_plan_passes(gencd_problem* p, const void* u_vec) {
       default: launch_fused<V, U, G, SV, DEPTH, ITEMS, 31>(p, u_vec, smem); break;
     }
     prof_end(p, e1);
-    prof_begin(p, K_PAIRS, &e2);
-    k_pairs_to_gacc<G><<<g2, kThreads, 0, p->stream>>>(P.hslot_ptr, P.heavy_cols, P.nheavy, (G*)P.partial,
-                                                        (G*)p->gnat, P.heavy_scale, P.light_counter);
-    prof_end(p, e2);
     GENCD_CUDA_TRY(cudaGetLastError());
     return GENCD_OK;
   }
@@ -703,17 +644,12 @@ static int launch_plan_passes(gencd_problem* p, const void* u_vec) {
   }
   if (P.nheavy > 0) {
     const size_t smem = (size_t)(P.slab_rows + kSlabZeroSlot) * sizeof(U);
-    const int g2 = (int)((P.nheavy + kThreads - 1) / kThreads);  // one thread per heavy column
-    cudaEvent_t e1 = nullptr, e2 = nullptr;
+    cudaEvent_t e1 = nullptr;
     prof_begin(p, K_PROPOSE_SLABS, &e1);
     k_propose_slabs<V, U, G, THREADS, DEPTH, ITEMS, SV><<<P.grid, THREADS, smem, p->stream>>>(
-        P.s_row, (const SV*)P.s_val, P.pmask, P.pair_slot, P.tile_start, P.tile_end, P.tile_pair, P.tile_slab,
-        P.slab_tile_begin, P.cta_tile_begin, (const U*)u_vec, p->n, P.slab_rows, (G*)P.partial);
+        P.s_row, (const SV*)P.s_val, P.pmask, P.pair_col, P.tile_start, P.tile_end, P.tile_pair, P.tile_slab,
+        P.slab_tile_begin, P.cta_tile_begin, (const U*)u_vec, p->n, P.slab_rows, (G*)p->gnat, p->col_val);
     prof_end(p, e1);
-    prof_begin(p, K_PAIRS, &e2);
-    k_pairs_to_gacc<G><<<g2, kThreads, 0, p->stream>>>(P.hslot_ptr, P.heavy_cols, P.nheavy, (G*)P.partial,
-                                                        (G*)p->gnat, P.heavy_scale, nullptr);
-    prof_end(p, e2);
     GENCD_CUDA_TRY(cudaGetLastError());
   }
   return GENCD_OK;
@@ -891,25 +827,11 @@ __global__ void k_plan_fill_pairs(const uint32_t* __restrict__ sk, const uint32_
   }
 }
 
-__global__ void k_plan_slots(const uint32_t* __restrict__ q_sorted, int64_t npairs, uint32_t* __restrict__ slot) {
+__global__ void k_plan_pair_cols(const uint32_t* __restrict__ pair_h, int64_t npairs,
+                                 const int32_t* __restrict__ heavy_cols, uint32_t* __restrict__ pair_col) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < npairs; s += stride) slot[q_sorted[s]] = (uint32_t)s;
-}
-
-__global__ void k_plan_lower_bounds(const uint32_t* __restrict__ sorted, int64_t m, int64_t count,
-                                    uint32_t* __restrict__ out) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= count; i += stride) {
-    int64_t lo = 0, hi = m;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi) >> 1;
-      if ((int64_t)sorted[mid] < i)
-        lo = mid + 1;
-      else
-        hi = mid;
-    }
-    out[i] = (uint32_t)lo;
-  }
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < npairs; q += stride)
+    pair_col[q] = (uint32_t)heavy_cols[pair_h[q]];
 }
 
 __global__ void k_plan_tiles(const int32_t* __restrict__ slab_tile_begin, const int64_t* __restrict__ pad_off,
@@ -948,8 +870,8 @@ __global__ void k_plan_tiles(const int32_t* __restrict__ slab_tile_begin, const 
 void free_propose_plan(gencd_problem* p) {
   ProposePlan& P = p->plan;
   void* bufs[] = {P.light_cols, P.light_col_ptr, P.light_row, P.light_val, P.light_tile_lc, P.lmask, P.light_scale,
-                  P.heavy_scale, P.heavy_cols,
-                  P.s_row, P.s_val, P.pmask, P.pair_slot, P.hslot_ptr, P.partial, P.tile_start,
+                  P.heavy_cols,
+                  P.s_row, P.s_val, P.pmask, P.pair_col, P.tile_start,
                   P.tile_end, P.tile_pair, P.tile_slab, P.slab_tile_begin, P.cta_tile_begin, P.light_counter};
   for (void* b : bufs)
     if (b) dev_free(p, b);
@@ -1150,10 +1072,7 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
     } else {
       GENCD_CUDA_TRY(cudaStreamSynchronize(st));
       dev_free(p, P.s_val);
-      P.s_val = nullptr;
-      GENCD_TRY(palloc(p, &P.heavy_scale, P.nheavy));
-      k_plan_gather_scales<<<grid_for(P.nheavy, kThreads, g), kThreads, 0, st>>>(P.heavy_cols, P.nheavy, p->col_val,
-                                                                                  P.heavy_scale);
+      P.s_val = nullptr;  // the row-slab pass scales each run sum by col_val[j]
     }
     GENCD_CUDA_TRY(cudaGetLastError());
   }
@@ -1165,30 +1084,17 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   GENCD_CUDA_TRY(cudaStreamSynchronize(st));
   P.npairs = np32;
 
-  // pairs: first entry and heavy column; the pairs of each column in slab order
-  uint32_t *pair_start, *pair_h, *qa, *qb, *ha, *qtmp;
+  // pairs: first entry and column
+  uint32_t *pair_start, *pair_h;
   GENCD_TRY(S.get(&pair_start, P.npairs + 1));
   GENCD_TRY(S.get(&pair_h, P.npairs));
   k_plan_fill_pairs<<<grid_for(E, kThreads, g), kThreads, 0, st>>>(sk, se, E, slab_begin, pad_off, hh, pidx,
                                                                     pair_start, pair_h);
   const uint32_t ent32 = (uint32_t)P.entries;
   GENCD_CUDA_TRY(cudaMemcpyAsync(pair_start + P.npairs, &ent32, 4, cudaMemcpyHostToDevice, st));
-  GENCD_TRY(S.get(&qa, P.npairs));
-  GENCD_TRY(S.get(&qb, P.npairs));
-  GENCD_TRY(S.get(&ha, P.npairs));
-  GENCD_TRY(S.get(&qtmp, (int64_t)radix_tmp_words(P.npairs)));
-  GENCD_TRY(iota_u32(p, qa, P.npairs));
-  bool q_alt = false;  // stable: a column's pairs stay in slab order
-  GENCD_TRY(radix_sort_with_tmp(p, pair_h, qa, P.npairs, bits_for_max(P.nheavy - 1), ha, qb, qtmp, &q_alt));
-  const uint32_t* h_sorted = q_alt ? ha : pair_h;
-  const uint32_t* q_sorted = q_alt ? qb : qa;
-  GENCD_TRY(palloc(p, &P.pair_slot, P.npairs));
-  GENCD_TRY(palloc(p, &P.hslot_ptr, P.nheavy + 1));
-  GENCD_TRY(palloc(p, (char**)&P.partial, P.npairs * (int64_t)vsz));
-  GENCD_CUDA_TRY(cudaMemsetAsync(P.partial, 0, vsz * (size_t)P.npairs, st));
-  k_plan_slots<<<grid_for(P.npairs, kThreads, g), kThreads, 0, st>>>(q_sorted, P.npairs, P.pair_slot);
-  k_plan_lower_bounds<<<grid_for(P.nheavy + 1, kThreads, g), kThreads, 0, st>>>(h_sorted, P.npairs, P.nheavy,
-                                                                                 P.hslot_ptr);
+  GENCD_TRY(palloc(p, &P.pair_col, P.npairs));
+  k_plan_pair_cols<<<grid_for(P.npairs, kThreads, g), kThreads, 0, st>>>(pair_h, P.npairs, P.heavy_cols,
+                                                                          P.pair_col);
   GENCD_CUDA_TRY(cudaGetLastError());
 
   // tiles inside each slab, and contiguous runs of tiles per CTA
@@ -1213,8 +1119,8 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
   // the autotuner below decides
   P.fused_split = 0;
   if (!f64 && P.nlight > 0 && P.nheavy > 0) {
-    GENCD_TRY(palloc(p, &P.light_counter, 1));
-    GENCD_CUDA_TRY(cudaMemsetAsync(P.light_counter, 0, sizeof(unsigned int), st));
+    GENCD_TRY(palloc(p, &P.light_counter, 2));  // tiles taken, warps finished
+    GENCD_CUDA_TRY(cudaMemsetAsync(P.light_counter, 0, 2 * sizeof(unsigned int), st));
   }
   std::vector<int32_t> ctb(P.grid + 1);
   for (int b = 0; b <= P.grid; ++b) ctb[b] = (int32_t)((int64_t)b * P.ntiles / P.grid);
