@@ -95,7 +95,7 @@ def parse():
     ap.add_argument("--path-ratio", type=float, default=1e-2,
                     help="smallest lambda / lambda_max of the path (below ~1/250 on this workload the solutions "
                          "near interpolation and Thread-Greedy stalls)")
-    ap.add_argument("--path-plain", type=int, default=2,
+    ap.add_argument("--path-plain", type=int, default=5,
                     help="also time the one-solve-per-call form on this many folds' chains (0: skip it)")
     ap.add_argument("--serve", type=int, default=1, help="add the serving-stream measurement (0/1)")
     ap.add_argument("--serve-requests", type=int, default=24)
@@ -392,8 +392,9 @@ def run_path(args, gb, stream):
     gaps_b = _certify_path(gb, prob, fold, F, lam, W_b.reshape(F, L, -1), stream)
     out["batched"]["certified_rel_gap_max"] = float(np.nanmax(gaps_b[st_b == 0])) if (st_b == 0).any() else None
     if args.path_plain:
-        # the plain form on the first --path-plain folds' chains (its solves/s
-        # is per solve, so a subset keeps the benchmark short)
+        # the plain form on the first --path-plain folds' chains (default: all
+        # of them, the batched form's work; the folds' chains differ in
+        # difficulty, so a subset would not compare like with like)
         Fp = max(1, min(F, args.path_plain))
         subs = [workloads.row_subset(prob, np.flatnonzero(fold != f)) for f in range(Fp)]  # host prep, untimed
         P_p = np.zeros((Fp, L))
