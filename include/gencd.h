@@ -303,11 +303,12 @@ int gencd_permutation(gencd_problem* p, uint64_t seed, int64_t epoch, int64_t m,
 
 /* Kernel launch counts and, when profiling is enabled, summed device time
  * (ms, CUDA events on the problem's stream) and number of timed invocations
- * per kernel family: 0 streaming propose (the whole family 9 + 10 + 11, or
- * 12 + 11), 1 finalize, 2 accept, 3 update, 4 refresh, 5 list propose,
- * 6 Coloring iteration, 7 objective, 8 setup/selection, 9 light-column pass,
- * 10 row-slab pass, 11 partial-sum reduction, 12 row-slab and light-column
- * passes in one kernel.  ms / calls is the mean duration of one
+ * per kernel family: 0 streaming propose (the whole family: 9 + 10, or 12,
+ * and 11 with index-only storage), 1 finalize, 2 accept, 3 update,
+ * 4 refresh, 5 list propose, 6 Coloring iteration, 7 objective,
+ * 8 setup/selection, 9 light-column pass, 10 row-slab pass, 11 the heavy
+ * columns' g_j times their value (index-only storage), 12 row-slab and
+ * light-column passes in one kernel.  ms / calls is the mean duration of one
  * invocation; ms, launches, calls may be NULL. */
 int gencd_profile_enable(gencd_problem* p, int32_t enable);
 int gencd_profile_read(gencd_problem* p, int32_t kernel, double* ms, int64_t* launches, int64_t* calls);

@@ -39,7 +39,7 @@ VARIANTS = {"shotgun": GENCD_SHOTGUN, "thread_greedy": GENCD_THREAD_GREEDY, "gre
             "coloring": GENCD_COLORING, "top_greedy": GENCD_TOP_GREEDY, "shotgun_blocks": GENCD_SHOTGUN_BLOCKS}
 PRECISIONS = {"f64": GENCD_F64, "f32": GENCD_F32, "bf16": GENCD_BF16, "binary": GENCD_BINARY}
 KERNELS = ["propose_all", "finalize", "accept", "update", "refresh", "propose_list", "coloring_iter",
-           "objective", "setup", "propose_light", "propose_slabs", "pairs_reduce", "propose_fused"]
+           "objective", "setup", "propose_light", "propose_slabs", "scale_heavy", "propose_fused"]
 
 # every symbol include/gencd.h declares
 EXPORTS = ["gencd_create", "gencd_destroy", "gencd_set_lambda", "gencd_set_loss", "gencd_lambda_max",

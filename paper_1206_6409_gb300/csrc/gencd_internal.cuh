@@ -75,7 +75,7 @@ enum KernelId {
   K_SETUP,            // one-time and selection kernels
   K_PROPOSE_LIGHT,    // streaming propose: lane-segmented pass over the light columns
   K_PROPOSE_SLABS,    // streaming propose: row-slab pass over the heavy columns
-  K_PAIRS,            // (not launched: the row-slab pass adds each partial into g_j itself)
+  K_SCALE_HEAVY,      // streaming propose, index-only storage: heavy columns' g_j times their value
   K_PROPOSE_FUSED,    // streaming propose: row-slab and light passes in one kernel
   K_NUM
 };

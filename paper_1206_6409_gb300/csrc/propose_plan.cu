@@ -78,10 +78,10 @@ __device__ __forceinline__ void emit_pair(G* __restrict__ out, uint32_t slot, G 
 struct NoVal {};
 
 // a heavy column's run sum into g_j: other slabs and tiles add to the same
-// column, so always atomically; index-only storage scales by the column's value
-template <typename G, typename SV>
-__device__ __forceinline__ void add_col(G* __restrict__ gacc, const float* __restrict__ cscale, uint32_t j, G v) {
-  if (std::is_same<SV, NoVal>::value) v *= (G)__ldg(cscale + j);
+// column, so always atomically (index-only storage: the sum of u over the
+// column's rows; k_scale_heavy applies the column's value afterwards)
+template <typename G>
+__device__ __forceinline__ void add_col(G* __restrict__ gacc, uint32_t j, G v) {
   atomicAdd(gacc + j, v);
 }
 
@@ -222,8 +222,7 @@ __device__ __forceinline__ void slab_pass(const uint16_t* __restrict__ s_row, co
                                           const int32_t* __restrict__ tile_slab,
                                           const int32_t* __restrict__ slab_tile_begin, int t0, const int t_end,
                                           const U* __restrict__ u, int64_t n, int32_t slab_rows,
-                                          G* __restrict__ gacc, const float* __restrict__ cscale, U* s_u,
-                                          const int warp, const int nw,
+                                          G* __restrict__ gacc, U* s_u, const int warp, const int nw,
                                           const int gtid, const int gthreads) {
   constexpr int TILE = 32 * ITEMS;
   constexpr uint32_t NOT_FIRST = ((1u << ITEMS) - 1u) & ~1u;  // start bits after a lane's first entry
@@ -312,7 +311,7 @@ __device__ __forceinline__ void slab_pass(const uint16_t* __restrict__ s_row, co
             if (i == bf)
               first = acc;
             else
-              add_col<G, SV>(gacc, cscale, __ldg(pair_col + qi), (G)acc);  // started and ended inside the lane
+              add_col<G>(gacc, __ldg(pair_col + qi), (G)acc);  // started and ended inside the lane
             acc = V(0);
             ++qi;
           }
@@ -320,7 +319,7 @@ __device__ __forceinline__ void slab_pass(const uint16_t* __restrict__ s_row, co
         }
         if (inner) {
           if (m & 1u)
-            add_col<G, SV>(gacc, cscale, __ldg(pair_col + q), (G)first);  // started at entry 0, ended inside
+            add_col<G>(gacc, __ldg(pair_col + q), (G)first);  // started at entry 0, ended inside
           else
             cont = first;  // continues from the left
           tail = acc;  // the last run started inside the lane
@@ -336,13 +335,13 @@ __device__ __forceinline__ void slab_pass(const uint16_t* __restrict__ s_row, co
       if (__ballot_sync(FULL, stop) == 0u) {
         // the whole tile lies inside pair q0
         const V sum = warp_sum(cont);
-        if (lane == 0) add_col<G, SV>(gacc, cscale, col0, (G)sum);
+        if (lane == 0) add_col<G>(gacc, col0, (G)sum);
       } else {
         bool ended;
         const V tsum = lane_suffix_sum(cont, stop, lane, ended);
         const V t1s = __shfl_down_sync(FULL, tsum, 1);
-        if (lead) add_col<G, SV>(gacc, cscale, col0, (G)tsum);  // pair from the previous tile
-        if (has_tail) add_col<G, SV>(gacc, cscale, col_last, (G)(tail + (lane < 31 ? t1s : V(0))));
+        if (lead) add_col<G>(gacc, col0, (G)tsum);  // pair from the previous tile
+        if (has_tail) add_col<G>(gacc, col_last, (G)(tail + (lane < 31 ? t1s : V(0))));
       }
     }
     t0 = t1;
@@ -358,12 +357,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const uint32_t* __restrict__ tile_end, const uint32_t* __restrict__ tile_pair,
                     const int32_t* __restrict__ tile_slab, const int32_t* __restrict__ slab_tile_begin,
                     const int32_t* __restrict__ cta_tile_begin, const U* __restrict__ u, int64_t n,
-                    int32_t slab_rows, G* __restrict__ gacc, const float* __restrict__ cscale) {
+                    int32_t slab_rows, G* __restrict__ gacc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   U* s_u = reinterpret_cast<U*>(smem_raw);
   slab_pass<V, U, G, DEPTH, ITEMS, SV, 0>(s_row, s_val, pmask, pair_col, tile_start, tile_end, tile_pair, tile_slab,
                                           slab_tile_begin, cta_tile_begin[blockIdx.x],
-                                          cta_tile_begin[blockIdx.x + 1], u, n, slab_rows, gacc, cscale, s_u,
+                                          cta_tile_begin[blockIdx.x + 1], u, n, slab_rows, gacc, s_u,
                                           threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x, blockDim.x);
 }
 
@@ -574,14 +573,14 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const uint8_t* __restrict__ lmask, const int32_t* __restrict__ tile_lc,
                     const int32_t* __restrict__ light_cols, const float* __restrict__ lscale, int64_t lnnz,
                     int64_t lntiles, unsigned int* counter, const U* __restrict__ u, int64_t n, int32_t slab_rows,
-                    G* __restrict__ gacc, const float* __restrict__ cscale) {
+                    G* __restrict__ gacc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   U* s_u = reinterpret_cast<U*>(smem_raw);
   const int warp = threadIdx.x >> 5;
   if (warp < SLAB_WARPS)
     slab_pass<V, U, G, DEPTH, ITEMS, SV, 32 * SLAB_WARPS>(
         s_row, s_val, pmask, pair_col, tile_start, tile_end, tile_pair, tile_slab, slab_tile_begin,
-        cta_tile_begin[blockIdx.x], cta_tile_begin[blockIdx.x + 1], u, n, slab_rows, gacc, cscale, s_u, warp, SLAB_WARPS,
+        cta_tile_begin[blockIdx.x], cta_tile_begin[blockIdx.x + 1], u, n, slab_rows, gacc, s_u, warp, SLAB_WARPS,
         threadIdx.x, 32 * SLAB_WARPS);
   light_pool<V, U, G, SV>(lrow, lval, lmask, tile_lc, light_cols, lscale, u, lnnz, lntiles, gacc, counter);
   // the last warp out resets the pool for the next launch: every warp has
@@ -594,6 +593,31 @@ __global__ void __launch_bounds__(THREADS, 1)
       counter[1] = 0u;
     }
   }
+}
+
+// index-only storage: g_j of every heavy column times the column's value
+// (the row-slab pass adds the sums of u over the column's rows)
+template <typename G>
+__global__ void k_scale_heavy(const int32_t* __restrict__ heavy_cols, int64_t nheavy,
+                              const float* __restrict__ col_val, G* __restrict__ gacc) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nheavy; h += stride) {
+    const int32_t j = heavy_cols[h];
+    gacc[j] *= (G)col_val[j];
+  }
+}
+
+template <typename G, typename SV>
+static int scale_heavy(gencd_problem* p) {
+  ProposePlan& P = p->plan;
+  if (!std::is_same<SV, NoVal>::value || P.nheavy == 0) return GENCD_OK;
+  cudaEvent_t e = nullptr;
+  prof_begin(p, K_SCALE_HEAVY, &e);
+  k_scale_heavy<G><<<grid_for(P.nheavy, kThreads, p->num_sms * 8), kThreads, 0, p->stream>>>(
+      P.heavy_cols, P.nheavy, p->col_val, (G*)p->gnat);
+  prof_end(p, e);
+  GENCD_CUDA_TRY(cudaGetLastError());
+  return GENCD_OK;
 }
 
 // the two streaming passes for one value storage SV (V compute type, U type
@@ -612,7 +636,7 @@ static void launch_fused(gencd_problem* p, const void* u_vec, size_t smem) {
       P.s_row, (const SV*)P.s_val, P.pmask, P.pair_col, P.tile_start, P.tile_end, P.tile_pair, P.tile_slab,
       P.slab_tile_begin, P.cta_tile_begin, P.light_row, (const SV*)P.light_val, P.lmask, P.light_tile_lc,
       P.light_cols, P.light_scale, P.light_nnz, P.light_ntiles, P.light_counter, (const U*)u_vec, p->n,
-      P.slab_rows, (G*)p->gnat, p->col_val);
+      P.slab_rows, (G*)p->gnat);
 }
 
 template <typename V, typename U, typename G, typename SV, int THREADS, int DEPTH, int ITEMS>
@@ -630,7 +654,7 @@ static int launch_plan_passes(gencd_problem* p, const void* u_vec) {
     }
     prof_end(p, e1);
     GENCD_CUDA_TRY(cudaGetLastError());
-    return GENCD_OK;
+    return scale_heavy<G, SV>(p);
   }
   if (P.nlight > 0) {
     cudaEvent_t e = nullptr;
@@ -648,11 +672,11 @@ static int launch_plan_passes(gencd_problem* p, const void* u_vec) {
     prof_begin(p, K_PROPOSE_SLABS, &e1);
     k_propose_slabs<V, U, G, THREADS, DEPTH, ITEMS, SV><<<P.grid, THREADS, smem, p->stream>>>(
         P.s_row, (const SV*)P.s_val, P.pmask, P.pair_col, P.tile_start, P.tile_end, P.tile_pair, P.tile_slab,
-        P.slab_tile_begin, P.cta_tile_begin, (const U*)u_vec, p->n, P.slab_rows, (G*)p->gnat, p->col_val);
+        P.slab_tile_begin, P.cta_tile_begin, (const U*)u_vec, p->n, P.slab_rows, (G*)p->gnat);
     prof_end(p, e1);
     GENCD_CUDA_TRY(cudaGetLastError());
   }
-  return GENCD_OK;
+  return scale_heavy<G, SV>(p);
 }
 
 template <typename V, typename U, typename G, typename SV, int THREADS, int DEPTH, int ITEMS>
@@ -1072,7 +1096,7 @@ static int build_plan_impl(gencd_problem* p, Scratch& S) {
     } else {
       GENCD_CUDA_TRY(cudaStreamSynchronize(st));
       dev_free(p, P.s_val);
-      P.s_val = nullptr;  // the row-slab pass scales each run sum by col_val[j]
+      P.s_val = nullptr;  // k_scale_heavy applies col_val[j] after the pass
     }
     GENCD_CUDA_TRY(cudaGetLastError());
   }
