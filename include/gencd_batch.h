@@ -154,8 +154,9 @@ int gencd_batch_propose(gencd_batch* b, double* delta, double* phi, int32_t memo
  * restarts from its start with 4G; checks covering 500 iterations in a row
  * with neither a new lowest objective (by 1e-12 of itself) nor a KKT
  * violation 1% below the lowest since the (re)start double G while the
- * violation is at least 1e-3 lambda.  A chain's next solve starts at half the G its predecessor
- * reached.
+ * violation is at least 1e-3 lambda.  A chain's next solve starts at half
+ * the G its predecessor reached, or at G = 1 after a solve of the chain that
+ * did not converge.
  */
 typedef struct {
   int32_t nchains;         /* chains (e.g. cross-validation folds)            */

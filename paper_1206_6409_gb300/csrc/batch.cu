@@ -1736,7 +1736,11 @@ static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* 
     return GENCD_ENOMEM;
   }
   std::vector<int> next(C, 0), ready(C, 1), pred_slot(C, -1), slot_solve(S, -1), last_q(C, -1);
-  std::vector<int> chain_group(C, 1), obj_wait(S, 0), stall(S, 0);
+  // a chain's next solve starts at half the accept group its live solves
+  // reached, unless one of them started before the chain's last solve that
+  // did not converge (fails[c]; slot_epoch: the count at the slot's start):
+  // after such a solve the chain starts again from G = 1
+  std::vector<int> chain_group(C, 1), obj_wait(S, 0), stall(S, 0), fails(C, 0), slot_epoch(S, 0);
   std::vector<int64_t> slot_iters(S, 0);
   std::vector<double> best_v(S, HUGE_VAL), best_p(S, HUGE_VAL), p_start(S, HUGE_VAL);
   const int g_sm = b->X->num_sms * 8;
@@ -1770,6 +1774,7 @@ static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* 
         k_b_get_w<<<grid_for(b->k, kThreads, g_sm), kThreads, 0, b->st>>>(b->w, b->k, S, s,
                                                                            w_start + (size_t)s * b->k);
       slot_solve[s] = q;
+      slot_epoch[s] = fails[c];
       slot_iters[s] = 0;
       obj_wait[s] = 0;
       stall[s] = 0;
@@ -1889,8 +1894,11 @@ static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* 
       obj_wait[s] = 0;
       stall[s] = 0;
     }
-    for (int s = 0; s < S; ++s)
-      if (slot_solve[s] >= 0) chain_group[slot_solve[s] / L] = std::max(1, b->h_group[s] / 2);
+    for (int s = 0; s < S; ++s) {
+      if (slot_solve[s] < 0) continue;
+      const int c = slot_solve[s] / L;
+      if (slot_epoch[s] == fails[c]) chain_group[c] = std::max(1, b->h_group[s] / 2);
+    }
     if (regroup) rc = upload_slots(b);
     if (rc != GENCD_OK || retire.empty()) continue;
     std::vector<double> ob;
@@ -1900,7 +1908,11 @@ static int batch_path(gencd_batch* b, const gencd_path* path, gencd_path_solve* 
       solves[q].objective = ob[r];
       solves[q].t_end = secs();
       solves[q].group = b->h_group[s];
-      if (solves[q].status != GENCD_OK) all_ok = 0;
+      if (solves[q].status != GENCD_OK) {
+        all_ok = 0;
+        fails[c] += 1;
+        chain_group[c] = 1;
+      }
       // the chain's latest finished lambda is the warm start of the solves still to come
       double* dst = q > last_q[c] ? w_last + (size_t)c * b->k : b->tmp_k;
       if (q > last_q[c]) last_q[c] = q;
